@@ -1,0 +1,227 @@
+"""FP64 CPU oracle of the scene-space gather-and-filter (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import this
+package.  It shares no code with the CUDA path (``paper_2102_03011_gb300``) and neither imports
+the other; the only common dependency is the seeded input generator ``synth``.
+
+The arithmetic lives in ``oracle.c`` (plain C, double precision, OpenMP over output pixels);
+this module marshals arrays and holds the two steps that are plain library primitives:
+the lower median of the valid input depths (a sort) and the derived default parameters.
+
+Readings of the paper used here (Sec. "Denoising", Eq. 4; Sec. "Sample Gathering", Eq. 2):
+  * depth is camera-space z; integer pixel coordinates are pixel centres;
+  * the radius r defaults to 0.5 % of the clip's lower-median valid input depth;
+  * colour is in [0, 1], so sigma_rgb = 40 / 255; sigma_f = 6 frames; sigma_xyz = r;
+  * the k x k window is centred on floor(x + 0.5) of the projected reference point.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libssvp_oracle.so")
+_lib = None
+
+MODE_DENOISE, MODE_APERTURE, MODE_MEAN = 0, 1, 3
+CODE_OUT, CODE_INVALID, CODE_REJECT, CODE_ACCEPT, CODE_BAND = 0, 1, 2, 3, 8
+
+
+class _Clip(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("F", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("rgb", ctypes.POINTER(ctypes.c_float)), ("depth", ctypes.POINTER(ctypes.c_float)),
+                ("K", ctypes.POINTER(ctypes.c_double)), ("w2c", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("k", ctypes.c_int32), ("T", ctypes.c_int32),
+                ("lens_samples", ctypes.c_int32), ("radius", ctypes.c_double), ("sigma_rgb", ctypes.c_double),
+                ("sigma_xyz", ctypes.c_double), ("sigma_f", ctypes.c_double), ("band_rel", ctypes.c_double),
+                ("tie_band", ctypes.c_double), ("aperture", ctypes.c_double), ("focal_depth", ctypes.c_double),
+                ("a0", ctypes.c_double), ("cap", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into libssvp_oracle.so (gcc -O2, OpenMP, no FMA contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                           "-o", tmp, src, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        dp, fp = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
+        i32p, u8p, i64p = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_int64)
+        lib.oc_compose.argtypes = [dp, dp, dp, dp, ctypes.c_int, dp, dp]
+        lib.oc_weight_denoise.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.oc_weight_denoise.restype = ctypes.c_double
+        lib.oc_filter.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, dp]
+        lib.oc_filter.restype = ctypes.c_double
+        lib.oc_gather_filter.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, i64p, i64p, i32p, i32p,
+                                         u8p, u8p, i32p]
+        lib.oc_bruteforce.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, u8p]
+        lib.oc_bruteforce.restype = ctypes.c_longlong
+        _lib = lib
+    return _lib
+
+
+def _p(a, t):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(t))
+
+
+@dataclass
+class Params:
+    """Gather-and-filter parameters as the oracle reads them (absolute radius)."""
+    mode: int = MODE_DENOISE
+    k: int = 7
+    T: int = 15
+    radius: float = 0.025
+    sigma_rgb: float = 40.0 / 255.0
+    sigma_xyz: float | None = None      # None: equal to the radius
+    sigma_f: float = 6.0
+    band_rel: float = 1e-5
+    tie_band: float = 1e-3
+    aperture: float = 0.05
+    focal_depth: float = 5.0
+    a0: float | None = None             # None: half a pixel footprint at the focal depth (0.5 z0 / fx)
+    lens_samples: int = 16
+    cap: int = 31
+
+    def c_struct(self, fx: float) -> _Params:
+        s = _Params()
+        s.mode, s.k, s.T, s.lens_samples = self.mode, self.k, self.T, self.lens_samples
+        s.radius = self.radius
+        s.sigma_rgb, s.sigma_f = self.sigma_rgb, self.sigma_f
+        s.sigma_xyz = self.radius if self.sigma_xyz is None else self.sigma_xyz
+        s.band_rel, s.tie_band = self.band_rel, self.tie_band
+        s.aperture, s.focal_depth = self.aperture, self.focal_depth
+        s.a0 = 0.5 * self.focal_depth / fx if self.a0 is None else self.a0
+        s.cap = self.cap
+        return s
+
+
+class ClipView:
+    """Keeps contiguous copies of a clip's arrays alive for the C side."""
+
+    def __init__(self, rgb, depth, K, w2c):
+        self.rgb = np.ascontiguousarray(rgb, dtype=np.float32)
+        self.depth = np.ascontiguousarray(depth, dtype=np.float32)
+        F, H, W = self.depth.shape
+        self.K = np.ascontiguousarray(np.broadcast_to(K, (F, 3, 3)), dtype=np.float64)
+        self.w2c = np.ascontiguousarray(w2c, dtype=np.float64)
+        assert self.rgb.shape == (F, H, W, 3) and self.w2c.shape == (F, 3, 4)
+        self.F, self.H, self.W = F, H, W
+        s = _Clip()
+        s.W, s.H, s.F = W, H, F
+        s.rgb, s.depth = _p(self.rgb, ctypes.c_float), _p(self.depth, ctypes.c_float)
+        s.K, s.w2c = _p(self.K, ctypes.c_double), _p(self.w2c, ctypes.c_double)
+        self.c = s
+
+    @classmethod
+    def of(cls, clip):
+        return cls(clip.rgb, clip.depth, clip.K, clip.w2c)
+
+
+def median_depth(depth) -> float:
+    """Lower median (rank floor((n-1)/2) of the sorted values) of the finite, positive depths."""
+    d = np.asarray(depth, dtype=np.float32).reshape(-1)
+    d = d[np.isfinite(d) & (d > 0)]
+    if d.size == 0:
+        raise ValueError("no valid depth")
+    return float(np.sort(d)[(d.size - 1) // 2])
+
+
+def default_params(clip_depth, mode=MODE_DENOISE, k=7, T=15, radius_rel=0.005, **kw) -> Params:
+    r = radius_rel * median_depth(clip_depth)
+    return Params(mode=mode, k=k, T=T, radius=r, **kw)
+
+
+def compose(K_O, w2c_O, K_J, w2c_J, same: bool):
+    """A1: returns (P_{J<-O}, G_{O<-J}) as 3x4 float64 arrays."""
+    P, G = np.zeros((3, 4)), np.zeros((3, 4))
+    args = [np.ascontiguousarray(a, dtype=np.float64) for a in (K_O, w2c_O, K_J, w2c_J)]
+    _load().oc_compose(*[_p(a, ctypes.c_double) for a in args], int(same), _p(P, ctypes.c_double),
+                       _p(G, ctypes.c_double))
+    return P, G
+
+
+def weight_denoise(s, sref, sigma_rgb, sigma_xyz, sigma_f) -> float:
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    r = np.ascontiguousarray(sref, dtype=np.float64)
+    return _load().oc_weight_denoise(_p(s, ctypes.c_double), _p(r, ctypes.c_double), sigma_rgb, sigma_xyz, sigma_f)
+
+
+def filter_samples(S, sref, mode, sigma_rgb, sigma_xyz, sigma_f):
+    """Eq. 3 over an explicit sample set S (n, 7) -> (colour (3,), W)."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    r = np.ascontiguousarray(sref, dtype=np.float64)
+    out = np.zeros(3)
+    W = _load().oc_filter(_p(S, ctypes.c_double), len(S), _p(r, ctypes.c_double), mode, sigma_rgb, sigma_xyz,
+                          sigma_f, _p(out, ctypes.c_double))
+    return out, W
+
+
+@dataclass
+class Result:
+    rgb: np.ndarray          # (ch, cw, 3) float64
+    sumw: np.ndarray         # (ch, cw)
+    nacc: np.ndarray         # (ch, cw) int64
+    nexam: np.ndarray        # (ch, cw) int64
+    status: np.ndarray | None = None   # (ch, cw, 2T+1) int32
+    centre: np.ndarray | None = None   # (ch, cw, 2T+1, 2) int32
+    amb: np.ndarray | None = None      # (ch, cw, 2T+1) uint8
+    codes: np.ndarray | None = None    # (ch, cw, 2T+1, k, k) uint8
+    box: np.ndarray | None = None      # (ch, cw, 2T+1, 4) int32 (aperture)
+
+
+def gather_filter(view: ClipView, prm: Params, O: int, crop=None, membership: bool = False) -> Result:
+    """Run the oracle on output frame O over crop (x0, y0, w, h) (default: the full frame)."""
+    x0, y0, cw, ch = crop if crop is not None else (0, 0, view.W, view.H)
+    n, ns, k = cw * ch, 2 * prm.T + 1, prm.k
+    out = np.zeros((ch, cw, 3))
+    sumw = np.zeros((ch, cw))
+    nacc = np.zeros((ch, cw), np.int64)
+    nexam = np.zeros((ch, cw), np.int64)
+    st = ce = am = co = bx = None
+    if membership:
+        st = np.full((ch, cw, ns), -9, np.int32)
+        ce = np.zeros((ch, cw, ns, 2), np.int32)
+        am = np.zeros((ch, cw, ns), np.uint8)
+        co = np.zeros((ch, cw, ns, k, k), np.uint8)
+        bx = np.zeros((ch, cw, ns, 4), np.int32)
+    ps = prm.c_struct(float(view.K[O, 0, 0]))
+    rc = _load().oc_gather_filter(ctypes.byref(view.c), ctypes.byref(ps), O, x0, y0, cw, ch,
+                                  _p(out, ctypes.c_double), _p(sumw, ctypes.c_double), _p(nacc, ctypes.c_int64),
+                                  _p(nexam, ctypes.c_int64), _p(st, ctypes.c_int32), _p(ce, ctypes.c_int32),
+                                  _p(am, ctypes.c_uint8), _p(co, ctypes.c_uint8), _p(bx, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments (code {rc})")
+    return Result(out, sumw, nacc, nexam, st, ce, am, co, bx)
+
+
+def bruteforce(view: ClipView, prm: Params, O: int, u: int, v: int, J: int) -> np.ndarray:
+    """(H, W) uint8 map of every pixel of frame J within the radius of pixel (u, v) of frame O."""
+    acc = np.zeros((view.H, view.W), np.uint8)
+    ps = prm.c_struct(float(view.K[O, 0, 0]))
+    _load().oc_bruteforce(ctypes.byref(view.c), ctypes.byref(ps), O, u, v, J, _p(acc, ctypes.c_uint8))
+    return acc
+
+
+def psnr(a, b) -> float:
+    """10 log10(1 / MSE) over all values, peak 1, no clipping."""
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse)

@@ -1,0 +1,423 @@
+/*
+ * oracle.c - FP64 CPU oracle of the scene-space gather-and-filter.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg may call it.  It shares no code with the CUDA path and is not a fallback for it.
+ *
+ * It is the plain definition, written out in double precision, one output pixel at a time:
+ *
+ *   A1  camera composition (Sec. "Sample Gathering", Eq. 2 uses C_O * C_J^-1):
+ *         P_{J<-O} = K_J [R_J R_O^T | t_J - R_J R_O^T t_O]          O-camera point -> J pixel (homog.)
+ *         G_{O<-J} = [R_O R_J^T K_J^-1 | t_O - R_O R_J^T t_J]       (q_x d, q_y d, d, 1) in J -> O camera
+ *       with P = [K_O | 0] and G = [K_O^-1 | 0] set directly when J = O.
+ *   A3  reference sample s_ref (Sec. "Denoising"): x_ref = D_O(p) K_O^-1 [u, v, 1], c_ref = I_O(p).
+ *   A4  project x_ref into every frame J of the temporal window [O-T, O+T]; the k x k window is
+ *       centred on (floor(x'/z' + 0.5), floor(y'/z' + 0.5)); frames with z' <= 1e-6 d_ref are
+ *       skipped, window pixels outside the image are skipped.
+ *   A5  candidate q with valid depth d_q (finite, > 0): X_q = G (q_x d_q, q_y d_q, d_q, 1);
+ *       accepted into S(p) iff |X_q - x_ref|^2 < r^2 (strict).
+ *   A6  weight w(s) of Eq. 4 with diagonal covariance: exp(-sum over the 7 dimensions of the
+ *       squared difference to s_ref over 2 sigma_d^2), sigma_rgb on colour, sigma_xyz on scene
+ *       position, sigma_f on frame time; mode "mean" uses w = 1 (the averaging of Sec. "Denoising").
+ *   A7  Eq. 3: O(p) = sum_s w(s) s_rgb / sum_s w(s).  An invalid reference depth gives c_ref.
+ *
+ * Virtual aperture (Sec. "Virtual aperture", Eq. 13-14) with the thin-lens footprint reading:
+ *   cone around the central ray of p (from the O camera centre through K_O^-1 [u, v, 1]);
+ *   r_al = distance of X_q along the ray, q_perp = distance of X_q to the ray;
+ *   a(r_al) = a0 + A |z0 - r_al| / z0 (Eq. 13 with slope A / z0);
+ *   per frame J the window is the bounding box of the projections of the n_lens seed points
+ *   (lens point L_i on a Vogel disc of radius A, ray L_i -> z0 K_O^-1 [u, v, 1], seed point at
+ *   camera z = d_ref), grown by h on each side and capped at `cap` pixels per axis around the
+ *   rounded centroid; accepted iff q_perp < a(r_al); weight s_area / (pi a(r_al)^2) with
+ *   s_area the squared scene length of one pixel edge of q (Eq. 6), i.e. (d_q / fx_J)^2 for a
+ *   camera without skew.  Output sum w c / sum w, or c_ref when nothing is accepted.
+ *
+ * Built with -ffp-contract=off: every product and sum is rounded on its own.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t W, H, F, pad_;
+    const float *rgb;    /* F*H*W*3, interleaved, row-major */
+    const float *depth;  /* F*H*W camera z */
+    const double *K;     /* F*9 intrinsics, row-major */
+    const double *w2c;   /* F*12 world->camera [R|t], row-major */
+} oc_clip;
+
+typedef struct {
+    int32_t mode;        /* 0 denoise (Eq. 4), 1 virtual aperture (Eq. 13-14), 3 mean (w = 1) */
+    int32_t k;           /* odd window width */
+    int32_t T;           /* temporal half window */
+    int32_t lens_samples;
+    double radius;       /* absolute radius r */
+    double sigma_rgb, sigma_xyz, sigma_f;
+    double band_rel;     /* |dist - r| <= band_rel * r marks a candidate as "in band" */
+    double tie_band;     /* |frac(x) - 0.5| < tie_band marks a window centre as ambiguous */
+    double aperture;     /* A: lens radius (scene units) */
+    double focal_depth;  /* z0 */
+    double a0;           /* cone waist */
+    int32_t cap;         /* aperture footprint cap per axis (pixels) */
+    int32_t pad_;
+} oc_params;
+
+/* membership codes (low 3 bits) and band flag */
+#define OC_OUT 0       /* window pixel outside the image */
+#define OC_INVALID 1   /* invalid depth */
+#define OC_REJECT 2
+#define OC_ACCEPT 3
+#define OC_BAND 8      /* or-ed in when |dist - r| <= band_rel * r (or the cone analogue) */
+
+/* ------------------------------------------------------------------ small linear algebra */
+
+static void mat3_inverse(const double *A, double *B) {
+    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    B[0] = c00 / det;
+    B[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    B[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    B[3] = c01 / det;
+    B[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    B[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    B[6] = c02 / det;
+    B[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    B[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+}
+
+static void mat3_mul(const double *A, const double *B, double *C) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
+static void mat3_vec(const double *A, const double *x, double *y) {
+    for (int i = 0; i < 3; ++i) y[i] = A[3 * i] * x[0] + A[3 * i + 1] * x[1] + A[3 * i + 2] * x[2];
+}
+
+static void split_rt(const double *w2c, double *R, double *t) {
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) R[3 * i + j] = w2c[4 * i + j];
+        t[i] = w2c[4 * i + 3];
+    }
+}
+
+/* apply a 3x4 matrix to (x, 1) */
+static void apply34(const double *M, const double *x, double *y) {
+    for (int i = 0; i < 3; ++i) y[i] = M[4 * i] * x[0] + M[4 * i + 1] * x[1] + M[4 * i + 2] * x[2] + M[4 * i + 3];
+}
+
+/* A1: P_{J<-O} and G_{O<-J} (both 3x4 row-major). */
+void oc_compose(const double *K_O, const double *w2c_O, const double *K_J, const double *w2c_J, int same,
+                double *P, double *G) {
+    if (same) {
+        double Ki[9];
+        mat3_inverse(K_O, Ki);
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) { P[4 * i + j] = K_O[3 * i + j]; G[4 * i + j] = Ki[3 * i + j]; }
+            P[4 * i + 3] = 0.0;
+            G[4 * i + 3] = 0.0;
+        }
+        return;
+    }
+    double RO[9], tO[3], RJ[9], tJ[3], ROt[9], RJt[9], RJO[9], ROJ[9], KJi[9], M[9], tmp[3];
+    split_rt(w2c_O, RO, tO);
+    split_rt(w2c_J, RJ, tJ);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) { ROt[3 * i + j] = RO[3 * j + i]; RJt[3 * i + j] = RJ[3 * j + i]; }
+    /* P = K_J [R_J R_O^T | t_J - R_J R_O^T t_O] */
+    mat3_mul(RJ, ROt, RJO);
+    mat3_vec(RJO, tO, tmp);
+    double tJO[3] = {tJ[0] - tmp[0], tJ[1] - tmp[1], tJ[2] - tmp[2]};
+    mat3_mul(K_J, RJO, M);
+    double KtJO[3];
+    mat3_vec(K_J, tJO, KtJO);
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) P[4 * i + j] = M[3 * i + j];
+        P[4 * i + 3] = KtJO[i];
+    }
+    /* G = [R_O R_J^T K_J^-1 | t_O - R_O R_J^T t_J] */
+    mat3_mul(RO, RJt, ROJ);
+    mat3_inverse(K_J, KJi);
+    mat3_mul(ROJ, KJi, M);
+    mat3_vec(ROJ, tJ, tmp);
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) G[4 * i + j] = M[3 * i + j];
+        G[4 * i + 3] = tO[i] - tmp[i];
+    }
+}
+
+/* ------------------------------------------------------------------ weights and filter */
+
+/* Eq. 4 with diagonal covariance: s = (r, g, b, x, y, z, f). */
+double oc_weight_denoise(const double *s, const double *sref, double sigma_rgb, double sigma_xyz, double sigma_f) {
+    double e = 0.0;
+    for (int i = 0; i < 3; ++i) e += (sref[i] - s[i]) * (sref[i] - s[i]) / (2.0 * sigma_rgb * sigma_rgb);
+    for (int i = 3; i < 6; ++i) e += (sref[i] - s[i]) * (sref[i] - s[i]) / (2.0 * sigma_xyz * sigma_xyz);
+    e += (sref[6] - s[6]) * (sref[6] - s[6]) / (2.0 * sigma_f * sigma_f);
+    return exp(-e);
+}
+
+/* Eq. 3 over an explicit sample set S (n x 7) with Eq. 4 weights (mode 0) or w = 1 (mode 3).
+ * Writes the colour and returns W = sum of weights. */
+double oc_filter(const double *S, int n, const double *sref, int mode, double sigma_rgb, double sigma_xyz,
+                 double sigma_f, double *out) {
+    double acc[3] = {0, 0, 0}, W = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double w = mode == 3 ? 1.0 : oc_weight_denoise(S + 7 * i, sref, sigma_rgb, sigma_xyz, sigma_f);
+        for (int c = 0; c < 3; ++c) acc[c] += w * S[7 * i + c];
+        W += w;
+    }
+    for (int c = 0; c < 3; ++c) out[c] = acc[c] / W;
+    return W;
+}
+
+static int valid_depth(float d) { return isfinite(d) && d > 0.0f; }
+
+/* ------------------------------------------------------------------ gather + filter, one pixel */
+
+typedef struct {
+    int32_t *status;  /* per slot: -2 invalid reference, -1 frame outside clip, 0 skipped (behind), 1 gathered */
+    int32_t *centre;  /* per slot: window centre (x, y) */
+    uint8_t *amb;     /* per slot: 1 if the window centre is within tie_band of a rounding tie */
+    uint8_t *codes;   /* per slot: k*k membership codes (row-major window) */
+    int32_t *box;     /* aperture: per slot window box (x0, y0, x1, y1) inclusive */
+} oc_member;
+
+/* Vogel-disc lens point i of n, radius A */
+static void lens_point(int i, int n, double A, double *L) {
+    double rho = A * sqrt((i + 0.5) / n);
+    double th = 2.399963229728653 * i;
+    L[0] = rho * cos(th);
+    L[1] = rho * sin(th);
+}
+
+static void pixel(const oc_clip *c, const oc_params *p, int O, int u, int v, const double *Pt, const double *Gt,
+                  double *out, double *sumw, int64_t *nacc, int64_t *nexam, oc_member *mem, size_t mi) {
+    const int W = c->W, H = c->H, F = c->F, k = p->k, h = (k - 1) / 2, ns = 2 * p->T + 1;
+    size_t pix = ((size_t)O * H + v) * W + u;
+    float dref_f = c->depth[pix];
+    double cref[3] = {c->rgb[3 * pix], c->rgb[3 * pix + 1], c->rgb[3 * pix + 2]};
+    *nacc = 0;
+    *nexam = 0;
+    *sumw = 0.0;
+    if (!valid_depth(dref_f)) {
+        for (int ch = 0; ch < 3; ++ch) out[ch] = cref[ch];
+        if (mem) for (int j = 0; j < ns; ++j) mem->status[mi * ns + j] = -2;
+        return;
+    }
+    double dref = dref_f;
+    double KOi[9], ray[3], xref[3];
+    mat3_inverse(c->K + 9 * O, KOi);
+    double uv1[3] = {u, v, 1.0};
+    mat3_vec(KOi, uv1, ray);
+    for (int i = 0; i < 3; ++i) xref[i] = dref * ray[i];
+
+    /* aperture: central ray direction (unit) and seed points at depth d_ref */
+    double rhat[3] = {0, 0, 0}, seeds[64][3];
+    int nl = p->lens_samples > 64 ? 64 : p->lens_samples;
+    if (p->mode == 1) {
+        double nr = sqrt(ray[0] * ray[0] + ray[1] * ray[1] + ray[2] * ray[2]);
+        for (int i = 0; i < 3; ++i) rhat[i] = ray[i] / nr;
+        double Fp[3] = {p->focal_depth * ray[0], p->focal_depth * ray[1], p->focal_depth * ray[2]};
+        for (int i = 0; i < nl; ++i) {
+            double L[2];
+            lens_point(i, nl, p->aperture, L);
+            /* point on the ray L -> Fp at camera z = d_ref */
+            double s = dref / p->focal_depth;
+            seeds[i][0] = L[0] + s * (Fp[0] - L[0]);
+            seeds[i][1] = L[1] + s * (Fp[1] - L[1]);
+            seeds[i][2] = dref;
+        }
+    }
+
+    double acc[3] = {0, 0, 0}, Wsum = 0.0;
+    for (int j = 0; j < ns; ++j) {
+        int J = O - p->T + j;
+        if (J < 0 || J >= F) {
+            if (mem) mem->status[mi * ns + j] = -1;
+            continue;
+        }
+        const double *P = Pt + 12 * j, *G = Gt + 12 * j;
+        int bx0, by0, bx1, by1, amb = 0;
+        if (p->mode != 1) {
+            double xp[3];
+            apply34(P, xref, xp);
+            if (xp[2] <= 1e-6 * dref) {
+                if (mem) mem->status[mi * ns + j] = 0;
+                continue;
+            }
+            double up = xp[0] / xp[2], vp = xp[1] / xp[2];
+            double fu = up - floor(up), fv = vp - floor(vp);
+            amb = fabs(fu - 0.5) < p->tie_band || fabs(fv - 0.5) < p->tie_band;
+            double cxd = floor(up + 0.5), cyd = floor(vp + 0.5);
+            /* a centre this far out cannot reach the image: clamp it far outside */
+            if (cxd < -(double)(4 * k + 8)) cxd = -(double)(4 * k + 8);
+            if (cxd > (double)(W + 4 * k + 8)) cxd = (double)(W + 4 * k + 8);
+            if (cyd < -(double)(4 * k + 8)) cyd = -(double)(4 * k + 8);
+            if (cyd > (double)(H + 4 * k + 8)) cyd = (double)(H + 4 * k + 8);
+            bx0 = (int)cxd - h; bx1 = (int)cxd + h; by0 = (int)cyd - h; by1 = (int)cyd + h;
+            if (mem) { mem->centre[2 * (mi * ns + j)] = (int)cxd; mem->centre[2 * (mi * ns + j) + 1] = (int)cyd; }
+        } else {
+            /* footprint: bbox of projected seed points, grown by h, capped around the centroid */
+            double mnx = 1e300, mny = 1e300, mxx = -1e300, mxy = -1e300, sx = 0, sy = 0;
+            int nin = 0;
+            for (int i = 0; i < nl; ++i) {
+                double xp[3];
+                apply34(P, seeds[i], xp);
+                if (xp[2] <= 1e-6 * dref) continue;
+                double up = xp[0] / xp[2], vp = xp[1] / xp[2];
+                if (up < mnx) mnx = up;
+                if (up > mxx) mxx = up;
+                if (vp < mny) mny = vp;
+                if (vp > mxy) mxy = vp;
+                sx += up; sy += vp; ++nin;
+            }
+            if (nin < nl) {  /* a seed behind the J camera: skip the frame */
+                if (mem) mem->status[mi * ns + j] = 0;
+                continue;
+            }
+            double lim = (double)(W + H + 4 * p->cap + 8);
+            double mx = sx / nl, my = sy / nl;
+            if (mx < -lim) mx = -lim;
+            if (mx > lim) mx = lim;
+            if (my < -lim) my = -lim;
+            if (my > lim) my = lim;
+            int ccx = (int)floor(mx + 0.5), ccy = (int)floor(my + 0.5), hc = (p->cap - 1) / 2;
+            double fx0 = floor(mnx + 0.5) - h, fx1 = floor(mxx + 0.5) + h;
+            double fy0 = floor(mny + 0.5) - h, fy1 = floor(mxy + 0.5) + h;
+            bx0 = fx0 < ccx - hc ? ccx - hc : (int)fx0;
+            bx1 = fx1 > ccx + hc ? ccx + hc : (int)fx1;
+            by0 = fy0 < ccy - hc ? ccy - hc : (int)fy0;
+            by1 = fy1 > ccy + hc ? ccy + hc : (int)fy1;
+            if (mem) {
+                int32_t *b = mem->box + 4 * (mi * ns + j);
+                b[0] = bx0; b[1] = by0; b[2] = bx1; b[3] = by1;
+            }
+        }
+        if (mem) { mem->status[mi * ns + j] = 1; mem->amb[mi * ns + j] = (uint8_t)amb; }
+        double fxJ = c->K[9 * J + 0];
+        for (int qy = by0; qy <= by1; ++qy) {
+            for (int qx = bx0; qx <= bx1; ++qx) {
+                int slot = (qy - by0) * (bx1 - bx0 + 1) + (qx - bx0);
+                uint8_t code;
+                if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
+                    code = OC_OUT;
+                } else {
+                    ++*nexam;
+                    size_t qi = ((size_t)J * H + qy) * W + qx;
+                    float dq = c->depth[qi];
+                    if (!valid_depth(dq)) {
+                        code = OC_INVALID;
+                    } else {
+                        double q3[3] = {qx * (double)dq, qy * (double)dq, (double)dq}, X[3];
+                        apply34(G, q3, X);
+                        double dx = X[0] - xref[0], dy = X[1] - xref[1], dz = X[2] - xref[2];
+                        double w = 0.0;
+                        int acc_ok;
+                        if (p->mode != 1) {
+                            double d2 = dx * dx + dy * dy + dz * dz;
+                            acc_ok = d2 < p->radius * p->radius;
+                            code = acc_ok ? OC_ACCEPT : OC_REJECT;
+                            if (fabs(sqrt(d2) - p->radius) <= p->band_rel * p->radius) code |= OC_BAND;
+                            if (acc_ok) {
+                                if (p->mode == 3) {
+                                    w = 1.0;
+                                } else {
+                                    double s[7] = {c->rgb[3 * qi], c->rgb[3 * qi + 1], c->rgb[3 * qi + 2], X[0], X[1], X[2], J};
+                                    double sr[7] = {cref[0], cref[1], cref[2], xref[0], xref[1], xref[2], O};
+                                    w = oc_weight_denoise(s, sr, p->sigma_rgb, p->sigma_xyz, p->sigma_f);
+                                }
+                            }
+                        } else {
+                            double ral = X[0] * rhat[0] + X[1] * rhat[1] + X[2] * rhat[2];
+                            double px = X[0] - ral * rhat[0], py = X[1] - ral * rhat[1], pz = X[2] - ral * rhat[2];
+                            double qperp = sqrt(px * px + py * py + pz * pz);
+                            double a = p->a0 + p->aperture * fabs(p->focal_depth - ral) / p->focal_depth;
+                            acc_ok = qperp < a;
+                            code = acc_ok ? OC_ACCEPT : OC_REJECT;
+                            if (fabs(qperp - a) <= p->band_rel * a) code |= OC_BAND;
+                            if (acc_ok) {
+                                double e = (double)dq / fxJ;
+                                double s_area = e * e;
+                                w = s_area / (3.141592653589793 * a * a);
+                            }
+                        }
+                        if (acc_ok) {
+                            for (int ch = 0; ch < 3; ++ch) acc[ch] += w * c->rgb[3 * qi + ch];
+                            Wsum += w;
+                            ++*nacc;
+                        }
+                    }
+                }
+                if (mem && p->mode != 1) mem->codes[(mi * ns + j) * (size_t)(k * k) + slot] = code;
+            }
+        }
+    }
+    *sumw = Wsum;
+    if (Wsum > 0.0) {
+        for (int ch = 0; ch < 3; ++ch) out[ch] = acc[ch] / Wsum;
+    } else {
+        for (int ch = 0; ch < 3; ++ch) out[ch] = cref[ch];
+    }
+}
+
+/*
+ * Gather and filter the crop [x0, x0+cw) x [y0, y0+ch) of output frame O.
+ * Outputs (row-major over the crop): out_rgb cw*ch*3, sumw, nacc, nexam.  mem_* may be NULL;
+ * otherwise they hold per (pixel, slot) records for slots J = O-T .. O+T.
+ */
+int oc_gather_filter(const oc_clip *c, const oc_params *p, int O, int x0, int y0, int cw, int ch, double *out_rgb,
+                     double *out_sumw, int64_t *out_nacc, int64_t *out_nexam, int32_t *mem_status,
+                     int32_t *mem_centre, uint8_t *mem_amb, uint8_t *mem_codes, int32_t *mem_box) {
+    if (p->k < 1 || (p->k & 1) == 0 || p->T < 0 || O < 0 || O >= c->F) return -1;
+    int ns = 2 * p->T + 1;
+    double *Pt = (double *)malloc(sizeof(double) * 12 * ns), *Gt = (double *)malloc(sizeof(double) * 12 * ns);
+    if (!Pt || !Gt) { free(Pt); free(Gt); return -2; }
+    for (int j = 0; j < ns; ++j) {
+        int J = O - p->T + j;
+        if (J < 0 || J >= c->F) continue;
+        oc_compose(c->K + 9 * O, c->w2c + 12 * O, c->K + 9 * J, c->w2c + 12 * J, J == O, Pt + 12 * j, Gt + 12 * j);
+    }
+    oc_member mem = {mem_status, mem_centre, mem_amb, mem_codes, mem_box};
+    oc_member *mp = mem_status ? &mem : NULL;
+    long long n = (long long)cw * ch;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (long long i = 0; i < n; ++i) {
+        int u = x0 + (int)(i % cw), v = y0 + (int)(i / cw);
+        pixel(c, p, O, u, v, Pt, Gt, out_rgb + 3 * i, out_sumw + i, out_nacc + i, out_nexam + i, mp, (size_t)i);
+    }
+    free(Pt);
+    free(Gt);
+    return 0;
+}
+
+/*
+ * Brute force: test EVERY pixel of frame J against the radius around x_ref of pixel (u, v) of
+ * frame O (no window).  accept is H*W bytes (1 accepted, 0 not); returns the count.
+ */
+long long oc_bruteforce(const oc_clip *c, const oc_params *p, int O, int u, int v, int J, uint8_t *accept) {
+    const int W = c->W, H = c->H;
+    double P[12], G[12], KOi[9], ray[3], xref[3];
+    oc_compose(c->K + 9 * O, c->w2c + 12 * O, c->K + 9 * J, c->w2c + 12 * J, J == O, P, G);
+    float dref = c->depth[((size_t)O * H + v) * W + u];
+    memset(accept, 0, (size_t)W * H);
+    if (!valid_depth(dref)) return 0;
+    mat3_inverse(c->K + 9 * O, KOi);
+    double uv1[3] = {u, v, 1.0};
+    mat3_vec(KOi, uv1, ray);
+    for (int i = 0; i < 3; ++i) xref[i] = (double)dref * ray[i];
+    long long cnt = 0;
+    for (int qy = 0; qy < H; ++qy) {
+        for (int qx = 0; qx < W; ++qx) {
+            float dq = c->depth[((size_t)J * H + qy) * W + qx];
+            if (!valid_depth(dq)) continue;
+            double q3[3] = {qx * (double)dq, qy * (double)dq, (double)dq}, X[3];
+            apply34(G, q3, X);
+            double d2 = (X[0] - xref[0]) * (X[0] - xref[0]) + (X[1] - xref[1]) * (X[1] - xref[1]) +
+                        (X[2] - xref[2]) * (X[2] - xref[2]);
+            if (d2 < p->radius * p->radius) { accept[(size_t)qy * W + qx] = 1; ++cnt; }
+        }
+    }
+    return cnt;
+}

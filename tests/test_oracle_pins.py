@@ -1,0 +1,373 @@
+"""Pins of the FP64 oracle to truths outside itself (no GPU).
+
+Each test ties one part of the oracle to something it does not compute itself: a library routine
+(scipy's multivariate normal, numpy's weighted average), the generator's ray-cast ground truth,
+closed-form special cases (self-reprojection, exact-geometry scenes), brute force over whole
+frames, and invariances that a dropped term, a wrong sign or a transposed operand would break.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.make_clip("planes3", 96, 54, 10, seed=3)
+
+
+@pytest.fixture(scope="module")
+def room_exact():
+    return synth.make_clip("room", 120, 68, 6, seed=2, with_world=True, sigma_depth=0.0, sigma_pose=0.0,
+                           sigma_img=0.0)
+
+
+# ------------------------------------------------------------------ Eq. 4 and Eq. 3 against libraries
+
+def test_weight_is_unnormalised_multivariate_normal():
+    """Eq. 4 with diagonal covariance = N(s; s_ref, diag(sigma^2)) / N(s_ref; s_ref, diag(sigma^2))."""
+    from scipy.stats import multivariate_normal
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        sr_rgb, sxyz, sf = rng.uniform(0.05, 0.5), rng.uniform(0.01, 0.3), rng.uniform(1, 10)
+        sref = np.concatenate([rng.uniform(0, 1, 3), rng.normal(0, 5, 3), [rng.integers(0, 50)]])
+        s = sref + np.concatenate([rng.normal(0, sr_rgb, 3), rng.normal(0, sxyz, 3), [rng.integers(-10, 10)]])
+        cov = np.diag([sr_rgb ** 2] * 3 + [sxyz ** 2] * 3 + [sf ** 2])
+        mvn = multivariate_normal(mean=sref, cov=cov)
+        want = mvn.pdf(s) / mvn.pdf(sref)
+        got = oracle.weight_denoise(s, sref, sr_rgb, sxyz, sf)
+        assert got == pytest.approx(want, rel=1e-10, abs=1e-300)
+
+
+def test_filter_is_weighted_average():
+    """Eq. 3: O = sum w s_rgb / sum w, with Eq. 4 weights from scipy, and w = 1 for the mean mode."""
+    from scipy.stats import multivariate_normal
+    rng = np.random.default_rng(1)
+    for n in (1, 2, 7, 64):
+        S = np.concatenate([rng.uniform(0, 1, (n, 3)), rng.normal(0, 0.05, (n, 3)), rng.integers(-5, 6, (n, 1))], 1)
+        sref = np.concatenate([rng.uniform(0, 1, 3), np.zeros(3), [0.0]])
+        sig = (0.15, 0.05, 6.0)
+        cov = np.diag([sig[0] ** 2] * 3 + [sig[1] ** 2] * 3 + [sig[2] ** 2])
+        w = multivariate_normal(mean=sref, cov=cov).pdf(S).reshape(-1) / multivariate_normal(mean=sref, cov=cov).pdf(sref)
+        out, W = oracle.filter_samples(S, sref, oracle.MODE_DENOISE, *sig)
+        np.testing.assert_allclose(out, np.average(S[:, :3], axis=0, weights=w), rtol=1e-10)
+        assert W == pytest.approx(w.sum(), rel=1e-10)
+        out_m, W_m = oracle.filter_samples(S, sref, oracle.MODE_MEAN, *sig)
+        np.testing.assert_allclose(out_m, S[:, :3].mean(0), rtol=1e-12)
+        assert W_m == n
+
+
+def test_paper_parameters_are_the_defaults():
+    g = json.load(open(os.path.join(GOLDEN, "paper_parameters.json")))
+    p = oracle.Params()
+    assert p.sigma_rgb == pytest.approx(g["denoise_sigma_rgb_0_255"]["value"] / 255.0)
+    assert p.sigma_f == g["denoise_sigma_f"]["value"]
+
+
+# ------------------------------------------------------------------ A1 against the generator's geometry
+
+def _world_to_cam(w2c, X):
+    return X @ w2c[:, :3].T + w2c[:, 3]
+
+
+@pytest.mark.parametrize("O,J", [(2, 2), (2, 0), (2, 5), (0, 5)])
+def test_compose_matches_ray_cast_geometry(room_exact, O, J):
+    """G_{O<-J} maps (q d, d, 1) of frame J to the ray-cast world point seen by q, in O's camera;
+    P_{J<-O} maps that point back to pixel q."""
+    c = room_exact
+    P, G = oracle.compose(c.K[O], c.w2c[O], c.K[J], c.w2c[J], O == J)
+    rng = np.random.default_rng(O * 10 + J)
+    qs = np.stack([rng.integers(0, c.W, 200), rng.integers(0, c.H, 200)], 1)
+    d = c.depth[J, qs[:, 1], qs[:, 0]].astype(np.float64)
+    Xw = c.world[J, qs[:, 1], qs[:, 0]]
+    want = _world_to_cam(c.w2c[O], Xw)
+    q4 = np.stack([qs[:, 0] * d, qs[:, 1] * d, d, np.ones_like(d)], 1)
+    got = q4 @ G.T
+    # depth is stored in float32: compare against the float32-rounded hit point's scale
+    np.testing.assert_allclose(got, want, atol=2e-6 * np.abs(d).max(), rtol=0)
+    proj = np.concatenate([got, np.ones((len(d), 1))], 1) @ P.T
+    uv = proj[:, :2] / proj[:, 2:3]
+    np.testing.assert_allclose(uv, qs, atol=1e-3)
+
+
+# ------------------------------------------------------------------ closed-form special cases
+
+def test_self_reprojection_single_sample(tiny):
+    """T = 0, k = 1: S(p) = {(O, p)} with weight 1, so O(p) = I(p) exactly."""
+    v = oracle.ClipView.of(tiny)
+    p = oracle.default_params(tiny.depth, k=1, T=0)
+    r = oracle.gather_filter(v, p, 4, membership=True)
+    assert (r.nacc == 1).all()
+    assert (r.sumw == 1.0).all()
+    np.testing.assert_array_equal(r.rgb, tiny.rgb[4].astype(np.float64))
+    assert (r.codes[..., 0, 0, 0] == oracle.CODE_ACCEPT).all()
+
+
+def test_self_sample_always_in_set(tiny):
+    """With a wide window, (O, p) is the window centre in frame O and is always accepted."""
+    v = oracle.ClipView.of(tiny)
+    p = oracle.default_params(tiny.depth, k=5, T=3)
+    O = 5
+    r = oracle.gather_filter(v, p, O, membership=True)
+    H, W = tiny.H, tiny.W
+    uu, vv = np.meshgrid(np.arange(W), np.arange(H))
+    np.testing.assert_array_equal(r.centre[:, :, p.T, 0], uu)
+    np.testing.assert_array_equal(r.centre[:, :, p.T, 1], vv)
+    assert ((r.codes[:, :, p.T, 2, 2] & 7) == oracle.CODE_ACCEPT).all()
+    assert (r.sumw >= 1.0).all()
+
+
+def test_exact_geometry_constant_planes_reproduce_clean():
+    """Exact depth and poses, no noise, constant-albedo planes far apart in depth: every accepted
+    sample has the reference colour, so the output is the clean render."""
+    c = synth.make_clip("exact_const", 96, 54, 9, seed=0)
+    v = oracle.ClipView.of(c)
+    p = oracle.default_params(c.depth, k=5, T=4)
+    r = oracle.gather_filter(v, p, 4)
+    np.testing.assert_allclose(r.rgb, c.clean[4], atol=1e-12, rtol=0)
+    assert r.nacc.mean() > 0.5 * c.F  # not just the self sample
+
+
+def test_exact_shift_membership_is_closed_form():
+    """Camera moving exactly one pixel footprint per frame over a fronto-parallel plane: pixel (u, v)
+    of O is seen at (u - (J - O), v) in J, at distance 0; the neighbours lie 2^-5 units away (> r).
+    S(p) is exactly that set, and the output is the clean colour."""
+    c = synth.make_clip("exact_shift", 64, 36, 7, seed=1)
+    v = oracle.ClipView.of(c)
+    p = oracle.default_params(c.depth, k=5, T=3)
+    assert p.radius < 2.0 ** -5
+    O = 3
+    r = oracle.gather_filter(v, p, O, membership=True)
+    H, W, h = c.H, c.W, 2
+    for j in range(2 * p.T + 1):
+        J = O - p.T + j
+        acc = (r.codes[:, :, j] & 7) == oracle.CODE_ACCEPT
+        uu = np.arange(W)[None, :].repeat(H, 0)
+        inside = (uu - (J - O) >= 0) & (uu - (J - O) < W)
+        # accepted exactly at the window centre when the shifted pixel is inside the image
+        np.testing.assert_array_equal(r.centre[:, :, j, 0], uu - (J - O))
+        assert (acc[:, :, h, h] == inside).all()
+        acc_c = acc.copy()
+        acc_c[:, :, h, h] = False
+        assert not acc_c.any()
+    np.testing.assert_allclose(r.rgb, c.clean[O], atol=1e-12, rtol=0)
+    # count = number of frames in which the point stays inside the image
+    uu = np.arange(W)[None, :].repeat(H, 0)
+    want = sum(((uu - (J - O) >= 0) & (uu - (J - O) < W)).astype(int) for J in range(O - p.T, O + p.T + 1))
+    np.testing.assert_array_equal(r.nacc, want)
+
+
+# ------------------------------------------------------------------ brute force
+
+def test_window_equals_brute_force_where_ball_fits(tiny):
+    """The k x k windowed set equals a scan of all pixels of J wherever the projected ball of
+    radius r fits inside the window, and is a subset of it everywhere."""
+    v = oracle.ClipView.of(tiny)
+    p = oracle.default_params(tiny.depth, k=5, T=4)
+    O, h = 4, 2
+    r = oracle.gather_filter(v, p, O, membership=True)
+    rng = np.random.default_rng(7)
+    fits = checked = 0
+    for _ in range(60):
+        u, w_ = int(rng.integers(0, tiny.W)), int(rng.integers(0, tiny.H))
+        for j in range(2 * p.T + 1):
+            J = O - p.T + j
+            if J < 0 or J >= tiny.F or r.status[w_, u, j] != 1:
+                continue
+            brute = oracle.bruteforce(v, p, O, u, w_, J)
+            win = np.zeros_like(brute)
+            cx, cy = r.centre[w_, u, j]
+            for dy in range(-h, h + 1):
+                for dx in range(-h, h + 1):
+                    if (r.codes[w_, u, j, dy + h, dx + h] & 7) == oracle.CODE_ACCEPT:
+                        win[cy + dy, cx + dx] = 1
+            assert (win <= brute).all()
+            # projected ball radius in pixels (ball centre at camera depth z' in J)
+            P, _ = oracle.compose(tiny.K[O], tiny.w2c[O], tiny.K[J], tiny.w2c[J], J == O)
+            xref = tiny.depth[O, w_, u] * np.linalg.solve(tiny.K[O], [u, w_, 1.0])
+            zp = (P @ np.append(xref, 1.0))[2]
+            rad_px = p.radius * tiny.K[J, 0, 0] / max(zp - p.radius, 1e-9)
+            checked += 1
+            if 1.1 * rad_px < h - 0.5:
+                fits += 1
+                np.testing.assert_array_equal(win, brute)
+    assert fits > 0.8 * checked, (fits, checked)
+
+
+# ------------------------------------------------------------------ invariances
+
+def _rigid(seed):
+    rng = np.random.default_rng(seed)
+    return synth.rodrigues(rng.normal(0, 0.7, 3)), rng.normal(0, 3.0, 3)
+
+
+def test_gauge_invariance(tiny):
+    """One rigid transform of the world (all poses) leaves every output unchanged."""
+    Rg, tg = _rigid(11)
+    w2c2 = np.empty_like(tiny.w2c)
+    for f in range(tiny.F):
+        R, t = tiny.w2c[f, :, :3], tiny.w2c[f, :, 3]
+        w2c2[f, :, :3] = R @ Rg.T
+        w2c2[f, :, 3] = t - R @ Rg.T @ tg
+    p = oracle.default_params(tiny.depth, k=5, T=4)
+    a = oracle.gather_filter(oracle.ClipView.of(tiny), p, 5)
+    b = oracle.gather_filter(oracle.ClipView(tiny.rgb, tiny.depth, tiny.K, w2c2), p, 5)
+    np.testing.assert_array_equal(a.nacc, b.nacc)
+    np.testing.assert_allclose(a.rgb, b.rgb, atol=1e-9, rtol=0)
+
+
+def test_scale_invariance(tiny):
+    """Scaling depth, translations, r and sigma_xyz by s leaves the output unchanged."""
+    s = 4.0  # a power of two keeps the float32 depths exact
+    w2c2 = tiny.w2c.copy()
+    w2c2[:, :, 3] *= s
+    p = oracle.default_params(tiny.depth, k=5, T=4)
+    p2 = oracle.Params(**{**p.__dict__, "radius": p.radius * s, "sigma_xyz": p.radius * s})
+    a = oracle.gather_filter(oracle.ClipView.of(tiny), p, 5)
+    b = oracle.gather_filter(oracle.ClipView(tiny.rgb, tiny.depth * s, tiny.K, w2c2), p2, 5)
+    np.testing.assert_array_equal(a.nacc, b.nacc)
+    np.testing.assert_allclose(a.rgb, b.rgb, atol=1e-9, rtol=0)
+
+
+def test_infinite_sigmas_give_the_unweighted_mean(tiny):
+    p = oracle.default_params(tiny.depth, k=5, T=4)
+    big = oracle.Params(**{**p.__dict__, "sigma_rgb": 1e9, "sigma_xyz": 1e9, "sigma_f": 1e9})
+    mean = oracle.Params(**{**p.__dict__, "mode": oracle.MODE_MEAN})
+    v = oracle.ClipView.of(tiny)
+    a = oracle.gather_filter(v, big, 5)
+    b = oracle.gather_filter(v, mean, 5)
+    np.testing.assert_array_equal(a.nacc, b.nacc)
+    np.testing.assert_allclose(a.rgb, b.rgb, atol=1e-12, rtol=0)
+
+
+def test_gather_output_is_the_filter_of_its_own_set_in_any_order(tiny):
+    """Rebuild S(p) from the membership record, shuffle it, filter with the scipy-pinned filter:
+    the gather's output must agree (accumulation order does not matter beyond rounding)."""
+    v = oracle.ClipView.of(tiny)
+    p = oracle.default_params(tiny.depth, k=5, T=4)
+    O, h = 5, 2
+    r = oracle.gather_filter(v, p, O, membership=True)
+    rng = np.random.default_rng(3)
+    Kinv = np.linalg.inv(tiny.K[O])
+    for _ in range(40):
+        u, w_ = int(rng.integers(0, tiny.W)), int(rng.integers(0, tiny.H))
+        d0 = float(tiny.depth[O, w_, u])
+        xref = d0 * (Kinv @ [u, w_, 1.0])
+        sref = np.concatenate([tiny.rgb[O, w_, u], xref, [O]])
+        S = []
+        for j in range(2 * p.T + 1):
+            J = O - p.T + j
+            if r.status[w_, u, j] != 1:
+                continue
+            _, G = oracle.compose(tiny.K[O], tiny.w2c[O], tiny.K[J], tiny.w2c[J], J == O)
+            cx, cy = r.centre[w_, u, j]
+            for dy in range(-h, h + 1):
+                for dx in range(-h, h + 1):
+                    if (r.codes[w_, u, j, dy + h, dx + h] & 7) == oracle.CODE_ACCEPT:
+                        qx, qy = cx + dx, cy + dy
+                        d = float(tiny.depth[J, qy, qx])
+                        X = G @ [qx * d, qy * d, d, 1.0]
+                        S.append(np.concatenate([tiny.rgb[J, qy, qx], X, [J]]))
+        S = np.array(S)
+        assert len(S) == r.nacc[w_, u]
+        rng.shuffle(S)
+        out, W = oracle.filter_samples(S, sref, oracle.MODE_DENOISE, p.sigma_rgb, p.radius, p.sigma_f)
+        np.testing.assert_allclose(r.rgb[w_, u], out, atol=1e-12)
+        assert r.sumw[w_, u] == pytest.approx(W, rel=1e-12)
+
+
+def test_membership_is_monotone_in_radius_and_window(tiny):
+    v = oracle.ClipView.of(tiny)
+    p = oracle.default_params(tiny.depth, k=3, T=3)
+    O = 4
+    small = oracle.gather_filter(v, p, O, membership=True)
+    big = oracle.gather_filter(v, oracle.Params(**{**p.__dict__, "radius": 2 * p.radius}), O, membership=True)
+    acc_s = (small.codes & 7) == oracle.CODE_ACCEPT
+    acc_b = (big.codes & 7) == oracle.CODE_ACCEPT
+    assert (acc_s <= acc_b).all() and acc_b.sum() > acc_s.sum()
+    wide = oracle.gather_filter(v, oracle.Params(**{**p.__dict__, "k": 5}), O, membership=True)
+    acc_w = (wide.codes & 7) == oracle.CODE_ACCEPT
+    assert (acc_s <= acc_w[:, :, :, 1:4, 1:4]).all()
+    assert (wide.nacc >= small.nacc).all()
+
+
+# ------------------------------------------------------------------ invalid data and edges
+
+def test_invalid_depths_are_never_gathered(tiny):
+    depth = tiny.depth.copy()
+    rng = np.random.default_rng(5)
+    bad = rng.random(depth.shape) < 0.1
+    vals = np.array([np.nan, 0.0, -1.0, np.inf], np.float32)
+    depth[bad] = vals[rng.integers(0, 4, bad.sum())]
+    v = oracle.ClipView(tiny.rgb, depth, tiny.K, tiny.w2c)
+    p = oracle.default_params(tiny.depth, k=5, T=3)
+    O = 4
+    r = oracle.gather_filter(v, p, O, membership=True)
+    ref_bad = bad[O]
+    np.testing.assert_array_equal(r.rgb[ref_bad], tiny.rgb[O][ref_bad].astype(np.float64))
+    assert (r.nacc[ref_bad] == 0).all() and (r.status[ref_bad] == -2).all()
+    # every accepted candidate has a valid depth
+    h = 2
+    ys, xs = np.nonzero(~ref_bad)
+    for y, x in zip(ys[::37], xs[::37]):
+        for j in range(2 * p.T + 1):
+            if r.status[y, x, j] != 1:
+                continue
+            J = O - p.T + j
+            cx, cy = r.centre[y, x, j]
+            for dy in range(-h, h + 1):
+                for dx in range(-h, h + 1):
+                    code = r.codes[y, x, j, dy + h, dx + h] & 7
+                    qx, qy = cx + dx, cy + dy
+                    inside = 0 <= qx < tiny.W and 0 <= qy < tiny.H
+                    if not inside:
+                        assert code == oracle.CODE_OUT
+                    elif bad[J, qy, qx]:
+                        assert code == oracle.CODE_INVALID
+
+
+def test_frames_outside_clip_and_behind_camera(tiny):
+    w2c = tiny.w2c.copy()
+    # frame 1 looks backwards: every reference point lies behind it
+    R = synth.rot_y(np.pi) @ w2c[1, :, :3]
+    w2c[1, :, :3] = R
+    v = oracle.ClipView(tiny.rgb, tiny.depth, tiny.K, w2c)
+    p = oracle.default_params(tiny.depth, k=3, T=3)
+    r = oracle.gather_filter(v, p, 0, membership=True)
+    assert (r.status[:, :, 0:3] == -1).all()          # J = -3..-1
+    assert (r.status[:, :, 4] == 0).all()             # J = 1 behind the camera
+    assert (r.status[:, :, 3] == 1).all()             # J = 0
+
+
+def test_lower_median_definition():
+    rng = np.random.default_rng(9)
+    for n in (1, 2, 5, 10, 101):
+        d = rng.uniform(0.5, 9, n).astype(np.float32)
+        noisy = np.concatenate([d, np.array([np.nan, -1, 0, np.inf], np.float32)])
+        rng.shuffle(noisy)
+        m = oracle.median_depth(noisy)
+        below = int((d < m).sum())
+        at_or_below = int((d <= m).sum())
+        rank = (n - 1) // 2
+        assert below <= rank < at_or_below
+
+
+def test_robust_weights_beat_plain_mean():
+    """Sec. Denoising: plain averaging of S(p) (w = 1) lets occluded samples corrupt the result while
+    the Eq. 4 weighting suppresses them.  The paper's gather admits occluded samples; a gate ten
+    times the default radius does the same here."""
+    c = synth.make_clip("room", 160, 90, 9, seed=4)
+    v = oracle.ClipView.of(c)
+    p = oracle.default_params(c.depth, k=7, T=4)
+    p = oracle.Params(**{**p.__dict__, "radius": 10 * p.radius})
+    a = oracle.gather_filter(v, p, 4)
+    b = oracle.gather_filter(v, oracle.Params(**{**p.__dict__, "mode": oracle.MODE_MEAN}), 4)
+    noisy = oracle.psnr(c.rgb[4], c.clean[4])
+    assert oracle.psnr(a.rgb, c.clean[4]) > oracle.psnr(b.rgb, c.clean[4]) + 1.0
+    assert oracle.psnr(a.rgb, c.clean[4]) > noisy + 3.0
