@@ -1,0 +1,316 @@
+"""Benchmark: scene-space denoising at 1080p over a +-30-frame window, k = 7, through libssvp.
+
+One step = one ssvp_gather_filter call over a batch of output frames of a clip resident in HBM
+(camera composition on the host, then the fused gather + filter kernel).  `value` is output
+Mpix/s over all ranks; `e2e` is the same metric through the C ABI with host buffers (upload +
+pack + median + gather + download every step).  `--impl reference` times the FP64 CPU oracle
+on the host cores, one full output frame of the same workload per step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--colour fp32|fp16]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gathered samples/s and output Mpix/s at 1080p; PSNR vs clean render & oracle"
+# workloads: name -> (W, H, frames, half window T, k, first output frame, output frames per step)
+WORKLOADS = {
+    "fhd": (1920, 1080, 68, 30, 7, 30, 8),   # 1080p denoising over +-30 frames (the headline)
+    "hd": (1280, 720, 60, 15, 7, 15, 8),     # 720p, +-15 frames
+}
+W, H, F, T, K_WIN, O_BEGIN, N_OUT = WORKLOADS["fhd"]
+RADIUS_REL = 0.005
+BYTES_PER_CANDIDATE = {"fp32": 16, "fp16": 12}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                self.out = ""
+        else:
+            self.out = ""
+
+    def summary(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _workload_clip(seed):
+    import synth
+    return synth.make_clip("room", W, H, F, seed=seed)
+
+
+def _config(colour):
+    return {"workload": f"denoise-{W}x{H}-pm{T}-k{K_WIN}-{colour}", "W": W, "H": H, "frames": F,
+            "out_frames_per_step": N_OUT, "half_window": T, "k": K_WIN, "radius": f"{RADIUS_REL:g} x median depth",
+            "scene": "synthetic 6 planes + 4 boxes, hand-held path, depth noise 2%, image noise 0.05",
+            "colour": colour, "l2": "no flush: packed input planes (~3.1 GB) exceed the 129 MB L2"}
+
+
+def cpu_oracle_sample(clip, target_s=10.0, O=None, max_frames=None):
+    """Times the FP64 oracle on whole output frames O, O+1, ... until about target_s seconds."""
+    import oracle
+    O = O_BEGIN if O is None else O
+    max_frames = N_OUT if max_frames is None else max_frames
+    v = oracle.ClipView.of(clip)
+    prm = oracle.default_params(clip.depth, k=K_WIN, T=T, radius_rel=RADIUS_REL)
+    results, dt = [], 0.0
+    while len(results) < max_frames and (not results or dt < target_s):
+        t0 = time.perf_counter()
+        results.append(oracle.gather_filter(v, prm, O + len(results)))
+        dt += time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    n = len(results)
+    return dict(frames=n, seconds=dt, mpix_s=n * W * H / dt / 1e6, cores=cores, results=results,
+                examined=sum(int(r.nexam.sum()) for r in results), accepted=sum(int(r.nacc.sum()) for r in results),
+                sample=f"{n} full output frame(s) {O}..{O + n - 1} ({dt:.1f} s)")
+
+
+def run_reference(args):
+    """The oracle on the host cores, on this benchmark's workload, metric and unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    clip = _workload_clip(0)
+    times = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        s = cpu_oracle_sample(clip, target_s=0.0, max_frames=1)
+        if i >= args.warmup:
+            times.append(s["seconds"])
+            samples.append(s)
+    s = samples[-1]
+    px = W * H
+    value = px / float(np.mean(times)) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config("fp32"),
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": s["cores"], "kind": "oracle",
+                             "sample": f"one full output frame ({O_BEGIN}) per step"},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "samples_per_s": {"examined": s["examined"] / float(np.mean(times)),
+                              "accepted": s["accepted"] / float(np.mean(times))}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--colour", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fhd", choices=sorted(WORKLOADS))
+    ap.add_argument("--out-frames", type=int, default=None, help="output frames per step (default per workload)")
+    args = ap.parse_args()
+    global W, H, F, T, K_WIN, O_BEGIN, N_OUT
+    W, H, F, T, K_WIN, O_BEGIN, N_OUT = WORKLOADS[args.workload]
+    if args.out_frames:
+        N_OUT = args.out_frames
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as g
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.build() if rank == 0 or world == 1 else None
+    if world > 1:
+        dist.barrier()
+        g.build()
+    import paper_2102_03011_gb300 as ss
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    clip = _workload_clip(seed=rank)
+    cfmt = ss.SSVP_COLOUR_F32 if args.colour == "fp32" else ss.SSVP_COLOUR_F16
+    ctx = ss.ssvp_create(local, stream)
+    rgb_d = torch.from_numpy(clip.rgb).to(dev)
+    dep_d = torch.from_numpy(clip.depth).to(dev)
+    ss.ssvp_load_clip(ctx, 0, W, H, F, rgb_d, dep_d, None, cfmt)
+    ss.ssvp_set_cameras(ctx, 0, clip.K, 1, clip.w2c)
+    ss.ssvp_sync(ctx)
+    del rgb_d, dep_d
+    p = ss.ssvp_params_default()
+    p.k, p.half_window, p.frame_begin, p.frame_end = K_WIN, T, O_BEGIN, O_BEGIN + N_OUT
+    p.radius = -RADIUS_REL
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---------------- device-resident timing
+    for _ in range(args.warmup):
+        ss.ssvp_gather_filter(ctx, p, [0])
+    ss.ssvp_sync(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            ss.ssvp_gather_filter(ctx, p, [0])
+            ev[i][1].record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    total_ms = t_all0.elapsed_time(t_all1)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    examined, accepted, sum_w = ss.ssvp_read_stats(ctx)
+    t = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / args.steps
+    mpix = N_OUT * W * H / 1e6
+    value = world * mpix / (ms_per_step / 1e3)
+
+    # quality: PSNR of the batch against the clean render
+    out = torch.empty((N_OUT, H, W, 3), dtype=torch.float32, device=dev)
+    ss.ssvp_read_output(ctx, 0, O_BEGIN, O_BEGIN + N_OUT, out)
+    ss.ssvp_sync(ctx)
+    outn = out.cpu().numpy()
+    clean = clip.clean[O_BEGIN:O_BEGIN + N_OUT]
+    noisy = clip.rgb[O_BEGIN:O_BEGIN + N_OUT]
+    psnr = lambda a, b: float(10 * np.log10(1.0 / np.mean((a.astype(np.float64) - b) ** 2)))
+    psnr_out, psnr_in = psnr(outn, clean), psnr(noisy, clean)
+
+    # ---------------- end to end through the C ABI with host buffers
+    rgb_h = torch.from_numpy(clip.rgb).pin_memory()
+    dep_h = torch.from_numpy(clip.depth).pin_memory()
+    out_h = torch.empty((N_OUT, H, W, 3), dtype=torch.float32).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+
+    def e2e_step():
+        ss.ssvp_load_clip(ctx, 1, W, H, F, rgb_h, dep_h, ss.SSVP_MEM_HOST, cfmt)
+        ss.ssvp_set_cameras(ctx, 1, clip.K, 1, clip.w2c)
+        ss.ssvp_gather_filter(ctx, p, [1])
+        ss.ssvp_read_output(ctx, 1, O_BEGIN, O_BEGIN + N_OUT, out_h, ss.SSVP_MEM_HOST)
+
+    e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = torch.tensor([e0.elapsed_time(e1) / e2e_steps], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_ms = float(te.item())
+    h2d = clip.rgb.nbytes + clip.depth.nbytes
+    d2h = out_h.numel() * 4
+    frames_per_chunk = max(1, min(F, (256 << 20) // (W * H * 16)))
+    e2e_launches = -(-F // frames_per_chunk) + 6 + 1
+
+    peaks, peak_kind = _peaks()
+    bpc = BYTES_PER_CANDIDATE[args.colour]
+    kernel_ms = float(np.mean(step_ms))
+    achieved = examined * bpc / (kernel_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.colour == "fp32" else "f16-colour/f32",
+        "data": "synthetic (seeded procedural scene, rendered on the host)", "config": _config(args.colour),
+        "samples_per_s": {"examined": world * examined / (ms_per_step / 1e3),
+                          "accepted": world * accepted / (ms_per_step / 1e3)},
+        "accepted_per_pixel": accepted / (N_OUT * W * H), "kept_weight_fraction": sum_w / max(accepted, 1),
+        "psnr_db": {"output_vs_clean": psnr_out, "input_vs_clean": psnr_in},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "accounting": f"{bpc} B per examined candidate (colour + depth touched), {peak_kind} peak",
+                     "kernel_ms": kernel_ms},
+        "e2e": {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "gpu_launches_per_step": e2e_launches},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = cpu_oracle_sample(clip)
+        diff = np.stack([np.abs(outn[i].astype(np.float64) - r.rgb).max(-1) for i, r in enumerate(s["results"])])
+        line["cpu_baseline"] = {"value": s["mpix_s"], "unit": "Mpix/s", "cores": s["cores"], "kind": "oracle",
+                                "sample": s["sample"]}
+        line["max_abs_vs_oracle"] = {"value": float(diff.max()), "p999": float(np.quantile(diff, 0.999)),
+                                     "frac_above_1e-3": float((diff > 1e-3).mean()), "pixels": int(diff.size),
+                                     "note": "all pixels, including radius-band and rounding-tie pixels"}
+    ss.ssvp_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

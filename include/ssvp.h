@@ -1,0 +1,182 @@
+/*
+ * ssvp.h - C ABI of the GB300 scene-space gather-and-filter library (libssvp.so).
+ *
+ * Method (Klose et al., "Sampling Based Scene-Space Video Processing"):
+ *   every output pixel p of frame O is unprojected by its depth and camera (the reference
+ *   sample s_ref, Sec. "Denoising"), projected into every frame J of a temporal window, and a
+ *   k x k neighbourhood around the projection is tested: a candidate q is gathered when its own
+ *   unprojection lies within radius r of the reference point (the back-projection test of
+ *   Sec. "Sample Gathering", Eq. 2, seeded by the output depth).  The gathered set S(p) is
+ *   reduced by the weighted mean of Eq. 3 with the weights of Eq. 4 (denoising) or of Eq. 13-14
+ *   (virtual aperture), fused into the same CUDA kernel.
+ *
+ * Conventions (all entry points)
+ *   - Every call returns an ssvp_status; nothing aborts.  ssvp_last_error() gives the text.
+ *   - Work is queued on the context's CUDA stream.  Errors raised by queued work surface at a
+ *     later call or at ssvp_sync().
+ *   - Pixel (x, y) with integer coordinates is the pixel centre.  Depth is camera-space z.
+ *     Depth values that are not finite or not > 0 are invalid and never gathered.
+ *   - Images are row-major, frame-major: colour F*H*W*3 floats interleaved (r, g, b), depth
+ *     F*H*W floats, output F*H*W*3 floats.
+ *   - Inputs are copied; the caller keeps ownership of its buffers.  The library owns its
+ *     device buffers until ssvp_destroy().
+ *   - A context is not thread-safe: one host thread per context at a time.
+ */
+#ifndef SSVP_H
+#define SSVP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssvp_ctx ssvp_ctx;
+
+typedef enum {
+    SSVP_OK = 0,
+    SSVP_EINVAL = -1,    /* bad argument: shape, k, window, unsupported camera, null pointer */
+    SSVP_ENOMEM = -2,    /* device or pinned host allocation failed */
+    SSVP_ECUDA = -3,     /* a CUDA call failed (text in ssvp_last_error) */
+    SSVP_ENOCLIP = -4,   /* clip id not loaded */
+    SSVP_ENOCAM = -5,    /* cameras not set for the clip */
+    SSVP_ETIMEOUT = -6,  /* a bounded device-side wait gave up */
+    SSVP_EDEVICE = -7    /* no usable CUDA device */
+} ssvp_status;
+
+enum { SSVP_MEM_HOST = 0, SSVP_MEM_DEVICE = 1 };
+enum { SSVP_COLOUR_F32 = 0, SSVP_COLOUR_F16 = 1 };
+enum {
+    SSVP_MODE_DENOISE = 0,   /* Eq. 4 weights (Sec. "Denoising") */
+    SSVP_MODE_APERTURE = 1,  /* Eq. 13-14 (Sec. "Virtual aperture") */
+    SSVP_MODE_LEARNED = 2,   /* per-sample weights from a small MLP, plain Eq. 4 as fallback */
+    SSVP_MODE_MEAN = 3       /* w = 1 (the plain average of Sec. "Denoising") */
+};
+
+#define SSVP_MAX_CLIPS 64
+#define SSVP_MAX_K 31
+#define SSVP_MAX_HALF_WINDOW 127
+
+/*
+ * Parameters of one gather-and-filter call.  Fill with ssvp_params_default() first.
+ *   mode          SSVP_MODE_*
+ *   k             window width in pixels, odd, 1 <= k <= 31
+ *   half_window   T: frames J = O-T .. O+T (clipped to the clip) are gathered, 0 <= T <= 127
+ *   frame_begin, frame_end   output frames [frame_begin, frame_end) of each clip
+ *   crop_*        output pixel rectangle; crop_w == 0 or crop_h == 0 means the full frame
+ *   radius        gather radius r: > 0 absolute scene units, < 0 means |radius| times the
+ *                 clip's lower-median valid input depth (computed at load)
+ *   sigma_rgb, sigma_xyz, sigma_f   Eq. 4 standard deviations (colour units, scene units,
+ *                 frames); sigma_xyz <= 0 means "equal to r"
+ *   aperture, focal_depth, a0, lens_samples, cap   virtual aperture (Eq. 13-14): lens radius A,
+ *                 focal depth z0 (<= 0: clip median depth), cone waist a0 (<= 0: 0.5 z0 / fx),
+ *                 lens seed points (1..64), footprint cap per axis (odd, <= 63)
+ *   max_samples, conf_threshold     learned filter: sample cap (<= 64), fallback threshold
+ *   membership_out   optional device buffer (debug): per crop pixel (row-major) and per slot
+ *                 j = 0..2T (J = O-T+j) a record of 3 + ceil(k*k/32) int32 words:
+ *                 status (-2 invalid reference depth, -1 J outside the clip, 0 J skipped: the
+ *                 reference point is behind camera J, 1 gathered, 2 no window pixel inside the
+ *                 image), window centre x, y, then the accepted bits of the k x k window
+ *                 (bit dy*k+dx).  Only valid with a single output frame.
+ *   pixel_stats_out  optional device buffer (debug): per crop pixel 3 words: int32 accepted,
+ *                 int32 examined (window pixels inside the image), float sum of weights.
+ */
+typedef struct ssvp_params {
+    int32_t mode;
+    int32_t k;
+    int32_t half_window;
+    int32_t frame_begin;
+    int32_t frame_end;
+    int32_t crop_x, crop_y, crop_w, crop_h;
+    float radius;
+    float sigma_rgb;
+    float sigma_xyz;
+    float sigma_f;
+    float aperture;
+    float focal_depth;
+    float a0;
+    int32_t lens_samples;
+    int32_t cap;
+    int32_t max_samples;
+    float conf_threshold;
+    void *membership_out;
+    void *pixel_stats_out;
+} ssvp_params;
+
+/* Defaults: denoise, k = 7, T = 15, radius = 0.5 % of the median depth, sigma_rgb = 40/255
+ * (the paper's 40 on a 0-255 scale, Sec. "Denoising"), sigma_xyz = r, sigma_f = 6, all frames
+ * of the clip, full frame; aperture 0.05, focal depth = median, 16 lens points, cap 31;
+ * learned cap 64, threshold 0.5; no debug outputs. */
+void ssvp_params_default(ssvp_params *p);
+
+/* Create a context on CUDA device `cuda_device`, queuing work on `cuda_stream` (a cudaStream_t;
+ * NULL means the legacy default stream).  *out receives the context.  SSVP_EDEVICE when no
+ * usable device exists. */
+int ssvp_create(ssvp_ctx **out, int cuda_device, void *cuda_stream);
+
+/* Release every device and host resource of the context (waits for queued work).  NULL is a no-op. */
+void ssvp_destroy(ssvp_ctx *ctx);
+
+/* Text of the last error on this context (or of the last failed ssvp_create when ctx is NULL). */
+const char *ssvp_last_error(const ssvp_ctx *ctx);
+
+/* Change the stream later calls queue work on. */
+int ssvp_set_stream(ssvp_ctx *ctx, void *cuda_stream);
+
+/*
+ * Load clip `clip_id` (0 <= id < SSVP_MAX_CLIPS), replacing any clip with that id.
+ * Inputs I and D of Sec. "Method overview": rgb F*H*W*3 floats (linear colour), depth F*H*W
+ * floats (camera z), on the host (mem_kind = SSVP_MEM_HOST, pinned memory is fastest) or on
+ * this context's device (SSVP_MEM_DEVICE).  colour_fmt selects the stored colour precision
+ * (SSVP_COLOUR_F32 or SSVP_COLOUR_F16, round to nearest even); depth is always stored as FP32.
+ * The lower-median valid depth is computed on the device for relative radii.
+ * Sizes: 1 <= W, H <= 16384, 1 <= F <= 65535.  The copy is queued: the caller's buffers may be
+ * reused once the context's stream has passed this call (ssvp_sync() waits for it).
+ */
+int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float *rgb, const float *depth,
+                   int mem_kind, int colour_fmt);
+
+/* Drop a clip and free its device memory. */
+int ssvp_unload_clip(ssvp_ctx *ctx, int clip_id);
+
+/*
+ * Cameras C of Sec. "Method overview" for clip `clip_id`, in double precision on the host:
+ * K intrinsics (3x3 row-major, shared: per_frame_K = 0, or F of them: per_frame_K = 1), upper
+ * triangular with zero skew and K[2][2] = 1; w2c world->camera [R|t] (F x 3x4 row-major, R a
+ * rotation).  The library composes the per-(O, J) transforms in FP64 (C_O C_J^-1 of Eq. 2).
+ */
+int ssvp_set_cameras(ssvp_ctx *ctx, int clip_id, const double *K, int per_frame_K, const double *w2c);
+
+/*
+ * Gather and filter output frames [frame_begin, frame_end) of each listed clip with the same
+ * parameters (Sec. "Sample Gathering" + Eq. 3).  Results go to the clip's output buffer, read
+ * with ssvp_read_output().  Statistics of this call (examined and accepted samples, sum of
+ * weights) replace the previous ones; read them with ssvp_read_stats().  Queued on the stream.
+ */
+int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, int n_clips);
+
+/* Copy output frames [frame_begin, frame_end) of a clip (full frames, F*H*W*3 layout) to `dst`
+ * on the host (mem_kind = SSVP_MEM_HOST; waits for completion) or device (SSVP_MEM_DEVICE;
+ * queued).  Pixels never written by a gather call hold 0. */
+int ssvp_read_output(ssvp_ctx *ctx, int clip_id, int frame_begin, int frame_end, float *dst, int mem_kind);
+
+/* Device pointer of a clip's output buffer (F*H*W*3 floats, owned by the library). */
+int ssvp_output_device_ptr(ssvp_ctx *ctx, int clip_id, void **dev_ptr);
+
+/* Statistics of the last ssvp_gather_filter call (waits for it): examined candidates (window
+ * pixels inside the image), accepted samples |S| summed over pixels, and the sum of weights W
+ * (Sec. "Filtering" reports W / |S|).  Any pointer may be NULL. */
+int ssvp_read_stats(ssvp_ctx *ctx, unsigned long long *examined, unsigned long long *accepted, double *sum_w);
+
+/* Lower-median valid input depth of a loaded clip (waits for the load). */
+int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median);
+
+/* Wait for all work queued on the context's stream; returns the first pending error. */
+int ssvp_sync(ssvp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSVP_H */

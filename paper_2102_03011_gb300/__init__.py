@@ -1,0 +1,179 @@
+"""Python binding of libssvp.so, the GB300 scene-space gather-and-filter library.
+
+Argument marshalling only: every step of the path runs in the library's CUDA kernels.  The
+functions carry the names of the C entry points declared in ``include/ssvp.h``; they accept
+torch tensors (host or CUDA) or numpy arrays where the C call takes a pointer, and raise
+``SsvpError`` when the C call returns a non-zero status.  There is no CPU fallback: importing
+this package fails when ``libssvp.so`` has not been built (``_build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libssvp.so")
+
+SSVP_OK, SSVP_EINVAL, SSVP_ENOMEM, SSVP_ECUDA = 0, -1, -2, -3
+SSVP_ENOCLIP, SSVP_ENOCAM, SSVP_ETIMEOUT, SSVP_EDEVICE = -4, -5, -6, -7
+SSVP_MEM_HOST, SSVP_MEM_DEVICE = 0, 1
+SSVP_COLOUR_F32, SSVP_COLOUR_F16 = 0, 1
+SSVP_MODE_DENOISE, SSVP_MODE_APERTURE, SSVP_MODE_LEARNED, SSVP_MODE_MEAN = 0, 1, 2, 3
+SSVP_MAX_CLIPS, SSVP_MAX_K, SSVP_MAX_HALF_WINDOW = 64, 31, 127
+
+
+class SsvpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ssvp error {code}: {msg}")
+        self.code = code
+
+
+class ssvp_params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("k", ctypes.c_int32), ("half_window", ctypes.c_int32),
+                ("frame_begin", ctypes.c_int32), ("frame_end", ctypes.c_int32),
+                ("crop_x", ctypes.c_int32), ("crop_y", ctypes.c_int32), ("crop_w", ctypes.c_int32),
+                ("crop_h", ctypes.c_int32), ("radius", ctypes.c_float), ("sigma_rgb", ctypes.c_float),
+                ("sigma_xyz", ctypes.c_float), ("sigma_f", ctypes.c_float), ("aperture", ctypes.c_float),
+                ("focal_depth", ctypes.c_float), ("a0", ctypes.c_float), ("lens_samples", ctypes.c_int32),
+                ("cap", ctypes.c_int32), ("max_samples", ctypes.c_int32), ("conf_threshold", ctypes.c_float),
+                ("membership_out", ctypes.c_void_p), ("pixel_stats_out", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2102_03011_gb300._build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    P = ctypes.POINTER(ssvp_params)
+    sig = {
+        "ssvp_params_default": (None, [P]),
+        "ssvp_create": (i, [ctypes.POINTER(vp), i, vp]),
+        "ssvp_destroy": (None, [vp]),
+        "ssvp_last_error": (ctypes.c_char_p, [vp]),
+        "ssvp_set_stream": (i, [vp, vp]),
+        "ssvp_load_clip": (i, [vp, i, i, i, i, vp, vp, i, i]),
+        "ssvp_unload_clip": (i, [vp, i]),
+        "ssvp_set_cameras": (i, [vp, i, vp, i, vp]),
+        "ssvp_gather_filter": (i, [vp, P, ctypes.POINTER(ctypes.c_int), i]),
+        "ssvp_read_output": (i, [vp, i, i, i, vp, i]),
+        "ssvp_output_device_ptr": (i, [vp, i, ctypes.POINTER(vp)]),
+        "ssvp_read_stats": (i, [vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong),
+                                ctypes.POINTER(ctypes.c_double)]),
+        "ssvp_clip_median_depth": (i, [vp, i, ctypes.POINTER(f)]),
+        "ssvp_sync": (i, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _ptr(x):
+    """(address, on_device) of a torch tensor, numpy array or raw address."""
+    if x is None:
+        return None, False
+    if isinstance(x, int):
+        return x, False
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), bool(x.is_cuda)
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, False
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def _check(ctx, rc):
+    if rc != SSVP_OK:
+        msg = lib.ssvp_last_error(ctx)
+        raise SsvpError(rc, msg.decode() if msg else "")
+
+
+def ssvp_params_default() -> ssvp_params:
+    p = ssvp_params()
+    lib.ssvp_params_default(ctypes.byref(p))
+    return p
+
+
+def ssvp_create(cuda_device: int = 0, cuda_stream=None):
+    """Returns a context handle; cuda_stream is a torch.cuda.Stream, a raw cudaStream_t or None."""
+    ctx = ctypes.c_void_p()
+    s = cuda_stream.cuda_stream if hasattr(cuda_stream, "cuda_stream") else cuda_stream
+    _check(None, lib.ssvp_create(ctypes.byref(ctx), int(cuda_device), s))
+    return ctx
+
+
+def ssvp_destroy(ctx) -> None:
+    lib.ssvp_destroy(ctx)
+
+
+def ssvp_last_error(ctx=None) -> str:
+    m = lib.ssvp_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def ssvp_set_stream(ctx, cuda_stream) -> None:
+    s = cuda_stream.cuda_stream if hasattr(cuda_stream, "cuda_stream") else cuda_stream
+    _check(ctx, lib.ssvp_set_stream(ctx, s))
+
+
+def ssvp_load_clip(ctx, clip_id: int, W: int, H: int, F: int, rgb, depth, mem_kind: int | None = None,
+                   colour_fmt: int = SSVP_COLOUR_F32) -> None:
+    (pr, dr), (pd, dd) = _ptr(rgb), _ptr(depth)
+    if mem_kind is None:
+        if dr != dd:
+            raise ValueError("rgb and depth must both be on the host or both on the device")
+        mem_kind = SSVP_MEM_DEVICE if dr else SSVP_MEM_HOST
+    _check(ctx, lib.ssvp_load_clip(ctx, clip_id, W, H, F, pr, pd, mem_kind, colour_fmt))
+
+
+def ssvp_unload_clip(ctx, clip_id: int) -> None:
+    _check(ctx, lib.ssvp_unload_clip(ctx, clip_id))
+
+
+def ssvp_set_cameras(ctx, clip_id: int, K, per_frame_K: int, w2c) -> None:
+    import numpy as np
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    w2c = np.ascontiguousarray(w2c, dtype=np.float64)
+    _check(ctx, lib.ssvp_set_cameras(ctx, clip_id, K.ctypes.data, int(per_frame_K), w2c.ctypes.data))
+
+
+def ssvp_gather_filter(ctx, params: ssvp_params, clip_ids) -> None:
+    ids = (ctypes.c_int * len(clip_ids))(*[int(c) for c in clip_ids])
+    _check(ctx, lib.ssvp_gather_filter(ctx, ctypes.byref(params), ids, len(clip_ids)))
+
+
+def ssvp_read_output(ctx, clip_id: int, frame_begin: int, frame_end: int, dst, mem_kind: int | None = None) -> None:
+    p, dev = _ptr(dst)
+    if mem_kind is None:
+        mem_kind = SSVP_MEM_DEVICE if dev else SSVP_MEM_HOST
+    _check(ctx, lib.ssvp_read_output(ctx, clip_id, frame_begin, frame_end, p, mem_kind))
+
+
+def ssvp_output_device_ptr(ctx, clip_id: int) -> int:
+    out = ctypes.c_void_p()
+    _check(ctx, lib.ssvp_output_device_ptr(ctx, clip_id, ctypes.byref(out)))
+    return int(out.value or 0)
+
+
+def ssvp_read_stats(ctx):
+    """-> (examined, accepted, sum_w) of the last gather call."""
+    e, a, w = ctypes.c_ulonglong(), ctypes.c_ulonglong(), ctypes.c_double()
+    _check(ctx, lib.ssvp_read_stats(ctx, ctypes.byref(e), ctypes.byref(a), ctypes.byref(w)))
+    return int(e.value), int(a.value), float(w.value)
+
+
+def ssvp_clip_median_depth(ctx, clip_id: int) -> float:
+    m = ctypes.c_float()
+    _check(ctx, lib.ssvp_clip_median_depth(ctx, clip_id, ctypes.byref(m)))
+    return float(m.value)
+
+
+def ssvp_sync(ctx) -> None:
+    _check(ctx, lib.ssvp_sync(ctx))

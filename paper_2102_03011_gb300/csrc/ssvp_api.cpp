@@ -1,0 +1,494 @@
+// ssvp_api.cpp - host runtime behind the C ABI of include/ssvp.h: context and device buffers,
+// input upload and packing, FP64 camera composition (step A1), argument checks, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ssvp.h"
+#include "ssvp_internal.h"
+
+using ssvp::GatherArgs;
+using ssvp::PairGeom;
+using ssvp::Planes;
+
+namespace {
+
+struct Clip {
+    bool loaded = false;
+    bool has_cams = false;
+    Planes p{};
+    std::vector<double> K;    // F * 9
+    std::vector<double> w2c;  // F * 12
+};
+
+char g_create_error[512] = "";
+
+}  // namespace
+
+struct ssvp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Clip clips[SSVP_MAX_CLIPS];
+    char err[512] = "";
+    // device scratch
+    unsigned long long *stat_counts = nullptr;  // [2]
+    double *stat_sumw = nullptr;
+    unsigned int *median_scratch = nullptr;
+    PairGeom *geom = nullptr;
+    size_t geom_cap = 0;  // entries
+    void *staging = nullptr;
+    size_t staging_bytes = 0;
+    std::vector<PairGeom> host_geom;
+};
+
+namespace {
+
+int fail(ssvp_ctx *c, int code, const char *fmt, ...) {
+    char *dst = c ? c->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(ssvp_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(c, SSVP_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(c, SSVP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+void free_clip(Clip &c) {
+    if (c.p.depth) cudaFree(c.p.depth);
+    if (c.p.colour) cudaFree(c.p.colour);
+    if (c.p.out) cudaFree(c.p.out);
+    if (c.p.median) cudaFree(c.p.median);
+    c = Clip();
+}
+
+bool finite_all(const double *v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// ---------------------------------------------------------------- A1: camera composition (FP64)
+
+void split(double x, float &hi, float &lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+void mat3_mul(const double *A, const double *B, double *C) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
+// M = K_J R_JO K_O^-1, e = K_J t_JO with R_JO = R_J R_O^T, t_JO = t_J - R_JO t_O: maps
+// d (u, v, 1) of frame O to homogeneous pixel coordinates of frame J (C_J C_O^-1 of Eq. 2).
+void compose_pair(const double *KO, const double *wO, const double *KJ, const double *wJ, bool same, int dJ,
+                  double sigma_f, PairGeom &g) {
+    double M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, e[3] = {0, 0, 0};
+    if (!same) {
+        double RO[9], RJ[9], tO[3], tJ[3];
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) { RO[3 * i + j] = wO[4 * i + j]; RJ[3 * i + j] = wJ[4 * i + j]; }
+            tO[i] = wO[4 * i + 3];
+            tJ[i] = wJ[4 * i + 3];
+        }
+        double RJO[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                RJO[3 * i + j] = RJ[3 * i] * RO[3 * j] + RJ[3 * i + 1] * RO[3 * j + 1] + RJ[3 * i + 2] * RO[3 * j + 2];
+        double tJO[3];
+        for (int i = 0; i < 3; ++i) tJO[i] = tJ[i] - (RJO[3 * i] * tO[0] + RJO[3 * i + 1] * tO[1] + RJO[3 * i + 2] * tO[2]);
+        // K_O^-1 of an upper-triangular, zero-skew K
+        const double KOi[9] = {1.0 / KO[0], 0.0, -KO[2] / KO[0], 0.0, 1.0 / KO[4], -KO[5] / KO[4], 0.0, 0.0, 1.0};
+        double T[9];
+        mat3_mul(KJ, RJO, T);
+        mat3_mul(T, KOi, M);
+        for (int i = 0; i < 3; ++i) e[i] = KJ[3 * i] * tJO[0] + KJ[3 * i + 1] * tJO[1] + KJ[3 * i + 2] * tJO[2];
+    }
+    for (int i = 0; i < 9; ++i) split(M[i], g.M_hi[i], g.M_lo[i]);
+    for (int i = 0; i < 3; ++i) split(e[i], g.e_hi[i], g.e_lo[i]);
+    g.ifx = (float)(1.0 / KJ[0]);
+    g.ify = (float)(1.0 / KJ[4]);
+    g.cx = (float)KJ[2];
+    g.cy = (float)KJ[5];
+    g.beta = (float)((double)dJ * dJ / (2.0 * sigma_f * sigma_f));
+    g.same = same ? 1 : 0;
+    g.pad_ = 0;
+}
+
+int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
+    if (!p) return fail(ctx, SSVP_EINVAL, "params is NULL");
+    if (p->mode != SSVP_MODE_DENOISE && p->mode != SSVP_MODE_MEAN)
+        return fail(ctx, SSVP_EINVAL, "mode %d is not available in this build", p->mode);
+    if (p->k < 1 || p->k > SSVP_MAX_K || (p->k & 1) == 0) return fail(ctx, SSVP_EINVAL, "k=%d must be odd in [1, 31]", p->k);
+    if (p->half_window < 0 || p->half_window > SSVP_MAX_HALF_WINDOW)
+        return fail(ctx, SSVP_EINVAL, "half_window=%d must be in [0, 127]", p->half_window);
+    if (!(std::isfinite(p->radius) && p->radius != 0.0f)) return fail(ctx, SSVP_EINVAL, "radius must be finite and non-zero");
+    if (!(p->sigma_rgb > 0.0f && std::isfinite(p->sigma_rgb))) return fail(ctx, SSVP_EINVAL, "sigma_rgb must be > 0");
+    if (!(p->sigma_f > 0.0f && std::isfinite(p->sigma_f))) return fail(ctx, SSVP_EINVAL, "sigma_f must be > 0");
+    if (!std::isfinite(p->sigma_xyz)) return fail(ctx, SSVP_EINVAL, "sigma_xyz must be finite");
+    if (p->crop_w < 0 || p->crop_h < 0) return fail(ctx, SSVP_EINVAL, "negative crop size");
+    return SSVP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ssvp_params_default(ssvp_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->mode = SSVP_MODE_DENOISE;
+    p->k = 7;
+    p->half_window = 15;
+    p->frame_begin = 0;
+    p->frame_end = -1;  // all frames
+    p->radius = -0.005f;
+    p->sigma_rgb = 40.0f / 255.0f;
+    p->sigma_xyz = 0.0f;
+    p->sigma_f = 6.0f;
+    p->aperture = 0.05f;
+    p->focal_depth = 0.0f;
+    p->a0 = 0.0f;
+    p->lens_samples = 16;
+    p->cap = 31;
+    p->max_samples = 64;
+    p->conf_threshold = 0.5f;
+}
+
+int ssvp_create(ssvp_ctx **out, int cuda_device, void *cuda_stream) {
+    if (!out) return fail(nullptr, SSVP_EINVAL, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return fail(nullptr, SSVP_EDEVICE, "no CUDA device: %s", e == cudaSuccess ? "count is 0" : cudaGetErrorString(e));
+    }
+    if (cuda_device < 0 || cuda_device >= n) return fail(nullptr, SSVP_EINVAL, "device %d out of range [0, %d)", cuda_device, n);
+    if ((e = cudaSetDevice(cuda_device)) != cudaSuccess) return fail(nullptr, SSVP_EDEVICE, "cudaSetDevice: %s", cudaGetErrorString(e));
+    ssvp_ctx *ctx = new (std::nothrow) ssvp_ctx();
+    if (!ctx) return fail(nullptr, SSVP_ENOMEM, "host allocation failed");
+    ctx->device = cuda_device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    if ((e = cudaMalloc(&ctx->stat_counts, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->stat_sumw, sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->median_scratch, ssvp::median_scratch_words() * sizeof(unsigned int))) != cudaSuccess) {
+        int rc = fail(nullptr, e == cudaErrorMemoryAllocation ? SSVP_ENOMEM : SSVP_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+        ssvp_destroy(ctx);
+        return rc;
+    }
+    cudaMemsetAsync(ctx->stat_counts, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    cudaMemsetAsync(ctx->stat_sumw, 0, sizeof(double), ctx->stream);
+    *out = ctx;
+    return SSVP_OK;
+}
+
+void ssvp_destroy(ssvp_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &c : ctx->clips) free_clip(c);
+    if (ctx->stat_counts) cudaFree(ctx->stat_counts);
+    if (ctx->stat_sumw) cudaFree(ctx->stat_sumw);
+    if (ctx->median_scratch) cudaFree(ctx->median_scratch);
+    if (ctx->geom) cudaFree(ctx->geom);
+    if (ctx->staging) cudaFree(ctx->staging);
+    delete ctx;
+}
+
+const char *ssvp_last_error(const ssvp_ctx *ctx) { return ctx ? ctx->err : g_create_error; }
+
+int ssvp_set_stream(ssvp_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return SSVP_OK;
+}
+
+int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float *rgb, const float *depth, int mem_kind,
+                   int colour_fmt) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    if (W < 1 || H < 1 || F < 1 || W > 16384 || H > 16384 || F > 65535)
+        return fail(ctx, SSVP_EINVAL, "bad clip shape W=%d H=%d F=%d", W, H, F);
+    if (!rgb || !depth) return fail(ctx, SSVP_EINVAL, "rgb and depth must not be NULL");
+    if (mem_kind != SSVP_MEM_HOST && mem_kind != SSVP_MEM_DEVICE) return fail(ctx, SSVP_EINVAL, "bad mem_kind %d", mem_kind);
+    if (colour_fmt != SSVP_COLOUR_F32 && colour_fmt != SSVP_COLOUR_F16)
+        return fail(ctx, SSVP_EINVAL, "bad colour_fmt %d", colour_fmt);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    Clip &c = ctx->clips[clip_id];
+    if (c.loaded) {
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        free_clip(c);
+    }
+    Planes &p = c.p;
+    p.W = W;
+    p.H = H;
+    p.F = F;
+    p.pitch = ((W + 2 * ssvp::kPad) + 31) / 32 * 32;
+    p.rows = H + 2 * ssvp::kPad;
+    p.fstride = (long long)p.pitch * p.rows;
+    p.colour_fmt = colour_fmt;
+    const size_t texel = colour_fmt == SSVP_COLOUR_F32 ? 16 : 8;
+    const size_t nplane = (size_t)F * (size_t)p.fstride;
+    const size_t nout = (size_t)F * H * W * 3;
+    cudaError_t e;
+    if ((e = cudaMalloc(&p.depth, nplane * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&p.colour, nplane * texel)) != cudaSuccess ||
+        (e = cudaMalloc(&p.out, nout * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&p.median, sizeof(float))) != cudaSuccess) {
+        free_clip(c);
+        return cuda_fail(ctx, e, "cudaMalloc (clip planes)");
+    }
+    // padding and invalid depth: NaN (all bits set); colour 0; output 0
+    CK(cudaMemsetAsync(p.depth, 0xff, nplane * sizeof(float), ctx->stream), "cudaMemsetAsync");
+    CK(cudaMemsetAsync(p.colour, 0, nplane * texel, ctx->stream), "cudaMemsetAsync");
+    CK(cudaMemsetAsync(p.out, 0, nout * sizeof(float), ctx->stream), "cudaMemsetAsync");
+    const size_t frame_px = (size_t)W * H;
+    if (mem_kind == SSVP_MEM_DEVICE) {
+        CK(ssvp::launch_pack(rgb, depth, W, H, F, p, 0, ctx->stream), "pack kernel");
+    } else {
+        // stage frames through a device buffer in chunks of about 256 MB
+        const size_t per_frame = frame_px * 16;
+        int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)F, (size_t)(256u << 20) / per_frame));
+        const size_t need = per_frame * (size_t)chunk;
+        if (ctx->staging_bytes < need) {
+            CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+            if (ctx->staging) cudaFree(ctx->staging);
+            ctx->staging = nullptr;
+            ctx->staging_bytes = 0;
+            if ((e = cudaMalloc(&ctx->staging, need)) != cudaSuccess) {
+                free_clip(c);
+                return cuda_fail(ctx, e, "cudaMalloc (staging)");
+            }
+            ctx->staging_bytes = need;
+        }
+        float *srgb = (float *)ctx->staging;
+        float *sdep = srgb + frame_px * 3 * (size_t)chunk;
+        for (int f0 = 0; f0 < F; f0 += chunk) {
+            int nf = std::min(chunk, F - f0);
+            CK(cudaMemcpyAsync(srgb, rgb + frame_px * 3 * (size_t)f0, frame_px * 3 * nf * sizeof(float),
+                               cudaMemcpyHostToDevice, ctx->stream), "cudaMemcpyAsync (rgb)");
+            CK(cudaMemcpyAsync(sdep, depth + frame_px * (size_t)f0, frame_px * nf * sizeof(float), cudaMemcpyHostToDevice,
+                               ctx->stream), "cudaMemcpyAsync (depth)");
+            CK(ssvp::launch_pack(srgb, sdep, W, H, nf, p, f0, ctx->stream), "pack kernel");
+        }
+    }
+    CK(ssvp::launch_median(p, ctx->median_scratch, ctx->stream), "median kernels");
+    c.loaded = true;
+    c.has_cams = false;
+    return SSVP_OK;
+}
+
+int ssvp_unload_clip(ssvp_ctx *ctx, int clip_id) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    if (!ctx->clips[clip_id].loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    free_clip(ctx->clips[clip_id]);
+    return SSVP_OK;
+}
+
+int ssvp_set_cameras(ssvp_ctx *ctx, int clip_id, const double *K, int per_frame_K, const double *w2c) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    Clip &c = ctx->clips[clip_id];
+    if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    if (!K || !w2c) return fail(ctx, SSVP_EINVAL, "K and w2c must not be NULL");
+    const int F = c.p.F;
+    std::vector<double> Kv((size_t)F * 9), Wv(w2c, w2c + (size_t)F * 12);
+    for (int f = 0; f < F; ++f) std::memcpy(&Kv[9 * (size_t)f], K + (per_frame_K ? 9 * (size_t)f : 0), 9 * sizeof(double));
+    if (!finite_all(Kv.data(), Kv.size()) || !finite_all(Wv.data(), Wv.size()))
+        return fail(ctx, SSVP_EINVAL, "cameras must be finite");
+    for (int f = 0; f < F; ++f) {
+        const double *k = &Kv[9 * (size_t)f];
+        if (!(k[0] > 0 && k[4] > 0) || k[1] != 0.0 || k[3] != 0.0 || k[6] != 0.0 || k[7] != 0.0 || k[8] != 1.0)
+            return fail(ctx, SSVP_EINVAL, "frame %d: K must be [[fx,0,cx],[0,fy,cy],[0,0,1]] with fx, fy > 0", f);
+        const double *R = &Wv[12 * (size_t)f];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double d = R[4 * i] * R[4 * j] + R[4 * i + 1] * R[4 * j + 1] + R[4 * i + 2] * R[4 * j + 2];
+                if (std::fabs(d - (i == j ? 1.0 : 0.0)) > 1e-6)
+                    return fail(ctx, SSVP_EINVAL, "frame %d: w2c rotation is not orthonormal", f);
+            }
+    }
+    c.K.swap(Kv);
+    c.w2c.swap(Wv);
+    c.has_cams = true;
+    return SSVP_OK;
+}
+
+int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, int n_clips) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    int rc = check_params(ctx, params);
+    if (rc != SSVP_OK) return rc;
+    if (!clip_ids || n_clips < 1 || n_clips > SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "bad clip list");
+    const ssvp_params &p = *params;
+    const int T = p.half_window, ns = 2 * T + 1;
+    // resolve ranges and compose the geometry of every (clip, O, slot)
+    std::vector<int> fb(n_clips), nout(n_clips), cx0(n_clips), cy0(n_clips), cw(n_clips), chh(n_clips);
+    size_t total = 0;
+    for (int i = 0; i < n_clips; ++i) {
+        int id = clip_ids[i];
+        if (id < 0 || id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", id);
+        Clip &c = ctx->clips[id];
+        if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", id);
+        if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", id);
+        int b = p.frame_begin, e = p.frame_end < 0 ? c.p.F : p.frame_end;
+        if (b < 0 || e > c.p.F || b > e) return fail(ctx, SSVP_EINVAL, "frame range [%d, %d) outside clip %d (F=%d)", b, e, id, c.p.F);
+        int x0 = p.crop_x, y0 = p.crop_y, w = p.crop_w, h = p.crop_h;
+        if (w == 0 || h == 0) { x0 = 0; y0 = 0; w = c.p.W; h = c.p.H; }
+        if (x0 < 0 || y0 < 0 || x0 + w > c.p.W || y0 + h > c.p.H)
+            return fail(ctx, SSVP_EINVAL, "crop (%d, %d, %d, %d) outside clip %d (%dx%d)", x0, y0, w, h, id, c.p.W, c.p.H);
+        fb[i] = b; nout[i] = e - b; cx0[i] = x0; cy0[i] = y0; cw[i] = w; chh[i] = h;
+        total += (size_t)(e - b) * ns;
+    }
+    if ((p.membership_out || p.pixel_stats_out) && (n_clips != 1 || nout[0] > 1))
+        return fail(ctx, SSVP_EINVAL, "debug outputs need exactly one clip and at most one output frame");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (total > ctx->geom_cap) {
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        if (ctx->geom) cudaFree(ctx->geom);
+        ctx->geom = nullptr;
+        ctx->geom_cap = 0;
+        size_t cap = std::max<size_t>(total, 4096);
+        CK(cudaMalloc(&ctx->geom, cap * sizeof(PairGeom)), "cudaMalloc (geometry)");
+        ctx->geom_cap = cap;
+    }
+    ctx->host_geom.resize(std::max<size_t>(total, 1));
+    size_t off = 0;
+    for (int i = 0; i < n_clips; ++i) {
+        Clip &c = ctx->clips[clip_ids[i]];
+        for (int oi = 0; oi < nout[i]; ++oi) {
+            const int O = fb[i] + oi;
+            for (int j = 0; j < ns; ++j) {
+                const int J = O - T + j;
+                PairGeom &g = ctx->host_geom[off + (size_t)oi * ns + j];
+                if (J < 0 || J >= c.p.F) {
+                    std::memset(&g, 0, sizeof(g));
+                    g.J = -1;
+                    continue;
+                }
+                compose_pair(&c.K[9 * (size_t)O], &c.w2c[12 * (size_t)O], &c.K[9 * (size_t)J], &c.w2c[12 * (size_t)J],
+                             J == O, J - O, p.sigma_f, g);
+                g.J = J;
+            }
+        }
+        off += (size_t)nout[i] * ns;
+    }
+    // pageable source: the call returns once the table is staged, so host_geom may be reused
+    if (total) CK(cudaMemcpyAsync(ctx->geom, ctx->host_geom.data(), total * sizeof(PairGeom), cudaMemcpyHostToDevice, ctx->stream),
+                  "cudaMemcpyAsync (geometry)");
+    CK(cudaMemsetAsync(ctx->stat_counts, 0, 2 * sizeof(unsigned long long), ctx->stream), "cudaMemsetAsync");
+    CK(cudaMemsetAsync(ctx->stat_sumw, 0, sizeof(double), ctx->stream), "cudaMemsetAsync");
+    off = 0;
+    for (int i = 0; i < n_clips; ++i) {
+        Clip &c = ctx->clips[clip_ids[i]];
+        GatherArgs a{};
+        a.clip = c.p;
+        a.geom = ctx->geom + off;
+        a.frame_begin = fb[i];
+        a.n_out = nout[i];
+        a.n_slots = ns;
+        a.T = T;
+        a.x0 = cx0[i]; a.y0 = cy0[i]; a.cw = cw[i]; a.ch = chh[i];
+        a.k = p.k;
+        a.mode = p.mode;
+        a.radius = p.radius;
+        a.sigma_rgb = p.sigma_rgb;
+        a.sigma_xyz = p.sigma_xyz;
+        a.sigma_f = p.sigma_f;
+        a.membership = (int32_t *)p.membership_out;
+        a.pixel_stats = (int32_t *)p.pixel_stats_out;
+        a.stat_counts = ctx->stat_counts;
+        a.stat_sumw = ctx->stat_sumw;
+        CK(ssvp::launch_gather(a, ctx->stream), "gather kernel");
+        off += (size_t)nout[i] * ns;
+    }
+    return SSVP_OK;
+}
+
+int ssvp_read_output(ssvp_ctx *ctx, int clip_id, int frame_begin, int frame_end, float *dst, int mem_kind) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    Clip &c = ctx->clips[clip_id];
+    if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    if (!dst) return fail(ctx, SSVP_EINVAL, "dst is NULL");
+    if (frame_begin < 0 || frame_end > c.p.F || frame_begin > frame_end)
+        return fail(ctx, SSVP_EINVAL, "frame range [%d, %d) outside the clip", frame_begin, frame_end);
+    if (mem_kind != SSVP_MEM_HOST && mem_kind != SSVP_MEM_DEVICE) return fail(ctx, SSVP_EINVAL, "bad mem_kind %d", mem_kind);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t per = (size_t)c.p.W * c.p.H * 3;
+    const size_t bytes = per * (size_t)(frame_end - frame_begin) * sizeof(float);
+    if (bytes) {
+        CK(cudaMemcpyAsync(dst, c.p.out + per * (size_t)frame_begin, bytes,
+                           mem_kind == SSVP_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream),
+           "cudaMemcpyAsync (output)");
+    }
+    if (mem_kind == SSVP_MEM_HOST) CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    return SSVP_OK;
+}
+
+int ssvp_output_device_ptr(ssvp_ctx *ctx, int clip_id, void **dev_ptr) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    if (!ctx->clips[clip_id].loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    if (!dev_ptr) return fail(ctx, SSVP_EINVAL, "dev_ptr is NULL");
+    *dev_ptr = ctx->clips[clip_id].p.out;
+    return SSVP_OK;
+}
+
+int ssvp_read_stats(ssvp_ctx *ctx, unsigned long long *examined, unsigned long long *accepted, double *sum_w) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    unsigned long long cnt[2];
+    double sw;
+    CK(cudaMemcpyAsync(cnt, ctx->stat_counts, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
+    CK(cudaMemcpyAsync(&sw, ctx->stat_sumw, sizeof(sw), cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    if (examined) *examined = cnt[0];
+    if (accepted) *accepted = cnt[1];
+    if (sum_w) *sum_w = sw;
+    return SSVP_OK;
+}
+
+int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    if (!ctx->clips[clip_id].loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    if (!median) return fail(ctx, SSVP_EINVAL, "median is NULL");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(median, ctx->clips[clip_id].p.median, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    return SSVP_OK;
+}
+
+int ssvp_sync(ssvp_ctx *ctx) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    CK(cudaGetLastError(), "pending CUDA error");
+    return SSVP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,381 @@
+// ssvp_gather.cu - the fused scene-space gather + filter kernel (steps A3-A7).
+//
+// One thread per output pixel p of frame O, CTAs of 32 x 8 pixels.  For every window slot j
+// (frame J = O - T + j) the thread projects its reference point into J, tests the k x k
+// candidates around the projection against the radius (the back-projection test of Eq. 2,
+// seeded by the output depth) and accumulates the Eq. 4 weighted colour (Eq. 3).
+//
+// Precision.  The radius is ~0.5 % of the scene depth, so the distance test needs the reference
+// point in J's pixel grid to ~1e-9 relative, beyond FP32.  The per-(pixel, J) reference
+// quantities (u', v' = projected position, z' = depth in J) are therefore carried as unevaluated
+// FP32 pairs ("double-float", error-free transformations with FMA), computed from the FP64 camera
+// composition the host splits into hi/lo pairs.  The per-candidate test then only forms small
+// differences, all in plain FP32:
+//     Y_q - y_ref = ((d_q - z') (q_x - c_x) + z' (q_x - u')) / f_x, ... , d_q - z'
+// so the FP32 error of the distance is ~1e-7 of the radius rather than ~1e-7 of the depth.
+//
+// Accepted candidates are recorded in a per-thread bit mask during the test loop and filtered
+// afterwards by iterating the set bits, so a warp pays for the filter arithmetic only as often
+// as its busiest lane accepts (warp-level compaction of the accepted samples).
+#include <cuda_fp16.h>
+
+#include "ssvp_internal.h"
+
+namespace ssvp {
+namespace {
+
+// ---------------------------------------------------------------- double-float helpers
+// The _rn intrinsics are never contracted into FMAs, which keeps the error-free transforms exact.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // requires |a| >= |b| (or a == 0)
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    df s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    df p = two_prod(a.hi, b);
+    return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+
+// a / b given r = 1 / b.hi (correctly rounded): one correction step.
+__device__ __forceinline__ df df_div(df a, df b, float r) {
+    float q1 = __fmul_rn(a.hi, r);
+    df p = two_prod(q1, b.hi);
+    float rem = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), __fsub_rn(a.lo, __fmul_rn(q1, b.lo)));
+    return fast_two_sum(q1, __fmul_rn(rem, r));
+}
+
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int CFMT>
+__device__ __forceinline__ float3 load_colour(const void *base, long long idx) {
+    if (CFMT == 0) {
+        float4 c = __ldg(reinterpret_cast<const float4 *>(base) + idx);
+        return make_float3(c.x, c.y, c.z);
+    } else {
+        uint2 raw = __ldg(reinterpret_cast<const uint2 *>(base) + idx);
+        __half2 rg = *reinterpret_cast<__half2 *>(&raw.x);
+        __half2 b0 = *reinterpret_cast<__half2 *>(&raw.y);
+        float2 f = __half22float2(rg);
+        return make_float3(f.x, f.y, __low2float(b0));
+    }
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kTileX = 32, kTileY = 8, kThreads = kTileX * kTileY;
+constexpr int kSlotVec = 6;  // float4 words of per-slot geometry in shared memory
+
+// Shared per-slot geometry (6 x float4):
+//  q0 = mb_hi0 mb_hi1 mb_hi2 mb_lo0   (mb = M (u0, v0, 1) of the CTA's first pixel, double-float)
+//  q1 = mb_lo1 mb_lo2 M00 M01
+//  q2 = M10 M11 M20 M21
+//  q3 = e_hi0 e_hi1 e_hi2 e_lo0
+//  q4 = e_lo1 e_lo2 ifx ify
+//  q5 = cx cy beta*log2e J(bits)
+__device__ void build_slot(const PairGeom &g, float u0, float v0, float4 *dst) {
+    df mb[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        df t = df_mul_f({g.M_hi[3 * r], g.M_lo[3 * r]}, u0);
+        t = df_add(t, df_mul_f({g.M_hi[3 * r + 1], g.M_lo[3 * r + 1]}, v0));
+        mb[r] = df_add(t, {g.M_hi[3 * r + 2], g.M_lo[3 * r + 2]});
+    }
+    dst[0] = make_float4(mb[0].hi, mb[1].hi, mb[2].hi, mb[0].lo);
+    dst[1] = make_float4(mb[1].lo, mb[2].lo, g.M_hi[0], g.M_hi[1]);
+    dst[2] = make_float4(g.M_hi[3], g.M_hi[4], g.M_hi[6], g.M_hi[7]);
+    dst[3] = make_float4(g.e_hi[0], g.e_hi[1], g.e_hi[2], g.e_lo[0]);
+    dst[4] = make_float4(g.e_lo[1], g.e_lo[2], g.ifx, g.ify);
+    dst[5] = make_float4(g.cx, g.cy, g.beta * kLog2e, __int_as_float(g.J));
+}
+
+// K > 0: compile-time window width (k*k <= 64, one 64-bit accept mask per frame).
+// K == 0: runtime k up to 31, one 32-bit accept mask per window row.
+template <int K, int CFMT, bool DEBUG>
+__global__ void __launch_bounds__(kThreads) gather_kernel(const GatherArgs a) {
+    extern __shared__ float4 sgeom[];
+    __shared__ float s_const[4];
+    __shared__ unsigned long long s_cnt[2][kThreads / 32];
+    __shared__ float s_w[kThreads / 32];
+
+    const int oi = blockIdx.z;
+    const int O = a.frame_begin + oi;
+    const int u0 = a.x0 + blockIdx.x * kTileX, v0 = a.y0 + blockIdx.y * kTileY;
+    for (int j = threadIdx.x; j < a.n_slots; j += kThreads)
+        build_slot(a.geom[(long long)oi * a.n_slots + j], (float)u0, (float)v0, sgeom + kSlotVec * j);
+    if (threadIdx.x == 0) {
+        float r = a.radius > 0.0f ? a.radius : -a.radius * *a.clip.median;
+        float sx = a.sigma_xyz > 0.0f ? a.sigma_xyz : r;
+        s_const[0] = r * r;
+        s_const[1] = kLog2e / (2.0f * a.sigma_rgb * a.sigma_rgb);
+        s_const[2] = kLog2e / (2.0f * sx * sx);
+        s_const[3] = a.mode == 3 ? 0.0f : 1.0f;
+    }
+    __syncthreads();
+
+    const Planes &P = a.clip;
+    const int k = K > 0 ? K : a.k;
+    const int h = (k - 1) >> 1;
+    const float r2 = s_const[0], a_rgb = s_const[1], a_xyz = s_const[2];
+    const bool weighted = s_const[3] != 0.0f;
+    const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
+    const int u = u0 + tx, v = v0 + ty;
+    const bool active = u < a.x0 + a.cw && v < a.y0 + a.ch;
+    const long long crop_idx = (long long)(v - a.y0) * a.cw + (u - a.x0);
+    const int rec_words = 3 + (k * k + 31) / 32;
+
+    int n_acc = 0, n_exam = 0;
+    float acc_w = 0.0f, acc_r = 0.0f, acc_g = 0.0f, acc_b = 0.0f;
+    float3 cref = make_float3(0.f, 0.f, 0.f);
+    float dref = 0.0f;
+    if (active) {
+        const long long pix = (long long)O * P.fstride + (long long)(v + kPad) * P.pitch + (u + kPad);
+        dref = __ldg(P.depth + pix);
+        cref = load_colour<CFMT>(P.colour, pix);
+    }
+    const bool gather = active && dref > 0.0f;  // false for NaN (invalid) depth
+    if (DEBUG && active && !gather && a.membership) {
+        for (int j = 0; j < a.n_slots; ++j) a.membership[(crop_idx * a.n_slots + j) * rec_words] = -2;
+    }
+
+    if (gather) {
+        const float du = (float)(u - u0), dv = (float)(v - v0);
+        for (int j = 0; j < a.n_slots; ++j) {
+            const float4 *g = sgeom + kSlotVec * j;
+            const float4 q5 = g[5];
+            const int J = __float_as_int(q5.w);
+            int32_t *rec = DEBUG && a.membership ? a.membership + (crop_idx * a.n_slots + j) * rec_words : nullptr;
+            if (J < 0) {
+                if (DEBUG && rec) rec[0] = -1;
+                continue;
+            }
+            const float4 q0 = g[0], q1 = g[1], q2 = g[2], q3 = g[3], q4 = g[4];
+            // m = M (u, v, 1) = M (u0, v0, 1) + M (du, dv, 0): the base in double-float, the small
+            // offset exactly enough in FP32
+            df m0 = df_add_f({q0.x, q0.w}, __fmaf_rn(q1.z, du, __fmul_rn(q1.w, dv)));
+            df m1 = df_add_f({q0.y, q1.x}, __fmaf_rn(q2.x, du, __fmul_rn(q2.y, dv)));
+            df m2 = df_add_f({q0.z, q1.y}, __fmaf_rn(q2.z, du, __fmul_rn(q2.w, dv)));
+            // w = d_ref m + e: homogeneous pixel coordinates of x_ref in J
+            df w0 = df_add(df_mul_f(m0, dref), {q3.x, q3.w});
+            df w1 = df_add(df_mul_f(m1, dref), {q3.y, q4.x});
+            df w2 = df_add(df_mul_f(m2, dref), {q3.z, q4.y});
+            if (!(w2.hi > 1e-6f * dref)) {  // behind (or at) camera J
+                if (DEBUG && rec) rec[0] = 0;
+                continue;
+            }
+            const float rz = __frcp_rn(w2.hi);
+            const df U = df_div(w0, w2, rz), V = df_div(w1, w2, rz);
+            // window centre floor(u' + 0.5) and the exact offset u' - centre in [-0.5, 0.5)
+            float cxf = floorf(U.hi + 0.5f), cyf = floorf(V.hi + 0.5f);
+            float ou = __fadd_rn(__fsub_rn(U.hi, cxf), U.lo), ov = __fadd_rn(__fsub_rn(V.hi, cyf), V.lo);
+            if (ou < -0.5f) { cxf -= 1.0f; ou += 1.0f; } else if (ou >= 0.5f) { cxf += 1.0f; ou -= 1.0f; }
+            if (ov < -0.5f) { cyf -= 1.0f; ov += 1.0f; } else if (ov >= 0.5f) { cyf += 1.0f; ov -= 1.0f; }
+            if (!(cxf >= (float)-h && cxf <= (float)(P.W - 1 + h) && cyf >= (float)-h && cyf <= (float)(P.H - 1 + h))) {
+                if (DEBUG && rec) { rec[0] = 2; }
+                continue;  // no window pixel inside the image
+            }
+            const int cx = (int)cxf, cy = (int)cyf;
+            {
+                int nx = min(cx + h, P.W - 1) - max(cx - h, 0) + 1;
+                int ny = min(cy + h, P.H - 1) - max(cy - h, 0) + 1;
+                n_exam += nx * ny;
+            }
+            const float ifx = q4.z, ify = q4.w;
+            const float zh = w2.hi, zl = w2.lo;
+            // ray_x(q) = (q_x - cx_J) / fx and z' (q_x - u') / fx as affine functions of dx
+            const float Ax0 = (cxf - (float)h - q5.x) * ifx, zix = zh * ifx, Bx0 = (-(float)h - ou) * zix;
+            const float Ay0 = (cyf - (float)h - q5.y) * ify, ziy = zh * ify, By0 = (-(float)h - ov) * ziy;
+            const long long wbase = (long long)J * P.fstride + (long long)(cy - h + kPad) * P.pitch + (cx - h + kPad);
+            const float *dwin = P.depth + wbase;
+            const float beta = q5.z;
+            if (DEBUG && rec) { rec[0] = 1; rec[1] = cx; rec[2] = cy; }
+
+            if (K > 0) {
+                float Ax[K > 0 ? K : 1], Bx[K > 0 ? K : 1];
+#pragma unroll
+                for (int dx = 0; dx < K; ++dx) {
+                    Ax[dx] = __fmaf_rn((float)dx, ifx, Ax0);
+                    Bx[dx] = __fmaf_rn((float)dx, zix, Bx0);
+                }
+                unsigned long long mask = 0ull;
+#pragma unroll
+                for (int dy = 0; dy < K; ++dy) {
+                    const float Ay = __fmaf_rn((float)dy, ify, Ay0), By = __fmaf_rn((float)dy, ziy, By0);
+                    const float *drow = dwin + (long long)dy * P.pitch;
+#pragma unroll
+                    for (int dx = 0; dx < K; ++dx) {
+                        const float dz = (__ldg(drow + dx) - zh) - zl;
+                        const float X = fmaf(dz, Ax[dx], Bx[dx]);
+                        const float Y = fmaf(dz, Ay, By);
+                        const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
+                        if (d2 < r2) mask |= 1ull << (dy * K + dx);
+                    }
+                }
+                if (DEBUG && rec) {
+                    rec[3] = (int32_t)(unsigned int)(mask & 0xffffffffull);
+                    if (K * K > 32) rec[4] = (int32_t)(unsigned int)(mask >> 32);
+                }
+                while (mask) {
+                    const int i = __ffsll((long long)mask) - 1;
+                    mask &= mask - 1ull;
+                    constexpr int KK = K > 0 ? K : 1;
+                    const int dy = i / KK, dx = i - dy * KK;
+                    const long long off = (long long)dy * P.pitch + dx;
+                    const float dz = (__ldg(dwin + off) - zh) - zl;
+                    const float X = fmaf(dz, __fmaf_rn((float)dx, ifx, Ax0), __fmaf_rn((float)dx, zix, Bx0));
+                    const float Y = fmaf(dz, __fmaf_rn((float)dy, ify, Ay0), __fmaf_rn((float)dy, ziy, By0));
+                    const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
+                    const float3 c = load_colour<CFMT>(P.colour, wbase + off);
+                    const float er = c.x - cref.x, eg = c.y - cref.y, eb = c.z - cref.z;
+                    float w = 1.0f;
+                    if (weighted) w = ex2(-fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta)));
+                    acc_r = fmaf(w, er, acc_r);
+                    acc_g = fmaf(w, eg, acc_g);
+                    acc_b = fmaf(w, eb, acc_b);
+                    acc_w += w;
+                    ++n_acc;
+                }
+            } else {
+                if (DEBUG && rec)
+                    for (int wd = 3; wd < rec_words; ++wd) rec[wd] = 0;
+                for (int dy = 0; dy < k; ++dy) {
+                    const float Ay = __fmaf_rn((float)dy, ify, Ay0), By = __fmaf_rn((float)dy, ziy, By0);
+                    const float *drow = dwin + (long long)dy * P.pitch;
+                    unsigned int mask = 0u;
+                    for (int dx = 0; dx < k; ++dx) {
+                        const float dz = (__ldg(drow + dx) - zh) - zl;
+                        const float X = fmaf(dz, __fmaf_rn((float)dx, ifx, Ax0), __fmaf_rn((float)dx, zix, Bx0));
+                        const float Y = fmaf(dz, Ay, By);
+                        const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
+                        if (d2 < r2) mask |= 1u << dx;
+                    }
+                    if (DEBUG && rec) {
+                        for (int dx = 0; dx < k; ++dx)
+                            if (mask >> dx & 1u) {
+                                const int bit = dy * k + dx;
+                                rec[3 + (bit >> 5)] |= (int32_t)(1u << (bit & 31));
+                            }
+                    }
+                    while (mask) {
+                        const int dx = __ffs((int)mask) - 1;
+                        mask &= mask - 1u;
+                        const long long off = (long long)dy * P.pitch + dx;
+                        const float dz = (__ldg(dwin + off) - zh) - zl;
+                        const float X = fmaf(dz, __fmaf_rn((float)dx, ifx, Ax0), __fmaf_rn((float)dx, zix, Bx0));
+                        const float Y = fmaf(dz, Ay, By);
+                        const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
+                        const float3 c = load_colour<CFMT>(P.colour, wbase + off);
+                        const float er = c.x - cref.x, eg = c.y - cref.y, eb = c.z - cref.z;
+                        float w = 1.0f;
+                        if (weighted) w = ex2(-fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta)));
+                        acc_r = fmaf(w, er, acc_r);
+                        acc_g = fmaf(w, eg, acc_g);
+                        acc_b = fmaf(w, eb, acc_b);
+                        acc_w += w;
+                        ++n_acc;
+                    }
+                }
+            }
+        }
+    }
+
+    if (active) {
+        // Eq. 3 written around the reference colour: c_ref + sum w (c - c_ref) / sum w
+        float o_r = cref.x, o_g = cref.y, o_b = cref.z;
+        if (acc_w > 0.0f) {
+            const float inv = 1.0f / acc_w;
+            o_r = fmaf(acc_r, inv, o_r);
+            o_g = fmaf(acc_g, inv, o_g);
+            o_b = fmaf(acc_b, inv, o_b);
+        }
+        float *o = P.out + (((long long)O * P.H + v) * P.W + u) * 3;
+        o[0] = o_r;
+        o[1] = o_g;
+        o[2] = o_b;
+        if (DEBUG && a.pixel_stats) {
+            int32_t *ps = a.pixel_stats + crop_idx * 3;
+            ps[0] = n_acc;
+            ps[1] = n_exam;
+            ps[2] = __float_as_int(acc_w);
+        }
+    }
+
+    // launch statistics: warp, then block, then one atomic per CTA
+    unsigned long long ce = (unsigned long long)n_exam, ca = (unsigned long long)n_acc;
+    float sw = acc_w;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ce += __shfl_xor_sync(0xffffffffu, ce, o);
+        ca += __shfl_xor_sync(0xffffffffu, ca, o);
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_cnt[0][warp] = ce; s_cnt[1][warp] = ca; s_w[warp] = sw; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long te = 0, ta = 0;
+        double tw = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) { te += s_cnt[0][i]; ta += s_cnt[1][i]; tw += s_w[i]; }
+        atomicAdd(a.stat_counts, te);
+        atomicAdd(a.stat_counts + 1, ta);
+        atomicAdd(a.stat_sumw, tw);
+    }
+}
+
+template <int K, int CFMT>
+cudaError_t launch_k(const GatherArgs &a, cudaStream_t s) {
+    dim3 grid((a.cw + kTileX - 1) / kTileX, (a.ch + kTileY - 1) / kTileY, a.n_out);
+    size_t smem = sizeof(float4) * kSlotVec * (size_t)a.n_slots;
+    const bool dbg = a.membership || a.pixel_stats;
+    if (dbg) gather_kernel<K, CFMT, true><<<grid, kThreads, smem, s>>>(a);
+    else gather_kernel<K, CFMT, false><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int CFMT>
+cudaError_t launch_c(const GatherArgs &a, cudaStream_t s) {
+    switch (a.k) {
+        case 1: return launch_k<1, CFMT>(a, s);
+        case 3: return launch_k<3, CFMT>(a, s);
+        case 5: return launch_k<5, CFMT>(a, s);
+        case 7: return launch_k<7, CFMT>(a, s);
+        default: return launch_k<0, CFMT>(a, s);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gather(const GatherArgs &a, cudaStream_t s) {
+    if (a.n_out <= 0 || a.cw <= 0 || a.ch <= 0) return cudaSuccess;
+    return a.clip.colour_fmt == 0 ? launch_c<0>(a, s) : launch_c<1>(a, s);
+}
+
+}  // namespace ssvp

@@ -1,0 +1,65 @@
+// ssvp_internal.h - device data layout shared by the host runtime (ssvp_api.cpp) and the CUDA
+// kernels (ssvp_gather.cu, ssvp_pack.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ssvp {
+
+// Every packed plane has kPad pixels of padding on each side.  A k x k window whose centre is
+// within h pixels of the image reaches at most 2h <= 30 pixels beyond it, so window loads never
+// leave the allocation and need no bounds test: padding depth is NaN, which fails the radius test.
+constexpr int kPad = 32;
+constexpr int kMaxSlots = 2 * 127 + 1;
+
+// One loaded clip on the device.
+struct Planes {
+    int W, H, F;
+    int pitch;             // elements per padded row, multiple of 32 (128-byte rows for depth)
+    int rows;              // H + 2 * kPad
+    long long fstride;     // pitch * rows: elements per frame
+    float *depth;          // F * fstride floats; pixel (x, y) at (y + kPad) * pitch + x + kPad
+    void *colour;          // F * fstride texels: float4 (r, g, b, 0) or 4 x half (r, g, b, 0)
+    int colour_fmt;        // 0 FP32, 1 FP16
+    float *median;         // device scalar: lower-median valid depth
+    float *out;            // F * H * W * 3 output floats (row-major, interleaved)
+};
+
+// Host-composed geometry of one (output frame O, window slot j) pair, J = O - T + j.
+// M = K_J R_JO K_O^-1 and e = K_J t_JO map (u d, v d, d) of O to homogeneous pixel coordinates
+// of J; they are stored as unevaluated FP32 pairs (hi + lo) of their FP64 values.
+struct __align__(16) PairGeom {
+    float M_hi[9], M_lo[9];
+    float e_hi[3], e_lo[3];
+    float ifx, ify, cx, cy;   // intrinsics of J (zero skew): 1/fx, 1/fy, cx, cy
+    float beta;               // (J - O)^2 / (2 sigma_f^2)
+    int32_t J;                // input frame, or -1 when outside the clip
+    int32_t same;             // J == O
+    int32_t pad_;
+};
+static_assert(sizeof(PairGeom) == 128, "PairGeom layout");
+
+// Arguments of one gather launch (one clip, a range of output frames).
+struct GatherArgs {
+    Planes clip;
+    const PairGeom *geom;     // n_out * n_slots entries
+    int frame_begin, n_out, n_slots, T;
+    int x0, y0, cw, ch;       // output crop
+    int k, mode;
+    float radius;             // > 0 absolute, < 0 relative to *clip.median
+    float sigma_rgb, sigma_xyz, sigma_f;  // sigma_xyz <= 0: equal to the radius
+    int32_t *membership;      // debug record per (crop pixel, slot) or null
+    int32_t *pixel_stats;     // debug record per crop pixel or null
+    unsigned long long *stat_counts;  // [0] examined, [1] accepted
+    double *stat_sumw;
+};
+
+cudaError_t launch_pack(const float *rgb, const float *depth, int W, int H, int nF, const Planes &dst, int frame0,
+                        cudaStream_t s);
+cudaError_t launch_fill_padding(const Planes &dst, cudaStream_t s);
+cudaError_t launch_median(const Planes &p, unsigned int *scratch, cudaStream_t s);
+size_t median_scratch_words();
+cudaError_t launch_gather(const GatherArgs &a, cudaStream_t s);
+
+}  // namespace ssvp

@@ -1,0 +1,143 @@
+// ssvp_pack.cu - load-time kernels: packing input frames into padded vector planes (A2) and the
+// lower-median valid depth by a three-pass radix select (used for relative radii).
+#include <cuda_fp16.h>
+
+#include "ssvp_internal.h"
+
+namespace ssvp {
+namespace {
+
+__device__ __forceinline__ bool valid_depth(float d) { return isfinite(d) && d > 0.0f; }
+
+// One thread per input pixel of frames [0, nF): interleaved rgb (12 B) + depth -> padded planes.
+// Invalid depths become NaN so that a single comparison rejects them in the gather.
+template <int CFMT>
+__global__ void pack_kernel(const float *__restrict__ rgb, const float *__restrict__ depth, int W, int H,
+                            long long npix, Planes P, int frame0) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long f = i / ((long long)W * H);
+        int rem = (int)(i - f * (long long)W * H);
+        int y = rem / W, x = rem - y * W;
+        float d = depth[i];
+        float r = rgb[3 * i], g = rgb[3 * i + 1], b = rgb[3 * i + 2];
+        long long o = (f + frame0) * P.fstride + (long long)(y + kPad) * P.pitch + (x + kPad);
+        P.depth[o] = valid_depth(d) ? d : __int_as_float(0x7fffffff);
+        if (CFMT == 0) {
+            reinterpret_cast<float4 *>(P.colour)[o] = make_float4(r, g, b, 0.0f);
+        } else {
+            __half2 rg = __floats2half2_rn(r, g);
+            __half2 b0 = __floats2half2_rn(b, 0.0f);
+            uint2 raw;
+            raw.x = *reinterpret_cast<unsigned int *>(&rg);
+            raw.y = *reinterpret_cast<unsigned int *>(&b0);
+            reinterpret_cast<uint2 *>(P.colour)[o] = raw;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- radix select
+// Positive finite floats order like their bit patterns.  Three passes over 11, 11 and 10 bits
+// narrow the bit pattern of the element of rank floor((n - 1) / 2).
+// scratch layout (32-bit words): [0, 2048) histogram, 2048 prefix, 2049 rank, 2050 n_valid.
+constexpr int kHistWords = 2048;
+__host__ __device__ constexpr int shift_of(int pass) { return pass == 0 ? 21 : (pass == 1 ? 10 : 0); }
+__host__ __device__ constexpr int bins_of(int pass) { return pass == 2 ? 1024 : 2048; }
+
+template <int PASS>
+__global__ void hist_kernel(const float *__restrict__ depth, long long n, unsigned int *scratch) {
+    __shared__ unsigned int h[kHistWords];
+    for (int i = threadIdx.x; i < bins_of(PASS); i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const unsigned int prefix = PASS == 0 ? 0u : scratch[2048];
+    const unsigned int *bits = reinterpret_cast<const unsigned int *>(depth);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned int b = __ldg(bits + i);
+        bool ok = b > 0u && b < 0x7f800000u;
+        if (PASS == 1) ok = ok && (b >> 21) == prefix;
+        if (PASS == 2) ok = ok && (b >> 10) == prefix;
+        if (ok) atomicAdd(&h[(b >> shift_of(PASS)) & (bins_of(PASS) - 1)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < bins_of(PASS); i += blockDim.x)
+        if (h[i]) atomicAdd(&scratch[i], h[i]);
+}
+
+// One block of 1024 threads: find the bin holding the wanted rank, fold it into the prefix,
+// clear the histogram for the next pass; the last pass writes the median.
+template <int PASS>
+__global__ void select_kernel(unsigned int *scratch, float *median) {
+    __shared__ unsigned int part[1024];
+    const int t = threadIdx.x;
+    const int per = bins_of(PASS) / 1024;  // 2 or 1 bins per thread
+    unsigned int local = 0;
+    for (int i = 0; i < per; ++i) local += scratch[t * per + i];
+    part[t] = local;
+    __syncthreads();
+    // inclusive scan (Hillis-Steele)
+    for (int off = 1; off < 1024; off <<= 1) {
+        unsigned int v = t >= off ? part[t - off] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    const unsigned int total = part[1023];
+    unsigned int rank;
+    if (PASS == 0) {
+        rank = total ? (total - 1) / 2 : 0u;
+    } else {
+        rank = scratch[2049];
+    }
+    __syncthreads();
+    unsigned int before = t ? part[t - 1] : 0u;
+    if (total > 0 && rank >= before && rank < part[t]) {
+        unsigned int r = rank - before;
+        int bin = t * per;
+        for (int i = 0; i < per; ++i) {
+            unsigned int c = scratch[t * per + i];
+            if (r < c) { bin = t * per + i; break; }
+            r -= c;
+        }
+        unsigned int prefix = PASS == 0 ? (unsigned int)bin : ((scratch[2048] << (PASS == 1 ? 11 : 10)) | (unsigned int)bin);
+        scratch[2048] = prefix;
+        scratch[2049] = r;
+        if (PASS == 2) *median = __uint_as_float(prefix);
+    }
+    if (PASS == 0) {
+        if (t == 0) scratch[2050] = total;
+        if (total == 0 && t == 0) *median = __int_as_float(0x7fffffff);
+    }
+    __syncthreads();
+    for (int i = t; i < kHistWords; i += 1024) scratch[i] = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const float *rgb, const float *depth, int W, int H, int nF, const Planes &dst, int frame0,
+                        cudaStream_t s) {
+    long long n = (long long)W * H * nF;
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (dst.colour_fmt == 0) pack_kernel<0><<<blocks, 256, 0, s>>>(rgb, depth, W, H, n, dst, frame0);
+    else pack_kernel<1><<<blocks, 256, 0, s>>>(rgb, depth, W, H, n, dst, frame0);
+    return cudaGetLastError();
+}
+
+size_t median_scratch_words() { return kHistWords + 4; }
+
+cudaError_t launch_median(const Planes &p, unsigned int *scratch, cudaStream_t s) {
+    long long n = (long long)p.F * p.fstride;
+    int blocks = 152 * 4;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, median_scratch_words() * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    hist_kernel<0><<<blocks, 512, 0, s>>>(p.depth, n, scratch);
+    select_kernel<0><<<1, 1024, 0, s>>>(scratch, p.median);
+    hist_kernel<1><<<blocks, 512, 0, s>>>(p.depth, n, scratch);
+    select_kernel<1><<<1, 1024, 0, s>>>(scratch, p.median);
+    hist_kernel<2><<<blocks, 512, 0, s>>>(p.depth, n, scratch);
+    select_kernel<2><<<1, 1024, 0, s>>>(scratch, p.median);
+    return cudaGetLastError();
+}
+
+}  // namespace ssvp

@@ -1,0 +1,217 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded inputs.
+
+Membership must match exactly except candidates within 1e-5 relative of the radius and window
+centres within 1e-3 px of a rounding tie; colour within 1e-3 max abs at every other pixel.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import COLOUR_TOL, Session, compare, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sess():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    s = Session()
+    yield s
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    # the tiny workload: 160x90, 16 frames, 3 textured planes
+    return synth.make_clip("planes3", 160, 90, 16, seed=0)
+
+
+@pytest.fixture(scope="module")
+def hd():
+    # the HD workload: 1280x720, 60 frames, 6 planes + 4 boxes, hand-held camera
+    return synth.make_clip("room", 1280, 720, 60, seed=0)
+
+
+def _both(sess, clip, cid, O, k, T, crop=None, colour_fmt=0, mode=0, **kw):
+    med = oracle.median_depth(clip.depth)
+    g = sess.run(cid, O, crop=crop, membership=True, k=k, half_window=T, mode=mode, **kw)
+    o = oracle.gather_filter(oracle.ClipView.of(clip), oracle_params(med, k, T, mode=mode), O, crop=crop,
+                             membership=True)
+    return g, o
+
+
+@pytest.mark.parametrize("O", [0, 7, 15])
+def test_tiny_full_frame(sess, tiny, O):
+    sess.load(0, tiny)
+    g, o = _both(sess, tiny, 0, O, k=5, T=15)
+    s = compare(g, o, 5)
+    assert s["members"] > 5 * s["pixels"]
+    assert s["excluded"] <= 0.001 * s["pixels"] + 2
+
+
+def test_hd_crop(sess, hd):
+    sess.load(1, hd)
+    g, o = _both(sess, hd, 1, 30, k=7, T=15, crop=(608, 328, 64, 64))
+    s = compare(g, o, 7)
+    assert s["excluded"] <= 0.001 * s["pixels"] + 2
+
+
+@pytest.mark.parametrize("k,T", [(1, 0), (3, 2), (9, 1), (31, 1), (5, 10)])
+def test_ragged_sizes_and_windows(sess, k, T):
+    clip = synth.make_clip("planes3", 77, 45, 6, seed=5)
+    sess.load(2, clip)
+    for O in (0, 3, 5):
+        g, o = _both(sess, clip, 2, O, k=k, T=T, crop=(3, 5, 41, 29))
+        compare(g, o, k)
+
+
+def test_self_reprojection_is_bit_exact(sess, tiny):
+    sess.load(0, tiny)
+    g = sess.run(0, 4, membership=True, k=1, half_window=0)
+    np.testing.assert_array_equal(g.rgb, tiny.rgb[4])
+    assert (g.nacc == 1).all()
+
+
+def test_invalid_depths(sess):
+    clip = synth.make_clip("planes3", 64, 40, 5, seed=2)
+    depth = clip.depth.copy()
+    rng = np.random.default_rng(1)
+    bad = rng.random(depth.shape) < 0.15
+    depth[bad] = np.array([np.nan, 0.0, -2.0, np.inf], np.float32)[rng.integers(0, 4, bad.sum())]
+    bad_clip = synth.Clip(clip.W, clip.H, clip.F, clip.K, clip.w2c, clip.w2c_true, clip.rgb, depth, clip.clean,
+                          clip.depth_true)
+    sess.load(3, bad_clip)
+    g, o = _both(sess, bad_clip, 3, 2, k=5, T=2)
+    compare(g, o, 5)
+    np.testing.assert_array_equal(g.rgb[bad[2]], clip.rgb[2][bad[2]])
+
+
+def test_mean_mode(sess, tiny):
+    sess.load(0, tiny)
+    g, o = _both(sess, tiny, 0, 8, k=5, T=4, mode=3)
+    compare(g, o, 5)
+
+
+def test_fp16_colour(sess, tiny):
+    """FP16 colour storage: arithmetic parity against the oracle on the FP16-rounded colours, and
+    the total error against the FP32-colour oracle reported (bounded by the FP16 rounding)."""
+    sess.load(4, tiny, colour_fmt=1)
+    rgb16 = tiny.rgb.astype(np.float16).astype(np.float32)
+    c16 = synth.Clip(tiny.W, tiny.H, tiny.F, tiny.K, tiny.w2c, tiny.w2c_true, rgb16, tiny.depth, tiny.clean,
+                     tiny.depth_true)
+    g, o16 = _both(sess, c16, 4, 8, k=5, T=15)
+    compare(g, o16, 5)
+    med = oracle.median_depth(tiny.depth)
+    o32 = oracle.gather_filter(oracle.ClipView.of(tiny), oracle_params(med, 5, 15), 8)
+    # total error of FP16 storage: colour rounding (2^-11 relative) plus its effect on the Eq. 4
+    # colour weights of outlying samples; stated, and bounded loosely
+    total = float(np.abs(g.rgb - o32.rgb).max())
+    print(f"FP16 colour: max |GPU - FP32-colour oracle| = {total:.3e}")
+    assert total < 1e-2
+
+
+def test_exact_geometry_reproduces_clean(sess):
+    """Exact depth and poses, constant-albedo planes: the output is the clean render to 1e-6."""
+    c = synth.make_clip("exact_const", 96, 54, 9, seed=0)
+    sess.load(5, c)
+    g = sess.run(5, 4, membership=True, k=5, half_window=4)
+    assert np.abs(g.rgb - c.clean[4]).max() <= 1e-6
+    assert g.nacc.mean() > 0.5 * c.F
+
+
+def test_exact_shift_membership_closed_form(sess):
+    c = synth.make_clip("exact_shift", 64, 36, 7, seed=1)
+    sess.load(6, c)
+    O, T, h = 3, 3, 2
+    g = sess.run(6, O, membership=True, k=5, half_window=T)
+    uu = np.arange(c.W)[None, :].repeat(c.H, 0)
+    for j in range(2 * T + 1):
+        J = O - T + j
+        inside = (uu - (J - O) >= 0) & (uu - (J - O) < c.W)
+        assert (g.bits[:, :, j, h, h] == inside).all()
+        b = g.bits[:, :, j].copy()
+        b[:, :, h, h] = False
+        assert not b.any()
+    assert np.abs(g.rgb - c.clean[O]).max() <= 1e-6
+
+
+def test_median_depth_is_exact(sess, tiny):
+    sess.load(0, tiny)
+    assert sess.ss.ssvp_clip_median_depth(sess.ctx, 0) == oracle.median_depth(tiny.depth)
+    d = tiny.depth[:3].copy()
+    d[0, :10] = np.nan
+    d[1, 5:20] = -1.0
+    d[2, :, :7] = 0.0
+    c = synth.Clip(tiny.W, tiny.H, 3, tiny.K[:3], tiny.w2c[:3], tiny.w2c_true[:3], tiny.rgb[:3], d, tiny.clean[:3],
+                   tiny.depth_true[:3])
+    sess.load(7, c)
+    assert sess.ss.ssvp_clip_median_depth(sess.ctx, 7) == oracle.median_depth(d)
+
+
+def test_host_upload_matches_device_upload(sess, tiny):
+    sess.load(0, tiny)
+    a = sess.run(0, 8, k=5, half_window=15).rgb
+    sess.load(8, tiny, host=True)
+    b = sess.run(8, 8, k=5, half_window=15).rgb
+    np.testing.assert_array_equal(a, b)
+
+
+def test_launch_stats_match_oracle(sess, tiny):
+    sess.load(0, tiny)
+    g, o = _both(sess, tiny, 0, 8, k=5, T=15)
+    e, a, w = sess.ss.ssvp_read_stats(sess.ctx)
+    assert e == int(g.nexam.sum()) and a == int(g.nacc.sum())
+    assert e == int(o.nexam.sum())
+    assert abs(a - int(o.nacc.sum())) <= int(((o.codes & oracle.CODE_BAND) != 0).sum())
+    assert w == pytest.approx(float(o.sumw.sum()), rel=1e-3)
+
+
+def test_argument_errors(sess, tiny):
+    ss = sess.ss
+    sess.load(0, tiny)
+    with pytest.raises(ss.SsvpError) as e:
+        sess.run(0, 4, k=4)
+    assert e.value.code == ss.SSVP_EINVAL
+    with pytest.raises(ss.SsvpError) as e:
+        sess.run(0, 4, crop=(150, 0, 20, 10))
+    assert e.value.code == ss.SSVP_EINVAL
+    with pytest.raises(ss.SsvpError) as e:
+        ss.ssvp_gather_filter(sess.ctx, sess.params(), [40])
+    assert e.value.code == ss.SSVP_ENOCLIP
+    import torch
+    z = torch.zeros((2, 4, 4, 3), device="cuda")
+    ss.ssvp_load_clip(sess.ctx, 9, 4, 4, 2, z, z[..., 0].contiguous())
+    with pytest.raises(ss.SsvpError) as e:
+        ss.ssvp_gather_filter(sess.ctx, sess.params(), [9])
+    assert e.value.code == ss.SSVP_ENOCAM
+    K = np.array([[1.0, 0.1, 2], [0, 1, 2], [0, 0, 1]])
+    with pytest.raises(ss.SsvpError) as e:
+        ss.ssvp_set_cameras(sess.ctx, 9, K, 0, np.tile(np.eye(3, 4), (2, 1, 1)))
+    assert e.value.code == ss.SSVP_EINVAL
+
+
+def test_full_size_sampled_against_oracle(sess):
+    """1920x1080, +-30 frames, k = 7 in the benchmark's launch (all pixels of the output frame,
+    no debug outputs); sampled crops compared with the oracle."""
+    clip = synth.make_clip("room", 1920, 1080, 61, seed=0)
+    sess.load(10, clip, colour_fmt=0)
+    O = 30
+    g = sess.run(10, O, k=7, half_window=30)
+    med = oracle.median_depth(clip.depth)
+    prm = oracle_params(med, 7, 30)
+    v = oracle.ClipView.of(clip)
+    worst = []
+    for crop in [(0, 0, 24, 24), (960, 540, 24, 24), (1896, 1056, 24, 24), (400, 900, 24, 24)]:
+        x0, y0, cw, ch = crop
+        o = oracle.gather_filter(v, prm, O, crop=crop, membership=True)
+        band = ((o.codes & oracle.CODE_BAND) != 0).any(axis=(-1, -2, -3)) | ((o.amb == 1) & (o.status == 1)).any(-1)
+        err = np.abs(g.rgb[y0:y0 + ch, x0:x0 + cw] - o.rgb).max(-1)
+        assert err[~band].max() <= COLOUR_TOL
+        worst.append(err[~band].max())
+    e, a, w = sess.ss.ssvp_read_stats(sess.ctx)
+    assert a >= clip.W * clip.H  # every valid pixel accepts at least its own sample
