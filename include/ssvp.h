@@ -175,6 +175,32 @@ int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median);
 /* Wait for all work queued on the context's stream; returns the first pending error. */
 int ssvp_sync(ssvp_ctx *ctx);
 
+/*
+ * Lower-median valid depth of a caller-owned device array, without allocating any memory.
+ *
+ * The paper has no counterpart: this is a service for callers that may not allocate device
+ * memory themselves or through this library -- for example a plug-in inside a video host that
+ * owns every GPU buffer through its own pool, or a per-frame real-time callback, where a
+ * cudaMalloc/cudaFree would synchronise the device and stall the host's pipeline.  It computes
+ * the same value as ssvp_clip_median_depth (the element of rank floor((m-1)/2) among the m
+ * finite, positive values) with the same radix-select kernels, but keeps their scratch (8,208
+ * bytes of histogram and bookkeeping) in a fixed array in the library's device memory, which
+ * every GPU that loads the library holds until the process exits.  No context is needed.
+ *
+ *   depth_dev   n floats in device memory of the current CUDA device (any layout; invalid
+ *               values are ignored)
+ *   n           1 <= n <= 4294967295 (the scratch counts in 32-bit words); other sizes return
+ *               SSVP_EINVAL with a message in ssvp_last_error(NULL)
+ *   median_dev  one float in device memory: the median, or NaN when no value is valid
+ *   cuda_stream stream to queue the work on (NULL: legacy default stream); asynchronous
+ *
+ * The first call on a device looks up the scratch array's device address for that device (the
+ * device must be current); make that first call before any stream capture.  All calls share
+ * the one array: each call clears it before use, and calls whose work overlaps on the GPU (for
+ * example on two streams at once) race on it and give wrong results.
+ */
+int ssvp_median_depth_noalloc(const float *depth_dev, unsigned long long n, float *median_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

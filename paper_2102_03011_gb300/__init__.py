@@ -61,6 +61,7 @@ def _load():
                                 ctypes.POINTER(ctypes.c_double)]),
         "ssvp_clip_median_depth": (i, [vp, i, ctypes.POINTER(f)]),
         "ssvp_sync": (i, [vp]),
+        "ssvp_median_depth_noalloc": (i, [vp, ctypes.c_ulonglong, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -177,3 +178,11 @@ def ssvp_clip_median_depth(ctx, clip_id: int) -> float:
 
 def ssvp_sync(ctx) -> None:
     _check(ctx, lib.ssvp_sync(ctx))
+
+
+def ssvp_median_depth_noalloc(depth_dev, n: int, median_dev, cuda_stream=None) -> None:
+    """Median of a device array with the library's fixed scratch (no allocation); see ssvp.h."""
+    pd, _ = _ptr(depth_dev)
+    pm, _ = _ptr(median_dev)
+    s = cuda_stream.cuda_stream if hasattr(cuda_stream, "cuda_stream") else cuda_stream
+    _check(None, lib.ssvp_median_depth_noalloc(pd, int(n), pm, s))

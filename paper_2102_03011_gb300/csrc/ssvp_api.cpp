@@ -152,6 +152,15 @@ int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
 
 }  // namespace
 
+namespace ssvp {
+void set_global_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_create_error, sizeof(g_create_error), fmt, ap);
+    va_end(ap);
+}
+}  // namespace ssvp
+
 extern "C" {
 
 void ssvp_params_default(ssvp_params *p) {

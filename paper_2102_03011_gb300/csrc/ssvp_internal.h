@@ -57,9 +57,13 @@ struct GatherArgs {
 
 cudaError_t launch_pack(const float *rgb, const float *depth, int W, int H, int nF, const Planes &dst, int frame0,
                         cudaStream_t s);
-cudaError_t launch_fill_padding(const Planes &dst, cudaStream_t s);
 cudaError_t launch_median(const Planes &p, unsigned int *scratch, cudaStream_t s);
 size_t median_scratch_words();
 cudaError_t launch_gather(const GatherArgs &a, cudaStream_t s);
+
+// largest input of ssvp_median_depth_noalloc: its fixed scratch counts values in 32-bit words
+constexpr unsigned long long kMedianNoallocMax = 0xffffffffull;
+// error text for entry points that have no context (read with ssvp_last_error(NULL))
+void set_global_error(const char *fmt, ...);
 
 }  // namespace ssvp

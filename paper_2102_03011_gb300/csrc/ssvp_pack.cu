@@ -2,6 +2,9 @@
 // lower-median valid depth by a three-pass radix select (used for relative radii).
 #include <cuda_fp16.h>
 
+#include <mutex>
+
+#include "../../include/ssvp.h"
 #include "ssvp_internal.h"
 
 namespace ssvp {
@@ -140,4 +143,75 @@ cudaError_t launch_median(const Planes &p, unsigned int *scratch, cudaStream_t s
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- median without allocation
+// Scratch of ssvp_median_depth_noalloc: the radix-select histogram and its prefix/rank/count
+// words live in this fixed device array instead of memory from cudaMalloc.  Every GPU that
+// loads the library holds these 8,208 bytes until the process exits.
+static __device__ __align__(256) unsigned int g_median_scratch[kHistWords + 4];
+
+namespace {
+
+// Device address of g_median_scratch, looked up once per device.  In host code the symbol's
+// name is only a host-side stand-in; a kernel must be given this address instead.
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+unsigned int *g_scratch_ptr[kMaxDevices] = {};
+
+cudaError_t median_scratch_for_current_device(unsigned int **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_median_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<unsigned int *>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
 }  // namespace ssvp
+
+extern "C" int ssvp_median_depth_noalloc(const float *depth_dev, unsigned long long n, float *median_dev,
+                                         void *cuda_stream) {
+    if (!depth_dev || !median_dev) {
+        ssvp::set_global_error("ssvp_median_depth_noalloc: depth_dev and median_dev must not be NULL");
+        return SSVP_EINVAL;
+    }
+    if (n == 0 || n > ssvp::kMedianNoallocMax) {
+        ssvp::set_global_error("ssvp_median_depth_noalloc: n=%llu outside [1, %llu]: the fixed scratch counts "
+                               "values in 32-bit words", n, (unsigned long long)ssvp::kMedianNoallocMax);
+        return SSVP_EINVAL;
+    }
+    unsigned int *scratch = nullptr;
+    cudaError_t e = ssvp::median_scratch_for_current_device(&scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ssvp::set_global_error("ssvp_median_depth_noalloc: scratch address: %s", cudaGetErrorString(e));
+        return SSVP_ECUDA;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const long long nn = (long long)n;
+    const int blocks = 152 * 4;
+    // the previous call's histogram stays in the array: clear it first
+    e = cudaMemsetAsync(scratch, 0, ssvp::median_scratch_words() * sizeof(unsigned int), s);
+    if (e == cudaSuccess) {
+        ssvp::hist_kernel<0><<<blocks, 512, 0, s>>>(depth_dev, nn, scratch);
+        ssvp::select_kernel<0><<<1, 1024, 0, s>>>(scratch, median_dev);
+        ssvp::hist_kernel<1><<<blocks, 512, 0, s>>>(depth_dev, nn, scratch);
+        ssvp::select_kernel<1><<<1, 1024, 0, s>>>(scratch, median_dev);
+        ssvp::hist_kernel<2><<<blocks, 512, 0, s>>>(depth_dev, nn, scratch);
+        ssvp::select_kernel<2><<<1, 1024, 0, s>>>(scratch, median_dev);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        ssvp::set_global_error("ssvp_median_depth_noalloc: %s", cudaGetErrorString(e));
+        return SSVP_ECUDA;
+    }
+    return SSVP_OK;
+}
