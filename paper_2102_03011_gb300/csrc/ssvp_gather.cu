@@ -62,7 +62,8 @@ __device__ __forceinline__ df df_mul_f(df a, float b) {
     return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
 }
 
-// a / b given r = 1 / b.hi (correctly rounded): one correction step.
+// a / b given r ~ 1 / b.hi (relative error ~1e-7): the correction step makes the quotient
+// accurate to ~1e-14 relative.
 __device__ __forceinline__ df df_div(df a, df b, float r) {
     float q1 = __fmul_rn(a.hi, r);
     df p = two_prod(q1, b.hi);
@@ -76,8 +77,8 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
-template <int CFMT>
-__device__ __forceinline__ float3 load_colour(const void *base, long long idx) {
+template <int CFMT, typename I>
+__device__ __forceinline__ float3 load_colour(const void *base, I idx) {
     if (CFMT == 0) {
         float4 c = __ldg(reinterpret_cast<const float4 *>(base) + idx);
         return make_float3(c.x, c.y, c.z);
@@ -90,8 +91,29 @@ __device__ __forceinline__ float3 load_colour(const void *base, long long idx) {
     }
 }
 
+#ifndef SSVP_MIN_CTAS
+#define SSVP_MIN_CTAS 4  // resident CTAs per SM the register allocation must allow
+#endif
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+#ifndef SSVP_ACC_BATCH
+#define SSVP_ACC_BATCH 1  // accepted samples processed per iteration of the filter loop
+#endif
+constexpr int kAccBatch = SSVP_ACC_BATCH;
+
+// exact float of a small non-negative integer (< 2^23) without a conversion instruction
+__device__ __forceinline__ float small_float(int v) { return __int_as_float(0x4b000000 | v) - 8388608.0f; }
+
 constexpr float kLog2e = 1.4426950408889634f;
-constexpr int kTileX = 32, kTileY = 8, kThreads = kTileX * kTileY;
+#ifndef SSVP_TILE_Y
+#define SSVP_TILE_Y 8  // output rows per CTA (a warp covers 32 pixels of one row)
+#endif
+constexpr int kTileX = 32, kTileY = SSVP_TILE_Y, kThreads = kTileX * kTileY;
 constexpr int kSlotVec = 6;  // float4 words of per-slot geometry in shared memory
 
 // Shared per-slot geometry (6 x float4):
@@ -120,7 +142,7 @@ __device__ void build_slot(const PairGeom &g, float u0, float v0, float4 *dst) {
 // K > 0: compile-time window width (k*k <= 64, one 64-bit accept mask per frame).
 // K == 0: runtime k up to 31, one 32-bit accept mask per window row.
 template <int K, int CFMT, bool DEBUG>
-__global__ void __launch_bounds__(kThreads) gather_kernel(const GatherArgs a) {
+__global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const GatherArgs a) {
     extern __shared__ float4 sgeom[];
     __shared__ float s_const[4];
     __shared__ unsigned long long s_cnt[2][kThreads / 32];
@@ -191,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(const GatherArgs a) {
                 if (DEBUG && rec) rec[0] = 0;
                 continue;
             }
-            const float rz = __frcp_rn(w2.hi);
+            const float rz = rcp_approx(w2.hi);
             const df U = df_div(w0, w2, rz), V = df_div(w1, w2, rz);
             // window centre floor(u' + 0.5) and the exact offset u' - centre in [-0.5, 0.5)
             float cxf = floorf(U.hi + 0.5f), cyf = floorf(V.hi + 0.5f);
@@ -215,6 +237,8 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(const GatherArgs a) {
             const float Ay0 = (cyf - (float)h - q5.y) * ify, ziy = zh * ify, By0 = (-(float)h - ov) * ziy;
             const long long wbase = (long long)J * P.fstride + (long long)(cy - h + kPad) * P.pitch + (cx - h + kPad);
             const float *dwin = P.depth + wbase;
+            const void *cwin = CFMT == 0 ? (const void *)(reinterpret_cast<const float4 *>(P.colour) + wbase)
+                                         : (const void *)(reinterpret_cast<const uint2 *>(P.colour) + wbase);
             const float beta = q5.z;
             if (DEBUG && rec) { rec[0] = 1; rec[1] = cx; rec[2] = cy; }
 
@@ -236,32 +260,53 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(const GatherArgs a) {
                         const float X = fmaf(dz, Ax[dx], Bx[dx]);
                         const float Y = fmaf(dz, Ay, By);
                         const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
-                        if (d2 < r2) mask |= 1ull << (dy * K + dx);
+                        if (d2 < r2) mask |= 1ull << (dy * 8 + dx);  // stride 8: cheap decode
                     }
                 }
                 if (DEBUG && rec) {
-                    rec[3] = (int32_t)(unsigned int)(mask & 0xffffffffull);
-                    if (K * K > 32) rec[4] = (int32_t)(unsigned int)(mask >> 32);
+                    unsigned long long packed = 0ull;  // record layout: bit dy*k+dx
+                    for (int dy = 0; dy < K; ++dy)
+                        packed |= ((mask >> (8 * dy)) & ((1ull << K) - 1ull)) << (dy * K);
+                    rec[3] = (int32_t)(unsigned int)(packed & 0xffffffffull);
+                    if (K * K > 32) rec[4] = (int32_t)(unsigned int)(packed >> 32);
                 }
+                // accepted samples, kAccBatch per iteration so that their loads overlap
+#pragma unroll 1
                 while (mask) {
-                    const int i = __ffsll((long long)mask) - 1;
-                    mask &= mask - 1ull;
-                    constexpr int KK = K > 0 ? K : 1;
-                    const int dy = i / KK, dx = i - dy * KK;
-                    const long long off = (long long)dy * P.pitch + dx;
-                    const float dz = (__ldg(dwin + off) - zh) - zl;
-                    const float X = fmaf(dz, __fmaf_rn((float)dx, ifx, Ax0), __fmaf_rn((float)dx, zix, Bx0));
-                    const float Y = fmaf(dz, __fmaf_rn((float)dy, ify, Ay0), __fmaf_rn((float)dy, ziy, By0));
-                    const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
-                    const float3 c = load_colour<CFMT>(P.colour, wbase + off);
-                    const float er = c.x - cref.x, eg = c.y - cref.y, eb = c.z - cref.z;
-                    float w = 1.0f;
-                    if (weighted) w = ex2(-fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta)));
-                    acc_r = fmaf(w, er, acc_r);
-                    acc_g = fmaf(w, eg, acc_g);
-                    acc_b = fmaf(w, eb, acc_b);
-                    acc_w += w;
-                    ++n_acc;
+                    int idx[kAccBatch];
+                    bool ok[kAccBatch];
+#pragma unroll
+                    for (int t = 0; t < kAccBatch; ++t) {
+                        ok[t] = mask != 0ull;
+                        idx[t] = ok[t] ? __ffsll((long long)mask) - 1 : 0;  // slot 0 is always in bounds
+                        mask &= mask - 1ull;
+                    }
+                    float dq[kAccBatch];
+                    float3 cq[kAccBatch];
+#pragma unroll
+                    for (int t = 0; t < kAccBatch; ++t) {
+                        const int off = (idx[t] >> 3) * P.pitch + (idx[t] & 7);
+                        dq[t] = __ldg(dwin + off);
+                        cq[t] = load_colour<CFMT>(cwin, off);
+                    }
+#pragma unroll
+                    for (int t = 0; t < kAccBatch; ++t) {
+                        const float dxf = small_float(idx[t] & 7), dyf = small_float(idx[t] >> 3);
+                        const float dz = (dq[t] - zh) - zl;
+                        const float X = fmaf(dz, __fmaf_rn(dxf, ifx, Ax0), __fmaf_rn(dxf, zix, Bx0));
+                        const float Y = fmaf(dz, __fmaf_rn(dyf, ify, Ay0), __fmaf_rn(dyf, ziy, By0));
+                        const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
+                        const float er = cq[t].x - cref.x, eg = cq[t].y - cref.y, eb = cq[t].z - cref.z;
+                        float w = 1.0f;
+                        if (weighted) w = ex2(-fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta)));
+                        if (ok[t]) {
+                            acc_r = fmaf(w, er, acc_r);
+                            acc_g = fmaf(w, eg, acc_g);
+                            acc_b = fmaf(w, eb, acc_b);
+                            acc_w += w;
+                            ++n_acc;
+                        }
+                    }
                 }
             } else {
                 if (DEBUG && rec)
