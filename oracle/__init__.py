@@ -85,7 +85,7 @@ def _p(a, t):
 
 @dataclass
 class Params:
-    """Gather-and-filter parameters as the oracle reads them (absolute radius)."""
+    """Gather-and-filter parameters as the oracle reads them (absolute radius, absolute focal depth)."""
     mode: int = MODE_DENOISE
     k: int = 7
     T: int = 15
@@ -184,14 +184,15 @@ class Result:
     status: np.ndarray | None = None   # (ch, cw, 2T+1) int32
     centre: np.ndarray | None = None   # (ch, cw, 2T+1, 2) int32
     amb: np.ndarray | None = None      # (ch, cw, 2T+1) uint8
-    codes: np.ndarray | None = None    # (ch, cw, 2T+1, k, k) uint8
+    codes: np.ndarray | None = None    # (ch, cw, 2T+1, k, k) uint8 (aperture: cap x cap from the box origin)
     box: np.ndarray | None = None      # (ch, cw, 2T+1, 4) int32 (aperture)
 
 
 def gather_filter(view: ClipView, prm: Params, O: int, crop=None, membership: bool = False) -> Result:
     """Run the oracle on output frame O over crop (x0, y0, w, h) (default: the full frame)."""
     x0, y0, cw, ch = crop if crop is not None else (0, 0, view.W, view.H)
-    n, ns, k = cw * ch, 2 * prm.T + 1, prm.k
+    n, ns = cw * ch, 2 * prm.T + 1
+    k = prm.cap if prm.mode == MODE_APERTURE else prm.k  # side of the per-slot code grid
     out = np.zeros((ch, cw, 3))
     sumw = np.zeros((ch, cw))
     nacc = np.zeros((ch, cw), np.int64)

@@ -22,15 +22,19 @@
  *   A7  Eq. 3: O(p) = sum_s w(s) s_rgb / sum_s w(s).  An invalid reference depth gives c_ref.
  *
  * Virtual aperture (Sec. "Virtual aperture", Eq. 13-14) with the thin-lens footprint reading:
- *   cone around the central ray of p (from the O camera centre through K_O^-1 [u, v, 1]);
- *   r_al = distance of X_q along the ray, q_perp = distance of X_q to the ray;
- *   a(r_al) = a0 + A |z0 - r_al| / z0 (Eq. 13 with slope A / z0);
- *   per frame J the window is the bounding box of the projections of the n_lens seed points
- *   (lens point L_i on a Vogel disc of radius A, ray L_i -> z0 K_O^-1 [u, v, 1], seed point at
- *   camera z = d_ref), grown by h on each side and capped at `cap` pixels per axis around the
- *   rounded centroid; accepted iff q_perp < a(r_al); weight s_area / (pi a(r_al)^2) with
- *   s_area the squared scene length of one pixel edge of q (Eq. 6), i.e. (d_q / fx_J)^2 for a
- *   camera without skew.  Output sum w c / sum w, or c_ref when nothing is accepted.
+ *   the cone's axis is the viewing ray of p (from the O camera centre along K_O^-1 [u, v, 1]);
+ *   for a sample X_q (O camera coordinates) t = O-camera depth of its foot point on the axis and
+ *   q_perp = its distance to the axis (|X_q x ray| / |ray|);
+ *   a(t) = a0 + A |z0 - t| / z0 (Eq. 13: focal plane at depth z0, slope A / z0 of a thin lens of
+ *   radius A);
+ *   per frame J the scanned box is the bounding box of the projections of the n_lens seed points
+ *   (lens point L_i on a Vogel disc of radius A in the camera's z = 0 plane, ray L_i -> focus
+ *   point z0 K_O^-1 [u, v, 1], seed point where that ray reaches depth d_ref), rounded with
+ *   floor(x + 0.5), grown by h on each side and capped at `cap` pixels per axis around the rounded
+ *   centroid, then clipped to the image; accepted iff q_perp < a(t); weight s_area / (pi a(t)^2)
+ *   with s_area the squared scene length of one pixel edge of q at its depth (Eq. 6), which is
+ *   (d_q / fx_J)^2 for a camera without skew.  Output sum w c / sum w (c_ref if nothing is
+ *   accepted).
  *
  * Built with -ffp-contract=off: every product and sum is rounded on its own.
  */
@@ -213,17 +217,14 @@ static void pixel(const oc_clip *c, const oc_params *p, int O, int u, int v, con
     mat3_vec(KOi, uv1, ray);
     for (int i = 0; i < 3; ++i) xref[i] = dref * ray[i];
 
-    /* aperture: central ray direction (unit) and seed points at depth d_ref */
-    double rhat[3] = {0, 0, 0}, seeds[64][3];
+    /* aperture: seed points where the lens rays through the focus point reach depth d_ref */
+    double rr = ray[0] * ray[0] + ray[1] * ray[1] + ray[2] * ray[2], seeds[64][3];
     int nl = p->lens_samples > 64 ? 64 : p->lens_samples;
     if (p->mode == 1) {
-        double nr = sqrt(ray[0] * ray[0] + ray[1] * ray[1] + ray[2] * ray[2]);
-        for (int i = 0; i < 3; ++i) rhat[i] = ray[i] / nr;
         double Fp[3] = {p->focal_depth * ray[0], p->focal_depth * ray[1], p->focal_depth * ray[2]};
         for (int i = 0; i < nl; ++i) {
             double L[2];
             lens_point(i, nl, p->aperture, L);
-            /* point on the ray L -> Fp at camera z = d_ref */
             double s = dref / p->focal_depth;
             seeds[i][0] = L[0] + s * (Fp[0] - L[0]);
             seeds[i][1] = L[1] + s * (Fp[1] - L[1]);
@@ -267,6 +268,7 @@ static void pixel(const oc_clip *c, const oc_params *p, int O, int u, int v, con
                 apply34(P, seeds[i], xp);
                 if (xp[2] <= 1e-6 * dref) continue;
                 double up = xp[0] / xp[2], vp = xp[1] / xp[2];
+                if (fabs(up - floor(up) - 0.5) < p->tie_band || fabs(vp - floor(vp) - 0.5) < p->tie_band) amb = 1;
                 if (up < mnx) mnx = up;
                 if (up > mxx) mxx = up;
                 if (vp < mny) mny = vp;
@@ -279,6 +281,7 @@ static void pixel(const oc_clip *c, const oc_params *p, int O, int u, int v, con
             }
             double lim = (double)(W + H + 4 * p->cap + 8);
             double mx = sx / nl, my = sy / nl;
+            if (fabs(mx - floor(mx) - 0.5) < p->tie_band || fabs(my - floor(my) - 0.5) < p->tie_band) amb = 1;
             if (mx < -lim) mx = -lim;
             if (mx > lim) mx = lim;
             if (my < -lim) my = -lim;
@@ -297,9 +300,10 @@ static void pixel(const oc_clip *c, const oc_params *p, int O, int u, int v, con
         }
         if (mem) { mem->status[mi * ns + j] = 1; mem->amb[mi * ns + j] = (uint8_t)amb; }
         double fxJ = c->K[9 * J + 0];
+        const int win = p->mode == 1 ? p->cap : k;
         for (int qy = by0; qy <= by1; ++qy) {
             for (int qx = bx0; qx <= bx1; ++qx) {
-                int slot = (qy - by0) * (bx1 - bx0 + 1) + (qx - bx0);
+                int slot = (qy - by0) * win + (qx - bx0);
                 uint8_t code;
                 if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
                     code = OC_OUT;
@@ -330,10 +334,13 @@ static void pixel(const oc_clip *c, const oc_params *p, int O, int u, int v, con
                                 }
                             }
                         } else {
-                            double ral = X[0] * rhat[0] + X[1] * rhat[1] + X[2] * rhat[2];
-                            double px = X[0] - ral * rhat[0], py = X[1] - ral * rhat[1], pz = X[2] - ral * rhat[2];
-                            double qperp = sqrt(px * px + py * py + pz * pz);
-                            double a = p->a0 + p->aperture * fabs(p->focal_depth - ral) / p->focal_depth;
+                            /* foot point depth t and distance to the axis (textbook point-line distance) */
+                            double xr = X[0] * ray[0] + X[1] * ray[1] + X[2] * ray[2];
+                            double t = xr / rr;
+                            double cr0 = X[1] * ray[2] - X[2] * ray[1], cr1 = X[2] * ray[0] - X[0] * ray[2],
+                                   cr2 = X[0] * ray[1] - X[1] * ray[0];
+                            double qperp = sqrt((cr0 * cr0 + cr1 * cr1 + cr2 * cr2) / rr);
+                            double a = p->a0 + p->aperture * fabs(p->focal_depth - t) / p->focal_depth;
                             acc_ok = qperp < a;
                             code = acc_ok ? OC_ACCEPT : OC_REJECT;
                             if (fabs(qperp - a) <= p->band_rel * a) code |= OC_BAND;
@@ -350,7 +357,7 @@ static void pixel(const oc_clip *c, const oc_params *p, int O, int u, int v, con
                         }
                     }
                 }
-                if (mem && p->mode != 1) mem->codes[(mi * ns + j) * (size_t)(k * k) + slot] = code;
+                if (mem) mem->codes[(mi * ns + j) * (size_t)(win * win) + slot] = code;
             }
         }
     }
@@ -394,7 +401,8 @@ int oc_gather_filter(const oc_clip *c, const oc_params *p, int O, int x0, int y0
 
 /*
  * Brute force: test EVERY pixel of frame J against the radius around x_ref of pixel (u, v) of
- * frame O (no window).  accept is H*W bytes (1 accepted, 0 not); returns the count.
+ * frame O, or against its aperture cone in mode 1 (no window, no box).  accept is H*W bytes
+ * (1 accepted, 0 not); returns the count.
  */
 long long oc_bruteforce(const oc_clip *c, const oc_params *p, int O, int u, int v, int J, uint8_t *accept) {
     const int W = c->W, H = c->H;
@@ -407,6 +415,7 @@ long long oc_bruteforce(const oc_clip *c, const oc_params *p, int O, int u, int 
     double uv1[3] = {u, v, 1.0};
     mat3_vec(KOi, uv1, ray);
     for (int i = 0; i < 3; ++i) xref[i] = (double)dref * ray[i];
+    double rr = ray[0] * ray[0] + ray[1] * ray[1] + ray[2] * ray[2];
     long long cnt = 0;
     for (int qy = 0; qy < H; ++qy) {
         for (int qx = 0; qx < W; ++qx) {
@@ -414,9 +423,20 @@ long long oc_bruteforce(const oc_clip *c, const oc_params *p, int O, int u, int 
             if (!valid_depth(dq)) continue;
             double q3[3] = {qx * (double)dq, qy * (double)dq, (double)dq}, X[3];
             apply34(G, q3, X);
-            double d2 = (X[0] - xref[0]) * (X[0] - xref[0]) + (X[1] - xref[1]) * (X[1] - xref[1]) +
-                        (X[2] - xref[2]) * (X[2] - xref[2]);
-            if (d2 < p->radius * p->radius) { accept[(size_t)qy * W + qx] = 1; ++cnt; }
+            int ok;
+            if (p->mode == 1) {
+                double xr = X[0] * ray[0] + X[1] * ray[1] + X[2] * ray[2];
+                double t = xr / rr;
+                double cr0 = X[1] * ray[2] - X[2] * ray[1], cr1 = X[2] * ray[0] - X[0] * ray[2],
+                       cr2 = X[0] * ray[1] - X[1] * ray[0];
+                double qperp = sqrt((cr0 * cr0 + cr1 * cr1 + cr2 * cr2) / rr);
+                ok = qperp < p->a0 + p->aperture * fabs(p->focal_depth - t) / p->focal_depth;
+            } else {
+                double d2 = (X[0] - xref[0]) * (X[0] - xref[0]) + (X[1] - xref[1]) * (X[1] - xref[1]) +
+                            (X[2] - xref[2]) * (X[2] - xref[2]);
+                ok = d2 < p->radius * p->radius;
+            }
+            if (ok) { accept[(size_t)qy * W + qx] = 1; ++cnt; }
         }
     }
     return cnt;
