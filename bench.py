@@ -23,12 +23,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "gathered samples/s and output Mpix/s at 1080p; PSNR vs clean render & oracle"
-# workloads: name -> (W, H, frames, half window T, k, first output frame, output frames per step)
+# workloads: name -> (W, H, frames, half window T, k, first output frame, output frames per step, mode)
 WORKLOADS = {
-    "fhd": (1920, 1080, 68, 30, 7, 30, 8),   # 1080p denoising over +-30 frames (the headline)
-    "hd": (1280, 720, 60, 15, 7, 15, 8),     # 720p, +-15 frames
+    "fhd": (1920, 1080, 68, 30, 7, 30, 8, 0),       # 1080p denoising over +-30 frames (the headline)
+    "hd": (1280, 720, 60, 15, 7, 15, 8, 0),         # 720p denoising, +-15 frames
+    "aperture": (1920, 1080, 68, 30, 7, 30, 8, 1),  # 1080p virtual aperture over +-30 frames
 }
-W, H, F, T, K_WIN, O_BEGIN, N_OUT = WORKLOADS["fhd"]
+W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE = WORKLOADS["fhd"]
+APERTURE, LENS, CAP = 0.05, 16, 31
 RADIUS_REL = 0.005
 BYTES_PER_CANDIDATE = {"fp32": 16, "fp16": 12}
 
@@ -117,6 +119,13 @@ def _workload_clip(seed):
 
 
 def _config(colour):
+    if MODE == 1:
+        return {"workload": f"aperture-{W}x{H}-pm{T}-{colour}", "W": W, "H": H, "frames": F,
+                "out_frames_per_step": N_OUT, "half_window": T, "aperture": APERTURE, "focal_plane": "median depth",
+                "lens_samples": LENS, "cap": CAP, "k": K_WIN,
+                "scene": "synthetic 6 planes + 4 boxes, hand-held path, depth noise 2%, image noise 0.05",
+                "colour": colour, "l2": "no flush: packed input planes exceed the 129 MB L2",
+                "note": "frames beyond O+T are never read, so the clip stops at 68 frames"}
     return {"workload": f"denoise-{W}x{H}-pm{T}-k{K_WIN}-{colour}", "W": W, "H": H, "frames": F,
             "out_frames_per_step": N_OUT, "half_window": T, "k": K_WIN, "radius": f"{RADIUS_REL:g} x median depth",
             "scene": "synthetic 6 planes + 4 boxes, hand-held path, depth noise 2%, image noise 0.05",
@@ -124,21 +133,39 @@ def _config(colour):
 
 
 def cpu_oracle_sample(clip, target_s=10.0, O=None, max_frames=None):
-    """Times the FP64 oracle on whole output frames O, O+1, ... until about target_s seconds."""
+    """Times the FP64 oracle on whole output frames O, O+1, ... until about target_s seconds
+    (denoising), or on a centred crop of frame O grown until about target_s / 4 seconds (aperture,
+    whose full frame takes minutes on the host)."""
     import oracle
     O = O_BEGIN if O is None else O
     max_frames = N_OUT if max_frames is None else max_frames
     v = oracle.ClipView.of(clip)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    if MODE == 1:
+        prm = oracle.Params(mode=oracle.MODE_APERTURE, k=K_WIN, T=T, aperture=APERTURE,
+                            focal_depth=oracle.median_depth(clip.depth), lens_samples=LENS, cap=CAP)
+        side = 32
+        while True:
+            crop = ((W - side) // 2, (H - side) // 2, side, side)
+            t0 = time.perf_counter()
+            res = oracle.gather_filter(v, prm, O, crop=crop)
+            dt = time.perf_counter() - t0
+            if dt > target_s / 4 or 2 * side > min(W, H):
+                break
+            side *= 2
+        return dict(frames=1, crop=crop, seconds=dt, mpix_s=side * side / dt / 1e6, cores=cores, results=[res],
+                    examined=int(res.nexam.sum()), accepted=int(res.nacc.sum()),
+                    sample=f"{side}x{side} centre crop of output frame {O} ({dt:.1f} s)")
     prm = oracle.default_params(clip.depth, k=K_WIN, T=T, radius_rel=RADIUS_REL)
     results, dt = [], 0.0
     while len(results) < max_frames and (not results or dt < target_s):
         t0 = time.perf_counter()
         results.append(oracle.gather_filter(v, prm, O + len(results)))
         dt += time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     n = len(results)
-    return dict(frames=n, seconds=dt, mpix_s=n * W * H / dt / 1e6, cores=cores, results=results,
-                examined=sum(int(r.nexam.sum()) for r in results), accepted=sum(int(r.nacc.sum()) for r in results),
+    return dict(frames=n, crop=(0, 0, W, H), seconds=dt, mpix_s=n * W * H / dt / 1e6, cores=cores,
+                results=results, examined=sum(int(r.nexam.sum()) for r in results),
+                accepted=sum(int(r.nacc.sum()) for r in results),
                 sample=f"{n} full output frame(s) {O}..{O + n - 1} ({dt:.1f} s)")
 
 
@@ -151,19 +178,19 @@ def run_reference(args):
     times = []
     samples = []
     for i in range(args.warmup + args.steps):
-        s = cpu_oracle_sample(clip, target_s=0.0, max_frames=1)
+        s = cpu_oracle_sample(clip, target_s=0.0 if MODE == 0 else 8.0, max_frames=1)
         if i >= args.warmup:
             times.append(s["seconds"])
             samples.append(s)
     s = samples[-1]
-    px = W * H
+    px = s["crop"][2] * s["crop"][3] * s["frames"]
     value = px / float(np.mean(times)) / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config("fp32"),
             "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": s["cores"], "kind": "oracle",
-                             "sample": f"one full output frame ({O_BEGIN}) per step"},
+                             "sample": s["sample"] + " per step"},
             "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "samples_per_s": {"examined": s["examined"] / float(np.mean(times)),
                               "accepted": s["accepted"] / float(np.mean(times))}}
@@ -182,8 +209,8 @@ def main():
     ap.add_argument("--workload", default="fhd", choices=sorted(WORKLOADS))
     ap.add_argument("--out-frames", type=int, default=None, help="output frames per step (default per workload)")
     args = ap.parse_args()
-    global W, H, F, T, K_WIN, O_BEGIN, N_OUT
-    W, H, F, T, K_WIN, O_BEGIN, N_OUT = WORKLOADS[args.workload]
+    global W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE
+    W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE = WORKLOADS[args.workload]
     if args.out_frames:
         N_OUT = args.out_frames
     if args.impl == "reference":
@@ -220,6 +247,8 @@ def main():
     p = ss.ssvp_params_default()
     p.k, p.half_window, p.frame_begin, p.frame_end = K_WIN, T, O_BEGIN, O_BEGIN + N_OUT
     p.radius = -RADIUS_REL
+    if MODE == 1:
+        p.mode, p.aperture, p.focal_depth, p.lens_samples, p.cap = 1, APERTURE, 0.0, LENS, CAP
 
     def barrier():
         if world > 1:
@@ -262,6 +291,16 @@ def main():
     noisy = clip.rgb[O_BEGIN:O_BEGIN + N_OUT]
     psnr = lambda a, b: float(10 * np.log10(1.0 / np.mean((a.astype(np.float64) - b) ** 2)))
     psnr_out, psnr_in = psnr(outn, clean), psnr(noisy, clean)
+    psnr_ref = "clean pinhole render"
+    if MODE == 1:
+        # reference: a thin-lens render (256 lens rays per pixel) of the first output frame
+        import synth
+        objs, _, _ = synth.scene_and_path("room", W, H, F, rank)
+        z0 = ss.ssvp_clip_median_depth(ctx, 0)
+        lens = synth.render_thinlens(objs, clip.K[O_BEGIN:O_BEGIN + 1], clip.w2c_true[O_BEGIN:O_BEGIN + 1], W, H,
+                                     APERTURE, z0, n_lens=256)
+        psnr_out, psnr_in = psnr(outn[:1], lens), psnr(noisy[:1], lens)
+        psnr_ref = "thin-lens render (256 rays/pixel) of the first output frame"
 
     # ---------------- end to end through the C ABI with host buffers
     rgb_h = torch.from_numpy(clip.rgb).pin_memory()
@@ -310,7 +349,7 @@ def main():
         "samples_per_s": {"examined": world * examined / (ms_per_step / 1e3),
                           "accepted": world * accepted / (ms_per_step / 1e3)},
         "accepted_per_pixel": accepted / (N_OUT * W * H), "kept_weight_fraction": sum_w / max(accepted, 1),
-        "psnr_db": {"output_vs_clean": psnr_out, "input_vs_clean": psnr_in},
+        "psnr_db": {"output_vs_clean": psnr_out, "input_vs_clean": psnr_in, "reference": psnr_ref},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -328,7 +367,9 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = cpu_oracle_sample(clip)
-        diff = np.stack([np.abs(outn[i].astype(np.float64) - r.rgb).max(-1) for i, r in enumerate(s["results"])])
+        x0, y0, cw, ch = s["crop"]
+        diff = np.stack([np.abs(outn[i, y0:y0 + ch, x0:x0 + cw].astype(np.float64) - r.rgb).max(-1)
+                         for i, r in enumerate(s["results"])])
         line["cpu_baseline"] = {"value": s["mpix_s"], "unit": "Mpix/s", "cores": s["cores"], "kind": "oracle",
                                 "sample": s["sample"]}
         line["max_abs_vs_oracle"] = {"value": float(diff.max()), "p999": float(np.quantile(diff, 0.999)),

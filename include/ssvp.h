@@ -78,7 +78,10 @@ enum {
  *                 status (-2 invalid reference depth, -1 J outside the clip, 0 J skipped: the
  *                 reference point is behind camera J, 1 gathered, 2 no window pixel inside the
  *                 image), window centre x, y, then the accepted bits of the k x k window
- *                 (bit dy*k+dx).  Only valid with a single output frame.
+ *                 (bit dy*k+dx).  In aperture mode the record is 5 + ceil(cap*cap/32) words:
+ *                 status, the scanned box x0, y0, x1, y1 (inclusive, before clipping to the
+ *                 image), then the accepted bits of the box (bit (y-y0)*cap + (x-x0)).
+ *                 Only valid with a single output frame.
  *   pixel_stats_out  optional device buffer (debug): per crop pixel 3 words: int32 accepted,
  *                 int32 examined (window pixels inside the image), float sum of weights.
  */

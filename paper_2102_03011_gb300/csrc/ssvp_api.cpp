@@ -137,8 +137,16 @@ void compose_pair(const double *KO, const double *wO, const double *KJ, const do
 
 int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
     if (!p) return fail(ctx, SSVP_EINVAL, "params is NULL");
-    if (p->mode != SSVP_MODE_DENOISE && p->mode != SSVP_MODE_MEAN)
+    if (p->mode != SSVP_MODE_DENOISE && p->mode != SSVP_MODE_MEAN && p->mode != SSVP_MODE_APERTURE)
         return fail(ctx, SSVP_EINVAL, "mode %d is not available in this build", p->mode);
+    if (p->mode == SSVP_MODE_APERTURE) {
+        if (p->cap < 1 || p->cap > 63 || (p->cap & 1) == 0) return fail(ctx, SSVP_EINVAL, "cap=%d must be odd in [1, 63]", p->cap);
+        if (p->lens_samples < 1 || p->lens_samples > 64)
+            return fail(ctx, SSVP_EINVAL, "lens_samples=%d must be in [1, 64]", p->lens_samples);
+        if (!(p->aperture >= 0.0f && std::isfinite(p->aperture))) return fail(ctx, SSVP_EINVAL, "aperture must be >= 0");
+        if (!std::isfinite(p->focal_depth) || !std::isfinite(p->a0))
+            return fail(ctx, SSVP_EINVAL, "focal_depth and a0 must be finite");
+    }
     if (p->k < 1 || p->k > SSVP_MAX_K || (p->k & 1) == 0) return fail(ctx, SSVP_EINVAL, "k=%d must be odd in [1, 31]", p->k);
     if (p->half_window < 0 || p->half_window > SSVP_MAX_HALF_WINDOW)
         return fail(ctx, SSVP_EINVAL, "half_window=%d must be in [0, 127]", p->half_window);
@@ -427,11 +435,23 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         a.sigma_rgb = p.sigma_rgb;
         a.sigma_xyz = p.sigma_xyz;
         a.sigma_f = p.sigma_f;
+        a.aperture = p.aperture;
+        a.focal_depth = p.focal_depth;
+        a.a0 = p.a0;
+        a.cap = p.cap;
+        a.lens_n = p.mode == SSVP_MODE_APERTURE ? p.lens_samples : 0;
+        for (int i = 0; i < a.lens_n; ++i) {
+            // Vogel (golden-angle) disc of unit radius; the kernel scales it by the lens radius
+            const double rho = std::sqrt((i + 0.5) / a.lens_n), th = 2.399963229728653 * i;
+            a.lens_xy[2 * i] = (float)(rho * std::cos(th));
+            a.lens_xy[2 * i + 1] = (float)(rho * std::sin(th));
+        }
         a.membership = (int32_t *)p.membership_out;
         a.pixel_stats = (int32_t *)p.pixel_stats_out;
         a.stat_counts = ctx->stat_counts;
         a.stat_sumw = ctx->stat_sumw;
-        CK(ssvp::launch_gather(a, ctx->stream), "gather kernel");
+        if (p.mode == SSVP_MODE_APERTURE) CK(ssvp::launch_aperture(a, ctx->stream), "aperture kernel");
+        else CK(ssvp::launch_gather(a, ctx->stream), "gather kernel");
         off += (size_t)nout[i] * ns;
     }
     return SSVP_OK;

@@ -49,6 +49,13 @@ struct GatherArgs {
     int k, mode;
     float radius;             // > 0 absolute, < 0 relative to *clip.median
     float sigma_rgb, sigma_xyz, sigma_f;  // sigma_xyz <= 0: equal to the radius
+    // virtual aperture (mode 1)
+    float aperture;           // A, lens radius
+    float focal_depth;        // z0; <= 0: *clip.median
+    float a0;                 // cone waist; <= 0: 0.5 z0 / fx_O
+    int lens_n;               // seed points
+    int cap;                  // box cap per axis (odd)
+    float lens_xy[128];       // seed lens points (x, y) on the unit-radius disc, scaled by A in the kernel
     int32_t *membership;      // debug record per (crop pixel, slot) or null
     int32_t *pixel_stats;     // debug record per crop pixel or null
     unsigned long long *stat_counts;  // [0] examined, [1] accepted
@@ -60,6 +67,7 @@ cudaError_t launch_pack(const float *rgb, const float *depth, int W, int H, int 
 cudaError_t launch_median(const Planes &p, unsigned int *scratch, cudaStream_t s);
 size_t median_scratch_words();
 cudaError_t launch_gather(const GatherArgs &a, cudaStream_t s);
+cudaError_t launch_aperture(const GatherArgs &a, cudaStream_t s);
 
 // largest input of ssvp_median_depth_noalloc: its fixed scratch counts values in 32-bit words
 constexpr unsigned long long kMedianNoallocMax = 0xffffffffull;

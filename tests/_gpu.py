@@ -18,7 +18,8 @@ class GpuResult:
     sumw: np.ndarray | None = None
     status: np.ndarray | None = None  # (ch, cw, ns)
     centre: np.ndarray | None = None  # (ch, cw, ns, 2)
-    bits: np.ndarray | None = None    # (ch, cw, ns, k, k) bool
+    bits: np.ndarray | None = None    # (ch, cw, ns, k, k) bool (aperture: cap x cap from the box origin)
+    box: np.ndarray | None = None     # (ch, cw, ns, 4) aperture box x0, y0, x1, y1
 
 
 class Session:
@@ -61,8 +62,11 @@ class Session:
         W, H, F = self.clips[cid]
         x0, y0, cw, ch = crop if crop is not None else (0, 0, W, H)
         p = self.params(frame_begin=O, frame_end=O + 1, crop_x=x0, crop_y=y0, crop_w=cw, crop_h=ch, **kw)
-        k, ns = p.k, 2 * p.half_window + 1
-        recw = 3 + (k * k + 31) // 32
+        ns = 2 * p.half_window + 1
+        aperture = p.mode == ss.SSVP_MODE_APERTURE
+        k = p.cap if aperture else p.k
+        head = 5 if aperture else 3
+        recw = head + (k * k + 31) // 32
         mem = stats = None
         if membership:
             mem = t.zeros((ch, cw, ns, recw), dtype=t.int32, device=self.dev)
@@ -81,8 +85,11 @@ class Session:
             res.nacc, res.nexam = s[..., 0].astype(np.int64), s[..., 1].astype(np.int64)
             res.sumw = s[..., 2].view(np.float32).astype(np.float64)
             res.status = m[..., 0]
-            res.centre = m[..., 1:3]
-            words = m[..., 3:].view(np.uint32)
+            if aperture:
+                res.box = m[..., 1:5]
+            else:
+                res.centre = m[..., 1:3]
+            words = m[..., head:].view(np.uint32)
             b = np.arange(k * k)
             bits = (words[..., b >> 5] >> (b & 31).astype(np.uint32)) & 1
             res.bits = bits.reshape(ch, cw, ns, k, k).astype(bool)
@@ -127,3 +134,34 @@ def compare(g: GpuResult, o: oracle.Result, k: int):
                 max_colour_err=float(cerr[ok].max(initial=0.0)), max_colour_err_all=float(cerr.max()),
                 band_candidates=int((band & (o.status == 1)[..., None, None]).sum()),
                 band_flips=int(bit_diff.sum()), ambiguous_windows=int(amb.sum()), centre_flips=int(win_diff.sum()))
+
+
+def compare_aperture(g: GpuResult, o: oracle.Result, cap: int):
+    """Aperture membership: the scanned box must match except at flagged rounding ties of the
+    seed projections; accepted bits must match except within 1e-5 of the cone radius; colour
+    and counts are compared wherever no such allowed difference occurred."""
+    amb = (o.amb == 1) & (o.status == 1)
+    band = (o.codes & oracle.CODE_BAND) != 0
+    o_acc = (o.codes & 7) == oracle.CODE_ACCEPT
+    o_none = (o.status == 1) & np.all((o.codes & 7) == oracle.CODE_OUT, axis=(-1, -2))
+    g_stat = np.where(g.status == 2, 1, g.status)
+    st_diff = o.status != g_stat
+    assert not (st_diff & ~amb).any(), f"status mismatch at {np.argwhere(st_diff & ~amb)[:5]}"
+    both = (o.status == 1) & (g.status == 1) & ~o_none
+    box_diff = both & np.any(o.box != g.box, axis=-1)
+    assert not (box_diff & ~amb).any(), f"box mismatch at {np.argwhere(box_diff & ~amb)[:5]}"
+    cmp = both & ~box_diff
+    bit_diff = (o_acc != g.bits) & cmp[..., None, None]
+    assert not (bit_diff & ~band).any(), \
+        f"{int((bit_diff & ~band).sum())} membership differences, first {np.argwhere(bit_diff & ~band)[:5]}"
+    excl = (st_diff | box_diff).any(-1) | bit_diff.any(axis=(-1, -2, -3))
+    ok = ~excl
+    cerr = np.abs(g.rgb.astype(np.float64) - o.rgb).max(-1)
+    assert cerr[ok].max(initial=0.0) <= COLOUR_TOL, f"colour max abs {cerr[ok].max()} > {COLOUR_TOL}"
+    np.testing.assert_array_equal(g.nacc[ok], o.nacc[ok])
+    np.testing.assert_array_equal(g.nexam[ok], o.nexam[ok])
+    np.testing.assert_allclose(g.sumw[ok], o.sumw[ok], rtol=1e-4)
+    ch, cw, ns = o.status.shape
+    return dict(pixels=ch * cw, excluded=int(excl.sum()), members=int((o_acc & cmp[..., None, None]).sum()),
+                max_colour_err=float(cerr[ok].max(initial=0.0)), band_flips=int(bit_diff.sum()),
+                box_flips=int(box_diff.sum()), ambiguous_windows=int(amb.sum()))
