@@ -172,6 +172,42 @@ int ssvp_output_device_ptr(ssvp_ctx *ctx, int clip_id, void **dev_ptr);
  * (Sec. "Filtering" reports W / |S|).  Any pointer may be NULL. */
 int ssvp_read_stats(ssvp_ctx *ctx, unsigned long long *examined, unsigned long long *accepted, double *sum_w);
 
+/*
+ * Batched plans (persistent launch of several clips, captured in a CUDA graph).
+ * A plan fixes the parameters, the clip list and their cameras: it composes every per-(O, J)
+ * transform once, numbers the work items (clip, output-frame chunk, 32 x tile_rows tile),
+ * sizes a persistent grid from the kernel's occupancy, and captures "reset counters + launch"
+ * as a CUDA graph that ssvp_plan_launch replays on the context's stream.  Denoise and mean
+ * modes, full frames, no debug outputs; all clips must share one colour format.  A plan must
+ * be destroyed before any of its clips is reloaded or unloaded (its launch then fails with
+ * SSVP_ENOCLIP) and re-created after ssvp_set_cameras.
+ */
+typedef struct ssvp_plan ssvp_plan;
+typedef struct ssvp_plan_config {
+    int32_t tile_rows;    /* output rows per CTA: 4 or 8 */
+    int32_t frame_chunk;  /* consecutive output frames per work item: 1 .. 16 */
+} ssvp_plan_config;
+
+/* Autotuner: times every (tile_rows, frame_chunk) candidate on a sample of the plan's work (the
+ * first 4 output frames of every listed clip) and keeps the fastest in the context for later
+ * plans with the same k, half window, mode and colour format; *best (may be NULL) receives it. */
+int ssvp_autotune(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, int n_clips, ssvp_plan_config *best);
+
+/* Create a plan.  config NULL: the context's tuned shape for these parameters if any, else
+ * tile_rows = 8, frame_chunk = 1.  Allocates device memory and synchronises the stream. */
+int ssvp_plan_create(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, int n_clips,
+                     const ssvp_plan_config *config, ssvp_plan **out);
+
+/* Replay the plan's graph on the context's stream (asynchronous); statistics as for
+ * ssvp_gather_filter. */
+int ssvp_plan_launch(ssvp_plan *plan);
+
+/* Shape, number of work items and persistent grid size of a plan (any pointer may be NULL). */
+int ssvp_plan_get_config(const ssvp_plan *plan, ssvp_plan_config *config, long long *n_items, int *grid);
+
+/* Free a plan (waits for its launches).  NULL is a no-op.  Destroy plans before their context. */
+void ssvp_plan_destroy(ssvp_plan *plan);
+
 /* Lower-median valid input depth of a loaded clip (waits for the load). */
 int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median);
 

@@ -39,6 +39,10 @@ class ssvp_params(ctypes.Structure):
                 ("membership_out", ctypes.c_void_p), ("pixel_stats_out", ctypes.c_void_p)]
 
 
+class ssvp_plan_config(ctypes.Structure):
+    _fields_ = [("tile_rows", ctypes.c_int32), ("frame_chunk", ctypes.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_2102_03011_gb300._build.build()")
@@ -62,6 +66,13 @@ def _load():
         "ssvp_clip_median_depth": (i, [vp, i, ctypes.POINTER(f)]),
         "ssvp_sync": (i, [vp]),
         "ssvp_median_depth_noalloc": (i, [vp, ctypes.c_ulonglong, vp, vp]),
+        "ssvp_autotune": (i, [vp, P, ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(ssvp_plan_config)]),
+        "ssvp_plan_create": (i, [vp, P, ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(ssvp_plan_config),
+                                 ctypes.POINTER(vp)]),
+        "ssvp_plan_launch": (i, [vp]),
+        "ssvp_plan_get_config": (i, [vp, ctypes.POINTER(ssvp_plan_config), ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_int)]),
+        "ssvp_plan_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -186,3 +197,41 @@ def ssvp_median_depth_noalloc(depth_dev, n: int, median_dev, cuda_stream=None) -
     pm, _ = _ptr(median_dev)
     s = cuda_stream.cuda_stream if hasattr(cuda_stream, "cuda_stream") else cuda_stream
     _check(None, lib.ssvp_median_depth_noalloc(pd, int(n), pm, s))
+
+
+def ssvp_autotune(ctx, params: ssvp_params, clip_ids) -> ssvp_plan_config:
+    ids = (ctypes.c_int * len(clip_ids))(*[int(c) for c in clip_ids])
+    best = ssvp_plan_config()
+    _check(ctx, lib.ssvp_autotune(ctx, ctypes.byref(params), ids, len(clip_ids), ctypes.byref(best)))
+    return best
+
+
+class Plan:
+    """Handle of an ssvp_plan together with its context (for error text)."""
+
+    def __init__(self, handle, ctx):
+        self.handle, self.ctx = handle, ctx
+
+
+def ssvp_plan_create(ctx, params: ssvp_params, clip_ids, config: ssvp_plan_config | None = None) -> Plan:
+    ids = (ctypes.c_int * len(clip_ids))(*[int(c) for c in clip_ids])
+    out = ctypes.c_void_p()
+    cfg = ctypes.byref(config) if config is not None else None
+    _check(ctx, lib.ssvp_plan_create(ctx, ctypes.byref(params), ids, len(clip_ids), cfg, ctypes.byref(out)))
+    return Plan(out, ctx)
+
+
+def ssvp_plan_launch(plan: Plan) -> None:
+    _check(plan.ctx, lib.ssvp_plan_launch(plan.handle))
+
+
+def ssvp_plan_get_config(plan: Plan):
+    """-> (ssvp_plan_config, n_items, grid)"""
+    cfg, n, g = ssvp_plan_config(), ctypes.c_longlong(), ctypes.c_int()
+    _check(plan.ctx, lib.ssvp_plan_get_config(plan.handle, ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(g)))
+    return cfg, int(n.value), int(g.value)
+
+
+def ssvp_plan_destroy(plan: Plan) -> None:
+    lib.ssvp_plan_destroy(plan.handle)
+    plan.handle = None

@@ -22,6 +22,7 @@ namespace {
 struct Clip {
     bool loaded = false;
     bool has_cams = false;
+    unsigned generation = 0;  // bumped on every load and unload
     Planes p{};
     std::vector<double> K;    // F * 9
     std::vector<double> w2c;  // F * 12
@@ -45,6 +46,29 @@ struct ssvp_ctx {
     void *staging = nullptr;
     size_t staging_bytes = 0;
     std::vector<PairGeom> host_geom;
+    unsigned clip_generation[SSVP_MAX_CLIPS] = {};
+    // tuned batch shapes: key (k, half window, mode, colour format) -> config
+    struct Tuned {
+        int k, T, mode, cfmt;
+        ssvp_plan_config cfg;
+    };
+    std::vector<Tuned> tuned;
+};
+
+struct ssvp_plan {
+    ssvp_ctx *ctx = nullptr;
+    ssvp_params params{};
+    std::vector<int> clip_ids;
+    std::vector<unsigned> generations;
+    ssvp_plan_config cfg{8, 1};
+    long long n_items = 0;
+    int grid = 0;
+    PairGeom *d_geom = nullptr;
+    ssvp::BatchClip *d_clips = nullptr;
+    unsigned long long *d_counter = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -135,6 +159,26 @@ void compose_pair(const double *KO, const double *wO, const double *KJ, const do
     g.pad_ = 0;
 }
 
+// A1 for output frames [fb, fb + n_out) of a clip: n_out * (2T + 1) entries, slot j <-> J = O - T + j.
+void compose_table(const Clip &c, int fb, int n_out, int T, double sigma_f, PairGeom *out) {
+    const int ns = 2 * T + 1;
+    for (int oi = 0; oi < n_out; ++oi) {
+        const int O = fb + oi;
+        for (int j = 0; j < ns; ++j) {
+            const int J = O - T + j;
+            PairGeom &g = out[(size_t)oi * ns + j];
+            if (J < 0 || J >= c.p.F) {
+                std::memset(&g, 0, sizeof(g));
+                g.J = -1;
+                continue;
+            }
+            compose_pair(&c.K[9 * (size_t)O], &c.w2c[12 * (size_t)O], &c.K[9 * (size_t)J], &c.w2c[12 * (size_t)J],
+                         J == O, J - O, sigma_f, g);
+            g.J = J;
+        }
+    }
+}
+
 int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
     if (!p) return fail(ctx, SSVP_EINVAL, "params is NULL");
     if (p->mode != SSVP_MODE_DENOISE && p->mode != SSVP_MODE_MEAN && p->mode != SSVP_MODE_APERTURE)
@@ -156,6 +200,100 @@ int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
     if (!std::isfinite(p->sigma_xyz)) return fail(ctx, SSVP_EINVAL, "sigma_xyz must be finite");
     if (p->crop_w < 0 || p->crop_h < 0) return fail(ctx, SSVP_EINVAL, "negative crop size");
     return SSVP_OK;
+}
+
+
+// ---------------------------------------------------------------- batched plans (A10)
+
+struct BatchSetup {
+    std::vector<ssvp::BatchClip> clips;
+    std::vector<PairGeom> geom;
+    std::vector<size_t> geom_off;
+    long long n_items = 0;
+    int cfmt = 0, ns = 0;
+};
+
+int batch_check(ssvp_ctx *ctx, const ssvp_params *p, const int *ids, int n, int &cfmt) {
+    int rc = check_params(ctx, p);
+    if (rc != SSVP_OK) return rc;
+    if (p->mode != SSVP_MODE_DENOISE && p->mode != SSVP_MODE_MEAN)
+        return fail(ctx, SSVP_EINVAL, "batched plans support the denoise and mean modes");
+    if (p->crop_w != 0 || p->crop_h != 0) return fail(ctx, SSVP_EINVAL, "batched plans gather full frames (crop_w = crop_h = 0)");
+    if (p->membership_out || p->pixel_stats_out) return fail(ctx, SSVP_EINVAL, "batched plans have no debug outputs");
+    if (!ids || n < 1 || n > SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "bad clip list");
+    for (int i = 0; i < n; ++i) {
+        if (ids[i] < 0 || ids[i] >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", ids[i]);
+        const Clip &c = ctx->clips[ids[i]];
+        if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", ids[i]);
+        if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", ids[i]);
+        if (i == 0) cfmt = c.p.colour_fmt;
+        else if (c.p.colour_fmt != cfmt) return fail(ctx, SSVP_EINVAL, "all clips of a plan must share one colour format");
+        int b = p->frame_begin, e = p->frame_end < 0 ? c.p.F : p->frame_end;
+        if (b < 0 || e > c.p.F || b > e) return fail(ctx, SSVP_EINVAL, "frame range [%d, %d) outside clip %d (F=%d)", b, e, ids[i], c.p.F);
+    }
+    return SSVP_OK;
+}
+
+// host tables of every clip, output frames [fb, fb + min(n_out, max_out))
+void batch_tables(ssvp_ctx *ctx, const ssvp_params &p, const int *ids, int n, int max_out, BatchSetup &bs) {
+    const int T = p.half_window;
+    bs.ns = 2 * T + 1;
+    bs.clips.assign(n, ssvp::BatchClip{});
+    bs.geom_off.assign(n, 0);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const Clip &c = ctx->clips[ids[i]];
+        const int b = p.frame_begin, e = p.frame_end < 0 ? c.p.F : p.frame_end;
+        ssvp::BatchClip &bc = bs.clips[i];
+        bc.p = c.p;
+        bc.frame_begin = b;
+        bc.n_out = std::min(e - b, max_out);
+        bs.geom_off[i] = total;
+        total += (size_t)bc.n_out * bs.ns;
+    }
+    bs.geom.resize(std::max<size_t>(total, 1));
+    for (int i = 0; i < n; ++i)
+        compose_table(ctx->clips[ids[i]], bs.clips[i].frame_begin, bs.clips[i].n_out, T, p.sigma_f, &bs.geom[bs.geom_off[i]]);
+}
+
+// number the work items for a shape; geometry pointers into d_geom
+void batch_items(BatchSetup &bs, const ssvp_plan_config &cfg, PairGeom *d_geom) {
+    long long item = 0;
+    for (size_t i = 0; i < bs.clips.size(); ++i) {
+        ssvp::BatchClip &bc = bs.clips[i];
+        bc.geom = d_geom + bs.geom_off[i];
+        bc.tiles_x = (bc.p.W + 31) / 32;
+        bc.tiles_y = (bc.p.H + cfg.tile_rows - 1) / cfg.tile_rows;
+        bc.item_begin = item;
+        const long long chunks = (bc.n_out + cfg.frame_chunk - 1) / cfg.frame_chunk;
+        item += chunks * bc.tiles_x * bc.tiles_y;
+    }
+    bs.n_items = item;
+}
+
+GatherArgs batch_gather_args(ssvp_ctx *ctx, const ssvp_params &p) {
+    GatherArgs a{};
+    a.n_slots = 2 * p.half_window + 1;
+    a.T = p.half_window;
+    a.k = p.k;
+    a.mode = p.mode;
+    a.radius = p.radius;
+    a.sigma_rgb = p.sigma_rgb;
+    a.sigma_xyz = p.sigma_xyz;
+    a.sigma_f = p.sigma_f;
+    a.stat_counts = ctx->stat_counts;
+    a.stat_sumw = ctx->stat_sumw;
+    return a;
+}
+
+bool valid_config(const ssvp_plan_config &c) {
+    return (c.tile_rows == 4 || c.tile_rows == 8) && c.frame_chunk >= 1 && c.frame_chunk <= 16;
+}
+
+const ssvp_plan_config *find_tuned(const ssvp_ctx *ctx, const ssvp_params &p, int cfmt) {
+    for (const auto &t : ctx->tuned)
+        if (t.k == p.k && t.T == p.half_window && t.mode == p.mode && t.cfmt == cfmt) return &t.cfg;
+    return nullptr;
 }
 
 }  // namespace
@@ -224,7 +362,7 @@ void ssvp_destroy(ssvp_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    for (auto &c : ctx->clips) free_clip(c);
+    for (auto &c : ctx->clips) free_clip(c);  // plans of this context must be destroyed first
     if (ctx->stat_counts) cudaFree(ctx->stat_counts);
     if (ctx->stat_sumw) cudaFree(ctx->stat_sumw);
     if (ctx->median_scratch) cudaFree(ctx->median_scratch);
@@ -313,6 +451,7 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
     CK(ssvp::launch_median(p, ctx->median_scratch, ctx->stream), "median kernels");
     c.loaded = true;
     c.has_cams = false;
+    c.generation = ++ctx->clip_generation[clip_id];
     return SSVP_OK;
 }
 
@@ -323,6 +462,7 @@ int ssvp_unload_clip(ssvp_ctx *ctx, int clip_id) {
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     free_clip(ctx->clips[clip_id]);
+    ++ctx->clip_generation[clip_id];
     return SSVP_OK;
 }
 
@@ -395,22 +535,7 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
     ctx->host_geom.resize(std::max<size_t>(total, 1));
     size_t off = 0;
     for (int i = 0; i < n_clips; ++i) {
-        Clip &c = ctx->clips[clip_ids[i]];
-        for (int oi = 0; oi < nout[i]; ++oi) {
-            const int O = fb[i] + oi;
-            for (int j = 0; j < ns; ++j) {
-                const int J = O - T + j;
-                PairGeom &g = ctx->host_geom[off + (size_t)oi * ns + j];
-                if (J < 0 || J >= c.p.F) {
-                    std::memset(&g, 0, sizeof(g));
-                    g.J = -1;
-                    continue;
-                }
-                compose_pair(&c.K[9 * (size_t)O], &c.w2c[12 * (size_t)O], &c.K[9 * (size_t)J], &c.w2c[12 * (size_t)J],
-                             J == O, J - O, p.sigma_f, g);
-                g.J = J;
-            }
-        }
+        compose_table(ctx->clips[clip_ids[i]], fb[i], nout[i], T, p.sigma_f, &ctx->host_geom[off]);
         off += (size_t)nout[i] * ns;
     }
     // pageable source: the call returns once the table is staged, so host_geom may be reused
@@ -509,6 +634,163 @@ int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median) {
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     CK(cudaMemcpyAsync(median, ctx->clips[clip_id].p.median, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
     CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    return SSVP_OK;
+}
+
+int ssvp_autotune(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, int n_clips, ssvp_plan_config *best) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    int cfmt = 0;
+    int rc = batch_check(ctx, params, clip_ids, n_clips, cfmt);
+    if (rc != SSVP_OK) return rc;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    BatchSetup bs;
+    batch_tables(ctx, *params, clip_ids, n_clips, 4, bs);
+    PairGeom *d_geom = nullptr;
+    ssvp::BatchClip *d_clips = nullptr;
+    unsigned long long *d_counter = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaSuccess;
+    ssvp_plan_config winner{8, 1};
+    float best_ms = 3.0e38f;
+    const ssvp_plan_config cands[] = {{4, 1}, {4, 2}, {4, 4}, {8, 1}, {8, 2}, {8, 4}};
+    GatherArgs a = batch_gather_args(ctx, *params);
+    do {
+        if ((e = cudaMalloc(&d_geom, bs.geom.size() * sizeof(PairGeom))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&d_clips, bs.clips.size() * sizeof(ssvp::BatchClip))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&d_counter, sizeof(unsigned long long))) != cudaSuccess) break;
+        if ((e = cudaMemcpy(d_geom, bs.geom.data(), bs.geom.size() * sizeof(PairGeom), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) break;
+        for (const auto &cfg : cands) {
+            batch_items(bs, cfg, d_geom);
+            if ((e = cudaMemcpyAsync(d_clips, bs.clips.data(), bs.clips.size() * sizeof(ssvp::BatchClip),
+                                     cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess) break;
+            const int grid = ssvp::batch_grid(params->k, cfg.tile_rows, cfmt, bs.ns);
+            ssvp::BatchArgs b{d_clips, n_clips, cfg.frame_chunk, bs.n_items, d_counter};
+            float ms = 0.0f;
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                if (rep == 1 && (e = cudaEventRecord(e0, ctx->stream)) != cudaSuccess) break;
+                if ((e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess) break;
+                e = ssvp::launch_batch(a, b, cfg.tile_rows, cfmt, grid, ctx->stream);
+            }
+            if (e != cudaSuccess) break;
+            if ((e = cudaEventRecord(e1, ctx->stream)) != cudaSuccess) break;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+            if (ms < best_ms) { best_ms = ms; winner = cfg; }
+        }
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(ctx->stream);
+    if (d_geom) cudaFree(d_geom);
+    if (d_clips) cudaFree(d_clips);
+    if (d_counter) cudaFree(d_counter);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+    bool stored = false;
+    for (auto &t : ctx->tuned)
+        if (t.k == params->k && t.T == params->half_window && t.mode == params->mode && t.cfmt == cfmt) {
+            t.cfg = winner;
+            stored = true;
+        }
+    if (!stored) ctx->tuned.push_back({params->k, params->half_window, params->mode, cfmt, winner});
+    if (best) *best = winner;
+    return SSVP_OK;
+}
+
+void ssvp_plan_destroy(ssvp_plan *plan) {
+    if (!plan) return;
+    if (plan->ctx) {
+        cudaSetDevice(plan->ctx->device);
+        cudaStreamSynchronize(plan->ctx->stream);
+    }
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+    if (plan->d_geom) cudaFree(plan->d_geom);
+    if (plan->d_clips) cudaFree(plan->d_clips);
+    if (plan->d_counter) cudaFree(plan->d_counter);
+    delete plan;
+}
+
+int ssvp_plan_create(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, int n_clips,
+                     const ssvp_plan_config *config, ssvp_plan **out) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (!out) return fail(ctx, SSVP_EINVAL, "out is NULL");
+    *out = nullptr;
+    int cfmt = 0;
+    int rc = batch_check(ctx, params, clip_ids, n_clips, cfmt);
+    if (rc != SSVP_OK) return rc;
+    ssvp_plan_config cfg{8, 1};
+    if (config) cfg = *config;
+    else if (const ssvp_plan_config *t = find_tuned(ctx, *params, cfmt)) cfg = *t;
+    if (!valid_config(cfg)) return fail(ctx, SSVP_EINVAL, "plan shape: tile_rows must be 4 or 8, frame_chunk 1..16");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    ssvp_plan *plan = new (std::nothrow) ssvp_plan();
+    if (!plan) return fail(ctx, SSVP_ENOMEM, "host allocation failed");
+    plan->ctx = ctx;
+    plan->params = *params;
+    plan->clip_ids.assign(clip_ids, clip_ids + n_clips);
+    for (int i = 0; i < n_clips; ++i) plan->generations.push_back(ctx->clips[clip_ids[i]].generation);
+    plan->cfg = cfg;
+    BatchSetup bs;
+    batch_tables(ctx, *params, clip_ids, n_clips, 1 << 30, bs);
+    cudaError_t e = cudaSuccess;
+    const char *what = "plan";
+    do {
+        what = "cudaMalloc (plan)";
+        if ((e = cudaMalloc(&plan->d_geom, bs.geom.size() * sizeof(PairGeom))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&plan->d_clips, bs.clips.size() * sizeof(ssvp::BatchClip))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&plan->d_counter, sizeof(unsigned long long))) != cudaSuccess) break;
+        batch_items(bs, cfg, plan->d_geom);
+        plan->n_items = bs.n_items;
+        what = "cudaMemcpy (plan)";
+        if ((e = cudaMemcpy(plan->d_geom, bs.geom.data(), bs.geom.size() * sizeof(PairGeom), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaMemcpy(plan->d_clips, bs.clips.data(), bs.clips.size() * sizeof(ssvp::BatchClip), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        plan->grid = ssvp::batch_grid(params->k, cfg.tile_rows, cfmt, bs.ns);
+        what = "occupancy";
+        if (plan->grid <= 0) { e = cudaErrorInvalidConfiguration; break; }
+        what = "graph capture";
+        if ((e = cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+        GatherArgs a = batch_gather_args(ctx, *params);
+        ssvp::BatchArgs b{plan->d_clips, n_clips, cfg.frame_chunk, plan->n_items, plan->d_counter};
+        cudaError_t e1 = cudaMemsetAsync(plan->d_counter, 0, sizeof(unsigned long long), plan->cap_stream);
+        cudaError_t e2 = cudaMemsetAsync(ctx->stat_counts, 0, 2 * sizeof(unsigned long long), plan->cap_stream);
+        cudaError_t e3 = cudaMemsetAsync(ctx->stat_sumw, 0, sizeof(double), plan->cap_stream);
+        cudaError_t e4 = ssvp::launch_batch(a, b, cfg.tile_rows, cfmt, plan->grid, plan->cap_stream);
+        e = cudaStreamEndCapture(plan->cap_stream, &plan->graph);
+        if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4;
+        if (e != cudaSuccess) break;
+        if ((e = cudaGraphInstantiate(&plan->exec, plan->graph, 0)) != cudaSuccess) break;
+    } while (0);
+    if (e != cudaSuccess) {
+        int code = cuda_fail(ctx, e, what);
+        ssvp_plan_destroy(plan);
+        return code;
+    }
+    *out = plan;
+    return SSVP_OK;
+}
+
+int ssvp_plan_launch(ssvp_plan *plan) {
+    if (!plan) return fail(nullptr, SSVP_EINVAL, "plan is NULL");
+    ssvp_ctx *ctx = plan->ctx;
+    for (size_t i = 0; i < plan->clip_ids.size(); ++i) {
+        const Clip &c = ctx->clips[plan->clip_ids[i]];
+        if (!c.loaded || c.generation != plan->generations[i])
+            return fail(ctx, SSVP_ENOCLIP, "clip %d was reloaded or unloaded after the plan was made", plan->clip_ids[i]);
+    }
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaGraphLaunch(plan->exec, ctx->stream), "cudaGraphLaunch");
+    return SSVP_OK;
+}
+
+int ssvp_plan_get_config(const ssvp_plan *plan, ssvp_plan_config *config, long long *n_items, int *grid) {
+    if (!plan) return fail(nullptr, SSVP_EINVAL, "plan is NULL");
+    if (config) *config = plan->cfg;
+    if (n_items) *n_items = plan->n_items;
+    if (grid) *grid = plan->grid;
     return SSVP_OK;
 }
 

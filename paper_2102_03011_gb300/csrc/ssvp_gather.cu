@@ -38,43 +38,21 @@ constexpr int kAccBatch = SSVP_ACC_BATCH;
 #define SSVP_TILE_Y 8  // output rows per CTA (a warp covers 32 pixels of one row)
 #endif
 constexpr int kTileX = 32, kTileY = SSVP_TILE_Y, kThreads = kTileX * kTileY;
+// The gather and filter of one output pixel (u, v) of frame O (steps A3-A7).  sgeom holds the
+// per-slot geometry built for the tile whose first pixel is (u0, v0).  n_acc, n_exam and acc_w
+// return the pixel's accepted and examined counts and sum of weights (they start at 0).
 // K > 0: compile-time window width (k*k <= 64, one 64-bit accept mask per frame).
 // K == 0: runtime k up to 31, one 32-bit accept mask per window row.
 template <int K, int CFMT, bool DEBUG>
-__global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const GatherArgs a) {
-    extern __shared__ float4 sgeom[];
-    __shared__ float s_const[4];
-    __shared__ unsigned long long s_cnt[2][kThreads / 32];
-    __shared__ float s_w[kThreads / 32];
-
-    const int oi = blockIdx.z;
-    const int O = a.frame_begin + oi;
-    const int u0 = a.x0 + blockIdx.x * kTileX, v0 = a.y0 + blockIdx.y * kTileY;
-    for (int j = threadIdx.x; j < a.n_slots; j += kThreads)
-        build_slot(a.geom[(long long)oi * a.n_slots + j], (float)u0, (float)v0, sgeom + kSlotVec * j);
-    if (threadIdx.x == 0) {
-        float r = a.radius > 0.0f ? a.radius : -a.radius * *a.clip.median;
-        float sx = a.sigma_xyz > 0.0f ? a.sigma_xyz : r;
-        s_const[0] = r * r;
-        s_const[1] = kLog2e / (2.0f * a.sigma_rgb * a.sigma_rgb);
-        s_const[2] = kLog2e / (2.0f * sx * sx);
-        s_const[3] = a.mode == 3 ? 0.0f : 1.0f;
-    }
-    __syncthreads();
-
-    const Planes &P = a.clip;
+__device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &P, const int O, const int u0,
+                                             const int v0, const int u, const int v, const bool active,
+                                             const long long crop_idx, const float4 *sgeom, const int n_slots,
+                                             const float r2, const float a_rgb, const float a_xyz, const bool weighted,
+                                             int &n_acc, int &n_exam, float &acc_w) {
     const int k = K > 0 ? K : a.k;
     const int h = (k - 1) >> 1;
-    const float r2 = s_const[0], a_rgb = s_const[1], a_xyz = s_const[2];
-    const bool weighted = s_const[3] != 0.0f;
-    const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
-    const int u = u0 + tx, v = v0 + ty;
-    const bool active = u < a.x0 + a.cw && v < a.y0 + a.ch;
-    const long long crop_idx = (long long)(v - a.y0) * a.cw + (u - a.x0);
     const int rec_words = 3 + (k * k + 31) / 32;
-
-    int n_acc = 0, n_exam = 0;
-    float acc_w = 0.0f, acc_r = 0.0f, acc_g = 0.0f, acc_b = 0.0f;
+    float acc_r = 0.0f, acc_g = 0.0f, acc_b = 0.0f;
     float3 cref = make_float3(0.f, 0.f, 0.f);
     float dref = 0.0f;
     if (active) {
@@ -84,16 +62,16 @@ __global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const G
     }
     const bool gather = active && dref > 0.0f;  // false for NaN (invalid) depth
     if (DEBUG && active && !gather && a.membership) {
-        for (int j = 0; j < a.n_slots; ++j) a.membership[(crop_idx * a.n_slots + j) * rec_words] = -2;
+        for (int j = 0; j < n_slots; ++j) a.membership[(crop_idx * n_slots + j) * rec_words] = -2;
     }
 
     if (gather) {
         const float du = (float)(u - u0), dv = (float)(v - v0);
-        for (int j = 0; j < a.n_slots; ++j) {
+        for (int j = 0; j < n_slots; ++j) {
             const float4 *g = sgeom + kSlotVec * j;
             const float4 q5 = g[5];
             const int J = __float_as_int(q5.w);
-            int32_t *rec = DEBUG && a.membership ? a.membership + (crop_idx * a.n_slots + j) * rec_words : nullptr;
+            int32_t *rec = DEBUG && a.membership ? a.membership + (crop_idx * n_slots + j) * rec_words : nullptr;
             if (J < 0) {
                 if (DEBUG && rec) rec[0] = -1;
                 continue;
@@ -272,6 +250,40 @@ __global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const G
         }
     }
 
+}
+
+// One CTA per 32 x kTileY output tile of one output frame (grid: tiles x output frames).
+template <int K, int CFMT, bool DEBUG>
+__global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const GatherArgs a) {
+    extern __shared__ float4 sgeom[];
+    __shared__ float s_const[4];
+    __shared__ unsigned long long s_cnt[2][kThreads / 32];
+    __shared__ float s_w[kThreads / 32];
+
+    const int oi = blockIdx.z;
+    const int O = a.frame_begin + oi;
+    const int u0 = a.x0 + blockIdx.x * kTileX, v0 = a.y0 + blockIdx.y * kTileY;
+    for (int j = threadIdx.x; j < a.n_slots; j += kThreads)
+        build_slot(a.geom[(long long)oi * a.n_slots + j], (float)u0, (float)v0, sgeom + kSlotVec * j);
+    if (threadIdx.x == 0) {
+        float r = a.radius > 0.0f ? a.radius : -a.radius * *a.clip.median;
+        float sx = a.sigma_xyz > 0.0f ? a.sigma_xyz : r;
+        s_const[0] = r * r;
+        s_const[1] = kLog2e / (2.0f * a.sigma_rgb * a.sigma_rgb);
+        s_const[2] = kLog2e / (2.0f * sx * sx);
+        s_const[3] = a.mode == 3 ? 0.0f : 1.0f;
+    }
+    __syncthreads();
+
+    const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
+    const int u = u0 + tx, v = v0 + ty;
+    const bool active = u < a.x0 + a.cw && v < a.y0 + a.ch;
+    const long long crop_idx = (long long)(v - a.y0) * a.cw + (u - a.x0);
+    int n_acc = 0, n_exam = 0;
+    float acc_w = 0.0f;
+    gather_pixel<K, CFMT, DEBUG>(a, a.clip, O, u0, v0, u, v, active, crop_idx, sgeom, a.n_slots, s_const[0], s_const[1],
+                                 s_const[2], s_const[3] != 0.0f, n_acc, n_exam, acc_w);
+
     // launch statistics: warp, then block, then one atomic per CTA
     unsigned long long ce = (unsigned long long)n_exam, ca = (unsigned long long)n_acc;
     float sw = acc_w;
@@ -292,6 +304,98 @@ __global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const G
         atomicAdd(a.stat_counts + 1, ta);
         atomicAdd(a.stat_sumw, tw);
     }
+}
+
+
+// Persistent batched gather (A10): CTAs of 32 x TY threads pull work items (clip, output-frame
+// chunk, tile) from a device counter until the list is exhausted, so clips of uneven size share
+// one launch without tail effects per clip.
+template <int K, int CFMT, int TY>
+__global__ void __launch_bounds__(32 * TY, 32 / TY) batch_kernel(const GatherArgs a, const BatchArgs b) {
+    constexpr int NT = 32 * TY;
+    extern __shared__ float4 sgeom[];
+    __shared__ float s_const[4];
+    __shared__ long long s_item;
+    __shared__ Planes s_P;
+    __shared__ unsigned long long s_cnt[2][NT / 32];
+    __shared__ float s_w[NT / 32];
+    unsigned long long t_acc = 0, t_exam = 0;
+    float t_w = 0.0f;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(b.counter, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= b.n_items) break;
+        int c = 0;
+        while (c + 1 < b.n_clips && b.clips[c + 1].item_begin <= item) ++c;
+        const BatchClip &bc = b.clips[c];
+        const long long local = item - bc.item_begin;
+        const int ntile = bc.tiles_x * bc.tiles_y;
+        const int tile = (int)(local % ntile), chunk = (int)(local / ntile);
+        const int u0 = (tile % bc.tiles_x) * 32, v0 = (tile / bc.tiles_x) * TY;
+        const int o_first = chunk * b.frame_chunk, o_last = min(o_first + b.frame_chunk, bc.n_out);
+        for (int oi = o_first; oi < o_last; ++oi) {
+            for (int j = threadIdx.x; j < a.n_slots; j += NT)
+                build_slot(bc.geom[(long long)oi * a.n_slots + j], (float)u0, (float)v0, sgeom + kSlotVec * j);
+            if (threadIdx.x == 0) {
+                s_P = bc.p;
+                const float r = a.radius > 0.0f ? a.radius : -a.radius * *bc.p.median;
+                const float sx = a.sigma_xyz > 0.0f ? a.sigma_xyz : r;
+                s_const[0] = r * r;
+                s_const[1] = kLog2e / (2.0f * a.sigma_rgb * a.sigma_rgb);
+                s_const[2] = kLog2e / (2.0f * sx * sx);
+                s_const[3] = a.mode == 3 ? 0.0f : 1.0f;
+            }
+            __syncthreads();
+            const int u = u0 + (threadIdx.x & 31), v = v0 + (threadIdx.x >> 5);
+            const bool active = u < s_P.W && v < s_P.H;
+            int n_acc = 0, n_exam = 0;
+            float acc_w = 0.0f;
+            gather_pixel<K, CFMT, false>(a, s_P, bc.frame_begin + oi, u0, v0, u, v, active, 0, sgeom, a.n_slots,
+                                         s_const[0], s_const[1], s_const[2], s_const[3] != 0.0f, n_acc, n_exam, acc_w);
+            t_acc += (unsigned long long)n_acc;
+            t_exam += (unsigned long long)n_exam;
+            t_w += acc_w;
+            __syncthreads();  // the shared geometry and s_P are rebuilt next
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t_exam += __shfl_xor_sync(0xffffffffu, t_exam, o);
+        t_acc += __shfl_xor_sync(0xffffffffu, t_acc, o);
+        t_w += __shfl_xor_sync(0xffffffffu, t_w, o);
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_cnt[0][warp] = t_exam; s_cnt[1][warp] = t_acc; s_w[warp] = t_w; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long te = 0, ta = 0;
+        double tw = 0.0;
+        for (int i = 0; i < NT / 32; ++i) { te += s_cnt[0][i]; ta += s_cnt[1][i]; tw += s_w[i]; }
+        atomicAdd(a.stat_counts, te);
+        atomicAdd(a.stat_counts + 1, ta);
+        atomicAdd(a.stat_sumw, tw);
+    }
+}
+
+template <int K, int CFMT, int TY>
+void *batch_fn() { return (void *)batch_kernel<K, CFMT, TY>; }
+
+template <int CFMT, int TY>
+void *batch_fn_k(int k) {
+    switch (k) {
+        case 1: return batch_fn<1, CFMT, TY>();
+        case 3: return batch_fn<3, CFMT, TY>();
+        case 5: return batch_fn<5, CFMT, TY>();
+        case 7: return batch_fn<7, CFMT, TY>();
+        default: return batch_fn<0, CFMT, TY>();
+    }
+}
+
+void *batch_fn_any(int k, int tile_rows, int cfmt) {
+    if (tile_rows == 4) return cfmt == 0 ? batch_fn_k<0, 4>(k) : batch_fn_k<1, 4>(k);
+    if (tile_rows == 8) return cfmt == 0 ? batch_fn_k<0, 8>(k) : batch_fn_k<1, 8>(k);
+    return nullptr;
 }
 
 template <int K, int CFMT>
@@ -320,6 +424,26 @@ cudaError_t launch_c(const GatherArgs &a, cudaStream_t s) {
 cudaError_t launch_gather(const GatherArgs &a, cudaStream_t s) {
     if (a.n_out <= 0 || a.cw <= 0 || a.ch <= 0) return cudaSuccess;
     return a.clip.colour_fmt == 0 ? launch_c<0>(a, s) : launch_c<1>(a, s);
+}
+
+int batch_grid(int k, int tile_rows, int colour_fmt, int n_slots) {
+    void *fn = batch_fn_any(k, tile_rows, colour_fmt);
+    if (!fn) return 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    size_t smem = sizeof(float4) * kSlotVec * (size_t)n_slots;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * tile_rows, smem) != cudaSuccess) return 0;
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+cudaError_t launch_batch(const GatherArgs &a, const BatchArgs &b, int tile_rows, int colour_fmt, int grid,
+                         cudaStream_t s) {
+    void *fn = batch_fn_any(a.k, tile_rows, colour_fmt);
+    if (!fn || grid <= 0) return cudaErrorInvalidValue;
+    size_t smem = sizeof(float4) * kSlotVec * (size_t)a.n_slots;
+    void *args[] = {(void *)&a, (void *)&b};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(32 * tile_rows), args, smem, s);
 }
 
 }  // namespace ssvp

@@ -62,12 +62,32 @@ struct GatherArgs {
     double *stat_sumw;
 };
 
+// One clip of a batched launch (A10).  Work items are (clip, output-frame chunk, tile) triples
+// numbered from item_begin; tiles are 32 x tile_rows output pixels.
+struct BatchClip {
+    Planes p;
+    const PairGeom *geom;     // n_out * n_slots entries
+    int frame_begin, n_out, tiles_x, tiles_y;
+    long long item_begin;
+};
+
+struct BatchArgs {
+    const BatchClip *clips;
+    int n_clips, frame_chunk;
+    long long n_items;
+    unsigned long long *counter;  // work counter, zero before the launch
+};
+
 cudaError_t launch_pack(const float *rgb, const float *depth, int W, int H, int nF, const Planes &dst, int frame0,
                         cudaStream_t s);
 cudaError_t launch_median(const Planes &p, unsigned int *scratch, cudaStream_t s);
 size_t median_scratch_words();
 cudaError_t launch_gather(const GatherArgs &a, cudaStream_t s);
 cudaError_t launch_aperture(const GatherArgs &a, cudaStream_t s);
+// persistent batched gather; grid = batch_grid(...) CTAs
+cudaError_t launch_batch(const GatherArgs &a, const BatchArgs &b, int tile_rows, int colour_fmt, int grid,
+                         cudaStream_t s);
+int batch_grid(int k, int tile_rows, int colour_fmt, int n_slots);
 
 // largest input of ssvp_median_depth_noalloc: its fixed scratch counts values in 32-bit words
 constexpr unsigned long long kMedianNoallocMax = 0xffffffffull;
