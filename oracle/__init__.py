@@ -75,6 +75,17 @@ def _load():
         lib.oc_bruteforce.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, u8p]
         lib.oc_bruteforce.restype = ctypes.c_longlong
+        lib.oc_learned_samples.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int), dp]
+        lib.oc_learned_samples.restype = ctypes.c_int
+        lib.oc_learned_crop.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, i32p, dp]
+        lib.oc_mlp_pixel.argtypes = [dp, dp, ctypes.c_int, dp, dp, dp, dp, ctypes.c_int, ctypes.c_double, dp, dp, dp,
+                                     dp, dp]
+        lib.oc_mlp_pixel.restype = ctypes.c_double
+        lib.oc_mlp_loss_grad.argtypes = [ctypes.c_int, dp, dp, i32p, dp, dp, dp, dp, dp, dp, ctypes.c_int,
+                                         ctypes.c_double, dp, dp, dp, dp]
+        lib.oc_mlp_loss_grad.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -226,3 +237,62 @@ def psnr(a, b) -> float:
     """10 log10(1 / MSE) over all values, peak 1, no clipping."""
     mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
     return float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse)
+
+
+# ------------------------------------------------------------------ learned per-sample weights
+
+MAX_SAMPLES, N_FEAT, N_HID = 64, 16, 64
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def learned_crop(view: ClipView, prm: Params, O: int, crop=None):
+    """Capped sample sets of a crop: features (ch, cw, 64, 16), colours (ch, cw, 64, 3), counts
+    (ch, cw) and the plain Eq. 4 outputs (ch, cw, 3)."""
+    x0, y0, cw, ch = crop if crop is not None else (0, 0, view.W, view.H)
+    feat = np.zeros((ch, cw, MAX_SAMPLES, N_FEAT))
+    col = np.zeros((ch, cw, MAX_SAMPLES, 3))
+    n = np.zeros((ch, cw), np.int32)
+    plain = np.zeros((ch, cw, 3))
+    ps = prm.c_struct(float(view.K[O, 0, 0]))
+    _load().oc_learned_crop(ctypes.byref(view.c), ctypes.byref(ps), O, x0, y0, cw, ch, _p(feat, ctypes.c_double),
+                            _p(col, ctypes.c_double), _p(n, ctypes.c_int32), _p(plain, ctypes.c_double))
+    return feat, col, n, plain
+
+
+def mlp_pixel(feat, col, n, W1, b1, W2, b2, round_bf16=True, tau=0.5, plain=None):
+    """Forward pass of one pixel -> (learned output, final output, conf, z (n, 2))."""
+    feat, col = _d(feat).reshape(-1, N_FEAT), _d(col).reshape(-1, 3)
+    W1, b1, W2, b2 = _d(W1), _d(b1), _d(W2), _d(b2)
+    plain = _d(np.zeros(3) if plain is None else plain)
+    ol, of, z = np.zeros(3), np.zeros(3), np.zeros((max(n, 1), 2))
+    conf = _load().oc_mlp_pixel(_p(feat, ctypes.c_double), _p(col, ctypes.c_double), int(n), _p(W1, ctypes.c_double),
+                                _p(b1, ctypes.c_double), _p(W2, ctypes.c_double), _p(b2, ctypes.c_double),
+                                int(round_bf16), float(tau), _p(plain, ctypes.c_double), _p(ol, ctypes.c_double),
+                                _p(of, ctypes.c_double), _p(z, ctypes.c_double), None)
+    return ol, of, conf, z[:n]
+
+
+def mlp_loss_grad(feat, col, nsamp, plain, clean, W1, b1, W2, b2, round_bf16=True, bce_w=0.1):
+    """Loss and gradients over pixels: feat (P, 64, 16), col (P, 64, 3), nsamp (P,), plain (P, 3),
+    clean (P, 3) -> (L, gW1 (64, 16), gb1 (64,), gW2 (2, 64), gb2 (2,))."""
+    feat, col, plain, clean = _d(feat), _d(col), _d(plain), _d(clean)
+    nsamp = np.ascontiguousarray(nsamp, dtype=np.int32)
+    W1, b1, W2, b2 = _d(W1), _d(b1), _d(W2), _d(b2)
+    g = [np.zeros((N_HID, N_FEAT)), np.zeros(N_HID), np.zeros((2, N_HID)), np.zeros(2)]
+    L = _load().oc_mlp_loss_grad(len(nsamp), _p(feat, ctypes.c_double), _p(col, ctypes.c_double),
+                                 _p(nsamp, ctypes.c_int32), _p(plain, ctypes.c_double), _p(clean, ctypes.c_double),
+                                 _p(W1, ctypes.c_double), _p(b1, ctypes.c_double), _p(W2, ctypes.c_double),
+                                 _p(b2, ctypes.c_double), int(round_bf16), float(bce_w),
+                                 *[_p(x, ctypes.c_double) for x in g])
+    return (L, *g)
+
+
+def he_init(seed=0):
+    """He-normal W1 (64 x 16), W2 (2 x 64), zero biases (numpy RNG, seeded)."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0, np.sqrt(2.0 / 11), (N_HID, N_FEAT))  # 11 non-zero inputs
+    W2 = rng.normal(0, np.sqrt(2.0 / N_HID), (2, N_HID))
+    return W1, np.zeros(N_HID), W2, np.zeros(2)

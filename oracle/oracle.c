@@ -441,3 +441,224 @@ long long oc_bruteforce(const oc_clip *c, const oc_params *p, int O, int u, int 
     }
     return cnt;
 }
+
+/* ================================================================== learned per-sample weights
+ *
+ * Samples (the capped set): the first n <= 64 accepted samples of S(p) in canonical order --
+ * frames J = O, O-1, O+1, O-2, O+2, ... (the earlier frame first on ties), then the k x k window
+ * in raster order.  Features of a sample s gathered from pixel q of frame J (16 per sample):
+ *   [c_s (3), c_s - c_ref (3), |X_q - x_ref| / r, (J - O) / max(T, 1), (d_q - z'_J) / r,
+ *    log w_denoise(s) (Eq. 4, natural log), 1, 0 x 5]
+ * with z'_J the depth of the reference point in camera J.  Network: h = ReLU(W1 f + b1) (64),
+ * (z_w, z_c) = W2 h + b2; w_s = softplus(z_w); conf = mean_s sigmoid(z_c);
+ * learned output = sum w_s c_s / sum w_s; final output = learned if conf >= tau else the plain
+ * Eq. 4 result.  With round_bf16 = 1 the features and W1, W2 are rounded to BF16 (the tensor-core
+ * input precision) and b1, b2 to FP32 before use, as on the GPU.
+ */
+#define OC_MAXS 64
+#define OC_NF 16
+#define OC_NH 64
+
+static double bf16_round(double x) {
+    float f = (float)x;
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    if ((b & 0x7f800000u) != 0x7f800000u) {
+        b += 0x7fffu + ((b >> 16) & 1u);
+        b &= 0xffff0000u;
+    }
+    memcpy(&f, &b, 4);
+    return (double)f;
+}
+
+/* Capped sample set, features and colours of pixel (u, v) of frame O; *n receives the count.
+ * plain receives the Eq. 4 output over the whole S(p).  Returns 0, or -1 for an invalid
+ * reference depth (then n = 0 and plain = c_ref). */
+int oc_learned_samples(const oc_clip *c, const oc_params *p, int O, int u, int v, double *feat, double *col,
+                       int *n, double *plain) {
+    const int W = c->W, H = c->H, F = c->F, k = p->k, h = (k - 1) / 2;
+    double sumw;
+    int64_t nacc, nexam;
+    double Pt[12], Gt[12];
+    *n = 0;
+    memset(feat, 0, sizeof(double) * OC_MAXS * OC_NF);
+    memset(col, 0, sizeof(double) * OC_MAXS * 3);
+    /* the plain result over all of S(p) */
+    {
+        int ns = 2 * p->T + 1;
+        double *PP = (double *)malloc(sizeof(double) * 12 * ns), *GG = (double *)malloc(sizeof(double) * 12 * ns);
+        for (int j = 0; j < ns; ++j) {
+            int J = O - p->T + j;
+            if (J < 0 || J >= F) continue;
+            oc_compose(c->K + 9 * O, c->w2c + 12 * O, c->K + 9 * J, c->w2c + 12 * J, J == O, PP + 12 * j, GG + 12 * j);
+        }
+        oc_params pd = *p;
+        pd.mode = 0;
+        pixel(c, &pd, O, u, v, PP, GG, plain, &sumw, &nacc, &nexam, NULL, 0);
+        free(PP);
+        free(GG);
+    }
+    size_t pix = ((size_t)O * H + v) * W + u;
+    float dref_f = c->depth[pix];
+    if (!valid_depth(dref_f)) return -1;
+    double dref = dref_f, cref[3] = {c->rgb[3 * pix], c->rgb[3 * pix + 1], c->rgb[3 * pix + 2]};
+    double KOi[9], ray[3], xref[3], uv1[3] = {u, v, 1.0};
+    mat3_inverse(c->K + 9 * O, KOi);
+    mat3_vec(KOi, uv1, ray);
+    for (int i = 0; i < 3; ++i) xref[i] = dref * ray[i];
+    const double r = p->radius, Tn = p->T > 0 ? p->T : 1;
+    for (int t = 0; t <= 2 * p->T && *n < OC_MAXS; ++t) {
+        /* canonical frame order: O, O-1, O+1, O-2, O+2, ... */
+        int J = O + (t == 0 ? 0 : ((t & 1) ? -(t + 1) / 2 : t / 2));
+        if (J < 0 || J >= F) continue;
+        oc_compose(c->K + 9 * O, c->w2c + 12 * O, c->K + 9 * J, c->w2c + 12 * J, J == O, Pt, Gt);
+        double xp[3];
+        apply34(Pt, xref, xp);
+        if (xp[2] <= 1e-6 * dref) continue;
+        double up = xp[0] / xp[2], vp = xp[1] / xp[2];
+        double cxd = floor(up + 0.5), cyd = floor(vp + 0.5);
+        if (cxd < -(double)(4 * k + 8) || cxd > (double)(W + 4 * k + 8) || cyd < -(double)(4 * k + 8) ||
+            cyd > (double)(H + 4 * k + 8))
+            continue;
+        const double zJ = xp[2];
+        for (int dy = -h; dy <= h && *n < OC_MAXS; ++dy) {
+            for (int dx = -h; dx <= h && *n < OC_MAXS; ++dx) {
+                int qx = (int)cxd + dx, qy = (int)cyd + dy;
+                if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+                size_t qi = ((size_t)J * H + qy) * W + qx;
+                float dq = c->depth[qi];
+                if (!valid_depth(dq)) continue;
+                double q3[3] = {qx * (double)dq, qy * (double)dq, (double)dq}, X[3];
+                apply34(Gt, q3, X);
+                double d2 = (X[0] - xref[0]) * (X[0] - xref[0]) + (X[1] - xref[1]) * (X[1] - xref[1]) +
+                            (X[2] - xref[2]) * (X[2] - xref[2]);
+                if (!(d2 < r * r)) continue;
+                double *f = feat + (size_t)*n * OC_NF, cs[3] = {c->rgb[3 * qi], c->rgb[3 * qi + 1], c->rgb[3 * qi + 2]};
+                double s[7] = {cs[0], cs[1], cs[2], X[0], X[1], X[2], J};
+                double sr[7] = {cref[0], cref[1], cref[2], xref[0], xref[1], xref[2], O};
+                for (int i = 0; i < 3; ++i) { f[i] = cs[i]; f[3 + i] = cs[i] - cref[i]; col[3 * *n + i] = cs[i]; }
+                f[6] = sqrt(d2) / r;
+                f[7] = (J - O) / Tn;
+                f[8] = ((double)dq - zJ) / r;
+                f[9] = log(oc_weight_denoise(s, sr, p->sigma_rgb, p->sigma_xyz, p->sigma_f));
+                f[10] = 1.0;
+                ++*n;
+            }
+        }
+    }
+    return 0;
+}
+
+static double softplus(double z) { return z > 0 ? z + log1p(exp(-z)) : log1p(exp(z)); }
+static double sigm(double z) { return z >= 0 ? 1.0 / (1.0 + exp(-z)) : exp(z) / (1.0 + exp(z)); }
+
+/* Forward pass of one pixel: z (n x 2) and h (n x 64) may be NULL.  Returns conf. */
+double oc_mlp_pixel(const double *feat, const double *col, int n, const double *W1, const double *b1,
+                    const double *W2, const double *b2, int round_bf16, double tau, const double *plain,
+                    double *out_learned, double *out_final, double *z, double *hid) {
+    double acc[3] = {0, 0, 0}, Wsum = 0.0, csum = 0.0;
+    for (int s = 0; s < n; ++s) {
+        double f[OC_NF], hh[OC_NH], zz[2];
+        for (int i = 0; i < OC_NF; ++i) f[i] = round_bf16 ? bf16_round(feat[s * OC_NF + i]) : feat[s * OC_NF + i];
+        for (int j = 0; j < OC_NH; ++j) {
+            double a = round_bf16 ? (double)(float)b1[j] : b1[j];
+            for (int i = 0; i < OC_NF; ++i) a += (round_bf16 ? bf16_round(W1[j * OC_NF + i]) : W1[j * OC_NF + i]) * f[i];
+            hh[j] = a > 0 ? a : 0.0;
+        }
+        for (int o = 0; o < 2; ++o) {
+            double a = round_bf16 ? (double)(float)b2[o] : b2[o];
+            for (int j = 0; j < OC_NH; ++j) a += (round_bf16 ? bf16_round(W2[o * OC_NH + j]) : W2[o * OC_NH + j]) * hh[j];
+            zz[o] = a;
+        }
+        if (z) { z[2 * s] = zz[0]; z[2 * s + 1] = zz[1]; }
+        if (hid) memcpy(hid + (size_t)s * OC_NH, hh, sizeof(hh));
+        double w = softplus(zz[0]);
+        for (int ch = 0; ch < 3; ++ch) acc[ch] += w * col[3 * s + ch];
+        Wsum += w;
+        csum += sigm(zz[1]);
+    }
+    double conf = n > 0 ? csum / n : 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+        out_learned[ch] = Wsum > 0 ? acc[ch] / Wsum : plain[ch];
+        out_final[ch] = (n > 0 && conf >= tau) ? out_learned[ch] : plain[ch];
+    }
+    return conf;
+}
+
+/*
+ * Training loss and gradients over n_px pixels (feature blocks of 64 x 16, colours 64 x 3):
+ *   L = (1/n_px) sum_p [ mean_c (o_p - y_p)^2 + bce_w BCE(clamp(conf_p), t_p) ],
+ *   t_p = 1 if mean_c (o_p - y_p)^2 <= mean_c (plain_p - y_p)^2 else 0 (a constant target),
+ * o_p the learned output, conf clamped to [1e-6, 1 - 1e-6].  Gradients (same layout as the
+ * weights) are overwritten.  Returns L.
+ */
+double oc_mlp_loss_grad(int n_px, const double *feat, const double *col, const int *nsamp, const double *plain,
+                        const double *clean, const double *W1, const double *b1, const double *W2, const double *b2,
+                        int round_bf16, double bce_w, double *gW1, double *gb1, double *gW2, double *gb2) {
+    memset(gW1, 0, sizeof(double) * OC_NH * OC_NF);
+    memset(gb1, 0, sizeof(double) * OC_NH);
+    memset(gW2, 0, sizeof(double) * 2 * OC_NH);
+    memset(gb2, 0, sizeof(double) * 2);
+    double L = 0.0;
+    double *z = (double *)malloc(sizeof(double) * OC_MAXS * 2), *hid = (double *)malloc(sizeof(double) * OC_MAXS * OC_NH);
+    for (int p = 0; p < n_px; ++p) {
+        const double *f = feat + (size_t)p * OC_MAXS * OC_NF, *cl = col + (size_t)p * OC_MAXS * 3, *y = clean + 3 * p;
+        int n = nsamp[p];
+        if (n <= 0) continue;
+        double ol[3], of[3];
+        double conf = oc_mlp_pixel(f, cl, n, W1, b1, W2, b2, round_bf16, 0.5, plain + 3 * p, ol, of, z, hid);
+        double el = 0, ep = 0;
+        for (int ch = 0; ch < 3; ++ch) {
+            el += (ol[ch] - y[ch]) * (ol[ch] - y[ch]) / 3.0;
+            ep += (plain[3 * p + ch] - y[ch]) * (plain[3 * p + ch] - y[ch]) / 3.0;
+        }
+        double t = el <= ep ? 1.0 : 0.0;
+        double cc = conf < 1e-6 ? 1e-6 : (conf > 1 - 1e-6 ? 1 - 1e-6 : conf);
+        L += el - bce_w * (t * log(cc) + (1 - t) * log(1 - cc));
+        /* d/d o_c and d/d conf (the clamp passes the gradient through only inside the interval) */
+        double dO[3], Wsum = 0.0;
+        for (int ch = 0; ch < 3; ++ch) dO[ch] = 2.0 * (ol[ch] - y[ch]) / 3.0;
+        double dconf = (conf > 1e-6 && conf < 1 - 1e-6) ? bce_w * (cc - t) / (cc * (1 - cc)) : 0.0;
+        for (int s = 0; s < n; ++s) Wsum += softplus(z[2 * s]);
+        for (int s = 0; s < n; ++s) {
+            double dw = 0.0;
+            for (int ch = 0; ch < 3; ++ch) dw += dO[ch] * (cl[3 * s + ch] - ol[ch]) / Wsum;
+            double dz[2] = {dw * sigm(z[2 * s]), dconf * sigm(z[2 * s + 1]) * (1 - sigm(z[2 * s + 1])) / n};
+            const double *hh = hid + (size_t)s * OC_NH;
+            double fr[OC_NF];
+            for (int i = 0; i < OC_NF; ++i) fr[i] = round_bf16 ? bf16_round(f[s * OC_NF + i]) : f[s * OC_NF + i];
+            for (int o = 0; o < 2; ++o) {
+                gb2[o] += dz[o];
+                for (int j = 0; j < OC_NH; ++j) gW2[o * OC_NH + j] += dz[o] * hh[j];
+            }
+            for (int j = 0; j < OC_NH; ++j) {
+                if (hh[j] <= 0.0) continue;
+                double w20 = round_bf16 ? bf16_round(W2[j]) : W2[j], w21 = round_bf16 ? bf16_round(W2[OC_NH + j]) : W2[OC_NH + j];
+                double dh = dz[0] * w20 + dz[1] * w21;
+                gb1[j] += dh;
+                for (int i = 0; i < OC_NF; ++i) gW1[j * OC_NF + i] += dh * fr[i];
+            }
+        }
+    }
+    free(z);
+    free(hid);
+    double inv = n_px > 0 ? 1.0 / n_px : 0.0;
+    for (int i = 0; i < OC_NH * OC_NF; ++i) gW1[i] *= inv;
+    for (int i = 0; i < OC_NH; ++i) gb1[i] *= inv;
+    for (int i = 0; i < 2 * OC_NH; ++i) gW2[i] *= inv;
+    for (int i = 0; i < 2; ++i) gb2[i] *= inv;
+    return L * inv;
+}
+
+/* oc_learned_samples over a crop (row-major): feat cw*ch*64*16, col cw*ch*64*3, nsamp, plain cw*ch*3 */
+void oc_learned_crop(const oc_clip *c, const oc_params *p, int O, int x0, int y0, int cw, int ch, double *feat,
+                     double *col, int32_t *nsamp, double *plain) {
+    long long n = (long long)cw * ch;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (long long i = 0; i < n; ++i) {
+        int cnt = 0;
+        oc_learned_samples(c, p, O, x0 + (int)(i % cw), y0 + (int)(i / cw), feat + i * OC_MAXS * OC_NF,
+                           col + i * OC_MAXS * 3, &cnt, plain + 3 * i);
+        nsamp[i] = cnt;
+    }
+}
