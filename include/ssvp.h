@@ -208,6 +208,58 @@ int ssvp_plan_get_config(const ssvp_plan *plan, ssvp_plan_config *config, long l
 /* Free a plan (waits for its launches).  NULL is a no-op.  Destroy plans before their context. */
 void ssvp_plan_destroy(ssvp_plan *plan);
 
+/*
+ * Learned per-sample weights (SSVP_MODE_LEARNED).  Per output pixel the first n <= 64 gathered
+ * samples in canonical order (frames O, O-1, O+1, ..., then window raster order) get 16 features
+ * [colour (3), colour - reference (3), distance / r, (J - O) / T, depth residual in the sample's
+ * frame / r, log of the Eq. 4 weight, 1, 0 x 5] (BF16); a 16 -> 64 -> 2 MLP (BF16 tensor cores,
+ * FP32 accumulation) gives per-sample weights softplus(z_w) and a confidence mean sigmoid(z_c);
+ * the output is the weighted mean of the samples' colours when the confidence is at least
+ * params.conf_threshold, else the plain Eq. 3/4 result.
+ */
+
+/* Set the network (FP32 host arrays: W1 64x16 hidden x feature row-major, b1 64, W2 2x64, b2 2).
+ * W1 and W2 are used rounded to BF16, b1 and b2 in FP32.  Resets the training state. */
+int ssvp_set_mlp(ssvp_ctx *ctx, const float *W1, const float *b1, const float *W2, const float *b2);
+
+/* Copy the current FP32 weights to the host (waits). */
+int ssvp_get_mlp(ssvp_ctx *ctx, float *W1, float *b1, float *W2, float *b2);
+
+/* Capped sample sets of one output frame's crop (params.frame_begin; crop_* as for gather) written
+ * to caller device buffers: feat (crop pixels x 64 x 16 BF16 bits), col (x 64 x 3 floats), nsamp
+ * (int32 per pixel) and plain (3 floats per pixel, the Eq. 3/4 result).  Slots beyond nsamp are
+ * left as they were. */
+int ssvp_learned_samples(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, unsigned short *feat, float *col,
+                         int32_t *nsamp, float *plain);
+
+typedef struct ssvp_train_config {
+    int32_t steps;         /* optimiser steps */
+    int32_t batch_pixels;  /* pixels per step, drawn uniformly from one frame of one clip */
+    float lr;              /* Adam learning rate */
+    float bce_weight;      /* weight of the confidence BCE term */
+    uint64_t seed;         /* frame/pixel draws and the He initialisation */
+    int32_t init;          /* 1: He-initialise from seed first, 0: continue from the current weights */
+    int32_t pad_;
+} ssvp_train_config;
+
+/*
+ * Train the network on the GPU (forward, loss, backward on the tensor cores; Adam on FP32 master
+ * weights).  Each step draws a clip and an output frame, extracts that frame's capped sample sets
+ * with params (mode is ignored; the gather and the plain fallback use params' k, T, radius and
+ * sigmas), draws batch_pixels pixels, and minimises mean (learned - clean)^2 + bce_weight *
+ * BCE(confidence, [learned error <= plain error]).  clean[i] is a device pointer to clip i's
+ * target frames (F x H x W x 3 floats).  loss_out (host, steps floats, may be NULL) receives the
+ * per-step batch losses (waits).
+ */
+int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, const float *const *clean, int n_clips,
+               const ssvp_train_config *cfg, float *loss_out);
+
+/* Loss and gradient at the current weights over listed pixels (crop-of-full-frame indices
+ * y * W + x) of output frame params.frame_begin of a clip; grad_out (host) receives the flat
+ * gradient W1 | b1 | W2 | b2 followed by the loss (1219 floats).  Waits. */
+int ssvp_mlp_grad(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, const int32_t *pixels, int n_pixels,
+                  const float *clean, float *grad_out);
+
 /* Lower-median valid input depth of a loaded clip (waits for the load). */
 int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median);
 

@@ -43,6 +43,12 @@ class ssvp_plan_config(ctypes.Structure):
     _fields_ = [("tile_rows", ctypes.c_int32), ("frame_chunk", ctypes.c_int32)]
 
 
+class ssvp_train_config(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch_pixels", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("bce_weight", ctypes.c_float), ("seed", ctypes.c_uint64), ("init", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_2102_03011_gb300._build.build()")
@@ -73,6 +79,12 @@ def _load():
         "ssvp_plan_get_config": (i, [vp, ctypes.POINTER(ssvp_plan_config), ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_int)]),
         "ssvp_plan_destroy": (None, [vp]),
+        "ssvp_set_mlp": (i, [vp, vp, vp, vp, vp]),
+        "ssvp_get_mlp": (i, [vp, vp, vp, vp, vp]),
+        "ssvp_learned_samples": (i, [vp, P, i, vp, vp, vp, vp]),
+        "ssvp_train": (i, [vp, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp), i,
+                           ctypes.POINTER(ssvp_train_config), vp]),
+        "ssvp_mlp_grad": (i, [vp, P, i, vp, i, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -235,3 +247,50 @@ def ssvp_plan_get_config(plan: Plan):
 def ssvp_plan_destroy(plan: Plan) -> None:
     lib.ssvp_plan_destroy(plan.handle)
     plan.handle = None
+
+
+def _f32(a, shape):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {shape}, got {a.shape}")
+    return a
+
+
+def ssvp_set_mlp(ctx, W1, b1, W2, b2) -> None:
+    arrs = [_f32(W1, (64, 16)), _f32(b1, (64,)), _f32(W2, (2, 64)), _f32(b2, (2,))]
+    _check(ctx, lib.ssvp_set_mlp(ctx, *[a.ctypes.data for a in arrs]))
+
+
+def ssvp_get_mlp(ctx):
+    """-> (W1 (64, 16), b1 (64,), W2 (2, 64), b2 (2,)) float32"""
+    import numpy as np
+    out = [np.zeros((64, 16), np.float32), np.zeros(64, np.float32), np.zeros((2, 64), np.float32), np.zeros(2, np.float32)]
+    _check(ctx, lib.ssvp_get_mlp(ctx, *[a.ctypes.data for a in out]))
+    return tuple(out)
+
+
+def ssvp_learned_samples(ctx, params: ssvp_params, clip_id: int, feat, col, nsamp, plain) -> None:
+    _check(ctx, lib.ssvp_learned_samples(ctx, ctypes.byref(params), clip_id, _ptr(feat)[0], _ptr(col)[0],
+                                         _ptr(nsamp)[0], _ptr(plain)[0]))
+
+
+def ssvp_train(ctx, params: ssvp_params, clip_ids, clean, cfg: ssvp_train_config):
+    """clean: device tensors (F, H, W, 3) float32, one per clip -> per-step losses (numpy)."""
+    import numpy as np
+    ids = (ctypes.c_int * len(clip_ids))(*[int(c) for c in clip_ids])
+    ptrs = (ctypes.c_void_p * len(clean))(*[_ptr(c)[0] for c in clean])
+    losses = np.zeros(max(cfg.steps, 1), np.float32)
+    _check(ctx, lib.ssvp_train(ctx, ctypes.byref(params), ids, ptrs, len(clip_ids), ctypes.byref(cfg),
+                               losses.ctypes.data))
+    return losses[:cfg.steps]
+
+
+def ssvp_mlp_grad(ctx, params: ssvp_params, clip_id: int, pixels, clean):
+    """Flat gradient W1 | b1 | W2 | b2 and the loss (1219 floats) at the current weights."""
+    import numpy as np
+    px = np.ascontiguousarray(pixels, dtype=np.int32)
+    g = np.zeros(1219, np.float32)
+    _check(ctx, lib.ssvp_mlp_grad(ctx, ctypes.byref(params), clip_id, px.ctypes.data, len(px), _ptr(clean)[0],
+                                  g.ctypes.data))
+    return g

@@ -47,6 +47,16 @@ struct ssvp_ctx {
     size_t staging_bytes = 0;
     std::vector<PairGeom> host_geom;
     unsigned clip_generation[SSVP_MAX_CLIPS] = {};
+    // learned filter: weights and training state, scratch of one frame's capped sample sets
+    ssvp::MlpState mlp{};
+    float *mlp_buf = nullptr;        // master | m | v | grad (+ loss) | W2_r
+    unsigned short *mlp_w1 = nullptr;
+    bool mlp_set = false;
+    int mlp_step = 0;
+    unsigned short *l_feat = nullptr;
+    float *l_col = nullptr, *l_plain = nullptr, *l_loss = nullptr;
+    int32_t *l_n = nullptr, *l_batch = nullptr;
+    size_t l_cap = 0, l_batch_cap = 0, l_loss_cap = 0;
     // tuned batch shapes: key (k, half window, mode, colour format) -> config
     struct Tuned {
         int k, T, mode, cfmt;
@@ -181,8 +191,11 @@ void compose_table(const Clip &c, int fb, int n_out, int T, double sigma_f, Pair
 
 int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
     if (!p) return fail(ctx, SSVP_EINVAL, "params is NULL");
-    if (p->mode != SSVP_MODE_DENOISE && p->mode != SSVP_MODE_MEAN && p->mode != SSVP_MODE_APERTURE)
+    if (p->mode != SSVP_MODE_DENOISE && p->mode != SSVP_MODE_MEAN && p->mode != SSVP_MODE_APERTURE &&
+        p->mode != SSVP_MODE_LEARNED)
         return fail(ctx, SSVP_EINVAL, "mode %d is not available in this build", p->mode);
+    if (p->mode == SSVP_MODE_LEARNED && !(std::isfinite(p->conf_threshold)))
+        return fail(ctx, SSVP_EINVAL, "conf_threshold must be finite");
     if (p->mode == SSVP_MODE_APERTURE) {
         if (p->cap < 1 || p->cap > 63 || (p->cap & 1) == 0) return fail(ctx, SSVP_EINVAL, "cap=%d must be odd in [1, 63]", p->cap);
         if (p->lens_samples < 1 || p->lens_samples > 64)
@@ -296,6 +309,103 @@ const ssvp_plan_config *find_tuned(const ssvp_ctx *ctx, const ssvp_params &p, in
     return nullptr;
 }
 
+
+// ---------------------------------------------------------------- learned filter (A8/A9)
+
+int mlp_alloc(ssvp_ctx *ctx) {
+    if (ctx->mlp_buf) return SSVP_OK;
+    const size_t nf = 4 * (size_t)ssvp::kMlpParams + 1 + 128;
+    CK(cudaMalloc(&ctx->mlp_buf, nf * sizeof(float)), "cudaMalloc (mlp)");
+    CK(cudaMalloc(&ctx->mlp_w1, 1024 * sizeof(unsigned short)), "cudaMalloc (mlp)");
+    ssvp::MlpState &st = ctx->mlp;
+    st.master = ctx->mlp_buf;
+    st.m = st.master + ssvp::kMlpParams;
+    st.v = st.m + ssvp::kMlpParams;
+    st.grad = st.v + ssvp::kMlpParams;
+    st.W2_r = st.grad + ssvp::kMlpParams + 1;
+    st.W1_bf16 = ctx->mlp_w1;
+    return SSVP_OK;
+}
+
+ssvp::MlpWeights mlp_weights(const ssvp_ctx *ctx) {
+    ssvp::MlpWeights w;
+    w.W1 = ctx->mlp.W1_bf16;
+    w.b1 = ctx->mlp.master + ssvp::kMlpB1;
+    w.W2 = ctx->mlp.W2_r;
+    w.b2 = ctx->mlp.master + ssvp::kMlpB2;
+    return w;
+}
+
+// scratch for the capped sample sets of n_px crop pixels
+int learned_scratch(ssvp_ctx *ctx, size_t n_px) {
+    if (n_px <= ctx->l_cap) return SSVP_OK;
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    for (void *q : {(void *)ctx->l_feat, (void *)ctx->l_col, (void *)ctx->l_plain, (void *)ctx->l_n})
+        if (q) cudaFree(q);
+    ctx->l_feat = nullptr; ctx->l_col = nullptr; ctx->l_plain = nullptr; ctx->l_n = nullptr;
+    ctx->l_cap = 0;
+    CK(cudaMalloc(&ctx->l_feat, n_px * 64 * 16 * sizeof(unsigned short)), "cudaMalloc (learned scratch)");
+    CK(cudaMalloc(&ctx->l_col, n_px * 64 * 3 * sizeof(float)), "cudaMalloc (learned scratch)");
+    CK(cudaMalloc(&ctx->l_plain, n_px * 3 * sizeof(float)), "cudaMalloc (learned scratch)");
+    CK(cudaMalloc(&ctx->l_n, n_px * sizeof(int32_t)), "cudaMalloc (learned scratch)");
+    ctx->l_cap = n_px;
+    return SSVP_OK;
+}
+
+// capped sample sets of output frame O of a clip over a crop, into the given buffers
+int extract_samples(ssvp_ctx *ctx, const ssvp_params &p, int clip_id, int O, int x0, int y0, int cw, int ch,
+                    unsigned short *feat, float *col, int32_t *nsamp, float *plain) {
+    Clip &c = ctx->clips[clip_id];
+    const int T = p.half_window, ns = 2 * T + 1;
+    if ((size_t)ns > ctx->geom_cap) {
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        if (ctx->geom) cudaFree(ctx->geom);
+        ctx->geom = nullptr;
+        ctx->geom_cap = 0;
+        CK(cudaMalloc(&ctx->geom, std::max<size_t>(ns, 4096) * sizeof(PairGeom)), "cudaMalloc (geometry)");
+        ctx->geom_cap = std::max<size_t>(ns, 4096);
+    }
+    ctx->host_geom.resize(ns);
+    compose_table(c, O, 1, T, p.sigma_f, ctx->host_geom.data());
+    CK(cudaMemcpyAsync(ctx->geom, ctx->host_geom.data(), ns * sizeof(PairGeom), cudaMemcpyHostToDevice, ctx->stream),
+       "cudaMemcpyAsync (geometry)");
+    GatherArgs a{};
+    a.clip = c.p;
+    a.geom = ctx->geom;
+    a.frame_begin = O;
+    a.n_out = 1;
+    a.n_slots = ns;
+    a.T = T;
+    a.x0 = x0; a.y0 = y0; a.cw = cw; a.ch = ch;
+    a.k = p.k;
+    a.mode = SSVP_MODE_DENOISE;
+    a.radius = p.radius;
+    a.sigma_rgb = p.sigma_rgb;
+    a.sigma_xyz = p.sigma_xyz;
+    a.sigma_f = p.sigma_f;
+    a.feat_out = feat;
+    a.col_out = col;
+    a.nsamp_out = nsamp;
+    a.plain_out = plain;
+    a.stat_counts = ctx->stat_counts;
+    a.stat_sumw = ctx->stat_sumw;
+    CK(ssvp::launch_gather(a, ctx->stream), "gather kernel (learned samples)");
+    return SSVP_OK;
+}
+
+// splitmix64 draws for training (frame and pixel sampling, He initialisation)
+struct Rng {
+    uint64_t s;
+    uint64_t next() {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return ((double)(next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+    double normal() { return std::sqrt(-2.0 * std::log(uniform())) * std::cos(6.283185307179586 * uniform()); }
+};
+
 }  // namespace
 
 namespace ssvp {
@@ -368,6 +478,9 @@ void ssvp_destroy(ssvp_ctx *ctx) {
     if (ctx->median_scratch) cudaFree(ctx->median_scratch);
     if (ctx->geom) cudaFree(ctx->geom);
     if (ctx->staging) cudaFree(ctx->staging);
+    for (void *q : {(void *)ctx->mlp_buf, (void *)ctx->mlp_w1, (void *)ctx->l_feat, (void *)ctx->l_col,
+                    (void *)ctx->l_plain, (void *)ctx->l_loss, (void *)ctx->l_n, (void *)ctx->l_batch})
+        if (q) cudaFree(q);
     delete ctx;
 }
 
@@ -523,6 +636,34 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
     if ((p.membership_out || p.pixel_stats_out) && (n_clips != 1 || nout[0] > 1))
         return fail(ctx, SSVP_EINVAL, "debug outputs need exactly one clip and at most one output frame");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (p.mode == SSVP_MODE_LEARNED) {
+        // per output frame: capped sample sets into scratch, then the tensor-core MLP
+        if (!ctx->mlp_set) return fail(ctx, SSVP_EINVAL, "learned mode needs a network (ssvp_set_mlp or ssvp_train)");
+        if (p.k > 7) return fail(ctx, SSVP_EINVAL, "the learned filter supports k <= 7");
+        if (p.membership_out || p.pixel_stats_out) return fail(ctx, SSVP_EINVAL, "learned mode has no debug outputs");
+        CK(cudaMemsetAsync(ctx->stat_counts, 0, 2 * sizeof(unsigned long long), ctx->stream), "cudaMemsetAsync");
+        CK(cudaMemsetAsync(ctx->stat_sumw, 0, sizeof(double), ctx->stream), "cudaMemsetAsync");
+        for (int i = 0; i < n_clips; ++i) {
+            Clip &c = ctx->clips[clip_ids[i]];
+            const size_t npx = (size_t)cw[i] * chh[i];
+            if ((rc = learned_scratch(ctx, npx)) != SSVP_OK) return rc;
+            for (int oi = 0; oi < nout[i]; ++oi) {
+                const int O = fb[i] + oi;
+                if ((rc = extract_samples(ctx, p, clip_ids[i], O, cx0[i], cy0[i], cw[i], chh[i], ctx->l_feat, ctx->l_col,
+                                          ctx->l_n, ctx->l_plain)) != SSVP_OK)
+                    return rc;
+                ssvp::MlpArgs m{};
+                m.w = mlp_weights(ctx);
+                m.feat = ctx->l_feat; m.col = ctx->l_col; m.nsamp = ctx->l_n; m.plain = ctx->l_plain;
+                m.n_px = (long long)npx;
+                m.O = O; m.W = c.p.W; m.H = c.p.H; m.x0 = cx0[i]; m.y0 = cy0[i]; m.cw = cw[i];
+                m.tau = p.conf_threshold;
+                m.out = c.p.out;
+                CK(ssvp::launch_mlp_infer(m, ctx->stream), "mlp inference kernel");
+            }
+        }
+        return SSVP_OK;
+    }
     if (total > ctx->geom_cap) {
         CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
         if (ctx->geom) cudaFree(ctx->geom);
@@ -791,6 +932,191 @@ int ssvp_plan_get_config(const ssvp_plan *plan, ssvp_plan_config *config, long l
     if (config) *config = plan->cfg;
     if (n_items) *n_items = plan->n_items;
     if (grid) *grid = plan->grid;
+    return SSVP_OK;
+}
+
+int ssvp_set_mlp(ssvp_ctx *ctx, const float *W1, const float *b1, const float *W2, const float *b2) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (!W1 || !b1 || !W2 || !b2) return fail(ctx, SSVP_EINVAL, "weights must not be NULL");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = mlp_alloc(ctx);
+    if (rc != SSVP_OK) return rc;
+    std::vector<float> flat(ssvp::kMlpParams);
+    std::memcpy(flat.data(), W1, 1024 * sizeof(float));
+    std::memcpy(flat.data() + ssvp::kMlpB1, b1, 64 * sizeof(float));
+    std::memcpy(flat.data() + ssvp::kMlpW2, W2, 128 * sizeof(float));
+    std::memcpy(flat.data() + ssvp::kMlpB2, b2, 2 * sizeof(float));
+    for (float x : flat)
+        if (!std::isfinite(x)) return fail(ctx, SSVP_EINVAL, "weights must be finite");
+    CK(cudaMemcpy(ctx->mlp.master, flat.data(), flat.size() * sizeof(float), cudaMemcpyHostToDevice), "cudaMemcpy (mlp)");
+    CK(cudaMemsetAsync(ctx->mlp.m, 0, 2 * ssvp::kMlpParams * sizeof(float), ctx->stream), "cudaMemsetAsync");
+    CK(ssvp::launch_mlp_refresh(ctx->mlp, ctx->stream), "mlp refresh");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    ctx->mlp_set = true;
+    ctx->mlp_step = 0;
+    return SSVP_OK;
+}
+
+int ssvp_get_mlp(ssvp_ctx *ctx, float *W1, float *b1, float *W2, float *b2) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (!ctx->mlp_set) return fail(ctx, SSVP_EINVAL, "no network has been set or trained");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    std::vector<float> flat(ssvp::kMlpParams);
+    CK(cudaMemcpyAsync(flat.data(), ctx->mlp.master, flat.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
+       "cudaMemcpyAsync (mlp)");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    if (W1) std::memcpy(W1, flat.data(), 1024 * sizeof(float));
+    if (b1) std::memcpy(b1, flat.data() + ssvp::kMlpB1, 64 * sizeof(float));
+    if (W2) std::memcpy(W2, flat.data() + ssvp::kMlpW2, 128 * sizeof(float));
+    if (b2) std::memcpy(b2, flat.data() + ssvp::kMlpB2, 2 * sizeof(float));
+    return SSVP_OK;
+}
+
+int ssvp_learned_samples(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, unsigned short *feat, float *col,
+                         int32_t *nsamp, float *plain) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    int rc = check_params(ctx, params);
+    if (rc != SSVP_OK) return rc;
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    Clip &c = ctx->clips[clip_id];
+    if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_id);
+    if (!feat || !col || !nsamp || !plain) return fail(ctx, SSVP_EINVAL, "output buffers must not be NULL");
+    const ssvp_params &p = *params;
+    if (p.frame_begin < 0 || p.frame_begin >= c.p.F) return fail(ctx, SSVP_EINVAL, "frame %d outside the clip", p.frame_begin);
+    if (p.k > 7) return fail(ctx, SSVP_EINVAL, "the learned filter supports k <= 7");
+    int x0 = p.crop_x, y0 = p.crop_y, w = p.crop_w, h = p.crop_h;
+    if (w == 0 || h == 0) { x0 = 0; y0 = 0; w = c.p.W; h = c.p.H; }
+    if (x0 < 0 || y0 < 0 || x0 + w > c.p.W || y0 + h > c.p.H) return fail(ctx, SSVP_EINVAL, "crop outside the clip");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    return extract_samples(ctx, p, clip_id, p.frame_begin, x0, y0, w, h, feat, col, nsamp, plain);
+}
+
+int ssvp_mlp_grad(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, const int32_t *pixels, int n_pixels,
+                  const float *clean, float *grad_out) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    int rc = check_params(ctx, params);
+    if (rc != SSVP_OK) return rc;
+    if (!ctx->mlp_set) return fail(ctx, SSVP_EINVAL, "no network has been set or trained");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    Clip &c = ctx->clips[clip_id];
+    if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_id);
+    if (!pixels || n_pixels < 1 || !clean || !grad_out) return fail(ctx, SSVP_EINVAL, "bad pixel list or buffers");
+    if (params->k > 7) return fail(ctx, SSVP_EINVAL, "the learned filter supports k <= 7");
+    const int O = params->frame_begin;
+    if (O < 0 || O >= c.p.F) return fail(ctx, SSVP_EINVAL, "frame %d outside the clip", O);
+    const size_t npx = (size_t)c.p.W * c.p.H;
+    for (int i = 0; i < n_pixels; ++i)
+        if (pixels[i] < 0 || (size_t)pixels[i] >= npx) return fail(ctx, SSVP_EINVAL, "pixel index out of range");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((rc = learned_scratch(ctx, npx)) != SSVP_OK) return rc;
+    if ((size_t)n_pixels > ctx->l_batch_cap) {
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        if (ctx->l_batch) cudaFree(ctx->l_batch);
+        ctx->l_batch = nullptr;
+        CK(cudaMalloc(&ctx->l_batch, n_pixels * sizeof(int32_t)), "cudaMalloc (batch)");
+        ctx->l_batch_cap = n_pixels;
+    }
+    if ((rc = extract_samples(ctx, *params, clip_id, O, 0, 0, c.p.W, c.p.H, ctx->l_feat, ctx->l_col, ctx->l_n,
+                              ctx->l_plain)) != SSVP_OK)
+        return rc;
+    CK(cudaMemcpyAsync(ctx->l_batch, pixels, n_pixels * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream), "cudaMemcpyAsync");
+    CK(cudaMemsetAsync(ctx->mlp.grad, 0, (ssvp::kMlpParams + 1) * sizeof(float), ctx->stream), "cudaMemsetAsync");
+    ssvp::MlpArgs m{};
+    m.w = mlp_weights(ctx);
+    m.feat = ctx->l_feat; m.col = ctx->l_col; m.nsamp = ctx->l_n; m.plain = ctx->l_plain;
+    m.n_px = (long long)npx;
+    m.O = O; m.W = c.p.W; m.H = c.p.H; m.x0 = 0; m.y0 = 0; m.cw = c.p.W;
+    m.batch = ctx->l_batch;
+    m.n_batch = n_pixels;
+    m.clean = clean;
+    m.bce_w = 0.1f;
+    m.grad = ctx->mlp.grad;
+    CK(ssvp::launch_mlp_train(m, ctx->stream), "mlp train kernel");
+    CK(cudaMemcpyAsync(grad_out, ctx->mlp.grad, (ssvp::kMlpParams + 1) * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
+       "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    return SSVP_OK;
+}
+
+int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, const float *const *clean, int n_clips,
+               const ssvp_train_config *cfg, float *loss_out) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    int rc = check_params(ctx, params);
+    if (rc != SSVP_OK) return rc;
+    if (!cfg || cfg->steps < 0 || cfg->batch_pixels < 1 || !(cfg->lr > 0.0f) || !(cfg->bce_weight >= 0.0f))
+        return fail(ctx, SSVP_EINVAL, "bad training configuration");
+    if (!clip_ids || !clean || n_clips < 1) return fail(ctx, SSVP_EINVAL, "bad clip list");
+    if (params->k > 7) return fail(ctx, SSVP_EINVAL, "the learned filter supports k <= 7");
+    size_t max_px = 0;
+    for (int i = 0; i < n_clips; ++i) {
+        if (clip_ids[i] < 0 || clip_ids[i] >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id out of range");
+        const Clip &c = ctx->clips[clip_ids[i]];
+        if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_ids[i]);
+        if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_ids[i]);
+        if (!clean[i]) return fail(ctx, SSVP_EINVAL, "clean target of clip %d is NULL", clip_ids[i]);
+        max_px = std::max(max_px, (size_t)c.p.W * c.p.H);
+    }
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((rc = mlp_alloc(ctx)) != SSVP_OK) return rc;
+    Rng rng{cfg->seed};
+    if (cfg->init || !ctx->mlp_set) {
+        // He-normal W1 (11 non-zero inputs), W2; zero biases
+        std::vector<float> W1(1024), b1(64, 0.0f), W2(128), b2(2, 0.0f);
+        for (auto &x : W1) x = (float)(rng.normal() * std::sqrt(2.0 / 11.0));
+        for (auto &x : W2) x = (float)(rng.normal() * std::sqrt(2.0 / 64.0));
+        if ((rc = ssvp_set_mlp(ctx, W1.data(), b1.data(), W2.data(), b2.data())) != SSVP_OK) return rc;
+    }
+    if ((rc = learned_scratch(ctx, max_px)) != SSVP_OK) return rc;
+    const size_t nb = (size_t)cfg->batch_pixels;
+    if (nb > ctx->l_batch_cap) {
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        if (ctx->l_batch) cudaFree(ctx->l_batch);
+        ctx->l_batch = nullptr;
+        CK(cudaMalloc(&ctx->l_batch, nb * sizeof(int32_t)), "cudaMalloc (batch)");
+        ctx->l_batch_cap = nb;
+    }
+    if ((size_t)cfg->steps > ctx->l_loss_cap) {
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        if (ctx->l_loss) cudaFree(ctx->l_loss);
+        ctx->l_loss = nullptr;
+        CK(cudaMalloc(&ctx->l_loss, std::max(cfg->steps, 1) * sizeof(float)), "cudaMalloc (loss)");
+        ctx->l_loss_cap = std::max(cfg->steps, 1);
+    }
+    std::vector<int32_t> batch(nb);
+    for (int step = 0; step < cfg->steps; ++step) {
+        const int ci = (int)(rng.next() % (uint64_t)n_clips);
+        const Clip &c = ctx->clips[clip_ids[ci]];
+        const int O = (int)(rng.next() % (uint64_t)c.p.F);
+        const uint64_t npx = (uint64_t)c.p.W * c.p.H;
+        for (auto &b : batch) b = (int32_t)(rng.next() % npx);
+        if ((rc = extract_samples(ctx, *params, clip_ids[ci], O, 0, 0, c.p.W, c.p.H, ctx->l_feat, ctx->l_col, ctx->l_n,
+                                  ctx->l_plain)) != SSVP_OK)
+            return rc;
+        // pageable source: the copy is staged before the call returns, so batch may be rewritten
+        CK(cudaMemcpyAsync(ctx->l_batch, batch.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream),
+           "cudaMemcpyAsync");
+        CK(cudaMemsetAsync(ctx->mlp.grad, 0, (ssvp::kMlpParams + 1) * sizeof(float), ctx->stream), "cudaMemsetAsync");
+        ssvp::MlpArgs m{};
+        m.w = mlp_weights(ctx);
+        m.feat = ctx->l_feat; m.col = ctx->l_col; m.nsamp = ctx->l_n; m.plain = ctx->l_plain;
+        m.n_px = (long long)npx;
+        m.O = O; m.W = c.p.W; m.H = c.p.H; m.x0 = 0; m.y0 = 0; m.cw = c.p.W;
+        m.batch = ctx->l_batch;
+        m.n_batch = (long long)nb;
+        m.clean = clean[ci];
+        m.bce_w = cfg->bce_weight;
+        m.grad = ctx->mlp.grad;
+        CK(ssvp::launch_mlp_train(m, ctx->stream), "mlp train kernel");
+        CK(ssvp::launch_adam(ctx->mlp, cfg->lr, ++ctx->mlp_step, ctx->stream), "adam kernel");
+        CK(cudaMemcpyAsync(ctx->l_loss + step, ctx->mlp.grad + ssvp::kMlpParams, sizeof(float), cudaMemcpyDeviceToDevice,
+                           ctx->stream), "cudaMemcpyAsync");
+    }
+    if (loss_out && cfg->steps > 0)
+        CK(cudaMemcpyAsync(loss_out, ctx->l_loss, cfg->steps * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
+           "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     return SSVP_OK;
 }
 

@@ -17,6 +17,7 @@
 // Accepted candidates are recorded in a per-thread bit mask during the test loop and filtered
 // afterwards by iterating the set bits, so a warp pays for the filter arithmetic only as often
 // as its busiest lane accepts (warp-level compaction of the accepted samples).
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "ssvp_df.cuh"
@@ -43,7 +44,31 @@ constexpr int kTileX = 32, kTileY = SSVP_TILE_Y, kThreads = kTileX * kTileY;
 // return the pixel's accepted and examined counts and sum of weights (they start at 0).
 // K > 0: compile-time window width (k*k <= 64, one 64-bit accept mask per frame).
 // K == 0: runtime k up to 31, one 32-bit accept mask per window row.
-template <int K, int CFMT, bool DEBUG>
+constexpr int kMaxSamples = 64;  // learned filter: capped sample set
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Features of one accepted sample for the learned filter (16 BF16 values) and its colour.
+__device__ __forceinline__ void store_sample(const GatherArgs &a, long long crop_idx, int slot, float3 c, float er,
+                                             float eg, float eb, float dist_r, float dj_t, float dz_r, float logw) {
+    const float f[16] = {c.x, c.y, c.z, er, eg, eb, dist_r, dj_t, dz_r, logw, 1.0f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    unsigned int packed[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+        packed[i] = *reinterpret_cast<unsigned int *>(&b2);
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(a.feat_out + (crop_idx * kMaxSamples + slot) * 16);
+    dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+    float *cd = a.col_out + (crop_idx * kMaxSamples + slot) * 3;
+    cd[0] = c.x;
+    cd[1] = c.y;
+    cd[2] = c.z;
+}
+
+// LEARN: visit the frames in canonical order (O, O-1, O+1, ...) and store the features of the
+// first kMaxSamples accepted samples (learned filter); the Eq. 3/4 result goes to a.plain_out.
+template <int K, int CFMT, bool DEBUG, bool LEARN = false>
 __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &P, const int O, const int u0,
                                              const int v0, const int u, const int v, const bool active,
                                              const long long crop_idx, const float4 *sgeom, const int n_slots,
@@ -53,6 +78,9 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
     const int h = (k - 1) >> 1;
     const int rec_words = 3 + (k * k + 31) / 32;
     float acc_r = 0.0f, acc_g = 0.0f, acc_b = 0.0f;
+    int n_feat = 0;
+    const int Tw = (n_slots - 1) >> 1;
+    const float inv_r = LEARN ? rsqrtf(r2) : 0.0f, inv_T = LEARN ? 1.0f / (float)max(Tw, 1) : 0.0f;
     float3 cref = make_float3(0.f, 0.f, 0.f);
     float dref = 0.0f;
     if (active) {
@@ -67,7 +95,9 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
 
     if (gather) {
         const float du = (float)(u - u0), dv = (float)(v - v0);
-        for (int j = 0; j < n_slots; ++j) {
+        for (int jj = 0; jj < n_slots; ++jj) {
+            // canonical order for the learned filter: O, O-1, O+1, O-2, O+2, ...
+            const int j = LEARN ? Tw + (jj == 0 ? 0 : ((jj & 1) ? -((jj + 1) >> 1) : (jj >> 1))) : jj;
             const float4 *g = sgeom + kSlotVec * j;
             const float4 q5 = g[5];
             const int J = __float_as_int(q5.w);
@@ -174,8 +204,14 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                         const float Y = fmaf(dz, __fmaf_rn(dyf, ify, Ay0), __fmaf_rn(dyf, ziy, By0));
                         const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
                         const float er = cq[t].x - cref.x, eg = cq[t].y - cref.y, eb = cq[t].z - cref.z;
+                        const float e = fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta));
                         float w = 1.0f;
-                        if (weighted) w = ex2(-fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta)));
+                        if (weighted) w = ex2(-e);
+                        if (LEARN && ok[t] && n_feat < kMaxSamples) {
+                            store_sample(a, crop_idx, n_feat, cq[t], er, eg, eb, sqrtf(d2) * inv_r,
+                                         (float)(j - Tw) * inv_T, dz * inv_r, -e * kLn2);
+                            ++n_feat;
+                        }
                         if (ok[t]) {
                             acc_r = fmaf(w, er, acc_r);
                             acc_g = fmaf(w, eg, acc_g);
@@ -216,8 +252,14 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                         const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
                         const float3 c = load_colour<CFMT>(P.colour, wbase + off);
                         const float er = c.x - cref.x, eg = c.y - cref.y, eb = c.z - cref.z;
+                        const float e = fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta));
                         float w = 1.0f;
-                        if (weighted) w = ex2(-fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta)));
+                        if (weighted) w = ex2(-e);
+                        if (LEARN && n_feat < kMaxSamples) {
+                            store_sample(a, crop_idx, n_feat, c, er, eg, eb, sqrtf(d2) * inv_r, (float)(j - Tw) * inv_T,
+                                         dz * inv_r, -e * kLn2);
+                            ++n_feat;
+                        }
                         acc_r = fmaf(w, er, acc_r);
                         acc_g = fmaf(w, eg, acc_g);
                         acc_b = fmaf(w, eb, acc_b);
@@ -238,10 +280,11 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
             o_g = fmaf(acc_g, inv, o_g);
             o_b = fmaf(acc_b, inv, o_b);
         }
-        float *o = P.out + (((long long)O * P.H + v) * P.W + u) * 3;
+        float *o = LEARN ? a.plain_out + crop_idx * 3 : P.out + (((long long)O * P.H + v) * P.W + u) * 3;
         o[0] = o_r;
         o[1] = o_g;
         o[2] = o_b;
+        if (LEARN) a.nsamp_out[crop_idx] = n_feat;
         if (DEBUG && a.pixel_stats) {
             int32_t *ps = a.pixel_stats + crop_idx * 3;
             ps[0] = n_acc;
@@ -253,7 +296,7 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
 }
 
 // One CTA per 32 x kTileY output tile of one output frame (grid: tiles x output frames).
-template <int K, int CFMT, bool DEBUG>
+template <int K, int CFMT, bool DEBUG, bool LEARN = false>
 __global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const GatherArgs a) {
     extern __shared__ float4 sgeom[];
     __shared__ float s_const[4];
@@ -281,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const G
     const long long crop_idx = (long long)(v - a.y0) * a.cw + (u - a.x0);
     int n_acc = 0, n_exam = 0;
     float acc_w = 0.0f;
-    gather_pixel<K, CFMT, DEBUG>(a, a.clip, O, u0, v0, u, v, active, crop_idx, sgeom, a.n_slots, s_const[0], s_const[1],
+    gather_pixel<K, CFMT, DEBUG, LEARN>(a, a.clip, O, u0, v0, u, v, active, crop_idx, sgeom, a.n_slots, s_const[0], s_const[1],
                                  s_const[2], s_const[3] != 0.0f, n_acc, n_exam, acc_w);
 
     // launch statistics: warp, then block, then one atomic per CTA
@@ -403,7 +446,8 @@ cudaError_t launch_k(const GatherArgs &a, cudaStream_t s) {
     dim3 grid((a.cw + kTileX - 1) / kTileX, (a.ch + kTileY - 1) / kTileY, a.n_out);
     size_t smem = sizeof(float4) * kSlotVec * (size_t)a.n_slots;
     const bool dbg = a.membership || a.pixel_stats;
-    if (dbg) gather_kernel<K, CFMT, true><<<grid, kThreads, smem, s>>>(a);
+    if (a.feat_out) gather_kernel<K, CFMT, false, true><<<grid, kThreads, smem, s>>>(a);
+    else if (dbg) gather_kernel<K, CFMT, true><<<grid, kThreads, smem, s>>>(a);
     else gather_kernel<K, CFMT, false><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -56,6 +56,12 @@ struct GatherArgs {
     int lens_n;               // seed points
     int cap;                  // box cap per axis (odd)
     float lens_xy[128];       // seed lens points (x, y) on the unit-radius disc, scaled by A in the kernel
+    // learned filter: capped sample features (crop pixel x 64 x 16 BF16), colours (x 64 x 3),
+    // counts and the plain Eq. 3/4 result per crop pixel
+    unsigned short *feat_out;
+    float *col_out;
+    int32_t *nsamp_out;
+    float *plain_out;
     int32_t *membership;      // debug record per (crop pixel, slot) or null
     int32_t *pixel_stats;     // debug record per crop pixel or null
     unsigned long long *stat_counts;  // [0] examined, [1] accepted
@@ -77,6 +83,48 @@ struct BatchArgs {
     long long n_items;
     unsigned long long *counter;  // work counter, zero before the launch
 };
+
+// ---------------------------------------------------------------- learned per-sample weights
+// Flat parameter vector: W1 (64 x 16, hidden x feature) | b1 (64) | W2 (2 x 64) | b2 (2).
+constexpr int kMlpParams = 64 * 16 + 64 + 2 * 64 + 2;
+constexpr int kMlpB1 = 64 * 16, kMlpW2 = kMlpB1 + 64, kMlpB2 = kMlpW2 + 128;
+
+struct MlpWeights {           // what the tensor-core kernels read
+    const unsigned short *W1; // BF16 bits
+    const float *b1;          // FP32
+    const float *W2;          // FP32 holding BF16-rounded values
+    const float *b2;          // FP32
+};
+
+struct MlpState {             // training state on the device
+    float *master, *m, *v;    // kMlpParams each
+    float *grad;              // kMlpParams + 1 (the batch loss last)
+    unsigned short *W1_bf16;  // 1024
+    float *W2_r;              // 128
+};
+
+struct MlpArgs {
+    MlpWeights w;
+    const unsigned short *feat;   // per crop pixel 64 x 16 BF16
+    const float *col;             // per crop pixel 64 x 3
+    const int32_t *nsamp;         // per crop pixel
+    const float *plain;           // per crop pixel 3 (Eq. 3/4 result)
+    long long n_px;               // crop pixels
+    int O, W, H, x0, y0, cw;      // output frame and crop (pixel px = (x0 + px % cw, y0 + px / cw))
+    float tau;                    // confidence threshold
+    float *out;                   // clip output buffer (inference)
+    float *conf_out;              // optional per crop pixel confidence
+    const int32_t *batch;         // training: crop pixel indices
+    long long n_batch;
+    const float *clean;           // training: target frames (F x H x W x 3, FP32)
+    float bce_w;
+    float *grad;                  // training: kMlpParams + 1 accumulators
+};
+
+cudaError_t launch_mlp_infer(const MlpArgs &m, cudaStream_t s);
+cudaError_t launch_mlp_train(const MlpArgs &m, cudaStream_t s);
+cudaError_t launch_adam(const MlpState &st, float lr, int step, cudaStream_t s);
+cudaError_t launch_mlp_refresh(const MlpState &st, cudaStream_t s);
 
 cudaError_t launch_pack(const float *rgb, const float *depth, int W, int H, int nF, const Planes &dst, int frame0,
                         cudaStream_t s);

@@ -1,0 +1,411 @@
+// ssvp_mlp.cu - the learned per-sample weighting: a 16 -> 64 -> 2 MLP over each pixel's capped
+// sample set (up to 64 samples), on the BF16 tensor cores with FP32 accumulation.
+//
+// One warp per pixel.  Layer 1 is H = F W1^T + b1 with F the pixel's 64 x 16 feature block (four
+// 16-row tiles) and W1^T held in B fragments for all eight 8-column tiles of the 64 hidden units:
+// 32 mma.sync.m16n8k16 (bf16 x bf16 -> f32) per pixel, b1 folded into the accumulator.  ReLU and
+// the 64 -> 2 head run in FP32 on the fragments; (z_w, z_c) per sample become w = softplus(z_w)
+// and conf = mean sigmoid(z_c); the output is sum w c / sum w, or the plain Eq. 3/4 result when
+// conf < tau.  Training recomputes H, forms dH in shared memory (BF16) and accumulates
+// dW1 = dH^T F as a second MMA over the sample dimension.
+#include <cuda_bf16.h>
+
+#include "ssvp_internal.h"
+
+namespace ssvp {
+namespace {
+
+constexpr int kS = 64, kF = 16, kH = 64;
+constexpr int kWarps = 4;          // warps (pixels in flight) per CTA
+constexpr int kLd = kH + 8;        // padded row of the shared dH tile (bf16 elements)
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1,
+                                         const float (&c)[4]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%11,%12,%13};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]), "f"(c[2]), "f"(c[3]));
+}
+
+// keep the kernels' copies of the master weights: W1 as BF16, W2 rounded to BF16 values
+__device__ __forceinline__ void refresh_one(const MlpState &st, int i, float p) {
+    if (i < kMlpB1) {
+        __nv_bfloat16 b = __float2bfloat16_rn(p);
+        st.W1_bf16[i] = *reinterpret_cast<unsigned short *>(&b);
+    } else if (i >= kMlpW2 && i < kMlpB2) {
+        st.W2_r[i - kMlpW2] = __bfloat162float(__float2bfloat16_rn(p));
+    }
+}
+
+__device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + log1pf(__expf(-fabsf(x))); }
+__device__ __forceinline__ float sigmoidf(float x) { return 1.0f / (1.0f + __expf(-x)); }
+
+__device__ __forceinline__ unsigned pack2(unsigned short lo, unsigned short hi) { return (unsigned)lo | ((unsigned)hi << 16); }
+
+// A fragments (rows = samples) of the four 16-sample tiles; rows >= n are zero
+__device__ __forceinline__ void load_features(const unsigned *fw, int n, int g, int t, unsigned (&a)[4][4]) {
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+        const int r0 = 16 * mt + g, r1 = r0 + 8;
+        a[mt][0] = r0 < n ? __ldg(fw + r0 * 8 + t) : 0u;
+        a[mt][1] = r1 < n ? __ldg(fw + r1 * 8 + t) : 0u;
+        a[mt][2] = r0 < n ? __ldg(fw + r0 * 8 + 4 + t) : 0u;
+        a[mt][3] = r1 < n ? __ldg(fw + r1 * 8 + 4 + t) : 0u;
+    }
+}
+
+// layer 1 + ReLU + head for one 8-column tile nt: accumulates z partials of the lane's rows
+__device__ __forceinline__ void head_tile(const unsigned (&a)[4][4], unsigned b0, unsigned b1, const MlpWeights &w, int nt,
+                                          int t, float (&zw)[4][2], float (&zc)[4][2]) {
+    const int c0 = 8 * nt + 2 * t;
+    const float bias0 = __ldg(w.b1 + c0), bias1 = __ldg(w.b1 + c0 + 1);
+    const float w00 = __ldg(w.W2 + c0), w01 = __ldg(w.W2 + c0 + 1);
+    const float w10 = __ldg(w.W2 + kH + c0), w11 = __ldg(w.W2 + kH + c0 + 1);
+    const float cinit[4] = {bias0, bias1, bias0, bias1};
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+        float d[4];
+        mma_bf16(d, a[mt], b0, b1, cinit);
+        const float h0 = fmaxf(d[0], 0.f), h1 = fmaxf(d[1], 0.f), h2 = fmaxf(d[2], 0.f), h3 = fmaxf(d[3], 0.f);
+        zw[mt][0] = fmaf(w00, h0, fmaf(w01, h1, zw[mt][0]));
+        zw[mt][1] = fmaf(w00, h2, fmaf(w01, h3, zw[mt][1]));
+        zc[mt][0] = fmaf(w10, h0, fmaf(w11, h1, zc[mt][0]));
+        zc[mt][1] = fmaf(w10, h2, fmaf(w11, h3, zc[mt][1]));
+    }
+}
+
+struct PixelForward {
+    float zw[4][2], zc[4][2];  // per lane: rows 16 mt + g (+ 8), summed over the hidden units
+};
+
+__device__ __forceinline__ void forward(const unsigned (&a)[4][4], const unsigned (&bw)[8][2], const MlpWeights &w,
+                                        int t, PixelForward &pf) {
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) pf.zw[mt][0] = pf.zw[mt][1] = pf.zc[mt][0] = pf.zc[mt][1] = 0.0f;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) head_tile(a, bw[nt][0], bw[nt][1], w, nt, t, pf.zw, pf.zc);
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            pf.zw[mt][r] += __shfl_xor_sync(0xffffffffu, pf.zw[mt][r], 1);
+            pf.zw[mt][r] += __shfl_xor_sync(0xffffffffu, pf.zw[mt][r], 2);
+            pf.zc[mt][r] += __shfl_xor_sync(0xffffffffu, pf.zc[mt][r], 1);
+            pf.zc[mt][r] += __shfl_xor_sync(0xffffffffu, pf.zc[mt][r], 2);
+        }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void load_w1(const MlpWeights &w, int g, int t, unsigned (&bw)[8][2]) {
+    const unsigned *w1 = reinterpret_cast<const unsigned *>(w.W1);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        bw[nt][0] = __ldg(w1 + (8 * nt + g) * 8 + t);
+        bw[nt][1] = __ldg(w1 + (8 * nt + g) * 8 + 4 + t);
+    }
+}
+
+// ---------------------------------------------------------------- inference
+__global__ void __launch_bounds__(32 * kWarps) mlp_infer_kernel(const MlpArgs m) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    unsigned bw[8][2];
+    load_w1(m.w, g, t, bw);
+    const float b20 = __ldg(m.w.b2), b21 = __ldg(m.w.b2 + 1);
+    const long long nwarps = (long long)gridDim.x * kWarps;
+    for (long long px = blockIdx.x * (long long)kWarps + (threadIdx.x >> 5); px < m.n_px; px += nwarps) {
+        const int n = m.nsamp[px];
+        const float *pl = m.plain + 3 * px;
+        float o0 = pl[0], o1 = pl[1], o2 = pl[2], conf = 0.0f;
+        if (n > 0) {
+            unsigned a[4][4];
+            load_features(reinterpret_cast<const unsigned *>(m.feat) + px * (kS * kF / 2), n, g, t, a);
+            PixelForward pf;
+            forward(a, bw, m.w, t, pf);
+            float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
+            if (t < 2) {
+#pragma unroll
+                for (int mt = 0; mt < 4; ++mt) {
+                    const int s = 16 * mt + g + 8 * t;
+                    if (s < n) {
+                        const float zw = (t == 0 ? pf.zw[mt][0] : pf.zw[mt][1]) + b20;
+                        const float zc = (t == 0 ? pf.zc[mt][0] : pf.zc[mt][1]) + b21;
+                        const float w = softplusf(zw);
+                        const float *c = m.col + (px * kS + s) * 3;
+                        sw += w;
+                        sr = fmaf(w, c[0], sr);
+                        sg = fmaf(w, c[1], sg);
+                        sb = fmaf(w, c[2], sb);
+                        sc += sigmoidf(zc);
+                    }
+                }
+            }
+            sw = warp_sum(sw);
+            sr = warp_sum(sr);
+            sg = warp_sum(sg);
+            sb = warp_sum(sb);
+            sc = warp_sum(sc);
+            conf = sc / (float)n;
+            if (conf >= m.tau && sw > 0.0f) {
+                const float inv = 1.0f / sw;
+                o0 = sr * inv;
+                o1 = sg * inv;
+                o2 = sb * inv;
+            }
+        }
+        if (lane == 0) {
+            const long long u = m.x0 + px % m.cw, v = m.y0 + px / m.cw;
+            float *o = m.out + (((long long)m.O * m.H + v) * m.W + u) * 3;
+            o[0] = o0;
+            o[1] = o1;
+            o[2] = o2;
+            if (m.conf_out) m.conf_out[px] = conf;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- training: forward + backward
+__global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m) {
+    __shared__ unsigned short s_dh[kWarps][kS * kLd];
+    __shared__ float s_g[kH + 2 * kH + 2 + 1];  // gb1, gW2, gb2, loss
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kH + 2 * kH + 3; i += blockDim.x) s_g[i] = 0.0f;
+    __syncthreads();
+    unsigned bw[8][2];
+    load_w1(m.w, g, t, bw);
+    const float b20 = __ldg(m.w.b2), b21 = __ldg(m.w.b2 + 1);
+    float dW1[4][2][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) dW1[i][j][0] = dW1[i][j][1] = dW1[i][j][2] = dW1[i][j][3] = 0.0f;
+    unsigned short *dh = s_dh[wid];
+    const float inv_np = 1.0f / (float)m.n_batch;
+    const long long nwarps = (long long)gridDim.x * kWarps;
+    for (long long bi = blockIdx.x * (long long)kWarps + wid; bi < m.n_batch; bi += nwarps) {
+        const long long px = m.batch[bi];
+        const int n = m.nsamp[px];
+        if (n <= 0) continue;  // warp-uniform
+        const unsigned *fw = reinterpret_cast<const unsigned *>(m.feat) + px * (kS * kF / 2);
+        const unsigned short *fh = m.feat + px * (kS * kF);
+        unsigned a[4][4];
+        load_features(fw, n, g, t, a);
+        PixelForward pf;
+        forward(a, bw, m.w, t, pf);
+        // per-sample weights, outputs and the pixel's loss
+        float zw[4], zc[4], w[4], cf[4], cr[4][3];
+        bool valid[4];
+        float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+            const int s = 16 * mt + g + 8 * t;
+            zw[mt] = (t == 0 ? pf.zw[mt][0] : pf.zw[mt][1]) + b20;
+            zc[mt] = (t == 0 ? pf.zc[mt][0] : pf.zc[mt][1]) + b21;
+            valid[mt] = t < 2 && s < n;
+            w[mt] = valid[mt] ? softplusf(zw[mt]) : 0.f;
+            cf[mt] = valid[mt] ? sigmoidf(zc[mt]) : 0.f;
+            const float *c = m.col + (px * kS + (valid[mt] ? s : 0)) * 3;
+            cr[mt][0] = valid[mt] ? c[0] : 0.f;
+            cr[mt][1] = valid[mt] ? c[1] : 0.f;
+            cr[mt][2] = valid[mt] ? c[2] : 0.f;
+            sw += w[mt];
+            sr = fmaf(w[mt], cr[mt][0], sr);
+            sg = fmaf(w[mt], cr[mt][1], sg);
+            sb = fmaf(w[mt], cr[mt][2], sb);
+            sc += cf[mt];
+        }
+        sw = warp_sum(sw);
+        sr = warp_sum(sr);
+        sg = warp_sum(sg);
+        sb = warp_sum(sb);
+        sc = warp_sum(sc);
+        const float inv_w = 1.0f / sw;
+        const float ol[3] = {sr * inv_w, sg * inv_w, sb * inv_w};
+        const float conf = sc / (float)n;
+        const long long u = px % m.cw + m.x0, v = px / m.cw + m.y0;
+        const float *y = m.clean + (((long long)m.O * m.H + v) * m.W + u) * 3;
+        const float *pl = m.plain + 3 * px;
+        float el = 0.f, ep = 0.f, dO[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            el += (ol[c] - y[c]) * (ol[c] - y[c]) * (1.0f / 3.0f);
+            ep += (pl[c] - y[c]) * (pl[c] - y[c]) * (1.0f / 3.0f);
+            dO[c] = 2.0f * (ol[c] - y[c]) * (1.0f / 3.0f) * inv_np;
+        }
+        const float tgt = el <= ep ? 1.0f : 0.0f;
+        const float cc = fminf(fmaxf(conf, 1e-6f), 1.0f - 1e-6f);
+        const bool inside = conf > 1e-6f && conf < 1.0f - 1e-6f;
+        const float dconf = inside ? m.bce_w * (cc - tgt) / (cc * (1.0f - cc)) * inv_np : 0.0f;
+        if (lane == 0) atomicAdd(&s_g[kH + 2 * kH + 2], (el - m.bce_w * (tgt * logf(cc) + (1.0f - tgt) * logf(1.0f - cc))) * inv_np);
+        // dz per sample (zero outside the set), broadcast to the lanes holding the same rows
+        float dzw_own[4], dzc_own[4], gz0 = 0.f, gz1 = 0.f;
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+            const float dw = (dO[0] * (cr[mt][0] - ol[0]) + dO[1] * (cr[mt][1] - ol[1]) + dO[2] * (cr[mt][2] - ol[2])) * inv_w;
+            dzw_own[mt] = valid[mt] ? dw * sigmoidf(zw[mt]) : 0.f;
+            dzc_own[mt] = valid[mt] ? dconf * cf[mt] * (1.0f - cf[mt]) / (float)n : 0.f;
+            gz0 += dzw_own[mt];
+            gz1 += dzc_own[mt];
+        }
+        gz0 = warp_sum(gz0);
+        gz1 = warp_sum(gz1);
+        if (lane == 0) {
+            atomicAdd(&s_g[kH + 2 * kH], gz0);
+            atomicAdd(&s_g[kH + 2 * kH + 1], gz1);
+        }
+        float dzw[4][2], dzc[4][2];
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+            dzw[mt][0] = __shfl_sync(0xffffffffu, dzw_own[mt], g * 4 + 0);
+            dzw[mt][1] = __shfl_sync(0xffffffffu, dzw_own[mt], g * 4 + 1);
+            dzc[mt][0] = __shfl_sync(0xffffffffu, dzc_own[mt], g * 4 + 0);
+            dzc[mt][1] = __shfl_sync(0xffffffffu, dzc_own[mt], g * 4 + 1);
+        }
+        // recompute H per 8-column tile: dW2, db1, dH (to shared memory as BF16)
+#pragma unroll 1
+        for (int nt = 0; nt < 8; ++nt) {
+            const int c0 = 8 * nt + 2 * t;
+            const float bias0 = __ldg(m.w.b1 + c0), bias1 = __ldg(m.w.b1 + c0 + 1);
+            const float w00 = __ldg(m.w.W2 + c0), w01 = __ldg(m.w.W2 + c0 + 1);
+            const float w10 = __ldg(m.w.W2 + kH + c0), w11 = __ldg(m.w.W2 + kH + c0 + 1);
+            const float cinit[4] = {bias0, bias1, bias0, bias1};
+            float g0a = 0.f, g0b = 0.f, g1a = 0.f, g1b = 0.f, gba = 0.f, gbb = 0.f;
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) {
+                float d[4];
+                mma_bf16(d, a[mt], bw[nt][0], bw[nt][1], cinit);
+                const float h0 = fmaxf(d[0], 0.f), h1 = fmaxf(d[1], 0.f), h2 = fmaxf(d[2], 0.f), h3 = fmaxf(d[3], 0.f);
+                g0a += dzw[mt][0] * h0 + dzw[mt][1] * h2;
+                g0b += dzw[mt][0] * h1 + dzw[mt][1] * h3;
+                g1a += dzc[mt][0] * h0 + dzc[mt][1] * h2;
+                g1b += dzc[mt][0] * h1 + dzc[mt][1] * h3;
+                const float dh0 = d[0] > 0.f ? dzw[mt][0] * w00 + dzc[mt][0] * w10 : 0.f;
+                const float dh1 = d[1] > 0.f ? dzw[mt][0] * w01 + dzc[mt][0] * w11 : 0.f;
+                const float dh2 = d[2] > 0.f ? dzw[mt][1] * w00 + dzc[mt][1] * w10 : 0.f;
+                const float dh3 = d[3] > 0.f ? dzw[mt][1] * w01 + dzc[mt][1] * w11 : 0.f;
+                gba += dh0 + dh2;
+                gbb += dh1 + dh3;
+                __nv_bfloat162 p01 = __floats2bfloat162_rn(dh0, dh1), p23 = __floats2bfloat162_rn(dh2, dh3);
+                *reinterpret_cast<__nv_bfloat162 *>(dh + (16 * mt + g) * kLd + c0) = p01;
+                *reinterpret_cast<__nv_bfloat162 *>(dh + (16 * mt + g + 8) * kLd + c0) = p23;
+            }
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                g0a += __shfl_xor_sync(0xffffffffu, g0a, o);
+                g0b += __shfl_xor_sync(0xffffffffu, g0b, o);
+                g1a += __shfl_xor_sync(0xffffffffu, g1a, o);
+                g1b += __shfl_xor_sync(0xffffffffu, g1b, o);
+                gba += __shfl_xor_sync(0xffffffffu, gba, o);
+                gbb += __shfl_xor_sync(0xffffffffu, gbb, o);
+            }
+            if (g == 0) {
+                atomicAdd(&s_g[kH + c0], g0a);
+                atomicAdd(&s_g[kH + c0 + 1], g0b);
+                atomicAdd(&s_g[kH + kH + c0], g1a);
+                atomicAdd(&s_g[kH + kH + c0 + 1], g1b);
+                atomicAdd(&s_g[c0], gba);
+                atomicAdd(&s_g[c0 + 1], gbb);
+            }
+        }
+        __syncwarp();
+        // dW1 (64 hidden x 16 features) += dH^T F over the 64 samples: M = hidden, N = feature, K = sample
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            const int s0 = 16 * kt + 2 * t, s1 = s0 + 1, s8 = s0 + 8, s9 = s0 + 9;
+            unsigned bf[2][2];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int i = 8 * nt + g;
+                bf[nt][0] = pack2(s0 < n ? fh[s0 * kF + i] : 0, s1 < n ? fh[s1 * kF + i] : 0);
+                bf[nt][1] = pack2(s8 < n ? fh[s8 * kF + i] : 0, s9 < n ? fh[s9 * kF + i] : 0);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) {
+                const int j0 = 16 * mt + g, j8 = j0 + 8;
+                unsigned af[4];
+                af[0] = pack2(dh[s0 * kLd + j0], dh[s1 * kLd + j0]);
+                af[1] = pack2(dh[s0 * kLd + j8], dh[s1 * kLd + j8]);
+                af[2] = pack2(dh[s8 * kLd + j0], dh[s9 * kLd + j0]);
+                af[3] = pack2(dh[s8 * kLd + j8], dh[s9 * kLd + j8]);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    float d[4];
+                    mma_bf16(d, af, bf[nt][0], bf[nt][1], dW1[mt][nt]);
+                    dW1[mt][nt][0] = d[0];
+                    dW1[mt][nt][1] = d[1];
+                    dW1[mt][nt][2] = d[2];
+                    dW1[mt][nt][3] = d[3];
+                }
+            }
+        }
+        __syncwarp();  // dH is rewritten by the next pixel
+    }
+    // flush: dW1 fragments (rows = hidden 16 mt + g (+8), cols = feature 8 nt + 2 t (+1))
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int j0 = 16 * mt + g, i0 = 8 * nt + 2 * t;
+            atomicAdd(m.grad + j0 * kF + i0, dW1[mt][nt][0]);
+            atomicAdd(m.grad + j0 * kF + i0 + 1, dW1[mt][nt][1]);
+            atomicAdd(m.grad + (j0 + 8) * kF + i0, dW1[mt][nt][2]);
+            atomicAdd(m.grad + (j0 + 8) * kF + i0 + 1, dW1[mt][nt][3]);
+        }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kH + 2 * kH + 3; i += blockDim.x) atomicAdd(m.grad + kH * kF + i, s_g[i]);
+}
+
+// ---------------------------------------------------------------- Adam on the FP32 master weights
+__global__ void adam_kernel(MlpState st, float lr, float b1, float b2, float eps, int step) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpParams) return;
+    const float gr = st.grad[i];
+    const float m = b1 * st.m[i] + (1.0f - b1) * gr;
+    const float v = b2 * st.v[i] + (1.0f - b2) * gr * gr;
+    st.m[i] = m;
+    st.v[i] = v;
+    const float mh = m / (1.0f - powf(b1, (float)step)), vh = v / (1.0f - powf(b2, (float)step));
+    const float p = st.master[i] - lr * mh / (sqrtf(vh) + eps);
+    st.master[i] = p;
+    refresh_one(st, i, p);
+}
+
+__global__ void refresh_kernel(MlpState st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kMlpParams) refresh_one(st, i, st.master[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_infer(const MlpArgs &m, cudaStream_t s) {
+    if (m.n_px <= 0) return cudaSuccess;
+    long long blocks = (m.n_px + kWarps - 1) / kWarps;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    mlp_infer_kernel<<<(unsigned)blocks, 32 * kWarps, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_train(const MlpArgs &m, cudaStream_t s) {
+    if (m.n_batch <= 0) return cudaSuccess;
+    long long blocks = (m.n_batch + kWarps - 1) / kWarps;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    mlp_train_kernel<<<(unsigned)blocks, 32 * kWarps, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(const MlpState &st, float lr, int step, cudaStream_t s) {
+    adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(st, lr, 0.9f, 0.999f, 1e-8f, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_refresh(const MlpState &st, cudaStream_t s) {
+    refresh_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+}  // namespace ssvp

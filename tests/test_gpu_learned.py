@@ -1,0 +1,170 @@
+"""GPU learned per-sample weighting against the oracle: samples and features, tensor-core
+inference, gradients of the training kernel, and a short training run."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import Session
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sess():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    s = Session()
+    yield s
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def clip():
+    return synth.make_clip("planes3", 96, 54, 10, seed=11)
+
+
+def bf16_to_f32(bits):
+    return (bits.astype(np.uint32) << 16).view(np.float32)
+
+
+def _flags(c, prm, O, crop):
+    """Pixels whose membership may legitimately differ (radius band or rounding tie)."""
+    o = oracle.gather_filter(oracle.ClipView.of(c), prm, O, crop=crop, membership=True)
+    band = ((o.codes & oracle.CODE_BAND) != 0).any(axis=(-1, -2, -3))
+    amb = ((o.amb == 1) & (o.status == 1)).any(-1)
+    return band | amb
+
+
+def _gpu_samples(sess, cid, O, k, T, crop):
+    t = sess.torch
+    x0, y0, cw, ch = crop
+    n = cw * ch
+    feat = t.zeros((n, 64, 16), dtype=t.int16, device=sess.dev)
+    col = t.zeros((n, 64, 3), dtype=t.float32, device=sess.dev)
+    ns = t.zeros(n, dtype=t.int32, device=sess.dev)
+    plain = t.zeros((n, 3), dtype=t.float32, device=sess.dev)
+    p = sess.params(k=k, half_window=T, frame_begin=O, frame_end=O + 1, crop_x=x0, crop_y=y0, crop_w=cw, crop_h=ch)
+    sess.ss.ssvp_learned_samples(sess.ctx, p, cid, feat, col, ns, plain)
+    sess.ss.ssvp_sync(sess.ctx)
+    return (bf16_to_f32(feat.cpu().numpy().view(np.uint16)).reshape(ch, cw, 64, 16), col.cpu().numpy().reshape(ch, cw, 64, 3),
+            ns.cpu().numpy().reshape(ch, cw), plain.cpu().numpy().reshape(ch, cw, 3))
+
+
+def test_samples_and_features_match_the_oracle(sess, clip):
+    sess.load(40, clip)
+    O, k, T, crop = 5, 5, 4, (0, 0, 96, 54)
+    prm = oracle.default_params(clip.depth, k=k, T=T)
+    gf, gc, gn, gp = _gpu_samples(sess, 40, O, k, T, crop)
+    of, oc, on, op = oracle.learned_crop(oracle.ClipView.of(clip), prm, O, crop=crop)
+    ok = ~_flags(clip, prm, O, crop)
+    assert ok.mean() > 0.95
+    np.testing.assert_array_equal(gn[ok], on[ok])
+    assert np.abs(gp[ok] - op[ok]).max() <= 1e-3
+    m = np.arange(64)[None, None, :] < on[..., None]
+    sel = ok[..., None] & m
+    np.testing.assert_array_equal(gc[sel], oc[sel].astype(np.float32))
+    # features: the oracle's FP64 values rounded to BF16; a rounding boundary may flip one ulp
+    ob = bf16_to_f32((np.asarray(of, np.float32).view(np.uint32) + 0x7FFF + ((np.asarray(of, np.float32).view(np.uint32) >> 16) & 1)) >> 16)
+    diff = np.abs(gf[sel] - ob[sel])
+    assert (diff <= np.abs(ob[sel]) * 2 ** -7 + 1e-6).all(), diff.max()
+
+
+def test_tensor_core_inference_matches_the_oracle(sess, clip):
+    sess.load(40, clip)
+    O, k, T, crop = 5, 5, 4, (8, 6, 48, 32)
+    prm = oracle.default_params(clip.depth, k=k, T=T)
+    rng = np.random.default_rng(3)
+    W1, b1, W2, b2 = oracle.he_init(4)
+    b1 = rng.normal(0, 0.1, 64)
+    b2 = np.array([0.2, 1.5])  # confidence mostly above the threshold: the learned weights are used
+    sess.ss.ssvp_set_mlp(sess.ctx, W1, b1, W2, b2)
+    g = sess.run(40, O, crop=crop, mode=2, k=k, half_window=T, conf_threshold=0.5)
+    of, oc, on, op = oracle.learned_crop(oracle.ClipView.of(clip), prm, O, crop=crop)
+    ok = ~_flags(clip, prm, O, crop)
+    x0, y0, cw, ch = crop
+    worst, near = 0.0, 0
+    for y in range(ch):
+        for x in range(cw):
+            if not ok[y, x]:
+                continue
+            ol, ofin, conf, _ = oracle.mlp_pixel(of[y, x], oc[y, x], on[y, x], W1, b1, W2, b2, round_bf16=True,
+                                                 plain=op[y, x])
+            if abs(conf - 0.5) < 1e-3:
+                near += 1
+                continue  # the fallback decision is a tie between FP32 and FP64
+            worst = max(worst, float(np.abs(g.rgb[y, x] - ofin).max()))
+    assert worst <= 1e-3, worst
+    assert near < 0.01 * cw * ch
+
+
+def test_high_threshold_reproduces_the_plain_denoiser(sess, clip):
+    sess.load(40, clip)
+    W1, b1, W2, b2 = oracle.he_init(5)
+    sess.ss.ssvp_set_mlp(sess.ctx, W1, b1, W2, b2)
+    a = sess.run(40, 4, mode=2, k=7, half_window=4, conf_threshold=2.0).rgb
+    b = sess.run(40, 4, mode=0, k=7, half_window=4).rgb
+    assert np.abs(a - b).max() <= 1e-5
+
+
+def test_training_gradients_match_the_oracle(sess, clip):
+    sess.load(40, clip)
+    O, k, T = 5, 5, 4
+    prm = oracle.default_params(clip.depth, k=k, T=T, radius_rel=0.02)
+    rel = 0.02
+    W1, b1, W2, b2 = oracle.he_init(6)
+    b2 = np.array([0.1, 0.0])
+    sess.ss.ssvp_set_mlp(sess.ctx, W1, b1, W2, b2)
+    of, oc, on, op = oracle.learned_crop(oracle.ClipView.of(clip), prm, O)
+    flags = _flags(clip, prm, O, (0, 0, clip.W, clip.H))
+    clean = clip.clean[O].astype(np.float64)
+    # pixels with several samples, no membership ambiguity and a clear BCE target
+    cand = []
+    for y in range(clip.H):
+        for x in range(clip.W):
+            if flags[y, x] or on[y, x] < 3:
+                continue
+            ol, _, _, _ = oracle.mlp_pixel(of[y, x], oc[y, x], on[y, x], W1, b1, W2, b2, plain=op[y, x])
+            el, ep = np.mean((ol - clean[y, x]) ** 2), np.mean((op[y, x] - clean[y, x]) ** 2)
+            if abs(el - ep) > 1e-3 * max(el, ep, 1e-12):
+                cand.append((y, x))
+    rng = np.random.default_rng(0)
+    pick = [cand[i] for i in rng.choice(len(cand), size=min(256, len(cand)), replace=False)]
+    idx = np.array([y * clip.W + x for y, x in pick], np.int32)
+    t = sess.torch
+    clean_d = t.from_numpy(clip.clean).to(sess.dev)
+    p = sess.params(k=k, half_window=T, frame_begin=O, frame_end=O + 1, radius=-rel)
+    g = sess.ss.ssvp_mlp_grad(sess.ctx, p, 40, idx, clean_d)
+    ys, xs = zip(*pick)
+    L, gW1, gb1, gW2, gb2 = oracle.mlp_loss_grad(of[ys, xs], oc[ys, xs], on[ys, xs], op[ys, xs], clean[ys, xs],
+                                                 W1, b1, W2, b2, round_bf16=True)
+    assert g[1218] == pytest.approx(L, rel=1e-4)
+    parts = [(g[:1024], gW1.ravel(), 2e-2), (g[1024:1088], gb1, 1e-3), (g[1088:1216], gW2.ravel(), 1e-3),
+             (g[1216:1218], gb2, 1e-3)]
+    for got, want, tol in parts:
+        err = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-12)
+        assert err <= tol, (err, tol)
+
+
+def test_short_training_lowers_the_loss(sess):
+    clips = [synth.make_clip("room", 160, 90, 10, seed=s) for s in (21, 22, 23)]
+    t = sess.torch
+    for i, c in enumerate(clips):
+        sess.load(41 + i, c)
+    clean = [t.from_numpy(c.clean).to(sess.dev) for c in clips]
+    p = sess.params(k=7, half_window=4)
+    cfg = sess.ss.ssvp_train_config(steps=300, batch_pixels=4096, lr=1e-3, bce_weight=0.1, seed=0, init=1)
+    losses = sess.ss.ssvp_train(sess.ctx, p, [41, 42, 43], clean, cfg)
+    assert np.isfinite(losses).all()
+    assert losses[-30:].mean() < losses[:30].mean()
+    held = synth.make_clip("room", 160, 90, 10, seed=29)
+    sess.load(44, held)
+    learned = sess.run(44, 5, mode=2, k=7, half_window=4, conf_threshold=0.5).rgb
+    plain = sess.run(44, 5, mode=0, k=7, half_window=4).rgb
+    psnr = lambda a: 10 * np.log10(1 / np.mean((a.astype(np.float64) - held.clean[5]) ** 2))
+    print(f"held-out PSNR: plain {psnr(plain):.3f} dB, learned {psnr(learned):.3f} dB, "
+          f"loss {losses[:30].mean():.5f} -> {losses[-30:].mean():.5f}")
+    assert psnr(learned) >= psnr(plain) - 0.3
