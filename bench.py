@@ -29,6 +29,7 @@ WORKLOADS = {
     "hd": (1280, 720, 60, 15, 7, 15, 8, 0),         # 720p denoising, +-15 frames
     "aperture": (1920, 1080, 68, 30, 7, 30, 8, 1),  # 1080p virtual aperture over +-30 frames
     "batch": (0, 0, 0, 15, 7, 0, 0, 0),              # 8 uneven clips in one plan (sizes by seed)
+    "learned": (1920, 1080, 68, 30, 7, 30, 8, 2),    # learned weights, trained on generated clips
 }
 W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE = WORKLOADS["fhd"]
 APERTURE, LENS, CAP = 0.05, 16, 31
@@ -281,6 +282,82 @@ def run_batch(args, ss, torch, dev, stream, world, rank):
     ss.ssvp_destroy(ctx)
     return line
 
+
+def run_learned(args, ss, torch, dev, stream, world, rank):
+    """Train the per-sample weighting network on the GPU over generated 640x360x30 clips (seeds
+    1000..), then denoise 1080p +-30 with it and with the plain filter."""
+    import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ctx = ss.ssvp_create(local, stream)
+    p = ss.ssvp_params_default()
+    p.k, p.half_window, p.radius = K_WIN, T, -RADIUS_REL
+    n_train, group, steps_per_group = args.train_clips, 8, 40
+    losses, t_render, t_train = [], 0.0, 0.0
+    for g0 in range(0, n_train, group):
+        t0 = time.perf_counter()
+        clips = [synth.make_clip("room", 640, 360, 30, seed=1000 + i) for i in range(g0, min(g0 + group, n_train))]
+        t_render += time.perf_counter() - t0
+        cleans = []
+        for j, c in enumerate(clips):
+            r, d = torch.from_numpy(c.rgb).to(dev), torch.from_numpy(c.depth).to(dev)
+            ss.ssvp_load_clip(ctx, j, c.W, c.H, c.F, r, d)
+            ss.ssvp_set_cameras(ctx, j, c.K, 1, c.w2c)
+            cleans.append(torch.from_numpy(c.clean).to(dev))
+        cfg = ss.ssvp_train_config(steps=steps_per_group, batch_pixels=16384, lr=1e-3, bce_weight=0.1,
+                                   seed=g0, init=1 if g0 == 0 else 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses += list(ss.ssvp_train(ctx, p, list(range(len(clips))), cleans, cfg))
+        t_train += time.perf_counter() - t0
+        for j in range(len(clips)):
+            ss.ssvp_unload_clip(ctx, j)
+    clip = _workload_clip(seed=rank)
+    r, d = torch.from_numpy(clip.rgb).to(dev), torch.from_numpy(clip.depth).to(dev)
+    ss.ssvp_load_clip(ctx, 0, W, H, F, r, d)
+    ss.ssvp_set_cameras(ctx, 0, clip.K, 1, clip.w2c)
+    del r, d
+    p.frame_begin, p.frame_end = O_BEGIN, O_BEGIN + N_OUT
+
+    def timed(mode, steps):
+        p.mode = mode
+        for _ in range(args.warmup):
+            ss.ssvp_gather_filter(ctx, p, [0])
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            ss.ssvp_gather_filter(ctx, p, [0])
+        b.record(stream)
+        torch.cuda.synchronize()
+        out = torch.empty((N_OUT, H, W, 3), dtype=torch.float32, device=dev)
+        ss.ssvp_read_output(ctx, 0, O_BEGIN, O_BEGIN + N_OUT, out)
+        ss.ssvp_sync(ctx)
+        return a.elapsed_time(b) / steps, out.cpu().numpy()
+
+    with ClockSampler(local) as clk:
+        ms_l, out_l = timed(ss.SSVP_MODE_LEARNED, args.steps)
+    ms_p, out_p = timed(ss.SSVP_MODE_DENOISE, args.steps)
+    clean = clip.clean[O_BEGIN:O_BEGIN + N_OUT]
+    psnr = lambda a_: float(10 * np.log10(1.0 / np.mean((a_.astype(np.float64) - clean) ** 2)))
+    mpix = N_OUT * W * H / 1e6
+    line = {
+        "metric": METRIC, "value": world * mpix / (ms_l / 1e3), "unit": "Mpix/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 gather, bf16 MLP (f32 accumulate)", "data": "synthetic (seeded procedural scenes)",
+        "config": {**_config("fp32"), "workload": f"learned-denoise-{W}x{H}-pm{T}-k{K_WIN}",
+                   "training": {"clips": n_train, "clip": "640x360x30 room scenes, seeds 1000..",
+                                "steps": len(losses), "batch_pixels": 16384, "lr": 1e-3, "bce_weight": 0.1,
+                                "loss_first_40": float(np.mean(losses[:40])), "loss_last_40": float(np.mean(losses[-40:])),
+                                "render_s": t_render, "train_s": t_train}},
+        "psnr_db": {"learned_vs_clean": psnr(out_l), "plain_vs_clean": psnr(out_p),
+                    "input_vs_clean": psnr(clip.rgb[O_BEGIN:O_BEGIN + N_OUT])},
+        "plain_same_run": {"value": world * mpix / (ms_p / 1e3), "unit": "Mpix/s", "ms_per_step": ms_p},
+        "gpu_launches": args.steps * N_OUT * 2,
+        "clocks": clk.summary(),
+    }
+    ss.ssvp_destroy(ctx)
+    return line
+
 def run_reference(args):
     """The oracle on the host cores, on this benchmark's workload, metric and unit."""
     rank = int(os.environ.get("RANK", "0"))
@@ -320,6 +397,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fhd", choices=sorted(WORKLOADS))
     ap.add_argument("--out-frames", type=int, default=None, help="output frames per step (default per workload)")
+    ap.add_argument("--train-clips", type=int, default=200, help="learned workload: generated training clips")
     args = ap.parse_args()
     global W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE
     W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE = WORKLOADS[args.workload]
@@ -347,8 +425,9 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    if args.workload == "batch":
-        line = run_batch(args, ss, torch, dev, stream, world, rank)
+    if args.workload in ("batch", "learned"):
+        fn = run_batch if args.workload == "batch" else run_learned
+        line = fn(args, ss, torch, dev, stream, world, rank)
         if rank == 0:
             print(json.dumps(line))
         if world > 1:
