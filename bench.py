@@ -28,6 +28,7 @@ WORKLOADS = {
     "fhd": (1920, 1080, 68, 30, 7, 30, 8, 0),       # 1080p denoising over +-30 frames (the headline)
     "hd": (1280, 720, 60, 15, 7, 15, 8, 0),         # 720p denoising, +-15 frames
     "aperture": (1920, 1080, 68, 30, 7, 30, 8, 1),  # 1080p virtual aperture over +-30 frames
+    "aperture-hd": (1280, 720, 60, 15, 7, 15, 8, 1),  # 720p virtual aperture, +-15 frames
     "batch": (0, 0, 0, 15, 7, 0, 0, 0),              # 8 uneven clips in one plan (sizes by seed)
     "learned": (1920, 1080, 68, 30, 7, 30, 8, 2),    # learned weights, trained on generated clips
 }
@@ -35,6 +36,23 @@ W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE = WORKLOADS["fhd"]
 APERTURE, LENS, CAP = 0.05, 16, 31
 RADIUS_REL = 0.005
 BYTES_PER_CANDIDATE = {"fp32": 16, "fp16": 12}
+
+
+def shard(rank: int, world: int):
+    """Weak scaling: every rank renders and denoises its own clip (seed = rank) and batch of output
+    frames; ranks exchange nothing but the barrier and the step-time maximum."""
+    return {"seed": rank, "frame_begin": O_BEGIN, "frame_end": O_BEGIN + N_OUT, "world": world}
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's value (the job's time), via an all-reduce MAX when world > 1."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def _measured_traffic(workload, colour, out_frames):
@@ -433,7 +451,7 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return 0
-    clip = _workload_clip(seed=rank)
+    clip = _workload_clip(seed=shard(rank, world)["seed"])
     cfmt = ss.SSVP_COLOUR_F32 if args.colour == "fp32" else ss.SSVP_COLOUR_F16
     ctx = ss.ssvp_create(local, stream)
     rgb_d = torch.from_numpy(clip.rgb).to(dev)
@@ -473,10 +491,7 @@ def main():
     total_ms = t_all0.elapsed_time(t_all1)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     examined, accepted, sum_w = ss.ssvp_read_stats(ctx)
-    t = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / args.steps
+    ms_per_step = max_over_ranks(total_ms, world, dev) / args.steps
     mpix = N_OUT * W * H / 1e6
     value = world * mpix / (ms_per_step / 1e3)
 
@@ -522,10 +537,7 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    te = torch.tensor([e0.elapsed_time(e1) / e2e_steps], device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_ms = float(te.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
     h2d = clip.rgb.nbytes + clip.depth.nbytes
     d2h = out_h.numel() * 4
     frames_per_chunk = max(1, min(F, (256 << 20) // (W * H * 16)))
