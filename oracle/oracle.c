@@ -448,7 +448,8 @@ long long oc_bruteforce(const oc_clip *c, const oc_params *p, int O, int u, int 
  * frames J = O, O-1, O+1, O-2, O+2, ... (the earlier frame first on ties), then the k x k window
  * in raster order.  Features of a sample s gathered from pixel q of frame J (16 per sample):
  *   [c_s (3), c_s - c_ref (3), |X_q - x_ref| / r, (J - O) / max(T, 1), (d_q - z'_J) / r,
- *    log w_denoise(s) (Eq. 4, natural log), 1, 0 x 5]
+ *    log w_denoise(s) (Eq. 4, natural log), 1, |S(p)| / 64, 0 x 4]
+ * (|S(p)| the size of the whole gathered set, which the plain fallback averages)
  * with z'_J the depth of the reference point in camera J.  Network: h = ReLU(W1 f + b1) (64),
  * (z_w, z_c) = W2 h + b2; w_s = softplus(z_w); conf = mean_s sigmoid(z_c);
  * learned output = sum w_s c_s / sum w_s; final output = learned if conf >= tau else the plain
@@ -506,7 +507,7 @@ int oc_learned_samples(const oc_clip *c, const oc_params *p, int O, int u, int v
     mat3_inverse(c->K + 9 * O, KOi);
     mat3_vec(KOi, uv1, ray);
     for (int i = 0; i < 3; ++i) xref[i] = dref * ray[i];
-    const double r = p->radius, Tn = p->T > 0 ? p->T : 1;
+    const double r = p->radius, Tn = p->T > 0 ? p->T : 1, ntot = (double)nacc / 64.0;
     for (int t = 0; t <= 2 * p->T && *n < OC_MAXS; ++t) {
         /* canonical frame order: O, O-1, O+1, O-2, O+2, ... */
         int J = O + (t == 0 ? 0 : ((t & 1) ? -(t + 1) / 2 : t / 2));
@@ -542,6 +543,7 @@ int oc_learned_samples(const oc_clip *c, const oc_params *p, int O, int u, int v
                 f[8] = ((double)dq - zJ) / r;
                 f[9] = log(oc_weight_denoise(s, sr, p->sigma_rgb, p->sigma_xyz, p->sigma_f));
                 f[10] = 1.0;
+                f[11] = ntot;
                 ++*n;
             }
         }

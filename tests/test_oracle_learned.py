@@ -61,7 +61,15 @@ def test_features_in_canonical_order_have_the_closed_form_on_exact_shift():
         assert f[s, 7] == pytest.approx(dJ / T)
         assert f[s, 8] == pytest.approx(0.0, abs=1e-9)
         assert f[s, 9] == pytest.approx(-dJ ** 2 / (2 * prm.sigma_f ** 2), abs=1e-12)
-        assert f[s, 10] == 1.0 and not f[s, 11:].any()
+        assert f[s, 10] == 1.0 and f[s, 11] == nn / 64.0 and not f[s, 12:].any()
+
+
+def test_set_size_feature_is_the_whole_gathered_set(tiny):
+    c, v, prm = tiny
+    feat, col, n, plain = oracle.learned_crop(v, prm, 4, crop=(0, 0, 64, 36))
+    full = oracle.gather_filter(v, prm, 4)
+    has = n > 0
+    np.testing.assert_array_equal(feat[..., 0, 11][has], full.nacc[has] / 64.0)
 
 
 def test_cap_keeps_the_first_64_in_canonical_order():
@@ -72,6 +80,7 @@ def test_cap_keeps_the_first_64_in_canonical_order():
     full = oracle.gather_filter(v, prm, 4, crop=(20, 12, 4, 3))
     assert (full.nacc > 64).all()
     assert (n == 64).all()
+    np.testing.assert_array_equal(feat[:, :, :, 11], np.repeat((full.nacc / 64.0)[..., None], 64, -1))
     rank = {0: 0, -1: 1, 1: 2, -2: 3, 2: 4, -3: 5, 3: 6, -4: 7, 4: 8}
     for y in range(3):
         for x in range(4):
