@@ -31,6 +31,7 @@ WORKLOADS = {
     "aperture-hd": (1280, 720, 60, 15, 7, 15, 8, 1),  # 720p virtual aperture, +-15 frames
     "batch": (0, 0, 0, 15, 7, 0, 0, 0),              # 8 uneven clips in one plan (sizes by seed)
     "learned": (1920, 1080, 68, 30, 7, 30, 8, 2),    # learned weights, trained on generated clips
+    "learned-hd": (1280, 720, 60, 15, 7, 15, 8, 2),  # same network, evaluated at 720p +-15
 }
 W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE = WORKLOADS["fhd"]
 APERTURE, LENS, CAP = 0.05, 16, 31
@@ -443,7 +444,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    if args.workload in ("batch", "learned"):
+    if args.workload in ("batch", "learned", "learned-hd"):
         fn = run_batch if args.workload == "batch" else run_learned
         line = fn(args, ss, torch, dev, stream, world, rank)
         if rank == 0:

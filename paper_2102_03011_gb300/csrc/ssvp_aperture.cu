@@ -159,15 +159,19 @@ __global__ void __launch_bounds__(kApThreads, 4) aperture_kernel(const GatherArg
             // error scale of the FP32 offsets: |o_fp32 - o| <= 8 u (|dz| Gm + Em)
             const float Gm = (fabsf(gx.hi) + (float)(x1c - bx0) + fabsf(gy.hi) + (float)(y1c - by0)) * fmaxf(ifx, ify);
             const float Em = zh * (fabsf(ex.hi) + (float)(x1c - bx0) + fabsf(ey.hi) + (float)(y1c - by0)) * fmaxf(ifx, ify);
+            // error of the FP32 fast path on diff = q^2 - a(t)^2: |err| <= 4 (a + E) E with
+            // E = 8 u (|dz| c1 + |o.b| c3 + c2) bounding both the offset error (8 u (|dz| Gm + Em))
+            // and the cone-radius error from t (slope 8 u (d_ref + |dz / b_z| + |o.b| foot))
+            const float c1 = Gm + slope * fabsf(inv_bz), c2 = Em + slope * dref, c3 = slope * foot;
             const long long jbase = (long long)J * P.fstride;
             for (int qy = y0c; qy <= y1c; ++qy) {
                 const float jf = (float)(qy - by0);
                 const float Gy = fmaf(jf, ify, gyf), Ey = fmaf(jf, ziy, eyf);
                 const long long rowb = jbase + (long long)(qy + kPad) * P.pitch + kPad;
-                for (int qx = x0c; qx <= x1c; ++qx) {
+                float iff = (float)(x0c - bx0);
+                for (int qx = x0c; qx <= x1c; ++qx, iff += 1.0f) {
+                    // invalid depth is NaN: it fails both comparisons below
                     const float d = __ldg(P.depth + rowb + qx);
-                    if (!(d > 0.0f)) continue;  // NaN: invalid depth
-                    const float iff = (float)(qx - bx0);
                     const float dz = (d - zh) - zl;
                     float ox = fmaf(dz, fmaf(iff, ifx, gxf), fmaf(iff, zix, exf));
                     float oy = fmaf(dz, Gy, Ey);
@@ -176,9 +180,8 @@ __global__ void __launch_bounds__(kApThreads, 4) aperture_kernel(const GatherArg
                     float t = fmaf(dz, inv_bz, dref) + ob * foot;
                     float ar = fmaf(slope, fabsf(z0 - t), a0);
                     float diff = p2 - ar * ar;
-                    const float eo = 8.0f * kU * fmaf(fabsf(dz), Gm, Em);
-                    const float et = 8.0f * kU * (fabsf(dref) + fabsf(dz * inv_bz) + fabsf(ob * foot));
-                    if (fabsf(diff) <= 4.0f * (ar + eo) * (eo + slope * et) + 1e-12f * ar * ar) {
+                    const float E = 8.0f * kU * fmaf(fabsf(dz), c1, fmaf(fabsf(ob), c3, c2));
+                    if (fabsf(diff) <= 4.0f * (ar + E) * E) {
                         // near the cone surface: recompute the offsets in double-float
                         const df dzd = fast_two_sum(d - zh, -zl);
                         const df Gd = df_add_f(gx, iff), Ed = df_add_f(ex, iff);

@@ -1062,9 +1062,9 @@ int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, co
     if ((rc = mlp_alloc(ctx)) != SSVP_OK) return rc;
     Rng rng{cfg->seed};
     if (cfg->init || !ctx->mlp_set) {
-        // He-normal W1 (11 non-zero inputs), W2; zero biases
+        // He-normal W1 (12 non-zero inputs), W2; zero biases
         std::vector<float> W1(1024), b1(64, 0.0f), W2(128), b2(2, 0.0f);
-        for (auto &x : W1) x = (float)(rng.normal() * std::sqrt(2.0 / 11.0));
+        for (auto &x : W1) x = (float)(rng.normal() * std::sqrt(2.0 / 12.0));
         for (auto &x : W2) x = (float)(rng.normal() * std::sqrt(2.0 / 64.0));
         if ((rc = ssvp_set_mlp(ctx, W1.data(), b1.data(), W2.data(), b2.data())) != SSVP_OK) return rc;
     }

@@ -47,7 +47,8 @@ constexpr int kTileX = 32, kTileY = SSVP_TILE_Y, kThreads = kTileX * kTileY;
 constexpr int kMaxSamples = 64;  // learned filter: capped sample set
 constexpr float kLn2 = 0.6931471805599453f;
 
-// Features of one accepted sample for the learned filter (16 BF16 values) and its colour.
+// Features of one accepted sample for the learned filter (16 BF16 values) and its colour;
+// feature 11 (the size of the whole set) is filled in once the pixel's gather is complete.
 __device__ __forceinline__ void store_sample(const GatherArgs &a, long long crop_idx, int slot, float3 c, float er,
                                              float eg, float eb, float dist_r, float dj_t, float dz_r, float logw) {
     const float f[16] = {c.x, c.y, c.z, er, eg, eb, dist_r, dj_t, dz_r, logw, 1.0f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -284,7 +285,13 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
         o[0] = o_r;
         o[1] = o_g;
         o[2] = o_b;
-        if (LEARN) a.nsamp_out[crop_idx] = n_feat;
+        if (LEARN) {
+            a.nsamp_out[crop_idx] = n_feat;
+            // feature 11: size of the whole gathered set (what the plain fallback averages) / 64
+            const __nv_bfloat16 nb = __float2bfloat16_rn((float)n_acc * (1.0f / 64.0f));
+            const unsigned short nbits = *reinterpret_cast<const unsigned short *>(&nb);
+            for (int s = 0; s < n_feat; ++s) a.feat_out[(crop_idx * kMaxSamples + s) * 16 + 11] = nbits;
+        }
         if (DEBUG && a.pixel_stats) {
             int32_t *ps = a.pixel_stats + crop_idx * 3;
             ps[0] = n_acc;
