@@ -12,7 +12,10 @@ Readings of the paper used here (Sec. "Denoising", Eq. 4; Sec. "Sample Gathering
   * depth is camera-space z; integer pixel coordinates are pixel centres;
   * the radius r defaults to 0.5 % of the clip's lower-median valid input depth;
   * colour is in [0, 1], so sigma_rgb = 40 / 255; sigma_f = 6 frames; sigma_xyz = r;
-  * the k x k window is centred on floor(x + 0.5) of the projected reference point.
+  * the k x k window is centred on floor(x + 0.5) of the projected reference point;
+  * the frustum gather (Eq. 1-2) takes Eq. 2's L1 distance as printed, strict, plus the frustum's
+    own depth range (near, far) = (0.01, 1000) of Eq. 1, l = 3 pixels; it tests every pixel of
+    every window frame.
 """
 from __future__ import annotations
 
@@ -28,6 +31,7 @@ _LIB_PATH = os.path.join(_HERE, "libssvp_oracle.so")
 _lib = None
 
 MODE_DENOISE, MODE_APERTURE, MODE_MEAN = 0, 1, 3
+GATHER_WINDOW, GATHER_FRUSTUM = 0, 1
 CODE_OUT, CODE_INVALID, CODE_REJECT, CODE_ACCEPT, CODE_BAND = 0, 1, 2, 3, 8
 
 
@@ -42,7 +46,8 @@ class _Params(ctypes.Structure):
                 ("lens_samples", ctypes.c_int32), ("radius", ctypes.c_double), ("sigma_rgb", ctypes.c_double),
                 ("sigma_xyz", ctypes.c_double), ("sigma_f", ctypes.c_double), ("band_rel", ctypes.c_double),
                 ("tie_band", ctypes.c_double), ("aperture", ctypes.c_double), ("focal_depth", ctypes.c_double),
-                ("a0", ctypes.c_double), ("cap", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("a0", ctypes.c_double), ("cap", ctypes.c_int32), ("gather", ctypes.c_int32),
+                ("frustum_l", ctypes.c_double), ("near_plane", ctypes.c_double), ("far_plane", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -75,6 +80,9 @@ def _load():
         lib.oc_bruteforce.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, u8p]
         lib.oc_bruteforce.restype = ctypes.c_longlong
+        lib.oc_frustum_filter.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, i64p, i32p,
+                                          ctypes.POINTER(ctypes.c_uint64), u8p]
         lib.oc_learned_samples.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int), dp]
         lib.oc_learned_samples.restype = ctypes.c_int
@@ -111,6 +119,10 @@ class Params:
     a0: float | None = None             # None: half a pixel footprint at the focal depth (0.5 z0 / fx)
     lens_samples: int = 16
     cap: int = 31
+    gather: int = GATHER_WINDOW
+    frustum_l: float = 3.0              # Eq. 1-2: frustum size in pixels (the paper's usual l = 3)
+    near_plane: float = 0.01            # Eq. 1: the paper's near and far depths
+    far_plane: float = 1000.0
 
     def c_struct(self, fx: float) -> _Params:
         s = _Params()
@@ -122,6 +134,8 @@ class Params:
         s.aperture, s.focal_depth = self.aperture, self.focal_depth
         s.a0 = 0.5 * self.focal_depth / fx if self.a0 is None else self.a0
         s.cap = self.cap
+        s.gather = self.gather
+        s.frustum_l, s.near_plane, s.far_plane = self.frustum_l, self.near_plane, self.far_plane
         return s
 
 
@@ -231,6 +245,37 @@ def bruteforce(view: ClipView, prm: Params, O: int, u: int, v: int, J: int) -> n
     ps = prm.c_struct(float(view.K[O, 0, 0]))
     _load().oc_bruteforce(ctypes.byref(view.c), ctypes.byref(ps), O, u, v, J, _p(acc, ctypes.c_uint8))
     return acc
+
+
+@dataclass
+class FrustumResult:
+    rgb: np.ndarray          # (ch, cw, 3) float64
+    sumw: np.ndarray         # (ch, cw)
+    nacc: np.ndarray         # (ch, cw) int64
+    count: np.ndarray | None = None  # (ch, cw, 2T+1) int32: samples per window frame
+    hash: np.ndarray | None = None   # (ch, cw, 2T+1) uint64: sum of mix64(qy * W + qx + 1)
+    band: np.ndarray | None = None   # (ch, cw, 2T+1) uint8: a tested pixel lies in the tie band
+
+
+def frustum_filter(view: ClipView, prm: Params, O: int, crop=None, membership: bool = False) -> FrustumResult:
+    """Frustum gather (Eq. 1-2) and the Eq. 3/4 filter on output frame O over crop (x0, y0, w, h)."""
+    x0, y0, cw, ch = crop if crop is not None else (0, 0, view.W, view.H)
+    ns = 2 * prm.T + 1
+    out = np.zeros((ch, cw, 3))
+    sumw = np.zeros((ch, cw))
+    nacc = np.zeros((ch, cw), np.int64)
+    cnt = hsh = bnd = None
+    if membership:
+        cnt = np.zeros((ch, cw, ns), np.int32)
+        hsh = np.zeros((ch, cw, ns), np.uint64)
+        bnd = np.zeros((ch, cw, ns), np.uint8)
+    ps = prm.c_struct(float(view.K[O, 0, 0]))
+    rc = _load().oc_frustum_filter(ctypes.byref(view.c), ctypes.byref(ps), O, x0, y0, cw, ch,
+                                   _p(out, ctypes.c_double), _p(sumw, ctypes.c_double), _p(nacc, ctypes.c_int64),
+                                   _p(cnt, ctypes.c_int32), _p(hsh, ctypes.c_uint64), _p(bnd, ctypes.c_uint8))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments (code {rc})")
+    return FrustumResult(out, sumw, nacc, cnt, hsh, bnd)
 
 
 def psnr(a, b) -> float:

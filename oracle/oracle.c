@@ -36,6 +36,15 @@
  *   (d_q / fx_J)^2 for a camera without skew.  Output sum w c / sum w (c_ref if nothing is
  *   accepted).
  *
+ * Frustum gather (Sec. "Sample Gathering", Eq. 1-2), the paper's own gather:
+ *   pixel (u, v) of O owns the frustum V of Eq. 1, the square of side l around the pixel swept
+ *   from O-camera depth near to far.  A pixel q of frame J (in the temporal window) with valid
+ *   depth d_q is a sample when X_q = G_{O<-J} (q_x d_q, q_y d_q, d_q, 1) has O depth in
+ *   (near, far) and its O pixel (u', v') satisfies |u - u'| + |v - v'| < l / 2 (Eq. 2 as
+ *   printed: the L1 distance, strict).  Every pixel of every window frame is tested; the paper's
+ *   rasterised hull V_J only skips pixels that fail.  The same Eq. 4 weights and Eq. 3 mean
+ *   follow (an invalid reference depth gives c_ref, as in the window gather).
+ *
  * Built with -ffp-contract=off: every product and sum is rounded on its own.
  */
 #include <math.h>
@@ -64,7 +73,9 @@ typedef struct {
     double focal_depth;  /* z0 */
     double a0;           /* cone waist */
     int32_t cap;         /* aperture footprint cap per axis (pixels) */
-    int32_t pad_;
+    int32_t gather;      /* 0 depth-seeded window (or the aperture cone), 1 frustum (Eq. 1-2) */
+    double frustum_l;    /* frustum size l in pixels (Eq. 1) */
+    double near_plane, far_plane;  /* frustum depth range (Eq. 1) */
 } oc_params;
 
 /* membership codes (low 3 bits) and band flag */
@@ -399,10 +410,119 @@ int oc_gather_filter(const oc_clip *c, const oc_params *p, int O, int x0, int y0
     return 0;
 }
 
+/* ================================================================== frustum gather (Eq. 1-2) */
+
+/* SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014): an order-independent
+ * membership checksum sums it over the linear indices qy * W + qx + 1 of a sample set. */
+static uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+/* Is X (O-camera coordinates) inside the frustum of pixel (u, v)?  *band is set when X lies
+ * within tie_band pixels of the L1 bound or within band_rel of the near or far depth. */
+static int in_frustum(const double *KO, const double *X, int u, int v, const oc_params *p, int *band) {
+    const double z = X[2];
+    *band = fabs(z - p->near_plane) <= p->band_rel * p->near_plane || fabs(z - p->far_plane) <= p->band_rel * p->far_plane;
+    if (!(z > p->near_plane && z < p->far_plane)) return 0;
+    const double up = (KO[0] * X[0] + KO[1] * X[1] + KO[2] * X[2]) / z;
+    const double vp = (KO[4] * X[1] + KO[5] * X[2]) / z;
+    const double l1 = fabs((double)u - up) + fabs((double)v - vp);
+    if (fabs(l1 - 0.5 * p->frustum_l) <= p->tie_band) *band = 1;
+    return l1 < 0.5 * p->frustum_l;
+}
+
+/*
+ * Frustum gather and filter of the crop [x0, x0+cw) x [y0, y0+ch) of output frame O.
+ * Outputs (row-major over the crop): out_rgb cw*ch*3, sumw, nacc.  mem_count, mem_hash and
+ * mem_band may be NULL; otherwise per (pixel, slot J = O-T+j): the number of samples from J,
+ * the wrapping sum of mix64(qy * W + qx + 1) over them, and 1 when any tested pixel of J lies in
+ * the tie band.  A pixel with an invalid reference depth gets c_ref and empty records.
+ */
+int oc_frustum_filter(const oc_clip *c, const oc_params *p, int O, int x0, int y0, int cw, int ch, double *out_rgb,
+                      double *out_sumw, int64_t *out_nacc, int32_t *mem_count, uint64_t *mem_hash, uint8_t *mem_band) {
+    if (p->T < 0 || O < 0 || O >= c->F || !(p->frustum_l > 0) || !(p->near_plane > 0) ||
+        !(p->far_plane > p->near_plane))
+        return -1;
+    const int ns = 2 * p->T + 1, W = c->W, H = c->H;
+    double *Gt = (double *)malloc(sizeof(double) * 12 * ns);
+    if (!Gt) return -2;
+    for (int j = 0; j < ns; ++j) {
+        int J = O - p->T + j;
+        double P[12];
+        if (J < 0 || J >= c->F) continue;
+        oc_compose(c->K + 9 * O, c->w2c + 12 * O, c->K + 9 * J, c->w2c + 12 * J, J == O, P, Gt + 12 * j);
+    }
+    const double *KO = c->K + 9 * O;
+    double KOi[9];
+    mat3_inverse(KO, KOi);
+    long long n = (long long)cw * ch;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long i = 0; i < n; ++i) {
+        const int u = x0 + (int)(i % cw), v = y0 + (int)(i / cw);
+        const size_t pix = ((size_t)O * H + v) * W + u;
+        const float dref = c->depth[pix];
+        double sref[7], acc[3] = {0, 0, 0}, sw = 0.0;
+        int64_t cnt = 0;
+        for (int ch3 = 0; ch3 < 3; ++ch3) sref[ch3] = c->rgb[3 * pix + ch3];
+        if (mem_count)
+            for (int j = 0; j < ns; ++j) {
+                mem_count[i * ns + j] = 0;
+                mem_hash[i * ns + j] = 0;
+                mem_band[i * ns + j] = 0;
+            }
+        if (valid_depth(dref)) {
+            double uv1[3] = {u, v, 1.0}, ray[3];
+            mat3_vec(KOi, uv1, ray);
+            for (int a = 0; a < 3; ++a) sref[3 + a] = (double)dref * ray[a];
+            sref[6] = O;
+            for (int j = 0; j < ns; ++j) {
+                const int J = O - p->T + j;
+                if (J < 0 || J >= c->F) continue;
+                const double *G = Gt + 12 * j;
+                int32_t mc = 0;
+                uint64_t mh = 0;
+                uint8_t mb = 0;
+                for (int qy = 0; qy < H; ++qy)
+                    for (int qx = 0; qx < W; ++qx) {
+                        const size_t qi = ((size_t)J * H + qy) * W + qx;
+                        const float dq = c->depth[qi];
+                        if (!valid_depth(dq)) continue;
+                        double q3[3] = {qx * (double)dq, qy * (double)dq, (double)dq}, X[3];
+                        apply34(G, q3, X);
+                        int band;
+                        const int in = in_frustum(KO, X, u, v, p, &band);
+                        mb |= (uint8_t)band;
+                        if (!in) continue;
+                        double s[7] = {c->rgb[3 * qi], c->rgb[3 * qi + 1], c->rgb[3 * qi + 2], X[0], X[1], X[2], (double)J};
+                        const double w = p->mode == 3 ? 1.0
+                                                      : oc_weight_denoise(s, sref, p->sigma_rgb, p->sigma_xyz, p->sigma_f);
+                        for (int a = 0; a < 3; ++a) acc[a] += w * s[a];
+                        sw += w;
+                        ++mc;
+                        mh += mix64((uint64_t)qy * (uint64_t)W + (uint64_t)qx + 1u);
+                    }
+                cnt += mc;
+                if (mem_count) {
+                    mem_count[i * ns + j] = mc;
+                    mem_hash[i * ns + j] = mh;
+                    mem_band[i * ns + j] = mb;
+                }
+            }
+        }
+        for (int a = 0; a < 3; ++a) out_rgb[3 * i + a] = sw > 0.0 ? acc[a] / sw : sref[a];
+        out_sumw[i] = sw;
+        out_nacc[i] = cnt;
+    }
+    free(Gt);
+    return 0;
+}
+
 /*
  * Brute force: test EVERY pixel of frame J against the radius around x_ref of pixel (u, v) of
- * frame O, or against its aperture cone in mode 1 (no window, no box).  accept is H*W bytes
- * (1 accepted, 0 not); returns the count.
+ * frame O, against its aperture cone in mode 1 (no window, no box), or against its frustum when
+ * gather = 1.  accept is H*W bytes (1 accepted, 0 not); returns the count.
  */
 long long oc_bruteforce(const oc_clip *c, const oc_params *p, int O, int u, int v, int J, uint8_t *accept) {
     const int W = c->W, H = c->H;
@@ -424,7 +544,10 @@ long long oc_bruteforce(const oc_clip *c, const oc_params *p, int O, int u, int 
             double q3[3] = {qx * (double)dq, qy * (double)dq, (double)dq}, X[3];
             apply34(G, q3, X);
             int ok;
-            if (p->mode == 1) {
+            if (p->gather == 1) {
+                int band;
+                ok = in_frustum(c->K + 9 * O, X, u, v, p, &band);
+            } else if (p->mode == 1) {
                 double xr = X[0] * ray[0] + X[1] * ray[1] + X[2] * ray[2];
                 double t = xr / rr;
                 double cr0 = X[1] * ray[2] - X[2] * ray[1], cr1 = X[2] * ray[0] - X[0] * ray[2],
