@@ -13,6 +13,9 @@ Readings of the paper used here (Sec. "Denoising", Eq. 4; Sec. "Sample Gathering
   * the radius r defaults to 0.5 % of the clip's lower-median valid input depth;
   * colour is in [0, 1], so sigma_rgb = 40 / 255; sigma_f = 6 frames; sigma_xyz = r;
   * the k x k window is centred on floor(x + 0.5) of the projected reference point;
+  * Eq. 5's blurriness is the sum over a frame of the forward-difference gradient magnitudes (L2
+    over the colour channels and both axes, pixels with a right and a lower neighbour); Eq. 10's
+    shutter function replaces the weight entirely;
   * the frustum gather (Eq. 1-2) takes Eq. 2's L1 distance as printed, strict, plus the frustum's
     own depth range (near, far) = (0.01, 1000) of Eq. 1, l = 3 pixels; it tests every pixel of
     every window frame.
@@ -30,7 +33,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libssvp_oracle.so")
 _lib = None
 
-MODE_DENOISE, MODE_APERTURE, MODE_MEAN = 0, 1, 3
+MODE_DENOISE, MODE_APERTURE, MODE_MEAN, MODE_DEBLUR, MODE_SHUTTER = 0, 1, 3, 4, 5
 GATHER_WINDOW, GATHER_FRUSTUM = 0, 1
 CODE_OUT, CODE_INVALID, CODE_REJECT, CODE_ACCEPT, CODE_BAND = 0, 1, 2, 3, 8
 
@@ -47,7 +50,8 @@ class _Params(ctypes.Structure):
                 ("sigma_xyz", ctypes.c_double), ("sigma_f", ctypes.c_double), ("band_rel", ctypes.c_double),
                 ("tie_band", ctypes.c_double), ("aperture", ctypes.c_double), ("focal_depth", ctypes.c_double),
                 ("a0", ctypes.c_double), ("cap", ctypes.c_int32), ("gather", ctypes.c_int32),
-                ("frustum_l", ctypes.c_double), ("near_plane", ctypes.c_double), ("far_plane", ctypes.c_double)]
+                ("frustum_l", ctypes.c_double), ("near_plane", ctypes.c_double), ("far_plane", ctypes.c_double),
+                ("frame_w", ctypes.POINTER(ctypes.c_double)), ("slot_w", ctypes.POINTER(ctypes.c_double))]
 
 
 def build(force: bool = False) -> str:
@@ -80,6 +84,7 @@ def _load():
         lib.oc_bruteforce.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, u8p]
         lib.oc_bruteforce.restype = ctypes.c_longlong
+        lib.oc_frame_sharpness.argtypes = [ctypes.POINTER(_Clip), dp]
         lib.oc_frustum_filter.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, i64p, i32p,
                                           ctypes.POINTER(ctypes.c_uint64), u8p]
@@ -123,6 +128,8 @@ class Params:
     frustum_l: float = 3.0              # Eq. 1-2: frustum size in pixels (the paper's usual l = 3)
     near_plane: float = 0.01            # Eq. 1: the paper's near and far depths
     far_plane: float = 1000.0
+    frame_w: np.ndarray | None = None   # MODE_DEBLUR: Eq. 5's per-frame factor (F values), e.g. frame_sharpness()
+    slot_w: np.ndarray | None = None    # MODE_SHUTTER: Eq. 10's xi(J - O) for J = O-T .. O+T (2T+1 values)
 
     def c_struct(self, fx: float) -> _Params:
         s = _Params()
@@ -136,6 +143,14 @@ class Params:
         s.cap = self.cap
         s.gather = self.gather
         s.frustum_l, s.near_plane, s.far_plane = self.frustum_l, self.near_plane, self.far_plane
+        keep = []
+        for name in ("frame_w", "slot_w"):
+            a = getattr(self, name)
+            if a is not None:
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                keep.append(a)
+                setattr(s, name, _p(a, ctypes.c_double))
+        s._keep = keep  # the arrays live as long as the struct
         return s
 
 
@@ -276,6 +291,13 @@ def frustum_filter(view: ClipView, prm: Params, O: int, crop=None, membership: b
     if rc != 0:
         raise ValueError(f"oracle rejected the arguments (code {rc})")
     return FrustumResult(out, sumw, nacc, cnt, hsh, bnd)
+
+
+def frame_sharpness(view: ClipView) -> np.ndarray:
+    """Eq. 5's blurriness measure per frame: the sum of forward-difference gradient magnitudes."""
+    out = np.zeros(view.F)
+    _load().oc_frame_sharpness(ctypes.byref(view.c), _p(out, ctypes.c_double))
+    return out
 
 
 def psnr(a, b) -> float:

@@ -45,6 +45,12 @@
  *   rasterised hull V_J only skips pixels that fail.  The same Eq. 4 weights and Eq. 3 mean
  *   follow (an invalid reference depth gives c_ref, as in the window gather).
  *
+ * Per-frame weights (Sec. "Deblurring", Eq. 5; Sec. "Computational scene-space shutters", Eq. 10):
+ *   mode 4 multiplies the Eq. 4 weight by the sum over frame J of the gradient magnitudes
+ *   |grad I_J(q)| (forward differences, the L2 norm over the three colour channels and both
+ *   axes, summed over the pixels that have a right and a lower neighbour); mode 5 replaces the
+ *   weight by the shutter function xi(J - O).  Both apply to either gather.
+ *
  * Built with -ffp-contract=off: every product and sum is rounded on its own.
  */
 #include <math.h>
@@ -76,6 +82,8 @@ typedef struct {
     int32_t gather;      /* 0 depth-seeded window (or the aperture cone), 1 frustum (Eq. 1-2) */
     double frustum_l;    /* frustum size l in pixels (Eq. 1) */
     double near_plane, far_plane;  /* frustum depth range (Eq. 1) */
+    const double *frame_w;  /* mode 4: per input frame J the blurriness factor of Eq. 5 (F values) */
+    const double *slot_w;   /* mode 5: the shutter function xi(J - O) of Eq. 10 at J = O-T+j (2T+1 values) */
 } oc_params;
 
 /* membership codes (low 3 bits) and band flag */
@@ -188,6 +196,38 @@ double oc_filter(const double *S, int n, const double *sref, int mode, double si
 }
 
 static int valid_depth(float d) { return isfinite(d) && d > 0.0f; }
+
+/* Weight of an accepted sample s (7-vector) against s_ref from window frame J (slot j) for the
+ * Eq. 4 based modes: 0 denoise, 3 mean, 4 deblurring (Eq. 5), 5 computational shutter (Eq. 10). */
+static double sample_weight(const oc_params *p, const double *s, const double *sr, int J, int j) {
+    switch (p->mode) {
+    case 3: return 1.0;
+    case 5: return p->slot_w ? p->slot_w[j] : 1.0;
+    case 4: return oc_weight_denoise(s, sr, p->sigma_rgb, p->sigma_xyz, p->sigma_f) * (p->frame_w ? p->frame_w[J] : 1.0);
+    default: return oc_weight_denoise(s, sr, p->sigma_rgb, p->sigma_xyz, p->sigma_f);
+    }
+}
+
+/* Eq. 5's blurriness measure: per frame the sum of the gradient magnitudes (see above); out F values. */
+void oc_frame_sharpness(const oc_clip *c, double *out) {
+    const int W = c->W, H = c->H;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int f = 0; f < c->F; ++f) {
+        double sum = 0.0;
+        for (int y = 0; y + 1 < H; ++y)
+            for (int x = 0; x + 1 < W; ++x) {
+                const float *a = c->rgb + 3 * (((size_t)f * H + y) * W + x);
+                const float *r = a + 3, *d = a + 3 * (size_t)W;
+                double g2 = 0.0;
+                for (int ch = 0; ch < 3; ++ch) {
+                    const double gx = (double)r[ch] - a[ch], gy = (double)d[ch] - a[ch];
+                    g2 += gx * gx + gy * gy;
+                }
+                sum += sqrt(g2);
+            }
+        out[f] = sum;
+    }
+}
 
 /* ------------------------------------------------------------------ gather + filter, one pixel */
 
@@ -336,13 +376,9 @@ static void pixel(const oc_clip *c, const oc_params *p, int O, int u, int v, con
                             code = acc_ok ? OC_ACCEPT : OC_REJECT;
                             if (fabs(sqrt(d2) - p->radius) <= p->band_rel * p->radius) code |= OC_BAND;
                             if (acc_ok) {
-                                if (p->mode == 3) {
-                                    w = 1.0;
-                                } else {
-                                    double s[7] = {c->rgb[3 * qi], c->rgb[3 * qi + 1], c->rgb[3 * qi + 2], X[0], X[1], X[2], J};
-                                    double sr[7] = {cref[0], cref[1], cref[2], xref[0], xref[1], xref[2], O};
-                                    w = oc_weight_denoise(s, sr, p->sigma_rgb, p->sigma_xyz, p->sigma_f);
-                                }
+                                double s[7] = {c->rgb[3 * qi], c->rgb[3 * qi + 1], c->rgb[3 * qi + 2], X[0], X[1], X[2], J};
+                                double sr[7] = {cref[0], cref[1], cref[2], xref[0], xref[1], xref[2], O};
+                                w = sample_weight(p, s, sr, J, j);
                             }
                         } else {
                             /* foot point depth t and distance to the axis (textbook point-line distance) */
@@ -496,8 +532,7 @@ int oc_frustum_filter(const oc_clip *c, const oc_params *p, int O, int x0, int y
                         mb |= (uint8_t)band;
                         if (!in) continue;
                         double s[7] = {c->rgb[3 * qi], c->rgb[3 * qi + 1], c->rgb[3 * qi + 2], X[0], X[1], X[2], (double)J};
-                        const double w = p->mode == 3 ? 1.0
-                                                      : oc_weight_denoise(s, sref, p->sigma_rgb, p->sigma_xyz, p->sigma_f);
+                        const double w = sample_weight(p, s, sref, J, j);
                         for (int a = 0; a < 3; ++a) acc[a] += w * s[a];
                         sw += w;
                         ++mc;
