@@ -32,11 +32,20 @@ WORKLOADS = {
     "batch": (0, 0, 0, 15, 7, 0, 0, 0),              # 8 uneven clips in one plan (sizes by seed)
     "learned": (1920, 1080, 68, 30, 7, 30, 8, 2),    # learned weights, trained on generated clips
     "learned-hd": (1280, 720, 60, 15, 7, 15, 8, 2),  # same network, evaluated at 720p +-15
+    "frustum": (1920, 1080, 68, 30, 7, 30, 1, 4),    # the paper's frustum gather (Eq. 1-2), 1080p +-30
+    "frustum-hd": (1280, 720, 60, 15, 7, 15, 1, 4),  # frustum gather at 720p +-15
+    "deblur": (1920, 1080, 68, 30, 7, 30, 8, 5),     # Eq. 5 weights, every 4th frame shaken, 1080p +-30
+    "shutter": (1920, 1080, 68, 30, 7, 30, 8, 6),    # Eq. 10 long exposure (box shutter), 1080p +-30
 }
 W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE = WORKLOADS["fhd"]
 APERTURE, LENS, CAP = 0.05, 16, 31
 RADIUS_REL = 0.005
+FRUSTUM_L, FRUSTUM_SIGMA_XYZ_REL = 3.0, 0.03  # frustum gather: l = 3 px, sigma_xyz = 3 % of the median depth
+# deblurring (Sec. "Deblurring"): the paper's sigma_rgb = 200 (0-255 scale) and sigma_f = 20; image
+# noise 0.01 and a 1 degree camera shake during every 4th frame's exposure
+DEBLUR_SIGMA_RGB, DEBLUR_SIGMA_F, DEBLUR_SIGMA_IMG, DEBLUR_SHAKE_DEG = 200.0 / 255.0, 20.0, 0.01, 1.0
 BYTES_PER_CANDIDATE = {"fp32": 16, "fp16": 12}
+COLOUR_BYTES = {"fp32": 16, "fp16": 8}
 
 
 def shard(rank: int, world: int):
@@ -136,10 +145,38 @@ class ClockSampler:
 
 def _workload_clip(seed):
     import synth
+    if MODE == 5:
+        c = synth.make_clip("room", W, H, F, seed=seed, sigma_img=DEBLUR_SIGMA_IMG)
+        return synth.shake_blur(c, range(2, F, 4), shake_deg=DEBLUR_SHAKE_DEG, seed=seed)
     return synth.make_clip("room", W, H, F, seed=seed)
 
 
+def _shutter_xi():
+    """The long exposure of Sec. "Computational scene-space shutters": a box over the window."""
+    return np.ones(2 * T + 1, np.float32)
+
+
+def _oracle_params(clip):
+    """The oracle's parameters for the current workload (window gather modes)."""
+    import oracle
+    if MODE == 5:
+        return oracle.default_params(clip.depth, mode=oracle.MODE_DEBLUR, k=K_WIN, T=T, radius_rel=RADIUS_REL,
+                                     sigma_rgb=DEBLUR_SIGMA_RGB, sigma_f=DEBLUR_SIGMA_F,
+                                     frame_w=oracle.frame_sharpness(oracle.ClipView.of(clip)))  # raw Eq. 5 factor
+    if MODE == 6:
+        return oracle.default_params(clip.depth, mode=oracle.MODE_SHUTTER, k=K_WIN, T=T, radius_rel=RADIUS_REL,
+                                     slot_w=_shutter_xi().astype(np.float64))
+    return oracle.default_params(clip.depth, k=K_WIN, T=T, radius_rel=RADIUS_REL)
+
+
 def _config(colour):
+    if MODE == 4:
+        return {"workload": f"frustum-{W}x{H}-pm{T}-l3-{colour}", "W": W, "H": H, "frames": F,
+                "out_frames_per_step": N_OUT, "half_window": T, "gather": "frustum (Eq. 1-2), l = 3 px, L1 test",
+                "near_far": [0.01, 1000.0], "sigma_xyz": f"{FRUSTUM_SIGMA_XYZ_REL:g} x median depth",
+                "scene": "synthetic 6 planes + 4 boxes, hand-held path, depth noise 2%, image noise 0.05",
+                "colour": colour, "l2": "no flush: packed input planes exceed the 129 MB L2",
+                "note": "frames beyond O+T are never read"}
     if MODE == 1:
         return {"workload": f"aperture-{W}x{H}-pm{T}-{colour}", "W": W, "H": H, "frames": F,
                 "out_frames_per_step": N_OUT, "half_window": T, "aperture": APERTURE, "focal_plane": "median depth",
@@ -147,6 +184,16 @@ def _config(colour):
                 "scene": "synthetic 6 planes + 4 boxes, hand-held path, depth noise 2%, image noise 0.05",
                 "colour": colour, "l2": "no flush: packed input planes exceed the 129 MB L2",
                 "note": "frames beyond O+T are never read, so the clip stops at 68 frames"}
+    if MODE in (5, 6):
+        name = "deblur" if MODE == 5 else "shutter-box"
+        extra = ({"weights": "Eq. 5: Eq. 4 x the sample frame's gradient-magnitude sum", "sigma_rgb": "200/255",
+                  "sigma_f": DEBLUR_SIGMA_F, "sigma_xyz": "r", "image_noise": DEBLUR_SIGMA_IMG,
+                  "blur": f"camera shake of {DEBLUR_SHAKE_DEG:g} deg during the exposure of frames 2, 6, 10, ..."}
+                 if MODE == 5 else {"weights": "Eq. 10: w = xi(J - O), box over the window (long exposure)"})
+        return {"workload": f"{name}-{W}x{H}-pm{T}-k{K_WIN}-{colour}", "W": W, "H": H, "frames": F,
+                "out_frames_per_step": N_OUT, "half_window": T, "k": K_WIN, "radius": f"{RADIUS_REL:g} x median depth",
+                "scene": "synthetic 6 planes + 4 boxes, hand-held path, depth noise 2%", "colour": colour,
+                "l2": "no flush: packed input planes (~3.1 GB) exceed the 129 MB L2", **extra}
     return {"workload": f"denoise-{W}x{H}-pm{T}-k{K_WIN}-{colour}", "W": W, "H": H, "frames": F,
             "out_frames_per_step": N_OUT, "half_window": T, "k": K_WIN, "radius": f"{RADIUS_REL:g} x median depth",
             "scene": "synthetic 6 planes + 4 boxes, hand-held path, depth noise 2%, image noise 0.05",
@@ -162,6 +209,23 @@ def cpu_oracle_sample(clip, target_s=10.0, O=None, max_frames=None):
     max_frames = N_OUT if max_frames is None else max_frames
     v = oracle.ClipView.of(clip)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    if MODE == 4:
+        med = oracle.median_depth(clip.depth)
+        prm = oracle.Params(mode=oracle.MODE_DENOISE, k=1, T=T, radius=RADIUS_REL * med,
+                            sigma_xyz=FRUSTUM_SIGMA_XYZ_REL * med, gather=oracle.GATHER_FRUSTUM, frustum_l=FRUSTUM_L)
+        side = 4
+        while True:
+            crop = ((W - side) // 2, (H - side) // 2, side, side)
+            t0 = time.perf_counter()
+            res = oracle.frustum_filter(v, prm, O, crop=crop)
+            dt = time.perf_counter() - t0
+            if dt > target_s / 4 or 2 * side > min(W, H):
+                break
+            side *= 2
+        return dict(frames=1, crop=crop, seconds=dt, mpix_s=side * side / dt / 1e6, cores=cores, results=[res],
+                    examined=0, accepted=int(res.nacc.sum()),
+                    sample=f"{side}x{side} centre crop of output frame {O}, every pixel of every window frame "
+                           f"tested ({dt:.1f} s)")
     if MODE == 1:
         prm = oracle.Params(mode=oracle.MODE_APERTURE, k=K_WIN, T=T, aperture=APERTURE,
                             focal_depth=oracle.median_depth(clip.depth), lens_samples=LENS, cap=CAP)
@@ -177,7 +241,7 @@ def cpu_oracle_sample(clip, target_s=10.0, O=None, max_frames=None):
         return dict(frames=1, crop=crop, seconds=dt, mpix_s=side * side / dt / 1e6, cores=cores, results=[res],
                     examined=int(res.nexam.sum()), accepted=int(res.nacc.sum()),
                     sample=f"{side}x{side} centre crop of output frame {O} ({dt:.1f} s)")
-    prm = oracle.default_params(clip.depth, k=K_WIN, T=T, radius_rel=RADIUS_REL)
+    prm = _oracle_params(clip)
     results, dt = [], 0.0
     while len(results) < max_frames and (not results or dt < target_s):
         t0 = time.perf_counter()
@@ -466,6 +530,14 @@ def main():
     p.radius = -RADIUS_REL
     if MODE == 1:
         p.mode, p.aperture, p.focal_depth, p.lens_samples, p.cap = 1, APERTURE, 0.0, LENS, CAP
+    if MODE == 4:
+        # the radius is no gather bound here; sigma_xyz = 0 takes it, relative to the median depth
+        p.gather, p.frustum_l, p.radius, p.sigma_xyz = ss.SSVP_GATHER_FRUSTUM, FRUSTUM_L, -FRUSTUM_SIGMA_XYZ_REL, 0.0
+    if MODE == 5:
+        p.mode, p.sigma_rgb, p.sigma_f = ss.SSVP_MODE_DEBLUR, DEBLUR_SIGMA_RGB, DEBLUR_SIGMA_F
+    if MODE == 6:
+        p.mode = ss.SSVP_MODE_SHUTTER
+        ss.ssvp_set_shutter(ctx, _shutter_xi(), T)
 
     def barrier():
         if world > 1:
@@ -516,6 +588,25 @@ def main():
         psnr_out, psnr_in = psnr(outn[:1], lens), psnr(noisy[:1], lens)
         psnr_ref = "thin-lens render (256 rays/pixel) of the first output frame"
 
+    extra_quality = {}
+    if MODE == 5:
+        # the same clip through plain Eq. 4 with the same sigmas, outside the timed region
+        p.mode = ss.SSVP_MODE_DENOISE
+        ss.ssvp_gather_filter(ctx, p, [0])
+        plain = torch.empty_like(out)
+        ss.ssvp_read_output(ctx, 0, O_BEGIN, O_BEGIN + N_OUT, plain)
+        ss.ssvp_sync(ctx)
+        p.mode = ss.SSVP_MODE_DEBLUR
+        plainn = plain.cpu().numpy()
+        blurred = [i for i in range(N_OUT) if (O_BEGIN + i) in clip.meta.get("blurred", [])]
+        extra_quality = {"plain_eq4_vs_clean": psnr(plainn, clean),
+                         "blurred_output_frames": [O_BEGIN + i for i in blurred]}
+        if blurred:
+            extra_quality.update({
+                "deblur_on_blurred_frames": psnr(outn[blurred], clean[blurred]),
+                "plain_eq4_on_blurred_frames": psnr(plainn[blurred], clean[blurred]),
+                "input_on_blurred_frames": psnr(noisy[blurred], clean[blurred])})
+
     # ---------------- end to end through the C ABI with host buffers
     rgb_h = torch.from_numpy(clip.rgb).pin_memory()
     dep_h = torch.from_numpy(clip.depth).pin_memory()
@@ -542,12 +633,24 @@ def main():
     h2d = clip.rgb.nbytes + clip.depth.nbytes
     d2h = out_h.numel() * 4
     frames_per_chunk = max(1, min(F, (256 << 20) // (W * H * 16)))
-    e2e_launches = -(-F // frames_per_chunk) + 6 + 1
+    e2e_launches = -(-F // frames_per_chunk) + 6 + 1 + 2 + 1  # packs, median passes, depth range, gradient sums, gather
 
     peaks, peak_kind = _peaks()
     bpc = BYTES_PER_CANDIDATE[args.colour]
     kernel_ms = float(np.mean(step_ms))
     achieved = examined * bpc / (kernel_ms / 1e3) / 1e9
+    accounting = (f"{bpc} B per examined candidate (colour + depth touched), {peak_kind} peak; "
+                  "frac > 1 because window loads are served from L1 (traffic = DRAM bytes per launch)")
+    alu_ops = 8
+    alu_note = "8 FP32 operations per examined candidate (the distance test)"
+    if MODE == 4:
+        cb = COLOUR_BYTES[args.colour]
+        achieved = (4 * examined + cb * accepted) / (kernel_ms / 1e3) / 1e9
+        accounting = (f"4 B depth per examined candidate + {cb} B colour per sample, {peak_kind} peak; the hull "
+                      "pixels of neighbouring output pixels overlap, so most loads are cache hits")
+        alu_ops = 11
+        alu_note = "11 FP32 operations per examined candidate (back-projection and the L1 / depth-range test)"
+    bpc_note = accounting
     traffic = _measured_traffic(args.workload, args.colour, N_OUT)
     clk_summary = clk.summary()
     sm_hz = (clk_summary["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
@@ -560,18 +663,15 @@ def main():
         "samples_per_s": {"examined": world * examined / (ms_per_step / 1e3),
                           "accepted": world * accepted / (ms_per_step / 1e3)},
         "accepted_per_pixel": accepted / (N_OUT * W * H), "kept_weight_fraction": sum_w / max(accepted, 1),
-        "psnr_db": {"output_vs_clean": psnr_out, "input_vs_clean": psnr_in, "reference": psnr_ref},
+        "psnr_db": {"output_vs_clean": psnr_out, "input_vs_clean": psnr_in, "reference": psnr_ref, **extra_quality},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "accounting": f"{bpc} B per examined candidate (colour + depth touched), {peak_kind} peak; "
-                                   "frac > 1 because window loads are served from L1 (traffic = DRAM bytes per launch)",
-                     "kernel_ms": kernel_ms},
-        "roofline_alu": {"bound": "alu", "achieved": examined * 8 / (kernel_ms / 1e3) / 1e12,
+                     "accounting": bpc_note, "kernel_ms": kernel_ms},
+        "roofline_alu": {"bound": "alu", "achieved": examined * alu_ops / (kernel_ms / 1e3) / 1e12,
                          "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": examined * 8 / (kernel_ms / 1e3) / 1e12 / fp32_peak,
-                         "accounting": "8 FP32 operations per examined candidate (the distance test); peak = 152 SMs "
-                                       "x 128 FP32 lanes x median SM clock"},
+                         "frac": examined * alu_ops / (kernel_ms / 1e3) / 1e12 / fp32_peak,
+                         "accounting": alu_note + "; peak = 152 SMs x 128 FP32 lanes x median SM clock"},
         "e2e": {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "gpu_launches_per_step": e2e_launches},
         "clocks": clk_summary,

@@ -51,7 +51,15 @@ enum {
     SSVP_MODE_DENOISE = 0,   /* Eq. 4 weights (Sec. "Denoising") */
     SSVP_MODE_APERTURE = 1,  /* Eq. 13-14 (Sec. "Virtual aperture") */
     SSVP_MODE_LEARNED = 2,   /* per-sample weights from a small MLP, plain Eq. 4 as fallback */
-    SSVP_MODE_MEAN = 3       /* w = 1 (the plain average of Sec. "Denoising") */
+    SSVP_MODE_MEAN = 3,      /* w = 1 (the plain average of Sec. "Denoising") */
+    SSVP_MODE_DEBLUR = 4,    /* Eq. 5: Eq. 4 times the sample frame's gradient-magnitude sum
+                                (Sec. "Deblurring"; see ssvp_frame_sharpness) */
+    SSVP_MODE_SHUTTER = 5    /* Eq. 10: w = xi(J - O) alone, xi from ssvp_set_shutter
+                                (Sec. "Computational scene-space shutters") */
+};
+enum {
+    SSVP_GATHER_WINDOW = 0,  /* depth-seeded k x k window + radius (or the aperture cone) */
+    SSVP_GATHER_FRUSTUM = 1  /* the pixel frustum of Sec. "Sample Gathering", Eq. 1-2 */
 };
 
 #define SSVP_MAX_CLIPS 64
@@ -73,6 +81,16 @@ enum {
  *                 focal depth z0 (<= 0: clip median depth), cone waist a0 (<= 0: 0.5 z0 / fx),
  *                 lens seed points (1..64), footprint cap per axis (odd, <= 63)
  *   max_samples, conf_threshold     learned filter: sample cap (<= 64), fallback threshold
+ *   gather        SSVP_GATHER_WINDOW, or SSVP_GATHER_FRUSTUM: the paper's own gather (Sec.
+ *                 "Sample Gathering", Eq. 1-2).  Every pixel q of every window frame J whose
+ *                 back-projection into O has O depth in (near_plane, far_plane) and lands within
+ *                 L1 distance frustum_l / 2 of the output pixel (|u - u'| + |v - v'| < l / 2,
+ *                 strict) is a sample, whatever its depth; the output depth is not used to
+ *                 gather, only for s_ref in Eq. 4 (an invalid output depth still gives c_ref).
+ *                 Denoise and mean modes only; k is ignored and the radius serves only as the
+ *                 default sigma_xyz.  Not available in batched plans.
+ *   frustum_l, near_plane, far_plane   frustum size l in pixels (0 < l <= 64; the paper uses 3)
+ *                 and its O depth range (0 < near < far; the paper uses 0.01 and 1000)
  *   membership_out   optional device buffer (debug): per crop pixel (row-major) and per slot
  *                 j = 0..2T (J = O-T+j) a record of 3 + ceil(k*k/32) int32 words:
  *                 status (-2 invalid reference depth, -1 J outside the clip, 0 J skipped: the
@@ -80,7 +98,11 @@ enum {
  *                 image), window centre x, y, then the accepted bits of the k x k window
  *                 (bit dy*k+dx).  In aperture mode the record is 5 + ceil(cap*cap/32) words:
  *                 status, the scanned box x0, y0, x1, y1 (inclusive, before clipping to the
- *                 image), then the accepted bits of the box (bit (y-y0)*cap + (x-x0)).
+ *                 image), then the accepted bits of the box (bit (y-y0)*cap + (x-x0)).  With
+ *                 the frustum gather it is 4 words: status (-2, -1 as above, 0 the frustum
+ *                 misses J's depth range or image, 1 scanned), the number of samples from J,
+ *                 and the low and high words of the wrapping 64-bit sum over them of
+ *                 SplitMix64's output function of qy*W + qx + 1 (an order-free checksum).
  *                 Only valid with a single output frame.
  *   pixel_stats_out  optional device buffer (debug): per crop pixel 3 words: int32 accepted,
  *                 int32 examined (window pixels inside the image), float sum of weights.
@@ -103,14 +125,41 @@ typedef struct ssvp_params {
     int32_t cap;
     int32_t max_samples;
     float conf_threshold;
+    int32_t gather;
+    float frustum_l;
+    float near_plane;
+    float far_plane;
     void *membership_out;
     void *pixel_stats_out;
 } ssvp_params;
 
+/*
+ * Shutter function xi of Eq. 10 (Sec. "Computational scene-space shutters") for
+ * SSVP_MODE_SHUTTER: xi[j] weighs every sample from frame J = O - half_window + j,
+ * j = 0 .. 2 half_window (host array, copied).  Values must be finite and >= 0; 0 drops a frame
+ * from the average.  A box (all ones) is a long exposure, a single non-zero entry projects one
+ * frame, a decaying tail leaves motion trails.  Shutter-mode calls must use this half_window.
+ * The weight has no colour, position or frame-distance term; a pixel whose samples all weigh 0
+ * keeps its input colour.  SSVP_EINVAL for a NULL table, a bad half_window or a bad value.
+ */
+int ssvp_set_shutter(ssvp_ctx *ctx, const float *xi, int half_window);
+
+/*
+ * Eq. 5's blurriness measure (Sec. "Deblurring") of every frame of clip `clip_id`: the sum over
+ * the pixels that have a right and a lower neighbour of the forward-difference gradient
+ * magnitude, the L2 norm over the three colour channels and both axes.  Computed on the device
+ * when the clip is loaded, from the stored colour (FP16-rounded with SSVP_COLOUR_F16), with a
+ * deterministic FP64 reduction.  SSVP_MODE_DEBLUR multiplies the Eq. 4 weight of a sample from J
+ * by out[J] / max(out) (the common scale cancels in Eq. 3).  out: F doubles on the host; the
+ * call waits for the context's stream.
+ */
+int ssvp_frame_sharpness(ssvp_ctx *ctx, int clip_id, double *out);
+
 /* Defaults: denoise, k = 7, T = 15, radius = 0.5 % of the median depth, sigma_rgb = 40/255
  * (the paper's 40 on a 0-255 scale, Sec. "Denoising"), sigma_xyz = r, sigma_f = 6, all frames
  * of the clip, full frame; aperture 0.05, focal depth = median, 16 lens points, cap 31;
- * learned cap 64, threshold 0.5; no debug outputs. */
+ * learned cap 64, threshold 0.5; window gather, frustum l = 3, near 0.01, far 1000; no debug
+ * outputs. */
 void ssvp_params_default(ssvp_params *p);
 
 /* Create a context on CUDA device `cuda_device`, queuing work on `cuda_stream` (a cudaStream_t;

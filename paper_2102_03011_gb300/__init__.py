@@ -19,6 +19,8 @@ SSVP_ENOCLIP, SSVP_ENOCAM, SSVP_ETIMEOUT, SSVP_EDEVICE = -4, -5, -6, -7
 SSVP_MEM_HOST, SSVP_MEM_DEVICE = 0, 1
 SSVP_COLOUR_F32, SSVP_COLOUR_F16 = 0, 1
 SSVP_MODE_DENOISE, SSVP_MODE_APERTURE, SSVP_MODE_LEARNED, SSVP_MODE_MEAN = 0, 1, 2, 3
+SSVP_MODE_DEBLUR, SSVP_MODE_SHUTTER = 4, 5
+SSVP_GATHER_WINDOW, SSVP_GATHER_FRUSTUM = 0, 1
 SSVP_MAX_CLIPS, SSVP_MAX_K, SSVP_MAX_HALF_WINDOW = 64, 31, 127
 
 
@@ -36,7 +38,8 @@ class ssvp_params(ctypes.Structure):
                 ("sigma_xyz", ctypes.c_float), ("sigma_f", ctypes.c_float), ("aperture", ctypes.c_float),
                 ("focal_depth", ctypes.c_float), ("a0", ctypes.c_float), ("lens_samples", ctypes.c_int32),
                 ("cap", ctypes.c_int32), ("max_samples", ctypes.c_int32), ("conf_threshold", ctypes.c_float),
-                ("membership_out", ctypes.c_void_p), ("pixel_stats_out", ctypes.c_void_p)]
+                ("gather", ctypes.c_int32), ("frustum_l", ctypes.c_float), ("near_plane", ctypes.c_float),
+                ("far_plane", ctypes.c_float), ("membership_out", ctypes.c_void_p), ("pixel_stats_out", ctypes.c_void_p)]
 
 
 class ssvp_plan_config(ctypes.Structure):
@@ -70,6 +73,8 @@ def _load():
         "ssvp_read_stats": (i, [vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong),
                                 ctypes.POINTER(ctypes.c_double)]),
         "ssvp_clip_median_depth": (i, [vp, i, ctypes.POINTER(f)]),
+        "ssvp_set_shutter": (i, [vp, ctypes.POINTER(f), i]),
+        "ssvp_frame_sharpness": (i, [vp, i, ctypes.POINTER(ctypes.c_double)]),
         "ssvp_sync": (i, [vp]),
         "ssvp_median_depth_noalloc": (i, [vp, ctypes.c_ulonglong, vp, vp]),
         "ssvp_autotune": (i, [vp, P, ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(ssvp_plan_config)]),
@@ -197,6 +202,23 @@ def ssvp_clip_median_depth(ctx, clip_id: int) -> float:
     m = ctypes.c_float()
     _check(ctx, lib.ssvp_clip_median_depth(ctx, clip_id, ctypes.byref(m)))
     return float(m.value)
+
+
+def ssvp_set_shutter(ctx, xi, half_window: int) -> None:
+    """Eq. 10 shutter function: xi[j] weighs samples from J = O - half_window + j."""
+    import numpy as np
+    a = np.ascontiguousarray(xi, dtype=np.float32)
+    if a.size != 2 * half_window + 1:
+        raise ValueError(f"xi needs {2 * half_window + 1} values, got {a.size}")
+    _check(ctx, lib.ssvp_set_shutter(ctx, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), half_window))
+
+
+def ssvp_frame_sharpness(ctx, clip_id: int, n_frames: int):
+    """Eq. 5's per-frame blurriness measure (sum of gradient magnitudes) -> float64 array."""
+    import numpy as np
+    out = np.zeros(n_frames, np.float64)
+    _check(ctx, lib.ssvp_frame_sharpness(ctx, clip_id, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
 
 
 def ssvp_sync(ctx) -> None:

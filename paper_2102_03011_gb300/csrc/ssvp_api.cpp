@@ -63,6 +63,9 @@ struct ssvp_ctx {
         ssvp_plan_config cfg;
     };
     std::vector<Tuned> tuned;
+    // Eq. 10 shutter function (host copy) and its per-slot log2 weights on the device
+    std::vector<float> shutter;
+    float *d_shutter_log2 = nullptr;
 };
 
 struct ssvp_plan {
@@ -111,6 +114,10 @@ void free_clip(Clip &c) {
     if (c.p.colour) cudaFree(c.p.colour);
     if (c.p.out) cudaFree(c.p.out);
     if (c.p.median) cudaFree(c.p.median);
+    if (c.p.zrange) cudaFree(c.p.zrange);
+    if (c.p.grad_sum) cudaFree(c.p.grad_sum);
+    if (c.p.grad_log2) cudaFree(c.p.grad_log2);
+    if (c.p.grad_partial) cudaFree(c.p.grad_partial);
     c = Clip();
 }
 
@@ -189,10 +196,31 @@ void compose_table(const Clip &c, int fb, int n_out, int T, double sigma_f, Pair
     }
 }
 
+// Back maps of the frustum gather: G_{O<-J} for every (O, slot), composed like the forward maps
+// with the roles of O and J exchanged (M = K_O R_OJ K_J^-1, e = K_O t_OJ; intrinsics of O).
+void compose_table_back(const Clip &c, int fb, int n_out, int T, double sigma_f, PairGeom *out) {
+    const int ns = 2 * T + 1;
+    for (int oi = 0; oi < n_out; ++oi) {
+        const int O = fb + oi;
+        for (int j = 0; j < ns; ++j) {
+            const int J = O - T + j;
+            PairGeom &g = out[(size_t)oi * ns + j];
+            if (J < 0 || J >= c.p.F) {
+                std::memset(&g, 0, sizeof(g));
+                g.J = -1;
+                continue;
+            }
+            compose_pair(&c.K[9 * (size_t)J], &c.w2c[12 * (size_t)J], &c.K[9 * (size_t)O], &c.w2c[12 * (size_t)O],
+                         J == O, J - O, sigma_f, g);
+            g.J = J;
+        }
+    }
+}
+
 int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
     if (!p) return fail(ctx, SSVP_EINVAL, "params is NULL");
     if (p->mode != SSVP_MODE_DENOISE && p->mode != SSVP_MODE_MEAN && p->mode != SSVP_MODE_APERTURE &&
-        p->mode != SSVP_MODE_LEARNED)
+        p->mode != SSVP_MODE_LEARNED && p->mode != SSVP_MODE_DEBLUR && p->mode != SSVP_MODE_SHUTTER)
         return fail(ctx, SSVP_EINVAL, "mode %d is not available in this build", p->mode);
     if (p->mode == SSVP_MODE_LEARNED && !(std::isfinite(p->conf_threshold)))
         return fail(ctx, SSVP_EINVAL, "conf_threshold must be finite");
@@ -203,6 +231,15 @@ int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
         if (!(p->aperture >= 0.0f && std::isfinite(p->aperture))) return fail(ctx, SSVP_EINVAL, "aperture must be >= 0");
         if (!std::isfinite(p->focal_depth) || !std::isfinite(p->a0))
             return fail(ctx, SSVP_EINVAL, "focal_depth and a0 must be finite");
+    }
+    if (p->gather != SSVP_GATHER_WINDOW && p->gather != SSVP_GATHER_FRUSTUM)
+        return fail(ctx, SSVP_EINVAL, "gather %d is not available in this build", p->gather);
+    if (p->gather == SSVP_GATHER_FRUSTUM) {
+        if (p->mode == SSVP_MODE_APERTURE || p->mode == SSVP_MODE_LEARNED)
+            return fail(ctx, SSVP_EINVAL, "the frustum gather supports the denoise, mean, deblur and shutter modes");
+        if (!(p->frustum_l > 0.0f && p->frustum_l <= 64.0f)) return fail(ctx, SSVP_EINVAL, "frustum_l must be in (0, 64]");
+        if (!(p->near_plane > 0.0f && p->far_plane > p->near_plane && std::isfinite(p->far_plane)))
+            return fail(ctx, SSVP_EINVAL, "need 0 < near_plane < far_plane < inf");
     }
     if (p->k < 1 || p->k > SSVP_MAX_K || (p->k & 1) == 0) return fail(ctx, SSVP_EINVAL, "k=%d must be odd in [1, 31]", p->k);
     if (p->half_window < 0 || p->half_window > SSVP_MAX_HALF_WINDOW)
@@ -233,6 +270,7 @@ int batch_check(ssvp_ctx *ctx, const ssvp_params *p, const int *ids, int n, int 
         return fail(ctx, SSVP_EINVAL, "batched plans support the denoise and mean modes");
     if (p->crop_w != 0 || p->crop_h != 0) return fail(ctx, SSVP_EINVAL, "batched plans gather full frames (crop_w = crop_h = 0)");
     if (p->membership_out || p->pixel_stats_out) return fail(ctx, SSVP_EINVAL, "batched plans have no debug outputs");
+    if (p->gather != SSVP_GATHER_WINDOW) return fail(ctx, SSVP_EINVAL, "batched plans use the window gather");
     if (!ids || n < 1 || n > SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "bad clip list");
     for (int i = 0; i < n; ++i) {
         if (ids[i] < 0 || ids[i] >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", ids[i]);
@@ -438,6 +476,10 @@ void ssvp_params_default(ssvp_params *p) {
     p->cap = 31;
     p->max_samples = 64;
     p->conf_threshold = 0.5f;
+    p->gather = SSVP_GATHER_WINDOW;
+    p->frustum_l = 3.0f;
+    p->near_plane = 0.01f;
+    p->far_plane = 1000.0f;
 }
 
 int ssvp_create(ssvp_ctx **out, int cuda_device, void *cuda_stream) {
@@ -478,6 +520,7 @@ void ssvp_destroy(ssvp_ctx *ctx) {
     if (ctx->median_scratch) cudaFree(ctx->median_scratch);
     if (ctx->geom) cudaFree(ctx->geom);
     if (ctx->staging) cudaFree(ctx->staging);
+    if (ctx->d_shutter_log2) cudaFree(ctx->d_shutter_log2);
     for (void *q : {(void *)ctx->mlp_buf, (void *)ctx->mlp_w1, (void *)ctx->l_feat, (void *)ctx->l_col,
                     (void *)ctx->l_plain, (void *)ctx->l_loss, (void *)ctx->l_n, (void *)ctx->l_batch})
         if (q) cudaFree(q);
@@ -523,7 +566,11 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
     if ((e = cudaMalloc(&p.depth, nplane * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&p.colour, nplane * texel)) != cudaSuccess ||
         (e = cudaMalloc(&p.out, nout * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&p.median, sizeof(float))) != cudaSuccess) {
+        (e = cudaMalloc(&p.median, sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&p.zrange, 2 * sizeof(unsigned int) * (size_t)F)) != cudaSuccess ||
+        (e = cudaMalloc(&p.grad_sum, sizeof(double) * (size_t)F)) != cudaSuccess ||
+        (e = cudaMalloc(&p.grad_log2, sizeof(float) * (size_t)F)) != cudaSuccess ||
+        (e = cudaMalloc(&p.grad_partial, sizeof(double) * ssvp::grad_partial_words(F))) != cudaSuccess) {
         free_clip(c);
         return cuda_fail(ctx, e, "cudaMalloc (clip planes)");
     }
@@ -562,6 +609,8 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
         }
     }
     CK(ssvp::launch_median(p, ctx->median_scratch, ctx->stream), "median kernels");
+    CK(ssvp::launch_zrange(p, ctx->stream), "depth range kernel");
+    CK(ssvp::launch_grad_sum(p, ctx->stream), "gradient sum kernels");
     c.loaded = true;
     c.has_cams = false;
     c.generation = ++ctx->clip_generation[clip_id];
@@ -664,24 +713,43 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         }
         return SSVP_OK;
     }
-    if (total > ctx->geom_cap) {
+    // Eq. 10: the shutter table must cover the window; its log2 weights go to the device per call
+    const bool shutter = p.mode == SSVP_MODE_SHUTTER;
+    if (shutter) {
+        if ((int)ctx->shutter.size() != ns)
+            return fail(ctx, SSVP_EINVAL, "shutter mode needs ssvp_set_shutter with half_window %d (have %d values)", T,
+                        (int)ctx->shutter.size());
+        if (!ctx->d_shutter_log2) CK(cudaMalloc(&ctx->d_shutter_log2, sizeof(float) * ssvp::kMaxSlots), "cudaMalloc (shutter)");
+        std::vector<float> lg(ns);
+        for (int j = 0; j < ns; ++j) lg[j] = (float)std::log2((double)ctx->shutter[j]);  // log2(0) = -inf: weight 0
+        CK(cudaMemcpyAsync(ctx->d_shutter_log2, lg.data(), sizeof(float) * ns, cudaMemcpyHostToDevice, ctx->stream),
+           "cudaMemcpyAsync (shutter)");
+    }
+    // the shutter weight has no frame-distance term: compose with sigma_f = infinity (beta = 0)
+    const double sigma_f = shutter ? INFINITY : (double)p.sigma_f;
+    // the frustum gather also needs the back maps: a second table of the same shape after the first
+    const bool frustum = p.gather == SSVP_GATHER_FRUSTUM;
+    const size_t entries = frustum ? 2 * total : total;
+    if (entries > ctx->geom_cap) {
         CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
         if (ctx->geom) cudaFree(ctx->geom);
         ctx->geom = nullptr;
         ctx->geom_cap = 0;
-        size_t cap = std::max<size_t>(total, 4096);
+        size_t cap = std::max<size_t>(entries, 4096);
         CK(cudaMalloc(&ctx->geom, cap * sizeof(PairGeom)), "cudaMalloc (geometry)");
         ctx->geom_cap = cap;
     }
-    ctx->host_geom.resize(std::max<size_t>(total, 1));
+    ctx->host_geom.resize(std::max<size_t>(entries, 1));
     size_t off = 0;
     for (int i = 0; i < n_clips; ++i) {
-        compose_table(ctx->clips[clip_ids[i]], fb[i], nout[i], T, p.sigma_f, &ctx->host_geom[off]);
+        compose_table(ctx->clips[clip_ids[i]], fb[i], nout[i], T, sigma_f, &ctx->host_geom[off]);
+        if (frustum) compose_table_back(ctx->clips[clip_ids[i]], fb[i], nout[i], T, sigma_f, &ctx->host_geom[total + off]);
         off += (size_t)nout[i] * ns;
     }
     // pageable source: the call returns once the table is staged, so host_geom may be reused
-    if (total) CK(cudaMemcpyAsync(ctx->geom, ctx->host_geom.data(), total * sizeof(PairGeom), cudaMemcpyHostToDevice, ctx->stream),
-                  "cudaMemcpyAsync (geometry)");
+    if (entries)
+        CK(cudaMemcpyAsync(ctx->geom, ctx->host_geom.data(), entries * sizeof(PairGeom), cudaMemcpyHostToDevice, ctx->stream),
+           "cudaMemcpyAsync (geometry)");
     CK(cudaMemsetAsync(ctx->stat_counts, 0, 2 * sizeof(unsigned long long), ctx->stream), "cudaMemsetAsync");
     CK(cudaMemsetAsync(ctx->stat_sumw, 0, sizeof(double), ctx->stream), "cudaMemsetAsync");
     off = 0;
@@ -716,10 +784,42 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         a.pixel_stats = (int32_t *)p.pixel_stats_out;
         a.stat_counts = ctx->stat_counts;
         a.stat_sumw = ctx->stat_sumw;
-        if (p.mode == SSVP_MODE_APERTURE) CK(ssvp::launch_aperture(a, ctx->stream), "aperture kernel");
+        a.geom_back = frustum ? ctx->geom + total + off : nullptr;
+        a.frame_log2w = p.mode == SSVP_MODE_DEBLUR ? c.p.grad_log2 : nullptr;
+        a.slot_log2w = shutter ? ctx->d_shutter_log2 : nullptr;
+        a.frustum_l = p.frustum_l;
+        a.near_plane = p.near_plane;
+        a.far_plane = p.far_plane;
+        if (frustum) CK(ssvp::launch_frustum(a, ctx->stream), "frustum kernel");
+        else if (p.mode == SSVP_MODE_APERTURE) CK(ssvp::launch_aperture(a, ctx->stream), "aperture kernel");
         else CK(ssvp::launch_gather(a, ctx->stream), "gather kernel");
         off += (size_t)nout[i] * ns;
     }
+    return SSVP_OK;
+}
+
+int ssvp_set_shutter(ssvp_ctx *ctx, const float *xi, int half_window) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (!xi) return fail(ctx, SSVP_EINVAL, "xi is NULL");
+    if (half_window < 0 || half_window > SSVP_MAX_HALF_WINDOW)
+        return fail(ctx, SSVP_EINVAL, "half_window=%d must be in [0, 127]", half_window);
+    const int n = 2 * half_window + 1;
+    for (int j = 0; j < n; ++j)
+        if (!(std::isfinite(xi[j]) && xi[j] >= 0.0f)) return fail(ctx, SSVP_EINVAL, "xi[%d] must be finite and >= 0", j);
+    ctx->shutter.assign(xi, xi + n);
+    return SSVP_OK;
+}
+
+int ssvp_frame_sharpness(ssvp_ctx *ctx, int clip_id, double *out) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    Clip &c = ctx->clips[clip_id];
+    if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    if (!out) return fail(ctx, SSVP_EINVAL, "out is NULL");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(out, c.p.grad_sum, sizeof(double) * (size_t)c.p.F, cudaMemcpyDeviceToHost, ctx->stream),
+       "cudaMemcpyAsync (gradient sums)");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     return SSVP_OK;
 }
 

@@ -1,0 +1,393 @@
+// ssvp_frustum.cu - the paper's frustum gather (Sec. "Sample Gathering", Eq. 1-2) fused with the
+// Eq. 3/4 filter.  One thread per output pixel, window frames in order.
+//
+// Per (pixel p, frame J):
+//   1. The frustum V of Eq. 1 (the l x l square around p swept over O depths [near, far]) is
+//      clipped to frame J's valid-depth slab [zlo_J, zhi_J] (no pixel of J has a depth outside
+//      it, so nothing is lost) and projected into J: the 12 edges of V are clipped in O depth
+//      and their end points projected.  A parallelogram along the projected central ray bounds
+//      that hull (grown by a rounding margin); only its pixels are tested.
+//   2. Each pixel q in it with depth d is back-projected into O through the homogeneous map
+//      h = M_{O<-J} (q_x d, q_y d, d) + e_{O<-J}; it is a sample when near < h_3 < far and
+//      |h_1 - u h_3| + |h_2 - v h_3| < (l / 2) h_3, which is Eq. 2's L1 test multiplied by the
+//      positive O depth h_3.
+//   3. Samples are weighted by Eq. 4 around s_ref (times the per-frame factors of Eq. 5, or by
+//      Eq. 10's shutter function alone) and reduced by Eq. 3, as in the window gather.
+#include <cuda_fp16.h>
+
+#include "../../include/ssvp.h"
+#include "ssvp_df.cuh"
+#include "ssvp_internal.h"
+
+namespace ssvp {
+namespace {
+
+constexpr int kFrTileX = 32, kFrTileY = 8, kFrThreads = kFrTileX * kFrTileY;
+
+// SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014); debug records sum it over the
+// linear indices qy * W + qx + 1 of a sample set, an order-independent membership checksum.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Bound of the projected hull: minor = b * major + [lo, hi], major in [mlo, mhi].
+struct HullBound {
+    float b, lo, hi, mlo, mhi;
+    bool xmajor, any;
+};
+
+__device__ __forceinline__ void bound_add(HullBound &hb, float px, float py) {
+    const float maj = hb.xmajor ? px : py, mnr = hb.xmajor ? py : px;
+    const float ic = fmaf(-hb.b, maj, mnr);
+    hb.lo = fminf(hb.lo, ic);
+    hb.hi = fmaxf(hb.hi, ic);
+    hb.mlo = fminf(hb.mlo, maj);
+    hb.mhi = fmaxf(hb.mhi, maj);
+    hb.any = true;
+}
+
+// Interval of t in [t0, t1] where w(t) = w0 + t dw lies in [zlo, zhi]; false when empty.
+__device__ __forceinline__ bool slab_interval(float w0, float dw, float zlo, float zhi, float t0, float t1, float &ta,
+                                              float &tb) {
+    if (dw != 0.0f) {
+        const float sa = (zlo - w0) / dw, sb = (zhi - w0) / dw;
+        ta = fmaxf(t0, fminf(sa, sb));
+        tb = fminf(t1, fmaxf(sa, sb));
+    } else {
+        if (!(w0 >= zlo && w0 <= zhi)) return false;
+        ta = t0;
+        tb = t1;
+    }
+    return ta <= tb;
+}
+
+// Lateral edge of V through the O pixel point (cu, cv): h(z) = z A + e for O depth z.
+__device__ __forceinline__ void lateral_edge(const float *M, const float *e, float cu, float cv, float nearp,
+                                             float farp, float zlo, float zhi, HullBound &hb) {
+    const float A0 = fmaf(M[0], cu, fmaf(M[1], cv, M[2]));
+    const float A1 = fmaf(M[3], cu, fmaf(M[4], cv, M[5]));
+    const float A2 = fmaf(M[6], cu, fmaf(M[7], cv, M[8]));
+    float za, zb;
+    // J depth along the edge: A2 z + e2
+    if (!slab_interval(e[2], A2, zlo, zhi, nearp, farp, za, zb)) return;
+    // the interval above is in units of z (w0 = e2 at z = 0), clipped to [near, far]
+    const float wa = fmaf(A2, za, e[2]), wb = fmaf(A2, zb, e[2]);
+    if (wa > 0.0f) bound_add(hb, fmaf(A0, za, e[0]) / wa, fmaf(A1, za, e[1]) / wa);
+    if (wb > 0.0f) bound_add(hb, fmaf(A0, zb, e[0]) / wb, fmaf(A1, zb, e[1]) / wb);
+}
+
+// Edge of the near or far face of V at O depth z0, from O pixel point (cu, cv) to (cu', cv').
+__device__ __forceinline__ void face_edge(const float *M, const float *e, float z0, float cu, float cv, float du,
+                                          float dv, float zlo, float zhi, HullBound &hb) {
+    // h(s) = z0 M (cu + s du, cv + s dv, 1) + e, s in [0, 1]
+    const float P0 = fmaf(z0, fmaf(M[0], cu, fmaf(M[1], cv, M[2])), e[0]);
+    const float P1 = fmaf(z0, fmaf(M[3], cu, fmaf(M[4], cv, M[5])), e[1]);
+    const float P2 = fmaf(z0, fmaf(M[6], cu, fmaf(M[7], cv, M[8])), e[2]);
+    const float D0 = z0 * fmaf(M[0], du, M[1] * dv), D1 = z0 * fmaf(M[3], du, M[4] * dv),
+                D2 = z0 * fmaf(M[6], du, M[7] * dv);
+    float sa, sb;
+    if (!slab_interval(P2, D2, zlo, zhi, 0.0f, 1.0f, sa, sb)) return;
+    const float wa = fmaf(D2, sa, P2), wb = fmaf(D2, sb, P2);
+    if (wa > 0.0f) bound_add(hb, fmaf(D0, sa, P0) / wa, fmaf(D1, sa, P1) / wa);
+    if (wb > 0.0f) bound_add(hb, fmaf(D0, sb, P0) / wb, fmaf(D1, sb, P1) / wb);
+}
+
+template <int CFMT, bool DEBUG>
+__global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a) {
+    __shared__ float s_const[4];
+    __shared__ unsigned long long s_cnt[2][kFrThreads / 32];
+    __shared__ float s_w[kFrThreads / 32];
+    const Planes &P = a.clip;
+    const int oi = blockIdx.z;
+    const int O = a.frame_begin + oi;
+    if (threadIdx.x == 0) {
+        const float r = a.radius > 0.0f ? a.radius : -a.radius * *P.median;
+        const float sx = a.sigma_xyz > 0.0f ? a.sigma_xyz : r;
+        // the shutter weight of Eq. 10 replaces Eq. 4: no colour and no position term
+        const bool shutter = a.mode == SSVP_MODE_SHUTTER;
+        s_const[0] = shutter ? 0.0f : kLog2e / (2.0f * a.sigma_rgb * a.sigma_rgb);
+        s_const[1] = shutter ? 0.0f : kLog2e / (2.0f * sx * sx);
+        s_const[2] = a.mode == SSVP_MODE_MEAN ? 0.0f : 1.0f;
+    }
+    __syncthreads();
+    const float a_rgb = s_const[0], a_xyz = s_const[1];
+    const bool weighted = s_const[2] != 0.0f;
+
+    const int u = a.x0 + blockIdx.x * kFrTileX + (threadIdx.x % kFrTileX);
+    const int v = a.y0 + blockIdx.y * kFrTileY + (threadIdx.x / kFrTileX);
+    const bool active = u < a.x0 + a.cw && v < a.y0 + a.ch;
+    const long long crop_idx = (long long)(v - a.y0) * a.cw + (u - a.x0);
+    const float L = 0.5f * a.frustum_l, nearp = a.near_plane, farp = a.far_plane;
+    const float zmid = 0.5f * (nearp + farp), zhalf = 0.5f * (farp - nearp);
+    const int ns = a.n_slots;
+
+    float3 cref = make_float3(0.f, 0.f, 0.f);
+    float dref = 0.0f;
+    if (active) {
+        const long long pix = (long long)O * P.fstride + (long long)(v + kPad) * P.pitch + (u + kPad);
+        dref = __ldg(P.depth + pix);
+        cref = load_colour<CFMT>(P.colour, pix);
+    }
+    const bool gather = active && dref > 0.0f;  // false for NaN (invalid) depth
+    // Accumulators carry the common factor 2^-m, m the largest log2 weight so far: without the
+    // reference sample (outside near / far) every weight can be far below FP32's range while
+    // Eq. 3 is still well defined.
+    float acc_r = 0.0f, acc_g = 0.0f, acc_b = 0.0f, acc_w = 0.0f, m_log2 = weighted ? -__int_as_float(0x7f800000) : 0.0f;
+    long long n_exam = 0;
+    int n_acc = 0;
+    if (DEBUG && active && !gather && a.membership)
+        for (int j = 0; j < ns; ++j) {
+            int32_t *rec = a.membership + (crop_idx * ns + j) * 4;
+            rec[0] = -2; rec[1] = 0; rec[2] = 0; rec[3] = 0;
+        }
+
+    if (gather) {
+        for (int j = 0; j < ns; ++j) {
+            const PairGeom &gf = a.geom[(long long)oi * ns + j];
+            const int J = __ldg(&gf.J);
+            int32_t *rec = DEBUG && a.membership ? a.membership + (crop_idx * ns + j) * 4 : nullptr;
+            if (J < 0) {
+                if (DEBUG && rec) { rec[0] = -1; rec[1] = 0; rec[2] = 0; rec[3] = 0; }
+                continue;
+            }
+            const PairGeom &gb = a.geom_back[(long long)oi * ns + j];
+            // J's valid depth range (order-preserving bit patterns; 0 words: no valid depth)
+            const unsigned int zmin_w = __ldg(P.zrange + 2 * J), zmax_w = __ldg(P.zrange + 2 * J + 1);
+            const float zlo = zmin_w ? __uint_as_float(~zmin_w) : __int_as_float(0x7f800000);
+            const float zhi = __uint_as_float(zmax_w);
+            float Mf[9], ef[3];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Mf[i] = __ldg(&gf.M_hi[i]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ef[i] = __ldg(&gf.e_hi[i]);
+            // ---- 1. bound of the projected frustum, clipped to the slab
+            HullBound hb;
+            hb.any = false;
+            hb.xmajor = true;
+            hb.b = 0.0f;
+            {
+                // direction of the projected central ray (its clipped end points), for the slope
+                const float A0 = fmaf(Mf[0], (float)u, fmaf(Mf[1], (float)v, Mf[2]));
+                const float A1 = fmaf(Mf[3], (float)u, fmaf(Mf[4], (float)v, Mf[5]));
+                const float A2 = fmaf(Mf[6], (float)u, fmaf(Mf[7], (float)v, Mf[8]));
+                float za, zb;
+                if (zlo <= zhi && slab_interval(ef[2], A2, zlo, zhi, nearp, farp, za, zb)) {
+                    const float wa = fmaf(A2, za, ef[2]), wb = fmaf(A2, zb, ef[2]);
+                    const float xa = fmaf(A0, za, ef[0]) / wa, ya = fmaf(A1, za, ef[1]) / wa;
+                    const float xb = fmaf(A0, zb, ef[0]) / wb, yb = fmaf(A1, zb, ef[1]) / wb;
+                    const float dx = xb - xa, dy = yb - ya;
+                    if (isfinite(dx) && isfinite(dy)) {
+                        hb.xmajor = fabsf(dx) >= fabsf(dy);
+                        const float den = hb.xmajor ? dx : dy;
+                        if (fabsf(den) > 1e-6f) hb.b = (hb.xmajor ? dy : dx) / den;
+                    }
+                }
+            }
+            hb.lo = hb.mlo = __int_as_float(0x7f800000);
+            hb.hi = hb.mhi = -__int_as_float(0x7f800000);
+            if (zlo <= zhi) {
+                const float cu[4] = {u - L, u + L, u + L, u - L}, cv[4] = {v - L, v - L, v + L, v + L};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    lateral_edge(Mf, ef, cu[c], cv[c], nearp, farp, zlo, zhi, hb);
+                    const int c2 = (c + 1) & 3;
+                    face_edge(Mf, ef, nearp, cu[c], cv[c], cu[c2] - cu[c], cv[c2] - cv[c], zlo, zhi, hb);
+                    face_edge(Mf, ef, farp, cu[c], cv[c], cu[c2] - cu[c], cv[c2] - cv[c], zlo, zhi, hb);
+                }
+            }
+            if (DEBUG && rec) { rec[0] = 0; rec[1] = 0; rec[2] = 0; rec[3] = 0; }
+            if (!hb.any) continue;
+            // rounding margin: FP32 end points are off by far less than 0.02 px + 1e-5 relative
+            const float mg = 0.02f;
+            const float lo = hb.lo - (mg + 1e-5f * fabsf(hb.lo)), hi = hb.hi + (mg + 1e-5f * fabsf(hb.hi));
+            const float mlo = hb.mlo - (mg + 1e-5f * fabsf(hb.mlo)), mhi = hb.mhi + (mg + 1e-5f * fabsf(hb.mhi));
+            const int nmaj = hb.xmajor ? P.W : P.H, nmin = hb.xmajor ? P.H : P.W;
+            // NaN bounds (degenerate projections) scan the whole image: fmaxf/fminf drop NaN; the
+            // clamps on both sides keep every float -> int conversion in range
+            const int m0 = (int)fminf(fmaxf(ceilf(mlo), 0.0f), (float)nmaj);
+            const int m1 = (int)fmaxf(fminf(floorf(mhi), (float)(nmaj - 1)), -1.0f);
+            if (m0 > m1) continue;
+            if (DEBUG && rec) rec[0] = 1;
+
+            // ---- 2. back-projection test rows, centred on p: val = d (R q~) + E
+            float R1[3], R2[3], R3[3], E1, E2, E3;
+            {
+                float Mb[9], eb[3];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Mb[i] = __ldg(&gb.M_hi[i]);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) eb[i] = __ldg(&gb.e_hi[i]);
+                const float fu = (float)u, fv = (float)v;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    R1[i] = fmaf(-fu, Mb[6 + i], Mb[i]);
+                    R2[i] = fmaf(-fv, Mb[6 + i], Mb[3 + i]);
+                    R3[i] = Mb[6 + i];
+                }
+                E1 = fmaf(-fu, eb[2], eb[0]);
+                E2 = fmaf(-fv, eb[2], eb[1]);
+                E3 = eb[2];
+            }
+            // O intrinsics (the back map's target camera) for the metric offset to x_ref
+            const float ifxO = __ldg(&gb.ifx), ifyO = __ldg(&gb.ify);
+            const float ux = (float)u - __ldg(&gb.cx), vy = (float)v - __ldg(&gb.cy);
+            // frame term of Eq. 4 plus the per-frame weights of Eq. 5 / Eq. 10, in log2 units
+            float beta = __ldg(&gf.beta) * kLog2e;
+            if (a.frame_log2w) beta -= __ldg(a.frame_log2w + J);
+            if (a.slot_log2w) beta -= __ldg(a.slot_log2w + j);
+            const long long fbase = (long long)J * P.fstride;
+            int mc = 0;
+            unsigned long long mh = 0ull;
+            for (int m = m0; m <= m1; ++m) {
+                const float fm = (float)m;
+                const int n0 = (int)fminf(fmaxf(ceilf(fmaf(hb.b, fm, lo)), 0.0f), (float)nmin);
+                const int n1 = (int)fmaxf(fminf(floorf(fmaf(hb.b, fm, hi)), (float)(nmin - 1)), -1.0f);
+                // the major coordinate's share of R q~
+                const int qx0 = hb.xmajor ? m : 0, qy0 = hb.xmajor ? 0 : m;
+                const float b1 = fmaf(R1[0], (float)qx0, fmaf(R1[1], (float)qy0, R1[2]));
+                const float b2 = fmaf(R2[0], (float)qx0, fmaf(R2[1], (float)qy0, R2[2]));
+                const float b3 = fmaf(R3[0], (float)qx0, fmaf(R3[1], (float)qy0, R3[2]));
+                const float s1 = hb.xmajor ? R1[1] : R1[0], s2 = hb.xmajor ? R2[1] : R2[0], s3 = hb.xmajor ? R3[1] : R3[0];
+                n_exam += max(n1 - n0 + 1, 0);
+                for (int n = n0; n <= n1; ++n) {
+                    const int qx = hb.xmajor ? m : n, qy = hb.xmajor ? n : m;
+                    const long long off = fbase + (long long)(qy + kPad) * P.pitch + (qx + kPad);
+                    const float d = __ldg(P.depth + off);
+                    const float fn = (float)n;
+                    const float h1 = fmaf(d, fmaf(s1, fn, b1), E1);
+                    const float h2 = fmaf(d, fmaf(s2, fn, b2), E2);
+                    const float h3 = fmaf(d, fmaf(s3, fn, b3), E3);
+                    // NaN depth fails both comparisons
+                    if (fabsf(h1) + fabsf(h2) < L * h3 && fabsf(h3 - zmid) < zhalf) {
+                        const float3 c = load_colour<CFMT>(P.colour, off);
+                        const float er = c.x - cref.x, eg = c.y - cref.y, eb = c.z - cref.z;
+                        float w = 1.0f;
+                        if (weighted) {
+                            const float dz = h3 - dref;
+                            const float ex = fmaf(ux, dz, h1) * ifxO, ey = fmaf(vy, dz, h2) * ifyO;
+                            const float d2 = fmaf(ex, ex, fmaf(ey, ey, dz * dz));
+                            const float x = -fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta));
+                            if (x > m_log2) {  // new largest weight: rescale what was summed so far
+                                const float sc = ex2(m_log2 - x);
+                                acc_r *= sc;
+                                acc_g *= sc;
+                                acc_b *= sc;
+                                acc_w *= sc;
+                                m_log2 = x;
+                            }
+                            w = x == -__int_as_float(0x7f800000) ? 0.0f : ex2(x - m_log2);
+                        }
+                        acc_r = fmaf(w, er, acc_r);
+                        acc_g = fmaf(w, eg, acc_g);
+                        acc_b = fmaf(w, eb, acc_b);
+                        acc_w += w;
+                        ++n_acc;
+                        if (DEBUG) {
+                            ++mc;
+                            mh += mix64((unsigned long long)qy * (unsigned long long)P.W + (unsigned long long)qx + 1ull);
+                        }
+                    }
+                }
+            }
+            if (DEBUG && rec) {
+                rec[1] = mc;
+                rec[2] = (int32_t)(unsigned int)(mh & 0xffffffffull);
+                rec[3] = (int32_t)(unsigned int)(mh >> 32);
+            }
+        }
+    }
+
+    if (active) {
+        float o_r = cref.x, o_g = cref.y, o_b = cref.z;
+        if (acc_w > 0.0f) {
+            const float inv = 1.0f / acc_w;
+            o_r = fmaf(acc_r, inv, o_r);
+            o_g = fmaf(acc_g, inv, o_g);
+            o_b = fmaf(acc_b, inv, o_b);
+        }
+        float *o = P.out + (((long long)O * P.H + v) * P.W + u) * 3;
+        o[0] = o_r;
+        o[1] = o_g;
+        o[2] = o_b;
+        if (DEBUG && a.pixel_stats) {
+            int32_t *ps = a.pixel_stats + crop_idx * 3;
+            ps[0] = n_acc;
+            ps[1] = (int32_t)min(n_exam, 0x7fffffffll);
+            ps[2] = __float_as_int(acc_w > 0.0f ? acc_w * exp2f(m_log2) : 0.0f);
+        }
+    }
+
+    unsigned long long ce = (unsigned long long)n_exam, ca = (unsigned long long)n_acc;
+    float sw = acc_w > 0.0f ? acc_w * exp2f(m_log2) : 0.0f;  // the true sum of weights
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ce += __shfl_xor_sync(0xffffffffu, ce, o);
+        ca += __shfl_xor_sync(0xffffffffu, ca, o);
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_cnt[0][warp] = ce; s_cnt[1][warp] = ca; s_w[warp] = sw; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long te = 0, ta = 0;
+        double tw = 0.0;
+        for (int i = 0; i < kFrThreads / 32; ++i) { te += s_cnt[0][i]; ta += s_cnt[1][i]; tw += s_w[i]; }
+        atomicAdd(a.stat_counts, te);
+        atomicAdd(a.stat_counts + 1, ta);
+        atomicAdd(a.stat_sumw, tw);
+    }
+}
+
+// Valid depth range of every frame: one block per (frame, row slice); positive floats order like
+// their bit patterns, so the range is kept as atomicMax of the bits (max) and of their complement
+// (min); zero words mean "no valid depth".
+__global__ void __launch_bounds__(256) zrange_kernel(Planes P, unsigned int *zr) {
+    const int f = blockIdx.y;
+    unsigned int mx = 0u, mn = 0u;
+    for (int y = blockIdx.x; y < P.H; y += gridDim.x) {
+        const float *row = P.depth + (long long)f * P.fstride + (long long)(y + kPad) * P.pitch + kPad;
+        for (int x = threadIdx.x; x < P.W; x += blockDim.x) {
+            const unsigned int bits = __float_as_uint(__ldg(row + x));
+            if (bits > 0u && bits < 0x7f800000u) {  // finite and > 0 (NaN pads fail)
+                mx = max(mx, bits);
+                mn = max(mn, ~bits);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = max(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    if ((threadIdx.x & 31) == 0 && mx) {
+        atomicMax(zr + 2 * f, mn);
+        atomicMax(zr + 2 * f + 1, mx);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_frustum(const GatherArgs &a, cudaStream_t s) {
+    const dim3 grid((a.cw + kFrTileX - 1) / kFrTileX, (a.ch + kFrTileY - 1) / kFrTileY, a.n_out);
+    const bool dbg = a.membership || a.pixel_stats;
+    if (a.clip.colour_fmt == 0) {
+        if (dbg) frustum_kernel<0, true><<<grid, kFrThreads, 0, s>>>(a);
+        else frustum_kernel<0, false><<<grid, kFrThreads, 0, s>>>(a);
+    } else {
+        if (dbg) frustum_kernel<1, true><<<grid, kFrThreads, 0, s>>>(a);
+        else frustum_kernel<1, false><<<grid, kFrThreads, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zrange(const Planes &p, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(p.zrange, 0, 2 * sizeof(unsigned int) * (size_t)p.F, s);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)min(p.H, 64), (unsigned)p.F);
+    zrange_kernel<<<grid, 256, 0, s>>>(p, p.zrange);
+    return cudaGetLastError();
+}
+
+}  // namespace ssvp

@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "../../include/ssvp.h"
 #include "ssvp_df.cuh"
 #include "ssvp_internal.h"
 
@@ -313,15 +314,23 @@ __global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const G
     const int oi = blockIdx.z;
     const int O = a.frame_begin + oi;
     const int u0 = a.x0 + blockIdx.x * kTileX, v0 = a.y0 + blockIdx.y * kTileY;
-    for (int j = threadIdx.x; j < a.n_slots; j += kThreads)
-        build_slot(a.geom[(long long)oi * a.n_slots + j], (float)u0, (float)v0, sgeom + kSlotVec * j);
+    for (int j = threadIdx.x; j < a.n_slots; j += kThreads) {
+        float4 *g = sgeom + kSlotVec * j;
+        build_slot(a.geom[(long long)oi * a.n_slots + j], (float)u0, (float)v0, g);
+        // per-frame weights (Eq. 5, Eq. 10) join the frame term of the exponent
+        const int J = __float_as_int(g[5].w);
+        if (J >= 0 && a.frame_log2w) g[5].z -= a.frame_log2w[J];
+        if (J >= 0 && a.slot_log2w) g[5].z -= a.slot_log2w[j];
+    }
     if (threadIdx.x == 0) {
         float r = a.radius > 0.0f ? a.radius : -a.radius * *a.clip.median;
         float sx = a.sigma_xyz > 0.0f ? a.sigma_xyz : r;
+        // the shutter weight of Eq. 10 replaces Eq. 4: no colour and no position term
+        const bool shutter = a.mode == SSVP_MODE_SHUTTER;
         s_const[0] = r * r;
-        s_const[1] = kLog2e / (2.0f * a.sigma_rgb * a.sigma_rgb);
-        s_const[2] = kLog2e / (2.0f * sx * sx);
-        s_const[3] = a.mode == 3 ? 0.0f : 1.0f;
+        s_const[1] = shutter ? 0.0f : kLog2e / (2.0f * a.sigma_rgb * a.sigma_rgb);
+        s_const[2] = shutter ? 0.0f : kLog2e / (2.0f * sx * sx);
+        s_const[3] = a.mode == SSVP_MODE_MEAN ? 0.0f : 1.0f;
     }
     __syncthreads();
 

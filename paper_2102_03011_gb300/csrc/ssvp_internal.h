@@ -23,6 +23,11 @@ struct Planes {
     void *colour;          // F * fstride texels: float4 (r, g, b, 0) or 4 x half (r, g, b, 0)
     int colour_fmt;        // 0 FP32, 1 FP16
     float *median;         // device scalar: lower-median valid depth
+    unsigned int *zrange;  // F x 2 words: valid depth range of each frame as bit patterns,
+                           // complement of the minimum's bits and the maximum's bits (0: none)
+    double *grad_sum;      // F: Eq. 5 blurriness measure (sum of gradient magnitudes) per frame
+    float *grad_log2;      // F: log2(grad_sum / max over frames), the Eq. 5 factor in log2 units
+    double *grad_partial;  // F x grad_partial_words(1): partial sums of grad_sum
     float *out;            // F * H * W * 3 output floats (row-major, interleaved)
 };
 
@@ -62,6 +67,13 @@ struct GatherArgs {
     float *col_out;
     int32_t *nsamp_out;
     float *plain_out;
+    // per-frame weights in log2 units, subtracted from the exponent of every sample from J:
+    // frame_log2w[J] (Eq. 5, indexed by input frame) and slot_log2w[j] (Eq. 10, by window slot)
+    const float *frame_log2w;
+    const float *slot_log2w;
+    // frustum gather (Eq. 1-2): back maps G_{O<-J} (same indexing as geom), frustum size and depths
+    const PairGeom *geom_back;
+    float frustum_l, near_plane, far_plane;
     int32_t *membership;      // debug record per (crop pixel, slot) or null
     int32_t *pixel_stats;     // debug record per crop pixel or null
     unsigned long long *stat_counts;  // [0] examined, [1] accepted
@@ -132,6 +144,10 @@ cudaError_t launch_median(const Planes &p, unsigned int *scratch, cudaStream_t s
 size_t median_scratch_words();
 cudaError_t launch_gather(const GatherArgs &a, cudaStream_t s);
 cudaError_t launch_aperture(const GatherArgs &a, cudaStream_t s);
+cudaError_t launch_frustum(const GatherArgs &a, cudaStream_t s);
+cudaError_t launch_grad_sum(const Planes &p, cudaStream_t s);
+size_t grad_partial_words(int F);
+cudaError_t launch_zrange(const Planes &p, cudaStream_t s);
 // persistent batched gather; grid = batch_grid(...) CTAs
 cudaError_t launch_batch(const GatherArgs &a, const BatchArgs &b, int tile_rows, int colour_fmt, int grid,
                          cudaStream_t s);

@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "../../include/ssvp.h"
+#include "ssvp_df.cuh"
 #include "ssvp_internal.h"
 
 namespace ssvp {
@@ -114,7 +115,77 @@ __global__ void select_kernel(unsigned int *scratch, float *median) {
     for (int i = t; i < kHistWords; i += 1024) scratch[i] = 0;
 }
 
+// ---------------------------------------------------------------- Eq. 5 blurriness measure
+// Per frame, the sum over pixels with a right and a lower neighbour of the forward-difference
+// gradient magnitude (L2 over the colour channels and both axes).  Two deterministic passes:
+// kGradSlices blocks per frame write FP64 partial sums, then one block adds them in order and
+// derives log2(sum / max over frames), the per-frame term of the Eq. 5 weight in log2 units.
+constexpr int kGradSlices = 64;
+
+template <int CFMT>
+__global__ void __launch_bounds__(256) grad_partial_kernel(Planes P, double *partial) {
+    const int f = blockIdx.y;
+    float sum = 0.0f;
+    for (int y = blockIdx.x; y + 1 < P.H; y += kGradSlices) {
+        const long long row = (long long)f * P.fstride + (long long)(y + kPad) * P.pitch + kPad;
+        for (int x = threadIdx.x; x + 1 < P.W; x += blockDim.x) {
+            const float3 a = load_colour<CFMT>(P.colour, row + x);
+            const float3 r = load_colour<CFMT>(P.colour, row + x + 1);
+            const float3 d = load_colour<CFMT>(P.colour, row + P.pitch + x);
+            const float gx0 = r.x - a.x, gx1 = r.y - a.y, gx2 = r.z - a.z;
+            const float gy0 = d.x - a.x, gy1 = d.y - a.y, gy2 = d.z - a.z;
+            sum += sqrtf(gx0 * gx0 + gx1 * gx1 + gx2 * gx2 + gy0 * gy0 + gy1 * gy1 + gy2 * gy2);
+        }
+    }
+    double v = sum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double s_part[8];
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 8; ++i) t += s_part[i];
+        partial[(long long)f * kGradSlices + blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) grad_final_kernel(int F, const double *partial, double *sum, float *log2w) {
+    __shared__ double s_max[256];
+    double mx = 0.0;
+    for (int f = threadIdx.x; f < F; f += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < kGradSlices; ++b) t += partial[(long long)f * kGradSlices + b];
+        sum[f] = t;
+        mx = fmax(mx, t);
+    }
+    s_max[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const double gmax = s_max[0];
+    for (int f = threadIdx.x; f < F; f += blockDim.x) {
+        // a frame without any gradient gets weight 0 (log2 = -inf); an all-flat clip weights all
+        // frames equally
+        log2w[f] = gmax > 0.0 ? (float)log2(sum[f] / gmax) : 0.0f;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_grad_sum(const Planes &p, cudaStream_t s) {
+    const dim3 grid(kGradSlices, (unsigned)p.F);
+    if (p.colour_fmt == 0) grad_partial_kernel<0><<<grid, 256, 0, s>>>(p, p.grad_partial);
+    else grad_partial_kernel<1><<<grid, 256, 0, s>>>(p, p.grad_partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    grad_final_kernel<<<1, 256, 0, s>>>(p.F, p.grad_partial, p.grad_sum, p.grad_log2);
+    return cudaGetLastError();
+}
+
+size_t grad_partial_words(int F) { return (size_t)F * kGradSlices; }
 
 cudaError_t launch_pack(const float *rgb, const float *depth, int W, int H, int nF, const Planes &dst, int frame0,
                         cudaStream_t s) {

@@ -364,6 +364,34 @@ def make_clip(preset: str, W: int, H: int, F: int, seed: int = 0, with_world: bo
                 meta=dict(preset=preset, seed=seed, objects=objs, **p))
 
 
+def shake_blur(clip: Clip, frames, shake_deg: float = 0.5, n_sub: int = 6, seed: int = 0) -> Clip:
+    """Motion blur from a sudden camera shake during the exposure of each listed frame: the clean
+    image becomes the mean of n_sub renders whose camera rotates from the frame's pose to a random
+    rotation of shake_deg degrees (the frame's pose, depth and clean reference stay those of the
+    sharp start pose); the frame's image noise is then drawn again with the same key.  Returns a
+    new Clip whose rgb holds the blurred, noisy frames."""
+    objs = clip.meta["objects"]
+    rgb = clip.rgb.copy()
+    rng = np.random.default_rng(40_000 + seed)
+    for f in frames:
+        axis = rng.normal(size=3)
+        axis /= np.linalg.norm(axis)
+        subs = np.empty((n_sub, 3, 4))
+        R0, t0 = clip.w2c_true[f, :, :3], clip.w2c_true[f, :, 3]
+        C = -R0.T @ t0
+        for i in range(n_sub):
+            Rs = rodrigues(np.radians(shake_deg) * (i / max(n_sub - 1, 1)) * axis) @ R0
+            subs[i] = _w2c(Rs.T, C)
+        img, _, _, _ = render(objs, np.repeat(clip.K[f:f + 1], n_sub, axis=0), subs, clip.W, clip.H)
+        blurred = img.mean(axis=0, dtype=np.float64).astype(np.float32)[None]
+        sig = clip.meta.get("sigma_img", 0.0)
+        if sig:
+            blurred, _ = add_noise(blurred, clip.depth_true[f:f + 1], clip.meta["seed"], sig, 0.0, frame0=f)
+        rgb[f] = blurred[0]
+    return Clip(clip.W, clip.H, clip.F, clip.K, clip.w2c, clip.w2c_true, rgb, clip.depth, clip.clean,
+                clip.depth_true, clip.world, clip.objid, meta=dict(clip.meta, blurred=list(frames), shake_deg=shake_deg))
+
+
 # ------------------------------------------------------------------ workload recipes
 
 WORKLOADS = {

@@ -20,6 +20,8 @@ class GpuResult:
     centre: np.ndarray | None = None  # (ch, cw, ns, 2)
     bits: np.ndarray | None = None    # (ch, cw, ns, k, k) bool (aperture: cap x cap from the box origin)
     box: np.ndarray | None = None     # (ch, cw, ns, 4) aperture box x0, y0, x1, y1
+    count: np.ndarray | None = None   # (ch, cw, ns) frustum gather: samples per window frame
+    hash: np.ndarray | None = None    # (ch, cw, ns) uint64 frustum membership checksum
 
 
 class Session:
@@ -165,3 +167,58 @@ def compare_aperture(g: GpuResult, o: oracle.Result, cap: int):
     return dict(pixels=ch * cw, excluded=int(excl.sum()), members=int((o_acc & cmp[..., None, None]).sum()),
                 max_colour_err=float(cerr[ok].max(initial=0.0)), band_flips=int(bit_diff.sum()),
                 box_flips=int(box_diff.sum()), ambiguous_windows=int(amb.sum()))
+
+
+def run_frustum(sess: Session, cid, O, crop=None, membership=False, **kw) -> GpuResult:
+    """Frustum gather (Eq. 1-2) through the C ABI; with membership, status (ch, cw, ns), the
+    per-slot sample counts in `nexam`'s place (`count`) and the 64-bit checksums (`hash`)."""
+    t, ss = sess.torch, sess.ss
+    W, H, F = sess.clips[cid]
+    x0, y0, cw, ch = crop if crop is not None else (0, 0, W, H)
+    p = sess.params(frame_begin=O, frame_end=O + 1, crop_x=x0, crop_y=y0, crop_w=cw, crop_h=ch,
+                    gather=ss.SSVP_GATHER_FRUSTUM, **kw)
+    ns = 2 * p.half_window + 1
+    mem = stats = None
+    if membership:
+        mem = t.zeros((ch, cw, ns, 4), dtype=t.int32, device=sess.dev)
+        stats = t.zeros((ch, cw, 3), dtype=t.int32, device=sess.dev)
+        p.membership_out = mem.data_ptr()
+        p.pixel_stats_out = stats.data_ptr()
+    ss.ssvp_gather_filter(sess.ctx, p, [cid])
+    out = t.empty((1, H, W, 3), dtype=t.float32, device=sess.dev)
+    ss.ssvp_read_output(sess.ctx, cid, O, O + 1, out)
+    ss.ssvp_sync(sess.ctx)
+    res = GpuResult(out[0, y0:y0 + ch, x0:x0 + cw].cpu().numpy())
+    if membership:
+        m = mem.cpu().numpy()
+        s = stats.cpu().numpy()
+        res.nacc, res.nexam = s[..., 0].astype(np.int64), s[..., 1].astype(np.int64)
+        res.sumw = s[..., 2].view(np.float32).astype(np.float64)
+        res.status = m[..., 0]
+        res.count = m[..., 1]
+        res.hash = m[..., 2].view(np.uint32).astype(np.uint64) | (m[..., 3].view(np.uint32).astype(np.uint64) << np.uint64(32))
+    return res
+
+
+def compare_frustum(g: GpuResult, o: oracle.FrustumResult, ref_valid: np.ndarray):
+    """Per (pixel, window frame): sample counts and membership checksums must match exactly
+    except where the oracle saw a candidate within the tie band of Eq. 2's bound (or of near /
+    far).  Pixels where such an allowed difference occurred are excluded from the colour and
+    count comparison; every other pixel must match colour within COLOUR_TOL."""
+    band = o.band != 0
+    # the GPU marks an invalid reference depth with -2 and frames outside the clip with -1
+    assert (g.status[~ref_valid] == -2).all()
+    diff = (g.count != o.count) | (g.hash != o.hash)
+    diff &= ref_valid[..., None]
+    assert not (diff & ~band).any(), \
+        f"{int((diff & ~band).sum())} membership differences, first {np.argwhere(diff & ~band)[:5]}"
+    excl = diff.any(-1)
+    ok = ~excl
+    cerr = np.abs(g.rgb.astype(np.float64) - o.rgb).max(-1)
+    assert cerr[ok].max(initial=0.0) <= COLOUR_TOL, f"colour max abs {cerr[ok].max()} > {COLOUR_TOL}"
+    np.testing.assert_array_equal(g.nacc[ok], o.nacc[ok])
+    # the GPU reports sum w in FP32: sums below its range read 0 (Eq. 3 itself is rescaled)
+    np.testing.assert_allclose(g.sumw[ok], o.sumw[ok], rtol=1e-4, atol=1e-30)
+    return dict(pixels=int(ok.size), excluded=int(excl.sum()), members=int(o.count.sum()),
+                band_slots=int(band.sum()), max_colour_err=float(cerr[ok].max(initial=0.0)),
+                max_colour_err_all=float(cerr.max()))
