@@ -51,7 +51,8 @@ class _Params(ctypes.Structure):
                 ("tie_band", ctypes.c_double), ("aperture", ctypes.c_double), ("focal_depth", ctypes.c_double),
                 ("a0", ctypes.c_double), ("cap", ctypes.c_int32), ("gather", ctypes.c_int32),
                 ("frustum_l", ctypes.c_double), ("near_plane", ctypes.c_double), ("far_plane", ctypes.c_double),
-                ("frame_w", ctypes.POINTER(ctypes.c_double)), ("slot_w", ctypes.POINTER(ctypes.c_double))]
+                ("frame_w", ctypes.POINTER(ctypes.c_double)), ("slot_w", ctypes.POINTER(ctypes.c_double)),
+                ("sigma_area", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -85,6 +86,10 @@ def _load():
                                       ctypes.c_int, ctypes.c_int, u8p]
         lib.oc_bruteforce.restype = ctypes.c_longlong
         lib.oc_frame_sharpness.argtypes = [ctypes.POINTER(_Clip), dp]
+        lib.oc_weight_superres.argtypes = [dp, dp] + [ctypes.c_double] * 6
+        lib.oc_weight_superres.restype = ctypes.c_double
+        lib.oc_superres_filter.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params)] + [ctypes.c_int] * 6 + \
+            [dp, dp, i64p, i32p, ctypes.POINTER(ctypes.c_uint64), u8p]
         lib.oc_frustum_filter.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, i64p, i32p,
                                           ctypes.POINTER(ctypes.c_uint64), u8p]
@@ -130,6 +135,7 @@ class Params:
     far_plane: float = 1000.0
     frame_w: np.ndarray | None = None   # MODE_DEBLUR: Eq. 5's per-frame factor (F values), e.g. frame_sharpness()
     slot_w: np.ndarray | None = None    # MODE_SHUTTER: Eq. 10's xi(J - O) for J = O-T .. O+T (2T+1 values)
+    sigma_area: float = 0.0             # super-resolution (Eq. 7) length scale; superres_filter fills 0 in
 
     def c_struct(self, fx: float) -> _Params:
         s = _Params()
@@ -151,6 +157,7 @@ class Params:
                 keep.append(a)
                 setattr(s, name, _p(a, ctypes.c_double))
         s._keep = keep  # the arrays live as long as the struct
+        s.sigma_area = self.sigma_area
         return s
 
 
@@ -288,6 +295,43 @@ def frustum_filter(view: ClipView, prm: Params, O: int, crop=None, membership: b
     rc = _load().oc_frustum_filter(ctypes.byref(view.c), ctypes.byref(ps), O, x0, y0, cw, ch,
                                    _p(out, ctypes.c_double), _p(sumw, ctypes.c_double), _p(nacc, ctypes.c_int64),
                                    _p(cnt, ctypes.c_int32), _p(hsh, ctypes.c_uint64), _p(bnd, ctypes.c_uint8))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments (code {rc})")
+    return FrustumResult(out, sumw, nacc, cnt, hsh, bnd)
+
+
+def weight_superres(s, sref, dq, fxJ, sigma_rgb, sigma_xyz, sigma_f, sigma_area) -> float:
+    """Eq. 7: Eq. 4 times exp(-s_area / (2 sigma_area^2)), s_area = (dq / fxJ)^2 (Eq. 6)."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    r = np.ascontiguousarray(sref, dtype=np.float64)
+    return _load().oc_weight_superres(_p(s, ctypes.c_double), _p(r, ctypes.c_double), float(dq), float(fxJ),
+                                      sigma_rgb, sigma_xyz, sigma_f, sigma_area)
+
+
+def superres_filter(view: ClipView, prm: Params, O: int, scale: int, crop=None, membership: bool = False,
+                    sigma_area: float | None = None) -> FrustumResult:
+    """Super-resolution (Eq. 6-7) of output frame O on the scale-times grid over an output-grid
+    crop (x0, y0, w, h) (default: the whole grid).  sigma_area defaults to prm.sigma_area, else to
+    one input-pixel footprint at the median depth (median depth / fx of O)."""
+    Wh, Hh = view.W * scale, view.H * scale
+    x0, y0, cw, ch = crop if crop is not None else (0, 0, Wh, Hh)
+    ns = 2 * prm.T + 1
+    out = np.zeros((ch, cw, 3))
+    sumw = np.zeros((ch, cw))
+    nacc = np.zeros((ch, cw), np.int64)
+    cnt = hsh = bnd = None
+    if membership:
+        cnt = np.zeros((ch, cw, ns), np.int32)
+        hsh = np.zeros((ch, cw, ns), np.uint64)
+        bnd = np.zeros((ch, cw, ns), np.uint8)
+    ps = prm.c_struct(float(view.K[O, 0, 0]))
+    if sigma_area is not None:
+        ps.sigma_area = sigma_area
+    elif not prm.sigma_area > 0:
+        ps.sigma_area = median_depth(view.depth) / float(view.K[O, 0, 0])
+    rc = _load().oc_superres_filter(ctypes.byref(view.c), ctypes.byref(ps), O, scale, x0, y0, cw, ch,
+                                    _p(out, ctypes.c_double), _p(sumw, ctypes.c_double), _p(nacc, ctypes.c_int64),
+                                    _p(cnt, ctypes.c_int32), _p(hsh, ctypes.c_uint64), _p(bnd, ctypes.c_uint8))
     if rc != 0:
         raise ValueError(f"oracle rejected the arguments (code {rc})")
     return FrustumResult(out, sumw, nacc, cnt, hsh, bnd)

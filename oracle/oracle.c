@@ -51,6 +51,17 @@
  *   axes, summed over the pixels that have a right and a lower neighbour); mode 5 replaces the
  *   weight by the shutter function xi(J - O).  Both apply to either gather.
  *
+ * Super-resolution (Sec. "Super resolution", Eq. 6-7): the output grid has `scale` times the
+ *   input resolution per axis; output pixel (U, V) sits at input coordinates
+ *   u = (U + 0.5) / scale - 0.5 (and v alike), and its camera is K_O with fx, fy scaled and the
+ *   principal point mapped the same way.  s_ref is the bilinear interpolation of colour and
+ *   depth at (u, v) (coordinates clamped to the image; an invalid depth among the four makes
+ *   the reference invalid, which outputs the interpolated colour).  Samples are gathered from
+ *   the output pixel's own frustum (Eq. 1-2 in output pixels) and weighted by Eq. 4 times
+ *   exp(-s_area / (2 sigma_area^2)) with s_area = (d_q / fx_J)^2, the squared scene length of
+ *   one pixel edge of the sample at its depth (Eq. 6 for a camera without skew); mode 3 uses
+ *   w = 1.
+ *
  * Built with -ffp-contract=off: every product and sum is rounded on its own.
  */
 #include <math.h>
@@ -84,6 +95,7 @@ typedef struct {
     double near_plane, far_plane;  /* frustum depth range (Eq. 1) */
     const double *frame_w;  /* mode 4: per input frame J the blurriness factor of Eq. 5 (F values) */
     const double *slot_w;   /* mode 5: the shutter function xi(J - O) of Eq. 10 at J = O-T+j (2T+1 values) */
+    double sigma_area;      /* super-resolution (Eq. 7): length scale of the s_area term */
 } oc_params;
 
 /* membership codes (low 3 bits) and band flag */
@@ -533,6 +545,135 @@ int oc_frustum_filter(const oc_clip *c, const oc_params *p, int O, int x0, int y
                         if (!in) continue;
                         double s[7] = {c->rgb[3 * qi], c->rgb[3 * qi + 1], c->rgb[3 * qi + 2], X[0], X[1], X[2], (double)J};
                         const double w = sample_weight(p, s, sref, J, j);
+                        for (int a = 0; a < 3; ++a) acc[a] += w * s[a];
+                        sw += w;
+                        ++mc;
+                        mh += mix64((uint64_t)qy * (uint64_t)W + (uint64_t)qx + 1u);
+                    }
+                cnt += mc;
+                if (mem_count) {
+                    mem_count[i * ns + j] = mc;
+                    mem_hash[i * ns + j] = mh;
+                    mem_band[i * ns + j] = mb;
+                }
+            }
+        }
+        for (int a = 0; a < 3; ++a) out_rgb[3 * i + a] = sw > 0.0 ? acc[a] / sw : sref[a];
+        out_sumw[i] = sw;
+        out_nacc[i] = cnt;
+    }
+    free(Gt);
+    return 0;
+}
+
+/* Eq. 7's weight of sample s (7-vector, depth d_q in frame J with focal length fx_J) against sref */
+double oc_weight_superres(const double *s, const double *sref, double dq, double fxJ, double sigma_rgb,
+                          double sigma_xyz, double sigma_f, double sigma_area) {
+    const double e = dq / fxJ;
+    const double s_area = e * e;
+    return oc_weight_denoise(s, sref, sigma_rgb, sigma_xyz, sigma_f) * exp(-s_area / (2.0 * sigma_area * sigma_area));
+}
+
+/* Output-grid intrinsics of super-resolution: K with fx, fy scaled and c -> scale (c + 0.5) - 0.5 */
+static void scaled_K(const double *K, int scale, double *Ks) {
+    memcpy(Ks, K, 9 * sizeof(double));
+    Ks[0] = K[0] * scale;
+    Ks[1] = K[1] * scale;
+    Ks[2] = scale * (K[2] + 0.5) - 0.5;
+    Ks[4] = K[4] * scale;
+    Ks[5] = scale * (K[5] + 0.5) - 0.5;
+}
+
+/* Bilinear value of a (H, W, nc) float image at (x, y), coordinates clamped to the image */
+static void bilinear(const float *img, int W, int H, int nc, double x, double y, double *out) {
+    x = x < 0 ? 0 : (x > W - 1 ? W - 1 : x);
+    y = y < 0 ? 0 : (y > H - 1 ? H - 1 : y);
+    int x0 = (int)floor(x), y0 = (int)floor(y);
+    int x1 = x0 + 1 < W ? x0 + 1 : W - 1, y1 = y0 + 1 < H ? y0 + 1 : H - 1;
+    double fx = x - x0, fy = y - y0;
+    for (int c = 0; c < nc; ++c) {
+        double a = img[((size_t)y0 * W + x0) * nc + c], b = img[((size_t)y0 * W + x1) * nc + c];
+        double d = img[((size_t)y1 * W + x0) * nc + c], e = img[((size_t)y1 * W + x1) * nc + c];
+        out[c] = (1.0 - fy) * ((1.0 - fx) * a + fx * b) + fy * ((1.0 - fx) * d + fx * e);
+    }
+}
+
+/*
+ * Super-resolution gather and filter of output frame O on the `scale`-times grid, over the
+ * output crop [X0, X0+CW) x [Y0, Y0+CH) (output-grid pixels).  Outputs as oc_frustum_filter.
+ */
+int oc_superres_filter(const oc_clip *c, const oc_params *p, int O, int scale, int X0, int Y0, int CW, int CH,
+                       double *out_rgb, double *out_sumw, int64_t *out_nacc, int32_t *mem_count, uint64_t *mem_hash,
+                       uint8_t *mem_band) {
+    if (p->T < 0 || O < 0 || O >= c->F || scale < 1 || !(p->frustum_l > 0) || !(p->near_plane > 0) ||
+        !(p->far_plane > p->near_plane) || !(p->sigma_area > 0))
+        return -1;
+    const int ns = 2 * p->T + 1, W = c->W, H = c->H;
+    double KOs[9], KOsi[9];
+    scaled_K(c->K + 9 * O, scale, KOs);
+    mat3_inverse(KOs, KOsi);
+    double *Gt = (double *)malloc(sizeof(double) * 12 * ns);
+    if (!Gt) return -2;
+    for (int j = 0; j < ns; ++j) {
+        int J = O - p->T + j;
+        double P[12];
+        if (J < 0 || J >= c->F) continue;
+        /* G_{O<-J} maps J pixels to O camera coordinates; the output grid only enters the test */
+        oc_compose(c->K + 9 * O, c->w2c + 12 * O, c->K + 9 * J, c->w2c + 12 * J, J == O, P, Gt + 12 * j);
+    }
+    long long n = (long long)CW * CH;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long i = 0; i < n; ++i) {
+        const int U = X0 + (int)(i % CW), V = Y0 + (int)(i / CW);
+        const double u = (U + 0.5) / scale - 0.5, v = (V + 0.5) / scale - 0.5;
+        double sref[7], dref, acc[3] = {0, 0, 0}, sw = 0.0;
+        int64_t cnt = 0;
+        bilinear(c->rgb + (size_t)O * H * W * 3, W, H, 3, u, v, sref);
+        bilinear(c->depth + (size_t)O * H * W, W, H, 1, u, v, &dref);
+        if (mem_count)
+            for (int j = 0; j < ns; ++j) {
+                mem_count[i * ns + j] = 0;
+                mem_hash[i * ns + j] = 0;
+                mem_band[i * ns + j] = 0;
+            }
+        /* an invalid depth among the four (NaN, inf or <= 0 before mixing) invalidates s_ref */
+        int ok = 1;
+        {
+            const double xc = u < 0 ? 0 : (u > W - 1 ? W - 1 : u), yc = v < 0 ? 0 : (v > H - 1 ? H - 1 : v);
+            const int x0 = (int)floor(xc), y0 = (int)floor(yc);
+            const int x1 = x0 + 1 < W ? x0 + 1 : W - 1, y1 = y0 + 1 < H ? y0 + 1 : H - 1;
+            const float *D = c->depth + (size_t)O * H * W;
+            ok = valid_depth(D[(size_t)y0 * W + x0]) && valid_depth(D[(size_t)y0 * W + x1]) &&
+                 valid_depth(D[(size_t)y1 * W + x0]) && valid_depth(D[(size_t)y1 * W + x1]);
+        }
+        if (ok) {
+            double UV1[3] = {U, V, 1.0}, ray[3];
+            mat3_vec(KOsi, UV1, ray);
+            for (int a = 0; a < 3; ++a) sref[3 + a] = dref * ray[a];
+            sref[6] = O;
+            for (int j = 0; j < ns; ++j) {
+                const int J = O - p->T + j;
+                if (J < 0 || J >= c->F) continue;
+                const double *G = Gt + 12 * j;
+                const double fxJ = c->K[9 * J];
+                int32_t mc = 0;
+                uint64_t mh = 0;
+                uint8_t mb = 0;
+                for (int qy = 0; qy < H; ++qy)
+                    for (int qx = 0; qx < W; ++qx) {
+                        const size_t qi = ((size_t)J * H + qy) * W + qx;
+                        const float dq = c->depth[qi];
+                        if (!valid_depth(dq)) continue;
+                        double q3[3] = {qx * (double)dq, qy * (double)dq, (double)dq}, X[3];
+                        apply34(G, q3, X);
+                        int band;
+                        const int in = in_frustum(KOs, X, U, V, p, &band);
+                        mb |= (uint8_t)band;
+                        if (!in) continue;
+                        double s[7] = {c->rgb[3 * qi], c->rgb[3 * qi + 1], c->rgb[3 * qi + 2], X[0], X[1], X[2], (double)J};
+                        const double w = p->mode == 3 ? 1.0
+                                                      : oc_weight_superres(s, sref, dq, fxJ, p->sigma_rgb, p->sigma_xyz,
+                                                                           p->sigma_f, p->sigma_area);
                         for (int a = 0; a < 3; ++a) acc[a] += w * s[a];
                         sw += w;
                         ++mc;
