@@ -86,6 +86,10 @@ def _load():
                                       ctypes.c_int, ctypes.c_int, u8p]
         lib.oc_bruteforce.restype = ctypes.c_longlong
         lib.oc_frame_sharpness.argtypes = [ctypes.POINTER(_Clip), dp]
+        lib.oc_mask_from_box.argtypes = [ctypes.POINTER(_Clip), dp, u8p]
+        lib.oc_inpaint_filter.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), u8p] + [ctypes.c_int] * 5 + \
+            [dp, dp, i64p, i32p, ctypes.POINTER(ctypes.c_uint64), u8p]
+        lib.oc_inpaint_filter.restype = ctypes.c_int
         lib.oc_weight_superres.argtypes = [dp, dp] + [ctypes.c_double] * 6
         lib.oc_weight_superres.restype = ctypes.c_double
         lib.oc_superres_filter.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params)] + [ctypes.c_int] * 6 + \
@@ -332,6 +336,38 @@ def superres_filter(view: ClipView, prm: Params, O: int, scale: int, crop=None, 
     rc = _load().oc_superres_filter(ctypes.byref(view.c), ctypes.byref(ps), O, scale, x0, y0, cw, ch,
                                     _p(out, ctypes.c_double), _p(sumw, ctypes.c_double), _p(nacc, ctypes.c_int64),
                                     _p(cnt, ctypes.c_int32), _p(hsh, ctypes.c_uint64), _p(bnd, ctypes.c_uint8))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments (code {rc})")
+    return FrustumResult(out, sumw, nacc, cnt, hsh, bnd)
+
+
+def mask_from_box(view: ClipView, box) -> np.ndarray:
+    """Eq. 8-9's removal mask (F, H, W) uint8 from a world-space box (xmin, ymin, zmin, xmax, ymax, zmax)."""
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    assert b.shape == (6,)
+    m = np.zeros((view.F, view.H, view.W), np.uint8)
+    _load().oc_mask_from_box(ctypes.byref(view.c), _p(b, ctypes.c_double), _p(m, ctypes.c_uint8))
+    return m
+
+
+def inpaint_filter(view: ClipView, prm: Params, mask, O: int, crop=None, membership: bool = False) -> FrustumResult:
+    """Inpainting (Eq. 8-9) of output frame O over crop (x0, y0, w, h) with the frustum gather."""
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    assert mask.shape == (view.F, view.H, view.W)
+    x0, y0, cw, ch = crop if crop is not None else (0, 0, view.W, view.H)
+    ns = 2 * prm.T + 1
+    out = np.zeros((ch, cw, 3))
+    sumw = np.zeros((ch, cw))
+    nacc = np.zeros((ch, cw), np.int64)
+    cnt = hsh = bnd = None
+    if membership:
+        cnt = np.zeros((ch, cw, ns), np.int32)
+        hsh = np.zeros((ch, cw, ns), np.uint64)
+        bnd = np.zeros((ch, cw, ns), np.uint8)
+    ps = prm.c_struct(float(view.K[O, 0, 0]))
+    rc = _load().oc_inpaint_filter(ctypes.byref(view.c), ctypes.byref(ps), _p(mask, ctypes.c_uint8), O, x0, y0, cw, ch,
+                                   _p(out, ctypes.c_double), _p(sumw, ctypes.c_double), _p(nacc, ctypes.c_int64),
+                                   _p(cnt, ctypes.c_int32), _p(hsh, ctypes.c_uint64), _p(bnd, ctypes.c_uint8))
     if rc != 0:
         raise ValueError(f"oracle rejected the arguments (code {rc})")
     return FrustumResult(out, sumw, nacc, cnt, hsh, bnd)

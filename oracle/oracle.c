@@ -62,6 +62,15 @@
  *   one pixel edge of the sample at its depth (Eq. 6 for a camera without skew); mode 3 uses
  *   w = 1.
  *
+ * Inpainting (Sec. "Inpainting and semi-transparency", Eq. 8-9): a per-frame mask M marks the
+ *   pixels to remove; from a scene-space box, M_J(q) = 1 when q's world point (its depth
+ *   unprojected with the camera of J) lies inside the box.  A pixel with M_O(p) = 0 keeps its
+ *   input colour.  A masked pixel gathers its frustum S(p) (Eq. 1-2; its own depth is not used)
+ *   and starts from the mean colour of all of S(p) (Eq. 8); two steps of the weighted mean of
+ *   Eq. 9 follow, each with w = exp(-|c_ref - c|^2 / (2 sigma_rgb^2)) for unmasked samples and 0
+ *   for masked ones, the result of a step being the next step's reference (a step whose weights
+ *   are all 0 keeps the reference).  An empty S(p) keeps the input colour.
+ *
  * Built with -ffp-contract=off: every product and sum is rounded on its own.
  */
 #include <math.h>
@@ -693,6 +702,149 @@ int oc_superres_filter(const oc_clip *c, const oc_params *p, int O, int scale, i
     }
     free(Gt);
     return 0;
+}
+
+/* Eq. 8-9's mask from a scene-space axis-aligned box = {xmin, ymin, zmin, xmax, ymax, zmax} (world
+ * coordinates, inclusive): mask F*H*W bytes, 1 inside, 0 outside or for an invalid depth. */
+void oc_mask_from_box(const oc_clip *c, const double *box, uint8_t *mask) {
+    const int W = c->W, H = c->H;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int f = 0; f < c->F; ++f) {
+        double Ki[9], R[9], t[3];
+        mat3_inverse(c->K + 9 * f, Ki);
+        split_rt(c->w2c + 12 * f, R, t);
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const size_t i = ((size_t)f * H + y) * W + x;
+                const float d = c->depth[i];
+                uint8_t m = 0;
+                if (valid_depth(d)) {
+                    double q[3] = {x, y, 1.0}, ray[3], Xc[3], Xw[3];
+                    mat3_vec(Ki, q, ray);
+                    for (int a = 0; a < 3; ++a) Xc[a] = (double)d * ray[a] - t[a];
+                    for (int a = 0; a < 3; ++a) Xw[a] = R[a] * Xc[0] + R[3 + a] * Xc[1] + R[6 + a] * Xc[2];  /* R^T */
+                    m = Xw[0] >= box[0] && Xw[1] >= box[1] && Xw[2] >= box[2] && Xw[0] <= box[3] && Xw[1] <= box[4] &&
+                        Xw[2] <= box[5];
+                }
+                mask[i] = m;
+            }
+    }
+}
+
+/*
+ * Inpainting of the crop [x0, x0+cw) x [y0, y0+ch) of output frame O (see the header comment).
+ * mask: F*H*W bytes (nonzero = remove).  Outputs as oc_frustum_filter (nacc = |S(p)| of masked
+ * pixels, sumw = the last step's sum of weights); records only for masked pixels.
+ */
+int oc_inpaint_filter(const oc_clip *c, const oc_params *p, const uint8_t *mask, int O, int x0, int y0, int cw, int ch,
+                      double *out_rgb, double *out_sumw, int64_t *out_nacc, int32_t *mem_count, uint64_t *mem_hash,
+                      uint8_t *mem_band) {
+    if (p->T < 0 || O < 0 || O >= c->F || !(p->frustum_l > 0) || !(p->near_plane > 0) ||
+        !(p->far_plane > p->near_plane) || !(p->sigma_rgb > 0))
+        return -1;
+    const int ns = 2 * p->T + 1, W = c->W, H = c->H;
+    double *Gt = (double *)malloc(sizeof(double) * 12 * ns);
+    if (!Gt) return -2;
+    for (int j = 0; j < ns; ++j) {
+        int J = O - p->T + j;
+        double P[12];
+        if (J < 0 || J >= c->F) continue;
+        oc_compose(c->K + 9 * O, c->w2c + 12 * O, c->K + 9 * J, c->w2c + 12 * J, J == O, P, Gt + 12 * j);
+    }
+    const double *KO = c->K + 9 * O;
+    long long n = (long long)cw * ch;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long i = 0; i < n; ++i) {
+        const int u = x0 + (int)(i % cw), v = y0 + (int)(i / cw);
+        const size_t pix = ((size_t)O * H + v) * W + u;
+        double ref[3] = {c->rgb[3 * pix], c->rgb[3 * pix + 1], c->rgb[3 * pix + 2]}, sw = 0.0;
+        int64_t cnt = 0;
+        if (mem_count)
+            for (int j = 0; j < ns; ++j) {
+                mem_count[i * ns + j] = 0;
+                mem_hash[i * ns + j] = 0;
+                mem_band[i * ns + j] = 0;
+            }
+        if (mask[pix]) {
+            /* S(p): colours and mask flags of every sample */
+            size_t cap = 1024, m = 0;
+            double *col = (double *)malloc(sizeof(double) * 3 * cap);
+            uint8_t *msk = (uint8_t *)malloc(cap);
+            for (int j = 0; j < ns && col && msk; ++j) {
+                const int J = O - p->T + j;
+                if (J < 0 || J >= c->F) continue;
+                const double *G = Gt + 12 * j;
+                int32_t mc = 0;
+                uint64_t mh = 0;
+                uint8_t mb = 0;
+                for (int qy = 0; qy < H; ++qy)
+                    for (int qx = 0; qx < W; ++qx) {
+                        const size_t qi = ((size_t)J * H + qy) * W + qx;
+                        const float dq = c->depth[qi];
+                        if (!valid_depth(dq)) continue;
+                        double q3[3] = {qx * (double)dq, qy * (double)dq, (double)dq}, X[3];
+                        apply34(G, q3, X);
+                        int band;
+                        const int in = in_frustum(KO, X, u, v, p, &band);
+                        mb |= (uint8_t)band;
+                        if (!in) continue;
+                        if (m == cap) {
+                            cap *= 2;
+                            double *c2 = (double *)realloc(col, sizeof(double) * 3 * cap);
+                            uint8_t *m2 = (uint8_t *)realloc(msk, cap);
+                            if (!c2 || !m2) { free(c2 ? c2 : col); free(m2 ? m2 : msk); col = NULL; msk = NULL; break; }
+                            col = c2;
+                            msk = m2;
+                        }
+                        for (int a = 0; a < 3; ++a) col[3 * m + a] = c->rgb[3 * qi + a];
+                        msk[m] = mask[qi] != 0;
+                        ++m;
+                        ++mc;
+                        mh += mix64((uint64_t)qy * (uint64_t)W + (uint64_t)qx + 1u);
+                    }
+                if (mem_count) {
+                    mem_count[i * ns + j] = mc;
+                    mem_hash[i * ns + j] = mh;
+                    mem_band[i * ns + j] = mb;
+                }
+                if (!col) break;
+            }
+            if (!col || !msk) {
+#pragma omp atomic write
+                err = 1;
+            } else if (m > 0) {
+                /* Eq. 8: the mean of all samples */
+                double acc[3] = {0, 0, 0};
+                for (size_t k = 0; k < m; ++k)
+                    for (int a = 0; a < 3; ++a) acc[a] += col[3 * k + a];
+                for (int a = 0; a < 3; ++a) ref[a] = acc[a] / (double)m;
+                /* Eq. 9, two steps */
+                for (int step = 0; step < 2; ++step) {
+                    double num[3] = {0, 0, 0}, den = 0.0;
+                    for (size_t k = 0; k < m; ++k) {
+                        if (msk[k]) continue;
+                        double d2 = 0.0;
+                        for (int a = 0; a < 3; ++a) d2 += (col[3 * k + a] - ref[a]) * (col[3 * k + a] - ref[a]);
+                        const double w = exp(-d2 / (2.0 * p->sigma_rgb * p->sigma_rgb));
+                        for (int a = 0; a < 3; ++a) num[a] += w * col[3 * k + a];
+                        den += w;
+                    }
+                    sw = den;
+                    if (den > 0.0)
+                        for (int a = 0; a < 3; ++a) ref[a] = num[a] / den;
+                }
+            }
+            cnt = (int64_t)m;
+            free(col);
+            free(msk);
+        }
+        for (int a = 0; a < 3; ++a) out_rgb[3 * i + a] = ref[a];
+        out_sumw[i] = sw;
+        out_nacc[i] = cnt;
+    }
+    free(Gt);
+    return err ? -2 : 0;
 }
 
 /*
