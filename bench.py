@@ -36,7 +36,11 @@ WORKLOADS = {
     "frustum-hd": (1280, 720, 60, 15, 7, 15, 1, 4),  # frustum gather at 720p +-15
     "deblur": (1920, 1080, 68, 30, 7, 30, 8, 5),     # Eq. 5 weights, every 4th frame shaken, 1080p +-30
     "shutter": (1920, 1080, 68, 30, 7, 30, 8, 6),    # Eq. 10 long exposure (box shutter), 1080p +-30
+    "superres": (640, 360, 68, 30, 7, 30, 2, 7),     # Eq. 6-7: 640x360 input -> 1920x1080 output, +-30
+    "inpaint": (1920, 1080, 68, 30, 7, 30, 8, 8),    # Eq. 8-9: one box of the scene removed, 1080p +-30
 }
+INPAINT_OBJECT, INPAINT_SIGMA_RGB = 9, 55.0 / 255.0  # the scene's fourth box; the paper's sigma_rgb = 55
+SR_SCALE = 3
 W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE = WORKLOADS["fhd"]
 APERTURE, LENS, CAP = 0.05, 16, 31
 RADIUS_REL = 0.005
@@ -151,6 +155,12 @@ def _workload_clip(seed):
     return synth.make_clip("room", W, H, F, seed=seed)
 
 
+def _inpaint_box(clip):
+    """World box around the removed object (kept off the floor and ceiling planes it may touch)."""
+    import synth
+    return synth.object_box(clip.meta["objects"][INPAINT_OBJECT], 0.02, (-2.2 + 0.02, 1.5 - 0.02))
+
+
 def _shutter_xi():
     """The long exposure of Sec. "Computational scene-space shutters": a box over the window."""
     return np.ones(2 * T + 1, np.float32)
@@ -170,6 +180,13 @@ def _oracle_params(clip):
 
 
 def _config(colour):
+    if MODE == 8:
+        return {"workload": f"inpaint-{W}x{H}-pm{T}-l3-{colour}", "W": W, "H": H, "frames": F,
+                "out_frames_per_step": N_OUT, "half_window": T, "gather": "frustum (Eq. 1-2), l = 3 px",
+                "weights": "Eq. 8 mean then two Eq. 9 steps, sigma_rgb = 55/255",
+                "mask": f"world box around object {INPAINT_OBJECT} (a box), unprojected depth inside it",
+                "scene": "synthetic 6 planes + 4 boxes, hand-held path, depth noise 2%, image noise 0.05",
+                "colour": colour, "l2": "no flush: packed input planes exceed the 129 MB L2"}
     if MODE == 4:
         return {"workload": f"frustum-{W}x{H}-pm{T}-l3-{colour}", "W": W, "H": H, "frames": F,
                 "out_frames_per_step": N_OUT, "half_window": T, "gather": "frustum (Eq. 1-2), l = 3 px, L1 test",
@@ -209,6 +226,40 @@ def cpu_oracle_sample(clip, target_s=10.0, O=None, max_frames=None):
     max_frames = N_OUT if max_frames is None else max_frames
     v = oracle.ClipView.of(clip)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    if MODE == 8:
+        prm = oracle.Params(mode=oracle.MODE_DENOISE, k=1, T=T, radius=RADIUS_REL, sigma_rgb=INPAINT_SIGMA_RGB,
+                            gather=oracle.GATHER_FRUSTUM, frustum_l=FRUSTUM_L)
+        mask = oracle.mask_from_box(v, _inpaint_box(clip))
+        ys, xs = np.nonzero(mask[O])
+        cy, cx = (int(np.median(ys)), int(np.median(xs))) if len(ys) else (H // 2, W // 2)
+        side = 4
+        while True:
+            crop = (min(max(cx - side // 2, 0), W - side), min(max(cy - side // 2, 0), H - side), side, side)
+            t0 = time.perf_counter()
+            res = oracle.inpaint_filter(v, prm, mask, O, crop=crop)
+            dt = time.perf_counter() - t0
+            if dt > target_s / 4 or 2 * side > 64:
+                break
+            side *= 2
+        return dict(frames=1, crop=crop, seconds=dt, mpix_s=side * side / dt / 1e6, cores=cores, results=[res],
+                    examined=0, accepted=int(res.nacc.sum()),
+                    sample=f"{side}x{side} crop on the removed object in output frame {O} ({dt:.1f} s)")
+    if MODE == 7:
+        med = oracle.median_depth(clip.depth)
+        prm = oracle.Params(mode=oracle.MODE_DENOISE, k=1, T=T, radius=RADIUS_REL * med, sigma_rgb=50.0 / 255.0,
+                            sigma_xyz=FRUSTUM_SIGMA_XYZ_REL * med, gather=oracle.GATHER_FRUSTUM, frustum_l=FRUSTUM_L)
+        Wo, Ho, side = W * SR_SCALE, H * SR_SCALE, 4
+        while True:
+            crop = ((Wo - side) // 2, (Ho - side) // 2, side, side)
+            t0 = time.perf_counter()
+            res = oracle.superres_filter(v, prm, O, SR_SCALE, crop=crop)
+            dt = time.perf_counter() - t0
+            if dt > target_s / 4 or 2 * side > 64:
+                break
+            side *= 2
+        return dict(frames=1, crop=crop, seconds=dt, mpix_s=side * side / dt / 1e6, cores=cores, results=[res],
+                    examined=0, accepted=int(res.nacc.sum()),
+                    sample=f"{side}x{side} centre crop of the 3x output grid of frame {O} ({dt:.1f} s)")
     if MODE == 4:
         med = oracle.median_depth(clip.depth)
         prm = oracle.Params(mode=oracle.MODE_DENOISE, k=1, T=T, radius=RADIUS_REL * med,
@@ -441,6 +492,135 @@ def run_learned(args, ss, torch, dev, stream, world, rank):
     ss.ssvp_destroy(ctx)
     return line
 
+def run_superres(args, ss, torch, dev, stream, world, rank):
+    """Super-resolution (Sec. "Super resolution", Eq. 6-7): 640x360 input frames, +-30, onto the
+    3x grid (1920x1080 output), frustum l = 3 output pixels, sigma_rgb = 50/255 (the paper's 50),
+    sigma_area = one input-pixel footprint at the median depth."""
+    import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    s = SR_SCALE
+    Wo, Ho = W * s, H * s
+    clip = _workload_clip(seed=shard(rank, world)["seed"])
+    ctx = ss.ssvp_create(local, stream)
+    r, d = torch.from_numpy(clip.rgb).to(dev), torch.from_numpy(clip.depth).to(dev)
+    ss.ssvp_load_clip(ctx, 0, W, H, F, r, d)
+    ss.ssvp_set_cameras(ctx, 0, clip.K, 1, clip.w2c)
+    ss.ssvp_sync(ctx)
+    del r, d
+    p = ss.ssvp_params_default()
+    p.half_window, p.frame_begin, p.frame_end = T, O_BEGIN, O_BEGIN + N_OUT
+    p.frustum_l, p.sigma_rgb, p.radius, p.sigma_xyz = FRUSTUM_L, 50.0 / 255.0, -FRUSTUM_SIGMA_XYZ_REL, 0.0
+    out = torch.empty((N_OUT, Ho, Wo, 3), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ss.ssvp_superres(ctx, p, 0, s, out)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            ss.ssvp_superres(ctx, p, 0, s, out)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = max_over_ranks(float(np.sum(step_ms)), world, dev) / args.steps
+    examined, accepted, _ = ss.ssvp_read_stats(ctx)
+    outn = out.cpu().numpy()
+    # references: the clean render on the output grid, and bilinear upsampling of the input
+    objs, _, _ = synth.scene_and_path("room", W, H, F, shard(rank, world)["seed"])
+    Kh = np.repeat(synth.intrinsics(Wo, Ho)[None], N_OUT, axis=0)
+    clean_hr, _, _, _ = synth.render(objs, Kh, clip.w2c_true[O_BEGIN:O_BEGIN + N_OUT], Wo, Ho)
+    psnr = lambda a_, b_: float(10 * np.log10(1.0 / np.mean((a_.astype(np.float64) - b_) ** 2)))
+
+    def upsample(img):
+        t = torch.from_numpy(np.ascontiguousarray(img.transpose(0, 3, 1, 2)))
+        return torch.nn.functional.interpolate(t, scale_factor=s, mode="bilinear", align_corners=False).numpy().transpose(0, 2, 3, 1)
+
+    bil_noisy = upsample(clip.rgb[O_BEGIN:O_BEGIN + N_OUT])
+    bil_clean = upsample(clip.clean[O_BEGIN:O_BEGIN + N_OUT])
+    # end to end: host inputs uploaded, output read back to pinned host memory
+    rgb_h = torch.from_numpy(clip.rgb).pin_memory()
+    dep_h = torch.from_numpy(clip.depth).pin_memory()
+    out_h = torch.empty((N_OUT, Ho, Wo, 3), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        ss.ssvp_load_clip(ctx, 1, W, H, F, rgb_h, dep_h, ss.SSVP_MEM_HOST, ss.SSVP_COLOUR_F32)
+        ss.ssvp_set_cameras(ctx, 1, clip.K, 1, clip.w2c)
+        ss.ssvp_superres(ctx, p, 1, s, out)
+        out_h.copy_(out, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(2, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
+    peaks, peak_kind = _peaks()
+    kernel_ms = float(np.mean(step_ms))
+    achieved = (4 * examined + 16 * accepted) / (kernel_ms / 1e3) / 1e9
+    clk_summary = clk.summary()
+    sm_hz = (clk_summary["sm_mhz"] or 2070.0) * 1e6
+    fp32_peak = 152 * 128 * sm_hz / 1e12
+    mpix = N_OUT * Wo * Ho / 1e6
+    line = {
+        "metric": METRIC, "value": world * mpix / (ms / 1e3), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded procedural scene, rendered on the host)",
+        "config": {"workload": f"superres-{W}x{H}-to-{Wo}x{Ho}-pm{T}-fp32", "W_in": W, "H_in": H, "scale": s,
+                   "frames": F, "out_frames_per_step": N_OUT, "half_window": T, "frustum_l_output_px": FRUSTUM_L,
+                   "sigma_rgb": "50/255", "sigma_xyz": f"{FRUSTUM_SIGMA_XYZ_REL:g} x median depth",
+                   "sigma_area": "median depth / fx (one input pixel at the median depth)",
+                   "scene": "synthetic 6 planes + 4 boxes, hand-held path, depth noise 2%, image noise 0.05",
+                   "l2": "no flush: the step reads 61 input frames per output frame (~0.9 GB) and writes 50 MB"},
+        "samples_per_s": {"examined": world * examined / (ms / 1e3), "accepted": world * accepted / (ms / 1e3)},
+        "accepted_per_pixel": accepted / (N_OUT * Wo * Ho),
+        "psnr_db": {"output_vs_clean_1080p": psnr(outn, clean_hr), "bilinear_of_input": psnr(bil_noisy, clean_hr),
+                    "bilinear_of_clean_input": psnr(bil_clean, clean_hr),
+                    "reference": "clean render on the 1920x1080 grid (true poses)"},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "accounting": f"4 B depth per examined candidate + 16 B colour per sample, {peak_kind} peak",
+                     "kernel_ms": kernel_ms},
+        "roofline_alu": {"bound": "alu", "achieved": examined * 11 / (kernel_ms / 1e3) / 1e12, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": examined * 11 / (kernel_ms / 1e3) / 1e12 / fp32_peak,
+                         "accounting": "11 FP32 operations per examined candidate; peak = 152 SMs x 128 lanes x clock"},
+        "e2e": {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s",
+                "h2d_bytes_per_step": clip.rgb.nbytes + clip.depth.nbytes, "d2h_bytes_per_step": out_h.numel() * 4,
+                "ms_per_step": e2e_ms},
+        "clocks": clk_summary,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        v = oracle.ClipView.of(clip)
+        med = oracle.median_depth(clip.depth)
+        prm = oracle.Params(mode=oracle.MODE_DENOISE, k=1, T=T, radius=RADIUS_REL * med, sigma_rgb=50.0 / 255.0,
+                            sigma_xyz=FRUSTUM_SIGMA_XYZ_REL * med, gather=oracle.GATHER_FRUSTUM, frustum_l=FRUSTUM_L)
+        side = 4
+        while True:
+            crop = ((Wo - side) // 2, (Ho - side) // 2, side, side)
+            t0 = time.perf_counter()
+            res = oracle.superres_filter(v, prm, O_BEGIN, s, crop=crop)
+            dt = time.perf_counter() - t0
+            if dt > 2.5 or 2 * side > 64:
+                break
+            side *= 2
+        x0, y0 = crop[:2]
+        diff = np.abs(outn[0, y0:y0 + side, x0:x0 + side].astype(np.float64) - res.rgb).max(-1)
+        line["cpu_baseline"] = {"value": side * side / dt / 1e6, "unit": "Mpix/s",
+                                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+                                "sample": f"{side}x{side} centre crop of output frame {O_BEGIN} ({dt:.1f} s)"}
+        line["max_abs_vs_oracle"] = {"value": float(diff.max()), "pixels": int(diff.size)}
+    ss.ssvp_destroy(ctx)
+    return line
+
+
 def run_reference(args):
     """The oracle on the host cores, on this benchmark's workload, metric and unit."""
     rank = int(os.environ.get("RANK", "0"))
@@ -508,8 +688,8 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    if args.workload in ("batch", "learned", "learned-hd"):
-        fn = run_batch if args.workload == "batch" else run_learned
+    if args.workload in ("batch", "learned", "learned-hd", "superres"):
+        fn = {"batch": run_batch, "superres": run_superres}.get(args.workload, run_learned)
         line = fn(args, ss, torch, dev, stream, world, rank)
         if rank == 0:
             print(json.dumps(line))
@@ -538,6 +718,9 @@ def main():
     if MODE == 6:
         p.mode = ss.SSVP_MODE_SHUTTER
         ss.ssvp_set_shutter(ctx, _shutter_xi(), T)
+    if MODE == 8:
+        p.mode, p.gather, p.frustum_l, p.sigma_rgb = ss.SSVP_MODE_INPAINT, ss.SSVP_GATHER_FRUSTUM, FRUSTUM_L, INPAINT_SIGMA_RGB
+        ss.ssvp_mask_from_box(ctx, 0, _inpaint_box(clip))
 
     def barrier():
         if world > 1:
@@ -589,6 +772,17 @@ def main():
         psnr_ref = "thin-lens render (256 rays/pixel) of the first output frame"
 
     extra_quality = {}
+    if MODE == 8:
+        # quality on the removed object's pixels against a render of the scene without it
+        import synth
+        objs = list(clip.meta["objects"])
+        del objs[INPAINT_OBJECT]
+        bg, _, _, _ = synth.render(objs, clip.K[O_BEGIN:O_BEGIN + N_OUT], clip.w2c_true[O_BEGIN:O_BEGIN + N_OUT], W, H)
+        m = ss.ssvp_read_mask(ctx, 0, F, H, W)[O_BEGIN:O_BEGIN + N_OUT].astype(bool)
+        extra_quality = {"masked_fraction": float(m.mean()),
+                         "inpainted_vs_object_free_render_on_mask": psnr(outn[m], bg[m]),
+                         "input_vs_object_free_render_on_mask": psnr(noisy[m], bg[m]),
+                         "outside_mask_unchanged": bool(np.array_equal(outn[~m], noisy[~m]))}
     if MODE == 5:
         # the same clip through plain Eq. 4 with the same sigmas, outside the timed region
         p.mode = ss.SSVP_MODE_DENOISE
@@ -616,6 +810,8 @@ def main():
     def e2e_step():
         ss.ssvp_load_clip(ctx, 1, W, H, F, rgb_h, dep_h, ss.SSVP_MEM_HOST, cfmt)
         ss.ssvp_set_cameras(ctx, 1, clip.K, 1, clip.w2c)
+        if MODE == 8:
+            ss.ssvp_mask_from_box(ctx, 1, _inpaint_box(clip))
         ss.ssvp_gather_filter(ctx, p, [1])
         ss.ssvp_read_output(ctx, 1, O_BEGIN, O_BEGIN + N_OUT, out_h, ss.SSVP_MEM_HOST)
 
@@ -643,8 +839,10 @@ def main():
                   "frac > 1 because window loads are served from L1 (traffic = DRAM bytes per launch)")
     alu_ops = 8
     alu_note = "8 FP32 operations per examined candidate (the distance test)"
-    if MODE == 4:
+    if MODE in (4, 8):
         cb = COLOUR_BYTES[args.colour]
+        passes = 3 if MODE == 8 else 1  # inpainting scans S(p) three times (Eq. 8 mean, two Eq. 9 steps)
+        examined, accepted = passes * examined, passes * accepted
         achieved = (4 * examined + cb * accepted) / (kernel_ms / 1e3) / 1e9
         accounting = (f"4 B depth per examined candidate + {cb} B colour per sample, {peak_kind} peak; the hull "
                       "pixels of neighbouring output pixels overlap, so most loads are cache hits")

@@ -54,8 +54,10 @@ enum {
     SSVP_MODE_MEAN = 3,      /* w = 1 (the plain average of Sec. "Denoising") */
     SSVP_MODE_DEBLUR = 4,    /* Eq. 5: Eq. 4 times the sample frame's gradient-magnitude sum
                                 (Sec. "Deblurring"; see ssvp_frame_sharpness) */
-    SSVP_MODE_SHUTTER = 5    /* Eq. 10: w = xi(J - O) alone, xi from ssvp_set_shutter
+    SSVP_MODE_SHUTTER = 5,   /* Eq. 10: w = xi(J - O) alone, xi from ssvp_set_shutter
                                 (Sec. "Computational scene-space shutters") */
+    SSVP_MODE_INPAINT = 6    /* Eq. 8-9 with the frustum gather: masked pixels are replaced
+                                (Sec. "Inpainting and semi-transparency"; see ssvp_set_mask) */
 };
 enum {
     SSVP_GATHER_WINDOW = 0,  /* depth-seeded k x k window + radius (or the aperture cone) */
@@ -87,10 +89,12 @@ enum {
  *                 L1 distance frustum_l / 2 of the output pixel (|u - u'| + |v - v'| < l / 2,
  *                 strict) is a sample, whatever its depth; the output depth is not used to
  *                 gather, only for s_ref in Eq. 4 (an invalid output depth still gives c_ref).
- *                 Denoise and mean modes only; k is ignored and the radius serves only as the
- *                 default sigma_xyz.  Not available in batched plans.
+ *                 Denoise, mean, deblur, shutter and inpaint modes; k is ignored and the radius
+ *                 serves only as the default sigma_xyz.  Not available in batched plans.
  *   frustum_l, near_plane, far_plane   frustum size l in pixels (0 < l <= 64; the paper uses 3)
  *                 and its O depth range (0 < near < far; the paper uses 0.01 and 1000)
+ *   sigma_area    ssvp_superres only: length scale of Eq. 7's area term (scene units); <= 0 means
+ *                 one input-pixel footprint at the median depth (median depth / fx of O)
  *   membership_out   optional device buffer (debug): per crop pixel (row-major) and per slot
  *                 j = 0..2T (J = O-T+j) a record of 3 + ceil(k*k/32) int32 words:
  *                 status (-2 invalid reference depth, -1 J outside the clip, 0 J skipped: the
@@ -99,7 +103,8 @@ enum {
  *                 (bit dy*k+dx).  In aperture mode the record is 5 + ceil(cap*cap/32) words:
  *                 status, the scanned box x0, y0, x1, y1 (inclusive, before clipping to the
  *                 image), then the accepted bits of the box (bit (y-y0)*cap + (x-x0)).  With
- *                 the frustum gather it is 4 words: status (-2, -1 as above, 0 the frustum
+ *                 the frustum gather it is 4 words: status (-2, -1 as above, -2 also for an
+ *                 unmasked pixel in inpainting, 0 the frustum
  *                 misses J's depth range or image, 1 scanned), the number of samples from J,
  *                 and the low and high words of the wrapping 64-bit sum over them of
  *                 SplitMix64's output function of qy*W + qx + 1 (an order-free checksum).
@@ -129,9 +134,53 @@ typedef struct ssvp_params {
     float frustum_l;
     float near_plane;
     float far_plane;
+    float sigma_area;
     void *membership_out;
     void *pixel_stats_out;
 } ssvp_params;
+
+/*
+ * Super-resolution (Sec. "Super resolution", Eq. 6-7) of output frames [frame_begin, frame_end)
+ * of clip `clip_id` on a grid of `scale` (1..8) times the input resolution per axis.  Output
+ * pixel (U, V) sits at input coordinates ((U + 0.5) / scale - 0.5, (V + 0.5) / scale - 0.5);
+ * its camera is K_O with fx, fy scaled and the principal point mapped the same way.  s_ref is
+ * the bilinear interpolation of the input colour and depth there (coordinates clamped to the
+ * image; an invalid depth among the four pixels makes the reference invalid and the output
+ * the interpolated colour).  Samples are gathered from the output pixel's own frustum (the
+ * frustum gather of Eq. 1-2 with frustum_l in output pixels, near_plane, far_plane) over the
+ * window [O - half_window, O + half_window] and weighted by Eq. 7: Eq. 4 (sigma_rgb, sigma_xyz,
+ * sigma_f; the paper uses sigma_rgb = 50 on a 0-255 scale) times exp(-s_area / (2
+ * sigma_area^2)) with s_area = (d_q / fx_J)^2, the squared scene length of one pixel edge of the
+ * sample at its depth (Eq. 6); SSVP_MODE_MEAN uses w = 1.  params.gather and k are ignored.
+ * out: a device buffer of (frame_end - frame_begin) x (H scale) x (W scale) x 3 floats owned by
+ * the caller (with a crop, in output-grid pixels, only the crop is written).  Debug outputs as
+ * for the frustum gather, per output-grid crop pixel.  Queued on the context's stream.
+ */
+int ssvp_superres(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, int scale, float *out);
+
+/*
+ * Inpainting mask of clip `clip_id` (Sec. "Inpainting and semi-transparency", Eq. 8-9): F*H*W
+ * bytes, nonzero = the pixel shows something to remove, on the host (SSVP_MEM_HOST) or device
+ * (SSVP_MEM_DEVICE), copied.  SSVP_MODE_INPAINT (with gather = SSVP_GATHER_FRUSTUM) replaces every
+ * masked output pixel: it gathers the pixel's frustum S(p) (its own depth is not used), starts
+ * from the mean colour of all of S(p) (Eq. 8) and takes two steps of the weighted mean with
+ * w = exp(-|c_ref - c|^2 / (2 sigma_rgb^2)) over the unmasked samples (masked ones weigh 0,
+ * Eq. 9), each step's result being the next step's c_ref; a step whose weights are all 0 keeps
+ * its reference, an empty S(p) keeps the input colour.  Unmasked pixels keep their input colour.
+ * The paper uses sigma_rgb = 55 on a 0-255 scale.  The mask lives until the clip is unloaded.
+ */
+int ssvp_set_mask(ssvp_ctx *ctx, int clip_id, const uint8_t *mask, int mem_kind);
+
+/*
+ * The same mask from a scene-space region (the paper's alternative to painted masks): box =
+ * {xmin, ymin, zmin, xmax, ymax, zmax} in world coordinates (inclusive).  A pixel of any frame is
+ * masked when its depth, unprojected with its frame's camera (FP64), gives a world point inside
+ * the box; invalid depths are not masked.  Needs the clip's cameras; waits for the stream.
+ */
+int ssvp_mask_from_box(ssvp_ctx *ctx, int clip_id, const double *box);
+
+/* Copy the clip's mask (F*H*W bytes, 0 or 1 for box masks) to host memory; waits for the stream. */
+int ssvp_read_mask(ssvp_ctx *ctx, int clip_id, uint8_t *out);
 
 /*
  * Shutter function xi of Eq. 10 (Sec. "Computational scene-space shutters") for

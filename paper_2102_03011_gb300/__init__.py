@@ -19,7 +19,7 @@ SSVP_ENOCLIP, SSVP_ENOCAM, SSVP_ETIMEOUT, SSVP_EDEVICE = -4, -5, -6, -7
 SSVP_MEM_HOST, SSVP_MEM_DEVICE = 0, 1
 SSVP_COLOUR_F32, SSVP_COLOUR_F16 = 0, 1
 SSVP_MODE_DENOISE, SSVP_MODE_APERTURE, SSVP_MODE_LEARNED, SSVP_MODE_MEAN = 0, 1, 2, 3
-SSVP_MODE_DEBLUR, SSVP_MODE_SHUTTER = 4, 5
+SSVP_MODE_DEBLUR, SSVP_MODE_SHUTTER, SSVP_MODE_INPAINT = 4, 5, 6
 SSVP_GATHER_WINDOW, SSVP_GATHER_FRUSTUM = 0, 1
 SSVP_MAX_CLIPS, SSVP_MAX_K, SSVP_MAX_HALF_WINDOW = 64, 31, 127
 
@@ -39,7 +39,8 @@ class ssvp_params(ctypes.Structure):
                 ("focal_depth", ctypes.c_float), ("a0", ctypes.c_float), ("lens_samples", ctypes.c_int32),
                 ("cap", ctypes.c_int32), ("max_samples", ctypes.c_int32), ("conf_threshold", ctypes.c_float),
                 ("gather", ctypes.c_int32), ("frustum_l", ctypes.c_float), ("near_plane", ctypes.c_float),
-                ("far_plane", ctypes.c_float), ("membership_out", ctypes.c_void_p), ("pixel_stats_out", ctypes.c_void_p)]
+                ("far_plane", ctypes.c_float), ("sigma_area", ctypes.c_float), ("membership_out", ctypes.c_void_p),
+                ("pixel_stats_out", ctypes.c_void_p)]
 
 
 class ssvp_plan_config(ctypes.Structure):
@@ -74,6 +75,10 @@ def _load():
                                 ctypes.POINTER(ctypes.c_double)]),
         "ssvp_clip_median_depth": (i, [vp, i, ctypes.POINTER(f)]),
         "ssvp_set_shutter": (i, [vp, ctypes.POINTER(f), i]),
+        "ssvp_superres": (i, [vp, P, i, i, vp]),
+        "ssvp_set_mask": (i, [vp, i, vp, i]),
+        "ssvp_mask_from_box": (i, [vp, i, ctypes.POINTER(ctypes.c_double)]),
+        "ssvp_read_mask": (i, [vp, i, vp]),
         "ssvp_frame_sharpness": (i, [vp, i, ctypes.POINTER(ctypes.c_double)]),
         "ssvp_sync": (i, [vp]),
         "ssvp_median_depth_noalloc": (i, [vp, ctypes.c_ulonglong, vp, vp]),
@@ -202,6 +207,38 @@ def ssvp_clip_median_depth(ctx, clip_id: int) -> float:
     m = ctypes.c_float()
     _check(ctx, lib.ssvp_clip_median_depth(ctx, clip_id, ctypes.byref(m)))
     return float(m.value)
+
+
+def ssvp_superres(ctx, params: ssvp_params, clip_id: int, scale: int, out) -> None:
+    """Super-resolution (Eq. 6-7) into `out`, a device tensor or pointer of
+    n_frames x (H scale) x (W scale) x 3 floats."""
+    p, dev = _ptr(out)
+    if not dev and not isinstance(out, int):
+        raise ValueError("ssvp_superres writes device memory: pass a CUDA tensor or a device pointer")
+    _check(ctx, lib.ssvp_superres(ctx, ctypes.byref(params), clip_id, scale, p))
+
+
+def ssvp_set_mask(ctx, clip_id: int, mask, mem_kind: int | None = None) -> None:
+    """Inpainting mask (Eq. 8-9): F*H*W bytes, nonzero = remove (host array or CUDA tensor)."""
+    p, dev = _ptr(mask)
+    _check(ctx, lib.ssvp_set_mask(ctx, clip_id, p, (SSVP_MEM_DEVICE if dev else SSVP_MEM_HOST) if mem_kind is None
+                                  else mem_kind))
+
+
+def ssvp_mask_from_box(ctx, clip_id: int, box) -> None:
+    """Mask every pixel whose world point lies in box = (xmin, ymin, zmin, xmax, ymax, zmax)."""
+    import numpy as np
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    if b.shape != (6,):
+        raise ValueError("box needs 6 values")
+    _check(ctx, lib.ssvp_mask_from_box(ctx, clip_id, b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def ssvp_read_mask(ctx, clip_id: int, n_frames: int, H: int, W: int):
+    import numpy as np
+    out = np.zeros((n_frames, H, W), np.uint8)
+    _check(ctx, lib.ssvp_read_mask(ctx, clip_id, out.ctypes.data))
+    return out
 
 
 def ssvp_set_shutter(ctx, xi, half_window: int) -> None:

@@ -118,6 +118,7 @@ void free_clip(Clip &c) {
     if (c.p.grad_sum) cudaFree(c.p.grad_sum);
     if (c.p.grad_log2) cudaFree(c.p.grad_log2);
     if (c.p.grad_partial) cudaFree(c.p.grad_partial);
+    if (c.p.mask) cudaFree(c.p.mask);
     c = Clip();
 }
 
@@ -217,10 +218,42 @@ void compose_table_back(const Clip &c, int fb, int n_out, int T, double sigma_f,
     }
 }
 
+// Super-resolution (Eq. 6-7): forward and back maps of every (O, slot) with the output-grid
+// camera of O (fx, fy scaled, principal point c -> scale (c + 0.5) - 0.5) in place of K_O.
+void compose_tables_sr(const Clip &c, int fb, int n_out, int T, double sigma_f, int scale, PairGeom *fwd,
+                       PairGeom *back) {
+    const int ns = 2 * T + 1;
+    for (int oi = 0; oi < n_out; ++oi) {
+        const int O = fb + oi;
+        double Ks[9];
+        std::memcpy(Ks, &c.K[9 * (size_t)O], sizeof(Ks));
+        Ks[0] *= scale;
+        Ks[2] = scale * (Ks[2] + 0.5) - 0.5;
+        Ks[4] *= scale;
+        Ks[5] = scale * (Ks[5] + 0.5) - 0.5;
+        for (int j = 0; j < ns; ++j) {
+            const int J = O - T + j;
+            PairGeom &g = fwd[(size_t)oi * ns + j], &h = back[(size_t)oi * ns + j];
+            if (J < 0 || J >= c.p.F) {
+                std::memset(&g, 0, sizeof(g));
+                std::memset(&h, 0, sizeof(h));
+                g.J = h.J = -1;
+                continue;
+            }
+            // the two cameras of O differ unless scale = 1, so J = O is exact only then
+            const bool same = J == O && scale == 1;
+            compose_pair(Ks, &c.w2c[12 * (size_t)O], &c.K[9 * (size_t)J], &c.w2c[12 * (size_t)J], same, J - O, sigma_f, g);
+            compose_pair(&c.K[9 * (size_t)J], &c.w2c[12 * (size_t)J], Ks, &c.w2c[12 * (size_t)O], same, J - O, sigma_f, h);
+            g.J = h.J = J;
+        }
+    }
+}
+
 int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
     if (!p) return fail(ctx, SSVP_EINVAL, "params is NULL");
     if (p->mode != SSVP_MODE_DENOISE && p->mode != SSVP_MODE_MEAN && p->mode != SSVP_MODE_APERTURE &&
-        p->mode != SSVP_MODE_LEARNED && p->mode != SSVP_MODE_DEBLUR && p->mode != SSVP_MODE_SHUTTER)
+        p->mode != SSVP_MODE_LEARNED && p->mode != SSVP_MODE_DEBLUR && p->mode != SSVP_MODE_SHUTTER &&
+        p->mode != SSVP_MODE_INPAINT)
         return fail(ctx, SSVP_EINVAL, "mode %d is not available in this build", p->mode);
     if (p->mode == SSVP_MODE_LEARNED && !(std::isfinite(p->conf_threshold)))
         return fail(ctx, SSVP_EINVAL, "conf_threshold must be finite");
@@ -234,6 +267,8 @@ int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
     }
     if (p->gather != SSVP_GATHER_WINDOW && p->gather != SSVP_GATHER_FRUSTUM)
         return fail(ctx, SSVP_EINVAL, "gather %d is not available in this build", p->gather);
+    if (p->mode == SSVP_MODE_INPAINT && p->gather != SSVP_GATHER_FRUSTUM)
+        return fail(ctx, SSVP_EINVAL, "inpainting gathers the pixel frustum: set gather = SSVP_GATHER_FRUSTUM");
     if (p->gather == SSVP_GATHER_FRUSTUM) {
         if (p->mode == SSVP_MODE_APERTURE || p->mode == SSVP_MODE_LEARNED)
             return fail(ctx, SSVP_EINVAL, "the frustum gather supports the denoise, mean, deblur and shutter modes");
@@ -480,6 +515,7 @@ void ssvp_params_default(ssvp_params *p) {
     p->frustum_l = 3.0f;
     p->near_plane = 0.01f;
     p->far_plane = 1000.0f;
+    p->sigma_area = 0.0f;
 }
 
 int ssvp_create(ssvp_ctx **out, int cuda_device, void *cuda_stream) {
@@ -725,8 +761,13 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         CK(cudaMemcpyAsync(ctx->d_shutter_log2, lg.data(), sizeof(float) * ns, cudaMemcpyHostToDevice, ctx->stream),
            "cudaMemcpyAsync (shutter)");
     }
-    // the shutter weight has no frame-distance term: compose with sigma_f = infinity (beta = 0)
-    const double sigma_f = shutter ? INFINITY : (double)p.sigma_f;
+    if (p.mode == SSVP_MODE_INPAINT)
+        for (int i = 0; i < n_clips; ++i)
+            if (!ctx->clips[clip_ids[i]].p.mask)
+                return fail(ctx, SSVP_EINVAL, "inpainting needs a mask for clip %d (ssvp_set_mask or ssvp_mask_from_box)",
+                            clip_ids[i]);
+    // the shutter and inpainting weights have no frame-distance term: sigma_f = infinity (beta = 0)
+    const double sigma_f = shutter || p.mode == SSVP_MODE_INPAINT ? INFINITY : (double)p.sigma_f;
     // the frustum gather also needs the back maps: a second table of the same shape after the first
     const bool frustum = p.gather == SSVP_GATHER_FRUSTUM;
     const size_t entries = frustum ? 2 * total : total;
@@ -795,6 +836,164 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         else CK(ssvp::launch_gather(a, ctx->stream), "gather kernel");
         off += (size_t)nout[i] * ns;
     }
+    return SSVP_OK;
+}
+
+int ssvp_superres(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, int scale, float *out) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    int rc = check_params(ctx, params);
+    if (rc != SSVP_OK) return rc;
+    const ssvp_params &p = *params;
+    if (p.mode != SSVP_MODE_DENOISE && p.mode != SSVP_MODE_MEAN)
+        return fail(ctx, SSVP_EINVAL, "super-resolution weights are Eq. 7 (SSVP_MODE_DENOISE) or w = 1 (SSVP_MODE_MEAN)");
+    if (scale < 1 || scale > 8) return fail(ctx, SSVP_EINVAL, "scale=%d must be in [1, 8]", scale);
+    if (!out) return fail(ctx, SSVP_EINVAL, "out is NULL");
+    if (!(p.frustum_l > 0.0f && p.frustum_l <= 64.0f)) return fail(ctx, SSVP_EINVAL, "frustum_l must be in (0, 64]");
+    if (!(p.near_plane > 0.0f && p.far_plane > p.near_plane && std::isfinite(p.far_plane)))
+        return fail(ctx, SSVP_EINVAL, "need 0 < near_plane < far_plane < inf");
+    if (!std::isfinite(p.sigma_area)) return fail(ctx, SSVP_EINVAL, "sigma_area must be finite");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    Clip &c = ctx->clips[clip_id];
+    if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_id);
+    const int b = p.frame_begin, e = p.frame_end < 0 ? c.p.F : p.frame_end;
+    if (b < 0 || e > c.p.F || b > e) return fail(ctx, SSVP_EINVAL, "frame range [%d, %d) outside the clip", b, e);
+    const long long Wo = (long long)c.p.W * scale, Ho = (long long)c.p.H * scale;
+    if (Wo > 65535 || Ho > 65535) return fail(ctx, SSVP_EINVAL, "output grid %lldx%lld too large", Wo, Ho);
+    int x0 = p.crop_x, y0 = p.crop_y, w = p.crop_w, h = p.crop_h;
+    if (w == 0 || h == 0) { x0 = 0; y0 = 0; w = (int)Wo; h = (int)Ho; }
+    if (x0 < 0 || y0 < 0 || x0 + w > Wo || y0 + h > Ho)
+        return fail(ctx, SSVP_EINVAL, "crop (%d, %d, %d, %d) outside the %lldx%lld output grid", x0, y0, w, h, Wo, Ho);
+    const int n_out = e - b, T = p.half_window, ns = 2 * T + 1;
+    if ((p.membership_out || p.pixel_stats_out) && n_out > 1)
+        return fail(ctx, SSVP_EINVAL, "debug outputs need at most one output frame");
+    if (n_out == 0) return SSVP_OK;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t total = (size_t)n_out * ns;
+    if (2 * total > ctx->geom_cap) {
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        if (ctx->geom) cudaFree(ctx->geom);
+        ctx->geom = nullptr;
+        ctx->geom_cap = 0;
+        const size_t cap = std::max<size_t>(2 * total, 4096);
+        CK(cudaMalloc(&ctx->geom, cap * sizeof(PairGeom)), "cudaMalloc (geometry)");
+        ctx->geom_cap = cap;
+    }
+    ctx->host_geom.resize(2 * total);
+    compose_tables_sr(c, b, n_out, T, p.sigma_f, scale, ctx->host_geom.data(), ctx->host_geom.data() + total);
+    CK(cudaMemcpyAsync(ctx->geom, ctx->host_geom.data(), 2 * total * sizeof(PairGeom), cudaMemcpyHostToDevice, ctx->stream),
+       "cudaMemcpyAsync (geometry)");
+    CK(cudaMemsetAsync(ctx->stat_counts, 0, 2 * sizeof(unsigned long long), ctx->stream), "cudaMemsetAsync");
+    CK(cudaMemsetAsync(ctx->stat_sumw, 0, sizeof(double), ctx->stream), "cudaMemsetAsync");
+    GatherArgs a{};
+    a.clip = c.p;
+    a.geom = ctx->geom;
+    a.geom_back = ctx->geom + total;
+    a.frame_begin = b;
+    a.n_out = n_out;
+    a.n_slots = ns;
+    a.T = T;
+    a.x0 = x0; a.y0 = y0; a.cw = w; a.ch = h;
+    a.k = 1;
+    a.mode = p.mode;
+    a.radius = p.radius;
+    a.sigma_rgb = p.sigma_rgb;
+    a.sigma_xyz = p.sigma_xyz;
+    a.sigma_f = p.sigma_f;
+    a.frustum_l = p.frustum_l;
+    a.near_plane = p.near_plane;
+    a.far_plane = p.far_plane;
+    a.sr_scale = scale;
+    a.sigma_area = p.sigma_area;
+    a.sr_out = out;
+    a.membership = (int32_t *)p.membership_out;
+    a.pixel_stats = (int32_t *)p.pixel_stats_out;
+    a.stat_counts = ctx->stat_counts;
+    a.stat_sumw = ctx->stat_sumw;
+    CK(ssvp::launch_frustum(a, ctx->stream), "super-resolution kernel");
+    return SSVP_OK;
+}
+
+// the clip's mask plane (padded like depth, pads 0), allocated and cleared on first use
+static int ensure_mask(ssvp_ctx *ctx, Clip &c) {
+    if (c.p.mask) return SSVP_OK;
+    const size_t bytes = (size_t)c.p.F * (size_t)c.p.fstride;
+    CK(cudaMalloc(&c.p.mask, bytes), "cudaMalloc (mask)");
+    CK(cudaMemsetAsync(c.p.mask, 0, bytes, ctx->stream), "cudaMemsetAsync (mask)");
+    return SSVP_OK;
+}
+
+static int mask_clip(ssvp_ctx *ctx, int clip_id, Clip **out) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    Clip &c = ctx->clips[clip_id];
+    if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    *out = &c;
+    return SSVP_OK;
+}
+
+int ssvp_set_mask(ssvp_ctx *ctx, int clip_id, const uint8_t *mask, int mem_kind) {
+    Clip *c = nullptr;
+    int rc = mask_clip(ctx, clip_id, &c);
+    if (rc != SSVP_OK) return rc;
+    if (!mask) return fail(ctx, SSVP_EINVAL, "mask is NULL");
+    if (mem_kind != SSVP_MEM_HOST && mem_kind != SSVP_MEM_DEVICE) return fail(ctx, SSVP_EINVAL, "bad mem_kind %d", mem_kind);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((rc = ensure_mask(ctx, *c)) != SSVP_OK) return rc;
+    const Planes &p = c->p;
+    for (int f = 0; f < p.F; ++f)
+        CK(cudaMemcpy2DAsync(p.mask + (size_t)f * p.fstride + (size_t)ssvp::kPad * p.pitch + ssvp::kPad, (size_t)p.pitch,
+                             mask + (size_t)f * p.W * p.H, (size_t)p.W, (size_t)p.W, (size_t)p.H,
+                             mem_kind == SSVP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream),
+           "cudaMemcpy2DAsync (mask)");
+    return SSVP_OK;
+}
+
+int ssvp_mask_from_box(ssvp_ctx *ctx, int clip_id, const double *box) {
+    Clip *c = nullptr;
+    int rc = mask_clip(ctx, clip_id, &c);
+    if (rc != SSVP_OK) return rc;
+    if (!c->has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_id);
+    if (!box || !finite_all(box, 6)) return fail(ctx, SSVP_EINVAL, "box must hold 6 finite values");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((rc = ensure_mask(ctx, *c)) != SSVP_OK) return rc;
+    const int F = c->p.F;
+    std::vector<double> cam((size_t)F * 21);
+    for (int f = 0; f < F; ++f) {
+        const double *K = &c->K[9 * (size_t)f], *w = &c->w2c[12 * (size_t)f];
+        double *o = &cam[21 * (size_t)f];
+        // K^-1 of an upper-triangular, zero-skew K; then R and t of the pose
+        const double Ki[9] = {1.0 / K[0], 0.0, -K[2] / K[0], 0.0, 1.0 / K[4], -K[5] / K[4], 0.0, 0.0, 1.0};
+        for (int i = 0; i < 9; ++i) o[i] = Ki[i];
+        for (int r = 0; r < 3; ++r) {
+            for (int k = 0; k < 3; ++k) o[9 + 3 * r + k] = w[4 * r + k];
+            o[18 + r] = w[4 * r + 3];
+        }
+    }
+    double *d_cam = nullptr;
+    CK(cudaMalloc(&d_cam, cam.size() * sizeof(double)), "cudaMalloc (cameras)");
+    cudaError_t e = cudaMemcpyAsync(d_cam, cam.data(), cam.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = ssvp::launch_mask_box(c->p, d_cam, box, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the table is freed next
+    cudaFree(d_cam);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mask from box");
+    return SSVP_OK;
+}
+
+int ssvp_read_mask(ssvp_ctx *ctx, int clip_id, uint8_t *out) {
+    Clip *c = nullptr;
+    int rc = mask_clip(ctx, clip_id, &c);
+    if (rc != SSVP_OK) return rc;
+    if (!out) return fail(ctx, SSVP_EINVAL, "out is NULL");
+    if (!c->p.mask) return fail(ctx, SSVP_EINVAL, "clip %d has no mask", clip_id);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const Planes &p = c->p;
+    for (int f = 0; f < p.F; ++f)
+        CK(cudaMemcpy2DAsync(out + (size_t)f * p.W * p.H, (size_t)p.W,
+                             p.mask + (size_t)f * p.fstride + (size_t)ssvp::kPad * p.pitch + ssvp::kPad, (size_t)p.pitch,
+                             (size_t)p.W, (size_t)p.H, cudaMemcpyDeviceToHost, ctx->stream),
+           "cudaMemcpy2DAsync (mask)");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     return SSVP_OK;
 }
 

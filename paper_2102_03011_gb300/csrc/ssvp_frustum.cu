@@ -15,6 +15,8 @@
 //      Eq. 10's shutter function alone) and reduced by Eq. 3, as in the window gather.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "../../include/ssvp.h"
 #include "ssvp_df.cuh"
 #include "ssvp_internal.h"
@@ -94,7 +96,13 @@ __device__ __forceinline__ void face_edge(const float *M, const float *e, float 
     if (wb > 0.0f) bound_add(hb, fmaf(D0, sb, P0) / wb, fmaf(D1, sb, P1) / wb);
 }
 
-template <int CFMT, bool DEBUG>
+// SR: super-resolution (Sec. "Super resolution", Eq. 6-7) on the a.sr_scale-times output grid;
+// the maps use the output-grid camera of O, s_ref is bilinear in the input frame, and the
+// exponent gains Eq. 7's area term.
+// INP: inpainting (Sec. "Inpainting and semi-transparency", Eq. 8-9): only pixels with a mask
+// gather; three passes over S(p): the mean of all samples (Eq. 8), then two steps of the
+// colour-weighted mean over unmasked samples (Eq. 9), each around the previous result.
+template <int CFMT, bool DEBUG, bool SR, bool INP>
 __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a) {
     __shared__ float s_const[4];
     __shared__ unsigned long long s_cnt[2][kFrThreads / 32];
@@ -108,12 +116,21 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
         // the shutter weight of Eq. 10 replaces Eq. 4: no colour and no position term
         const bool shutter = a.mode == SSVP_MODE_SHUTTER;
         s_const[0] = shutter ? 0.0f : kLog2e / (2.0f * a.sigma_rgb * a.sigma_rgb);
-        s_const[1] = shutter ? 0.0f : kLog2e / (2.0f * sx * sx);
+        s_const[1] = shutter || INP ? 0.0f : kLog2e / (2.0f * sx * sx);
         s_const[2] = a.mode == SSVP_MODE_MEAN ? 0.0f : 1.0f;
+        if (SR) {
+            // sigma_area <= 0: one input-pixel footprint at the median depth (median / fx_O); the
+            // back map of slot T (J = O) carries the output-grid 1 / fx of O
+            const float ifx_grid = a.geom_back[(long long)oi * a.n_slots + a.T].ifx;
+            const float sa = a.sigma_area > 0.0f ? a.sigma_area : *P.median * ifx_grid * (float)a.sr_scale;
+            s_const[3] = kLog2e / (2.0f * sa * sa);
+        }
     }
     __syncthreads();
-    const float a_rgb = s_const[0], a_xyz = s_const[1];
+    const float a_rgb = s_const[0], a_xyz = s_const[1], a_area = SR ? s_const[3] : 0.0f;
     const bool weighted = s_const[2] != 0.0f;
+    const int Wo = SR ? P.W * a.sr_scale : P.W;
+    const int Ho = SR ? P.H * a.sr_scale : P.H;
 
     const int u = a.x0 + blockIdx.x * kFrTileX + (threadIdx.x % kFrTileX);
     const int v = a.y0 + blockIdx.y * kFrTileY + (threadIdx.x / kFrTileX);
@@ -125,16 +142,44 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
 
     float3 cref = make_float3(0.f, 0.f, 0.f);
     float dref = 0.0f;
-    if (active) {
+    if (active && !SR) {
         const long long pix = (long long)O * P.fstride + (long long)(v + kPad) * P.pitch + (u + kPad);
         dref = __ldg(P.depth + pix);
         cref = load_colour<CFMT>(P.colour, pix);
     }
-    const bool gather = active && dref > 0.0f;  // false for NaN (invalid) depth
+    if (active && SR) {
+        // bilinear s_ref at input coordinates ((u, v) + 0.5) / scale - 0.5, clamped to the image; an
+        // invalid (NaN) depth among the four propagates and invalidates the reference
+        const float is = 1.0f / (float)a.sr_scale;
+        const float xc = fminf(fmaxf(((float)u + 0.5f) * is - 0.5f, 0.0f), (float)(P.W - 1));
+        const float yc = fminf(fmaxf(((float)v + 0.5f) * is - 0.5f, 0.0f), (float)(P.H - 1));
+        const int x0 = (int)floorf(xc), y0 = (int)floorf(yc);
+        const int x1 = min(x0 + 1, P.W - 1), y1 = min(y0 + 1, P.H - 1);
+        const float fx = xc - (float)x0, fy = yc - (float)y0;
+        const long long fb = (long long)O * P.fstride;
+        const long long p00 = fb + (long long)(y0 + kPad) * P.pitch + (x0 + kPad), p10 = p00 + (x1 - x0);
+        const long long p01 = fb + (long long)(y1 + kPad) * P.pitch + (x0 + kPad), p11 = p01 + (x1 - x0);
+        const float3 c00 = load_colour<CFMT>(P.colour, p00), c10 = load_colour<CFMT>(P.colour, p10);
+        const float3 c01 = load_colour<CFMT>(P.colour, p01), c11 = load_colour<CFMT>(P.colour, p11);
+        const float d00 = __ldg(P.depth + p00), d10 = __ldg(P.depth + p10), d01 = __ldg(P.depth + p01),
+                    d11 = __ldg(P.depth + p11);
+        const float gx = 1.0f - fx, gy = 1.0f - fy;
+        cref.x = gy * (gx * c00.x + fx * c10.x) + fy * (gx * c01.x + fx * c11.x);
+        cref.y = gy * (gx * c00.y + fx * c10.y) + fy * (gx * c01.y + fx * c11.y);
+        cref.z = gy * (gx * c00.z + fx * c10.z) + fy * (gx * c01.z + fx * c11.z);
+        dref = gy * (gx * d00 + fx * d10) + fy * (gx * d01 + fx * d11);
+    }
+    // inpainting gathers for masked pixels only and does not need their depth; the others need
+    // a valid reference depth (NaN fails)
+    const long long pix_o = (long long)O * P.fstride + (long long)(v + kPad) * P.pitch + (u + kPad);
+    const bool gather = INP ? active && __ldg(P.mask + pix_o) != 0 : active && dref > 0.0f;
+    if (INP && active) cref = load_colour<CFMT>(P.colour, pix_o);
     // Accumulators carry the common factor 2^-m, m the largest log2 weight so far: without the
     // reference sample (outside near / far) every weight can be far below FP32's range while
-    // Eq. 3 is still well defined.
-    float acc_r = 0.0f, acc_g = 0.0f, acc_b = 0.0f, acc_w = 0.0f, m_log2 = weighted ? -__int_as_float(0x7f800000) : 0.0f;
+    // Eq. 3 is still well defined.  The start, -1e30, is below every finite exponent, and a
+    // weight of exactly 0 (an exponent of -inf) stays 0.
+    constexpr float kNoWeight = -1e30f;
+    float acc_r = 0.0f, acc_g = 0.0f, acc_b = 0.0f, acc_w = 0.0f, m_log2 = 0.0f, sw_true = 0.0f;
     long long n_exam = 0;
     int n_acc = 0;
     if (DEBUG && active && !gather && a.membership)
@@ -143,11 +188,16 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
             rec[0] = -2; rec[1] = 0; rec[2] = 0; rec[3] = 0;
         }
 
+    constexpr int kPasses = INP ? 3 : 1;
+    for (int pass = 0; pass < kPasses; ++pass) {
+    const bool wpass = INP ? pass > 0 : weighted;
+    acc_r = acc_g = acc_b = acc_w = 0.0f;
+    m_log2 = wpass ? kNoWeight : 0.0f;
     if (gather) {
         for (int j = 0; j < ns; ++j) {
             const PairGeom &gf = a.geom[(long long)oi * ns + j];
             const int J = __ldg(&gf.J);
-            int32_t *rec = DEBUG && a.membership ? a.membership + (crop_idx * ns + j) * 4 : nullptr;
+            int32_t *rec = DEBUG && a.membership && pass == 0 ? a.membership + (crop_idx * ns + j) * 4 : nullptr;
             if (J < 0) {
                 if (DEBUG && rec) { rec[0] = -1; rec[1] = 0; rec[2] = 0; rec[3] = 0; }
                 continue;
@@ -233,6 +283,7 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
             // O intrinsics (the back map's target camera) for the metric offset to x_ref
             const float ifxO = __ldg(&gb.ifx), ifyO = __ldg(&gb.ify);
             const float ux = (float)u - __ldg(&gb.cx), vy = (float)v - __ldg(&gb.cy);
+            const float ifxJ = SR ? __ldg(&gf.ifx) : 0.0f;  // 1 / fx of J for Eq. 7's area term
             // frame term of Eq. 4 plus the per-frame weights of Eq. 5 / Eq. 10, in log2 units
             float beta = __ldg(&gf.beta) * kLog2e;
             if (a.frame_log2w) beta -= __ldg(a.frame_log2w + J);
@@ -250,7 +301,7 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
                 const float b2 = fmaf(R2[0], (float)qx0, fmaf(R2[1], (float)qy0, R2[2]));
                 const float b3 = fmaf(R3[0], (float)qx0, fmaf(R3[1], (float)qy0, R3[2]));
                 const float s1 = hb.xmajor ? R1[1] : R1[0], s2 = hb.xmajor ? R2[1] : R2[0], s3 = hb.xmajor ? R3[1] : R3[0];
-                n_exam += max(n1 - n0 + 1, 0);
+                if (pass == 0) n_exam += max(n1 - n0 + 1, 0);
                 for (int n = n0; n <= n1; ++n) {
                     const int qx = hb.xmajor ? m : n, qy = hb.xmajor ? n : m;
                     const long long off = fbase + (long long)(qy + kPad) * P.pitch + (qx + kPad);
@@ -261,14 +312,20 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
                     const float h3 = fmaf(d, fmaf(s3, fn, b3), E3);
                     // NaN depth fails both comparisons
                     if (fabsf(h1) + fabsf(h2) < L * h3 && fabsf(h3 - zmid) < zhalf) {
+                        // Eq. 9: masked samples weigh 0 in the mean-shift steps
+                        if (INP && pass > 0 && __ldg(P.mask + off) != 0) continue;
                         const float3 c = load_colour<CFMT>(P.colour, off);
                         const float er = c.x - cref.x, eg = c.y - cref.y, eb = c.z - cref.z;
                         float w = 1.0f;
-                        if (weighted) {
+                        if (wpass) {
                             const float dz = h3 - dref;
                             const float ex = fmaf(ux, dz, h1) * ifxO, ey = fmaf(vy, dz, h2) * ifyO;
                             const float d2 = fmaf(ex, ex, fmaf(ey, ey, dz * dz));
-                            const float x = -fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta));
+                            float x = -fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta));
+                            if (SR) {  // Eq. 7: s_area = (d / fx_J)^2, the sample's pixel edge squared
+                                const float edge = d * ifxJ;
+                                x = fmaf(-a_area, edge * edge, x);
+                            }
                             if (x > m_log2) {  // new largest weight: rescale what was summed so far
                                 const float sc = ex2(m_log2 - x);
                                 acc_r *= sc;
@@ -277,14 +334,14 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
                                 acc_w *= sc;
                                 m_log2 = x;
                             }
-                            w = x == -__int_as_float(0x7f800000) ? 0.0f : ex2(x - m_log2);
+                            w = ex2(x - m_log2);
                         }
                         acc_r = fmaf(w, er, acc_r);
                         acc_g = fmaf(w, eg, acc_g);
                         acc_b = fmaf(w, eb, acc_b);
                         acc_w += w;
-                        ++n_acc;
-                        if (DEBUG) {
+                        if (pass == 0) ++n_acc;
+                        if (DEBUG && pass == 0) {
                             ++mc;
                             mh += mix64((unsigned long long)qy * (unsigned long long)P.W + (unsigned long long)qx + 1ull);
                         }
@@ -298,6 +355,16 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
             }
         }
     }
+    sw_true = acc_w > 0.0f ? acc_w * exp2f(m_log2) : 0.0f;  // the true sum of weights of this pass
+    if (INP && acc_w > 0.0f) {
+        // this pass's weighted mean is the next pass's reference (and, after the last, the output)
+        const float inv = 1.0f / acc_w;
+        cref.x = fmaf(acc_r, inv, cref.x);
+        cref.y = fmaf(acc_g, inv, cref.y);
+        cref.z = fmaf(acc_b, inv, cref.z);
+        acc_r = acc_g = acc_b = acc_w = 0.0f;
+    }
+    }  // passes
 
     if (active) {
         float o_r = cref.x, o_g = cref.y, o_b = cref.z;
@@ -307,7 +374,7 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
             o_g = fmaf(acc_g, inv, o_g);
             o_b = fmaf(acc_b, inv, o_b);
         }
-        float *o = P.out + (((long long)O * P.H + v) * P.W + u) * 3;
+        float *o = SR ? a.sr_out + (((long long)oi * Ho + v) * Wo + u) * 3 : P.out + (((long long)O * P.H + v) * P.W + u) * 3;
         o[0] = o_r;
         o[1] = o_g;
         o[2] = o_b;
@@ -315,12 +382,12 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
             int32_t *ps = a.pixel_stats + crop_idx * 3;
             ps[0] = n_acc;
             ps[1] = (int32_t)min(n_exam, 0x7fffffffll);
-            ps[2] = __float_as_int(acc_w > 0.0f ? acc_w * exp2f(m_log2) : 0.0f);
+            ps[2] = __float_as_int(sw_true);
         }
     }
 
     unsigned long long ce = (unsigned long long)n_exam, ca = (unsigned long long)n_acc;
-    float sw = acc_w > 0.0f ? acc_w * exp2f(m_log2) : 0.0f;  // the true sum of weights
+    float sw = sw_true;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ce += __shfl_xor_sync(0xffffffffu, ce, o);
@@ -367,18 +434,65 @@ __global__ void __launch_bounds__(256) zrange_kernel(Planes P, unsigned int *zr)
     }
 }
 
+template <bool SR, bool INP>
+void launch_frustum_t(const GatherArgs &a, const dim3 grid, cudaStream_t s) {
+    const bool dbg = a.membership || a.pixel_stats;
+    if (a.clip.colour_fmt == 0) {
+        if (dbg) frustum_kernel<0, true, SR, INP><<<grid, kFrThreads, 0, s>>>(a);
+        else frustum_kernel<0, false, SR, INP><<<grid, kFrThreads, 0, s>>>(a);
+    } else {
+        if (dbg) frustum_kernel<1, true, SR, INP><<<grid, kFrThreads, 0, s>>>(a);
+        else frustum_kernel<1, false, SR, INP><<<grid, kFrThreads, 0, s>>>(a);
+    }
+}
+
+// Eq. 8-9's mask from a scene-space box: per pixel of every frame, the world point of its depth
+// (unprojected with K_J^-1 and the pose of J, in FP64 with every operation rounded on its own)
+// inside the inclusive box -> 1.  cam: per frame K^-1 (9), R (9), t (3).  Pads stay 0.
+__global__ void __launch_bounds__(256) mask_box_kernel(Planes P, const double *cam, double bx0, double by0, double bz0,
+                                                       double bx1, double by1, double bz1) {
+    const long long npx = (long long)P.W * P.H * P.F;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npx; i += (long long)gridDim.x * blockDim.x) {
+        const long long f = i / ((long long)P.W * P.H);
+        const int rem = (int)(i - f * (long long)P.W * P.H);
+        const int y = rem / P.W, x = rem - y * P.W;
+        const long long o = f * P.fstride + (long long)(y + kPad) * P.pitch + (x + kPad);
+        const float d = P.depth[o];
+        unsigned char m = 0;
+        if (d > 0.0f && d < __int_as_float(0x7f800000)) {  // NaN (invalid) fails
+            const double *Ki = cam + 21 * f, *R = Ki + 9, *t = Ki + 18;
+            const double q[3] = {(double)x, (double)y, 1.0};
+            double Xc[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const double ray = __dadd_rn(__dadd_rn(__dmul_rn(Ki[3 * r], q[0]), __dmul_rn(Ki[3 * r + 1], q[1])),
+                                             __dmul_rn(Ki[3 * r + 2], q[2]));
+                Xc[r] = __dsub_rn(__dmul_rn((double)d, ray), t[r]);
+            }
+            double Xw[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Xw[c] = __dadd_rn(__dadd_rn(__dmul_rn(R[c], Xc[0]), __dmul_rn(R[3 + c], Xc[1])), __dmul_rn(R[6 + c], Xc[2]));
+            m = Xw[0] >= bx0 && Xw[1] >= by0 && Xw[2] >= bz0 && Xw[0] <= bx1 && Xw[1] <= by1 && Xw[2] <= bz1;
+        }
+        P.mask[o] = m;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_frustum(const GatherArgs &a, cudaStream_t s) {
     const dim3 grid((a.cw + kFrTileX - 1) / kFrTileX, (a.ch + kFrTileY - 1) / kFrTileY, a.n_out);
-    const bool dbg = a.membership || a.pixel_stats;
-    if (a.clip.colour_fmt == 0) {
-        if (dbg) frustum_kernel<0, true><<<grid, kFrThreads, 0, s>>>(a);
-        else frustum_kernel<0, false><<<grid, kFrThreads, 0, s>>>(a);
-    } else {
-        if (dbg) frustum_kernel<1, true><<<grid, kFrThreads, 0, s>>>(a);
-        else frustum_kernel<1, false><<<grid, kFrThreads, 0, s>>>(a);
-    }
+    if (a.sr_out) launch_frustum_t<true, false>(a, grid, s);
+    else if (a.mode == SSVP_MODE_INPAINT) launch_frustum_t<false, true>(a, grid, s);
+    else launch_frustum_t<false, false>(a, grid, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask_box(const Planes &p, const double *cam, const double *box, cudaStream_t s) {
+    const long long n = (long long)p.W * p.H * p.F;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    mask_box_kernel<<<blocks, 256, 0, s>>>(p, cam, box[0], box[1], box[2], box[3], box[4], box[5]);
     return cudaGetLastError();
 }
 

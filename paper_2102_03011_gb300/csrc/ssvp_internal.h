@@ -28,6 +28,7 @@ struct Planes {
     double *grad_sum;      // F: Eq. 5 blurriness measure (sum of gradient magnitudes) per frame
     float *grad_log2;      // F: log2(grad_sum / max over frames), the Eq. 5 factor in log2 units
     double *grad_partial;  // F x grad_partial_words(1): partial sums of grad_sum
+    unsigned char *mask;   // inpainting mask (Eq. 8-9), same indexing as depth, pads 0; null until set
     float *out;            // F * H * W * 3 output floats (row-major, interleaved)
 };
 
@@ -74,6 +75,11 @@ struct GatherArgs {
     // frustum gather (Eq. 1-2): back maps G_{O<-J} (same indexing as geom), frustum size and depths
     const PairGeom *geom_back;
     float frustum_l, near_plane, far_plane;
+    // super-resolution (Eq. 6-7): output grid scale, Eq. 7's sigma_area (<= 0: median / fx_O) and
+    // the caller's output, n_out x (H scale) x (W scale) x 3 floats; null for the other gathers
+    int sr_scale;
+    float sigma_area;
+    float *sr_out;
     int32_t *membership;      // debug record per (crop pixel, slot) or null
     int32_t *pixel_stats;     // debug record per crop pixel or null
     unsigned long long *stat_counts;  // [0] examined, [1] accepted
@@ -146,6 +152,7 @@ cudaError_t launch_gather(const GatherArgs &a, cudaStream_t s);
 cudaError_t launch_aperture(const GatherArgs &a, cudaStream_t s);
 cudaError_t launch_frustum(const GatherArgs &a, cudaStream_t s);
 cudaError_t launch_grad_sum(const Planes &p, cudaStream_t s);
+cudaError_t launch_mask_box(const Planes &p, const double *cam, const double *box, cudaStream_t s);
 size_t grad_partial_words(int F);
 cudaError_t launch_zrange(const Planes &p, cudaStream_t s);
 // persistent batched gather; grid = batch_grid(...) CTAs

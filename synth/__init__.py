@@ -364,6 +364,19 @@ def make_clip(preset: str, W: int, H: int, F: int, seed: int = 0, with_world: bo
                 meta=dict(preset=preset, seed=seed, objects=objs, **p))
 
 
+def object_box(obj, margin: float = 0.0, y_range=None):
+    """World-space axis-aligned bounds (xmin, ymin, zmin, xmax, ymax, zmax) of a BOX object, grown by
+    margin and optionally clipped to y_range (to keep a floor or ceiling the box rests on out)."""
+    ax = np.array(obj.ax[:]).reshape(3, 3)
+    half = np.array(obj.half[:])
+    ext = np.abs(ax).T @ half + margin
+    c = np.array(obj.c[:])
+    lo, hi = c - ext, c + ext
+    if y_range is not None:
+        lo[1], hi[1] = max(lo[1], y_range[0]), min(hi[1], y_range[1])
+    return tuple(lo) + tuple(hi)
+
+
 def shake_blur(clip: Clip, frames, shake_deg: float = 0.5, n_sub: int = 6, seed: int = 0) -> Clip:
     """Motion blur from a sudden camera shake during the exposure of each listed frame: the clean
     image becomes the mean of n_sub renders whose camera rotates from the frame's pose to a random

@@ -217,8 +217,38 @@ def compare_frustum(g: GpuResult, o: oracle.FrustumResult, ref_valid: np.ndarray
     cerr = np.abs(g.rgb.astype(np.float64) - o.rgb).max(-1)
     assert cerr[ok].max(initial=0.0) <= COLOUR_TOL, f"colour max abs {cerr[ok].max()} > {COLOUR_TOL}"
     np.testing.assert_array_equal(g.nacc[ok], o.nacc[ok])
-    # the GPU reports sum w in FP32: sums below its range read 0 (Eq. 3 itself is rescaled)
-    np.testing.assert_allclose(g.sumw[ok], o.sumw[ok], rtol=1e-4, atol=1e-30)
+    # the GPU reports sum w in FP32: Gaussian-tail weights carry relative error growing with their
+    # exponent, and sums below its range read 0 (Eq. 3 itself is rescaled)
+    np.testing.assert_allclose(g.sumw[ok], o.sumw[ok], rtol=1e-4, atol=1e-6)
     return dict(pixels=int(ok.size), excluded=int(excl.sum()), members=int(o.count.sum()),
                 band_slots=int(band.sum()), max_colour_err=float(cerr[ok].max(initial=0.0)),
                 max_colour_err_all=float(cerr.max()))
+
+
+def run_superres(sess: Session, cid, O, scale, crop=None, membership=False, **kw) -> GpuResult:
+    """Super-resolution (Eq. 6-7) through the C ABI; crop in output-grid pixels."""
+    t, ss = sess.torch, sess.ss
+    W, H, F = sess.clips[cid]
+    Wo, Ho = W * scale, H * scale
+    x0, y0, cw, ch = crop if crop is not None else (0, 0, Wo, Ho)
+    p = sess.params(frame_begin=O, frame_end=O + 1, crop_x=x0, crop_y=y0, crop_w=cw, crop_h=ch, **kw)
+    ns = 2 * p.half_window + 1
+    mem = stats = None
+    if membership:
+        mem = t.zeros((ch, cw, ns, 4), dtype=t.int32, device=sess.dev)
+        stats = t.zeros((ch, cw, 3), dtype=t.int32, device=sess.dev)
+        p.membership_out = mem.data_ptr()
+        p.pixel_stats_out = stats.data_ptr()
+    out = t.zeros((1, Ho, Wo, 3), dtype=t.float32, device=sess.dev)
+    ss.ssvp_superres(sess.ctx, p, cid, scale, out)
+    ss.ssvp_sync(sess.ctx)
+    res = GpuResult(out[0, y0:y0 + ch, x0:x0 + cw].cpu().numpy())
+    if membership:
+        m = mem.cpu().numpy()
+        s = stats.cpu().numpy()
+        res.nacc, res.nexam = s[..., 0].astype(np.int64), s[..., 1].astype(np.int64)
+        res.sumw = s[..., 2].view(np.float32).astype(np.float64)
+        res.status = m[..., 0]
+        res.count = m[..., 1]
+        res.hash = m[..., 2].view(np.uint32).astype(np.uint64) | (m[..., 3].view(np.uint32).astype(np.uint64) << np.uint64(32))
+    return res
