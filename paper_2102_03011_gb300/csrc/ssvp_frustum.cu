@@ -102,6 +102,42 @@ __device__ __forceinline__ void face_edge(const float *M, const float *e, float 
 // INP: inpainting (Sec. "Inpainting and semi-transparency", Eq. 8-9): only pixels with a mask
 // gather; three passes over S(p): the mean of all samples (Eq. 8), then two steps of the
 // colour-weighted mean over unmasked samples (Eq. 9), each around the previous result.
+// Fast path of the hull: the 4 lateral rays of the frustum, h(z) = z A + e, clipped to the slab
+// alone.  Valid (returns true) when every ray's depth in J grows (or every one falls) with z and
+// every clipped interval lies strictly inside (near, far): then no face of V touches the slab,
+// every point of V in the slab has its O depth inside (near, far), and the hull is that of the
+// 8 end points, which are projected here with approximate reciprocals (the bound's margin
+// covers their error).
+// corner c = 0..3 of the l x l square around (u, v), counter-clockwise from (u - L, v - L)
+__device__ __forceinline__ float corner_u(int c, float u, float L) { return (c == 1 || c == 2) ? u + L : u - L; }
+__device__ __forceinline__ float corner_v(int c, float v, float L) { return c >= 2 ? v + L : v - L; }
+
+__device__ __forceinline__ bool lateral_fast(const float *M, const float *e, float u, float v, float L, float nearp,
+                                             float farp, float zlo, float zhi, HullBound &hb) {
+    float sgn = 0.0f;
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float cu = corner_u(c, u, L), cv = corner_v(c, v, L);
+        const float A0 = fmaf(M[0], cu, fmaf(M[1], cv, M[2]));
+        const float A1 = fmaf(M[3], cu, fmaf(M[4], cv, M[5]));
+        const float A2 = fmaf(M[6], cu, fmaf(M[7], cv, M[8]));
+        const float s = A2 > 0.0f ? 1.0f : (A2 < 0.0f ? -1.0f : 0.0f);
+        ok = ok && s != 0.0f && (c == 0 || s == sgn);
+        sgn = s;
+        const float r = rcp_approx(A2);
+        const float sa = (zlo - e[2]) * r, sb = (zhi - e[2]) * r;
+        const float za = fminf(sa, sb), zb = fmaxf(sa, sb);
+        ok = ok && za > nearp * 1.0001f && zb < farp * 0.9999f;
+        const float wa = fmaf(A2, za, e[2]), wb = fmaf(A2, zb, e[2]);
+        const float ra = rcp_approx(wa), rb = rcp_approx(wb);
+        ok = ok && wa > 0.0f && wb > 0.0f;
+        bound_add(hb, fmaf(A0, za, e[0]) * ra, fmaf(A1, za, e[1]) * ra);
+        bound_add(hb, fmaf(A0, zb, e[0]) * rb, fmaf(A1, zb, e[1]) * rb);
+    }
+    return ok;
+}
+
 template <int CFMT, bool DEBUG, bool SR, bool INP>
 __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a) {
     __shared__ float s_const[4];
@@ -237,14 +273,24 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
             }
             hb.lo = hb.mlo = __int_as_float(0x7f800000);
             hb.hi = hb.mhi = -__int_as_float(0x7f800000);
+            bool check_nf = true;  // per-candidate near / far test needed
             if (zlo <= zhi) {
-                const float cu[4] = {u - L, u + L, u + L, u - L}, cv[4] = {v - L, v - L, v + L, v + L};
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    lateral_edge(Mf, ef, cu[c], cv[c], nearp, farp, zlo, zhi, hb);
-                    const int c2 = (c + 1) & 3;
-                    face_edge(Mf, ef, nearp, cu[c], cv[c], cu[c2] - cu[c], cv[c2] - cv[c], zlo, zhi, hb);
-                    face_edge(Mf, ef, farp, cu[c], cv[c], cu[c2] - cu[c], cv[c2] - cv[c], zlo, zhi, hb);
+                if (lateral_fast(Mf, ef, (float)u, (float)v, L, nearp, farp, zlo, zhi, hb)) {
+                    check_nf = false;
+                } else {
+                    // general case: all 12 edges of V clipped to the slab and to [near, far]
+                    hb.any = false;
+                    hb.lo = hb.mlo = __int_as_float(0x7f800000);
+                    hb.hi = hb.mhi = -__int_as_float(0x7f800000);
+#pragma unroll 1
+                    for (int c = 0; c < 4; ++c) {
+                        const float cu = corner_u(c, (float)u, L), cv = corner_v(c, (float)v, L);
+                        const int c2 = (c + 1) & 3;
+                        const float du = corner_u(c2, (float)u, L) - cu, dv = corner_v(c2, (float)v, L) - cv;
+                        lateral_edge(Mf, ef, cu, cv, nearp, farp, zlo, zhi, hb);
+                        face_edge(Mf, ef, nearp, cu, cv, du, dv, zlo, zhi, hb);
+                        face_edge(Mf, ef, farp, cu, cv, du, dv, zlo, zhi, hb);
+                    }
                 }
             }
             if (DEBUG && rec) { rec[0] = 0; rec[1] = 0; rec[2] = 0; rec[3] = 0; }
@@ -291,27 +337,75 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
             const long long fbase = (long long)J * P.fstride;
             int mc = 0;
             unsigned long long mh = 0ull;
-            for (int m = m0; m <= m1; ++m) {
-                const float fm = (float)m;
-                const int n0 = (int)fminf(fmaxf(ceilf(fmaf(hb.b, fm, lo)), 0.0f), (float)nmin);
-                const int n1 = (int)fmaxf(fminf(floorf(fmaf(hb.b, fm, hi)), (float)(nmin - 1)), -1.0f);
-                // the major coordinate's share of R q~
-                const int qx0 = hb.xmajor ? m : 0, qy0 = hb.xmajor ? 0 : m;
-                const float b1 = fmaf(R1[0], (float)qx0, fmaf(R1[1], (float)qy0, R1[2]));
-                const float b2 = fmaf(R2[0], (float)qx0, fmaf(R2[1], (float)qy0, R2[2]));
-                const float b3 = fmaf(R3[0], (float)qx0, fmaf(R3[1], (float)qy0, R3[2]));
-                const float s1 = hb.xmajor ? R1[1] : R1[0], s2 = hb.xmajor ? R2[1] : R2[0], s3 = hb.xmajor ? R3[1] : R3[0];
-                if (pass == 0) n_exam += max(n1 - n0 + 1, 0);
-                for (int n = n0; n <= n1; ++n) {
-                    const int qx = hb.xmajor ? m : n, qy = hb.xmajor ? n : m;
-                    const long long off = fbase + (long long)(qy + kPad) * P.pitch + (qx + kPad);
-                    const float d = __ldg(P.depth + off);
-                    const float fn = (float)n;
-                    const float h1 = fmaf(d, fmaf(s1, fn, b1), E1);
-                    const float h2 = fmaf(d, fmaf(s2, fn, b2), E2);
-                    const float h3 = fmaf(d, fmaf(s3, fn, b3), E3);
-                    // NaN depth fails both comparisons
-                    if (fabsf(h1) + fabsf(h2) < L * h3 && fabsf(h3 - zmid) < zhalf) {
+            // The band is walked row by row of its minor axis (|b| <= 1 by the choice of the major
+            // axis), each row a run along the major axis: runs are long for the flat epipolar
+            // bands of a sideways-moving camera, and every candidate of the parallelogram
+            // b m + lo <= n <= b m + hi, m in [m0, m1], is visited once.
+            const float fb0 = fmaf(hb.b, (float)m0, 0.0f), fb1 = fmaf(hb.b, (float)m1, 0.0f);
+            const int r0 = (int)fminf(fmaxf(ceilf(fminf(fb0, fb1) + lo), 0.0f), (float)nmin);
+            const int r1 = (int)fmaxf(fminf(floorf(fmaxf(fb0, fb1) + hi), (float)(nmin - 1)), -1.0f);
+            const bool flat = fabsf(hb.b) < 1e-6f;
+            const float ib = flat ? 0.0f : 1.0f / hb.b;
+            // major / minor shares of R q~ and the memory stride along the major axis
+            const float sm1 = hb.xmajor ? R1[0] : R1[1], sm2 = hb.xmajor ? R2[0] : R2[1], sm3 = hb.xmajor ? R3[0] : R3[1];
+            const float sn1 = hb.xmajor ? R1[1] : R1[0], sn2 = hb.xmajor ? R2[1] : R2[0], sn3 = hb.xmajor ? R3[1] : R3[0];
+            const long long mstep = hb.xmajor ? 1ll : (long long)P.pitch;
+            const long long nstep = hb.xmajor ? (long long)P.pitch : 1ll;
+            const float *plane = P.depth + fbase + (long long)kPad * P.pitch + kPad;
+            for (int n = r0; n <= r1; ++n) {
+                const float fn = (float)n;
+                int ma = m0, mb = m1;
+                if (!flat) {
+                    // rounding of ta, tb is far below the 0.02 px margin already in lo and hi
+                    const float ta = (fn - hi) * ib, tb = (fn - lo) * ib;
+                    ma = max(m0, (int)fminf(fmaxf(ceilf(fminf(ta, tb) - 1e-3f), -1.0f), (float)nmaj));
+                    mb = min(m1, (int)fmaxf(fminf(floorf(fmaxf(ta, tb) + 1e-3f), (float)nmaj), -1.0f));
+                }
+                if (ma > mb) continue;
+                if (pass == 0) n_exam += mb - ma + 1;
+                const float b1 = fmaf(sn1, fn, R1[2]), b2 = fmaf(sn2, fn, R2[2]), b3 = fmaf(sn3, fn, R3[2]);
+                const float *rowp = plane + (long long)n * nstep;
+                // test up to 32 candidates of the run into a hit mask (no branch per candidate),
+                // then take the hits; the same arithmetic on the same operands gives the same h
+                for (int mc0 = ma; mc0 <= mb; mc0 += 32) {
+                    const int cnt = min(mb - mc0, 31);
+                    const float *dp = rowp + (long long)mc0 * mstep;
+                    float fm = (float)mc0;
+                    unsigned int hit = 0u;
+                    // four candidates per step, their loads in flight together; the last step may
+                    // read up to 3 pixels past the run, inside the image or its 32-pixel padding,
+                    // and their bits are dropped
+                    for (int k = 0; k <= cnt; k += 4, dp += 4 * mstep, fm += 4.0f) {
+                        float dq[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) dq[i] = __ldg(dp + i * mstep);
+                        unsigned int bits = 0u;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float fmi = fm + (float)i;
+                            const float h1 = fmaf(dq[i], fmaf(sm1, fmi, b1), E1);
+                            const float h2 = fmaf(dq[i], fmaf(sm2, fmi, b2), E2);
+                            const float h3 = fmaf(dq[i], fmaf(sm3, fmi, b3), E3);
+                            // NaN depth fails the comparisons
+                            bool t = fabsf(h1) + fabsf(h2) < L * h3;
+                            if (check_nf) t = t && fabsf(h3 - zmid) < zhalf;
+                            bits |= (unsigned int)t << i;
+                        }
+                        // keep the bits of candidates inside the run (k + i <= cnt)
+                        bits &= (2u << min(cnt - k, 3)) - 1u;
+                        hit |= bits << k;
+                    }
+                    while (hit) {
+                        const int k = __ffs((int)hit) - 1;
+                        hit &= hit - 1u;
+                        const int m = mc0 + k;
+                        const int qx = hb.xmajor ? m : n, qy = hb.xmajor ? n : m;
+                        const long long off = fbase + (long long)(qy + kPad) * P.pitch + (qx + kPad);
+                        const float d = __ldg(P.depth + off);
+                        const float fmk = (float)m;
+                        const float h1 = fmaf(d, fmaf(sm1, fmk, b1), E1);
+                        const float h2 = fmaf(d, fmaf(sm2, fmk, b2), E2);
+                        const float h3 = fmaf(d, fmaf(sm3, fmk, b3), E3);
                         // Eq. 9: masked samples weigh 0 in the mean-shift steps
                         if (INP && pass > 0 && __ldg(P.mask + off) != 0) continue;
                         const float3 c = load_colour<CFMT>(P.colour, off);
