@@ -440,6 +440,6 @@ def mlp_loss_grad(feat, col, nsamp, plain, clean, W1, b1, W2, b2, round_bf16=Tru
 def he_init(seed=0):
     """He-normal W1 (64 x 16), W2 (2 x 64), zero biases (numpy RNG, seeded)."""
     rng = np.random.default_rng(seed)
-    W1 = rng.normal(0, np.sqrt(2.0 / 12), (N_HID, N_FEAT))  # 12 non-zero inputs
+    W1 = rng.normal(0, np.sqrt(2.0 / 15), (N_HID, N_FEAT))  # 15 non-zero inputs
     W2 = rng.normal(0, np.sqrt(2.0 / N_HID), (2, N_HID))
     return W1, np.zeros(N_HID), W2, np.zeros(2)

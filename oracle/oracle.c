@@ -899,8 +899,9 @@ long long oc_bruteforce(const oc_clip *c, const oc_params *p, int O, int u, int 
  * frames J = O, O-1, O+1, O-2, O+2, ... (the earlier frame first on ties), then the k x k window
  * in raster order.  Features of a sample s gathered from pixel q of frame J (16 per sample):
  *   [c_s (3), c_s - c_ref (3), |X_q - x_ref| / r, (J - O) / max(T, 1), (d_q - z'_J) / r,
- *    log w_denoise(s) (Eq. 4, natural log), 1, |S(p)| / 64, 0 x 4]
- * (|S(p)| the size of the whole gathered set, which the plain fallback averages)
+ *    log w_denoise(s) (Eq. 4, natural log), 1, |S(p)| / 64, c_s - plain (3), 0]
+ * (|S(p)| the size of the whole gathered set, which the plain fallback averages, and plain the
+ * Eq. 4 result over it: the network sees each sample against the robust estimate it may replace)
  * with z'_J the depth of the reference point in camera J.  Network: h = ReLU(W1 f + b1) (64),
  * (z_w, z_c) = W2 h + b2; w_s = softplus(z_w); conf = mean_s sigmoid(z_c);
  * learned output = sum w_s c_s / sum w_s; final output = learned if conf >= tau else the plain
@@ -995,6 +996,8 @@ int oc_learned_samples(const oc_clip *c, const oc_params *p, int O, int u, int v
                 f[9] = log(oc_weight_denoise(s, sr, p->sigma_rgb, p->sigma_xyz, p->sigma_f));
                 f[10] = 1.0;
                 f[11] = ntot;
+                /* the sample against the plain Eq. 4 estimate of the whole set */
+                for (int i = 0; i < 3; ++i) f[12 + i] = cs[i] - plain[i];
                 ++*n;
             }
         }

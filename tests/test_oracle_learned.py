@@ -61,7 +61,9 @@ def test_features_in_canonical_order_have_the_closed_form_on_exact_shift():
         assert f[s, 7] == pytest.approx(dJ / T)
         assert f[s, 8] == pytest.approx(0.0, abs=1e-9)
         assert f[s, 9] == pytest.approx(-dJ ** 2 / (2 * prm.sigma_f ** 2), abs=1e-12)
-        assert f[s, 10] == 1.0 and f[s, 11] == nn / 64.0 and not f[s, 12:].any()
+        assert f[s, 10] == 1.0 and f[s, 11] == nn / 64.0 and f[s, 15] == 0.0
+        # every sample has the reference's colour, so the plain result does too
+        np.testing.assert_allclose(f[s, 12:15], 0.0, atol=1e-12)
 
 
 def test_set_size_feature_is_the_whole_gathered_set(tiny):
@@ -70,6 +72,19 @@ def test_set_size_feature_is_the_whole_gathered_set(tiny):
     full = oracle.gather_filter(v, prm, 4)
     has = n > 0
     np.testing.assert_array_equal(feat[..., 0, 11][has], full.nacc[has] / 64.0)
+
+
+def test_plain_residual_features_against_the_filter_output(tiny):
+    """Features 12-14 are each sample's colour minus the plain Eq. 4 output of the whole set:
+    checked against the gather-and-filter's own output and the stored sample colours."""
+    c, v, prm = tiny
+    feat, col, n, plain = oracle.learned_crop(v, prm, 4, crop=(0, 0, 64, 36))
+    full = oracle.gather_filter(v, prm, 4)
+    m = np.arange(64)[None, None, :] < n[..., None]
+    resid = col - full.rgb[:36, :64][:, :, None, :]
+    np.testing.assert_allclose(feat[..., 12:15][m], resid[m], atol=1e-12, rtol=0)
+    assert (feat[..., 15] == 0).all()
+    assert np.abs(feat[..., 12:15][m]).max() > 0.01
 
 
 def test_cap_keeps_the_first_64_in_canonical_order():
