@@ -310,7 +310,8 @@ void ssvp_plan_destroy(ssvp_plan *plan);
  * Learned per-sample weights (SSVP_MODE_LEARNED).  Per output pixel the first n <= 64 gathered
  * samples in canonical order (frames O, O-1, O+1, ..., then window raster order) get 16 features
  * [colour (3), colour - reference (3), distance / r, (J - O) / T, depth residual in the sample's
- * frame / r, log of the Eq. 4 weight, 1, size of the whole gathered set / 64, 0 x 4] (BF16); a
+ * frame / r, log of the Eq. 4 weight, 1, size of the whole gathered set / 64, colour - the plain
+ * Eq. 4 result (3), 0] (BF16); a
  * 16 -> 64 -> 2 MLP (BF16 tensor cores,
  * FP32 accumulation) gives per-sample weights softplus(z_w) and a confidence mean sigmoid(z_c);
  * the output is the weighted mean of the samples' colours when the confidence is at least

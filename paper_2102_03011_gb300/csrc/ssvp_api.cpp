@@ -1288,7 +1288,10 @@ int ssvp_learned_samples(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, 
     if (w == 0 || h == 0) { x0 = 0; y0 = 0; w = c.p.W; h = c.p.H; }
     if (x0 < 0 || y0 < 0 || x0 + w > c.p.W || y0 + h > c.p.H) return fail(ctx, SSVP_EINVAL, "crop outside the clip");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    return extract_samples(ctx, p, clip_id, p.frame_begin, x0, y0, w, h, feat, col, nsamp, plain);
+    if ((rc = extract_samples(ctx, p, clip_id, p.frame_begin, x0, y0, w, h, feat, col, nsamp, plain)) != SSVP_OK) return rc;
+    // the MLP kernels form features 12-14 on the fly; this caller gets them written out
+    CK(ssvp::launch_complete_features(feat, col, nsamp, plain, (long long)w * h, ctx->stream), "feature completion kernel");
+    return SSVP_OK;
 }
 
 int ssvp_mlp_grad(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, const int32_t *pixels, int n_pixels,
@@ -1361,9 +1364,9 @@ int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, co
     if ((rc = mlp_alloc(ctx)) != SSVP_OK) return rc;
     Rng rng{cfg->seed};
     if (cfg->init || !ctx->mlp_set) {
-        // He-normal W1 (12 non-zero inputs), W2; zero biases
+        // He-normal W1 (15 non-zero inputs), W2; zero biases
         std::vector<float> W1(1024), b1(64, 0.0f), W2(128), b2(2, 0.0f);
-        for (auto &x : W1) x = (float)(rng.normal() * std::sqrt(2.0 / 12.0));
+        for (auto &x : W1) x = (float)(rng.normal() * std::sqrt(2.0 / 15.0));
         for (auto &x : W2) x = (float)(rng.normal() * std::sqrt(2.0 / 64.0));
         if ((rc = ssvp_set_mlp(ctx, W1.data(), b1.data(), W2.data(), b2.data())) != SSVP_OK) return rc;
     }

@@ -49,7 +49,8 @@ constexpr int kMaxSamples = 64;  // learned filter: capped sample set
 constexpr float kLn2 = 0.6931471805599453f;
 
 // Features of one accepted sample for the learned filter (16 BF16 values) and its colour;
-// feature 11 (the size of the whole set) is filled in once the pixel's gather is complete.
+// feature 11 (the size of the whole set) is filled in once the pixel's gather is complete and
+// features 12-14 (the colour against the plain estimate) by their readers.
 __device__ __forceinline__ void store_sample(const GatherArgs &a, long long crop_idx, int slot, float3 c, float er,
                                              float eg, float eb, float dist_r, float dj_t, float dz_r, float logw) {
     const float f[16] = {c.x, c.y, c.z, er, eg, eb, dist_r, dj_t, dz_r, logw, 1.0f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -158,18 +159,40 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                     Ax[dx] = __fmaf_rn((float)dx, ifx, Ax0);
                     Bx[dx] = __fmaf_rn((float)dx, zix, Bx0);
                 }
+                // columns (dx, dx + 1) are tested as pairs with packed FP32x2 arithmetic: each half
+                // runs the scalar sequence below, so the distances are the same to the bit
+                constexpr int KP = K / 2;
+                f32x2 AxP[KP > 0 ? KP : 1], BxP[KP > 0 ? KP : 1];
+#pragma unroll
+                for (int q = 0; q < KP; ++q) {
+                    AxP[q] = f2_pack(Ax[2 * q], Ax[2 * q + 1]);
+                    BxP[q] = f2_pack(Bx[2 * q], Bx[2 * q + 1]);
+                }
+                const f32x2 zh2 = f2_pack(zh, zh), zl2 = f2_pack(zl, zl);
                 unsigned long long mask = 0ull;
 #pragma unroll
                 for (int dy = 0; dy < K; ++dy) {
                     const float Ay = __fmaf_rn((float)dy, ify, Ay0), By = __fmaf_rn((float)dy, ziy, By0);
+                    const f32x2 Ay2 = f2_pack(Ay, Ay), By2 = f2_pack(By, By);
                     const float *drow = dwin + (long long)dy * P.pitch;
 #pragma unroll
-                    for (int dx = 0; dx < K; ++dx) {
+                    for (int q = 0; q < KP; ++q) {
+                        const f32x2 dz = f2_sub(f2_sub(f2_pack(__ldg(drow + 2 * q), __ldg(drow + 2 * q + 1)), zh2), zl2);
+                        const f32x2 X = f2_fma(dz, AxP[q], BxP[q]);
+                        const f32x2 Y = f2_fma(dz, Ay2, By2);
+                        const f32x2 d2 = f2_fma(X, X, f2_fma(Y, Y, f2_mul(dz, dz)));
+                        float d2a, d2b;
+                        f2_unpack(d2, d2a, d2b);
+                        if (d2a < r2) mask |= 1ull << (dy * 8 + 2 * q);  // stride 8: cheap decode
+                        if (d2b < r2) mask |= 1ull << (dy * 8 + 2 * q + 1);
+                    }
+                    if (K & 1) {
+                        constexpr int dx = K - 1;
                         const float dz = (__ldg(drow + dx) - zh) - zl;
                         const float X = fmaf(dz, Ax[dx], Bx[dx]);
                         const float Y = fmaf(dz, Ay, By);
                         const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
-                        if (d2 < r2) mask |= 1ull << (dy * 8 + dx);  // stride 8: cheap decode
+                        if (d2 < r2) mask |= 1ull << (dy * 8 + dx);
                     }
                 }
                 if (DEBUG && rec) {
@@ -288,7 +311,9 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
         o[2] = o_b;
         if (LEARN) {
             a.nsamp_out[crop_idx] = n_feat;
-            // feature 11: size of the whole gathered set (what the plain fallback averages) / 64
+            // feature 11: size of the whole gathered set (what the plain fallback averages) / 64;
+            // features 12-14 (colour minus this plain result) are formed where they are read, from
+            // the stored colours and plain_out
             const __nv_bfloat16 nb = __float2bfloat16_rn((float)n_acc * (1.0f / 64.0f));
             const unsigned short nbits = *reinterpret_cast<const unsigned short *>(&nb);
             for (int s = 0; s < n_feat; ++s) a.feat_out[(crop_idx * kMaxSamples + s) * 16 + 11] = nbits;

@@ -143,6 +143,8 @@ cudaError_t launch_mlp_infer(const MlpArgs &m, cudaStream_t s);
 cudaError_t launch_mlp_train(const MlpArgs &m, cudaStream_t s);
 cudaError_t launch_adam(const MlpState &st, float lr, int step, cudaStream_t s);
 cudaError_t launch_mlp_refresh(const MlpState &st, cudaStream_t s);
+cudaError_t launch_complete_features(unsigned short *feat, const float *col, const int32_t *nsamp, const float *plain,
+                                     long long n_px, cudaStream_t s);
 
 cudaError_t launch_pack(const float *rgb, const float *depth, int W, int H, int nF, const Planes &dst, int frame0,
                         cudaStream_t s);

@@ -43,15 +43,42 @@ __device__ __forceinline__ float sigmoidf(float x) { return 1.0f / (1.0f + __exp
 
 __device__ __forceinline__ unsigned pack2(unsigned short lo, unsigned short hi) { return (unsigned)lo | ((unsigned)hi << 16); }
 
-// A fragments (rows = samples) of the four 16-sample tiles; rows >= n are zero
-__device__ __forceinline__ void load_features(const unsigned *fw, int n, int g, int t, unsigned (&a)[4][4]) {
+__device__ __forceinline__ unsigned short bf16_bits(float x) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(x);
+    return *reinterpret_cast<const unsigned short *>(&b);
+}
+
+// Features 12-15 of one sample as BF16 words: (c0 - p0, c1 - p1) for word 6, (c2 - p2, 0) for
+// word 7 - the sample's colour against the pixel's plain Eq. 4 result.
+__device__ __forceinline__ unsigned resid_word(const float *c, const float *pl, int word) {
+    return word == 6 ? pack2(bf16_bits(__ldg(c) - pl[0]), bf16_bits(__ldg(c + 1) - pl[1]))
+                     : pack2(bf16_bits(__ldg(c + 2) - pl[2]), 0);
+}
+
+// Feature i of sample s as BF16 bits (the B operand of the dW1 product)
+__device__ __forceinline__ unsigned short feature_bits(const unsigned short *fh, const float *col, const float *pl,
+                                                       int s, int i) {
+    if (i < 12) return fh[s * kF + i];
+    if (i == 15) return 0;
+    return bf16_bits(__ldg(col + s * 3 + (i - 12)) - pl[i - 12]);
+}
+
+// A fragments (rows = samples) of the four 16-sample tiles; rows >= n are zero.  col and pl: the
+// pixel's sample colours and plain result, from which words 6 and 7 (features 12-15) are formed.
+__device__ __forceinline__ void load_features(const unsigned *fw, const float *col, const float *pl, int n, int g,
+                                              int t, unsigned (&a)[4][4]) {
 #pragma unroll
     for (int mt = 0; mt < 4; ++mt) {
         const int r0 = 16 * mt + g, r1 = r0 + 8;
         a[mt][0] = r0 < n ? __ldg(fw + r0 * 8 + t) : 0u;
         a[mt][1] = r1 < n ? __ldg(fw + r1 * 8 + t) : 0u;
-        a[mt][2] = r0 < n ? __ldg(fw + r0 * 8 + 4 + t) : 0u;
-        a[mt][3] = r1 < n ? __ldg(fw + r1 * 8 + 4 + t) : 0u;
+        if (t < 2) {
+            a[mt][2] = r0 < n ? __ldg(fw + r0 * 8 + 4 + t) : 0u;
+            a[mt][3] = r1 < n ? __ldg(fw + r1 * 8 + 4 + t) : 0u;
+        } else {
+            a[mt][2] = r0 < n ? resid_word(col + r0 * 3, pl, 4 + t) : 0u;
+            a[mt][3] = r1 < n ? resid_word(col + r1 * 3, pl, 4 + t) : 0u;
+        }
     }
 }
 
@@ -124,7 +151,9 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_infer_kernel(const MlpArgs m)
         float o0 = pl[0], o1 = pl[1], o2 = pl[2], conf = 0.0f;
         if (n > 0) {
             unsigned a[4][4];
-            load_features(reinterpret_cast<const unsigned *>(m.feat) + px * (kS * kF / 2), n, g, t, a);
+            const float plv[3] = {o0, o1, o2};
+            load_features(reinterpret_cast<const unsigned *>(m.feat) + px * (kS * kF / 2), m.col + px * kS * 3, plv, n,
+                          g, t, a);
             PixelForward pf;
             forward(a, bw, m.w, t, pf);
             float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
@@ -193,8 +222,10 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
         if (n <= 0) continue;  // warp-uniform
         const unsigned *fw = reinterpret_cast<const unsigned *>(m.feat) + px * (kS * kF / 2);
         const unsigned short *fh = m.feat + px * (kS * kF);
+        const float *colp = m.col + px * kS * 3;
+        const float plv[3] = {m.plain[3 * px], m.plain[3 * px + 1], m.plain[3 * px + 2]};
         unsigned a[4][4];
-        load_features(fw, n, g, t, a);
+        load_features(fw, colp, plv, n, g, t, a);
         PixelForward pf;
         forward(a, bw, m.w, t, pf);
         // per-sample weights, outputs and the pixel's loss
@@ -321,8 +352,8 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
                 const int i = 8 * nt + g;
-                bf[nt][0] = pack2(s0 < n ? fh[s0 * kF + i] : 0, s1 < n ? fh[s1 * kF + i] : 0);
-                bf[nt][1] = pack2(s8 < n ? fh[s8 * kF + i] : 0, s9 < n ? fh[s9 * kF + i] : 0);
+                bf[nt][0] = pack2(s0 < n ? feature_bits(fh, colp, plv, s0, i) : 0, s1 < n ? feature_bits(fh, colp, plv, s1, i) : 0);
+                bf[nt][1] = pack2(s8 < n ? feature_bits(fh, colp, plv, s8, i) : 0, s9 < n ? feature_bits(fh, colp, plv, s9, i) : 0);
             }
 #pragma unroll
             for (int mt = 0; mt < 4; ++mt) {
@@ -361,6 +392,22 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
 }
 
 // ---------------------------------------------------------------- Adam on the FP32 master weights
+// Features 12-14 of every stored sample, written into the feature buffer (for callers that read
+// the sample sets themselves; the MLP kernels form them on the fly).
+__global__ void complete_features_kernel(unsigned short *feat, const float *col, const int32_t *nsamp,
+                                         const float *plain, long long n_px) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n_px * kS) return;
+    const long long px = i / kS;
+    const int s = (int)(i - px * kS);
+    if (s >= nsamp[px]) return;
+    const float *c = col + i * 3, *pl = plain + 3 * px;
+    unsigned short *f = feat + i * kF;
+    f[12] = bf16_bits(c[0] - pl[0]);
+    f[13] = bf16_bits(c[1] - pl[1]);
+    f[14] = bf16_bits(c[2] - pl[2]);
+}
+
 __global__ void adam_kernel(MlpState st, float lr, float b1, float b2, float eps, int step) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kMlpParams) return;
@@ -405,6 +452,14 @@ cudaError_t launch_adam(const MlpState &st, float lr, int step, cudaStream_t s) 
 
 cudaError_t launch_mlp_refresh(const MlpState &st, cudaStream_t s) {
     refresh_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_complete_features(unsigned short *feat, const float *col, const int32_t *nsamp, const float *plain,
+                                     long long n_px, cudaStream_t s) {
+    const long long n = n_px * kS;
+    if (n == 0) return cudaSuccess;
+    complete_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(feat, col, nsamp, plain, n_px);
     return cudaGetLastError();
 }
 
