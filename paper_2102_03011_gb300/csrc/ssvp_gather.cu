@@ -31,10 +31,7 @@ namespace {
 #define SSVP_MIN_CTAS 4  // resident CTAs per SM the register allocation must allow
 #endif
 
-#ifndef SSVP_ACC_BATCH
-#define SSVP_ACC_BATCH 1  // accepted samples processed per iteration of the filter loop
-#endif
-constexpr int kAccBatch = SSVP_ACC_BATCH;
+
 
 #ifndef SSVP_TILE_Y
 #define SSVP_TILE_Y 8  // output rows per CTA (a warp covers 32 pixels of one row)
@@ -71,7 +68,9 @@ __device__ __forceinline__ void store_sample(const GatherArgs &a, long long crop
 
 // LEARN: visit the frames in canonical order (O, O-1, O+1, ...) and store the features of the
 // first kMaxSamples accepted samples (learned filter); the Eq. 3/4 result goes to a.plain_out.
-template <int K, int CFMT, bool DEBUG, bool LEARN = false>
+// ACCB: accepted samples taken per iteration of the filter loop (1, or 2 in packed FP32x2; two
+// pays off where registers allow it: the plain per-launch kernel, not the batched or learned one)
+template <int K, int CFMT, bool DEBUG, bool LEARN = false, int ACCB = 1>
 __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &P, const int O, const int u0,
                                              const int v0, const int u, const int v, const bool active,
                                              const long long crop_idx, const float4 *sgeom, const int n_slots,
@@ -202,27 +201,73 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                     rec[3] = (int32_t)(unsigned int)(packed & 0xffffffffull);
                     if (K * K > 32) rec[4] = (int32_t)(unsigned int)(packed >> 32);
                 }
-                // accepted samples, kAccBatch per iteration so that their loads overlap
+                // accepted samples, ACCB per iteration so that their loads overlap; with two,
+                // the pair's sums are kept in packed partial sums and folded after the frame
+                f32x2 pr = 0ull, pg = 0ull, pb = 0ull, pw = 0ull;  // +0.0f in both halves
 #pragma unroll 1
                 while (mask) {
-                    int idx[kAccBatch];
-                    bool ok[kAccBatch];
+                    int idx[ACCB];
+                    bool ok[ACCB];
 #pragma unroll
-                    for (int t = 0; t < kAccBatch; ++t) {
+                    for (int t = 0; t < ACCB; ++t) {
                         ok[t] = mask != 0ull;
                         idx[t] = ok[t] ? __ffsll((long long)mask) - 1 : 0;  // slot 0 is always in bounds
                         mask &= mask - 1ull;
                     }
-                    float dq[kAccBatch];
-                    float3 cq[kAccBatch];
+                    float dq[ACCB];
+                    float3 cq[ACCB];
 #pragma unroll
-                    for (int t = 0; t < kAccBatch; ++t) {
+                    for (int t = 0; t < ACCB; ++t) {
                         const int off = (idx[t] >> 3) * P.pitch + (idx[t] & 7);
                         dq[t] = __ldg(dwin + off);
                         cq[t] = load_colour<CFMT>(cwin, off);
                     }
+                    if constexpr (ACCB == 2) {
+                        // the two samples in packed FP32x2: per half the scalar sequence below
+                        const f32x2 dxf = f2_pack(small_float(idx[0] & 7), small_float(idx[1] & 7));
+                        const f32x2 dyf = f2_pack(small_float(idx[0] >> 3), small_float(idx[1] >> 3));
+                        const f32x2 dz = f2_sub(f2_sub(f2_pack(dq[0], dq[1]), f2_pack(zh, zh)), f2_pack(zl, zl));
+                        const f32x2 X = f2_fma(dz, f2_fma(dxf, f2_pack(ifx, ifx), f2_pack(Ax0, Ax0)),
+                                               f2_fma(dxf, f2_pack(zix, zix), f2_pack(Bx0, Bx0)));
+                        const f32x2 Y = f2_fma(dz, f2_fma(dyf, f2_pack(ify, ify), f2_pack(Ay0, Ay0)),
+                                               f2_fma(dyf, f2_pack(ziy, ziy), f2_pack(By0, By0)));
+                        const f32x2 d2 = f2_fma(X, X, f2_fma(Y, Y, f2_mul(dz, dz)));
+                        const f32x2 er = f2_sub(f2_pack(cq[0].x, cq[1].x), f2_pack(cref.x, cref.x));
+                        const f32x2 eg = f2_sub(f2_pack(cq[0].y, cq[1].y), f2_pack(cref.y, cref.y));
+                        const f32x2 eb = f2_sub(f2_pack(cq[0].z, cq[1].z), f2_pack(cref.z, cref.z));
+                        const f32x2 e = f2_fma(f2_pack(a_rgb, a_rgb), f2_fma(er, er, f2_fma(eg, eg, f2_mul(eb, eb))),
+                                               f2_fma(f2_pack(a_xyz, a_xyz), d2, f2_pack(beta, beta)));
+                        float e0, e1;
+                        f2_unpack(e, e0, e1);
+                        const float w0 = weighted ? ex2(-e0) : 1.0f;
+                        const float w1 = ok[1] ? (weighted ? ex2(-e1) : 1.0f) : 0.0f;  // ok[0] holds in the loop
+                        if (LEARN) {
+                            float er0, er1, eg0, eg1, eb0, eb1, dd0, dd1, dz0, dz1;
+                            f2_unpack(er, er0, er1);
+                            f2_unpack(eg, eg0, eg1);
+                            f2_unpack(eb, eb0, eb1);
+                            f2_unpack(d2, dd0, dd1);
+                            f2_unpack(dz, dz0, dz1);
+                            if (n_feat < kMaxSamples) {
+                                store_sample(a, crop_idx, n_feat, cq[0], er0, eg0, eb0, sqrtf(dd0) * inv_r,
+                                             (float)(j - Tw) * inv_T, dz0 * inv_r, -e0 * kLn2);
+                                ++n_feat;
+                            }
+                            if (ok[1] && n_feat < kMaxSamples) {
+                                store_sample(a, crop_idx, n_feat, cq[1], er1, eg1, eb1, sqrtf(dd1) * inv_r,
+                                             (float)(j - Tw) * inv_T, dz1 * inv_r, -e1 * kLn2);
+                                ++n_feat;
+                            }
+                        }
+                        const f32x2 w = f2_pack(w0, w1);
+                        pr = f2_fma(w, er, pr);
+                        pg = f2_fma(w, eg, pg);
+                        pb = f2_fma(w, eb, pb);
+                        pw = f2_add(pw, w);
+                        n_acc += 1 + (ok[1] ? 1 : 0);
+                    } else {
 #pragma unroll
-                    for (int t = 0; t < kAccBatch; ++t) {
+                    for (int t = 0; t < ACCB; ++t) {
                         const float dxf = small_float(idx[t] & 7), dyf = small_float(idx[t] >> 3);
                         const float dz = (dq[t] - zh) - zl;
                         const float X = fmaf(dz, __fmaf_rn(dxf, ifx, Ax0), __fmaf_rn(dxf, zix, Bx0));
@@ -245,6 +290,18 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                             ++n_acc;
                         }
                     }
+                    }
+                }
+                if (ACCB == 2) {
+                    float lo, hi;
+                    f2_unpack(pr, lo, hi);
+                    acc_r += lo + hi;
+                    f2_unpack(pg, lo, hi);
+                    acc_g += lo + hi;
+                    f2_unpack(pb, lo, hi);
+                    acc_b += lo + hi;
+                    f2_unpack(pw, lo, hi);
+                    acc_w += lo + hi;
                 }
             } else {
                 if (DEBUG && rec)
@@ -365,8 +422,9 @@ __global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const G
     const long long crop_idx = (long long)(v - a.y0) * a.cw + (u - a.x0);
     int n_acc = 0, n_exam = 0;
     float acc_w = 0.0f;
-    gather_pixel<K, CFMT, DEBUG, LEARN>(a, a.clip, O, u0, v0, u, v, active, crop_idx, sgeom, a.n_slots, s_const[0], s_const[1],
-                                 s_const[2], s_const[3] != 0.0f, n_acc, n_exam, acc_w);
+    gather_pixel<K, CFMT, DEBUG, LEARN, LEARN ? 1 : 2>(a, a.clip, O, u0, v0, u, v, active, crop_idx, sgeom, a.n_slots,
+                                                       s_const[0], s_const[1], s_const[2], s_const[3] != 0.0f, n_acc,
+                                                       n_exam, acc_w);
 
     // launch statistics: warp, then block, then one atomic per CTA
     unsigned long long ce = (unsigned long long)n_exam, ca = (unsigned long long)n_acc;
