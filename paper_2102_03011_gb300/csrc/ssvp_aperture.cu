@@ -163,53 +163,87 @@ __global__ void __launch_bounds__(kApThreads, 4) aperture_kernel(const GatherArg
             // E = 8 u (|dz| c1 + |o.b| c3 + c2) bounding both the offset error (8 u (|dz| Gm + Em))
             // and the cone-radius error from t (slope 8 u (d_ref + |dz / b_z| + |o.b| foot))
             const float c1 = Gm + slope * fabsf(inv_bz), c2 = Em + slope * dref, c3 = slope * foot;
+            // one candidate: the FP32 fast path's diff and a(t) come in; refine near the cone
+            // surface in double-float, then accumulate when inside
+            auto finish = [&](float d, float iff, float jf, float diff, float ar, float E, long long idx, int qx, int qy) {
+                if (fabsf(diff) <= 4.0f * (ar + E) * E) {
+                    // near the cone surface: recompute the offsets in double-float
+                    const df dzd = fast_two_sum(d - zh, -zl);
+                    const df Gd = df_add_f(gx, iff), Ed = df_add_f(ex, iff);
+                    const df Sx = df_add(df_mul(dzd, Gd), df_mul({zh, zl}, Ed));
+                    const df Gyd = df_add_f(gy, jf), Eyd = df_add_f(ey, jf);
+                    const df Sy = df_add(df_mul(dzd, Gyd), df_mul({zh, zl}, Eyd));
+                    const float ox = (Sx.hi + Sx.lo) * ifx;
+                    const float oy = (Sy.hi + Sy.lo) * ify;
+                    const float ob = fmaf(ox, bnx, oy * bny);
+                    const float p2 = fmaf(ox, ox, fmaf(oy, oy, -ob * ob));
+                    const float t = fmaf(dzd.hi, inv_bz, dref) + ob * foot;
+                    ar = fmaf(slope, fabsf(z0 - t), a0);
+                    diff = p2 - ar * ar;
+                }
+                if (diff < 0.0f) {
+                    const float3 c = load_colour<CFMT>(P.colour, idx);
+                    const float e = d * ifx;
+                    const float w = e * e * kInvPi / (ar * ar);
+                    acc_r = fmaf(w, c.x - cref.x, acc_r);
+                    acc_g = fmaf(w, c.y - cref.y, acc_g);
+                    acc_b = fmaf(w, c.z - cref.z, acc_b);
+                    acc_w += w;
+                    ++n_acc;
+                    if (DEBUG && rec) {
+                        const int bit = (qy - by0) * a.cap + (qx - bx0);
+                        rec[5 + (bit >> 5)] |= (int32_t)(1u << (bit & 31));
+                    }
+                }
+            };
+            // per-(pixel, J) constants, duplicated for the packed FP32x2 path
+            const f32x2 zh2 = f2_pack(zh, zh), zl2 = f2_pack(zl, zl), ifx2 = f2_pack(ifx, ifx), zix2 = f2_pack(zix, zix);
+            const f32x2 gxf2 = f2_pack(gxf, gxf), exf2 = f2_pack(exf, exf), bnx2 = f2_pack(bnx, bnx), bny2 = f2_pack(bny, bny);
+            const f32x2 ibz2 = f2_pack(inv_bz, inv_bz), dref2 = f2_pack(dref, dref), foot2 = f2_pack(foot, foot);
+            const f32x2 z02 = f2_pack(z0, z0), slope2 = f2_pack(slope, slope), a02 = f2_pack(a0, a0);
+            const f32x2 c12 = f2_pack(c1, c1), c22 = f2_pack(c2, c2), c32 = f2_pack(c3, c3);
+            const f32x2 k8u = f2_pack(8.0f * kU, 8.0f * kU), neg1 = f2_pack(-1.0f, -1.0f);
             const long long jbase = (long long)J * P.fstride;
             for (int qy = y0c; qy <= y1c; ++qy) {
                 const float jf = (float)(qy - by0);
                 const float Gy = fmaf(jf, ify, gyf), Ey = fmaf(jf, ziy, eyf);
+                const f32x2 Gy2 = f2_pack(Gy, Gy), Ey2 = f2_pack(Ey, Ey);
                 const long long rowb = jbase + (long long)(qy + kPad) * P.pitch + kPad;
                 float iff = (float)(x0c - bx0);
-                for (int qx = x0c; qx <= x1c; ++qx, iff += 1.0f) {
-                    // invalid depth is NaN: it fails both comparisons below
+                int qx = x0c;
+                // two candidates per step in packed FP32x2 (invalid depth is NaN: it fails both
+                // comparisons of finish)
+                for (; qx + 1 <= x1c; qx += 2, iff += 2.0f) {
+                    const float d0 = __ldg(P.depth + rowb + qx), d1 = __ldg(P.depth + rowb + qx + 1);
+                    const f32x2 dz = f2_sub(f2_sub(f2_pack(d0, d1), zh2), zl2);
+                    const f32x2 if2 = f2_pack(iff, iff + 1.0f);
+                    const f32x2 ox = f2_fma(dz, f2_fma(if2, ifx2, gxf2), f2_fma(if2, zix2, exf2));
+                    const f32x2 oy = f2_fma(dz, Gy2, Ey2);
+                    const f32x2 ob = f2_fma(ox, bnx2, f2_mul(oy, bny2));
+                    const f32x2 p2 = f2_fma(ox, ox, f2_fma(oy, oy, f2_mul(f2_mul(ob, neg1), ob)));
+                    const f32x2 t = f2_fma(ob, foot2, f2_fma(dz, ibz2, dref2));
+                    const f32x2 ar = f2_fma(slope2, f2_abs(f2_sub(z02, t)), a02);
+                    const f32x2 diff = f2_fma(f2_mul(ar, neg1), ar, p2);
+                    const f32x2 E = f2_mul(k8u, f2_fma(f2_abs(dz), c12, f2_fma(f2_abs(ob), c32, c22)));
+                    float df0, df1, ar0, ar1, E0, E1;
+                    f2_unpack(diff, df0, df1);
+                    f2_unpack(ar, ar0, ar1);
+                    f2_unpack(E, E0, E1);
+                    finish(d0, iff, jf, df0, ar0, E0, rowb + qx, qx, qy);
+                    finish(d1, iff + 1.0f, jf, df1, ar1, E1, rowb + qx + 1, qx + 1, qy);
+                }
+                if (qx <= x1c) {  // the odd last column
                     const float d = __ldg(P.depth + rowb + qx);
                     const float dz = (d - zh) - zl;
-                    float ox = fmaf(dz, fmaf(iff, ifx, gxf), fmaf(iff, zix, exf));
-                    float oy = fmaf(dz, Gy, Ey);
-                    float ob = fmaf(ox, bnx, oy * bny);
-                    float p2 = fmaf(ox, ox, fmaf(oy, oy, -ob * ob));
-                    float t = fmaf(dz, inv_bz, dref) + ob * foot;
-                    float ar = fmaf(slope, fabsf(z0 - t), a0);
-                    float diff = p2 - ar * ar;
+                    const float ox = fmaf(dz, fmaf(iff, ifx, gxf), fmaf(iff, zix, exf));
+                    const float oy = fmaf(dz, Gy, Ey);
+                    const float ob = fmaf(ox, bnx, oy * bny);
+                    const float p2 = fmaf(ox, ox, fmaf(oy, oy, -ob * ob));
+                    const float t = fmaf(ob, foot, fmaf(dz, inv_bz, dref));
+                    const float ar = fmaf(slope, fabsf(z0 - t), a0);
+                    const float diff = fmaf(-ar, ar, p2);
                     const float E = 8.0f * kU * fmaf(fabsf(dz), c1, fmaf(fabsf(ob), c3, c2));
-                    if (fabsf(diff) <= 4.0f * (ar + E) * E) {
-                        // near the cone surface: recompute the offsets in double-float
-                        const df dzd = fast_two_sum(d - zh, -zl);
-                        const df Gd = df_add_f(gx, iff), Ed = df_add_f(ex, iff);
-                        const df Sx = df_add(df_mul(dzd, Gd), df_mul({zh, zl}, Ed));
-                        const df Gyd = df_add_f(gy, jf), Eyd = df_add_f(ey, jf);
-                        const df Sy = df_add(df_mul(dzd, Gyd), df_mul({zh, zl}, Eyd));
-                        ox = (Sx.hi + Sx.lo) * ifx;
-                        oy = (Sy.hi + Sy.lo) * ify;
-                        ob = fmaf(ox, bnx, oy * bny);
-                        p2 = fmaf(ox, ox, fmaf(oy, oy, -ob * ob));
-                        t = fmaf(dzd.hi, inv_bz, dref) + ob * foot;
-                        ar = fmaf(slope, fabsf(z0 - t), a0);
-                        diff = p2 - ar * ar;
-                    }
-                    if (diff < 0.0f) {
-                        const float3 c = load_colour<CFMT>(P.colour, rowb + qx);
-                        const float e = d * ifx;
-                        const float w = e * e * kInvPi / (ar * ar);
-                        acc_r = fmaf(w, c.x - cref.x, acc_r);
-                        acc_g = fmaf(w, c.y - cref.y, acc_g);
-                        acc_b = fmaf(w, c.z - cref.z, acc_b);
-                        acc_w += w;
-                        ++n_acc;
-                        if (DEBUG && rec) {
-                            const int bit = (qy - by0) * a.cap + (qx - bx0);
-                            rec[5 + (bit >> 5)] |= (int32_t)(1u << (bit & 31));
-                        }
-                    }
+                    finish(d, iff, jf, diff, ar, E, rowb + qx, qx, qy);
                 }
             }
         }

@@ -119,6 +119,8 @@ __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
     return d;
 }
 
+__device__ __forceinline__ f32x2 f2_abs(f32x2 a) { return a & 0x7fffffff7fffffffull; }
+
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kSlotVec = 6;  // float4 words of per-slot geometry in shared memory
 
