@@ -371,6 +371,27 @@ def run_batch(args, ss, torch, dev, stream, world, rank):
         psnr_in.append(10 * np.log10(1 / mse(c.rgb, c.clean)))
     ss.ssvp_plan_destroy(plan)
 
+    # the plain FP32 form on the same clips: FP32 colour planes, 8 sequential launches
+    n = len(clips)
+    for i, c in enumerate(clips):
+        r, d = torch.from_numpy(c.rgb).to(dev), torch.from_numpy(c.depth).to(dev)
+        ss.ssvp_load_clip(ctx, n + i, c.W, c.H, c.F, r, d, None, ss.SSVP_COLOUR_F32)
+        ss.ssvp_set_cameras(ctx, n + i, c.K, 1, c.w2c)
+        del r, d
+
+    def sequential_fp32():
+        for i in ids:
+            ss.ssvp_gather_filter(ctx, p, [n + i])
+
+    seq32_ms = timed(sequential_fp32, max(1, args.steps // 2))
+    psnr32 = []
+    for i, c in enumerate(clips):
+        o = torch.empty((c.F, c.H, c.W, 3), dtype=torch.float32, device=dev)
+        ss.ssvp_read_output(ctx, n + i, 0, c.F, o)
+        ss.ssvp_sync(ctx)
+        psnr32.append(10 * np.log10(1 / float(np.mean((o.cpu().numpy().astype(np.float64) - c.clean) ** 2))))
+        ss.ssvp_unload_clip(ctx, n + i)
+
     # end to end: upload all clips from pinned host memory, plan, launch, download, every step
     pinned = [(torch.from_numpy(c.rgb).pin_memory(), torch.from_numpy(c.depth).pin_memory(),
                torch.empty((c.F, c.H, c.W, 3), dtype=torch.float32).pin_memory()) for c in clips]
@@ -399,7 +420,10 @@ def run_batch(args, ss, torch, dev, stream, world, rank):
                             "grid": grid, "autotune_s": tune_s},
                    "l2": "no flush: packed planes of 8 clips (GBs) exceed the 129 MB L2"},
         "sequential_plain_launches": {"value": world * total_px / 1e6 / (seq_ms / 1e3), "unit": "Mpix/s",
-                                      "ms_per_step": seq_ms},
+                                      "ms_per_step": seq_ms, "colour": "fp16"},
+        "plain_fp32_sequential": {"value": world * total_px / 1e6 / (seq32_ms / 1e3), "unit": "Mpix/s",
+                                  "ms_per_step": seq32_ms, "psnr_db": float(np.mean(psnr32)),
+                                  "note": "the same clips with FP32 colour, one plain launch per clip"},
         "samples_per_s": {"examined": world * examined / (plan_ms / 1e3), "accepted": world * accepted / (plan_ms / 1e3)},
         "psnr_db": {"output_vs_clean": float(np.mean(psnr_out)), "input_vs_clean": float(np.mean(psnr_in)),
                     "reference": "clean pinhole renders, mean over clips"},
