@@ -53,9 +53,9 @@ struct ssvp_ctx {
     unsigned short *mlp_w1 = nullptr;
     bool mlp_set = false;
     int mlp_step = 0;
-    unsigned short *l_feat = nullptr;
-    float *l_col = nullptr, *l_plain = nullptr, *l_loss = nullptr;
-    int32_t *l_n = nullptr, *l_batch = nullptr;
+    ssvp::SampleSets l_sets{};  // compact capped sample sets of one frame's crop
+    float *l_loss = nullptr;
+    int32_t *l_batch = nullptr;
     size_t l_cap = 0, l_batch_cap = 0, l_loss_cap = 0;
     // tuned batch shapes: key (k, half window, mode, colour format) -> config
     struct Tuned {
@@ -410,24 +410,29 @@ ssvp::MlpWeights mlp_weights(const ssvp_ctx *ctx) {
 }
 
 // scratch for the capped sample sets of n_px crop pixels
+void free_sets(ssvp::SampleSets &S) {
+    for (void *q : {(void *)S.col, (void *)S.f89, (void *)S.info, (void *)S.n, (void *)S.plain})
+        if (q) cudaFree(q);
+    S = ssvp::SampleSets{};
+}
+
 int learned_scratch(ssvp_ctx *ctx, size_t n_px) {
     if (n_px <= ctx->l_cap) return SSVP_OK;
     CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
-    for (void *q : {(void *)ctx->l_feat, (void *)ctx->l_col, (void *)ctx->l_plain, (void *)ctx->l_n})
-        if (q) cudaFree(q);
-    ctx->l_feat = nullptr; ctx->l_col = nullptr; ctx->l_plain = nullptr; ctx->l_n = nullptr;
+    free_sets(ctx->l_sets);
     ctx->l_cap = 0;
-    CK(cudaMalloc(&ctx->l_feat, n_px * 64 * 16 * sizeof(unsigned short)), "cudaMalloc (learned scratch)");
-    CK(cudaMalloc(&ctx->l_col, n_px * 64 * 3 * sizeof(float)), "cudaMalloc (learned scratch)");
-    CK(cudaMalloc(&ctx->l_plain, n_px * 3 * sizeof(float)), "cudaMalloc (learned scratch)");
-    CK(cudaMalloc(&ctx->l_n, n_px * sizeof(int32_t)), "cudaMalloc (learned scratch)");
+    ssvp::SampleSets &S = ctx->l_sets;
+    CK(cudaMalloc(&S.col, n_px * 64 * sizeof(float4)), "cudaMalloc (learned scratch)");
+    CK(cudaMalloc(&S.f89, n_px * 64 * sizeof(unsigned)), "cudaMalloc (learned scratch)");
+    CK(cudaMalloc(&S.info, n_px * sizeof(float4)), "cudaMalloc (learned scratch)");
+    CK(cudaMalloc(&S.n, n_px * sizeof(int32_t)), "cudaMalloc (learned scratch)");
+    CK(cudaMalloc(&S.plain, n_px * 3 * sizeof(float)), "cudaMalloc (learned scratch)");
     ctx->l_cap = n_px;
     return SSVP_OK;
 }
 
-// capped sample sets of output frame O of a clip over a crop, into the given buffers
-int extract_samples(ssvp_ctx *ctx, const ssvp_params &p, int clip_id, int O, int x0, int y0, int cw, int ch,
-                    unsigned short *feat, float *col, int32_t *nsamp, float *plain) {
+// capped sample sets of output frame O of a clip over a crop, into the context's scratch
+int extract_samples(ssvp_ctx *ctx, const ssvp_params &p, int clip_id, int O, int x0, int y0, int cw, int ch) {
     Clip &c = ctx->clips[clip_id];
     const int T = p.half_window, ns = 2 * T + 1;
     if ((size_t)ns > ctx->geom_cap) {
@@ -456,10 +461,7 @@ int extract_samples(ssvp_ctx *ctx, const ssvp_params &p, int clip_id, int O, int
     a.sigma_rgb = p.sigma_rgb;
     a.sigma_xyz = p.sigma_xyz;
     a.sigma_f = p.sigma_f;
-    a.feat_out = feat;
-    a.col_out = col;
-    a.nsamp_out = nsamp;
-    a.plain_out = plain;
+    a.sets = ctx->l_sets;
     a.stat_counts = ctx->stat_counts;
     a.stat_sumw = ctx->stat_sumw;
     CK(ssvp::launch_gather(a, ctx->stream), "gather kernel (learned samples)");
@@ -557,8 +559,8 @@ void ssvp_destroy(ssvp_ctx *ctx) {
     if (ctx->geom) cudaFree(ctx->geom);
     if (ctx->staging) cudaFree(ctx->staging);
     if (ctx->d_shutter_log2) cudaFree(ctx->d_shutter_log2);
-    for (void *q : {(void *)ctx->mlp_buf, (void *)ctx->mlp_w1, (void *)ctx->l_feat, (void *)ctx->l_col,
-                    (void *)ctx->l_plain, (void *)ctx->l_loss, (void *)ctx->l_n, (void *)ctx->l_batch})
+    free_sets(ctx->l_sets);
+    for (void *q : {(void *)ctx->mlp_buf, (void *)ctx->mlp_w1, (void *)ctx->l_loss, (void *)ctx->l_batch})
         if (q) cudaFree(q);
     delete ctx;
 }
@@ -734,12 +736,11 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
             if ((rc = learned_scratch(ctx, npx)) != SSVP_OK) return rc;
             for (int oi = 0; oi < nout[i]; ++oi) {
                 const int O = fb[i] + oi;
-                if ((rc = extract_samples(ctx, p, clip_ids[i], O, cx0[i], cy0[i], cw[i], chh[i], ctx->l_feat, ctx->l_col,
-                                          ctx->l_n, ctx->l_plain)) != SSVP_OK)
+                if ((rc = extract_samples(ctx, p, clip_ids[i], O, cx0[i], cy0[i], cw[i], chh[i])) != SSVP_OK)
                     return rc;
                 ssvp::MlpArgs m{};
                 m.w = mlp_weights(ctx);
-                m.feat = ctx->l_feat; m.col = ctx->l_col; m.nsamp = ctx->l_n; m.plain = ctx->l_plain;
+                m.sets = ctx->l_sets;
                 m.n_px = (long long)npx;
                 m.O = O; m.W = c.p.W; m.H = c.p.H; m.x0 = cx0[i]; m.y0 = cy0[i]; m.cw = cw[i];
                 m.tau = p.conf_threshold;
@@ -1288,9 +1289,10 @@ int ssvp_learned_samples(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, 
     if (w == 0 || h == 0) { x0 = 0; y0 = 0; w = c.p.W; h = c.p.H; }
     if (x0 < 0 || y0 < 0 || x0 + w > c.p.W || y0 + h > c.p.H) return fail(ctx, SSVP_EINVAL, "crop outside the clip");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    if ((rc = extract_samples(ctx, p, clip_id, p.frame_begin, x0, y0, w, h, feat, col, nsamp, plain)) != SSVP_OK) return rc;
-    // the MLP kernels form features 12-14 on the fly; this caller gets them written out
-    CK(ssvp::launch_complete_features(feat, col, nsamp, plain, (long long)w * h, ctx->stream), "feature completion kernel");
+    if ((rc = learned_scratch(ctx, (size_t)w * h)) != SSVP_OK) return rc;
+    if ((rc = extract_samples(ctx, p, clip_id, p.frame_begin, x0, y0, w, h)) != SSVP_OK) return rc;
+    // the kernels keep the sets compact; this caller gets the full feature layout
+    CK(ssvp::launch_expand_sets(ctx->l_sets, feat, col, nsamp, plain, (long long)w * h, ctx->stream), "sample set expansion kernel");
     return SSVP_OK;
 }
 
@@ -1320,14 +1322,13 @@ int ssvp_mlp_grad(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, const i
         CK(cudaMalloc(&ctx->l_batch, n_pixels * sizeof(int32_t)), "cudaMalloc (batch)");
         ctx->l_batch_cap = n_pixels;
     }
-    if ((rc = extract_samples(ctx, *params, clip_id, O, 0, 0, c.p.W, c.p.H, ctx->l_feat, ctx->l_col, ctx->l_n,
-                              ctx->l_plain)) != SSVP_OK)
+    if ((rc = extract_samples(ctx, *params, clip_id, O, 0, 0, c.p.W, c.p.H)) != SSVP_OK)
         return rc;
     CK(cudaMemcpyAsync(ctx->l_batch, pixels, n_pixels * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream), "cudaMemcpyAsync");
     CK(cudaMemsetAsync(ctx->mlp.grad, 0, (ssvp::kMlpParams + 1) * sizeof(float), ctx->stream), "cudaMemsetAsync");
     ssvp::MlpArgs m{};
     m.w = mlp_weights(ctx);
-    m.feat = ctx->l_feat; m.col = ctx->l_col; m.nsamp = ctx->l_n; m.plain = ctx->l_plain;
+    m.sets = ctx->l_sets;
     m.n_px = (long long)npx;
     m.O = O; m.W = c.p.W; m.H = c.p.H; m.x0 = 0; m.y0 = 0; m.cw = c.p.W;
     m.batch = ctx->l_batch;
@@ -1393,8 +1394,7 @@ int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, co
         const int O = (int)(rng.next() % (uint64_t)c.p.F);
         const uint64_t npx = (uint64_t)c.p.W * c.p.H;
         for (auto &b : batch) b = (int32_t)(rng.next() % npx);
-        if ((rc = extract_samples(ctx, *params, clip_ids[ci], O, 0, 0, c.p.W, c.p.H, ctx->l_feat, ctx->l_col, ctx->l_n,
-                                  ctx->l_plain)) != SSVP_OK)
+        if ((rc = extract_samples(ctx, *params, clip_ids[ci], O, 0, 0, c.p.W, c.p.H)) != SSVP_OK)
             return rc;
         // pageable source: the copy is staged before the call returns, so batch may be rewritten
         CK(cudaMemcpyAsync(ctx->l_batch, batch.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream),
@@ -1402,7 +1402,7 @@ int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, co
         CK(cudaMemsetAsync(ctx->mlp.grad, 0, (ssvp::kMlpParams + 1) * sizeof(float), ctx->stream), "cudaMemsetAsync");
         ssvp::MlpArgs m{};
         m.w = mlp_weights(ctx);
-        m.feat = ctx->l_feat; m.col = ctx->l_col; m.nsamp = ctx->l_n; m.plain = ctx->l_plain;
+        m.sets = ctx->l_sets;
         m.n_px = (long long)npx;
         m.O = O; m.W = c.p.W; m.H = c.p.H; m.x0 = 0; m.y0 = 0; m.cw = c.p.W;
         m.batch = ctx->l_batch;

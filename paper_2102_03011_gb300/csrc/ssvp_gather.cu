@@ -45,29 +45,22 @@ constexpr int kTileX = 32, kTileY = SSVP_TILE_Y, kThreads = kTileX * kTileY;
 constexpr int kMaxSamples = 64;  // learned filter: capped sample set
 constexpr float kLn2 = 0.6931471805599453f;
 
-// Features of one accepted sample for the learned filter (16 BF16 values) and its colour;
-// feature 11 (the size of the whole set) is filled in once the pixel's gather is complete and
-// features 12-14 (the colour against the plain estimate) by their readers.
-__device__ __forceinline__ void store_sample(const GatherArgs &a, long long crop_idx, int slot, float3 c, float er,
-                                             float eg, float eb, float dist_r, float dj_t, float dz_r, float logw) {
-    const float f[16] = {c.x, c.y, c.z, er, eg, eb, dist_r, dj_t, dz_r, logw, 1.0f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    unsigned int packed[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-        packed[i] = *reinterpret_cast<unsigned int *>(&b2);
-    }
-    uint4 *dst = reinterpret_cast<uint4 *>(a.feat_out + (crop_idx * kMaxSamples + slot) * 16);
-    dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-    dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-    float *cd = a.col_out + (crop_idx * kMaxSamples + slot) * 3;
-    cd[0] = c.x;
-    cd[1] = c.y;
-    cd[2] = c.z;
+// One accepted sample of the learned filter's capped set, compactly: its FP32 colour with the
+// BF16 pair (dist / r, (J - O) / T) in one 16-byte record and the pair (depth residual / r,
+// log w) in one word; the other features are rebuilt by the MLP kernels.
+__device__ __forceinline__ unsigned bf16_pair(float lo, float hi) {
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned *>(&b2);
+}
+__device__ __forceinline__ void store_sample(const GatherArgs &a, long long crop_idx, int slot, float3 c, float dist_r,
+                                             float dj_t, float dz_r, float logw) {
+    const long long i = crop_idx * kMaxSamples + slot;
+    a.sets.col[i] = make_float4(c.x, c.y, c.z, __uint_as_float(bf16_pair(dist_r, dj_t)));
+    a.sets.f89[i] = bf16_pair(dz_r, logw);
 }
 
 // LEARN: visit the frames in canonical order (O, O-1, O+1, ...) and store the features of the
-// first kMaxSamples accepted samples (learned filter); the Eq. 3/4 result goes to a.plain_out.
+// first kMaxSamples accepted samples (learned filter); the Eq. 3/4 result goes to a.sets.plain.
 // ACCB: accepted samples taken per iteration of the filter loop (1, or 2 in packed FP32x2; two
 // pays off where registers allow it: the plain per-launch kernel, not the batched or learned one)
 template <int K, int CFMT, bool DEBUG, bool LEARN = false, int ACCB = 1>
@@ -242,20 +235,17 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                         const float w0 = weighted ? ex2(-e0) : 1.0f;
                         const float w1 = ok[1] ? (weighted ? ex2(-e1) : 1.0f) : 0.0f;  // ok[0] holds in the loop
                         if (LEARN) {
-                            float er0, er1, eg0, eg1, eb0, eb1, dd0, dd1, dz0, dz1;
-                            f2_unpack(er, er0, er1);
-                            f2_unpack(eg, eg0, eg1);
-                            f2_unpack(eb, eb0, eb1);
+                            float dd0, dd1, dz0, dz1;
                             f2_unpack(d2, dd0, dd1);
                             f2_unpack(dz, dz0, dz1);
                             if (n_feat < kMaxSamples) {
-                                store_sample(a, crop_idx, n_feat, cq[0], er0, eg0, eb0, sqrtf(dd0) * inv_r,
-                                             (float)(j - Tw) * inv_T, dz0 * inv_r, -e0 * kLn2);
+                                store_sample(a, crop_idx, n_feat, cq[0], sqrtf(dd0) * inv_r, (float)(j - Tw) * inv_T,
+                                             dz0 * inv_r, -e0 * kLn2);
                                 ++n_feat;
                             }
                             if (ok[1] && n_feat < kMaxSamples) {
-                                store_sample(a, crop_idx, n_feat, cq[1], er1, eg1, eb1, sqrtf(dd1) * inv_r,
-                                             (float)(j - Tw) * inv_T, dz1 * inv_r, -e1 * kLn2);
+                                store_sample(a, crop_idx, n_feat, cq[1], sqrtf(dd1) * inv_r, (float)(j - Tw) * inv_T,
+                                             dz1 * inv_r, -e1 * kLn2);
                                 ++n_feat;
                             }
                         }
@@ -278,8 +268,8 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                         float w = 1.0f;
                         if (weighted) w = ex2(-e);
                         if (LEARN && ok[t] && n_feat < kMaxSamples) {
-                            store_sample(a, crop_idx, n_feat, cq[t], er, eg, eb, sqrtf(d2) * inv_r,
-                                         (float)(j - Tw) * inv_T, dz * inv_r, -e * kLn2);
+                            store_sample(a, crop_idx, n_feat, cq[t], sqrtf(d2) * inv_r, (float)(j - Tw) * inv_T,
+                                         dz * inv_r, -e * kLn2);
                             ++n_feat;
                         }
                         if (ok[t]) {
@@ -338,8 +328,8 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                         float w = 1.0f;
                         if (weighted) w = ex2(-e);
                         if (LEARN && n_feat < kMaxSamples) {
-                            store_sample(a, crop_idx, n_feat, c, er, eg, eb, sqrtf(d2) * inv_r, (float)(j - Tw) * inv_T,
-                                         dz * inv_r, -e * kLn2);
+                            store_sample(a, crop_idx, n_feat, c, sqrtf(d2) * inv_r, (float)(j - Tw) * inv_T, dz * inv_r,
+                                         -e * kLn2);
                             ++n_feat;
                         }
                         acc_r = fmaf(w, er, acc_r);
@@ -362,18 +352,15 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
             o_g = fmaf(acc_g, inv, o_g);
             o_b = fmaf(acc_b, inv, o_b);
         }
-        float *o = LEARN ? a.plain_out + crop_idx * 3 : P.out + (((long long)O * P.H + v) * P.W + u) * 3;
+        float *o = LEARN ? a.sets.plain + crop_idx * 3 : P.out + (((long long)O * P.H + v) * P.W + u) * 3;
         o[0] = o_r;
         o[1] = o_g;
         o[2] = o_b;
         if (LEARN) {
-            a.nsamp_out[crop_idx] = n_feat;
-            // feature 11: size of the whole gathered set (what the plain fallback averages) / 64;
-            // features 12-14 (colour minus this plain result) are formed where they are read, from
-            // the stored colours and plain_out
-            const __nv_bfloat16 nb = __float2bfloat16_rn((float)n_acc * (1.0f / 64.0f));
-            const unsigned short nbits = *reinterpret_cast<const unsigned short *>(&nb);
-            for (int s = 0; s < n_feat; ++s) a.feat_out[(crop_idx * kMaxSamples + s) * 16 + 11] = nbits;
+            // per pixel: the count kept, c_ref and the size of the whole set / 64 (what the plain
+            // fallback averages)
+            a.sets.n[crop_idx] = n_feat;
+            a.sets.info[crop_idx] = make_float4(cref.x, cref.y, cref.z, (float)n_acc * (1.0f / 64.0f));
         }
         if (DEBUG && a.pixel_stats) {
             int32_t *ps = a.pixel_stats + crop_idx * 3;
@@ -545,7 +532,7 @@ cudaError_t launch_k(const GatherArgs &a, cudaStream_t s) {
     dim3 grid((a.cw + kTileX - 1) / kTileX, (a.ch + kTileY - 1) / kTileY, a.n_out);
     size_t smem = sizeof(float4) * kSlotVec * (size_t)a.n_slots;
     const bool dbg = a.membership || a.pixel_stats;
-    if (a.feat_out) gather_kernel<K, CFMT, false, true><<<grid, kThreads, smem, s>>>(a);
+    if (a.sets.col) gather_kernel<K, CFMT, false, true><<<grid, kThreads, smem, s>>>(a);
     else if (dbg) gather_kernel<K, CFMT, true><<<grid, kThreads, smem, s>>>(a);
     else gather_kernel<K, CFMT, false><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();

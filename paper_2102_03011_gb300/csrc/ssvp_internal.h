@@ -46,6 +46,18 @@ struct __align__(16) PairGeom {
 };
 static_assert(sizeof(PairGeom) == 128, "PairGeom layout");
 
+// Capped sample sets of the learned filter, per crop pixel up to 64 samples in canonical order,
+// stored compactly; the MLP kernels rebuild the 16 BF16 features of a sample from them:
+// [colour (3), colour - c_ref (3), dist / r, (J - O) / T, depth residual / r, log w, 1,
+//  |S(p)| / 64, colour - plain (3), 0].
+struct SampleSets {
+    float4 *col;     // pixel x 64: FP32 colour (x, y, z); w holds the BF16 pair (dist / r, (J - O) / T)
+    unsigned *f89;   // pixel x 64: the BF16 pair (depth residual / r, log w)
+    float4 *info;    // pixel: c_ref (x, y, z) and |S(p)| / 64
+    int32_t *n;      // pixel: samples kept (<= 64)
+    float *plain;    // pixel x 3: the plain Eq. 3/4 result over the whole set
+};
+
 // Arguments of one gather launch (one clip, a range of output frames).
 struct GatherArgs {
     Planes clip;
@@ -62,12 +74,8 @@ struct GatherArgs {
     int lens_n;               // seed points
     int cap;                  // box cap per axis (odd)
     float lens_xy[128];       // seed lens points (x, y) on the unit-radius disc, scaled by A in the kernel
-    // learned filter: capped sample features (crop pixel x 64 x 16 BF16), colours (x 64 x 3),
-    // counts and the plain Eq. 3/4 result per crop pixel
-    unsigned short *feat_out;
-    float *col_out;
-    int32_t *nsamp_out;
-    float *plain_out;
+    // learned filter: the capped sample sets of the crop (set when extracting them)
+    SampleSets sets;
     // per-frame weights in log2 units, subtracted from the exponent of every sample from J:
     // frame_log2w[J] (Eq. 5, indexed by input frame) and slot_log2w[j] (Eq. 10, by window slot)
     const float *frame_log2w;
@@ -123,10 +131,7 @@ struct MlpState {             // training state on the device
 
 struct MlpArgs {
     MlpWeights w;
-    const unsigned short *feat;   // per crop pixel 64 x 16 BF16
-    const float *col;             // per crop pixel 64 x 3
-    const int32_t *nsamp;         // per crop pixel
-    const float *plain;           // per crop pixel 3 (Eq. 3/4 result)
+    SampleSets sets;              // the crop's capped sample sets (read only)
     long long n_px;               // crop pixels
     int O, W, H, x0, y0, cw;      // output frame and crop (pixel px = (x0 + px % cw, y0 + px / cw))
     float tau;                    // confidence threshold
@@ -143,8 +148,9 @@ cudaError_t launch_mlp_infer(const MlpArgs &m, cudaStream_t s);
 cudaError_t launch_mlp_train(const MlpArgs &m, cudaStream_t s);
 cudaError_t launch_adam(const MlpState &st, float lr, int step, cudaStream_t s);
 cudaError_t launch_mlp_refresh(const MlpState &st, cudaStream_t s);
-cudaError_t launch_complete_features(unsigned short *feat, const float *col, const int32_t *nsamp, const float *plain,
-                                     long long n_px, cudaStream_t s);
+// expand compact sample sets into 64 x 16 BF16 features, 64 x 3 colours, counts and plain results
+cudaError_t launch_expand_sets(const SampleSets &sets, unsigned short *feat, float *col, int32_t *nsamp, float *plain,
+                               long long n_px, cudaStream_t s);
 
 cudaError_t launch_pack(const float *rgb, const float *depth, int W, int H, int nF, const Planes &dst, int frame0,
                         cudaStream_t s);

@@ -48,36 +48,47 @@ __device__ __forceinline__ unsigned short bf16_bits(float x) {
     return *reinterpret_cast<const unsigned short *>(&b);
 }
 
-// Features 12-15 of one sample as BF16 words: (c0 - p0, c1 - p1) for word 6, (c2 - p2, 0) for
-// word 7 - the sample's colour against the pixel's plain Eq. 4 result.
-__device__ __forceinline__ unsigned resid_word(const float *c, const float *pl, int word) {
-    return word == 6 ? pack2(bf16_bits(__ldg(c) - pl[0]), bf16_bits(__ldg(c + 1) - pl[1]))
-                     : pack2(bf16_bits(__ldg(c + 2) - pl[2]), 0);
+// Feature word w (features 2w, 2w + 1 as a BF16 pair, the lower index in the low half) of one
+// sample, rebuilt from its compact record (colour c, stored pairs c.w and f89) and the pixel's
+// info (c_ref, |S(p)| / 64) and plain result:
+//   w0 (c.x, c.y)  w1 (c.z, c.x - cref.x)  w2 (c.y - cref.y, c.z - cref.z)  w3 (dist / r, dJ / T)
+//   w4 (dz / r, log w)  w5 (1, |S| / 64)  w6 (c.x - p.x, c.y - p.y)  w7 (c.z - p.z, 0)
+// The differences are taken in FP32 before rounding, as the features are defined.
+__device__ __forceinline__ unsigned feat_word(int w, float4 c, unsigned f89, float4 info, const float (&pl)[3]) {
+    switch (w) {
+    case 0: return pack2(bf16_bits(c.x), bf16_bits(c.y));
+    case 1: return pack2(bf16_bits(c.z), bf16_bits(c.x - info.x));
+    case 2: return pack2(bf16_bits(c.y - info.y), bf16_bits(c.z - info.z));
+    case 3: return __float_as_uint(c.w);
+    case 4: return f89;
+    case 5: return pack2(0x3f80, bf16_bits(info.w));  // BF16 1.0
+    case 6: return pack2(bf16_bits(c.x - pl[0]), bf16_bits(c.y - pl[1]));
+    default: return pack2(bf16_bits(c.z - pl[2]), 0);
+    }
 }
 
 // Feature i of sample s as BF16 bits (the B operand of the dW1 product)
-__device__ __forceinline__ unsigned short feature_bits(const unsigned short *fh, const float *col, const float *pl,
-                                                       int s, int i) {
-    if (i < 12) return fh[s * kF + i];
-    if (i == 15) return 0;
-    return bf16_bits(__ldg(col + s * 3 + (i - 12)) - pl[i - 12]);
+__device__ __forceinline__ unsigned short feature_bits(const SampleSets &S, long long px, int s, int i, float4 info,
+                                                       const float (&pl)[3]) {
+    const long long k = px * kS + s;
+    const unsigned w = feat_word(i >> 1, __ldg(S.col + k), i >> 1 == 4 ? __ldg(S.f89 + k) : 0u, info, pl);
+    return (unsigned short)((i & 1) ? w >> 16 : w & 0xffffu);
 }
 
-// A fragments (rows = samples) of the four 16-sample tiles; rows >= n are zero.  col and pl: the
-// pixel's sample colours and plain result, from which words 6 and 7 (features 12-15) are formed.
-__device__ __forceinline__ void load_features(const unsigned *fw, const float *col, const float *pl, int n, int g,
-                                              int t, unsigned (&a)[4][4]) {
+// A fragments (rows = samples) of the four 16-sample tiles of pixel px; rows >= n are zero.  The
+// lane's words are t and 4 + t of rows 16 mt + g and + 8.
+__device__ __forceinline__ void load_features(const SampleSets &S, long long px, int n, int g, int t, float4 info,
+                                              const float (&pl)[3], unsigned (&a)[4][4]) {
 #pragma unroll
     for (int mt = 0; mt < 4; ++mt) {
-        const int r0 = 16 * mt + g, r1 = r0 + 8;
-        a[mt][0] = r0 < n ? __ldg(fw + r0 * 8 + t) : 0u;
-        a[mt][1] = r1 < n ? __ldg(fw + r1 * 8 + t) : 0u;
-        if (t < 2) {
-            a[mt][2] = r0 < n ? __ldg(fw + r0 * 8 + 4 + t) : 0u;
-            a[mt][3] = r1 < n ? __ldg(fw + r1 * 8 + 4 + t) : 0u;
-        } else {
-            a[mt][2] = r0 < n ? resid_word(col + r0 * 3, pl, 4 + t) : 0u;
-            a[mt][3] = r1 < n ? resid_word(col + r1 * 3, pl, 4 + t) : 0u;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = 16 * mt + g + 8 * h;
+            const long long k = px * kS + (r < n ? r : 0);
+            const float4 c = r < n ? __ldg(S.col + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const unsigned f89 = (t == 0 && r < n) ? __ldg(S.f89 + k) : 0u;
+            a[mt][h] = r < n ? feat_word(t, c, f89, info, pl) : 0u;
+            a[mt][2 + h] = r < n ? feat_word(4 + t, c, f89, info, pl) : 0u;
         }
     }
 }
@@ -146,14 +157,13 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_infer_kernel(const MlpArgs m)
     const float b20 = __ldg(m.w.b2), b21 = __ldg(m.w.b2 + 1);
     const long long nwarps = (long long)gridDim.x * kWarps;
     for (long long px = blockIdx.x * (long long)kWarps + (threadIdx.x >> 5); px < m.n_px; px += nwarps) {
-        const int n = m.nsamp[px];
-        const float *pl = m.plain + 3 * px;
+        const int n = m.sets.n[px];
+        const float *pl = m.sets.plain + 3 * px;
         float o0 = pl[0], o1 = pl[1], o2 = pl[2], conf = 0.0f;
         if (n > 0) {
             unsigned a[4][4];
             const float plv[3] = {o0, o1, o2};
-            load_features(reinterpret_cast<const unsigned *>(m.feat) + px * (kS * kF / 2), m.col + px * kS * 3, plv, n,
-                          g, t, a);
+            load_features(m.sets, px, n, g, t, __ldg(m.sets.info + px), plv, a);
             PixelForward pf;
             forward(a, bw, m.w, t, pf);
             float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
@@ -165,11 +175,11 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_infer_kernel(const MlpArgs m)
                         const float zw = (t == 0 ? pf.zw[mt][0] : pf.zw[mt][1]) + b20;
                         const float zc = (t == 0 ? pf.zc[mt][0] : pf.zc[mt][1]) + b21;
                         const float w = softplusf(zw);
-                        const float *c = m.col + (px * kS + s) * 3;
+                        const float4 c = __ldg(m.sets.col + px * kS + s);
                         sw += w;
-                        sr = fmaf(w, c[0], sr);
-                        sg = fmaf(w, c[1], sg);
-                        sb = fmaf(w, c[2], sb);
+                        sr = fmaf(w, c.x, sr);
+                        sg = fmaf(w, c.y, sg);
+                        sb = fmaf(w, c.z, sb);
                         sc += sigmoidf(zc);
                     }
                 }
@@ -218,14 +228,12 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
     const long long nwarps = (long long)gridDim.x * kWarps;
     for (long long bi = blockIdx.x * (long long)kWarps + wid; bi < m.n_batch; bi += nwarps) {
         const long long px = m.batch[bi];
-        const int n = m.nsamp[px];
+        const int n = m.sets.n[px];
         if (n <= 0) continue;  // warp-uniform
-        const unsigned *fw = reinterpret_cast<const unsigned *>(m.feat) + px * (kS * kF / 2);
-        const unsigned short *fh = m.feat + px * (kS * kF);
-        const float *colp = m.col + px * kS * 3;
-        const float plv[3] = {m.plain[3 * px], m.plain[3 * px + 1], m.plain[3 * px + 2]};
+        const float plv[3] = {m.sets.plain[3 * px], m.sets.plain[3 * px + 1], m.sets.plain[3 * px + 2]};
+        const float4 info = __ldg(m.sets.info + px);
         unsigned a[4][4];
-        load_features(fw, colp, plv, n, g, t, a);
+        load_features(m.sets, px, n, g, t, info, plv, a);
         PixelForward pf;
         forward(a, bw, m.w, t, pf);
         // per-sample weights, outputs and the pixel's loss
@@ -240,10 +248,10 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
             valid[mt] = t < 2 && s < n;
             w[mt] = valid[mt] ? softplusf(zw[mt]) : 0.f;
             cf[mt] = valid[mt] ? sigmoidf(zc[mt]) : 0.f;
-            const float *c = m.col + (px * kS + (valid[mt] ? s : 0)) * 3;
-            cr[mt][0] = valid[mt] ? c[0] : 0.f;
-            cr[mt][1] = valid[mt] ? c[1] : 0.f;
-            cr[mt][2] = valid[mt] ? c[2] : 0.f;
+            const float4 c = __ldg(m.sets.col + px * kS + (valid[mt] ? s : 0));
+            cr[mt][0] = valid[mt] ? c.x : 0.f;
+            cr[mt][1] = valid[mt] ? c.y : 0.f;
+            cr[mt][2] = valid[mt] ? c.z : 0.f;
             sw += w[mt];
             sr = fmaf(w[mt], cr[mt][0], sr);
             sg = fmaf(w[mt], cr[mt][1], sg);
@@ -260,7 +268,7 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
         const float conf = sc / (float)n;
         const long long u = px % m.cw + m.x0, v = px / m.cw + m.y0;
         const float *y = m.clean + (((long long)m.O * m.H + v) * m.W + u) * 3;
-        const float *pl = m.plain + 3 * px;
+        const float *pl = plv;
         float el = 0.f, ep = 0.f, dO[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -352,8 +360,10 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
                 const int i = 8 * nt + g;
-                bf[nt][0] = pack2(s0 < n ? feature_bits(fh, colp, plv, s0, i) : 0, s1 < n ? feature_bits(fh, colp, plv, s1, i) : 0);
-                bf[nt][1] = pack2(s8 < n ? feature_bits(fh, colp, plv, s8, i) : 0, s9 < n ? feature_bits(fh, colp, plv, s9, i) : 0);
+                bf[nt][0] = pack2(s0 < n ? feature_bits(m.sets, px, s0, i, info, plv) : 0,
+                                  s1 < n ? feature_bits(m.sets, px, s1, i, info, plv) : 0);
+                bf[nt][1] = pack2(s8 < n ? feature_bits(m.sets, px, s8, i, info, plv) : 0,
+                                  s9 < n ? feature_bits(m.sets, px, s9, i, info, plv) : 0);
             }
 #pragma unroll
             for (int mt = 0; mt < 4; ++mt) {
@@ -392,20 +402,31 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
 }
 
 // ---------------------------------------------------------------- Adam on the FP32 master weights
-// Features 12-14 of every stored sample, written into the feature buffer (for callers that read
-// the sample sets themselves; the MLP kernels form them on the fly).
-__global__ void complete_features_kernel(unsigned short *feat, const float *col, const int32_t *nsamp,
-                                         const float *plain, long long n_px) {
+// Compact sample sets expanded to the full layout (64 x 16 BF16 features, 64 x 3 colours per
+// pixel), for callers that read the sets themselves.
+__global__ void expand_sets_kernel(const SampleSets S, unsigned short *feat, float *col, int32_t *nsamp, float *plain,
+                                   long long n_px) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n_px * kS) return;
     const long long px = i / kS;
-    const int s = (int)(i - px * kS);
-    if (s >= nsamp[px]) return;
-    const float *c = col + i * 3, *pl = plain + 3 * px;
-    unsigned short *f = feat + i * kF;
-    f[12] = bf16_bits(c[0] - pl[0]);
-    f[13] = bf16_bits(c[1] - pl[1]);
-    f[14] = bf16_bits(c[2] - pl[2]);
+    const int s = (int)(i - px * kS), n = S.n[px];
+    const float pl[3] = {S.plain[3 * px], S.plain[3 * px + 1], S.plain[3 * px + 2]};
+    if (s == 0) {
+        nsamp[px] = n;
+        for (int c = 0; c < 3; ++c) plain[3 * px + c] = pl[c];
+    }
+    unsigned *f = reinterpret_cast<unsigned *>(feat + i * kF);
+    if (s >= n) {
+        for (int w = 0; w < 8; ++w) f[w] = 0u;
+        col[3 * i] = col[3 * i + 1] = col[3 * i + 2] = 0.0f;
+        return;
+    }
+    const float4 c = S.col[i], info = S.info[px];
+    const unsigned f89 = S.f89[i];
+    for (int w = 0; w < 8; ++w) f[w] = feat_word(w, c, f89, info, pl);
+    col[3 * i] = c.x;
+    col[3 * i + 1] = c.y;
+    col[3 * i + 2] = c.z;
 }
 
 __global__ void adam_kernel(MlpState st, float lr, float b1, float b2, float eps, int step) {
@@ -455,11 +476,11 @@ cudaError_t launch_mlp_refresh(const MlpState &st, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_complete_features(unsigned short *feat, const float *col, const int32_t *nsamp, const float *plain,
-                                     long long n_px, cudaStream_t s) {
+cudaError_t launch_expand_sets(const SampleSets &sets, unsigned short *feat, float *col, int32_t *nsamp, float *plain,
+                               long long n_px, cudaStream_t s) {
     const long long n = n_px * kS;
     if (n == 0) return cudaSuccess;
-    complete_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(feat, col, nsamp, plain, n_px);
+    expand_sets_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sets, feat, col, nsamp, plain, n_px);
     return cudaGetLastError();
 }
 
