@@ -68,6 +68,22 @@ def test_paper_parameters_are_the_defaults():
     p = oracle.Params()
     assert p.sigma_rgb == pytest.approx(g["denoise_sigma_rgb_0_255"]["value"] / 255.0)
     assert p.sigma_f == g["denoise_sigma_f"]["value"]
+    # the frustum gather (Eq. 1-2) defaults
+    assert (p.frustum_l, p.near_plane, p.far_plane) == (g["frustum_l"]["value"], g["near"]["value"], g["far"]["value"])
+
+
+def test_paper_parameters_of_the_benchmark_workloads():
+    """The per-application sigmas the paper prints (on the 0-255 colour scale) are the ones the
+    deblurring, super-resolution and inpainting workloads run with."""
+    import bench
+    g = json.load(open(os.path.join(GOLDEN, "paper_parameters.json")))
+    assert bench.DEBLUR_SIGMA_RGB == pytest.approx(g["deblur_sigma_rgb_0_255"]["value"] / 255.0)
+    assert bench.DEBLUR_SIGMA_F == g["deblur_sigma_f"]["value"]
+    assert bench.INPAINT_SIGMA_RGB == pytest.approx(g["inpaint_sigma_rgb_0_255"]["value"] / 255.0)
+    assert bench.FRUSTUM_L == g["frustum_l"]["value"]
+    src = open(bench.__file__).read()
+    assert "50.0 / 255.0" in src  # super-resolution sigma_rgb, set where the workload runs
+    assert g["superres_sigma_rgb_0_255"]["value"] == 50
 
 
 # ------------------------------------------------------------------ A1 against the generator's geometry
