@@ -905,8 +905,10 @@ long long oc_bruteforce(const oc_clip *c, const oc_params *p, int O, int u, int 
  * with z'_J the depth of the reference point in camera J.  Network: h = ReLU(W1 f + b1) (64),
  * (z_w, z_c) = W2 h + b2; w_s = softplus(z_w); conf = mean_s sigmoid(z_c);
  * learned output = sum w_s c_s / sum w_s; final output = learned if conf >= tau else the plain
- * Eq. 4 result.  With round_bf16 = 1 the features and W1, W2 are rounded to BF16 (the tensor-core
- * input precision) and b1, b2 to FP32 before use, as on the GPU.
+ * Eq. 4 result.  With round_bf16 = 1 the features, W1, W2 and the hidden activations (after the
+ * ReLU) are rounded to BF16 -- the input precision of the tensor-core products of both layers --
+ * and b1, b2 to FP32 before use, as on the GPU.  The backward pass treats that rounding of h as
+ * the identity (the gradient of W2 uses the rounded h).
  */
 #define OC_MAXS 64
 #define OC_NF 16
@@ -1019,7 +1021,7 @@ double oc_mlp_pixel(const double *feat, const double *col, int n, const double *
         for (int j = 0; j < OC_NH; ++j) {
             double a = round_bf16 ? (double)(float)b1[j] : b1[j];
             for (int i = 0; i < OC_NF; ++i) a += (round_bf16 ? bf16_round(W1[j * OC_NF + i]) : W1[j * OC_NF + i]) * f[i];
-            hh[j] = a > 0 ? a : 0.0;
+            hh[j] = a > 0 ? (round_bf16 ? bf16_round(a) : a) : 0.0;
         }
         for (int o = 0; o < 2; ++o) {
             double a = round_bf16 ? (double)(float)b2[o] : b2[o];

@@ -62,7 +62,7 @@ __device__ __forceinline__ void store_sample(const GatherArgs &a, long long crop
 // LEARN: visit the frames in canonical order (O, O-1, O+1, ...) and store the features of the
 // first kMaxSamples accepted samples (learned filter); the Eq. 3/4 result goes to a.sets.plain.
 // ACCB: accepted samples taken per iteration of the filter loop (1, or 2 in packed FP32x2; two
-// pays off where registers allow it: the plain per-launch kernel, not the batched or learned one)
+// pays off in the per-launch kernels, plain and learned, not in the batched one)
 template <int K, int CFMT, bool DEBUG, bool LEARN = false, int ACCB = 1>
 __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &P, const int O, const int u0,
                                              const int v0, const int u, const int v, const bool active,
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const G
     const long long crop_idx = (long long)(v - a.y0) * a.cw + (u - a.x0);
     int n_acc = 0, n_exam = 0;
     float acc_w = 0.0f;
-    gather_pixel<K, CFMT, DEBUG, LEARN, LEARN ? 1 : 2>(a, a.clip, O, u0, v0, u, v, active, crop_idx, sgeom, a.n_slots,
+    gather_pixel<K, CFMT, DEBUG, LEARN, 2>(a, a.clip, O, u0, v0, u, v, active, crop_idx, sgeom, a.n_slots,
                                                        s_const[0], s_const[1], s_const[2], s_const[3] != 0.0f, n_acc,
                                                        n_exam, acc_w);
 

@@ -1,13 +1,15 @@
 // ssvp_mlp.cu - the learned per-sample weighting: a 16 -> 64 -> 2 MLP over each pixel's capped
 // sample set (up to 64 samples), on the BF16 tensor cores with FP32 accumulation.
 //
-// One warp per pixel.  Layer 1 is H = F W1^T + b1 with F the pixel's 64 x 16 feature block (four
-// 16-row tiles) and W1^T held in B fragments for all eight 8-column tiles of the 64 hidden units:
-// 32 mma.sync.m16n8k16 (bf16 x bf16 -> f32) per pixel, b1 folded into the accumulator.  ReLU and
-// the 64 -> 2 head run in FP32 on the fragments; (z_w, z_c) per sample become w = softplus(z_w)
-// and conf = mean sigmoid(z_c); the output is sum w c / sum w, or the plain Eq. 3/4 result when
-// conf < tau.  Training recomputes H, forms dH in shared memory (BF16) and accumulates
-// dW1 = dH^T F as a second MMA over the sample dimension.
+// One warp per pixel, 16 samples (one MMA row tile) at a time.  Layer 1 is H = F W1^T + b1 with
+// F the tile's 16 x 16 feature block and W1^T held in B fragments for all eight 8-column tiles
+// of the 64 hidden units (eight mma.sync.m16n8k16, bf16 x bf16 -> f32, b1 in the accumulator).
+// ReLU and the rounding to BF16 happen in one conversion, and the accumulator fragments of two
+// neighbouring hidden tiles are exactly the A fragment of the next product, so layer 2 (64 -> 2,
+// padded to 8 output columns) is four more MMAs with b2 in the accumulator.  (z_w, z_c) per
+// sample become w = softplus(z_w) and conf = mean sigmoid(z_c); the output is sum w c / sum w,
+// or the plain Eq. 3/4 result when conf < tau.  Training recomputes H, forms dH in shared memory
+// (BF16) and accumulates dW1 = dH^T F as a second MMA over the sample dimension.
 #include <cuda_bf16.h>
 
 #include "ssvp_internal.h"
@@ -28,6 +30,15 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]), "f"(c[2]), "f"(c[3]));
 }
 
+// the same with the accumulator's initial value as one quad (a 16-byte shared-memory load)
+__device__ __forceinline__ void mma_bf16_q(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1, float4 c) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%11,%12,%13};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c.x), "f"(c.y), "f"(c.z), "f"(c.w));
+}
+
 // keep the kernels' copies of the master weights: W1 as BF16, W2 rounded to BF16 values
 __device__ __forceinline__ void refresh_one(const MlpState &st, int i, float p) {
     if (i < kMlpB1) {
@@ -39,7 +50,8 @@ __device__ __forceinline__ void refresh_one(const MlpState &st, int i, float p) 
 }
 
 __device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + log1pf(__expf(-fabsf(x))); }
-__device__ __forceinline__ float sigmoidf(float x) { return 1.0f / (1.0f + __expf(-x)); }
+// sigmoid with the fast reciprocal: it only enters the confidence mean and its derivative
+__device__ __forceinline__ float sigmoidf(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 
 __device__ __forceinline__ unsigned pack2(unsigned short lo, unsigned short hi) { return (unsigned)lo | ((unsigned)hi << 16); }
 
@@ -75,63 +87,123 @@ __device__ __forceinline__ unsigned short feature_bits(const SampleSets &S, long
     return (unsigned short)((i & 1) ? w >> 16 : w & 0xffffu);
 }
 
-// A fragments (rows = samples) of the four 16-sample tiles of pixel px; rows >= n are zero.  The
-// lane's words are t and 4 + t of rows 16 mt + g and + 8.
+// The A fragments hold the features in a different order from the logical one above, chosen so
+// that lane t of a quad builds both of its words (t and 4 + t) with the same few operations:
+//   word t < 3:   (c_t, c_t - cref_t)            word 3: (dist / r, dJ / T) as stored
+//   word 4 + t:   (c_t - plain_t, x_t), x = (1, |S| / 64, 0)   word 7: (dz / r, log w) as stored
+// slot_feature(word, half) is the logical feature in that half of that word; W1's B fragments
+// are gathered in the same order, so F W1^T is unchanged.
+__device__ __forceinline__ int slot_feature(int word, int half) {
+    const int t = word & 3;
+    if (word < 4) return t < 3 ? t + 3 * half : 6 + half;
+    if (t == 3) return 8 + half;
+    return half == 0 ? 12 + t : (t == 2 ? 15 : 10 + t);
+}
+
+__device__ __forceinline__ unsigned bf16x2(float lo, float hi) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned *>(&b);
+}
+
+__device__ __forceinline__ __nv_bfloat162 u32_as_bf162(unsigned u) { return *reinterpret_cast<const __nv_bfloat162 *>(&u); }
+
+// ReLU, then round to BF16 (the A operand of layer 2): one conversion for a pair
+__device__ __forceinline__ unsigned relu_bf16x2(float lo, float hi) {
+    unsigned r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// Per-lane constants of a pixel for the feature words: cref_t, plain_t, x_t
+struct LaneFeat {
+    float cr, pt, xt;
+};
+__device__ __forceinline__ LaneFeat lane_feat(int t, float4 info, const float (&pl)[3]) {
+    LaneFeat f;
+    f.cr = t == 0 ? info.x : (t == 1 ? info.y : info.z);
+    f.pt = t == 0 ? pl[0] : (t == 1 ? pl[1] : pl[2]);
+    f.xt = t == 0 ? 1.0f : (t == 1 ? info.w : 0.0f);
+    return f;
+}
+
+// Words t (lo) and 4 + t (hi) of one sample (the differences in FP32, then rounded)
+__device__ __forceinline__ void sample_words(int t, float4 c, unsigned f89, const LaneFeat &f, unsigned &lo,
+                                             unsigned &hi) {
+    const float ct = t == 0 ? c.x : (t == 1 ? c.y : c.z);
+    lo = t == 3 ? __float_as_uint(c.w) : bf16x2(ct, ct - f.cr);
+    hi = t == 3 ? f89 : bf16x2(ct - f.pt, f.xt);
+}
+
+// The two rows (g, g + 8) of 16-sample tile mt of pixel px; rows >= n read nothing
+struct TileRows {
+    float4 c[2];
+    unsigned f89[2];
+};
+__device__ __forceinline__ void load_rows(const SampleSets &S, long long px, int mt, int n, int g, int t,
+                                          TileRows &r) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int s = 16 * mt + g + 8 * h;
+        const long long k = px * kS + s;
+        r.c[h] = s < n ? __ldg(S.col + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        r.f89[h] = (t == 3 && s < n) ? __ldg(S.f89 + k) : 0u;
+    }
+}
+
+// A fragment of a tile: words t (a0 row g, a1 row g + 8) and 4 + t (a2, a3); rows >= n are zero
+__device__ __forceinline__ void tile_fragment(const TileRows &r, int mt, int n, int g, int t, const LaneFeat &f,
+                                              unsigned (&a)[4]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        unsigned lo, hi;
+        sample_words(t, r.c[h], r.f89[h], f, lo, hi);
+        const bool in = 16 * mt + g + 8 * h < n;
+        a[h] = in ? lo : 0u;
+        a[2 + h] = in ? hi : 0u;
+    }
+}
+
+// A fragments of all four tiles (the training kernel keeps them for the backward pass)
 __device__ __forceinline__ void load_features(const SampleSets &S, long long px, int n, int g, int t, float4 info,
                                               const float (&pl)[3], unsigned (&a)[4][4]) {
+    const LaneFeat f = lane_feat(t, info, pl);
 #pragma unroll
     for (int mt = 0; mt < 4; ++mt) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = 16 * mt + g + 8 * h;
-            const long long k = px * kS + (r < n ? r : 0);
-            const float4 c = r < n ? __ldg(S.col + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const unsigned f89 = (t == 0 && r < n) ? __ldg(S.f89 + k) : 0u;
-            a[mt][h] = r < n ? feat_word(t, c, f89, info, pl) : 0u;
-            a[mt][2 + h] = r < n ? feat_word(4 + t, c, f89, info, pl) : 0u;
-        }
+        TileRows r;
+        load_rows(S, px, mt, n, g, t, r);
+        tile_fragment(r, mt, n, g, t, f, a[mt]);
     }
 }
 
-// layer 1 + ReLU + head for one 8-column tile nt: accumulates z partials of the lane's rows
-__device__ __forceinline__ void head_tile(const unsigned (&a)[4][4], unsigned b0, unsigned b1, const MlpWeights &w, int nt,
-                                          int t, float (&zw)[4][2], float (&zc)[4][2]) {
-    const int c0 = 8 * nt + 2 * t;
-    const float bias0 = __ldg(w.b1 + c0), bias1 = __ldg(w.b1 + c0 + 1);
-    const float w00 = __ldg(w.W2 + c0), w01 = __ldg(w.W2 + c0 + 1);
-    const float w10 = __ldg(w.W2 + kH + c0), w11 = __ldg(w.W2 + kH + c0 + 1);
-    const float cinit[4] = {bias0, bias1, bias0, bias1};
+// Layer-2 B fragments: column n = g of W2^T (n = 0: z_w, 1: z_c, 2..7 zero), k = hidden units
+__device__ __forceinline__ void load_w2(const MlpWeights &w, int g, int t, unsigned (&b)[4][2]) {
 #pragma unroll
-    for (int mt = 0; mt < 4; ++mt) {
-        float d[4];
-        mma_bf16(d, a[mt], b0, b1, cinit);
-        const float h0 = fmaxf(d[0], 0.f), h1 = fmaxf(d[1], 0.f), h2 = fmaxf(d[2], 0.f), h3 = fmaxf(d[3], 0.f);
-        zw[mt][0] = fmaf(w00, h0, fmaf(w01, h1, zw[mt][0]));
-        zw[mt][1] = fmaf(w00, h2, fmaf(w01, h3, zw[mt][1]));
-        zc[mt][0] = fmaf(w10, h0, fmaf(w11, h1, zc[mt][0]));
-        zc[mt][1] = fmaf(w10, h2, fmaf(w11, h3, zc[mt][1]));
+    for (int kt = 0; kt < 4; ++kt) {
+        const int j = 16 * kt + 2 * t;
+        b[kt][0] = g < 2 ? bf16x2(__ldg(w.W2 + g * kH + j), __ldg(w.W2 + g * kH + j + 1)) : 0u;
+        b[kt][1] = g < 2 ? bf16x2(__ldg(w.W2 + g * kH + j + 8), __ldg(w.W2 + g * kH + j + 9)) : 0u;
     }
 }
 
-struct PixelForward {
-    float zw[4][2], zc[4][2];  // per lane: rows 16 mt + g (+ 8), summed over the hidden units
-};
-
-__device__ __forceinline__ void forward(const unsigned (&a)[4][4], const unsigned (&bw)[8][2], const MlpWeights &w,
-                                        int t, PixelForward &pf) {
+// Both layers of one 16-sample tile.  sb1[4 nt + t] = (b1[8 nt + 2 t], b1[8 nt + 2 t + 1]) twice:
+// the layer-1 accumulator's initial quad for lane t of hidden tile nt.
+// Returns the layer-2 accumulator: lane (g, 0) holds (z_w, z_c) of row g in e[0], e[1] and of
+// row g + 8 in e[2], e[3] (b2 included); the other lanes hold the zero padding columns.
+__device__ __forceinline__ void tile_forward(const unsigned (&a)[4], const unsigned (&bw)[8][2], const float4 *sb1,
+                                             const unsigned (&bw2)[4][2], float b20, float b21, int t,
+                                             float (&e)[4]) {
+    e[0] = e[2] = t == 0 ? b20 : 0.0f;
+    e[1] = e[3] = t == 0 ? b21 : 0.0f;
 #pragma unroll
-    for (int mt = 0; mt < 4; ++mt) pf.zw[mt][0] = pf.zw[mt][1] = pf.zc[mt][0] = pf.zc[mt][1] = 0.0f;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) head_tile(a, bw[nt][0], bw[nt][1], w, nt, t, pf.zw, pf.zc);
-#pragma unroll
-    for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            pf.zw[mt][r] += __shfl_xor_sync(0xffffffffu, pf.zw[mt][r], 1);
-            pf.zw[mt][r] += __shfl_xor_sync(0xffffffffu, pf.zw[mt][r], 2);
-            pf.zc[mt][r] += __shfl_xor_sync(0xffffffffu, pf.zc[mt][r], 1);
-            pf.zc[mt][r] += __shfl_xor_sync(0xffffffffu, pf.zc[mt][r], 2);
-        }
+    for (int kt = 0; kt < 4; ++kt) {
+        float d0[4], d1[4];
+        mma_bf16_q(d0, a, bw[2 * kt][0], bw[2 * kt][1], sb1[4 * (2 * kt) + t]);
+        mma_bf16_q(d1, a, bw[2 * kt + 1][0], bw[2 * kt + 1][1], sb1[4 * (2 * kt + 1) + t]);
+        // hidden columns 16 kt + 2 t (+1) and + 8: the A fragment of layer 2's k-tile kt
+        const unsigned h[4] = {relu_bf16x2(d0[0], d0[1]), relu_bf16x2(d0[2], d0[3]), relu_bf16x2(d1[0], d1[1]),
+                               relu_bf16x2(d1[2], d1[3])};
+        mma_bf16(e, h, bw2[kt][0], bw2[kt][1], e);
+    }
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -140,20 +212,37 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Layer-1 B fragments of the eight hidden tiles, in the A fragments' feature order
 __device__ __forceinline__ void load_w1(const MlpWeights &w, int g, int t, unsigned (&bw)[8][2]) {
-    const unsigned *w1 = reinterpret_cast<const unsigned *>(w.W1);
+    const unsigned short *w1 = w.W1;
+    const int f0 = slot_feature(t, 0), f1 = slot_feature(t, 1), f2 = slot_feature(4 + t, 0),
+              f3 = slot_feature(4 + t, 1);
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-        bw[nt][0] = __ldg(w1 + (8 * nt + g) * 8 + t);
-        bw[nt][1] = __ldg(w1 + (8 * nt + g) * 8 + 4 + t);
+        const unsigned short *row = w1 + (8 * nt + g) * kF;
+        bw[nt][0] = pack2(__ldg(row + f0), __ldg(row + f1));
+        bw[nt][1] = pack2(__ldg(row + f2), __ldg(row + f3));
     }
 }
 
+// b1 pairs, each twice, in shared memory (the layer-1 accumulator's initial quads); synchronises
+// the block
+__device__ __forceinline__ void load_b1(const MlpWeights &w, float4 *sb1) {
+    for (int i = threadIdx.x; i < kH / 2; i += blockDim.x) {
+        const float x = __ldg(w.b1 + 2 * i), y = __ldg(w.b1 + 2 * i + 1);
+        sb1[i] = make_float4(x, y, x, y);
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- inference
-__global__ void __launch_bounds__(32 * kWarps) mlp_infer_kernel(const MlpArgs m) {
+__global__ void __launch_bounds__(32 * kWarps, 8) mlp_infer_kernel(const MlpArgs m) {
+    __shared__ float4 s_b1[kH / 2];
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    unsigned bw[8][2];
+    load_b1(m.w, s_b1);
+    unsigned bw[8][2], bw2[4][2];
     load_w1(m.w, g, t, bw);
+    load_w2(m.w, g, t, bw2);
     const float b20 = __ldg(m.w.b2), b21 = __ldg(m.w.b2 + 1);
     const long long nwarps = (long long)gridDim.x * kWarps;
     for (long long px = blockIdx.x * (long long)kWarps + (threadIdx.x >> 5); px < m.n_px; px += nwarps) {
@@ -161,27 +250,32 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_infer_kernel(const MlpArgs m)
         const float *pl = m.sets.plain + 3 * px;
         float o0 = pl[0], o1 = pl[1], o2 = pl[2], conf = 0.0f;
         if (n > 0) {
-            unsigned a[4][4];
             const float plv[3] = {o0, o1, o2};
-            load_features(m.sets, px, n, g, t, __ldg(m.sets.info + px), plv, a);
-            PixelForward pf;
-            forward(a, bw, m.w, t, pf);
+            const LaneFeat lf = lane_feat(t, __ldg(m.sets.info + px), plv);
+            const int n_tiles = (n + 15) >> 4;
             float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
-            if (t < 2) {
-#pragma unroll
-                for (int mt = 0; mt < 4; ++mt) {
-                    const int s = 16 * mt + g + 8 * t;
-                    if (s < n) {
-                        const float zw = (t == 0 ? pf.zw[mt][0] : pf.zw[mt][1]) + b20;
-                        const float zc = (t == 0 ? pf.zc[mt][0] : pf.zc[mt][1]) + b21;
-                        const float w = softplusf(zw);
-                        const float4 c = __ldg(m.sets.col + px * kS + s);
-                        sw += w;
-                        sr = fmaf(w, c.x, sr);
-                        sg = fmaf(w, c.y, sg);
-                        sb = fmaf(w, c.z, sb);
-                        sc += sigmoidf(zc);
-                    }
+#pragma unroll 1
+            for (int mt = 0; mt < n_tiles; ++mt) {
+                TileRows cur;
+                load_rows(m.sets, px, mt, n, g, t, cur);
+                unsigned a[4];
+                tile_fragment(cur, mt, n, g, t, lf, a);
+                // lane (g, 0) takes row g, lane (g, 1) row g + 8
+                const float3 c = t == 0 ? make_float3(cur.c[0].x, cur.c[0].y, cur.c[0].z)
+                                        : make_float3(cur.c[1].x, cur.c[1].y, cur.c[1].z);
+                float e[4];
+                tile_forward(a, bw, s_b1, bw2, b20, b21, t, e);
+                const float zw8 = __shfl_sync(0xffffffffu, e[2], lane & ~3);
+                const float zc8 = __shfl_sync(0xffffffffu, e[3], lane & ~3);
+                const int s = 16 * mt + g + 8 * t;
+                if (t < 2 && s < n) {
+                    const float zw = t == 0 ? e[0] : zw8, zc = t == 0 ? e[1] : zc8;
+                    const float w = softplusf(zw);
+                    sw += w;
+                    sr = fmaf(w, c.x, sr);
+                    sg = fmaf(w, c.y, sg);
+                    sb = fmaf(w, c.z, sb);
+                    sc += sigmoidf(zc);
                 }
             }
             sw = warp_sum(sw);
@@ -212,11 +306,13 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_infer_kernel(const MlpArgs m)
 __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m) {
     __shared__ unsigned short s_dh[kWarps][kS * kLd];
     __shared__ float s_g[kH + 2 * kH + 2 + 1];  // gb1, gW2, gb2, loss
+    __shared__ float4 s_b1[kH / 2];
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kH + 2 * kH + 3; i += blockDim.x) s_g[i] = 0.0f;
-    __syncthreads();
-    unsigned bw[8][2];
+    load_b1(m.w, s_b1);  // synchronises the block
+    unsigned bw[8][2], bw2[4][2];
     load_w1(m.w, g, t, bw);
+    load_w2(m.w, g, t, bw2);
     const float b20 = __ldg(m.w.b2), b21 = __ldg(m.w.b2 + 1);
     float dW1[4][2][4];
 #pragma unroll
@@ -234,8 +330,6 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
         const float4 info = __ldg(m.sets.info + px);
         unsigned a[4][4];
         load_features(m.sets, px, n, g, t, info, plv, a);
-        PixelForward pf;
-        forward(a, bw, m.w, t, pf);
         // per-sample weights, outputs and the pixel's loss
         float zw[4], zc[4], w[4], cf[4], cr[4][3];
         bool valid[4];
@@ -243,8 +337,12 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
 #pragma unroll
         for (int mt = 0; mt < 4; ++mt) {
             const int s = 16 * mt + g + 8 * t;
-            zw[mt] = (t == 0 ? pf.zw[mt][0] : pf.zw[mt][1]) + b20;
-            zc[mt] = (t == 0 ? pf.zc[mt][0] : pf.zc[mt][1]) + b21;
+            float e[4];
+            tile_forward(a[mt], bw, s_b1, bw2, b20, b21, t, e);
+            const float zw8 = __shfl_sync(0xffffffffu, e[2], lane & ~3);
+            const float zc8 = __shfl_sync(0xffffffffu, e[3], lane & ~3);
+            zw[mt] = t == 0 ? e[0] : zw8;
+            zc[mt] = t == 0 ? e[1] : zc8;
             valid[mt] = t < 2 && s < n;
             w[mt] = valid[mt] ? softplusf(zw[mt]) : 0.f;
             cf[mt] = valid[mt] ? sigmoidf(zc[mt]) : 0.f;
@@ -318,7 +416,9 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_train_kernel(const MlpArgs m)
             for (int mt = 0; mt < 4; ++mt) {
                 float d[4];
                 mma_bf16(d, a[mt], bw[nt][0], bw[nt][1], cinit);
-                const float h0 = fmaxf(d[0], 0.f), h1 = fmaxf(d[1], 0.f), h2 = fmaxf(d[2], 0.f), h3 = fmaxf(d[3], 0.f);
+                // the hidden values layer 2 saw: ReLU, rounded to BF16
+                const __nv_bfloat162 r01 = u32_as_bf162(relu_bf16x2(d[0], d[1])), r23 = u32_as_bf162(relu_bf16x2(d[2], d[3]));
+                const float h0 = __low2float(r01), h1 = __high2float(r01), h2 = __low2float(r23), h3 = __high2float(r23);
                 g0a += dzw[mt][0] * h0 + dzw[mt][1] * h2;
                 g0b += dzw[mt][0] * h1 + dzw[mt][1] * h3;
                 g1a += dzc[mt][0] * h0 + dzc[mt][1] * h2;

@@ -120,6 +120,35 @@ def test_softplus_weights_and_sigmoid_confidence_against_scipy():
     assert conf == pytest.approx(expit(-2 * feat[:, 0]).mean(), abs=1e-15)
 
 
+def test_bf16_mode_rounds_inputs_weights_and_hidden_activations():
+    """round_bf16: features, W1, W2 and the ReLU output enter the products as BF16 (8 significant
+    bits, round to nearest even); b1, b2 as FP32.  One sample, one hidden unit, closed forms."""
+    feat = np.zeros((1, 16))
+    col = np.array([[0.5, 0.5, 0.5]])
+    W1 = np.zeros((64, 16))
+    W2 = np.zeros((2, 64)); W2[0, 0] = 1.0
+    b1, b2 = np.zeros(64), np.zeros(2)
+    # h = 1 + 2^-10 is not a BF16 value: it rounds to 1 (z_w exactly 1), or is kept (z_w = h)
+    feat[0, 10] = 1.0
+    b1[0] = 1.0 + 2.0 ** -10
+    z_r = oracle.mlp_pixel(feat, col, 1, W1, b1, W2, b2, round_bf16=True)[3]
+    z_f = oracle.mlp_pixel(feat, col, 1, W1, b1, W2, b2, round_bf16=False)[3]
+    assert z_r[0, 0] == 1.0 and z_f[0, 0] == 1.0 + 2.0 ** -10
+    # a tie between two BF16 values rounds to the even one: 1 + 3 * 2^-8 -> 1 + 2^-6
+    b1[0] = 1.0 + 3 * 2.0 ** -8
+    assert oracle.mlp_pixel(feat, col, 1, W1, b1, W2, b2, round_bf16=True)[3][0, 0] == 1.0 + 2.0 ** -6
+    # a feature and a weight are rounded too: f = 1 + 2^-9 (down to 1), W1 = 3 + 3 * 2^-8 (up to 3 + 2^-6)
+    b1[0] = 0.0
+    feat[0, 10] = 0.0
+    feat[0, 3] = 1.0 + 2.0 ** -9
+    W1[0, 3] = 3.0 + 3 * 2.0 ** -8
+    z = oracle.mlp_pixel(feat, col, 1, W1, b1, W2, b2, round_bf16=True)[3][0, 0]
+    assert z == 3.0 + 2.0 ** -6
+    # W2 likewise: 1 + 2^-9 rounds to 1
+    W2[0, 0] = 1.0 + 2.0 ** -9
+    assert oracle.mlp_pixel(feat, col, 1, W1, b1, W2, b2, round_bf16=True)[3][0, 0] == 3.0 + 2.0 ** -6
+
+
 def test_gradients_match_central_differences(tiny):
     c, v, _ = tiny
     prm = oracle.default_params(c.depth, k=5, T=4, radius_rel=0.03)  # a wider gate: several samples per pixel
