@@ -89,6 +89,21 @@ __device__ __forceinline__ float3 load_colour(const void *base, I idx) {
     }
 }
 
+// Depth and colour of one window sample.  The FP32 colour record carries the depth in its fourth
+// lane (the same value as the depth plane), so one 16-byte load brings both; the FP16 record has
+// no room for it and the depth comes from the depth plane.
+template <int CFMT, typename I>
+__device__ __forceinline__ void load_sample(const float *dwin, const void *cwin, I idx, float &d, float3 &c) {
+    if (CFMT == 0) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(cwin) + idx);
+        d = v.w;
+        c = make_float3(v.x, v.y, v.z);
+    } else {
+        d = __ldg(dwin + idx);
+        c = load_colour<1>(cwin, idx);
+    }
+}
+
 // Packed FP32x2 arithmetic (sm_100 family): two IEEE single-precision operations, rounded to
 // nearest each, in one instruction; the halves are exactly the scalar results.
 typedef unsigned long long f32x2;

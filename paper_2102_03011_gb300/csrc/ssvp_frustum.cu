@@ -401,14 +401,15 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
                         const int m = mc0 + k;
                         const int qx = hb.xmajor ? m : n, qy = hb.xmajor ? n : m;
                         const long long off = fbase + (long long)(qy + kPad) * P.pitch + (qx + kPad);
-                        const float d = __ldg(P.depth + off);
+                        float d;
+                        float3 c;
+                        load_sample<CFMT>(P.depth, P.colour, off, d, c);
                         const float fmk = (float)m;
                         const float h1 = fmaf(d, fmaf(sm1, fmk, b1), E1);
                         const float h2 = fmaf(d, fmaf(sm2, fmk, b2), E2);
                         const float h3 = fmaf(d, fmaf(sm3, fmk, b3), E3);
                         // Eq. 9: masked samples weigh 0 in the mean-shift steps
                         if (INP && pass > 0 && __ldg(P.mask + off) != 0) continue;
-                        const float3 c = load_colour<CFMT>(P.colour, off);
                         const float er = c.x - cref.x, eg = c.y - cref.y, eb = c.z - cref.z;
                         float w = 1.0f;
                         if (wpass) {

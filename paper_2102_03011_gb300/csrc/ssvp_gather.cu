@@ -212,8 +212,7 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
 #pragma unroll
                     for (int t = 0; t < ACCB; ++t) {
                         const int off = (idx[t] >> 3) * P.pitch + (idx[t] & 7);
-                        dq[t] = __ldg(dwin + off);
-                        cq[t] = load_colour<CFMT>(cwin, off);
+                        load_sample<CFMT>(dwin, cwin, off, dq[t], cq[t]);
                     }
                     if constexpr (ACCB == 2) {
                         // the two samples in packed FP32x2: per half the scalar sequence below
@@ -318,11 +317,13 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                         const int dx = __ffs((int)mask) - 1;
                         mask &= mask - 1u;
                         const long long off = (long long)dy * P.pitch + dx;
-                        const float dz = (__ldg(dwin + off) - zh) - zl;
+                        float dq;
+                        float3 c;
+                        load_sample<CFMT>(dwin, cwin, off, dq, c);
+                        const float dz = (dq - zh) - zl;
                         const float X = fmaf(dz, __fmaf_rn((float)dx, ifx, Ax0), __fmaf_rn((float)dx, zix, Bx0));
                         const float Y = fmaf(dz, Ay, By);
                         const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
-                        const float3 c = load_colour<CFMT>(P.colour, wbase + off);
                         const float er = c.x - cref.x, eg = c.y - cref.y, eb = c.z - cref.z;
                         const float e = fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta));
                         float w = 1.0f;

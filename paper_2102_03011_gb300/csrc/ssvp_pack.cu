@@ -13,7 +13,8 @@ namespace {
 
 __device__ __forceinline__ bool valid_depth(float d) { return isfinite(d) && d > 0.0f; }
 
-// One thread per input pixel of frames [0, nF): interleaved rgb (12 B) + depth -> padded planes.
+// One thread per input pixel of frames [0, nF): interleaved rgb (12 B) + depth -> padded planes
+// (FP32: (r, g, b, depth) records; FP16: (r, g, b, 0) half records).
 // Invalid depths become NaN so that a single comparison rejects them in the gather.
 template <int CFMT>
 __global__ void pack_kernel(const float *__restrict__ rgb, const float *__restrict__ depth, int W, int H,
@@ -26,9 +27,11 @@ __global__ void pack_kernel(const float *__restrict__ rgb, const float *__restri
         float d = depth[i];
         float r = rgb[3 * i], g = rgb[3 * i + 1], b = rgb[3 * i + 2];
         long long o = (f + frame0) * P.fstride + (long long)(y + kPad) * P.pitch + (x + kPad);
-        P.depth[o] = valid_depth(d) ? d : __int_as_float(0x7fffffff);
+        const float dv = valid_depth(d) ? d : __int_as_float(0x7fffffff);
+        P.depth[o] = dv;
         if (CFMT == 0) {
-            reinterpret_cast<float4 *>(P.colour)[o] = make_float4(r, g, b, 0.0f);
+            // the fourth lane repeats the depth: the gather's filter loop reads both in one load
+            reinterpret_cast<float4 *>(P.colour)[o] = make_float4(r, g, b, dv);
         } else {
             __half2 rg = __floats2half2_rn(r, g);
             __half2 b0 = __floats2half2_rn(b, 0.0f);
