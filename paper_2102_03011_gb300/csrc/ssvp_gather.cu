@@ -61,8 +61,8 @@ __device__ __forceinline__ void store_sample(const GatherArgs &a, long long crop
 
 // LEARN: visit the frames in canonical order (O, O-1, O+1, ...) and store the features of the
 // first kMaxSamples accepted samples (learned filter); the Eq. 3/4 result goes to a.sets.plain.
-// ACCB: accepted samples taken per iteration of the filter loop (1, or 2 in packed FP32x2; two
-// pays off in the per-launch kernels, plain and learned, not in the batched one)
+// ACCB: accepted samples taken per iteration of the filter loop of a compile-time window (1, or
+// 2 in packed FP32x2, which the kernels use; the runtime-k path takes them one at a time)
 template <int K, int CFMT, bool DEBUG, bool LEARN = false, int ACCB = 1>
 __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &P, const int O, const int u0,
                                              const int v0, const int u, const int v, const bool active,
@@ -445,30 +445,47 @@ __global__ void __launch_bounds__(32 * TY, 32 / TY) batch_kernel(const GatherArg
     constexpr int NT = 32 * TY;
     extern __shared__ float4 sgeom[];
     __shared__ float s_const[4];
-    __shared__ long long s_item;
     __shared__ Planes s_P;
+    // the work unit (one output frame of one item), kept in shared memory by thread 0 so that no
+    // loop state stays live in registers across the gather
+    __shared__ const PairGeom *s_geom;
+    __shared__ int s_c, s_O, s_u0, s_v0, s_oi, s_olast, s_done;
     __shared__ unsigned long long s_cnt[2][NT / 32];
-    __shared__ float s_w[NT / 32];
-    unsigned long long t_acc = 0, t_exam = 0;
-    float t_w = 0.0f;
+    __shared__ double s_w[NT / 32];
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_cnt[0][warp] = 0ull; s_cnt[1][warp] = 0ull; s_w[warp] = 0.0; }
+    if (threadIdx.x == 0) { s_oi = 0; s_olast = 0; s_done = 0; }
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(b.counter, 1ull);
-        __syncthreads();
-        const long long item = s_item;
-        if (item >= b.n_items) break;
-        int c = 0;
-        while (c + 1 < b.n_clips && b.clips[c + 1].item_begin <= item) ++c;
-        const BatchClip &bc = b.clips[c];
-        const long long local = item - bc.item_begin;
-        const int ntile = bc.tiles_x * bc.tiles_y;
-        const int tile = (int)(local % ntile), chunk = (int)(local / ntile);
-        const int u0 = (tile % bc.tiles_x) * 32, v0 = (tile / bc.tiles_x) * TY;
-        const int o_first = chunk * b.frame_chunk, o_last = min(o_first + b.frame_chunk, bc.n_out);
-        for (int oi = o_first; oi < o_last; ++oi) {
-            for (int j = threadIdx.x; j < a.n_slots; j += NT)
-                build_slot(bc.geom[(long long)oi * a.n_slots + j], (float)u0, (float)v0, sgeom + kSlotVec * j);
-            if (threadIdx.x == 0) {
+        if (threadIdx.x == 0) {
+            // the next output frame of the current item, else the next item
+            int c = -1;
+            if (s_oi + 1 < s_olast) {
+                ++s_oi;
+                c = s_c;
+            } else {
+                const long long item = (long long)atomicAdd(b.counter, 1ull);
+                if (item >= b.n_items) {
+                    s_done = 1;
+                } else {
+                    c = 0;
+                    while (c + 1 < b.n_clips && b.clips[c + 1].item_begin <= item) ++c;
+                    s_c = c;
+                    const BatchClip &bc = b.clips[c];
+                    const long long local = item - bc.item_begin;
+                    const int ntile = bc.tiles_x * bc.tiles_y;
+                    const int tile = (int)(local % ntile), chunk = (int)(local / ntile);
+                    s_u0 = (tile % bc.tiles_x) * 32;
+                    s_v0 = (tile / bc.tiles_x) * TY;
+                    s_oi = chunk * b.frame_chunk;
+                    s_olast = min(s_oi + b.frame_chunk, bc.n_out);
+                }
+            }
+            if (c >= 0) {
+                const BatchClip &bc = b.clips[c];
                 s_P = bc.p;
+                s_O = bc.frame_begin + s_oi;
+                s_geom = bc.geom + (long long)s_oi * a.n_slots;
                 const float r = a.radius > 0.0f ? a.radius : -a.radius * *bc.p.median;
                 const float sx = a.sigma_xyz > 0.0f ? a.sigma_xyz : r;
                 s_const[0] = r * r;
@@ -476,28 +493,31 @@ __global__ void __launch_bounds__(32 * TY, 32 / TY) batch_kernel(const GatherArg
                 s_const[2] = kLog2e / (2.0f * sx * sx);
                 s_const[3] = a.mode == 3 ? 0.0f : 1.0f;
             }
-            __syncthreads();
-            const int u = u0 + (threadIdx.x & 31), v = v0 + (threadIdx.x >> 5);
-            const bool active = u < s_P.W && v < s_P.H;
-            int n_acc = 0, n_exam = 0;
-            float acc_w = 0.0f;
-            gather_pixel<K, CFMT, false>(a, s_P, bc.frame_begin + oi, u0, v0, u, v, active, 0, sgeom, a.n_slots,
-                                         s_const[0], s_const[1], s_const[2], s_const[3] != 0.0f, n_acc, n_exam, acc_w);
-            t_acc += (unsigned long long)n_acc;
-            t_exam += (unsigned long long)n_exam;
-            t_w += acc_w;
-            __syncthreads();  // the shared geometry and s_P are rebuilt next
         }
-    }
+        __syncthreads();
+        if (s_done) break;
+        for (int j = threadIdx.x; j < a.n_slots; j += NT)
+            build_slot(s_geom[j], (float)s_u0, (float)s_v0, sgeom + kSlotVec * j);
+        __syncthreads();
+        const int u0 = s_u0, v0 = s_v0;
+        const int u = u0 + (threadIdx.x & 31), v = v0 + (threadIdx.x >> 5);
+        const bool active = u < s_P.W && v < s_P.H;
+        int n_acc = 0, n_exam = 0;
+        float acc_w = 0.0f;
+        gather_pixel<K, CFMT, false, false, 2>(a, s_P, s_O, u0, v0, u, v, active, 0, sgeom, a.n_slots, s_const[0], s_const[1],
+                                     s_const[2], s_const[3] != 0.0f, n_acc, n_exam, acc_w);
+        // launch statistics go to per-warp shared slots after every tile
+        unsigned ce = (unsigned)n_exam, ca = (unsigned)n_acc;
+        float sw = acc_w;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        t_exam += __shfl_xor_sync(0xffffffffu, t_exam, o);
-        t_acc += __shfl_xor_sync(0xffffffffu, t_acc, o);
-        t_w += __shfl_xor_sync(0xffffffffu, t_w, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            ce += __shfl_xor_sync(0xffffffffu, ce, o);
+            ca += __shfl_xor_sync(0xffffffffu, ca, o);
+            sw += __shfl_xor_sync(0xffffffffu, sw, o);
+        }
+        if ((threadIdx.x & 31) == 0) { s_cnt[0][warp] += ce; s_cnt[1][warp] += ca; s_w[warp] += sw; }
+        __syncthreads();  // the shared geometry and the work unit are rebuilt next
     }
-    const int warp = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) { s_cnt[0][warp] = t_exam; s_cnt[1][warp] = t_acc; s_w[warp] = t_w; }
-    __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long te = 0, ta = 0;
         double tw = 0.0;

@@ -44,9 +44,9 @@ def _plain(sess, p):
 
 
 def test_default_plan_matches_the_plain_path(sess):
-    """Same tiles as the plain launch: the same samples with the same weights (identical counts);
-    the plain kernel sums accepted samples two at a time in packed partial sums and the batched
-    one singly, so colours agree to FP32 summation order; graph replays are bitwise identical."""
+    """Same tiles as the plain launch: the same samples with the same weights (identical counts),
+    summed in the same order (two at a time in packed partial sums in both kernels), so colours
+    agree to the bit; graph replays are bitwise identical."""
     ss = sess.ss
     p = sess.params(k=5, half_window=3)
     want, totals = _plain(sess, p)
@@ -60,7 +60,7 @@ def test_default_plan_matches_the_plain_path(sess):
             ss.ssvp_plan_launch(plan)
             got = _outputs(sess)
             for a, b in zip(got, want):
-                np.testing.assert_allclose(a, b, atol=2e-6, rtol=0)
+                np.testing.assert_array_equal(a, b)
             if first is None:
                 first = [g.copy() for g in got]
             else:
