@@ -384,6 +384,13 @@ def run_batch(args, ss, torch, dev, stream, world, rank):
             ss.ssvp_gather_filter(ctx, p, [n + i])
 
     seq32_ms = timed(sequential_fp32, max(1, args.steps // 2))
+    # and the batched plan over the FP32 clips (its own autotuned shape)
+    ids32 = [n + i for i in ids]
+    ss.ssvp_autotune(ctx, p, ids32)
+    plan32 = ss.ssvp_plan_create(ctx, p, ids32)
+    cfg32, _, _ = ss.ssvp_plan_get_config(plan32)
+    plan32_ms = timed(lambda: ss.ssvp_plan_launch(plan32), max(1, args.steps // 2))
+    ss.ssvp_plan_destroy(plan32)
     psnr32 = []
     for i, c in enumerate(clips):
         o = torch.empty((c.F, c.H, c.W, 3), dtype=torch.float32, device=dev)
@@ -424,6 +431,9 @@ def run_batch(args, ss, torch, dev, stream, world, rank):
         "plain_fp32_sequential": {"value": world * total_px / 1e6 / (seq32_ms / 1e3), "unit": "Mpix/s",
                                   "ms_per_step": seq32_ms, "psnr_db": float(np.mean(psnr32)),
                                   "note": "the same clips with FP32 colour, one plain launch per clip"},
+        "batched_fp32": {"value": world * total_px / 1e6 / (plan32_ms / 1e3), "unit": "Mpix/s",
+                         "ms_per_step": plan32_ms, "tile_rows": cfg32.tile_rows, "frame_chunk": cfg32.frame_chunk,
+                         "note": "the same graph-captured plan over the FP32 clips"},
         "samples_per_s": {"examined": world * examined / (plan_ms / 1e3), "accepted": world * accepted / (plan_ms / 1e3)},
         "psnr_db": {"output_vs_clean": float(np.mean(psnr_out)), "input_vs_clean": float(np.mean(psnr_in)),
                     "reference": "clean pinhole renders, mean over clips"},
