@@ -363,7 +363,10 @@ int ssvp_mlp_grad(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, const i
 /* Lower-median valid input depth of a loaded clip (waits for the load). */
 int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median);
 
-/* Wait for all work queued on the context's stream; returns the first pending error. */
+/* Wait for all work queued on the context's stream; returns the first pending error, or
+ * SSVP_ETIMEOUT when a kernel's bounded wait for its tensor-core products gave up since the last
+ * call (the learned inference waits on an MMA-completion barrier with a limit of about 2 s; the
+ * outputs of that launch are then not valid).  The time-out is reported once. */
 int ssvp_sync(ssvp_ctx *ctx);
 
 /*

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libssvp.so")
-SOURCES = ["ssvp_api.cpp", "ssvp_gather.cu", "ssvp_aperture.cu", "ssvp_mlp.cu", "ssvp_pack.cu", "ssvp_frustum.cu"]
+SOURCES = ["ssvp_api.cpp", "ssvp_gather.cu", "ssvp_aperture.cu", "ssvp_mlp.cu", "ssvp_mlp_tc.cu", "ssvp_pack.cu", "ssvp_frustum.cu"]
 HEADERS = ["ssvp_internal.h", "ssvp_df.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

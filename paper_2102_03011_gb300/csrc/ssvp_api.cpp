@@ -41,6 +41,7 @@ struct ssvp_ctx {
     unsigned long long *stat_counts = nullptr;  // [2]
     double *stat_sumw = nullptr;
     unsigned int *median_scratch = nullptr;
+    int *d_kerr = nullptr;  // set by a kernel whose bounded device-side wait gave up; read by ssvp_sync
     PairGeom *geom = nullptr;
     size_t geom_cap = 0;  // entries
     void *staging = nullptr;
@@ -537,13 +538,15 @@ int ssvp_create(ssvp_ctx **out, int cuda_device, void *cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
     if ((e = cudaMalloc(&ctx->stat_counts, 2 * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMalloc(&ctx->stat_sumw, sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&ctx->median_scratch, ssvp::median_scratch_words() * sizeof(unsigned int))) != cudaSuccess) {
+        (e = cudaMalloc(&ctx->median_scratch, ssvp::median_scratch_words() * sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_kerr, sizeof(int))) != cudaSuccess) {
         int rc = fail(nullptr, e == cudaErrorMemoryAllocation ? SSVP_ENOMEM : SSVP_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
         ssvp_destroy(ctx);
         return rc;
     }
     cudaMemsetAsync(ctx->stat_counts, 0, 2 * sizeof(unsigned long long), ctx->stream);
     cudaMemsetAsync(ctx->stat_sumw, 0, sizeof(double), ctx->stream);
+    cudaMemsetAsync(ctx->d_kerr, 0, sizeof(int), ctx->stream);
     *out = ctx;
     return SSVP_OK;
 }
@@ -556,6 +559,7 @@ void ssvp_destroy(ssvp_ctx *ctx) {
     if (ctx->stat_counts) cudaFree(ctx->stat_counts);
     if (ctx->stat_sumw) cudaFree(ctx->stat_sumw);
     if (ctx->median_scratch) cudaFree(ctx->median_scratch);
+    if (ctx->d_kerr) cudaFree(ctx->d_kerr);
     if (ctx->geom) cudaFree(ctx->geom);
     if (ctx->staging) cudaFree(ctx->staging);
     if (ctx->d_shutter_log2) cudaFree(ctx->d_shutter_log2);
@@ -745,7 +749,7 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
                 m.O = O; m.W = c.p.W; m.H = c.p.H; m.x0 = cx0[i]; m.y0 = cy0[i]; m.cw = cw[i];
                 m.tau = p.conf_threshold;
                 m.out = c.p.out;
-                CK(ssvp::launch_mlp_infer(m, ctx->stream), "mlp inference kernel");
+                CK(ssvp::launch_mlp_infer_tc(m, ctx->d_kerr, ctx->stream), "mlp inference kernel");
             }
         }
         return SSVP_OK;
@@ -1427,6 +1431,12 @@ int ssvp_sync(ssvp_ctx *ctx) {
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     CK(cudaGetLastError(), "pending CUDA error");
+    int kerr = 0;
+    CK(cudaMemcpy(&kerr, ctx->d_kerr, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy (kernel error word)");
+    if (kerr) {
+        CK(cudaMemset(ctx->d_kerr, 0, sizeof(int)), "cudaMemset (kernel error word)");
+        return fail(ctx, SSVP_ETIMEOUT, "a tensor-core completion wait of the learned inference timed out");
+    }
     return SSVP_OK;
 }
 

@@ -144,7 +144,9 @@ struct MlpArgs {
     float *grad;                  // training: kMlpParams + 1 accumulators
 };
 
-cudaError_t launch_mlp_infer(const MlpArgs &m, cudaStream_t s);
+// learned inference on the tcgen05 tensor cores; err (device word) is raised if one of its bounded
+// waits for MMA completion times out
+cudaError_t launch_mlp_infer_tc(const MlpArgs &m, int *err, cudaStream_t s);
 cudaError_t launch_mlp_train(const MlpArgs &m, cudaStream_t s);
 cudaError_t launch_adam(const MlpState &st, float lr, int step, cudaStream_t s);
 cudaError_t launch_mlp_refresh(const MlpState &st, cudaStream_t s);

@@ -1,5 +1,6 @@
-// ssvp_mlp.cu - the learned per-sample weighting: a 16 -> 64 -> 2 MLP over each pixel's capped
-// sample set (up to 64 samples), on the BF16 tensor cores with FP32 accumulation.
+// ssvp_mlp.cu - training of the learned per-sample weighting: a 16 -> 64 -> 2 MLP over each
+// pixel's capped sample set (up to 64 samples), on the BF16 tensor cores (warp-level mma.sync)
+// with FP32 accumulation; inference runs on tcgen05 (ssvp_mlp_tc.cu) with the same arithmetic.
 //
 // One warp per pixel, 16 samples (one MMA row tile) at a time.  Layer 1 is H = F W1^T + b1 with
 // F the tile's 16 x 16 feature block and W1^T held in B fragments for all eight 8-column tiles
@@ -7,9 +8,10 @@
 // ReLU and the rounding to BF16 happen in one conversion, and the accumulator fragments of two
 // neighbouring hidden tiles are exactly the A fragment of the next product, so layer 2 (64 -> 2,
 // padded to 8 output columns) is four more MMAs with b2 in the accumulator.  (z_w, z_c) per
-// sample become w = softplus(z_w) and conf = mean sigmoid(z_c); the output is sum w c / sum w,
-// or the plain Eq. 3/4 result when conf < tau.  Training recomputes H, forms dH in shared memory
-// (BF16) and accumulates dW1 = dH^T F as a second MMA over the sample dimension.
+// sample give w = softplus(z_w) and conf = mean sigmoid(z_c), the loss and dz; the backward pass
+// recomputes H, forms dH in shared memory (BF16) and accumulates dW1 = dH^T F as a second MMA
+// over the sample dimension.  The compact sample sets are also expanded here for callers that
+// read them (ssvp_learned_samples).
 #include <cuda_bf16.h>
 
 #include "ssvp_internal.h"
@@ -233,73 +235,6 @@ __device__ __forceinline__ void load_b1(const MlpWeights &w, float4 *sb1) {
         sb1[i] = make_float4(x, y, x, y);
     }
     __syncthreads();
-}
-
-// ---------------------------------------------------------------- inference
-__global__ void __launch_bounds__(32 * kWarps, 8) mlp_infer_kernel(const MlpArgs m) {
-    __shared__ float4 s_b1[kH / 2];
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    load_b1(m.w, s_b1);
-    unsigned bw[8][2], bw2[4][2];
-    load_w1(m.w, g, t, bw);
-    load_w2(m.w, g, t, bw2);
-    const float b20 = __ldg(m.w.b2), b21 = __ldg(m.w.b2 + 1);
-    const long long nwarps = (long long)gridDim.x * kWarps;
-    for (long long px = blockIdx.x * (long long)kWarps + (threadIdx.x >> 5); px < m.n_px; px += nwarps) {
-        const int n = m.sets.n[px];
-        const float *pl = m.sets.plain + 3 * px;
-        float o0 = pl[0], o1 = pl[1], o2 = pl[2], conf = 0.0f;
-        if (n > 0) {
-            const float plv[3] = {o0, o1, o2};
-            const LaneFeat lf = lane_feat(t, __ldg(m.sets.info + px), plv);
-            const int n_tiles = (n + 15) >> 4;
-            float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
-#pragma unroll 1
-            for (int mt = 0; mt < n_tiles; ++mt) {
-                TileRows cur;
-                load_rows(m.sets, px, mt, n, g, t, cur);
-                unsigned a[4];
-                tile_fragment(cur, mt, n, g, t, lf, a);
-                // lane (g, 0) takes row g, lane (g, 1) row g + 8
-                const float3 c = t == 0 ? make_float3(cur.c[0].x, cur.c[0].y, cur.c[0].z)
-                                        : make_float3(cur.c[1].x, cur.c[1].y, cur.c[1].z);
-                float e[4];
-                tile_forward(a, bw, s_b1, bw2, b20, b21, t, e);
-                const float zw8 = __shfl_sync(0xffffffffu, e[2], lane & ~3);
-                const float zc8 = __shfl_sync(0xffffffffu, e[3], lane & ~3);
-                const int s = 16 * mt + g + 8 * t;
-                if (t < 2 && s < n) {
-                    const float zw = t == 0 ? e[0] : zw8, zc = t == 0 ? e[1] : zc8;
-                    const float w = softplusf(zw);
-                    sw += w;
-                    sr = fmaf(w, c.x, sr);
-                    sg = fmaf(w, c.y, sg);
-                    sb = fmaf(w, c.z, sb);
-                    sc += sigmoidf(zc);
-                }
-            }
-            sw = warp_sum(sw);
-            sr = warp_sum(sr);
-            sg = warp_sum(sg);
-            sb = warp_sum(sb);
-            sc = warp_sum(sc);
-            conf = sc / (float)n;
-            if (conf >= m.tau && sw > 0.0f) {
-                const float inv = 1.0f / sw;
-                o0 = sr * inv;
-                o1 = sg * inv;
-                o2 = sb * inv;
-            }
-        }
-        if (lane == 0) {
-            const long long u = m.x0 + px % m.cw, v = m.y0 + px / m.cw;
-            float *o = m.out + (((long long)m.O * m.H + v) * m.W + u) * 3;
-            o[0] = o0;
-            o[1] = o1;
-            o[2] = o2;
-            if (m.conf_out) m.conf_out[px] = conf;
-        }
-    }
 }
 
 // ---------------------------------------------------------------- training: forward + backward
@@ -549,14 +484,6 @@ __global__ void refresh_kernel(MlpState st) {
 }
 
 }  // namespace
-
-cudaError_t launch_mlp_infer(const MlpArgs &m, cudaStream_t s) {
-    if (m.n_px <= 0) return cudaSuccess;
-    long long blocks = (m.n_px + kWarps - 1) / kWarps;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    mlp_infer_kernel<<<(unsigned)blocks, 32 * kWarps, 0, s>>>(m);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_mlp_train(const MlpArgs &m, cudaStream_t s) {
     if (m.n_batch <= 0) return cudaSuccess;

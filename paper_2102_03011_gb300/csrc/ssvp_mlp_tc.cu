@@ -1,0 +1,483 @@
+// ssvp_mlp_tc.cu - learned-filter inference on the 5th-generation tensor cores (tcgen05).
+//
+// One CTA of 128 threads takes two pixels at a time: their 2 x 64 capped samples are the 128 rows
+// of the layer-1 product, and two such pairs are in flight (a two-stage pipeline: while layer 2
+// of one pair runs, the threads build the next pair's features and finish the previous pair;
+// the next pair's loads are issued before the waits).  Each thread owns one row (one sample):
+//   1. it builds the sample's 16 BF16 features and stores them into shared memory in the
+//      tensor cores' K-major core-matrix layout (8 rows x 16 bytes per core matrix);
+//   2. one elected thread issues tcgen05.mma: D1 (128 x 64, FP32, in tensor memory) = F W1^T;
+//      b1 enters the same accumulator: the logical feature 15 is the constant 0, so its slot
+//      carries 1.0 and W1's column 15 b1's leading BF16 part, and a second MMA with a constant
+//      operand adds b1's two lower BF16 parts (hi + mid + lo represent the FP32 b1 exactly);
+//   3. each thread reads its row of D1 back (tcgen05.ld), applies the ReLU and rounds to BF16 in
+//      one conversion, and stores the row as layer 2's A operand;
+//   4. four tcgen05.mma (K = 16 each): D2 (128 x 16, columns 0 and 1 used) = H W2^T;
+//   5. each thread reads (z_w, z_c) of its row, adds b2, and forms softplus / sigmoid; the two
+//      warps of each pixel reduce the weighted sums.
+// The arithmetic is that of the mma.sync kernels: BF16 operands, FP32 accumulation, h rounded to
+// BF16 before layer 2.  Waits on the MMA-completion barrier are bounded: on a time-out the kernel
+// raises the error word, leaves its loop, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "ssvp_internal.h"
+
+namespace ssvp {
+namespace {
+
+constexpr int kS = 64, kF = 16, kH = 64;
+constexpr int kTcThreads = 128;   // one sample row per thread, two pixels per CTA
+constexpr unsigned kTmemCols = 128;  // two stages of 64 columns (D1; D2 reuses the first 16)
+// shared operands, K-major core matrices; core (i, j) of an R x K operand holds rows 8i..8i+7 and
+// K elements 8j..8j+7 at byte offset (i * K / 8 + j) * 128, row r of it at + 16 (r % 8)
+constexpr int kSmStageA1 = 4096, kSmStageA2 = 16384;  // per pipeline stage
+constexpr int kSmA1 = 0;        // features, 128 x 16, two stages
+constexpr int kSmB1 = 8192;     // W1, 64 x 16
+constexpr int kSmA2 = 10240;    // H, 128 x 64, two stages
+constexpr int kSmB2 = 43008;    // W2 padded to 16 rows, 16 x 64
+constexpr int kSmA0 = 45056;    // constant operand for the b1 residual: ones in K slots 0 and 1, 128 x 16
+constexpr int kSmB0 = 49152;    // b1's two lower BF16 parts in K slots 0 and 1, 64 x 16
+constexpr int kSmBytes = 51200;
+// dynamic shared memory per CTA: the operands, 50 KB.  At most four CTAs fit on an SM (all 608 in
+// one wave on 152 SMs), so their 4 x 128 tensor-memory columns always fit in the SM's 512
+constexpr int kSmRequest = kSmBytes;
+// a waiting thread suspends in try_wait for up to kWaitHintNs per poll; kWaitLimit polls (about
+// 2 s) before a wait counts as timed out
+constexpr unsigned kWaitHintNs = 100000, kWaitLimit = 20000;
+
+__device__ __forceinline__ unsigned core_off(int r, int kc, int k_chunks) {
+    return (unsigned)(((r >> 3) * k_chunks + kc) * 128 + (r & 7) * 16);
+}
+
+// shared-memory matrix descriptor: start, leading (K-direction) and stride (8-row direction) byte
+// offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ unsigned long long smem_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((saddr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, N x M
+__host__ __device__ constexpr unsigned instr_desc(int n, int m) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mma_tc(unsigned d_tmem, unsigned long long adesc, unsigned long long bdesc,
+                                       unsigned idesc, int accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(unsigned mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// bounded wait for the barrier phase with parity `parity`; false on time-out
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity), "r"(kWaitHintNs)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 32 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld2(unsigned taddr, float &a, float &b) {
+    unsigned r0, r1;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    a = __uint_as_float(r0);
+    b = __uint_as_float(r1);
+}
+
+__device__ __forceinline__ unsigned pack2(unsigned short lo, unsigned short hi) { return (unsigned)lo | ((unsigned)hi << 16); }
+__device__ __forceinline__ unsigned short bf16_bits(float x) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(x);
+    return *reinterpret_cast<const unsigned short *>(&b);
+}
+__device__ __forceinline__ unsigned bf16x2(float lo, float hi) { return pack2(bf16_bits(lo), bf16_bits(hi)); }
+__device__ __forceinline__ unsigned relu_bf16x2(float lo, float hi) {
+    unsigned r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + log1pf(__expf(-fabsf(x))); }
+__device__ __forceinline__ float sigmoidf(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
+
+// Feature word w of one sample in the logical order (features 2w, 2w + 1, the lower in the low half)
+__device__ __forceinline__ unsigned feat_word(int w, float4 c, unsigned f89, float4 info, const float (&pl)[3]) {
+    switch (w) {
+    case 0: return bf16x2(c.x, c.y);
+    case 1: return bf16x2(c.z, c.x - info.x);
+    case 2: return bf16x2(c.y - info.y, c.z - info.z);
+    case 3: return __float_as_uint(c.w);
+    case 4: return f89;
+    case 5: return pack2(0x3f80, bf16_bits(info.w));  // BF16 1.0
+    case 6: return bf16x2(c.x - pl[0], c.y - pl[1]);
+    default: return bf16x2(c.z - pl[2], 0.0f);
+    }
+}
+
+// One pixel pair's data as a thread needs it: its sample row (colour record, depth / weight
+// pair), the pixel's info, plain result and set size
+struct RowData {
+    float4 c, info;
+    unsigned f89;
+    float pl[3];
+    int n;
+    long long px;
+};
+
+// what the epilogue of the previous pair keeps
+struct PrevRow {
+    float3 c;
+    float pl[3];
+    int n;
+    long long px;
+};
+
+__device__ __forceinline__ void load_row(const MlpArgs &m, long long pair, int tid, RowData &r) {
+    r.px = 2 * pair + (tid >> 6);
+    const int s = tid & 63;
+    r.n = 0;
+    r.c = r.info = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.f89 = 0u;
+    r.pl[0] = r.pl[1] = r.pl[2] = 0.0f;
+    if (r.px < m.n_px) {
+        // the set's storage holds 64 rows per pixel: rows past n are read (in bounds) and ignored,
+        // so that no load waits on the count
+        const long long k = r.px * kS + s;
+        r.n = m.sets.n[r.px];
+        r.c = __ldg(m.sets.col + k);
+        r.f89 = __ldg(m.sets.f89 + k);
+        r.info = __ldg(m.sets.info + r.px);
+        r.pl[0] = m.sets.plain[3 * r.px];
+        r.pl[1] = m.sets.plain[3 * r.px + 1];
+        r.pl[2] = m.sets.plain[3 * r.px + 2];
+    }
+}
+
+// Two pixel pairs are in flight: while the tensor cores run layer 2 of pair i, the threads build
+// the features of pair i + 1 and finish pair i - 1.  Stage s = i % 2 owns the operand buffers
+// A1[s], A2[s] and the tensor-memory columns [64 s, 64 s + 64) (D1, then D2 in its first 16).
+__global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpArgs m, int *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ float s_red[4][5];
+    __shared__ unsigned long long s_mbar[2];  // layer-1 and layer-2 completion
+    __shared__ unsigned s_tmem;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, s_row = tid & 63;
+
+    {
+        // W1 with b1's leading BF16 part in column 15; b1's two lower parts for the residual product
+        const int row = tid >> 1, kc = tid & 1;
+        uint4 w = __ldg(reinterpret_cast<const uint4 *>(m.w.W1 + row * kF + kc * 8));
+        const float b = __ldg(m.w.b1 + row);
+        const unsigned short hi = bf16_bits(b);
+        const float r1 = b - __uint_as_float((unsigned)hi << 16);
+        const unsigned short mid = bf16_bits(r1);
+        const unsigned short lo = bf16_bits(r1 - __uint_as_float((unsigned)mid << 16));
+        if (kc == 1) w.w = (w.w & 0xffffu) | ((unsigned)hi << 16);
+        *reinterpret_cast<uint4 *>(sm + kSmB1 + core_off(row, kc, 2)) = w;
+        *reinterpret_cast<uint4 *>(sm + kSmB0 + core_off(row, kc, 2)) =
+            kc == 0 ? make_uint4(pack2(mid, lo), 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+        // the constant operand: rows of (1, 1, 0, ..., 0)
+        *reinterpret_cast<uint4 *>(sm + kSmA0 + core_off(tid, 0, 2)) = make_uint4(pack2(0x3f80, 0x3f80), 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(sm + kSmA0 + core_off(tid, 1, 2)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    {
+        const int row = tid >> 3, kc = tid & 7;
+        unsigned q[4] = {0u, 0u, 0u, 0u};
+        if (row < 2) {
+            const float *src = m.w.W2 + row * kH + kc * 8;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) q[i] = bf16x2(__ldg(src + 2 * i), __ldg(src + 2 * i + 1));
+        }
+        *reinterpret_cast<uint4 *>(sm + kSmB2 + core_off(row, kc, 8)) = make_uint4(q[0], q[1], q[2], q[3]);
+    }
+    const float b20 = __ldg(m.w.b2), b21 = __ldg(m.w.b2 + 1);
+    const unsigned bar1 = smem_u32(&s_mbar[0]), bar2 = smem_u32(&s_mbar[1]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar2) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_bad = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = s_tmem;
+    const unsigned lane_base = (unsigned)(warp * 32) << 16;  // this warp's 32 lanes
+    const unsigned sbase = smem_u32(sm);
+    const unsigned long long dB1 = smem_desc(sbase + kSmB1, 128, 256), dA0 = smem_desc(sbase + kSmA0, 128, 256),
+                             dB0 = smem_desc(sbase + kSmB0, 128, 256);
+    constexpr unsigned id1 = instr_desc(kH, 128), id2 = instr_desc(16, 128);
+    unsigned ph1 = 0, ph2 = 0;
+    bool bad = false;
+
+    const long long n_pairs = (m.n_px + 1) / 2;
+    // two register sets take turns: one is consumed while the loads of the next pair land in the
+    // other, so no copy waits on loads in flight
+    RowData set0, set1;
+    PrevRow prev;
+    prev.n = 0;
+    prev.px = m.n_px;
+    long long pair = blockIdx.x;
+    if (pair < n_pairs) load_row(m, pair, tid, set0);
+    int it = 0;
+    auto body = [&](const RowData &cur, RowData &nxt) -> bool {
+        const int st = it & 1;
+        const unsigned a1 = sbase + kSmA1 + st * kSmStageA1, a2 = sbase + kSmA2 + st * kSmStageA2;
+        const unsigned d_st = tmem + 64u * st;
+        // 1. features of this pair, then layer 1 on the tensor cores
+        {
+            unsigned wd[8];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) wd[w] = s_row < cur.n ? feat_word(w, cur.c, cur.f89, cur.info, cur.pl) : 0u;
+            if (s_row < cur.n) wd[7] |= 0x3f80u << 16;  // slot 15 (feature 15 = 0) carries 1.0 for b1
+            unsigned char *A1 = sm + (a1 - sbase);
+            *reinterpret_cast<uint4 *>(A1 + core_off(tid, 0, 2)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+            *reinterpret_cast<uint4 *>(A1 + core_off(tid, 1, 2)) = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (s_bad) return false;  // uniform: written only between the second barrier and the next first one
+        if (tid == 0) {
+            fence_after();
+            mma_tc(d_st, smem_desc(a1, 128, 256), dB1, id1, 0);
+            mma_tc(d_st, dA0, dB0, id1, 1);
+            mma_commit(bar1);
+        }
+        // 2. the previous pair: (z_w, z_c) from its layer 2, weighted sums per warp
+        if (it > 0) {
+            bad |= !mbar_wait(bar2, ph2);
+            ph2 ^= 1u;
+            fence_after();
+            float zw, zc;
+            tmem_ld2(tmem + 64u * (st ^ 1) + lane_base, zw, zc);
+            float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
+            if (s_row < prev.n) {
+                const float w = softplusf(zw + b20);
+                sw = w;
+                sr = w * prev.c.x;
+                sg = w * prev.c.y;
+                sb = w * prev.c.z;
+                sc = sigmoidf(zc + b21);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sw += __shfl_xor_sync(0xffffffffu, sw, o);
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                sg += __shfl_xor_sync(0xffffffffu, sg, o);
+                sb += __shfl_xor_sync(0xffffffffu, sb, o);
+                sc += __shfl_xor_sync(0xffffffffu, sc, o);
+            }
+            if (lane == 0) {
+                s_red[warp][0] = sw;
+                s_red[warp][1] = sr;
+                s_red[warp][2] = sg;
+                s_red[warp][3] = sb;
+                s_red[warp][4] = sc;
+            }
+        }
+        // 3. the next pair's loads, in flight during the waits below
+        const long long pair_next = pair + gridDim.x;
+        if (pair_next < n_pairs) load_row(m, pair_next, tid, nxt);
+        // 4. H = ReLU(D1 + b1) in BF16 as layer 2's A operand, then layer 2
+        bad |= !mbar_wait(bar1, ph1);
+        ph1 ^= 1u;
+        fence_after();
+        {
+            unsigned char *A2 = sm + (a2 - sbase);
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float v[32];
+                tmem_ld32(d_st + lane_base + 32 * half, v);
+                unsigned h[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    h[i] = relu_bf16x2(v[2 * i], v[2 * i + 1]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4 *>(A2 + core_off(tid, 4 * half + q, 8)) =
+                        make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+            }
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_tc(d_st, smem_desc(a2 + kk * 256, 128, 1024), smem_desc(sbase + kSmB2 + kk * 256, 128, 1024), id2,
+                       kk);
+            mma_commit(bar2);
+        }
+        if (bad) s_bad = 1;
+        // 5. the previous pair's outputs (its per-warp sums are complete after the barrier)
+        // (threads 32 and 96: the second warp of each pixel, so that warp 0, which issues the
+        // MMAs, reaches the next barrier first)
+        if (it > 0 && s_row == 32 && prev.px < m.n_px) {
+            const int w0 = warp - 1;
+            float o0 = prev.pl[0], o1 = prev.pl[1], o2 = prev.pl[2], conf = 0.0f;
+            if (prev.n > 0) {
+                const float tw = s_red[w0][0] + s_red[w0 + 1][0];
+                conf = __fdividef(s_red[w0][4] + s_red[w0 + 1][4], (float)prev.n);
+                if (conf >= m.tau && tw > 0.0f) {
+                    const float inv = __frcp_rn(tw);
+                    o0 = (s_red[w0][1] + s_red[w0 + 1][1]) * inv;
+                    o1 = (s_red[w0][2] + s_red[w0 + 1][2]) * inv;
+                    o2 = (s_red[w0][3] + s_red[w0 + 1][3]) * inv;
+                }
+            }
+            const long long u = m.x0 + prev.px % m.cw, v = m.y0 + prev.px / m.cw;
+            float *o = m.out + (((long long)m.O * m.H + v) * m.W + u) * 3;
+            o[0] = o0;
+            o[1] = o1;
+            o[2] = o2;
+            if (m.conf_out) m.conf_out[prev.px] = conf;
+        }
+        prev.c = make_float3(cur.c.x, cur.c.y, cur.c.z);
+        prev.n = cur.n;
+        prev.px = cur.px;
+        prev.pl[0] = cur.pl[0];
+        prev.pl[1] = cur.pl[1];
+        prev.pl[2] = cur.pl[2];
+        pair += gridDim.x;
+        ++it;
+        return pair < n_pairs;
+    };
+    while (pair < n_pairs) {
+        if (!body(set0, set1)) break;
+        if (!body(set1, set0)) break;
+    }
+    __syncthreads();  // s_bad is settled for every thread
+    // the last pair: its layer 2 is in flight
+    if (it > 0 && !s_bad) {
+        const int st = (it - 1) & 1;
+        bad |= !mbar_wait(bar2, ph2);
+        ph2 ^= 1u;
+        fence_after();
+        float zw, zc;
+        tmem_ld2(tmem + 64u * st + lane_base, zw, zc);
+        float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
+        if (s_row < prev.n) {
+            const float w = softplusf(zw + b20);
+            sw = w;
+            sr = w * prev.c.x;
+            sg = w * prev.c.y;
+            sb = w * prev.c.z;
+            sc = sigmoidf(zc + b21);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sw += __shfl_xor_sync(0xffffffffu, sw, o);
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            sg += __shfl_xor_sync(0xffffffffu, sg, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        }
+        if (lane == 0) {
+            s_red[warp][0] = sw;
+            s_red[warp][1] = sr;
+            s_red[warp][2] = sg;
+            s_red[warp][3] = sb;
+            s_red[warp][4] = sc;
+        }
+        __syncthreads();
+        if (s_row == 32 && prev.px < m.n_px) {
+            const int w0 = warp - 1;
+            float o0 = prev.pl[0], o1 = prev.pl[1], o2 = prev.pl[2], conf = 0.0f;
+            if (prev.n > 0) {
+                const float tw = s_red[w0][0] + s_red[w0 + 1][0];
+                conf = __fdividef(s_red[w0][4] + s_red[w0 + 1][4], (float)prev.n);
+                if (conf >= m.tau && tw > 0.0f) {
+                    const float inv = __frcp_rn(tw);
+                    o0 = (s_red[w0][1] + s_red[w0 + 1][1]) * inv;
+                    o1 = (s_red[w0][2] + s_red[w0 + 1][2]) * inv;
+                    o2 = (s_red[w0][3] + s_red[w0 + 1][3]) * inv;
+                }
+            }
+            const long long u = m.x0 + prev.px % m.cw, v = m.y0 + prev.px / m.cw;
+            float *o = m.out + (((long long)m.O * m.H + v) * m.W + u) * 3;
+            o[0] = o0;
+            o[1] = o1;
+            o[2] = o2;
+            if (m.conf_out) m.conf_out[prev.px] = conf;
+        }
+    }
+    if (bad) atomicOr(err, 1);
+    // after a time-out the tensor cores may still be busy: one more bounded wait on each barrier
+    if (s_bad && tid == 0) {
+        mbar_wait(bar1, ph1);
+        mbar_wait(bar2, ph2);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_infer_tc(const MlpArgs &m, int *err, cudaStream_t s) {
+    if (m.n_px <= 0) return cudaSuccess;
+    static int configured_device = -1;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured_device != dev) {
+        e = cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmRequest);
+        if (e != cudaSuccess) return e;
+        configured_device = dev;
+    }
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long pairs = (m.n_px + 1) / 2;
+    long long blocks = (long long)sms * 4;
+    if (blocks > pairs) blocks = pairs;
+    static_assert(kSmBytes <= kSmRequest, "operands exceed the requested shared memory");
+    mlp_infer_tc_kernel<<<(unsigned)blocks, kTcThreads, kSmRequest, s>>>(m, err);
+    return cudaGetLastError();
+}
+
+}  // namespace ssvp
