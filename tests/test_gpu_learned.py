@@ -101,6 +101,47 @@ def test_tensor_core_inference_matches_the_oracle(sess, clip):
     assert near < 0.01 * cw * ch
 
 
+@pytest.mark.parametrize("crop,radius_rel", [((3, 5, 17, 9), 0.02), ((3, 5, 17, 9), 0.03), ((0, 0, 96, 54), 0.005)])
+def test_tensor_core_inference_on_odd_crops_empty_and_short_sets(sess, clip, crop, radius_rel):
+    """The tensor-core inference takes pixels two at a time and 64 sample rows each: an odd crop
+    leaves the last pair half empty, pixels without a valid depth have no samples, a tight radius
+    gives sets shorter than a 16-row tile and a wide one full 64-sample sets; all must match the
+    oracle."""
+    c = synth.make_clip("planes3", 96, 54, 10, seed=11)
+    O, k, T = 5, 5, 4
+    x0, y0, cw, ch = crop
+    # invalid reference depths inside the crop: empty sets, output = plain = c_ref
+    c.depth[O, y0 + 1, x0 + 2] = 0.0
+    c.depth[O, y0 + ch // 2, x0 + cw // 2] = np.nan
+    c.depth[O, y0 + ch - 1, x0 + cw - 1] = -1.0
+    sess.load(44, c)
+    prm = oracle.default_params(c.depth, k=k, T=T, radius_rel=radius_rel)
+    rng2 = np.random.default_rng(7)
+    W1, b1, W2, b2 = oracle.he_init(8)
+    b1 = rng2.normal(0, 0.1, 64)
+    b2 = np.array([0.2, 1.5])
+    sess.ss.ssvp_set_mlp(sess.ctx, W1, b1, W2, b2)
+    g = sess.run(44, O, crop=crop, mode=2, k=k, half_window=T, conf_threshold=0.5, radius=-radius_rel)
+    of, oc, on, op = oracle.learned_crop(oracle.ClipView.of(c), prm, O, crop=crop)
+    ok = ~_flags(c, prm, O, crop)
+    assert (on == 0).sum() >= 3
+    if radius_rel <= 0.005:
+        assert ((on > 0) & (on < 16)).sum() > 1000  # sets shorter than one 16-row tile
+    else:
+        assert ((on > 16) & (on % 16 != 0)).sum() > 0 or (on == 64).sum() > 100  # partial last tiles or full sets
+    worst = 0.0
+    for y in range(ch):
+        for x in range(cw):
+            if not ok[y, x]:
+                continue
+            _, ofin, conf, _ = oracle.mlp_pixel(of[y, x], oc[y, x], on[y, x], W1, b1, W2, b2, round_bf16=True,
+                                                plain=op[y, x])
+            if abs(conf - 0.5) < 1e-3:
+                continue
+            worst = max(worst, float(np.abs(g.rgb[y, x] - ofin).max()))
+    assert worst <= 1e-3, worst
+
+
 def test_high_threshold_reproduces_the_plain_denoiser(sess, clip):
     sess.load(40, clip)
     W1, b1, W2, b2 = oracle.he_init(5)
