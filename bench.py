@@ -459,8 +459,13 @@ def run_learned(args, ss, torch, dev, stream, world, rank):
     ctx = ss.ssvp_create(local, stream)
     p = ss.ssvp_params_default()
     p.k, p.half_window, p.radius = K_WIN, T, -RADIUS_REL
+    # a second operating point: the same method with a shorter window (its own network and context)
+    TS = args.learned_short_window
+    ctx_s = ss.ssvp_create(local, stream) if TS > 0 else None
+    p_s = ss.ssvp_params_default()
+    p_s.k, p_s.half_window, p_s.radius = K_WIN, TS, -RADIUS_REL
     n_train, group, steps_per_group = args.train_clips, 8, 40
-    losses, t_render, t_train = [], 0.0, 0.0
+    losses, losses_s, t_render, t_train = [], [], 0.0, 0.0
     for g0 in range(0, n_train, group):
         t0 = time.perf_counter()
         clips = [synth.make_clip("room", 640, 360, 30, seed=1000 + i) for i in range(g0, min(g0 + group, n_train))]
@@ -468,8 +473,9 @@ def run_learned(args, ss, torch, dev, stream, world, rank):
         cleans = []
         for j, c in enumerate(clips):
             r, d = torch.from_numpy(c.rgb).to(dev), torch.from_numpy(c.depth).to(dev)
-            ss.ssvp_load_clip(ctx, j, c.W, c.H, c.F, r, d)
-            ss.ssvp_set_cameras(ctx, j, c.K, 1, c.w2c)
+            for cx in (ctx, ctx_s) if ctx_s else (ctx,):
+                ss.ssvp_load_clip(cx, j, c.W, c.H, c.F, r, d)
+                ss.ssvp_set_cameras(cx, j, c.K, 1, c.w2c)
             cleans.append(torch.from_numpy(c.clean).to(dev))
         cfg = ss.ssvp_train_config(steps=steps_per_group, batch_pixels=16384, lr=1e-3, bce_weight=0.1,
                                    seed=g0, init=1 if g0 == 0 else 0)
@@ -477,29 +483,36 @@ def run_learned(args, ss, torch, dev, stream, world, rank):
         t0 = time.perf_counter()
         losses += list(ss.ssvp_train(ctx, p, list(range(len(clips))), cleans, cfg))
         t_train += time.perf_counter() - t0
+        if ctx_s:
+            losses_s += list(ss.ssvp_train(ctx_s, p_s, list(range(len(clips))), cleans, cfg))
         for j in range(len(clips)):
-            ss.ssvp_unload_clip(ctx, j)
+            for cx in (ctx, ctx_s) if ctx_s else (ctx,):
+                ss.ssvp_unload_clip(cx, j)
     clip = _workload_clip(seed=rank)
     r, d = torch.from_numpy(clip.rgb).to(dev), torch.from_numpy(clip.depth).to(dev)
     ss.ssvp_load_clip(ctx, 0, W, H, F, r, d)
     ss.ssvp_set_cameras(ctx, 0, clip.K, 1, clip.w2c)
+    if ctx_s:
+        ss.ssvp_load_clip(ctx_s, 0, W, H, F, r, d)
+        ss.ssvp_set_cameras(ctx_s, 0, clip.K, 1, clip.w2c)
     del r, d
     p.frame_begin, p.frame_end = O_BEGIN, O_BEGIN + N_OUT
+    p_s.frame_begin, p_s.frame_end = O_BEGIN, O_BEGIN + N_OUT
 
-    def timed(mode, steps):
-        p.mode = mode
+    def timed(mode, steps, cx=ctx, pp=p):
+        pp.mode = mode
         for _ in range(args.warmup):
-            ss.ssvp_gather_filter(ctx, p, [0])
+            ss.ssvp_gather_filter(cx, pp, [0])
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(steps):
-            ss.ssvp_gather_filter(ctx, p, [0])
+            ss.ssvp_gather_filter(cx, pp, [0])
         b.record(stream)
         torch.cuda.synchronize()
         out = torch.empty((N_OUT, H, W, 3), dtype=torch.float32, device=dev)
-        ss.ssvp_read_output(ctx, 0, O_BEGIN, O_BEGIN + N_OUT, out)
-        ss.ssvp_sync(ctx)
+        ss.ssvp_read_output(cx, 0, O_BEGIN, O_BEGIN + N_OUT, out)
+        ss.ssvp_sync(cx)
         return a.elapsed_time(b) / steps, out.cpu().numpy()
 
     with ClockSampler(local) as clk:
@@ -508,6 +521,17 @@ def run_learned(args, ss, torch, dev, stream, world, rank):
     clean = clip.clean[O_BEGIN:O_BEGIN + N_OUT]
     psnr = lambda a_: float(10 * np.log10(1.0 / np.mean((a_.astype(np.float64) - clean) ** 2)))
     mpix = N_OUT * W * H / 1e6
+    short = None
+    if ctx_s:
+        ms_ls, out_ls = timed(ss.SSVP_MODE_LEARNED, args.steps, ctx_s, p_s)
+        ms_ps, out_ps = timed(ss.SSVP_MODE_DENOISE, args.steps, ctx_s, p_s)
+        short = {"half_window": TS, "learned": {"value": world * mpix / (ms_ls / 1e3), "unit": "Mpix/s",
+                                                 "ms_per_step": ms_ls, "psnr_db": psnr(out_ls)},
+                 "plain_same_window": {"value": world * mpix / (ms_ps / 1e3), "unit": "Mpix/s", "psnr_db": psnr(out_ps)},
+                 "loss_last_40": float(np.mean(losses_s[-40:])),
+                 "note": "the same method and training clips with a +-%d window and its own network, against the "
+                         "plain +-%d form above (an operating point, not the workload's configuration)" % (TS, T)}
+        ss.ssvp_destroy(ctx_s)
     line = {
         "metric": METRIC, "value": world * mpix / (ms_l / 1e3), "unit": "Mpix/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
@@ -520,6 +544,7 @@ def run_learned(args, ss, torch, dev, stream, world, rank):
         "psnr_db": {"learned_vs_clean": psnr(out_l), "plain_vs_clean": psnr(out_p),
                     "input_vs_clean": psnr(clip.rgb[O_BEGIN:O_BEGIN + N_OUT])},
         "plain_same_run": {"value": world * mpix / (ms_p / 1e3), "unit": "Mpix/s", "ms_per_step": ms_p},
+        "learned_short_window": short,
         "gpu_launches": args.steps * N_OUT * 2,
         "clocks": clk.summary(),
     }
@@ -695,6 +720,8 @@ def main():
     ap.add_argument("--workload", default="fhd", choices=sorted(WORKLOADS))
     ap.add_argument("--out-frames", type=int, default=None, help="output frames per step (default per workload)")
     ap.add_argument("--train-clips", type=int, default=200, help="learned workload: generated training clips")
+    ap.add_argument("--learned-short-window", type=int, default=8,
+                    help="learned workload: also train and time a network at this half window (0: off)")
     args = ap.parse_args()
     global W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE
     W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE = WORKLOADS[args.workload]
