@@ -95,6 +95,10 @@ enum {
  *                 and its O depth range (0 < near < far; the paper uses 0.01 and 1000)
  *   sigma_area    ssvp_superres only: length scale of Eq. 7's area term (scene units); <= 0 means
  *                 one input-pixel footprint at the median depth (median depth / fx of O)
+ *   test_skip_mma 0 normally.  1 (a test of the time-out path, learned mode only): the learned
+ *                 inference issues none of its tensor-core products, so its bounded waits for
+ *                 them run out (within about 1 s each); ssvp_sync then returns SSVP_ETIMEOUT, the
+ *                 outputs of the call are not valid, and the context stays usable.
  *   membership_out   optional device buffer (debug): per crop pixel (row-major) and per slot
  *                 j = 0..2T (J = O-T+j) a record of 3 + ceil(k*k/32) int32 words:
  *                 status (-2 invalid reference depth, -1 J outside the clip, 0 J skipped: the
@@ -135,6 +139,7 @@ typedef struct ssvp_params {
     float near_plane;
     float far_plane;
     float sigma_area;
+    int32_t test_skip_mma;
     void *membership_out;
     void *pixel_stats_out;
 } ssvp_params;
@@ -365,7 +370,7 @@ int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median);
 
 /* Wait for all work queued on the context's stream; returns the first pending error, or
  * SSVP_ETIMEOUT when a kernel's bounded wait for its tensor-core products gave up since the last
- * call (the learned inference waits on an MMA-completion barrier with a limit of about 2 s; the
+ * call (the learned inference waits on an MMA-completion barrier with a limit of about 1 s; the
  * outputs of that launch are then not valid).  The time-out is reported once. */
 int ssvp_sync(ssvp_ctx *ctx);
 

@@ -39,7 +39,8 @@ class ssvp_params(ctypes.Structure):
                 ("focal_depth", ctypes.c_float), ("a0", ctypes.c_float), ("lens_samples", ctypes.c_int32),
                 ("cap", ctypes.c_int32), ("max_samples", ctypes.c_int32), ("conf_threshold", ctypes.c_float),
                 ("gather", ctypes.c_int32), ("frustum_l", ctypes.c_float), ("near_plane", ctypes.c_float),
-                ("far_plane", ctypes.c_float), ("sigma_area", ctypes.c_float), ("membership_out", ctypes.c_void_p),
+                ("far_plane", ctypes.c_float), ("sigma_area", ctypes.c_float), ("test_skip_mma", ctypes.c_int32),
+                ("membership_out", ctypes.c_void_p),
                 ("pixel_stats_out", ctypes.c_void_p)]
 
 

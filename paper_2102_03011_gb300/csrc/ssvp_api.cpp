@@ -732,6 +732,7 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         if (!ctx->mlp_set) return fail(ctx, SSVP_EINVAL, "learned mode needs a network (ssvp_set_mlp or ssvp_train)");
         if (p.k > 7) return fail(ctx, SSVP_EINVAL, "the learned filter supports k <= 7");
         if (p.membership_out || p.pixel_stats_out) return fail(ctx, SSVP_EINVAL, "learned mode has no debug outputs");
+        if (p.test_skip_mma != 0 && p.test_skip_mma != 1) return fail(ctx, SSVP_EINVAL, "test_skip_mma must be 0 or 1");
         CK(cudaMemsetAsync(ctx->stat_counts, 0, 2 * sizeof(unsigned long long), ctx->stream), "cudaMemsetAsync");
         CK(cudaMemsetAsync(ctx->stat_sumw, 0, sizeof(double), ctx->stream), "cudaMemsetAsync");
         for (int i = 0; i < n_clips; ++i) {
@@ -749,6 +750,7 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
                 m.O = O; m.W = c.p.W; m.H = c.p.H; m.x0 = cx0[i]; m.y0 = cy0[i]; m.cw = cw[i];
                 m.tau = p.conf_threshold;
                 m.out = c.p.out;
+                m.skip_mma = p.test_skip_mma;
                 CK(ssvp::launch_mlp_infer_tc(m, ctx->d_kerr, ctx->stream), "mlp inference kernel");
             }
         }

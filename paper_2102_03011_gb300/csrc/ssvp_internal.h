@@ -142,6 +142,7 @@ struct MlpArgs {
     const float *clean;           // training: target frames (F x H x W x 3, FP32)
     float bce_w;
     float *grad;                  // training: kMlpParams + 1 accumulators
+    int skip_mma;                 // inference: issue no tensor-core products (test of the time-out path)
 };
 
 // learned inference on the tcgen05 tensor cores; err (device word) is raised if one of its bounded

@@ -15,8 +15,8 @@
 //   4. four tcgen05.mma (K = 16 each): D2 (128 x 16, columns 0 and 1 used) = H W2^T;
 //   5. each thread reads (z_w, z_c) of its row, adds b2, and forms softplus / sigmoid; the two
 //      warps of each pixel reduce the weighted sums.
-// The arithmetic is that of the mma.sync kernels: BF16 operands, FP32 accumulation, h rounded to
-// BF16 before layer 2.  Waits on the MMA-completion barrier are bounded: on a time-out the kernel
+// The arithmetic is that of the training kernel's forward pass (ssvp_mlp.cu): BF16 operands,
+// FP32 accumulation, h rounded to BF16 before layer 2.  Waits on the MMA-completion barrier are bounded: on a time-out the kernel
 // raises the error word, leaves its loop, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
@@ -42,8 +42,8 @@ constexpr int kSmBytes = 51200;
 // one wave on 152 SMs), so their 4 x 128 tensor-memory columns always fit in the SM's 512
 constexpr int kSmRequest = kSmBytes;
 // a waiting thread suspends in try_wait for up to kWaitHintNs per poll; kWaitLimit polls (about
-// 2 s) before a wait counts as timed out
-constexpr unsigned kWaitHintNs = 100000, kWaitLimit = 20000;
+// 1 s) before a wait counts as timed out
+constexpr unsigned kWaitHintNs = 100000, kWaitLimit = 10000;
 
 __device__ __forceinline__ unsigned core_off(int r, int kc, int k_chunks) {
     return (unsigned)(((r >> 3) * k_chunks + kc) * 128 + (r & 7) * 16);
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpAr
         fence_before();
         __syncthreads();
         if (s_bad) return false;  // uniform: written only between the second barrier and the next first one
-        if (tid == 0) {
+        if (tid == 0 && !m.skip_mma) {
             fence_after();
             mma_tc(d_st, smem_desc(a1, 128, 256), dB1, id1, 0);
             mma_tc(d_st, dA0, dB0, id1, 1);
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpAr
         fence_async_smem();
         fence_before();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !m.skip_mma) {
             fence_after();
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
@@ -461,15 +461,12 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpAr
 
 cudaError_t launch_mlp_infer_tc(const MlpArgs &m, int *err, cudaStream_t s) {
     if (m.n_px <= 0) return cudaSuccess;
-    static int configured_device = -1;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (configured_device != dev) {
-        e = cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmRequest);
-        if (e != cudaSuccess) return e;
-        configured_device = dev;
-    }
+    // more than the default 48 KB of dynamic shared memory (a per-device attribute; cheap to repeat)
+    e = cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmRequest);
+    if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const long long pairs = (m.n_px + 1) / 2;

@@ -142,6 +142,28 @@ def test_tensor_core_inference_on_odd_crops_empty_and_short_sets(sess, clip, cro
     assert worst <= 1e-3, worst
 
 
+def test_tensor_core_wait_times_out_and_the_context_recovers(sess, clip):
+    """The inference kernel's waits for its tensor-core products are bounded: with the products
+    left out (the test flag), each wait runs out after about a second, ssvp_sync reports
+    SSVP_ETIMEOUT once, and the next call on the same context gives the normal result."""
+    ss = sess.ss
+    sess.load(45, clip)
+    W1, b1, W2, b2 = oracle.he_init(9)
+    ss.ssvp_set_mlp(sess.ctx, W1, b1, W2, b2)
+    crop = (10, 10, 16, 4)  # 64 pixels: 32 CTAs, each times out once per wait
+    want = sess.run(45, 5, crop=crop, mode=2, k=5, half_window=4).rgb
+    p = sess.params(mode=2, k=5, half_window=4, frame_begin=5, frame_end=6, crop_x=10, crop_y=10, crop_w=16,
+                    crop_h=4)
+    p.test_skip_mma = 1
+    ss.ssvp_gather_filter(sess.ctx, p, [45])
+    with pytest.raises(ss.SsvpError) as e:
+        ss.ssvp_sync(sess.ctx)
+    assert e.value.code == ss.SSVP_ETIMEOUT and "timed out" in str(e.value)
+    ss.ssvp_sync(sess.ctx)  # reported once
+    again = sess.run(45, 5, crop=crop, mode=2, k=5, half_window=4).rgb
+    np.testing.assert_array_equal(again, want)
+
+
 def test_high_threshold_reproduces_the_plain_denoiser(sess, clip):
     sess.load(40, clip)
     W1, b1, W2, b2 = oracle.he_init(5)
