@@ -139,7 +139,7 @@ __device__ __forceinline__ bool lateral_fast(const float *M, const float *e, flo
 }
 
 template <int CFMT, bool DEBUG, bool SR, bool INP>
-__global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a) {
+__global__ void __launch_bounds__(kFrThreads, 3) frustum_kernel(const GatherArgs a) {
     __shared__ float s_const[4];
     __shared__ unsigned long long s_cnt[2][kFrThreads / 32];
     __shared__ float s_w[kFrThreads / 32];
@@ -352,6 +352,14 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
             const long long mstep = hb.xmajor ? 1ll : (long long)P.pitch;
             const long long nstep = hb.xmajor ? (long long)P.pitch : 1ll;
             const float *plane = P.depth + fbase + (long long)kPad * P.pitch + kPad;
+            // The test in the form |h1 + h2| < L h3 and |h1 - h2| < L h3 (|h1| + |h2| is the larger of
+            // |h1 + h2| and |h1 - h2|), with the sums and differences of the coefficients taken once,
+            // so that two candidates share each packed FP32x2 operation and the comparisons keep
+            // their free absolute values
+            const f32x2 sp2 = f2_pack(sm1 + sm2, sm1 + sm2), sq2 = f2_pack(sm1 - sm2, sm1 - sm2),
+                        s32 = f2_pack(sm3, sm3);
+            const f32x2 Ep2 = f2_pack(E1 + E2, E1 + E2), Eq2 = f2_pack(E1 - E2, E1 - E2), E32 = f2_pack(E3, E3);
+            const f32x2 L2 = f2_pack(L, L), off01 = f2_pack(0.0f, 1.0f), off23 = f2_pack(2.0f, 3.0f);
             for (int n = r0; n <= r1; ++n) {
                 const float fn = (float)n;
                 int ma = m0, mb = m1;
@@ -364,9 +372,10 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
                 if (ma > mb) continue;
                 if (pass == 0) n_exam += mb - ma + 1;
                 const float b1 = fmaf(sn1, fn, R1[2]), b2 = fmaf(sn2, fn, R2[2]), b3 = fmaf(sn3, fn, R3[2]);
+                const f32x2 bp2 = f2_pack(b1 + b2, b1 + b2), bq2 = f2_pack(b1 - b2, b1 - b2), b32 = f2_pack(b3, b3);
                 const float *rowp = plane + (long long)n * nstep;
                 // test up to 32 candidates of the run into a hit mask (no branch per candidate),
-                // then take the hits; the same arithmetic on the same operands gives the same h
+                // then take the hits (their h1, h2, h3 for the weights are computed again in FP32)
                 for (int mc0 = ma; mc0 <= mb; mc0 += 32) {
                     const int cnt = min(mb - mc0, 31);
                     const float *dp = rowp + (long long)mc0 * mstep;
@@ -380,16 +389,28 @@ __global__ void __launch_bounds__(kFrThreads) frustum_kernel(const GatherArgs a)
 #pragma unroll
                         for (int i = 0; i < 4; ++i) dq[i] = __ldg(dp + i * mstep);
                         unsigned int bits = 0u;
+                        const f32x2 fm2 = f2_pack(fm, fm);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float fmi = fm + (float)i;
-                            const float h1 = fmaf(dq[i], fmaf(sm1, fmi, b1), E1);
-                            const float h2 = fmaf(dq[i], fmaf(sm2, fmi, b2), E2);
-                            const float h3 = fmaf(dq[i], fmaf(sm3, fmi, b3), E3);
+                        for (int pr = 0; pr < 2; ++pr) {
+                            const f32x2 fmp = f2_add(fm2, pr == 0 ? off01 : off23);
+                            const f32x2 d2 = f2_pack(dq[2 * pr], dq[2 * pr + 1]);
+                            const f32x2 sv = f2_fma(d2, f2_fma(sp2, fmp, bp2), Ep2);  // h1 + h2
+                            const f32x2 tv = f2_fma(d2, f2_fma(sq2, fmp, bq2), Eq2);  // h1 - h2
+                            const f32x2 h3 = f2_fma(d2, f2_fma(s32, fmp, b32), E32);
+                            const f32x2 cv = f2_mul(L2, h3);
+                            float sa, sb, ta, tb, ca, cb;
+                            f2_unpack(sv, sa, sb);
+                            f2_unpack(tv, ta, tb);
+                            f2_unpack(cv, ca, cb);
                             // NaN depth fails the comparisons
-                            bool t = fabsf(h1) + fabsf(h2) < L * h3;
-                            if (check_nf) t = t && fabsf(h3 - zmid) < zhalf;
-                            bits |= (unsigned int)t << i;
+                            bool t0 = fabsf(sa) < ca && fabsf(ta) < ca, t1 = fabsf(sb) < cb && fabsf(tb) < cb;
+                            if (check_nf) {
+                                float h3a, h3b;
+                                f2_unpack(h3, h3a, h3b);
+                                t0 = t0 && fabsf(h3a - zmid) < zhalf;
+                                t1 = t1 && fabsf(h3b - zmid) < zhalf;
+                            }
+                            bits |= ((unsigned int)t0 << (2 * pr)) | ((unsigned int)t1 << (2 * pr + 1));
                         }
                         // keep the bits of candidates inside the run (k + i <= cnt)
                         bits &= (2u << min(cnt - k, 3)) - 1u;
