@@ -238,7 +238,10 @@ int ssvp_set_stream(ssvp_ctx *ctx, void *cuda_stream);
  * (SSVP_COLOUR_F32 or SSVP_COLOUR_F16, round to nearest even); depth is always stored as FP32.
  * The lower-median valid depth is computed on the device for relative radii.
  * Sizes: 1 <= W, H <= 16384, 1 <= F <= 65535.  The copy is queued: the caller's buffers may be
- * reused once the context's stream has passed this call (ssvp_sync() waits for it).
+ * reused once the context's stream has passed this call (ssvp_sync() waits for it).  Reloading
+ * an id with the same W, H, F and colour_fmt (and no inpainting mask set) reuses its device
+ * planes without allocating; work already queued on the stream still sees the old contents.
+ * Any reload invalidates batched plans that include the id.
  */
 int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float *rgb, const float *depth,
                    int mem_kind, int colour_fmt);

@@ -589,7 +589,11 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
         return fail(ctx, SSVP_EINVAL, "bad colour_fmt %d", colour_fmt);
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     Clip &c = ctx->clips[clip_id];
-    if (c.loaded) {
+    // a reload with the same shape and format (and no inpainting mask) keeps the planes: the work
+    // queued on the context's stream that still reads them runs before the new upload
+    const bool reuse = c.loaded && c.p.W == W && c.p.H == H && c.p.F == F && c.p.colour_fmt == colour_fmt &&
+                       c.p.mask == nullptr;
+    if (c.loaded && !reuse) {
         CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
         free_clip(c);
     }
@@ -604,15 +608,15 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
     const size_t texel = colour_fmt == SSVP_COLOUR_F32 ? 16 : 8;
     const size_t nplane = (size_t)F * (size_t)p.fstride;
     const size_t nout = (size_t)F * H * W * 3;
-    cudaError_t e;
-    if ((e = cudaMalloc(&p.depth, nplane * sizeof(float))) != cudaSuccess ||
+    cudaError_t e = cudaSuccess;
+    if (!reuse && ((e = cudaMalloc(&p.depth, nplane * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&p.colour, nplane * texel)) != cudaSuccess ||
         (e = cudaMalloc(&p.out, nout * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&p.median, sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&p.zrange, 2 * sizeof(unsigned int) * (size_t)F)) != cudaSuccess ||
         (e = cudaMalloc(&p.grad_sum, sizeof(double) * (size_t)F)) != cudaSuccess ||
         (e = cudaMalloc(&p.grad_log2, sizeof(float) * (size_t)F)) != cudaSuccess ||
-        (e = cudaMalloc(&p.grad_partial, sizeof(double) * ssvp::grad_partial_words(F))) != cudaSuccess) {
+        (e = cudaMalloc(&p.grad_partial, sizeof(double) * ssvp::grad_partial_words(F))) != cudaSuccess)) {
         free_clip(c);
         return cuda_fail(ctx, e, "cudaMalloc (clip planes)");
     }

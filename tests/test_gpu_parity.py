@@ -161,6 +161,20 @@ def test_host_upload_matches_device_upload(sess, tiny):
     np.testing.assert_array_equal(a, b)
 
 
+def test_reload_with_the_same_shape_replaces_the_contents(sess, tiny):
+    """A reload of an id with the same shape keeps the device planes: the new frames, depths,
+    cameras and median must replace the old ones completely (also through a host upload)."""
+    other = synth.make_clip("room", tiny.W, tiny.H, tiny.F, seed=9)
+    sess.load(9, other)
+    want_other = sess.run(9, 8, k=5, half_window=15).rgb
+    sess.load(9, tiny)  # same W, H, F and format: the planes are reused
+    assert sess.ss.ssvp_clip_median_depth(sess.ctx, 9) == oracle.median_depth(tiny.depth)
+    sess.load(10, tiny)  # a fresh id for the reference
+    np.testing.assert_array_equal(sess.run(9, 8, k=5, half_window=15).rgb, sess.run(10, 8, k=5, half_window=15).rgb)
+    sess.load(9, other, host=True)
+    np.testing.assert_array_equal(sess.run(9, 8, k=5, half_window=15).rgb, want_other)
+
+
 def test_launch_stats_match_oracle(sess, tiny):
     sess.load(0, tiny)
     g, o = _both(sess, tiny, 0, 8, k=5, T=15)
