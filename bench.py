@@ -868,25 +868,58 @@ def main():
     out_h = torch.empty((N_OUT, H, W, 3), dtype=torch.float32).pin_memory()
     e2e_steps = max(2, min(args.steps, 5))
 
-    def e2e_step():
-        ss.ssvp_load_clip(ctx, 1, W, H, F, rgb_h, dep_h, ss.SSVP_MEM_HOST, cfmt)
-        ss.ssvp_set_cameras(ctx, 1, clip.K, 1, clip.w2c)
-        if MODE == 8:
-            ss.ssvp_mask_from_box(ctx, 1, _inpaint_box(clip))
-        ss.ssvp_gather_filter(ctx, p, [1])
-        ss.ssvp_read_output(ctx, 1, O_BEGIN, O_BEGIN + N_OUT, out_h, ss.SSVP_MEM_HOST)
+    # Steps alternate between two contexts on two streams (double buffering, as a streaming
+    # deployment would): step i + 1's upload and gather are queued before step i's output is read
+    # back to the host, so the copies of one step overlap the kernels of the other.  Every step
+    # still uploads its own inputs and reads back its own result inside the timed region.
+    # Inpainting re-creates its mask per step, which reallocates: it runs the steps one after
+    # another on one context.
+    pipelined = MODE != 8
+    stream2 = torch.cuda.Stream(dev) if pipelined else stream
+    ctx2 = ss.ssvp_create(local, stream2) if pipelined else ctx
+    ctxs, streams = (ctx, ctx2), (stream, stream2)
+    out_hs = (out_h, torch.empty_like(out_h).pin_memory() if pipelined else out_h)
 
-    e2e_step()
+    def issue(i):
+        cx = ctxs[i % 2]
+        ss.ssvp_load_clip(cx, 1, W, H, F, rgb_h, dep_h, ss.SSVP_MEM_HOST, cfmt)
+        ss.ssvp_set_cameras(cx, 1, clip.K, 1, clip.w2c)
+        if MODE == 8:
+            ss.ssvp_mask_from_box(cx, 1, _inpaint_box(clip))
+        ss.ssvp_gather_filter(cx, p, [1])
+
+    def read_back(i):  # waits for step i on its stream
+        ss.ssvp_read_output(ctxs[i % 2], 1, O_BEGIN, O_BEGIN + N_OUT, out_hs[i % 2], ss.SSVP_MEM_HOST)
+
+    def e2e_run(n):
+        issue(0)
+        for i in range(1, n):
+            if pipelined:
+                issue(i)
+                read_back(i - 1)
+            else:
+                read_back(i - 1)
+                issue(i)
+        read_back(n - 1)
+
+    e2e_run(2)  # both contexts hold the clip's planes: later reloads reuse them
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
+    if pipelined:
+        stream2.wait_event(e0)
+    e2e_run(e2e_steps)
+    if pipelined:
+        done2 = torch.cuda.Event()
+        done2.record(stream2)
+        stream.wait_event(done2)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
+    if pipelined:
+        ss.ssvp_destroy(ctx2)
     h2d = clip.rgb.nbytes + clip.depth.nbytes
     d2h = out_h.numel() * 4
     frames_per_chunk = max(1, min(F, (256 << 20) // (W * H * 16)))
@@ -932,7 +965,9 @@ def main():
                          "frac": examined * alu_ops / (kernel_ms / 1e3) / 1e12 / fp32_peak,
                          "accounting": alu_note + "; peak = 152 SMs x 128 FP32 lanes x median SM clock"},
         "e2e": {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "gpu_launches_per_step": e2e_launches},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "gpu_launches_per_step": e2e_launches,
+                "pipelining": "two contexts on two streams, step i + 1 queued before step i is read back"
+                              if pipelined else "none"},
         "clocks": clk_summary,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
