@@ -877,6 +877,8 @@ def main():
     pipelined = MODE != 8
     stream2 = torch.cuda.Stream(dev) if pipelined else stream
     ctx2 = ss.ssvp_create(local, stream2) if pipelined else ctx
+    if pipelined and MODE == 6:  # the context's own state: the Eq. 10 shutter table
+        ss.ssvp_set_shutter(ctx2, _shutter_xi(), T)
     ctxs, streams = (ctx, ctx2), (stream, stream2)
     out_hs = (out_h, torch.empty_like(out_h).pin_memory() if pipelined else out_h)
 
