@@ -16,8 +16,9 @@
 //   5. each thread reads (z_w, z_c) of its row, adds b2, and forms softplus / sigmoid; the two
 //      warps of each pixel reduce the weighted sums.
 // The arithmetic is that of the training kernel's forward pass (ssvp_mlp.cu): BF16 operands,
-// FP32 accumulation, h rounded to BF16 before layer 2.  Waits on the MMA-completion barrier are bounded: on a time-out the kernel
-// raises the error word, leaves its loop, frees its tensor memory and returns.
+// FP32 accumulation, h rounded to BF16 before layer 2.  Waits on the MMA-completion barrier are
+// bounded: on a time-out the kernel raises the error word, leaves its loop, frees its tensor
+// memory and returns.
 #include <cuda_bf16.h>
 
 #include "ssvp_internal.h"
