@@ -175,6 +175,39 @@ def test_reload_with_the_same_shape_replaces_the_contents(sess, tiny):
     np.testing.assert_array_equal(sess.run(9, 8, k=5, half_window=15).rgb, want_other)
 
 
+def test_empty_frame_range_is_a_no_op(sess, tiny):
+    """frame_begin == frame_end: nothing is gathered, the output and the statistics stay as they are."""
+    ss = sess.ss
+    sess.load(0, tiny)
+    before = sess.run(0, 4, k=5, half_window=2).rgb
+    ss.ssvp_gather_filter(sess.ctx, sess.params(k=5, half_window=2, frame_begin=4, frame_end=4), [0])
+    ss.ssvp_sync(sess.ctx)
+    assert ss.ssvp_read_stats(sess.ctx) == (0, 0, 0.0)
+    t = sess.torch
+    out = t.empty((1, tiny.H, tiny.W, 3), dtype=t.float32, device=sess.dev)
+    ss.ssvp_read_output(sess.ctx, 0, 4, 5, out)
+    ss.ssvp_sync(sess.ctx)
+    np.testing.assert_array_equal(out.cpu().numpy()[0], before)
+
+
+def test_one_pixel_clip(sess):
+    """A 1 x 1 clip: every window is the image border; the pixel keeps only its own sample."""
+    c = synth.make_clip("planes3", 1, 1, 4, seed=3)
+    sess.load(11, c)
+    for O in range(c.F):
+        g, o = _both(sess, c, 11, O, k=3, T=2)
+        compare(g, o, 3)
+        np.testing.assert_array_equal(g.rgb, c.rgb[O])
+
+
+def test_window_beyond_the_clip_equals_the_clipped_window(sess, tiny):
+    """T = 127 on a 16-frame clip gathers the same frames, in the same order, as T = 8 at O = 8."""
+    sess.load(0, tiny)
+    a = sess.run(0, 8, k=5, half_window=8).rgb
+    b = sess.run(0, 8, k=5, half_window=127).rgb
+    np.testing.assert_array_equal(a, b)
+
+
 def test_launch_stats_match_oracle(sess, tiny):
     sess.load(0, tiny)
     g, o = _both(sess, tiny, 0, 8, k=5, T=15)
