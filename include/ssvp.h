@@ -389,17 +389,20 @@ int ssvp_sync(ssvp_ctx *ctx);
  * bytes of histogram and bookkeeping) in a fixed array in the library's device memory, which
  * every GPU that loads the library holds until the process exits.  No context is needed.
  *
- *   depth_dev   n floats in device memory of the current CUDA device (any layout; invalid
- *               values are ignored)
+ *   depth_dev   n floats in device (or managed) memory of the current CUDA device (any layout;
+ *               invalid values are ignored); a host address returns SSVP_EINVAL
  *   n           1 <= n <= 4294967295 (the scratch counts in 32-bit words); other sizes return
  *               SSVP_EINVAL with a message in ssvp_last_error(NULL)
- *   median_dev  one float in device memory: the median, or NaN when no value is valid
+ *   median_dev  one float in device (or managed) memory: the median, or NaN when no value is
+ *               valid; a host address returns SSVP_EINVAL
  *   cuda_stream stream to queue the work on (NULL: legacy default stream); asynchronous
  *
  * The first call on a device looks up the scratch array's device address for that device (the
- * device must be current); make that first call before any stream capture.  All calls share
- * the one array: each call clears it before use, and calls whose work overlaps on the GPU (for
- * example on two streams at once) race on it and give wrong results.
+ * device must be current); make that first call before any stream capture.  The address is kept
+ * for the life of the process, so the library must not be used on a device after a
+ * cudaDeviceReset of it.  All calls share the one array: each call clears it before use, and
+ * calls whose work overlaps on the GPU (for example on two streams at once) race on it and give
+ * wrong results.
  */
 int ssvp_median_depth_noalloc(const float *depth_dev, unsigned long long n, float *median_dev, void *cuda_stream);
 

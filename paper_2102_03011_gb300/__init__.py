@@ -263,10 +263,28 @@ def ssvp_sync(ctx) -> None:
     _check(ctx, lib.ssvp_sync(ctx))
 
 
+def _device_f32(x, name, need):
+    """Address of a contiguous CUDA float32 tensor on the current device holding >= need values."""
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (device memory), not {type(x).__name__}")
+    if x.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32, not {x.dtype}")
+    if x.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {x.device}, the current device is cuda:{torch.cuda.current_device()}")
+    if x.numel() < need:
+        raise ValueError(f"{name} holds {x.numel()} values, {need} are needed")
+    return _ptr(x)[0]
+
+
 def ssvp_median_depth_noalloc(depth_dev, n: int, median_dev, cuda_stream=None) -> None:
-    """Median of a device array with the library's fixed scratch (no allocation); see ssvp.h."""
-    pd, _ = _ptr(depth_dev)
-    pm, _ = _ptr(median_dev)
+    """Median of a device array with the library's fixed scratch (no allocation); see ssvp.h.
+    depth_dev and median_dev must be float32 CUDA tensors on the current device; n values of
+    depth_dev are read (n <= depth_dev.numel())."""
+    pm = _device_f32(median_dev, "median_dev", 1)
+    pd = _device_f32(depth_dev, "depth_dev", 0)
+    if int(n) > depth_dev.numel():
+        raise ValueError(f"n={int(n)} exceeds depth_dev's {depth_dev.numel()} values")
     s = cuda_stream.cuda_stream if hasattr(cuda_stream, "cuda_stream") else cuda_stream
     _check(None, lib.ssvp_median_depth_noalloc(pd, int(n), pm, s))
 

@@ -226,7 +226,9 @@ static __device__ __align__(256) unsigned int g_median_scratch[kHistWords + 4];
 namespace {
 
 // Device address of g_median_scratch, looked up once per device.  In host code the symbol's
-// name is only a host-side stand-in; a kernel must be given this address instead.
+// name is only a host-side stand-in; a kernel must be given this address instead.  The cached
+// address belongs to the device's current context: the library must not be used across a
+// cudaDeviceReset of that device (the module, and with it the array, is then loaded anew).
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 unsigned int *g_scratch_ptr[kMaxDevices] = {};
@@ -261,6 +263,19 @@ extern "C" int ssvp_median_depth_noalloc(const float *depth_dev, unsigned long l
         ssvp::set_global_error("ssvp_median_depth_noalloc: n=%llu outside [1, %llu]: the fixed scratch counts "
                                "values in 32-bit words", n, (unsigned long long)ssvp::kMedianNoallocMax);
         return SSVP_EINVAL;
+    }
+    // both pointers must be memory the current device can read and write: a host address would
+    // fault inside the kernels, so it is refused here
+    for (int i = 0; i < 2; ++i) {
+        const void *ptr = i == 0 ? (const void *)depth_dev : (const void *)median_dev;
+        cudaPointerAttributes at{};
+        const cudaError_t pe = cudaPointerGetAttributes(&at, ptr);
+        if (pe != cudaSuccess || (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            ssvp::set_global_error("ssvp_median_depth_noalloc: %s is not device or managed memory",
+                                   i == 0 ? "depth_dev" : "median_dev");
+            return SSVP_EINVAL;
+        }
     }
     unsigned int *scratch = nullptr;
     cudaError_t e = ssvp::median_scratch_for_current_device(&scratch);

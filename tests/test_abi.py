@@ -74,3 +74,14 @@ def test_create_without_device_reports_edevice(ss):
     with pytest.raises(ss.SsvpError) as e:
         ss.ssvp_create(0, None)
     assert e.value.code == ss.SSVP_EDEVICE
+
+
+def test_noalloc_median_refuses_host_arrays_before_any_launch(ss):
+    """The allocation-free median takes device memory only: host arrays and CPU tensors are
+    refused by the binding before the library is called (no GPU needed)."""
+    import numpy as np
+    import torch
+    with pytest.raises(TypeError):
+        ss.ssvp_median_depth_noalloc(np.ones(8, np.float32), 8, np.zeros(1, np.float32))
+    with pytest.raises(TypeError):
+        ss.ssvp_median_depth_noalloc(torch.ones(8), 8, torch.zeros(1))
