@@ -106,7 +106,7 @@ def _load():
                                      dp, dp]
         lib.oc_mlp_pixel.restype = ctypes.c_double
         lib.oc_mlp_loss_grad.argtypes = [ctypes.c_int, dp, dp, i32p, dp, dp, dp, dp, dp, dp, ctypes.c_int,
-                                         ctypes.c_double, dp, dp, dp, dp]
+                                         ctypes.c_double, dp, dp, dp, dp, dp, dp, dp, dp]
         lib.oc_mlp_loss_grad.restype = ctypes.c_double
         _lib = lib
     return _lib
@@ -422,19 +422,21 @@ def mlp_pixel(feat, col, n, W1, b1, W2, b2, round_bf16=True, tau=0.5, plain=None
     return ol, of, conf, z[:n]
 
 
-def mlp_loss_grad(feat, col, nsamp, plain, clean, W1, b1, W2, b2, round_bf16=True, bce_w=0.1):
+def mlp_loss_grad(feat, col, nsamp, plain, clean, W1, b1, W2, b2, round_bf16=True, bce_w=0.1, term_scale=False):
     """Loss and gradients over pixels: feat (P, 64, 16), col (P, 64, 3), nsamp (P,), plain (P, 3),
-    clean (P, 3) -> (L, gW1 (64, 16), gb1 (64,), gW2 (2, 64), gb2 (2,))."""
+    clean (P, 3) -> (L, gW1 (64, 16), gb1 (64,), gW2 (2, 64), gb2 (2,)).  With term_scale, also
+    the per-entry sums of the absolute values of the terms (same shapes), appended."""
     feat, col, plain, clean = _d(feat), _d(col), _d(plain), _d(clean)
     nsamp = np.ascontiguousarray(nsamp, dtype=np.int32)
     W1, b1, W2, b2 = _d(W1), _d(b1), _d(W2), _d(b2)
     g = [np.zeros((N_HID, N_FEAT)), np.zeros(N_HID), np.zeros((2, N_HID)), np.zeros(2)]
+    a = [np.zeros((N_HID, N_FEAT)), np.zeros(N_HID), np.zeros((2, N_HID)), np.zeros(2)] if term_scale else [None] * 4
     L = _load().oc_mlp_loss_grad(len(nsamp), _p(feat, ctypes.c_double), _p(col, ctypes.c_double),
                                  _p(nsamp, ctypes.c_int32), _p(plain, ctypes.c_double), _p(clean, ctypes.c_double),
                                  _p(W1, ctypes.c_double), _p(b1, ctypes.c_double), _p(W2, ctypes.c_double),
                                  _p(b2, ctypes.c_double), int(round_bf16), float(bce_w),
-                                 *[_p(x, ctypes.c_double) for x in g])
-    return (L, *g)
+                                 *[_p(x, ctypes.c_double) for x in g], *[_p(x, ctypes.c_double) for x in a])
+    return (L, *g, *a) if term_scale else (L, *g)
 
 
 def he_init(seed=0):

@@ -1049,14 +1049,23 @@ double oc_mlp_pixel(const double *feat, const double *col, int n, const double *
  *   t_p = 1 if mean_c (o_p - y_p)^2 <= mean_c (plain_p - y_p)^2 else 0 (a constant target),
  * o_p the learned output, conf clamped to [1e-6, 1 - 1e-6].  Gradients (same layout as the
  * weights) are overwritten.  Returns L.
+ *
+ * aW1, ab1, aW2, ab2 (each may be NULL) receive, per gradient entry, the same sum taken over the
+ * absolute values of its terms (|dh_j fr_i|, |dh_j|, |dz_o h_j|, |dz_o|, divided by n_px): the
+ * scale against which a rounding error in the terms of that entry is measured.
  */
 double oc_mlp_loss_grad(int n_px, const double *feat, const double *col, const int *nsamp, const double *plain,
                         const double *clean, const double *W1, const double *b1, const double *W2, const double *b2,
-                        int round_bf16, double bce_w, double *gW1, double *gb1, double *gW2, double *gb2) {
+                        int round_bf16, double bce_w, double *gW1, double *gb1, double *gW2, double *gb2,
+                        double *aW1, double *ab1, double *aW2, double *ab2) {
     memset(gW1, 0, sizeof(double) * OC_NH * OC_NF);
     memset(gb1, 0, sizeof(double) * OC_NH);
     memset(gW2, 0, sizeof(double) * 2 * OC_NH);
     memset(gb2, 0, sizeof(double) * 2);
+    if (aW1) memset(aW1, 0, sizeof(double) * OC_NH * OC_NF);
+    if (ab1) memset(ab1, 0, sizeof(double) * OC_NH);
+    if (aW2) memset(aW2, 0, sizeof(double) * 2 * OC_NH);
+    if (ab2) memset(ab2, 0, sizeof(double) * 2);
     double L = 0.0;
     double *z = (double *)malloc(sizeof(double) * OC_MAXS * 2), *hid = (double *)malloc(sizeof(double) * OC_MAXS * OC_NH);
     for (int p = 0; p < n_px; ++p) {
@@ -1087,14 +1096,22 @@ double oc_mlp_loss_grad(int n_px, const double *feat, const double *col, const i
             for (int i = 0; i < OC_NF; ++i) fr[i] = round_bf16 ? bf16_round(f[s * OC_NF + i]) : f[s * OC_NF + i];
             for (int o = 0; o < 2; ++o) {
                 gb2[o] += dz[o];
-                for (int j = 0; j < OC_NH; ++j) gW2[o * OC_NH + j] += dz[o] * hh[j];
+                if (ab2) ab2[o] += fabs(dz[o]);
+                for (int j = 0; j < OC_NH; ++j) {
+                    gW2[o * OC_NH + j] += dz[o] * hh[j];
+                    if (aW2) aW2[o * OC_NH + j] += fabs(dz[o] * hh[j]);
+                }
             }
             for (int j = 0; j < OC_NH; ++j) {
                 if (hh[j] <= 0.0) continue;
                 double w20 = round_bf16 ? bf16_round(W2[j]) : W2[j], w21 = round_bf16 ? bf16_round(W2[OC_NH + j]) : W2[OC_NH + j];
                 double dh = dz[0] * w20 + dz[1] * w21;
                 gb1[j] += dh;
-                for (int i = 0; i < OC_NF; ++i) gW1[j * OC_NF + i] += dh * fr[i];
+                if (ab1) ab1[j] += fabs(dh);
+                for (int i = 0; i < OC_NF; ++i) {
+                    gW1[j * OC_NF + i] += dh * fr[i];
+                    if (aW1) aW1[j * OC_NF + i] += fabs(dh * fr[i]);
+                }
             }
         }
     }
@@ -1105,6 +1122,10 @@ double oc_mlp_loss_grad(int n_px, const double *feat, const double *col, const i
     for (int i = 0; i < OC_NH; ++i) gb1[i] *= inv;
     for (int i = 0; i < 2 * OC_NH; ++i) gW2[i] *= inv;
     for (int i = 0; i < 2; ++i) gb2[i] *= inv;
+    for (int i = 0; aW1 && i < OC_NH * OC_NF; ++i) aW1[i] *= inv;
+    for (int i = 0; ab1 && i < OC_NH; ++i) ab1[i] *= inv;
+    for (int i = 0; aW2 && i < 2 * OC_NH; ++i) aW2[i] *= inv;
+    for (int i = 0; ab2 && i < 2; ++i) ab2[i] *= inv;
     return L * inv;
 }
 

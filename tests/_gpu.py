@@ -252,3 +252,18 @@ def run_superres(sess: Session, cid, O, scale, crop=None, membership=False, **kw
         res.count = m[..., 1]
         res.hash = m[..., 2].view(np.uint32).astype(np.uint64) | (m[..., 3].view(np.uint32).astype(np.uint64) << np.uint64(32))
     return res
+
+
+def compare_flagged(rgb: np.ndarray, o: oracle.Result):
+    """Colour parity where no GPU membership record exists (the batched plan): pixels holding a
+    candidate within 1e-5 relative of the radius or a window centre within the tie band (the
+    oracle's flags) are excluded; every other pixel must match within COLOUR_TOL.  Returns a
+    summary with the excluded count and the largest error at compared pixels."""
+    band = ((o.codes & oracle.CODE_BAND) != 0).any(axis=(-1, -2, -3))
+    amb = ((o.amb == 1) & (o.status == 1)).any(-1)
+    ok = ~(band | amb)
+    cerr = np.abs(rgb.astype(np.float64) - o.rgb).max(-1)
+    assert cerr[ok].max(initial=0.0) <= COLOUR_TOL, \
+        f"colour max abs {cerr[ok].max()} > {COLOUR_TOL} at {np.argwhere(ok & (cerr > COLOUR_TOL))[:5]}"
+    return dict(pixels=int(ok.size), excluded=int((~ok).sum()), max_colour_err=float(cerr[ok].max(initial=0.0)),
+                max_colour_err_all=float(cerr.max()))

@@ -1,0 +1,107 @@
+"""The batched plan (one persistent, graph-captured launch over clips of uneven size and length,
+shape picked by the autotuner, FP16 colour) against the FP64 oracle.
+
+The clips follow the uneven mixed-clip workload: 8 room scenes, 16:9, widths drawn by seed from
+640..1920 and 30..150 frames, half window 15, k = 7.  Their widths and heights are scaled by 1/4
+(clips that are already 640 x 360 keep their size) so that the host renders them in seconds; the
+frame counts stay as drawn, so one clip is 640 x 360 x 138 and two others have more than 90
+frames.  Every clip's output is compared with the oracle on crops of three output frames (the
+first, one in the middle and the last, whose windows the clip's ends cut), one interior crop and
+one at the image corner (ragged tiles):
+  * arithmetic parity: against the oracle run on the FP16-rounded colours, within 1e-3 at every
+    pixel without a radius-band candidate or a rounding-tie window;
+  * the total error of FP16 colour storage: against the oracle on the FP32 colours, stated.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import COLOUR_TOL, Session, compare_flagged, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+T, K_WIN, CROP = 15, 7, 40
+
+
+def clip_specs():
+    """(W, H, F, seed) of the 8 clips: the workload's draws, W and H scaled by 1/4 down to 640 x 360."""
+    specs = []
+    for seed in range(8):
+        rng = np.random.default_rng(30_000 + seed)
+        Wc = 640 + 160 * int(rng.integers(0, 9))
+        Fc = int(rng.integers(30, 151))
+        Ws = Wc if Wc == 640 else Wc // 4
+        specs.append((Ws, Ws * 9 // 16, Fc, seed))
+    return specs
+
+
+@pytest.fixture(scope="module")
+def setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    s = Session()
+    clips = []
+    for i, (W, H, F, seed) in enumerate(clip_specs()):
+        c = synth.make_clip("room", W, H, F, seed=seed)
+        s.load(60 + i, c, colour_fmt=1)
+        clips.append(c)
+    yield s, clips
+    s.close()
+
+
+def test_clip_shapes_cover_the_workload():
+    specs = clip_specs()
+    assert any(W >= 640 and H >= 360 for W, H, _, _ in specs)
+    assert sum(F >= 90 for _, _, F, _ in specs) >= 2
+    assert len({(W, H) for W, H, _, _ in specs}) >= 5 and all(30 <= F <= 150 for *_, F, _ in specs)
+    assert any(H % 8 for _, H, _, _ in specs) and any(W % 32 for W, _, _, _ in specs)  # ragged tiles
+
+
+def test_autotuned_graph_plan_matches_the_oracle(setup):
+    sess, clips = setup
+    ss, t = sess.ss, sess.torch
+    ids = [60 + i for i in range(len(clips))]
+    p = sess.params(k=K_WIN, half_window=T, frame_begin=0, frame_end=-1)
+    best = ss.ssvp_autotune(sess.ctx, p, ids)
+    plan = ss.ssvp_plan_create(sess.ctx, p, ids)
+    try:
+        cfg, n_items, grid = ss.ssvp_plan_get_config(plan)
+        assert (cfg.tile_rows, cfg.frame_chunk) == (best.tile_rows, best.frame_chunk) and grid > 0
+        ss.ssvp_plan_launch(plan)
+        ss.ssvp_plan_launch(plan)  # a graph replay over the same clips
+        ss.ssvp_sync(sess.ctx)
+    finally:
+        ss.ssvp_plan_destroy(plan)
+    worst16, worst32, excluded, compared = 0.0, 0.0, 0, 0
+    for i, c in enumerate(clips):
+        out = t.empty((c.F, c.H, c.W, 3), dtype=t.float32, device=sess.dev)
+        ss.ssvp_read_output(sess.ctx, ids[i], 0, c.F, out)
+        ss.ssvp_sync(sess.ctx)
+        out = out.cpu().numpy()
+        rgb16 = c.rgb.astype(np.float16).astype(np.float32)
+        v16 = oracle.ClipView(rgb16, c.depth, c.K, c.w2c)
+        v32 = oracle.ClipView.of(c)
+        prm = oracle_params(oracle.median_depth(c.depth), K_WIN, T)
+        for O in (0, c.F // 2, c.F - 1):
+            for x0, y0 in ((c.W // 3, c.H // 3), (c.W - CROP, c.H - CROP)):
+                crop = (x0, y0, CROP, CROP)
+                g = out[O, y0:y0 + CROP, x0:x0 + CROP]
+                o16 = oracle.gather_filter(v16, prm, O, crop=crop, membership=True)
+                s = compare_flagged(g, o16)
+                worst16 = max(worst16, s["max_colour_err"])
+                excluded += s["excluded"]
+                compared += s["pixels"]
+                o32 = oracle.gather_filter(v32, prm, O, crop=crop)
+                worst32 = max(worst32, float(np.abs(g.astype(np.float64) - o32.rgb).max()))
+    print(f"batched plan {cfg.tile_rows}x{cfg.frame_chunk}, {n_items} items: max |GPU - oracle on FP16 colours| = "
+          f"{worst16:.2e} over {compared} pixels ({excluded} band/tie pixels excluded); FP16 colour total error, "
+          f"max |GPU - FP64 oracle on FP32 colours| = {worst32:.2e}")
+    assert worst16 <= COLOUR_TOL
+    assert excluded <= 0.002 * compared + 4
+    # FP16 storage rounds each colour by at most 2^-12 (values below 1); the output is a weighted
+    # mean, moved further only through the colour weights of outlying samples
+    assert worst32 < 1e-2

@@ -202,14 +202,26 @@ def test_training_gradients_match_the_oracle(sess, clip):
     p = sess.params(k=k, half_window=T, frame_begin=O, frame_end=O + 1, radius=-rel)
     g = sess.ss.ssvp_mlp_grad(sess.ctx, p, 40, idx, clean_d)
     ys, xs = zip(*pick)
-    L, gW1, gb1, gW2, gb2 = oracle.mlp_loss_grad(of[ys, xs], oc[ys, xs], on[ys, xs], op[ys, xs], clean[ys, xs],
-                                                 W1, b1, W2, b2, round_bf16=True)
+    L, gW1, gb1, gW2, gb2, aW1, ab1, aW2, ab2 = oracle.mlp_loss_grad(
+        of[ys, xs], oc[ys, xs], on[ys, xs], op[ys, xs], clean[ys, xs], W1, b1, W2, b2, round_bf16=True,
+        term_scale=True)
     assert g[1218] == pytest.approx(L, rel=1e-4)
-    parts = [(g[:1024], gW1.ravel(), 2e-2), (g[1024:1088], gb1, 1e-3), (g[1088:1216], gW2.ravel(), 1e-3),
-             (g[1216:1218], gb2, 1e-3)]
-    for got, want, tol in parts:
-        err = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-12)
-        assert err <= tol, (err, tol)
+    # Element by element: |GPU - oracle| <= 1e-3 |oracle| + c * (sum of |terms| of the entry).
+    # c covers the rounding of the terms: FP32 accumulation and the rare flip of a BF16 rounding of
+    # a hidden activation (2e-4); for dW1 also the BF16 rounding of dH, the operand of the dW1
+    # tensor-core product, which perturbs each term by at most 2^-8 of itself.
+    parts = [("gW1", g[:1024], gW1.ravel(), aW1.ravel(), 2.0 ** -8 + 2e-4),
+             ("gb1", g[1024:1088], gb1, ab1, 2e-4), ("gW2", g[1088:1216], gW2.ravel(), aW2.ravel(), 2e-4),
+             ("gb2", g[1216:1218], gb2, ab2, 2e-4)]
+    for name, got, want, scale, c in parts:
+        err = np.abs(got - want)
+        tol = 1e-3 * np.abs(want) + c * scale
+        bad = np.flatnonzero(err > tol)
+        assert bad.size == 0, (name, bad[:5], err[bad[:5]], tol[bad[:5]])
+        # stated: the largest error in units of the entry's term scale
+        print(f"{name}: max |GPU - oracle| / term scale = {float(np.max(err / np.maximum(scale, 1e-30))):.2e}, "
+              f"max relative (entries above 1e-2 of the largest) = "
+              f"{float(np.max((err / np.abs(want))[np.abs(want) > 1e-2 * np.abs(want).max()])):.2e}")
 
 
 def test_short_training_lowers_the_loss(sess):

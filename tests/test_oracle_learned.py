@@ -185,6 +185,37 @@ def test_gradients_match_central_differences(tiny):
     assert checked >= 40
 
 
+def test_gradient_term_scales_bound_the_gradients(tiny):
+    """The per-entry sums of |term| that the GPU gradient tolerance is scaled by: they bound the
+    gradients (triangle inequality), and for one pixel with one sample and a positive hidden unit
+    each entry has a single term, so the two are equal in magnitude (layer 2 and b1 of that
+    unit); doubling the batch by repeating its pixels leaves them unchanged (both are means)."""
+    c, v, _ = tiny
+    prm = oracle.default_params(c.depth, k=5, T=4, radius_rel=0.03)
+    feat, col, n, plain = oracle.learned_crop(v, prm, 4, crop=(20, 10, 8, 6))
+    P = 48
+    feat, col, n, plain = feat.reshape(P, 64, 16), col.reshape(P, 64, 3), n.reshape(P), plain.reshape(P, 3)
+    clean = c.clean[4, 10:16, 20:28].reshape(P, 3).astype(np.float64)
+    W1, b1, W2, b2 = oracle.he_init(5)
+    b2 = np.array([0.3, 0.1])
+    out = oracle.mlp_loss_grad(feat, col, n, plain, clean, W1, b1, W2, b2, term_scale=True)
+    for g, a in zip(out[1:5], out[5:9]):
+        assert (np.abs(g) <= a * (1 + 1e-12) + 1e-300).all()
+        assert (a >= 0).all()
+    assert out[5].max() > 0 and out[7].max() > 0
+    out2 = oracle.mlp_loss_grad(np.concatenate([feat, feat]), np.concatenate([col, col]), np.concatenate([n, n]),
+                                np.concatenate([plain, plain]), np.concatenate([clean, clean]), W1, b1, W2, b2,
+                                term_scale=True)
+    for x, y in zip(out[1:], out2[1:]):
+        np.testing.assert_allclose(x, y, rtol=1e-12, atol=1e-300)
+    # one pixel, one sample: every entry of gW2, gb2 and gb1 is a single term
+    one = [np.where(n >= 1)[0][0]]
+    n1 = np.ones(1, np.int32)
+    o1 = oracle.mlp_loss_grad(feat[one], col[one], n1, plain[one], clean[one], W1, b1, W2, b2, term_scale=True)
+    for g, a in ((o1[2], o1[6]), (o1[3], o1[7]), (o1[4], o1[8])):
+        np.testing.assert_allclose(np.abs(g), a, rtol=1e-12, atol=1e-300)
+
+
 def test_depth_residual_feature_sign_and_size():
     """Raising the depth of every other frame by delta < r keeps each sample (it moves along its
     own ray, still inside the gate) and makes its depth residual exactly +delta."""
