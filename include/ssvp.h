@@ -56,8 +56,11 @@ enum {
                                 (Sec. "Deblurring"; see ssvp_frame_sharpness) */
     SSVP_MODE_SHUTTER = 5,   /* Eq. 10: w = xi(J - O) alone, xi from ssvp_set_shutter
                                 (Sec. "Computational scene-space shutters") */
-    SSVP_MODE_INPAINT = 6    /* Eq. 8-9 with the frustum gather: masked pixels are replaced
+    SSVP_MODE_INPAINT = 6,   /* Eq. 8-9 with the frustum gather: masked pixels are replaced
                                 (Sec. "Inpainting and semi-transparency"; see ssvp_set_mask) */
+    SSVP_MODE_SEMI = 7       /* semi-transparency: Eq. 8-9 plus, in the second Eq. 9 step, the
+                                Eq. 4 weight of every sample around the pixel's own sample (the
+                                same section, after Eq. 9; see ssvp_set_mask) */
 };
 enum {
     SSVP_GATHER_WINDOW = 0,  /* depth-seeded k x k window + radius (or the aperture cone) */
@@ -173,6 +176,13 @@ int ssvp_superres(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, int sca
  * Eq. 9), each step's result being the next step's c_ref; a step whose weights are all 0 keeps
  * its reference, an empty S(p) keeps the input colour.  Unmasked pixels keep their input colour.
  * The paper uses sigma_rgb = 55 on a 0-255 scale.  The mask lives until the clip is unloaded.
+ *
+ * SSVP_MODE_SEMI (semi-transparency, same gather and mask) makes the masked region see-through
+ * instead: its second step also gives every sample s of S(p), masked or not, the Eq. 4 weight
+ * exp(-|I(p) - c_s|^2 / (2 sigma_rgb^2) - |x_ref - X_s|^2 / (2 sigma_xyz^2) - (J - O)^2 /
+ * (2 sigma_f^2)) around the pixel's own sample (I(p), x_ref = D(p) K_O^-1 (u, v, 1), O), added to
+ * its Eq. 9 weight, so the object's samples near x_ref blend with the background's estimate.  A
+ * masked pixel without a valid depth gets the inpainting result.  The paper uses sigma_rgb = 80.
  */
 int ssvp_set_mask(ssvp_ctx *ctx, int clip_id, const uint8_t *mask, int mem_kind);
 

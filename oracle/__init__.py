@@ -90,6 +90,8 @@ def _load():
         lib.oc_inpaint_filter.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params), u8p] + [ctypes.c_int] * 5 + \
             [dp, dp, i64p, i32p, ctypes.POINTER(ctypes.c_uint64), u8p]
         lib.oc_inpaint_filter.restype = ctypes.c_int
+        lib.oc_semitransparent_filter.argtypes = lib.oc_inpaint_filter.argtypes
+        lib.oc_semitransparent_filter.restype = ctypes.c_int
         lib.oc_weight_superres.argtypes = [dp, dp] + [ctypes.c_double] * 6
         lib.oc_weight_superres.restype = ctypes.c_double
         lib.oc_superres_filter.argtypes = [ctypes.POINTER(_Clip), ctypes.POINTER(_Params)] + [ctypes.c_int] * 6 + \
@@ -350,8 +352,11 @@ def mask_from_box(view: ClipView, box) -> np.ndarray:
     return m
 
 
-def inpaint_filter(view: ClipView, prm: Params, mask, O: int, crop=None, membership: bool = False) -> FrustumResult:
-    """Inpainting (Eq. 8-9) of output frame O over crop (x0, y0, w, h) with the frustum gather."""
+def inpaint_filter(view: ClipView, prm: Params, mask, O: int, crop=None, membership: bool = False,
+                   semi: bool = False) -> FrustumResult:
+    """Inpainting (Eq. 8-9) of output frame O over crop (x0, y0, w, h) with the frustum gather;
+    with semi, the semi-transparency variant (the pixel's own sample adds Eq. 4 weights to the
+    second Eq. 9 step; prm.sigma_xyz and prm.sigma_f must be set)."""
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     assert mask.shape == (view.F, view.H, view.W)
     x0, y0, cw, ch = crop if crop is not None else (0, 0, view.W, view.H)
@@ -365,9 +370,10 @@ def inpaint_filter(view: ClipView, prm: Params, mask, O: int, crop=None, members
         hsh = np.zeros((ch, cw, ns), np.uint64)
         bnd = np.zeros((ch, cw, ns), np.uint8)
     ps = prm.c_struct(float(view.K[O, 0, 0]))
-    rc = _load().oc_inpaint_filter(ctypes.byref(view.c), ctypes.byref(ps), _p(mask, ctypes.c_uint8), O, x0, y0, cw, ch,
-                                   _p(out, ctypes.c_double), _p(sumw, ctypes.c_double), _p(nacc, ctypes.c_int64),
-                                   _p(cnt, ctypes.c_int32), _p(hsh, ctypes.c_uint64), _p(bnd, ctypes.c_uint8))
+    fn = _load().oc_semitransparent_filter if semi else _load().oc_inpaint_filter
+    rc = fn(ctypes.byref(view.c), ctypes.byref(ps), _p(mask, ctypes.c_uint8), O, x0, y0, cw, ch,
+            _p(out, ctypes.c_double), _p(sumw, ctypes.c_double), _p(nacc, ctypes.c_int64),
+            _p(cnt, ctypes.c_int32), _p(hsh, ctypes.c_uint64), _p(bnd, ctypes.c_uint8))
     if rc != 0:
         raise ValueError(f"oracle rejected the arguments (code {rc})")
     return FrustumResult(out, sumw, nacc, cnt, hsh, bnd)

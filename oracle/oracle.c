@@ -71,6 +71,16 @@
  *   for masked ones, the result of a step being the next step's reference (a step whose weights
  *   are all 0 keeps the reference).  An empty S(p) keeps the input colour.
  *
+ * Semi-transparency (same section, the sentence after Eq. 9: the standard multivariate weighting
+ *   is added, for the input frame's own sample, with sigma_rgb = 80 on the 0-255 scale): the
+ *   masked pixel's own sample s_I = (I_O(p), x_ref, O), x_ref from its depth as in denoising,
+ *   serves as a second reference.  The mean of Eq. 8 and the first step of Eq. 9 are those of
+ *   inpainting; in the second step every sample s of S(p), masked or not, additionally weighs
+ *   the Eq. 4 weight w(s; s_I) (colour, scene position and frame terms), so a sample's weight is
+ *   [M(s) = 0] exp(-|c_ref - c_s|^2 / (2 sigma_rgb^2)) + w_Eq4(s; s_I) and the output is Eq. 3
+ *   with it: the object's own samples near x_ref blend with the background's mean-shift estimate.
+ *   A masked pixel without a valid depth has no x_ref and gets the inpainting result.
+ *
  * Built with -ffp-contract=off: every product and sum is rounded on its own.
  */
 #include <math.h>
@@ -732,13 +742,14 @@ void oc_mask_from_box(const oc_clip *c, const double *box, uint8_t *mask) {
 }
 
 /*
- * Inpainting of the crop [x0, x0+cw) x [y0, y0+ch) of output frame O (see the header comment).
- * mask: F*H*W bytes (nonzero = remove).  Outputs as oc_frustum_filter (nacc = |S(p)| of masked
- * pixels, sumw = the last step's sum of weights); records only for masked pixels.
+ * Inpainting (semi = 0) or semi-transparency (semi = 1) of the crop [x0, x0+cw) x [y0, y0+ch) of
+ * output frame O (see the header comment).  mask: F*H*W bytes (nonzero = remove).  Outputs as
+ * oc_frustum_filter (nacc = |S(p)| of masked pixels, sumw = the last step's sum of weights);
+ * records only for masked pixels.
  */
-int oc_inpaint_filter(const oc_clip *c, const oc_params *p, const uint8_t *mask, int O, int x0, int y0, int cw, int ch,
-                      double *out_rgb, double *out_sumw, int64_t *out_nacc, int32_t *mem_count, uint64_t *mem_hash,
-                      uint8_t *mem_band) {
+static int inpaint_body(const oc_clip *c, const oc_params *p, const uint8_t *mask, int O, int x0, int y0, int cw,
+                        int ch, int semi, double *out_rgb, double *out_sumw, int64_t *out_nacc, int32_t *mem_count,
+                        uint64_t *mem_hash, uint8_t *mem_band) {
     if (p->T < 0 || O < 0 || O >= c->F || !(p->frustum_l > 0) || !(p->near_plane > 0) ||
         !(p->far_plane > p->near_plane) || !(p->sigma_rgb > 0))
         return -1;
@@ -767,11 +778,12 @@ int oc_inpaint_filter(const oc_clip *c, const oc_params *p, const uint8_t *mask,
                 mem_band[i * ns + j] = 0;
             }
         if (mask[pix]) {
-            /* S(p): colours and mask flags of every sample */
+            /* S(p): colours, mask flags, O-camera positions and frames of every sample */
             size_t cap = 1024, m = 0;
             double *col = (double *)malloc(sizeof(double) * 3 * cap);
+            double *pos = (double *)malloc(sizeof(double) * 4 * cap);
             uint8_t *msk = (uint8_t *)malloc(cap);
-            for (int j = 0; j < ns && col && msk; ++j) {
+            for (int j = 0; j < ns && col && pos && msk; ++j) {
                 const int J = O - p->T + j;
                 if (J < 0 || J >= c->F) continue;
                 const double *G = Gt + 12 * j;
@@ -792,12 +804,24 @@ int oc_inpaint_filter(const oc_clip *c, const oc_params *p, const uint8_t *mask,
                         if (m == cap) {
                             cap *= 2;
                             double *c2 = (double *)realloc(col, sizeof(double) * 3 * cap);
+                            double *p2 = (double *)realloc(pos, sizeof(double) * 4 * cap);
                             uint8_t *m2 = (uint8_t *)realloc(msk, cap);
-                            if (!c2 || !m2) { free(c2 ? c2 : col); free(m2 ? m2 : msk); col = NULL; msk = NULL; break; }
+                            if (!c2 || !p2 || !m2) {
+                                free(c2 ? c2 : col);
+                                free(p2 ? p2 : pos);
+                                free(m2 ? m2 : msk);
+                                col = NULL;
+                                pos = NULL;
+                                msk = NULL;
+                                break;
+                            }
                             col = c2;
+                            pos = p2;
                             msk = m2;
                         }
                         for (int a = 0; a < 3; ++a) col[3 * m + a] = c->rgb[3 * qi + a];
+                        for (int a = 0; a < 3; ++a) pos[4 * m + a] = X[a];
+                        pos[4 * m + 3] = J;
                         msk[m] = mask[qi] != 0;
                         ++m;
                         ++mc;
@@ -810,23 +834,42 @@ int oc_inpaint_filter(const oc_clip *c, const oc_params *p, const uint8_t *mask,
                 }
                 if (!col) break;
             }
-            if (!col || !msk) {
+            if (!col || !pos || !msk) {
 #pragma omp atomic write
                 err = 1;
             } else if (m > 0) {
+                /* semi-transparency: the pixel's own sample s_I = (I_O(p), x_ref, O) */
+                double sI[7] = {ref[0], ref[1], ref[2], 0.0, 0.0, 0.0, (double)O};
+                const float dp = c->depth[pix];
+                const int has_sI = semi && valid_depth(dp);
+                if (has_sI) {
+                    double KOi[9], uv1[3] = {u, v, 1.0}, ray[3];
+                    mat3_inverse(KO, KOi);
+                    mat3_vec(KOi, uv1, ray);
+                    for (int a = 0; a < 3; ++a) sI[3 + a] = (double)dp * ray[a];
+                }
                 /* Eq. 8: the mean of all samples */
                 double acc[3] = {0, 0, 0};
                 for (size_t k = 0; k < m; ++k)
                     for (int a = 0; a < 3; ++a) acc[a] += col[3 * k + a];
                 for (int a = 0; a < 3; ++a) ref[a] = acc[a] / (double)m;
-                /* Eq. 9, two steps */
+                /* Eq. 9, two steps (the second with the added Eq. 4 weight for semi-transparency) */
                 for (int step = 0; step < 2; ++step) {
+                    const int add4 = has_sI && step == 1;
                     double num[3] = {0, 0, 0}, den = 0.0;
                     for (size_t k = 0; k < m; ++k) {
-                        if (msk[k]) continue;
-                        double d2 = 0.0;
-                        for (int a = 0; a < 3; ++a) d2 += (col[3 * k + a] - ref[a]) * (col[3 * k + a] - ref[a]);
-                        const double w = exp(-d2 / (2.0 * p->sigma_rgb * p->sigma_rgb));
+                        if (msk[k] && !add4) continue;
+                        double w = 0.0;
+                        if (!msk[k]) {
+                            double d2 = 0.0;
+                            for (int a = 0; a < 3; ++a) d2 += (col[3 * k + a] - ref[a]) * (col[3 * k + a] - ref[a]);
+                            w = exp(-d2 / (2.0 * p->sigma_rgb * p->sigma_rgb));
+                        }
+                        if (add4) {
+                            const double sk[7] = {col[3 * k], col[3 * k + 1], col[3 * k + 2], pos[4 * k], pos[4 * k + 1],
+                                                  pos[4 * k + 2], pos[4 * k + 3]};
+                            w += oc_weight_denoise(sk, sI, p->sigma_rgb, p->sigma_xyz, p->sigma_f);
+                        }
                         for (int a = 0; a < 3; ++a) num[a] += w * col[3 * k + a];
                         den += w;
                     }
@@ -837,6 +880,7 @@ int oc_inpaint_filter(const oc_clip *c, const oc_params *p, const uint8_t *mask,
             }
             cnt = (int64_t)m;
             free(col);
+            free(pos);
             free(msk);
         }
         for (int a = 0; a < 3; ++a) out_rgb[3 * i + a] = ref[a];
@@ -845,6 +889,19 @@ int oc_inpaint_filter(const oc_clip *c, const oc_params *p, const uint8_t *mask,
     }
     free(Gt);
     return err ? -2 : 0;
+}
+
+int oc_inpaint_filter(const oc_clip *c, const oc_params *p, const uint8_t *mask, int O, int x0, int y0, int cw, int ch,
+                      double *out_rgb, double *out_sumw, int64_t *out_nacc, int32_t *mem_count, uint64_t *mem_hash,
+                      uint8_t *mem_band) {
+    return inpaint_body(c, p, mask, O, x0, y0, cw, ch, 0, out_rgb, out_sumw, out_nacc, mem_count, mem_hash, mem_band);
+}
+
+int oc_semitransparent_filter(const oc_clip *c, const oc_params *p, const uint8_t *mask, int O, int x0, int y0, int cw,
+                              int ch, double *out_rgb, double *out_sumw, int64_t *out_nacc, int32_t *mem_count,
+                              uint64_t *mem_hash, uint8_t *mem_band) {
+    if (!(p->sigma_xyz > 0) || !(p->sigma_f > 0)) return -1;
+    return inpaint_body(c, p, mask, O, x0, y0, cw, ch, 1, out_rgb, out_sumw, out_nacc, mem_count, mem_hash, mem_band);
 }
 
 /*

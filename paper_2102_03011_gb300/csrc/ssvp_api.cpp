@@ -254,7 +254,7 @@ int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
     if (!p) return fail(ctx, SSVP_EINVAL, "params is NULL");
     if (p->mode != SSVP_MODE_DENOISE && p->mode != SSVP_MODE_MEAN && p->mode != SSVP_MODE_APERTURE &&
         p->mode != SSVP_MODE_LEARNED && p->mode != SSVP_MODE_DEBLUR && p->mode != SSVP_MODE_SHUTTER &&
-        p->mode != SSVP_MODE_INPAINT)
+        p->mode != SSVP_MODE_INPAINT && p->mode != SSVP_MODE_SEMI)
         return fail(ctx, SSVP_EINVAL, "mode %d is not available in this build", p->mode);
     if (p->mode == SSVP_MODE_LEARNED && !(std::isfinite(p->conf_threshold)))
         return fail(ctx, SSVP_EINVAL, "conf_threshold must be finite");
@@ -268,7 +268,7 @@ int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
     }
     if (p->gather != SSVP_GATHER_WINDOW && p->gather != SSVP_GATHER_FRUSTUM)
         return fail(ctx, SSVP_EINVAL, "gather %d is not available in this build", p->gather);
-    if (p->mode == SSVP_MODE_INPAINT && p->gather != SSVP_GATHER_FRUSTUM)
+    if ((p->mode == SSVP_MODE_INPAINT || p->mode == SSVP_MODE_SEMI) && p->gather != SSVP_GATHER_FRUSTUM)
         return fail(ctx, SSVP_EINVAL, "inpainting gathers the pixel frustum: set gather = SSVP_GATHER_FRUSTUM");
     if (p->gather == SSVP_GATHER_FRUSTUM) {
         if (p->mode == SSVP_MODE_APERTURE || p->mode == SSVP_MODE_LEARNED)
@@ -772,12 +772,13 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         CK(cudaMemcpyAsync(ctx->d_shutter_log2, lg.data(), sizeof(float) * ns, cudaMemcpyHostToDevice, ctx->stream),
            "cudaMemcpyAsync (shutter)");
     }
-    if (p.mode == SSVP_MODE_INPAINT)
+    if (p.mode == SSVP_MODE_INPAINT || p.mode == SSVP_MODE_SEMI)
         for (int i = 0; i < n_clips; ++i)
             if (!ctx->clips[clip_ids[i]].p.mask)
                 return fail(ctx, SSVP_EINVAL, "inpainting needs a mask for clip %d (ssvp_set_mask or ssvp_mask_from_box)",
                             clip_ids[i]);
-    // the shutter and inpainting weights have no frame-distance term: sigma_f = infinity (beta = 0)
+    // the shutter and inpainting weights have no frame-distance term: sigma_f = infinity (beta = 0);
+    // semi-transparency keeps it for its Eq. 4 term (the kernel leaves it out of the Eq. 9 term)
     const double sigma_f = shutter || p.mode == SSVP_MODE_INPAINT ? INFINITY : (double)p.sigma_f;
     // the frustum gather also needs the back maps: a second table of the same shape after the first
     const bool frustum = p.gather == SSVP_GATHER_FRUSTUM;

@@ -102,6 +102,9 @@ __device__ __forceinline__ void face_edge(const float *M, const float *e, float 
 // INP: inpainting (Sec. "Inpainting and semi-transparency", Eq. 8-9): only pixels with a mask
 // gather; three passes over S(p): the mean of all samples (Eq. 8), then two steps of the
 // colour-weighted mean over unmasked samples (Eq. 9), each around the previous result.
+// INP == 2: semi-transparency (the same section, after Eq. 9): in the last pass every sample,
+// masked or not, also weighs the Eq. 4 weight around the pixel's own sample (I(p), x_ref, O),
+// so the object's samples near x_ref blend with the background's mean-shift estimate.
 // Fast path of the hull: the 4 lateral rays of the frustum, h(z) = z A + e, clipped to the slab
 // alone.  Valid (returns true) when every ray's depth in J grows (or every one falls) with z and
 // every clipped interval lies strictly inside (near, far): then no face of V touches the slab,
@@ -138,7 +141,7 @@ __device__ __forceinline__ bool lateral_fast(const float *M, const float *e, flo
     return ok;
 }
 
-template <int CFMT, bool DEBUG, bool SR, bool INP>
+template <int CFMT, bool DEBUG, bool SR, int INP>
 __global__ void __launch_bounds__(kFrThreads, 3) frustum_kernel(const GatherArgs a) {
     __shared__ float s_const[4];
     __shared__ unsigned long long s_cnt[2][kFrThreads / 32];
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(kFrThreads, 3) frustum_kernel(const GatherArgs
         // the shutter weight of Eq. 10 replaces Eq. 4: no colour and no position term
         const bool shutter = a.mode == SSVP_MODE_SHUTTER;
         s_const[0] = shutter ? 0.0f : kLog2e / (2.0f * a.sigma_rgb * a.sigma_rgb);
-        s_const[1] = shutter || INP ? 0.0f : kLog2e / (2.0f * sx * sx);
+        s_const[1] = shutter || INP == 1 ? 0.0f : kLog2e / (2.0f * sx * sx);
         s_const[2] = a.mode == SSVP_MODE_MEAN ? 0.0f : 1.0f;
         if (SR) {
             // sigma_area <= 0: one input-pixel footprint at the median depth (median / fx_O); the
@@ -210,6 +213,9 @@ __global__ void __launch_bounds__(kFrThreads, 3) frustum_kernel(const GatherArgs
     const long long pix_o = (long long)O * P.fstride + (long long)(v + kPad) * P.pitch + (u + kPad);
     const bool gather = INP ? active && __ldg(P.mask + pix_o) != 0 : active && dref > 0.0f;
     if (INP && active) cref = load_colour<CFMT>(P.colour, pix_o);
+    // semi-transparency: the pixel's own sample (I(p), x_ref, O) needs a valid depth (NaN fails)
+    const float3 c_in = cref;
+    const bool own = INP == 2 && dref > 0.0f;
     // Accumulators carry the common factor 2^-m, m the largest log2 weight so far: without the
     // reference sample (outside near / far) every weight can be far below FP32's range while
     // Eq. 3 is still well defined.  The start, -1e30, is below every finite exponent, and a
@@ -429,15 +435,29 @@ __global__ void __launch_bounds__(kFrThreads, 3) frustum_kernel(const GatherArgs
                         const float h1 = fmaf(d, fmaf(sm1, fmk, b1), E1);
                         const float h2 = fmaf(d, fmaf(sm2, fmk, b2), E2);
                         const float h3 = fmaf(d, fmaf(sm3, fmk, b3), E3);
-                        // Eq. 9: masked samples weigh 0 in the mean-shift steps
-                        if (INP && pass > 0 && __ldg(P.mask + off) != 0) continue;
+                        // Eq. 9: masked samples weigh 0 in the mean-shift steps (semi-transparency:
+                        // except for their Eq. 4 term in the last pass)
+                        const bool masked = INP && pass > 0 && __ldg(P.mask + off) != 0;
+                        const bool add4 = INP == 2 && pass == 2 && own;
+                        if (masked && !add4) continue;
                         const float er = c.x - cref.x, eg = c.y - cref.y, eb = c.z - cref.z;
                         float w = 1.0f;
                         if (wpass) {
                             const float dz = h3 - dref;
                             const float ex = fmaf(ux, dz, h1) * ifxO, ey = fmaf(vy, dz, h2) * ifyO;
                             const float d2 = fmaf(ex, ex, fmaf(ey, ey, dz * dz));
-                            float x = -fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta));
+                            // inpainting's colour term has no position or frame term
+                            float x = INP ? -a_rgb * fmaf(er, er, fmaf(eg, eg, eb * eb))
+                                          : -fmaf(a_rgb, fmaf(er, er, fmaf(eg, eg, eb * eb)), fmaf(a_xyz, d2, beta));
+                            float w_rel = 1.0f;  // the sample's weight relative to 2^x
+                            if (add4) {
+                                // the two weights of the semi-transparency step, relative to the larger
+                                const float fr = c.x - c_in.x, fg = c.y - c_in.y, fb = c.z - c_in.z;
+                                const float x4 = -fmaf(a_rgb, fmaf(fr, fr, fmaf(fg, fg, fb * fb)), fmaf(a_xyz, d2, beta));
+                                const float xi = masked ? -__int_as_float(0x7f800000) : x;
+                                x = fmaxf(xi, x4);
+                                w_rel = ex2(xi - x) + ex2(x4 - x);
+                            }
                             if (SR) {  // Eq. 7: s_area = (d / fx_J)^2, the sample's pixel edge squared
                                 const float edge = d * ifxJ;
                                 x = fmaf(-a_area, edge * edge, x);
@@ -450,7 +470,7 @@ __global__ void __launch_bounds__(kFrThreads, 3) frustum_kernel(const GatherArgs
                                 acc_w *= sc;
                                 m_log2 = x;
                             }
-                            w = ex2(x - m_log2);
+                            w = w_rel * ex2(x - m_log2);
                         }
                         acc_r = fmaf(w, er, acc_r);
                         acc_g = fmaf(w, eg, acc_g);
@@ -550,7 +570,7 @@ __global__ void __launch_bounds__(256) zrange_kernel(Planes P, unsigned int *zr)
     }
 }
 
-template <bool SR, bool INP>
+template <bool SR, int INP>
 void launch_frustum_t(const GatherArgs &a, const dim3 grid, cudaStream_t s) {
     const bool dbg = a.membership || a.pixel_stats;
     if (a.clip.colour_fmt == 0) {
@@ -599,9 +619,10 @@ __global__ void __launch_bounds__(256) mask_box_kernel(Planes P, const double *c
 
 cudaError_t launch_frustum(const GatherArgs &a, cudaStream_t s) {
     const dim3 grid((a.cw + kFrTileX - 1) / kFrTileX, (a.ch + kFrTileY - 1) / kFrTileY, a.n_out);
-    if (a.sr_out) launch_frustum_t<true, false>(a, grid, s);
-    else if (a.mode == SSVP_MODE_INPAINT) launch_frustum_t<false, true>(a, grid, s);
-    else launch_frustum_t<false, false>(a, grid, s);
+    if (a.sr_out) launch_frustum_t<true, 0>(a, grid, s);
+    else if (a.mode == SSVP_MODE_INPAINT) launch_frustum_t<false, 1>(a, grid, s);
+    else if (a.mode == SSVP_MODE_SEMI) launch_frustum_t<false, 2>(a, grid, s);
+    else launch_frustum_t<false, 0>(a, grid, s);
     return cudaGetLastError();
 }
 

@@ -47,7 +47,7 @@ def setup():
     clips = []
     for i, (W, H, F, seed) in enumerate(clip_specs()):
         c = synth.make_clip("room", W, H, F, seed=seed)
-        s.load(60 + i, c, colour_fmt=1)
+        s.load(50 + i, c, colour_fmt=1)
         clips.append(c)
     yield s, clips
     s.close()
@@ -64,7 +64,7 @@ def test_clip_shapes_cover_the_workload():
 def test_autotuned_graph_plan_matches_the_oracle(setup):
     sess, clips = setup
     ss, t = sess.ss, sess.torch
-    ids = [60 + i for i in range(len(clips))]
+    ids = [50 + i for i in range(len(clips))]
     p = sess.params(k=K_WIN, half_window=T, frame_begin=0, frame_end=-1)
     best = ss.ssvp_autotune(sess.ctx, p, ids)
     plan = ss.ssvp_plan_create(sess.ctx, p, ids)

@@ -93,3 +93,63 @@ def test_argument_errors(sess):
     with pytest.raises(ss.SsvpError) as e:
         ss.ssvp_mask_from_box(sess.ctx, 3, (0, 0, 0, np.nan, 1, 1))
     assert e.value.code == ss.SSVP_EINVAL
+
+
+# ---------------------------------------------------------------- semi-transparency (after Eq. 9)
+SEMI_SIGMA_RGB = 80.0 / 255.0  # the paper's sigma_rgb = 80 for semi-transparency
+
+
+def _semi_both(sess, c, cid, mask, O, T, sigma_xyz, crop=None):
+    g = run_frustum(sess, cid, O, crop=crop, membership=True, half_window=T, mode=sess.ss.SSVP_MODE_SEMI,
+                    sigma_rgb=SEMI_SIGMA_RGB, sigma_xyz=sigma_xyz)
+    prm = oracle.Params(mode=oracle.MODE_DENOISE, k=1, T=T, radius=0.01, sigma_rgb=SEMI_SIGMA_RGB, sigma_xyz=sigma_xyz,
+                        gather=oracle.GATHER_FRUSTUM, frustum_l=3.0)
+    o = oracle.inpaint_filter(oracle.ClipView.of(c), prm, mask, O, crop=crop, membership=True, semi=True)
+    x0, y0, cw, ch = crop if crop is not None else (0, 0, c.W, c.H)
+    return g, o, mask[O, y0:y0 + ch, x0:x0 + cw] != 0
+
+
+def test_semitransparency_on_constant_planes(sess):
+    c = synth.make_clip("exact_const", 192, 108, 13, seed=0)
+    sess.load(4, c)
+    sess.ss.ssvp_mask_from_box(sess.ctx, 4, BOX)
+    mask = oracle.mask_from_box(oracle.ClipView.of(c), BOX)
+    g, o, masked = _semi_both(sess, c, 4, mask, 6, 6, sigma_xyz=0.05)
+    s = compare_frustum(g, o, masked)
+    assert s["excluded"] == 0
+    np.testing.assert_array_equal(g.rgb[~masked], c.rgb[6][~masked])
+    # see-through: revealed pixels differ from both the object's colour and inpainting's result
+    gi = run_frustum(sess, 4, 6, half_window=6, mode=sess.ss.SSVP_MODE_INPAINT, sigma_rgb=SEMI_SIGMA_RGB)
+    mid = masked & (np.abs(gi.rgb - c.rgb[6]).max(-1) > 0.05)
+    assert mid.sum() > 50
+    assert (np.abs(g.rgb[mid] - gi.rgb[mid]).max(-1) > 1e-3).all()
+    assert (np.abs(g.rgb[mid] - c.rgb[6][mid]).max(-1) > 1e-3).all()
+
+
+def test_semitransparency_on_the_room_scene_with_invalid_depths(sess):
+    c = synth.make_clip("room", 96, 54, 9, seed=0)
+    box = synth.object_box(c.meta["objects"][9], 0.02, (-2.18, 1.48))
+    mask = oracle.mask_from_box(oracle.ClipView.of(c), box)
+    ys, xs = np.nonzero(mask[4])
+    depth = c.depth.copy()
+    for i in range(0, len(ys), max(1, len(ys) // 5)):  # masked pixels without a valid depth
+        depth[4, ys[i], xs[i]] = np.nan
+    bad = synth.Clip(c.W, c.H, c.F, c.K, c.w2c, c.w2c_true, c.rgb, depth, c.clean, c.depth_true)
+    sess.load(5, bad)
+    sess.ss.ssvp_set_mask(sess.ctx, 5, mask)
+    med = oracle.median_depth(c.depth)
+    g, o, masked = _semi_both(sess, bad, 5, mask, 4, 4, sigma_xyz=0.03 * med)
+    s = compare_frustum(g, o, masked)
+    assert s["excluded"] <= 0.01 * s["pixels"] + 2
+
+
+def test_semitransparency_of_a_fully_masked_frame_is_the_eq4_frustum_filter(sess):
+    c = synth.make_clip("room", 64, 36, 7, seed=3)
+    sess.load(6, c)
+    mask = np.ones((c.F, c.H, c.W), np.uint8)
+    sess.ss.ssvp_set_mask(sess.ctx, 6, mask)
+    sx = 0.02
+    g, o, masked = _semi_both(sess, c, 6, mask, 3, 3, sigma_xyz=sx, crop=(5, 3, 41, 29))
+    compare_frustum(g, o, masked)
+    f = run_frustum(sess, 6, 3, crop=(5, 3, 41, 29), half_window=3, sigma_rgb=SEMI_SIGMA_RGB, sigma_xyz=sx)
+    assert np.abs(g.rgb - f.rgb).max() <= 1e-5

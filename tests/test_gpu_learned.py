@@ -224,22 +224,39 @@ def test_training_gradients_match_the_oracle(sess, clip):
               f"{float(np.max((err / np.abs(want))[np.abs(want) > 1e-2 * np.abs(want).max()])):.2e}")
 
 
-def test_short_training_lowers_the_loss(sess):
-    clips = [synth.make_clip("room", 160, 90, 10, seed=s) for s in (21, 22, 23)]
-    t = sess.torch
-    for i, c in enumerate(clips):
-        sess.load(41 + i, c)
+def test_trained_network_gains_over_the_plain_filter_on_held_out_clips(sess):
+    """What the learned weighting gains: the network is trained on the GPU (the library's own
+    forward and backward kernels and Adam) on 16 generated 320 x 180 x 24 room clips against their
+    clean renders, then both filters denoise 3 held-out clips (other seeds, so other scenes,
+    paths and noise) over +-8 frames.  The learned output must beat the plain Eq. 4 filter by at
+    least 0.3 dB of PSNR against the clean render on average and by 0.2 dB on every clip (about
+    0.6-0.7 dB is typical for this setup)."""
+    t, ss = sess.torch, sess.ss
+    W, H, F, T = 320, 180, 24, 8
+    ids = list(range(16))
+    clips = [synth.make_clip("room", W, H, F, seed=1000 + i) for i in ids]
+    for i, c in zip(ids, clips):
+        sess.load(i, c)
     clean = [t.from_numpy(c.clean).to(sess.dev) for c in clips]
-    p = sess.params(k=7, half_window=4)
-    cfg = sess.ss.ssvp_train_config(steps=300, batch_pixels=4096, lr=1e-3, bce_weight=0.1, seed=0, init=1)
-    losses = sess.ss.ssvp_train(sess.ctx, p, [41, 42, 43], clean, cfg)
-    assert np.isfinite(losses).all()
-    assert losses[-30:].mean() < losses[:30].mean()
-    held = synth.make_clip("room", 160, 90, 10, seed=29)
-    sess.load(44, held)
-    learned = sess.run(44, 5, mode=2, k=7, half_window=4, conf_threshold=0.5).rgb
-    plain = sess.run(44, 5, mode=0, k=7, half_window=4).rgb
-    psnr = lambda a: 10 * np.log10(1 / np.mean((a.astype(np.float64) - held.clean[5]) ** 2))
-    print(f"held-out PSNR: plain {psnr(plain):.3f} dB, learned {psnr(learned):.3f} dB, "
-          f"loss {losses[:30].mean():.5f} -> {losses[-30:].mean():.5f}")
-    assert psnr(learned) >= psnr(plain) - 0.3
+    p = sess.params(k=7, half_window=T)
+    cfg = ss.ssvp_train_config(steps=600, batch_pixels=16384, lr=1e-3, bce_weight=0.1, seed=0, init=1)
+    losses = ss.ssvp_train(sess.ctx, p, ids, clean, cfg)
+    assert np.isfinite(losses).all() and losses[-20:].mean() < losses[:20].mean()
+    for i in ids:
+        ss.ssvp_unload_clip(sess.ctx, i)
+    gains = []
+    for seed in (2000, 2001, 2002):
+        held = synth.make_clip("room", W, H, F, seed=seed)
+        sess.load(20, held)
+        res = {}
+        for mode in (ss.SSVP_MODE_DENOISE, ss.SSVP_MODE_LEARNED):
+            q = sess.params(mode=mode, k=7, half_window=T, frame_begin=T, frame_end=F - T, conf_threshold=0.5)
+            ss.ssvp_gather_filter(sess.ctx, q, [20])
+            out = t.empty((F - 2 * T, H, W, 3), dtype=t.float32, device=sess.dev)
+            ss.ssvp_read_output(sess.ctx, 20, T, F - T, out)
+            ss.ssvp_sync(sess.ctx)
+            res[mode] = oracle.psnr(out.cpu().numpy(), held.clean[T:F - T])
+        gains.append(res[ss.SSVP_MODE_LEARNED] - res[ss.SSVP_MODE_DENOISE])
+        print(f"held-out clip {seed}: plain {res[ss.SSVP_MODE_DENOISE]:.3f} dB, learned "
+              f"{res[ss.SSVP_MODE_LEARNED]:.3f} dB, gain {gains[-1]:+.3f} dB")
+    assert np.mean(gains) >= 0.3 and min(gains) >= 0.2, gains
