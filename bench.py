@@ -69,24 +69,79 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def _measured_traffic(workload, colour, out_frames):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this exact kernel."""
+# ncu summaries whose machine-readable block bench.py reads (per workload), and the kernel source
+# each was taken on: a figure is used only while that source is unchanged
+PROFILE_SUMMARIES = {"fhd": ("gather_kernel_counters_denoise_1080p.md", "ssvp_gather.cu")}
+# Algorithmic FP32 operations (an FMA counts as one) of the dominant kernel: per examined
+# candidate (the membership test) and per accepted sample (weight and accumulation)
+ALU_OPS = {
+    0: (8, 13, "window gather: per examined candidate the radius test (dz 2, X and Y 2 FMA, d^2 3, compare 1); "
+               "per accepted sample the Eq. 4 weight and Eq. 3 sums (colour differences 3, |dc|^2 3, exponent 2, "
+               "exp 1, sums 4)"),
+    1: (17, 14, "aperture gather: per box candidate the cone test (offset to the axis 6, distance and foot depth "
+                "6, cone radius 3, compare 2); per accepted sample the Eq. 14 weight and Eq. 3 sums"),
+    4: (10, 13, "frustum gather: per candidate the back-projection (3 FMA pairs) and Eq. 2's L1 test (2 adds, "
+                "2 compares, the product L h3); per sample the Eq. 4 weight and Eq. 3 sums"),
+}
+
+
+def _profile_figures(workload, colour, out_frames):
+    """The committed ncu summary's figures for this launch, if they were taken on this exact kernel
+    source, workload and launch size: DRAM bytes per launch and warp instructions per examined
+    candidate."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"gather_kernel_traffic_denoise_1080p.md")
-    src = os.path.join(ROOT, "paper_2102_03011_gb300", "csrc", "ssvp_gather.cu")
+    if workload not in PROFILE_SUMMARIES:
+        return {}
+    name, src_name = PROFILE_SUMMARIES[workload]
     try:
         kv = {}
-        for line in open(path):
+        for line in open(os.path.join(ROOT, "profiles", name)):
             if ":" in line and line.startswith("    "):
                 k, v = line.strip().split(":", 1)
                 kv[k.strip()] = v.strip()
+        src = os.path.join(ROOT, "paper_2102_03011_gb300", "csrc", src_name)
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if (kv.get("source_sha256") == sha and kv.get("workload") == workload and kv.get("colour") == colour
-                and int(kv.get("out_frames", -1)) == out_frames):
-            return int(kv["traffic_bytes_per_launch"])
+        if kv.get("source_sha256") != sha or kv.get("workload") != workload or kv.get("colour") != colour:
+            return {}
+        out = {"source": f"profiles/{name}"}
+        if int(kv.get("out_frames", -1)) == out_frames and "dram_bytes_per_launch" in kv:
+            out["traffic"] = int(kv["dram_bytes_per_launch"])
+        if "warp_inst_per_examined" in kv:
+            out["warp_inst_per_examined"] = float(kv["warp_inst_per_examined"])
+        return out
     except Exception:
-        pass
-    return None
+        return {}
+
+
+def roofline_block(mode, examined, accepted, kernel_ms, sm_mhz, peaks, peak_kind, prof, touched_bytes):
+    """The dominant kernel against the FP32 ALU roof it is bound by (its loads are served from L1,
+    its DRAM traffic is a few percent of HBM): algorithmic FP32 operations per launch / kernel time
+    against 152 SMs x 128 FP32 lanes x the SM clock sampled during the timed region.  Beside it the
+    measured issue-slot use, the DRAM fraction of HBM and the touched-bytes figure (L1 hits
+    included: not a roofline)."""
+    t = kernel_ms / 1e3
+    per_exam, per_acc, note = ALU_OPS[mode]
+    ops = per_exam * examined + per_acc * accepted
+    peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+    traffic = prof.get("traffic")
+    blk = {"bound": "alu", "achieved": ops / t / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": ops / t / 1e12 / peak,
+           "traffic": traffic, "kernel_ms": kernel_ms,
+           "accounting": f"{per_exam} FP32 operations per examined candidate + {per_acc} per accepted sample "
+                         f"(FMA = 1; {note}); peak = 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock "
+                         f"sampled during the timed region), derived, not measured"}
+    if traffic is not None:
+        blk["hbm"] = {"achieved": traffic / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                      "frac": traffic / t / 1e9 / peaks["hbm_gbs"],
+                      "accounting": f"DRAM bytes per launch ({prof['source']}) / kernel time, {peak_kind} peak"}
+    if "warp_inst_per_examined" in prof:
+        slots = 152 * 4 * sm_mhz * 1e6 * t
+        blk["issue"] = {"frac": prof["warp_inst_per_examined"] * examined / slots,
+                        "accounting": f"warp instructions per examined candidate ({prof['source']}) x examined "
+                                      "candidates / (152 SMs x 4 schedulers x SM clock x kernel time)"}
+    blk["touched_bytes"] = {"achieved": touched_bytes / t / 1e9, "unit": "GB/s",
+                            "frac_of_hbm": touched_bytes / t / 1e9 / peaks["hbm_gbs"],
+                            "note": "effective bytes of every candidate load, L1 hits included (not a roofline)"}
+    return blk
 
 
 def _peaks():
@@ -415,8 +470,9 @@ def run_batch(args, ss, torch, dev, stream, world, rank):
 
     e2e_ms = timed(e2e_step, max(1, min(args.steps, 2)))
     peaks, peak_kind = _peaks()
-    achieved = examined * 12 / (plan_ms / 1e3) / 1e9
     clk_summary = clk.summary()
+    roofline = roofline_block(0, examined, accepted, plan_ms, clk_summary["sm_mhz"] or 2070.0, peaks, peak_kind, {},
+                              12 * examined)
     line = {
         "metric": METRIC, "value": world * total_px / 1e6 / (plan_ms / 1e3), "unit": "Mpix/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": plan_ms, "higher_is_better": True,
@@ -438,10 +494,7 @@ def run_batch(args, ss, torch, dev, stream, world, rank):
         "psnr_db": {"output_vs_clean": float(np.mean(psnr_out)), "input_vs_clean": float(np.mean(psnr_in)),
                     "reference": "clean pinhole renders, mean over clips"},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "accounting": f"12 B per examined candidate (FP16 colour + depth touched), {peak_kind} peak",
-                     "kernel_ms": plan_ms},
+        "roofline": roofline,
         "e2e": {"value": world * total_px / 1e6 / (e2e_ms / 1e3), "unit": "Mpix/s",
                 "h2d_bytes_per_step": sum(c.rgb.nbytes + c.depth.nbytes for c in clips),
                 "d2h_bytes_per_step": sum(c.clean.nbytes for c in clips), "ms_per_step": e2e_ms},
@@ -622,10 +675,9 @@ def run_superres(args, ss, torch, dev, stream, world, rank):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
     peaks, peak_kind = _peaks()
     kernel_ms = float(np.mean(step_ms))
-    achieved = (4 * examined + 16 * accepted) / (kernel_ms / 1e3) / 1e9
     clk_summary = clk.summary()
-    sm_hz = (clk_summary["sm_mhz"] or 2070.0) * 1e6
-    fp32_peak = 152 * 128 * sm_hz / 1e12
+    roofline = roofline_block(4, examined, accepted, kernel_ms, clk_summary["sm_mhz"] or 2070.0, peaks, peak_kind, {},
+                              4 * examined + 16 * accepted)
     mpix = N_OUT * Wo * Ho / 1e6
     line = {
         "metric": METRIC, "value": world * mpix / (ms / 1e3), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
@@ -643,13 +695,7 @@ def run_superres(args, ss, torch, dev, stream, world, rank):
                     "bilinear_of_clean_input": psnr(bil_clean, clean_hr),
                     "reference": "clean render on the 1920x1080 grid (true poses)"},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "accounting": f"4 B depth per examined candidate + 16 B colour per sample, {peak_kind} peak",
-                     "kernel_ms": kernel_ms},
-        "roofline_alu": {"bound": "alu", "achieved": examined * 11 / (kernel_ms / 1e3) / 1e12, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": examined * 11 / (kernel_ms / 1e3) / 1e12 / fp32_peak,
-                         "accounting": "11 FP32 operations per examined candidate; peak = 152 SMs x 128 lanes x clock"},
+        "roofline": roofline,
         "e2e": {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s",
                 "h2d_bytes_per_step": clip.rgb.nbytes + clip.depth.nbytes, "d2h_bytes_per_step": out_h.numel() * 4,
                 "ms_per_step": e2e_ms},
@@ -928,27 +974,19 @@ def main():
     e2e_launches = -(-F // frames_per_chunk) + 6 + 1 + 2 + 1  # packs, median passes, depth range, gradient sums, gather
 
     peaks, peak_kind = _peaks()
-    bpc = BYTES_PER_CANDIDATE[args.colour]
     kernel_ms = float(np.mean(step_ms))
-    achieved = examined * bpc / (kernel_ms / 1e3) / 1e9
-    accounting = (f"{bpc} B per examined candidate (colour + depth touched), {peak_kind} peak; "
-                  "frac > 1 because window loads are served from L1 (traffic = DRAM bytes per launch)")
-    alu_ops = 8
-    alu_note = "8 FP32 operations per examined candidate (the distance test)"
     if MODE in (4, 8):
         cb = COLOUR_BYTES[args.colour]
         passes = 3 if MODE == 8 else 1  # inpainting scans S(p) three times (Eq. 8 mean, two Eq. 9 steps)
-        examined, accepted = passes * examined, passes * accepted
-        achieved = (4 * examined + cb * accepted) / (kernel_ms / 1e3) / 1e9
-        accounting = (f"4 B depth per examined candidate + {cb} B colour per sample, {peak_kind} peak; the hull "
-                      "pixels of neighbouring output pixels overlap, so most loads are cache hits")
-        alu_ops = 11
-        alu_note = "11 FP32 operations per examined candidate (back-projection and the L1 / depth-range test)"
-    bpc_note = accounting
-    traffic = _measured_traffic(args.workload, args.colour, N_OUT)
+        touched = passes * (4 * examined + cb * accepted)
+        rl_mode, rl_exam, rl_acc = 4, passes * examined, passes * accepted
+    else:
+        touched = examined * BYTES_PER_CANDIDATE[args.colour]
+        rl_mode, rl_exam, rl_acc = (1 if MODE == 1 else 0), examined, accepted
     clk_summary = clk.summary()
-    sm_hz = (clk_summary["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    fp32_peak = 152 * 128 * sm_hz / 1e12  # FP32 lane operations per second (TFLOP-equivalent)
+    sm_mhz = clk_summary["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    prof = _profile_figures(args.workload, args.colour, N_OUT)
+    roofline = roofline_block(rl_mode, rl_exam, rl_acc, kernel_ms, sm_mhz, peaks, peak_kind, prof, touched)
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -959,13 +997,7 @@ def main():
         "accepted_per_pixel": accepted / (N_OUT * W * H), "kept_weight_fraction": sum_w / max(accepted, 1),
         "psnr_db": {"output_vs_clean": psnr_out, "input_vs_clean": psnr_in, "reference": psnr_ref, **extra_quality},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "accounting": bpc_note, "kernel_ms": kernel_ms},
-        "roofline_alu": {"bound": "alu", "achieved": examined * alu_ops / (kernel_ms / 1e3) / 1e12,
-                         "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": examined * alu_ops / (kernel_ms / 1e3) / 1e12 / fp32_peak,
-                         "accounting": alu_note + "; peak = 152 SMs x 128 FP32 lanes x median SM clock"},
+        "roofline": roofline,
         "e2e": {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "gpu_launches_per_step": e2e_launches,
                 "pipelining": "two contexts on two streams, step i + 1 queued before step i is read back"

@@ -124,13 +124,40 @@ __device__ __forceinline__ unsigned short bf16_bits(float x) {
     const __nv_bfloat16 b = __float2bfloat16_rn(x);
     return *reinterpret_cast<const unsigned short *>(&b);
 }
-__device__ __forceinline__ unsigned bf16x2(float lo, float hi) { return pack2(bf16_bits(lo), bf16_bits(hi)); }
+// two floats rounded to BF16 in one conversion, the first in the low half
+__device__ __forceinline__ unsigned bf16x2(float lo, float hi) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned *>(&b);
+}
 __device__ __forceinline__ unsigned relu_bf16x2(float lo, float hi) {
     unsigned r;
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
 }
-__device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + log1pf(__expf(-fabsf(x))); }
+// softplus(x) = max(x, 0) + log(1 + y), y = e^-|x| in (0, 1]: log(1 + y) from the fast logarithm of
+// 1 + y (absolute error ~1e-7), or y itself below 1e-4 (relative error < y / 2), so every weight
+// keeps a relative error below ~1e-4 down to the smallest ones
+__device__ __forceinline__ float softplusf(float x) {
+    const float y = __expf(-fabsf(x));
+    return fmaxf(x, 0.0f) + (y < 1e-4f ? y : __logf(1.0f + y));
+}
+
+// Sums of (a, b, c, d) over the warp's 32 lanes in 6 shuffles: each exchange hands half of the
+// values still held to the partner lane, so that after the xor-16 and xor-8 steps every lane holds
+// one value (a for lanes with bits (4, 3) = (0, 0), b for (0, 1), c for (1, 0), d for (1, 1)),
+// which three more steps complete.  Returns the total of the lane's value.
+__device__ __forceinline__ float warp_sum4(float a, float b, float c, float d, int lane) {
+    const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0;
+    const float ka = h4 ? c : a, kb = h4 ? d : b;
+    const float sa = h4 ? a : c, sb = h4 ? b : d;
+    const float x = ka + __shfl_xor_sync(0xffffffffu, sa, 16);
+    const float y = kb + __shfl_xor_sync(0xffffffffu, sb, 16);
+    float v = (h3 ? y : x) + __shfl_xor_sync(0xffffffffu, h3 ? x : y, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
 __device__ __forceinline__ float sigmoidf(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 
 // Feature word w of one sample in the logical order (features 2w, 2w + 1, the lower in the low half)
@@ -301,21 +328,11 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpAr
                 sb = w * prev.c.z;
                 sc = sigmoidf(zc + b21);
             }
+            const float t4 = warp_sum4(sw, sr, sg, sb, lane);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sw += __shfl_xor_sync(0xffffffffu, sw, o);
-                sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                sg += __shfl_xor_sync(0xffffffffu, sg, o);
-                sb += __shfl_xor_sync(0xffffffffu, sb, o);
-                sc += __shfl_xor_sync(0xffffffffu, sc, o);
-            }
-            if (lane == 0) {
-                s_red[warp][0] = sw;
-                s_red[warp][1] = sr;
-                s_red[warp][2] = sg;
-                s_red[warp][3] = sb;
-                s_red[warp][4] = sc;
-            }
+            for (int o = 16; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
+            if ((lane & 7) == 0) s_red[warp][lane >> 3] = t4;
+            if (lane == 0) s_red[warp][4] = sc;
         }
         // 3. the next pair's loads, in flight during the waits below
         const long long pair_next = pair + gridDim.x;
@@ -407,21 +424,11 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpAr
             sb = w * prev.c.z;
             sc = sigmoidf(zc + b21);
         }
+        const float t4 = warp_sum4(sw, sr, sg, sb, lane);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sw += __shfl_xor_sync(0xffffffffu, sw, o);
-            sr += __shfl_xor_sync(0xffffffffu, sr, o);
-            sg += __shfl_xor_sync(0xffffffffu, sg, o);
-            sb += __shfl_xor_sync(0xffffffffu, sb, o);
-            sc += __shfl_xor_sync(0xffffffffu, sc, o);
-        }
-        if (lane == 0) {
-            s_red[warp][0] = sw;
-            s_red[warp][1] = sr;
-            s_red[warp][2] = sg;
-            s_red[warp][3] = sb;
-            s_red[warp][4] = sc;
-        }
+        for (int o = 16; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        if ((lane & 7) == 0) s_red[warp][lane >> 3] = t4;
+        if (lane == 0) s_red[warp][4] = sc;
         __syncthreads();
         if (s_row == 32 && prev.px < m.n_px) {
             const int w0 = warp - 1;

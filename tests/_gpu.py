@@ -255,15 +255,16 @@ def run_superres(sess: Session, cid, O, scale, crop=None, membership=False, **kw
 
 
 def compare_flagged(rgb: np.ndarray, o: oracle.Result):
-    """Colour parity where no GPU membership record exists (the batched plan): pixels holding a
-    candidate within 1e-5 relative of the radius or a window centre within the tie band (the
-    oracle's flags) are excluded; every other pixel must match within COLOUR_TOL.  Returns a
-    summary with the excluded count and the largest error at compared pixels."""
+    """Colour parity where no GPU membership record exists (the batched plan): every pixel must
+    match within COLOUR_TOL except pixels the oracle flags (a candidate within 1e-5 relative of
+    the radius or a window centre within the tie band), where membership may legitimately differ.
+    Returns the number of flagged pixels, how many of them actually differ by more than
+    COLOUR_TOL, and the largest error at unflagged pixels."""
     band = ((o.codes & oracle.CODE_BAND) != 0).any(axis=(-1, -2, -3))
     amb = ((o.amb == 1) & (o.status == 1)).any(-1)
     ok = ~(band | amb)
     cerr = np.abs(rgb.astype(np.float64) - o.rgb).max(-1)
     assert cerr[ok].max(initial=0.0) <= COLOUR_TOL, \
         f"colour max abs {cerr[ok].max()} > {COLOUR_TOL} at {np.argwhere(ok & (cerr > COLOUR_TOL))[:5]}"
-    return dict(pixels=int(ok.size), excluded=int((~ok).sum()), max_colour_err=float(cerr[ok].max(initial=0.0)),
-                max_colour_err_all=float(cerr.max()))
+    return dict(pixels=int(ok.size), flagged=int((~ok).sum()), differing=int((cerr > COLOUR_TOL).sum()),
+                max_colour_err=float(cerr[ok].max(initial=0.0)), max_colour_err_all=float(cerr.max()))

@@ -76,7 +76,7 @@ def test_autotuned_graph_plan_matches_the_oracle(setup):
         ss.ssvp_sync(sess.ctx)
     finally:
         ss.ssvp_plan_destroy(plan)
-    worst16, worst32, excluded, compared = 0.0, 0.0, 0, 0
+    worst16, worst32, flagged, differing, compared = 0.0, 0.0, 0, 0, 0
     for i, c in enumerate(clips):
         out = t.empty((c.F, c.H, c.W, 3), dtype=t.float32, device=sess.dev)
         ss.ssvp_read_output(sess.ctx, ids[i], 0, c.F, out)
@@ -93,15 +93,18 @@ def test_autotuned_graph_plan_matches_the_oracle(setup):
                 o16 = oracle.gather_filter(v16, prm, O, crop=crop, membership=True)
                 s = compare_flagged(g, o16)
                 worst16 = max(worst16, s["max_colour_err"])
-                excluded += s["excluded"]
+                flagged += s["flagged"]
+                differing += s["differing"]
                 compared += s["pixels"]
                 o32 = oracle.gather_filter(v32, prm, O, crop=crop)
                 worst32 = max(worst32, float(np.abs(g.astype(np.float64) - o32.rgb).max()))
     print(f"batched plan {cfg.tile_rows}x{cfg.frame_chunk}, {n_items} items: max |GPU - oracle on FP16 colours| = "
-          f"{worst16:.2e} over {compared} pixels ({excluded} band/tie pixels excluded); FP16 colour total error, "
-          f"max |GPU - FP64 oracle on FP32 colours| = {worst32:.2e}")
+          f"{worst16:.2e} over {compared} pixels outside the {flagged} flagged band/tie pixels, of which {differing} "
+          f"differ by more than {COLOUR_TOL}; FP16 colour total error, max |GPU - FP64 oracle on FP32 colours| = "
+          f"{worst32:.2e}")
     assert worst16 <= COLOUR_TOL
-    assert excluded <= 0.002 * compared + 4
+    # a flagged pixel differs only where a candidate on the radius or a tied window actually flipped
+    assert differing <= 0.002 * compared + 4
     # FP16 storage rounds each colour by at most 2^-12 (values below 1); the output is a weighted
     # mean, moved further only through the colour weights of outlying samples
     assert worst32 < 1e-2

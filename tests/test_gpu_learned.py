@@ -206,16 +206,19 @@ def test_training_gradients_match_the_oracle(sess, clip):
         of[ys, xs], oc[ys, xs], on[ys, xs], op[ys, xs], clean[ys, xs], W1, b1, W2, b2, round_bf16=True,
         term_scale=True)
     assert g[1218] == pytest.approx(L, rel=1e-4)
-    # Element by element: |GPU - oracle| <= 1e-3 |oracle| + c * (sum of |terms| of the entry).
-    # c covers the rounding of the terms: FP32 accumulation and the rare flip of a BF16 rounding of
-    # a hidden activation (2e-4); for dW1 also the BF16 rounding of dH, the operand of the dW1
-    # tensor-core product, which perturbs each term by at most 2^-8 of itself.
+    # Element by element: |GPU - oracle| <= 1e-3 |oracle| + c * (sum of |terms| of the entry)
+    # + 1e-6 * (the largest such sum of the block).  c covers the rounding of the terms: FP32
+    # accumulation and the rare flip of a BF16 rounding of a hidden activation (2e-4); for dW1 also
+    # the BF16 rounding of dH, the operand of the dW1 tensor-core product, which perturbs each term
+    # by at most 2^-8 of itself.  The last, absolute floor covers ReLU gates whose pre-activation
+    # lies within FP32 rounding of zero, which may open on one side only: such an entry's oracle
+    # terms can all be ~1e-22 (a unit that barely fires) while the other side holds one more.
     parts = [("gW1", g[:1024], gW1.ravel(), aW1.ravel(), 2.0 ** -8 + 2e-4),
              ("gb1", g[1024:1088], gb1, ab1, 2e-4), ("gW2", g[1088:1216], gW2.ravel(), aW2.ravel(), 2e-4),
              ("gb2", g[1216:1218], gb2, ab2, 2e-4)]
     for name, got, want, scale, c in parts:
         err = np.abs(got - want)
-        tol = 1e-3 * np.abs(want) + c * scale
+        tol = 1e-3 * np.abs(want) + c * scale + 1e-6 * scale.max()
         bad = np.flatnonzero(err > tol)
         assert bad.size == 0, (name, bad[:5], err[bad[:5]], tol[bad[:5]])
         # stated: the largest error in units of the entry's term scale
