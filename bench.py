@@ -745,7 +745,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config("fp32"),
+            "config": _config(args.colour),
             "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": s["cores"], "kind": "oracle",
                              "sample": s["sample"] + " per step"},
             "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -761,7 +761,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--colour", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--colour", default=None, choices=["fp32", "fp16"],
+                    help="colour storage (default: fp16 for the virtual-aperture workloads, fp32 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fhd", choices=sorted(WORKLOADS))
     ap.add_argument("--out-frames", type=int, default=None, help="output frames per step (default per workload)")
@@ -773,6 +774,9 @@ def main():
     W, H, F, T, K_WIN, O_BEGIN, N_OUT, MODE = WORKLOADS[args.workload]
     if args.out_frames:
         N_OUT = args.out_frames
+    if args.colour is None:
+        # the 1080p virtual-aperture workload stores colour in FP16 (geometry and sums in FP32)
+        args.colour = "fp16" if MODE == 1 else "fp32"
     if args.impl == "reference":
         return run_reference(args)
 
