@@ -78,7 +78,6 @@ struct ssvp_plan {
     long long n_items = 0;
     int grid = 0;
     PairGeom *d_geom = nullptr;
-    ssvp::BatchClip *d_clips = nullptr;
     unsigned long long *d_counter = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -1089,6 +1088,17 @@ int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median) {
     return SSVP_OK;
 }
 
+// Kernel arguments of a batched launch: the clip table goes by value into the parameter space
+ssvp::BatchArgs batch_args(const BatchSetup &bs, int n_clips, int frame_chunk, unsigned long long *counter) {
+    ssvp::BatchArgs b{};
+    b.n_clips = n_clips;
+    b.frame_chunk = frame_chunk;
+    b.n_items = bs.n_items;
+    b.counter = counter;
+    for (int i = 0; i < n_clips && i < ssvp::kMaxBatchClips; ++i) b.clip[i] = bs.clips[i];
+    return b;
+}
+
 int ssvp_autotune(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, int n_clips, ssvp_plan_config *best) {
     if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
     int cfmt = 0;
@@ -1098,7 +1108,6 @@ int ssvp_autotune(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids,
     BatchSetup bs;
     batch_tables(ctx, *params, clip_ids, n_clips, 4, bs);
     PairGeom *d_geom = nullptr;
-    ssvp::BatchClip *d_clips = nullptr;
     unsigned long long *d_counter = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaSuccess;
@@ -1108,16 +1117,13 @@ int ssvp_autotune(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids,
     GatherArgs a = batch_gather_args(ctx, *params);
     do {
         if ((e = cudaMalloc(&d_geom, bs.geom.size() * sizeof(PairGeom))) != cudaSuccess) break;
-        if ((e = cudaMalloc(&d_clips, bs.clips.size() * sizeof(ssvp::BatchClip))) != cudaSuccess) break;
         if ((e = cudaMalloc(&d_counter, sizeof(unsigned long long))) != cudaSuccess) break;
         if ((e = cudaMemcpy(d_geom, bs.geom.data(), bs.geom.size() * sizeof(PairGeom), cudaMemcpyHostToDevice)) != cudaSuccess) break;
         if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) break;
         for (const auto &cfg : cands) {
             batch_items(bs, cfg, d_geom);
-            if ((e = cudaMemcpyAsync(d_clips, bs.clips.data(), bs.clips.size() * sizeof(ssvp::BatchClip),
-                                     cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess) break;
             const int grid = ssvp::batch_grid(params->k, cfg.tile_rows, cfmt, bs.ns);
-            ssvp::BatchArgs b{d_clips, n_clips, cfg.frame_chunk, bs.n_items, d_counter};
+            const ssvp::BatchArgs b = batch_args(bs, n_clips, cfg.frame_chunk, d_counter);
             float ms = 0.0f;
             for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
                 if (rep == 1 && (e = cudaEventRecord(e0, ctx->stream)) != cudaSuccess) break;
@@ -1135,7 +1141,6 @@ int ssvp_autotune(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids,
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(ctx->stream);
     if (d_geom) cudaFree(d_geom);
-    if (d_clips) cudaFree(d_clips);
     if (d_counter) cudaFree(d_counter);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
     bool stored = false;
@@ -1159,7 +1164,6 @@ void ssvp_plan_destroy(ssvp_plan *plan) {
     if (plan->graph) cudaGraphDestroy(plan->graph);
     if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
     if (plan->d_geom) cudaFree(plan->d_geom);
-    if (plan->d_clips) cudaFree(plan->d_clips);
     if (plan->d_counter) cudaFree(plan->d_counter);
     delete plan;
 }
@@ -1192,13 +1196,11 @@ int ssvp_plan_create(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_i
     do {
         what = "cudaMalloc (plan)";
         if ((e = cudaMalloc(&plan->d_geom, bs.geom.size() * sizeof(PairGeom))) != cudaSuccess) break;
-        if ((e = cudaMalloc(&plan->d_clips, bs.clips.size() * sizeof(ssvp::BatchClip))) != cudaSuccess) break;
         if ((e = cudaMalloc(&plan->d_counter, sizeof(unsigned long long))) != cudaSuccess) break;
         batch_items(bs, cfg, plan->d_geom);
         plan->n_items = bs.n_items;
         what = "cudaMemcpy (plan)";
         if ((e = cudaMemcpy(plan->d_geom, bs.geom.data(), bs.geom.size() * sizeof(PairGeom), cudaMemcpyHostToDevice)) != cudaSuccess) break;
-        if ((e = cudaMemcpy(plan->d_clips, bs.clips.data(), bs.clips.size() * sizeof(ssvp::BatchClip), cudaMemcpyHostToDevice)) != cudaSuccess) break;
         plan->grid = ssvp::batch_grid(params->k, cfg.tile_rows, cfmt, bs.ns);
         what = "occupancy";
         if (plan->grid <= 0) { e = cudaErrorInvalidConfiguration; break; }
@@ -1206,7 +1208,7 @@ int ssvp_plan_create(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_i
         if ((e = cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
         GatherArgs a = batch_gather_args(ctx, *params);
-        ssvp::BatchArgs b{plan->d_clips, n_clips, cfg.frame_chunk, plan->n_items, plan->d_counter};
+        const ssvp::BatchArgs b = batch_args(bs, n_clips, cfg.frame_chunk, plan->d_counter);
         cudaError_t e1 = cudaMemsetAsync(plan->d_counter, 0, sizeof(unsigned long long), plan->cap_stream);
         cudaError_t e2 = cudaMemsetAsync(ctx->stat_counts, 0, 2 * sizeof(unsigned long long), plan->cap_stream);
         cudaError_t e3 = cudaMemsetAsync(ctx->stat_sumw, 0, sizeof(double), plan->cap_stream);

@@ -439,17 +439,16 @@ __global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const G
 
 // Persistent batched gather (A10): CTAs of 32 x TY threads pull work items (clip, output-frame
 // chunk, tile) from a device counter until the list is exhausted, so clips of uneven size share
-// one launch without tail effects per clip.
+// one launch without tail effects per clip.  The clip table is read from the kernel's parameter
+// space (constant bank), so the per-clip plane pointers and strides need no registers.
 template <int K, int CFMT, int TY>
 __global__ void __launch_bounds__(32 * TY, 32 / TY) batch_kernel(const GatherArgs a, const BatchArgs b) {
     constexpr int NT = 32 * TY;
     extern __shared__ float4 sgeom[];
     __shared__ float s_const[4];
-    __shared__ Planes s_P;
     // the work unit (one output frame of one item), kept in shared memory by thread 0 so that no
     // loop state stays live in registers across the gather
-    __shared__ const PairGeom *s_geom;
-    __shared__ int s_c, s_O, s_u0, s_v0, s_oi, s_olast, s_done;
+    __shared__ int s_c, s_u0, s_v0, s_oi, s_olast, s_done;
     __shared__ unsigned long long s_cnt[2][NT / 32];
     __shared__ double s_w[NT / 32];
     const int warp = threadIdx.x >> 5;
@@ -469,9 +468,9 @@ __global__ void __launch_bounds__(32 * TY, 32 / TY) batch_kernel(const GatherArg
                     s_done = 1;
                 } else {
                     c = 0;
-                    while (c + 1 < b.n_clips && b.clips[c + 1].item_begin <= item) ++c;
+                    while (c + 1 < b.n_clips && b.clip[c + 1].item_begin <= item) ++c;
                     s_c = c;
-                    const BatchClip &bc = b.clips[c];
+                    const BatchClip &bc = b.clip[c];
                     const long long local = item - bc.item_begin;
                     const int ntile = bc.tiles_x * bc.tiles_y;
                     const int tile = (int)(local % ntile), chunk = (int)(local / ntile);
@@ -482,11 +481,7 @@ __global__ void __launch_bounds__(32 * TY, 32 / TY) batch_kernel(const GatherArg
                 }
             }
             if (c >= 0) {
-                const BatchClip &bc = b.clips[c];
-                s_P = bc.p;
-                s_O = bc.frame_begin + s_oi;
-                s_geom = bc.geom + (long long)s_oi * a.n_slots;
-                const float r = a.radius > 0.0f ? a.radius : -a.radius * *bc.p.median;
+                const float r = a.radius > 0.0f ? a.radius : -a.radius * *b.clip[c].p.median;
                 const float sx = a.sigma_xyz > 0.0f ? a.sigma_xyz : r;
                 s_const[0] = r * r;
                 s_const[1] = kLog2e / (2.0f * a.sigma_rgb * a.sigma_rgb);
@@ -496,16 +491,19 @@ __global__ void __launch_bounds__(32 * TY, 32 / TY) batch_kernel(const GatherArg
         }
         __syncthreads();
         if (s_done) break;
+        const int c = s_c, oi = s_oi, u0 = s_u0, v0 = s_v0;
+        const BatchClip &bc = b.clip[c];
+        const PairGeom *geom = bc.geom + (long long)oi * a.n_slots;
         for (int j = threadIdx.x; j < a.n_slots; j += NT)
-            build_slot(s_geom[j], (float)s_u0, (float)s_v0, sgeom + kSlotVec * j);
+            build_slot(geom[j], (float)u0, (float)v0, sgeom + kSlotVec * j);
         __syncthreads();
-        const int u0 = s_u0, v0 = s_v0;
         const int u = u0 + (threadIdx.x & 31), v = v0 + (threadIdx.x >> 5);
-        const bool active = u < s_P.W && v < s_P.H;
+        const bool active = u < bc.p.W && v < bc.p.H;
         int n_acc = 0, n_exam = 0;
         float acc_w = 0.0f;
-        gather_pixel<K, CFMT, false, false, 2>(a, s_P, s_O, u0, v0, u, v, active, 0, sgeom, a.n_slots, s_const[0], s_const[1],
-                                     s_const[2], s_const[3] != 0.0f, n_acc, n_exam, acc_w);
+        gather_pixel<K, CFMT, false, false, 2>(a, bc.p, bc.frame_begin + oi, u0, v0, u, v, active, 0, sgeom, a.n_slots,
+                                               s_const[0], s_const[1], s_const[2], s_const[3] != 0.0f, n_acc, n_exam,
+                                               acc_w);
         // launch statistics go to per-warp shared slots after every tile
         unsigned ce = (unsigned)n_exam, ca = (unsigned)n_acc;
         float sw = acc_w;

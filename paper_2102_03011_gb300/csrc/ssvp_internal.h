@@ -103,11 +103,15 @@ struct BatchClip {
     long long item_begin;
 };
 
+constexpr int kMaxBatchClips = 64;  // SSVP_MAX_CLIPS
+
 struct BatchArgs {
-    const BatchClip *clips;
     int n_clips, frame_chunk;
     long long n_items;
     unsigned long long *counter;  // work counter, zero before the launch
+    // the clip table itself travels in the kernel's parameter space: read-only constant-bank data
+    // that the compiler may reload at will instead of holding it in registers
+    BatchClip clip[kMaxBatchClips];
 };
 
 // ---------------------------------------------------------------- learned per-sample weights

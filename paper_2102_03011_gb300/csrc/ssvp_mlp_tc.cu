@@ -95,9 +95,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
     return false;
 }
 
-// 32 consecutive FP32 columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
-    unsigned r[32];
+// 32 consecutive FP32 columns of this thread's tensor-memory lane; the caller waits
+// (tcgen05.wait::ld) before using them, so that several loads share one wait
+__device__ __forceinline__ void tmem_ld32_nowait(unsigned taddr, unsigned (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
@@ -106,10 +106,8 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld2(unsigned taddr, float &a, float &b) {
     unsigned r0, r1;
@@ -343,14 +341,18 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpAr
         fence_after();
         {
             unsigned char *A2 = sm + (a2 - sbase);
+            // both halves of the row in flight together, one wait
+            unsigned v0[32], v1[32];
+            tmem_ld32_nowait(d_st + lane_base, v0);
+            tmem_ld32_nowait(d_st + lane_base + 32, v1);
+            tmem_wait_ld();
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
-                float v[32];
-                tmem_ld32(d_st + lane_base + 32 * half, v);
+                const unsigned (&v)[32] = half ? v1 : v0;
                 unsigned h[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
-                    h[i] = relu_bf16x2(v[2 * i], v[2 * i + 1]);
+                    h[i] = relu_bf16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     *reinterpret_cast<uint4 *>(A2 + core_off(tid, 4 * half + q, 8)) =
