@@ -248,7 +248,12 @@ int ssvp_set_stream(ssvp_ctx *ctx, void *cuda_stream);
  * (SSVP_COLOUR_F32 or SSVP_COLOUR_F16, round to nearest even); depth is always stored as FP32.
  * The lower-median valid depth is computed on the device for relative radii.
  * Sizes: 1 <= W, H <= 16384, 1 <= F <= 65535.  The copy is queued: the caller's buffers may be
- * reused once the context's stream has passed this call (ssvp_sync() waits for it).  Reloading
+ * reused once the context's stream has passed this call (ssvp_sync() waits for it).  The load
+ * itself runs on the context's internal stream of the device's highest priority, after the
+ * work queued on the context's stream before the call; the context's stream waits for it, so
+ * work queued after the call sees the new clip.  (Its kernels are short: at high priority they
+ * overlap a long gather another context runs on another stream.)  Host inputs up to 4 GB go to
+ * the device in one copy through a staging buffer the context keeps.  Reloading
  * an id with the same W, H, F and colour_fmt (and no inpainting mask set) reuses its device
  * planes without allocating; work already queued on the stream still sees the old contents.
  * Any reload invalidates batched plans that include the id.

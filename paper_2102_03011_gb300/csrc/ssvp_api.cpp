@@ -46,6 +46,12 @@ struct ssvp_ctx {
     size_t geom_cap = 0;  // entries
     void *staging = nullptr;
     size_t staging_bytes = 0;
+    // Loads run on an internal stream of the device's highest priority, ordered after the work
+    // already queued on the context's stream and before everything queued after the load: their
+    // short kernels (pack, median, depth ranges, gradient sums) then start as soon as SMs free up,
+    // instead of queueing behind a long gather launched on another stream
+    cudaStream_t load_stream = nullptr;
+    cudaEvent_t ev_load_in = nullptr, ev_load_out = nullptr;
     std::vector<PairGeom> host_geom;
     unsigned clip_generation[SSVP_MAX_CLIPS] = {};
     // learned filter: weights and training state, scratch of one frame's capped sample sets
@@ -535,6 +541,15 @@ int ssvp_create(ssvp_ctx **out, int cuda_device, void *cuda_stream) {
     if (!ctx) return fail(nullptr, SSVP_ENOMEM, "host allocation failed");
     ctx->device = cuda_device;
     ctx->stream = (cudaStream_t)cuda_stream;
+    int prio_least = 0, prio_greatest = 0;
+    if ((e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest)) != cudaSuccess ||
+        (e = cudaStreamCreateWithPriority(&ctx->load_stream, cudaStreamNonBlocking, prio_greatest)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->ev_load_in, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->ev_load_out, cudaEventDisableTiming)) != cudaSuccess) {
+        int rc = fail(nullptr, SSVP_ECUDA, "load stream: %s", cudaGetErrorString(e));
+        ssvp_destroy(ctx);
+        return rc;
+    }
     if ((e = cudaMalloc(&ctx->stat_counts, 2 * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMalloc(&ctx->stat_sumw, sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&ctx->median_scratch, ssvp::median_scratch_words() * sizeof(unsigned int))) != cudaSuccess ||
@@ -554,6 +569,7 @@ void ssvp_destroy(ssvp_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->load_stream) cudaStreamSynchronize(ctx->load_stream);
     for (auto &c : ctx->clips) free_clip(c);  // plans of this context must be destroyed first
     if (ctx->stat_counts) cudaFree(ctx->stat_counts);
     if (ctx->stat_sumw) cudaFree(ctx->stat_sumw);
@@ -565,6 +581,9 @@ void ssvp_destroy(ssvp_ctx *ctx) {
     free_sets(ctx->l_sets);
     for (void *q : {(void *)ctx->mlp_buf, (void *)ctx->mlp_w1, (void *)ctx->l_loss, (void *)ctx->l_batch})
         if (q) cudaFree(q);
+    if (ctx->ev_load_in) cudaEventDestroy(ctx->ev_load_in);
+    if (ctx->ev_load_out) cudaEventDestroy(ctx->ev_load_out);
+    if (ctx->load_stream) cudaStreamDestroy(ctx->load_stream);
     delete ctx;
 }
 
@@ -594,6 +613,7 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
                        c.p.mask == nullptr;
     if (c.loaded && !reuse) {
         CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        CK(cudaStreamSynchronize(ctx->load_stream), "cudaStreamSynchronize");
         free_clip(c);
     }
     Planes &p = c.p;
@@ -619,20 +639,30 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
         free_clip(c);
         return cuda_fail(ctx, e, "cudaMalloc (clip planes)");
     }
-    // padding and invalid depth: NaN (all bits set); colour 0; output 0
-    CK(cudaMemsetAsync(p.depth, 0xff, nplane * sizeof(float), ctx->stream), "cudaMemsetAsync");
-    CK(cudaMemsetAsync(p.colour, 0, nplane * texel, ctx->stream), "cudaMemsetAsync");
-    CK(cudaMemsetAsync(p.out, 0, nout * sizeof(float), ctx->stream), "cudaMemsetAsync");
+    // the load's work goes to the high-priority load stream, after everything already queued on
+    // the context's stream (which may still read the planes being replaced)
+    cudaStream_t ls = ctx->load_stream;
+    CK(cudaEventRecord(ctx->ev_load_in, ctx->stream), "cudaEventRecord");
+    CK(cudaStreamWaitEvent(ls, ctx->ev_load_in, 0), "cudaStreamWaitEvent");
+    // padding and invalid depth: NaN (all bits set); colour 0; output 0.  A reload keeps the
+    // padding of the planes it reuses (the packing rewrites every pixel inside them)
+    if (!reuse) {
+        CK(cudaMemsetAsync(p.depth, 0xff, nplane * sizeof(float), ls), "cudaMemsetAsync");
+        CK(cudaMemsetAsync(p.colour, 0, nplane * texel, ls), "cudaMemsetAsync");
+    }
+    CK(cudaMemsetAsync(p.out, 0, nout * sizeof(float), ls), "cudaMemsetAsync");
     const size_t frame_px = (size_t)W * H;
     if (mem_kind == SSVP_MEM_DEVICE) {
-        CK(ssvp::launch_pack(rgb, depth, W, H, F, p, 0, ctx->stream), "pack kernel");
+        CK(ssvp::launch_pack(rgb, depth, W, H, F, p, 0, ls), "pack kernel");
     } else {
-        // stage frames through a device buffer in chunks of about 256 MB
+        // stage the frames through a device buffer: the whole clip in one copy up to 4 GB (the
+        // copy engines then run without waiting for a pack kernel between chunks), larger clips
+        // in chunks of that size
         const size_t per_frame = frame_px * 16;
-        int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)F, (size_t)(256u << 20) / per_frame));
+        int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)F, ((size_t)4 << 30) / per_frame));
         const size_t need = per_frame * (size_t)chunk;
         if (ctx->staging_bytes < need) {
-            CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+            CK(cudaStreamSynchronize(ls), "cudaStreamSynchronize");
             if (ctx->staging) cudaFree(ctx->staging);
             ctx->staging = nullptr;
             ctx->staging_bytes = 0;
@@ -647,15 +677,18 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
         for (int f0 = 0; f0 < F; f0 += chunk) {
             int nf = std::min(chunk, F - f0);
             CK(cudaMemcpyAsync(srgb, rgb + frame_px * 3 * (size_t)f0, frame_px * 3 * nf * sizeof(float),
-                               cudaMemcpyHostToDevice, ctx->stream), "cudaMemcpyAsync (rgb)");
+                               cudaMemcpyHostToDevice, ls), "cudaMemcpyAsync (rgb)");
             CK(cudaMemcpyAsync(sdep, depth + frame_px * (size_t)f0, frame_px * nf * sizeof(float), cudaMemcpyHostToDevice,
-                               ctx->stream), "cudaMemcpyAsync (depth)");
-            CK(ssvp::launch_pack(srgb, sdep, W, H, nf, p, f0, ctx->stream), "pack kernel");
+                               ls), "cudaMemcpyAsync (depth)");
+            CK(ssvp::launch_pack(srgb, sdep, W, H, nf, p, f0, ls), "pack kernel");
         }
     }
-    CK(ssvp::launch_median(p, ctx->median_scratch, ctx->stream), "median kernels");
-    CK(ssvp::launch_zrange(p, ctx->stream), "depth range kernel");
-    CK(ssvp::launch_grad_sum(p, ctx->stream), "gradient sum kernels");
+    CK(ssvp::launch_median(p, ctx->median_scratch, ls), "median kernels");
+    CK(ssvp::launch_zrange(p, ls), "depth range kernel");
+    CK(ssvp::launch_grad_sum(p, ls), "gradient sum kernels");
+    // everything queued on the context's stream from here on runs after the load
+    CK(cudaEventRecord(ctx->ev_load_out, ls), "cudaEventRecord");
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_load_out, 0), "cudaStreamWaitEvent");
     c.loaded = true;
     c.has_cams = false;
     c.generation = ++ctx->clip_generation[clip_id];
