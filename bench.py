@@ -937,7 +937,7 @@ def main():
     rgb_h = torch.from_numpy(clip.rgb).pin_memory()
     dep_h = torch.from_numpy(clip.depth).pin_memory()
     out_h = torch.empty((N_OUT, H, W, 3), dtype=torch.float32).pin_memory()
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(2, min(args.steps, 10))
 
     # Steps alternate between two contexts on two streams (double buffering, as a streaming
     # deployment would): step i + 1's upload and gather are queued before step i's output is read

@@ -99,6 +99,21 @@ def test_tensor_core_inference_matches_the_oracle(sess, clip):
             worst = max(worst, float(np.abs(g.rgb[y, x] - ofin).max()))
     assert worst <= 1e-3, worst
     assert near < 0.01 * cw * ch
+    # stated: the total error of the BF16 tensor-core arithmetic, against the oracle without the
+    # BF16 rounding of features, weights and hidden activations (FP64 throughout)
+    total = 0.0
+    for y in range(ch):
+        for x in range(cw):
+            if not ok[y, x]:
+                continue
+            _, o64, conf64, _ = oracle.mlp_pixel(of[y, x], oc[y, x], on[y, x], W1, b1, W2, b2, round_bf16=False,
+                                                 plain=op[y, x])
+            if abs(conf64 - 0.5) < 2e-2:
+                continue  # BF16 rounding may move the confidence across the threshold
+            total = max(total, float(np.abs(g.rgb[y, x] - o64).max()))
+    print(f"learned inference: max |GPU - oracle with BF16 rounding| = {worst:.2e}, "
+          f"max |GPU - FP64 oracle without it| = {total:.2e}")
+    assert total < 5e-2
 
 
 @pytest.mark.parametrize("crop,radius_rel", [((3, 5, 17, 9), 0.02), ((3, 5, 17, 9), 0.03), ((0, 0, 96, 54), 0.005)])
