@@ -310,8 +310,9 @@ typedef struct ssvp_plan_config {
 } ssvp_plan_config;
 
 /* Autotuner: times every (tile_rows, frame_chunk) candidate on a sample of the plan's work (the
- * first 4 output frames of every listed clip) and keeps the fastest in the context for later
- * plans with the same k, half window, mode and colour format; *best (may be NULL) receives it. */
+ * first 8 output frames of every listed clip: tile_rows 4 or 8 x frame_chunk 1, 2, 4 or 8) and
+ * keeps the fastest in the context for later plans with the same k, half window, mode and
+ * colour format; *best (may be NULL) receives it. */
 int ssvp_autotune(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, int n_clips, ssvp_plan_config *best);
 
 /* Create a plan.  config NULL: the context's tuned shape for these parameters if any, else

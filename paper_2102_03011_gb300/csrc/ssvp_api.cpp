@@ -1139,14 +1139,14 @@ int ssvp_autotune(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids,
     if (rc != SSVP_OK) return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     BatchSetup bs;
-    batch_tables(ctx, *params, clip_ids, n_clips, 4, bs);
+    batch_tables(ctx, *params, clip_ids, n_clips, 8, bs);
     PairGeom *d_geom = nullptr;
     unsigned long long *d_counter = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaSuccess;
     ssvp_plan_config winner{8, 1};
     float best_ms = 3.0e38f;
-    const ssvp_plan_config cands[] = {{4, 1}, {4, 2}, {4, 4}, {8, 1}, {8, 2}, {8, 4}};
+    const ssvp_plan_config cands[] = {{4, 1}, {4, 2}, {4, 4}, {4, 8}, {8, 1}, {8, 2}, {8, 4}, {8, 8}};
     GatherArgs a = batch_gather_args(ctx, *params);
     do {
         if ((e = cudaMalloc(&d_geom, bs.geom.size() * sizeof(PairGeom))) != cudaSuccess) break;
