@@ -423,6 +423,9 @@ void free_sets(ssvp::SampleSets &S) {
 }
 
 int learned_scratch(ssvp_ctx *ctx, size_t n_px) {
+    // the kernels address a crop's sets with one 32-bit sample index (pixel * 64 + slot)
+    if (n_px * 64 > 0xffffffffull)
+        return fail(ctx, SSVP_EINVAL, "the learned filter takes crops of at most 67,108,863 pixels (have %zu)", n_px);
     if (n_px <= ctx->l_cap) return SSVP_OK;
     CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     free_sets(ctx->l_sets);

@@ -52,11 +52,19 @@ __device__ __forceinline__ unsigned bf16_pair(float lo, float hi) {
     const __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const unsigned *>(&b2);
 }
-__device__ __forceinline__ void store_sample(const GatherArgs &a, long long crop_idx, int slot, float3 c, float dist_r,
-                                             float dj_t, float dz_r, float logw) {
-    const long long i = crop_idx * kMaxSamples + slot;
+// i = crop pixel * 64 + slot: the host keeps the sets of a crop below 2^32 samples, so one 32-bit
+// index (widened in the address arithmetic) addresses both arrays
+__device__ __forceinline__ void store_sample(const GatherArgs &a, unsigned i, float3 c, float dist_r, float dj_t,
+                                             float dz_r, float logw) {
     a.sets.col[i] = make_float4(c.x, c.y, c.z, __uint_as_float(bf16_pair(dist_r, dj_t)));
     a.sets.f89[i] = bf16_pair(dz_r, logw);
+}
+// the distance feature is rounded to BF16 (8 significant bits): the approximate square root
+// (a few FP32 ulp, exact at 0) is enough
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // LEARN: visit the frames in canonical order (O, O-1, O+1, ...) and store the features of the
@@ -76,6 +84,7 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
     int n_feat = 0;
     const int Tw = (n_slots - 1) >> 1;
     const float inv_r = LEARN ? rsqrtf(r2) : 0.0f, inv_T = LEARN ? 1.0f / (float)max(Tw, 1) : 0.0f;
+    const unsigned set0 = LEARN ? (unsigned)crop_idx * (unsigned)kMaxSamples : 0u;
     float3 cref = make_float3(0.f, 0.f, 0.f);
     float dref = 0.0f;
     if (active) {
@@ -142,6 +151,7 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
             const void *cwin = CFMT == 0 ? (const void *)(reinterpret_cast<const float4 *>(P.colour) + wbase)
                                          : (const void *)(reinterpret_cast<const uint2 *>(P.colour) + wbase);
             const float beta = q5.z;
+            const float dj_t = LEARN ? (float)(j - Tw) * inv_T : 0.0f;  // the frame-offset feature
             if (DEBUG && rec) { rec[0] = 1; rec[1] = cx; rec[2] = cy; }
 
             if (K > 0) {
@@ -238,13 +248,13 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                             f2_unpack(d2, dd0, dd1);
                             f2_unpack(dz, dz0, dz1);
                             if (n_feat < kMaxSamples) {
-                                store_sample(a, crop_idx, n_feat, cq[0], sqrtf(dd0) * inv_r, (float)(j - Tw) * inv_T,
-                                             dz0 * inv_r, -e0 * kLn2);
+                                store_sample(a, set0 + n_feat, cq[0], sqrt_approx(dd0) * inv_r, dj_t, dz0 * inv_r,
+                                             -e0 * kLn2);
                                 ++n_feat;
                             }
                             if (ok[1] && n_feat < kMaxSamples) {
-                                store_sample(a, crop_idx, n_feat, cq[1], sqrtf(dd1) * inv_r, (float)(j - Tw) * inv_T,
-                                             dz1 * inv_r, -e1 * kLn2);
+                                store_sample(a, set0 + n_feat, cq[1], sqrt_approx(dd1) * inv_r, dj_t, dz1 * inv_r,
+                                             -e1 * kLn2);
                                 ++n_feat;
                             }
                         }
@@ -267,8 +277,8 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                         float w = 1.0f;
                         if (weighted) w = ex2(-e);
                         if (LEARN && ok[t] && n_feat < kMaxSamples) {
-                            store_sample(a, crop_idx, n_feat, cq[t], sqrtf(d2) * inv_r, (float)(j - Tw) * inv_T,
-                                         dz * inv_r, -e * kLn2);
+                            store_sample(a, set0 + n_feat, cq[t], sqrt_approx(d2) * inv_r, dj_t, dz * inv_r,
+                                         -e * kLn2);
                             ++n_feat;
                         }
                         if (ok[t]) {
@@ -329,8 +339,7 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                         float w = 1.0f;
                         if (weighted) w = ex2(-e);
                         if (LEARN && n_feat < kMaxSamples) {
-                            store_sample(a, crop_idx, n_feat, c, sqrtf(d2) * inv_r, (float)(j - Tw) * inv_T, dz * inv_r,
-                                         -e * kLn2);
+                            store_sample(a, set0 + n_feat, c, sqrt_approx(d2) * inv_r, dj_t, dz * inv_r, -e * kLn2);
                             ++n_feat;
                         }
                         acc_r = fmaf(w, er, acc_r);
