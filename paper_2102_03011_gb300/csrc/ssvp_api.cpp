@@ -1385,11 +1385,10 @@ int ssvp_mlp_grad(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, const i
     m.clean = clean;
     m.bce_w = 0.1f;
     m.grad = ctx->mlp.grad;
-    CK(ssvp::launch_mlp_train(m, ctx->stream), "mlp train kernel");
+    CK(ssvp::launch_mlp_train_tc(m, ctx->d_kerr, ctx->stream), "mlp train kernel");
     CK(cudaMemcpyAsync(grad_out, ctx->mlp.grad, (ssvp::kMlpParams + 1) * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
        "cudaMemcpyAsync");
-    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
-    return SSVP_OK;
+    return ssvp_sync(ctx);  // also reports a timed-out tensor-core wait
 }
 
 int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, const float *const *clean, int n_clips,
@@ -1459,7 +1458,7 @@ int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, co
         m.clean = clean[ci];
         m.bce_w = cfg->bce_weight;
         m.grad = ctx->mlp.grad;
-        CK(ssvp::launch_mlp_train(m, ctx->stream), "mlp train kernel");
+        CK(ssvp::launch_mlp_train_tc(m, ctx->d_kerr, ctx->stream), "mlp train kernel");
         CK(ssvp::launch_adam(ctx->mlp, cfg->lr, ++ctx->mlp_step, ctx->stream), "adam kernel");
         CK(cudaMemcpyAsync(ctx->l_loss + step, ctx->mlp.grad + ssvp::kMlpParams, sizeof(float), cudaMemcpyDeviceToDevice,
                            ctx->stream), "cudaMemcpyAsync");
@@ -1467,8 +1466,7 @@ int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, co
     if (loss_out && cfg->steps > 0)
         CK(cudaMemcpyAsync(loss_out, ctx->l_loss, cfg->steps * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
            "cudaMemcpyAsync");
-    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
-    return SSVP_OK;
+    return ssvp_sync(ctx);  // also reports a timed-out tensor-core wait
 }
 
 int ssvp_sync(ssvp_ctx *ctx) {
@@ -1480,7 +1478,7 @@ int ssvp_sync(ssvp_ctx *ctx) {
     CK(cudaMemcpy(&kerr, ctx->d_kerr, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy (kernel error word)");
     if (kerr) {
         CK(cudaMemset(ctx->d_kerr, 0, sizeof(int)), "cudaMemset (kernel error word)");
-        return fail(ctx, SSVP_ETIMEOUT, "a tensor-core completion wait of the learned inference timed out");
+        return fail(ctx, SSVP_ETIMEOUT, "a tensor-core completion wait of the learned filter timed out");
     }
     return SSVP_OK;
 }

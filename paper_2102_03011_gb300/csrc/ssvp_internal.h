@@ -153,6 +153,9 @@ struct MlpArgs {
 // waits for MMA completion times out
 cudaError_t launch_mlp_infer_tc(const MlpArgs &m, int *err, cudaStream_t s);
 cudaError_t launch_mlp_train(const MlpArgs &m, cudaStream_t s);
+// training on the tcgen05 tensor cores (forward, loss, backward; gradients accumulated into
+// m.grad); err as for the inference
+cudaError_t launch_mlp_train_tc(const MlpArgs &m, int *err, cudaStream_t s);
 cudaError_t launch_adam(const MlpState &st, float lr, int step, cudaStream_t s);
 cudaError_t launch_mlp_refresh(const MlpState &st, cudaStream_t s);
 // expand compact sample sets into 64 x 16 BF16 features, 64 x 3 colours, counts and plain results

@@ -172,6 +172,39 @@ __device__ __forceinline__ unsigned feat_word(int w, float4 c, unsigned f89, flo
     }
 }
 
+// The network's operands in shared memory, by the 128 threads of a CTA: W1 (64 x 16) with b1's
+// leading BF16 part in column 15 (the logical feature 15 is the constant 0, so its A slot can
+// carry 1.0), b1's two lower BF16 parts as the B operand of a residual product with the constant
+// operand A0 (rows (1, 1, 0, ..., 0)), and W2 padded to 16 rows (16 x 64)
+__device__ __forceinline__ void stage_weights(unsigned char *sm, int offB1, int offB0, int offA0, int offB2,
+                                              const MlpWeights &mw, int tid) {
+    {
+        const int row = tid >> 1, kc = tid & 1;
+        uint4 w = __ldg(reinterpret_cast<const uint4 *>(mw.W1 + row * kF + kc * 8));
+        const float b = __ldg(mw.b1 + row);
+        const unsigned short hi = bf16_bits(b);
+        const float r1 = b - __uint_as_float((unsigned)hi << 16);
+        const unsigned short mid = bf16_bits(r1);
+        const unsigned short lo = bf16_bits(r1 - __uint_as_float((unsigned)mid << 16));
+        if (kc == 1) w.w = (w.w & 0xffffu) | ((unsigned)hi << 16);
+        *reinterpret_cast<uint4 *>(sm + offB1 + core_off(row, kc, 2)) = w;
+        *reinterpret_cast<uint4 *>(sm + offB0 + core_off(row, kc, 2)) =
+            kc == 0 ? make_uint4(pack2(mid, lo), 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(sm + offA0 + core_off(tid, 0, 2)) = make_uint4(pack2(0x3f80, 0x3f80), 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(sm + offA0 + core_off(tid, 1, 2)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    {
+        const int row = tid >> 3, kc = tid & 7;
+        unsigned q[4] = {0u, 0u, 0u, 0u};
+        if (row < 2) {
+            const float *src = mw.W2 + row * kH + kc * 8;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) q[i] = bf16x2(__ldg(src + 2 * i), __ldg(src + 2 * i + 1));
+        }
+        *reinterpret_cast<uint4 *>(sm + offB2 + core_off(row, kc, 8)) = make_uint4(q[0], q[1], q[2], q[3]);
+    }
+}
+
 // One pixel pair's data as a thread needs it: its sample row (colour record, depth / weight
 // pair), the pixel's info, plain result and set size
 struct RowData {
@@ -222,33 +255,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpAr
     __shared__ int s_bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, s_row = tid & 63;
 
-    {
-        // W1 with b1's leading BF16 part in column 15; b1's two lower parts for the residual product
-        const int row = tid >> 1, kc = tid & 1;
-        uint4 w = __ldg(reinterpret_cast<const uint4 *>(m.w.W1 + row * kF + kc * 8));
-        const float b = __ldg(m.w.b1 + row);
-        const unsigned short hi = bf16_bits(b);
-        const float r1 = b - __uint_as_float((unsigned)hi << 16);
-        const unsigned short mid = bf16_bits(r1);
-        const unsigned short lo = bf16_bits(r1 - __uint_as_float((unsigned)mid << 16));
-        if (kc == 1) w.w = (w.w & 0xffffu) | ((unsigned)hi << 16);
-        *reinterpret_cast<uint4 *>(sm + kSmB1 + core_off(row, kc, 2)) = w;
-        *reinterpret_cast<uint4 *>(sm + kSmB0 + core_off(row, kc, 2)) =
-            kc == 0 ? make_uint4(pack2(mid, lo), 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
-        // the constant operand: rows of (1, 1, 0, ..., 0)
-        *reinterpret_cast<uint4 *>(sm + kSmA0 + core_off(tid, 0, 2)) = make_uint4(pack2(0x3f80, 0x3f80), 0u, 0u, 0u);
-        *reinterpret_cast<uint4 *>(sm + kSmA0 + core_off(tid, 1, 2)) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    {
-        const int row = tid >> 3, kc = tid & 7;
-        unsigned q[4] = {0u, 0u, 0u, 0u};
-        if (row < 2) {
-            const float *src = m.w.W2 + row * kH + kc * 8;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) q[i] = bf16x2(__ldg(src + 2 * i), __ldg(src + 2 * i + 1));
-        }
-        *reinterpret_cast<uint4 *>(sm + kSmB2 + core_off(row, kc, 8)) = make_uint4(q[0], q[1], q[2], q[3]);
-    }
+    stage_weights(sm, kSmB1, kSmB0, kSmA0, kSmB2, m.w, tid);
     const float b20 = __ldg(m.w.b2), b21 = __ldg(m.w.b2 + 1);
     const unsigned bar1 = smem_u32(&s_mbar[0]), bar2 = smem_u32(&s_mbar[1]);
     if (tid == 0) {
@@ -467,6 +474,305 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpAr
     }
 }
 
+// ---------------------------------------------------------------- training on the tensor cores
+// One CTA of 128 threads takes two batch pixels at a time, one thread per sample row, and runs
+// the forward pass exactly as the inference does (layer 1 with b1 folded in, ReLU and BF16
+// rounding, layer 2).  Two threads then form their pixel's loss terms (the learned output, the
+// MSE of it and of the plain result against the clean target, the BCE target and its confidence
+// derivative), and every thread its sample's dz = (dL/dz_w, dL/dz_c) and
+// dh_j = (dz_w W2[0][j] + dz_c W2[1][j]) [h_j > 0].  The weight gradients are one tcgen05 product
+// per pair, accumulated over the whole kernel in tensor memory:
+//   G (128 x 32) += A_G B_G^T, K = the pair's 128 sample rows, with
+//   A_G rows 0..63 = h^T and rows 64..127 = dh^T (hidden unit x sample), and
+//   B_G rows 0, 1 = dz_w, dz_c, rows 2..17 = the 16 features, row 18 = 1, rows 19..31 = 0,
+// so G[j][0..1] holds dW2^T, G[64 + j][2..17] dW1 and G[64 + j][18] db1 (the other blocks go
+// unused).  Each thread writes its sample's column of both operands (K-major, so a sample's
+// values spread over the rows).  All operands are BF16 with FP32 accumulation: h, dh, dz and
+// the features enter the gradient products rounded to BF16.  db2 and the loss are FP32 sums.
+constexpr int kTrSmA1 = 0;          // features, 128 x 16
+constexpr int kTrSmB1 = 4096;       // W1, 64 x 16
+constexpr int kTrSmA0 = 6144;       // constant operand of the b1 residual, 128 x 16
+constexpr int kTrSmB0 = 10240;      // b1's lower parts, 64 x 16
+constexpr int kTrSmB2 = 12288;      // W2 padded, 16 x 64
+constexpr int kTrSmA2 = 14336;      // H, 128 x 64
+constexpr int kTrSmAG = 30720;      // A_G, 128 x 128
+constexpr int kTrSmBG = 63488;      // B_G, 32 x 128
+constexpr int kTrSmBytes = 71680;   // three CTAs per SM: 3 x 128 tensor-memory columns fit in 512
+constexpr unsigned kTrTmemCols = 128;   // D1 [0, 64), D2 [64, 80), G [96, 128)
+constexpr unsigned kTrColD2 = 64, kTrColG = 96;
+
+// byte offset of element (row, k) of a K-major operand with K = 128 (16 core matrices per row group)
+__device__ __forceinline__ unsigned kmajor128(int row, int k) { return core_off(row, k >> 3, 16) + (unsigned)(k & 7) * 2u; }
+
+__global__ void __launch_bounds__(kTcThreads, 3) mlp_train_tc_kernel(const MlpArgs m, int *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ float s_red[4][5];
+    __shared__ float s_pix[2][8];  // per pixel: dL/d output (3), dL/d conf, 1 / sum w, learned output (3)
+    __shared__ float s_w2[2][kH];  // W2 as rounded to BF16
+    __shared__ float s_acc[3];     // db2 (2) and the loss of the CTA
+    __shared__ unsigned long long s_mbar[3];  // layer 1, layer 2, gradient product
+    __shared__ unsigned s_tmem;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, srow = tid & 63, pix = tid >> 6;
+
+    stage_weights(sm, kTrSmB1, kTrSmB0, kTrSmA0, kTrSmB2, m.w, tid);
+    // the constant rows of B_G at this thread's sample column: row 18 = 1, rows 19..31 = 0
+#pragma unroll
+    for (int n = 18; n < 32; ++n)
+        *reinterpret_cast<unsigned short *>(sm + kTrSmBG + kmajor128(n, tid)) = n == 18 ? (unsigned short)0x3f80 : 0;
+    s_w2[tid >> 6][tid & 63] = __ldg(m.w.W2 + tid);
+    const float b20 = __ldg(m.w.b2), b21 = __ldg(m.w.b2 + 1);
+    const unsigned bar1 = smem_u32(&s_mbar[0]), bar2 = smem_u32(&s_mbar[1]), bar3 = smem_u32(&s_mbar[2]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar2) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar3) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_bad = 0;
+        s_acc[0] = s_acc[1] = s_acc[2] = 0.0f;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTrTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = s_tmem;
+    const unsigned lane_base = (unsigned)(warp * 32) << 16;
+    const unsigned sbase = smem_u32(sm);
+    const unsigned long long dA1 = smem_desc(sbase + kTrSmA1, 128, 256), dB1 = smem_desc(sbase + kTrSmB1, 128, 256),
+                             dA0 = smem_desc(sbase + kTrSmA0, 128, 256), dB0 = smem_desc(sbase + kTrSmB0, 128, 256);
+    constexpr unsigned id1 = instr_desc(kH, 128), id2 = instr_desc(16, 128), idg = instr_desc(32, 128);
+    unsigned ph1 = 0, ph2 = 0, ph3 = 0;
+    bool bad = false, g_started = false;
+    float db2w = 0.0f, db2c = 0.0f, loss = 0.0f;
+    const float inv_np = 1.0f / (float)m.n_batch;
+    const long long n_pairs = (m.n_batch + 1) / 2;
+
+    for (long long pair = blockIdx.x; pair < n_pairs; pair += gridDim.x) {
+        // 1. the sample row of this thread
+        const long long bi = 2 * pair + pix;
+        long long px = 0;
+        int n = 0;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f), info = make_float4(0.f, 0.f, 0.f, 0.f);
+        unsigned f89 = 0u;
+        float pl[3] = {0.f, 0.f, 0.f};
+        if (bi < m.n_batch) {
+            px = m.batch[bi];
+            n = m.sets.n[px];
+            const long long k = px * kS + srow;
+            c = __ldg(m.sets.col + k);
+            f89 = __ldg(m.sets.f89 + k);
+            info = __ldg(m.sets.info + px);
+            pl[0] = m.sets.plain[3 * px];
+            pl[1] = m.sets.plain[3 * px + 1];
+            pl[2] = m.sets.plain[3 * px + 2];
+        }
+        const bool valid = srow < n;
+        // 2. features (logical order; slot 15 carries 1.0 for b1 in the layer-1 operand only)
+        unsigned wd[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) wd[w] = valid ? feat_word(w, c, f89, info, pl) : 0u;
+        *reinterpret_cast<uint4 *>(sm + kTrSmA1 + core_off(tid, 0, 2)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        *reinterpret_cast<uint4 *>(sm + kTrSmA1 + core_off(tid, 1, 2)) =
+            make_uint4(wd[4], wd[5], wd[6], valid ? wd[7] | (0x3f80u << 16) : 0u);
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (s_bad) break;  // uniform: written only before the barrier above
+        if (tid == 0 && !m.skip_mma) {
+            fence_after();
+            mma_tc(tmem, dA1, dB1, id1, 0);
+            mma_tc(tmem, dA0, dB0, id1, 1);
+            mma_commit(bar1);
+        }
+        bad |= !mbar_wait(bar1, ph1);
+        ph1 ^= 1u;
+        fence_after();
+        // 3. H = ReLU(D1) in BF16: layer 2's A operand, kept in registers for the gradients
+        unsigned h[32];
+        {
+            unsigned v0[32], v1[32];
+            tmem_ld32_nowait(tmem + lane_base, v0);
+            tmem_ld32_nowait(tmem + lane_base + 32, v1);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                h[i] = relu_bf16x2(__uint_as_float(v0[2 * i]), __uint_as_float(v0[2 * i + 1]));
+                h[16 + i] = relu_bf16x2(__uint_as_float(v1[2 * i]), __uint_as_float(v1[2 * i + 1]));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<uint4 *>(sm + kTrSmA2 + core_off(tid, q, 8)) =
+                make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (tid == 0 && !m.skip_mma) {
+            fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_tc(tmem + kTrColD2, smem_desc(sbase + kTrSmA2 + kk * 256, 128, 1024),
+                       smem_desc(sbase + kTrSmB2 + kk * 256, 128, 1024), id2, kk);
+            mma_commit(bar2);
+        }
+        bad |= !mbar_wait(bar2, ph2);
+        ph2 ^= 1u;
+        fence_after();
+        float zw, zc;
+        tmem_ld2(tmem + kTrColD2 + lane_base, zw, zc);
+        zw += b20;
+        zc += b21;
+        // 4. the pixel's sums: weights, weighted colours, confidences
+        const float wgt = valid ? softplusf(zw) : 0.0f, sgm = valid ? sigmoidf(zc) : 0.0f;
+        const float t4 = warp_sum4(wgt, wgt * c.x, wgt * c.y, wgt * c.z, lane);
+        float sc = sgm;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        if ((lane & 7) == 0) s_red[warp][lane >> 3] = t4;
+        if (lane == 0) s_red[warp][4] = sc;
+        __syncthreads();
+        // 5. the pixel's loss and the derivatives of its output and confidence
+        if (srow == 32) {
+            float P[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (n > 0) {
+                const int w0 = warp - 1;
+                const float sw = s_red[w0][0] + s_red[w0 + 1][0];
+                const float inv_w = 1.0f / sw;
+                const float ol[3] = {(s_red[w0][1] + s_red[w0 + 1][1]) * inv_w, (s_red[w0][2] + s_red[w0 + 1][2]) * inv_w,
+                                     (s_red[w0][3] + s_red[w0 + 1][3]) * inv_w};
+                const float conf = (s_red[w0][4] + s_red[w0 + 1][4]) / (float)n;
+                const long long u = px % m.cw + m.x0, v = px / m.cw + m.y0;
+                const float *y = m.clean + (((long long)m.O * m.H + v) * m.W + u) * 3;
+                float el = 0.f, ep = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    el += (ol[ch] - y[ch]) * (ol[ch] - y[ch]) * (1.0f / 3.0f);
+                    ep += (pl[ch] - y[ch]) * (pl[ch] - y[ch]) * (1.0f / 3.0f);
+                    P[ch] = 2.0f * (ol[ch] - y[ch]) * (1.0f / 3.0f) * inv_np;
+                    P[5 + ch] = ol[ch];
+                }
+                const float tgt = el <= ep ? 1.0f : 0.0f;
+                const float cc = fminf(fmaxf(conf, 1e-6f), 1.0f - 1e-6f);
+                const bool inside = conf > 1e-6f && conf < 1.0f - 1e-6f;
+                P[3] = inside ? m.bce_w * (cc - tgt) / (cc * (1.0f - cc)) * inv_np : 0.0f;
+                P[4] = inv_w;
+                loss += (el - m.bce_w * (tgt * logf(cc) + (1.0f - tgt) * logf(1.0f - cc))) * inv_np;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s_pix[pix][i] = P[i];
+        }
+        __syncthreads();
+        // 6. this sample's dz
+        float dzw = 0.0f, dzc = 0.0f;
+        if (valid) {
+            const float *P = s_pix[pix];
+            const float dw = (P[0] * (c.x - P[5]) + P[1] * (c.y - P[6]) + P[2] * (c.z - P[7])) * P[4];
+            dzw = dw * sigmoidf(zw);
+            dzc = P[3] * sgm * (1.0f - sgm) / (float)n;
+        }
+        db2w += dzw;
+        db2c += dzc;
+        // 7. the previous gradient product has read A_G and B_G before they are rewritten
+        if (g_started) {
+            bad |= !mbar_wait(bar3, ph3);
+            ph3 ^= 1u;
+        }
+        // 8. this sample's column of A_G (h, then dh) and of B_G (dz, features)
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const float h0 = __uint_as_float(h[q] << 16), h1 = __uint_as_float(h[q] & 0xffff0000u);
+            const int j = 2 * q;
+            const float dh0 = h0 > 0.0f ? fmaf(dzw, s_w2[0][j], dzc * s_w2[1][j]) : 0.0f;
+            const float dh1 = h1 > 0.0f ? fmaf(dzw, s_w2[0][j + 1], dzc * s_w2[1][j + 1]) : 0.0f;
+            const unsigned d2 = bf16x2(dh0, dh1);
+            *reinterpret_cast<unsigned short *>(sm + kTrSmAG + kmajor128(j, tid)) = (unsigned short)(h[q] & 0xffffu);
+            *reinterpret_cast<unsigned short *>(sm + kTrSmAG + kmajor128(j + 1, tid)) = (unsigned short)(h[q] >> 16);
+            *reinterpret_cast<unsigned short *>(sm + kTrSmAG + kmajor128(64 + j, tid)) = (unsigned short)(d2 & 0xffffu);
+            *reinterpret_cast<unsigned short *>(sm + kTrSmAG + kmajor128(65 + j, tid)) = (unsigned short)(d2 >> 16);
+        }
+        {
+            const unsigned dz2 = bf16x2(dzw, dzc);
+            *reinterpret_cast<unsigned short *>(sm + kTrSmBG + kmajor128(0, tid)) = (unsigned short)(dz2 & 0xffffu);
+            *reinterpret_cast<unsigned short *>(sm + kTrSmBG + kmajor128(1, tid)) = (unsigned short)(dz2 >> 16);
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                *reinterpret_cast<unsigned short *>(sm + kTrSmBG + kmajor128(2 + i, tid)) =
+                    (unsigned short)((i & 1) ? wd[i >> 1] >> 16 : wd[i >> 1] & 0xffffu);
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (tid == 0 && !m.skip_mma) {
+            fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+                mma_tc(tmem + kTrColG, smem_desc(sbase + kTrSmAG + kk * 256, 128, 2048),
+                       smem_desc(sbase + kTrSmBG + kk * 256, 128, 2048), idg, (g_started || kk > 0) ? 1 : 0);
+            mma_commit(bar3);
+        }
+        g_started = true;
+        if (bad) s_bad = 1;
+    }
+    __syncthreads();  // s_bad is settled for every thread
+    // db2 and the loss: per-warp sums, then one atomic per warp into shared memory
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        db2w += __shfl_xor_sync(0xffffffffu, db2w, o);
+        db2c += __shfl_xor_sync(0xffffffffu, db2c, o);
+        loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&s_acc[0], db2w);
+        atomicAdd(&s_acc[1], db2c);
+        atomicAdd(&s_acc[2], loss);
+    }
+    // the accumulated weight gradients: row tid of G
+    if (g_started && !s_bad) {
+        bad |= !mbar_wait(bar3, ph3);
+        ph3 ^= 1u;
+        fence_after();
+        unsigned gv[32];
+        tmem_ld32_nowait(tmem + kTrColG + lane_base, gv);
+        tmem_wait_ld();
+        if (!bad) {
+            if (tid < 64) {
+                atomicAdd(m.grad + kMlpW2 + tid, __uint_as_float(gv[0]));
+                atomicAdd(m.grad + kMlpW2 + kH + tid, __uint_as_float(gv[1]));
+            } else {
+                const int j = tid - 64;
+#pragma unroll
+                for (int i = 0; i < kF; ++i) atomicAdd(m.grad + j * kF + i, __uint_as_float(gv[2 + i]));
+                atomicAdd(m.grad + kMlpB1 + j, __uint_as_float(gv[18]));
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && !s_bad && !bad) {
+        atomicAdd(m.grad + kMlpB2, s_acc[0]);
+        atomicAdd(m.grad + kMlpB2 + 1, s_acc[1]);
+        atomicAdd(m.grad + kMlpParams, s_acc[2]);
+    }
+    if (bad) atomicOr(err, 1);
+    // after a time-out the tensor cores may still be busy: one more bounded wait on each barrier
+    if (s_bad && tid == 0) {
+        mbar_wait(bar1, ph1);
+        mbar_wait(bar2, ph2);
+        if (g_started) mbar_wait(bar3, ph3);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTrTmemCols) : "memory");
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_mlp_infer_tc(const MlpArgs &m, int *err, cudaStream_t s) {
@@ -484,6 +790,22 @@ cudaError_t launch_mlp_infer_tc(const MlpArgs &m, int *err, cudaStream_t s) {
     if (blocks > pairs) blocks = pairs;
     static_assert(kSmBytes <= kSmRequest, "operands exceed the requested shared memory");
     mlp_infer_tc_kernel<<<(unsigned)blocks, kTcThreads, kSmRequest, s>>>(m, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_train_tc(const MlpArgs &m, int *err, cudaStream_t s) {
+    if (m.n_batch <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(mlp_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrSmBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long pairs = (m.n_batch + 1) / 2;
+    long long blocks = (long long)sms * 3;
+    if (blocks > pairs) blocks = pairs;
+    mlp_train_tc_kernel<<<(unsigned)blocks, kTcThreads, kTrSmBytes, s>>>(m, err);
     return cudaGetLastError();
 }
 

@@ -223,14 +223,15 @@ def test_training_gradients_match_the_oracle(sess, clip):
     assert g[1218] == pytest.approx(L, rel=1e-4)
     # Element by element: |GPU - oracle| <= 1e-3 |oracle| + c * (sum of |terms| of the entry)
     # + 1e-6 * (the largest such sum of the block).  c covers the rounding of the terms: FP32
-    # accumulation and the rare flip of a BF16 rounding of a hidden activation (2e-4); for dW1 also
-    # the BF16 rounding of dH, the operand of the dW1 tensor-core product, which perturbs each term
-    # by at most 2^-8 of itself.  The last, absolute floor covers ReLU gates whose pre-activation
-    # lies within FP32 rounding of zero, which may open on one side only: such an entry's oracle
-    # terms can all be ~1e-22 (a unit that barely fires) while the other side holds one more.
-    parts = [("gW1", g[:1024], gW1.ravel(), aW1.ravel(), 2.0 ** -8 + 2e-4),
-             ("gb1", g[1024:1088], gb1, ab1, 2e-4), ("gW2", g[1088:1216], gW2.ravel(), aW2.ravel(), 2e-4),
-             ("gb2", g[1216:1218], gb2, ab2, 2e-4)]
+    # accumulation and the rare flip of a BF16 rounding of a hidden activation (2e-4); the weight
+    # gradients are tensor-core products whose operands dH, dz and h enter rounded to BF16, which
+    # perturbs each term of dW1, db1 and dW2 by at most 2^-8 of itself (db2 is an FP32 sum).  The
+    # last, absolute floor covers ReLU gates whose pre-activation lies within FP32 rounding of
+    # zero, which may open on one side only: such an entry's oracle terms can all be ~1e-22 (a unit
+    # that barely fires) while the other side holds one more.
+    bf = 2.0 ** -8 + 2e-4
+    parts = [("gW1", g[:1024], gW1.ravel(), aW1.ravel(), bf), ("gb1", g[1024:1088], gb1, ab1, bf),
+             ("gW2", g[1088:1216], gW2.ravel(), aW2.ravel(), bf), ("gb2", g[1216:1218], gb2, ab2, 2e-4)]
     for name, got, want, scale, c in parts:
         err = np.abs(got - want)
         tol = 1e-3 * np.abs(want) + c * scale + 1e-6 * scale.max()
