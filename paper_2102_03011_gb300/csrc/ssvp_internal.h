@@ -152,7 +152,6 @@ struct MlpArgs {
 // learned inference on the tcgen05 tensor cores; err (device word) is raised if one of its bounded
 // waits for MMA completion times out
 cudaError_t launch_mlp_infer_tc(const MlpArgs &m, int *err, cudaStream_t s);
-cudaError_t launch_mlp_train(const MlpArgs &m, cudaStream_t s);
 // training on the tcgen05 tensor cores (forward, loss, backward; gradients accumulated into
 // m.grad); err as for the inference
 cudaError_t launch_mlp_train_tc(const MlpArgs &m, int *err, cudaStream_t s);

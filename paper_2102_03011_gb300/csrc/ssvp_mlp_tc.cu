@@ -1,4 +1,5 @@
-// ssvp_mlp_tc.cu - learned-filter inference on the 5th-generation tensor cores (tcgen05).
+// ssvp_mlp_tc.cu - learned-filter inference and training on the 5th-generation tensor cores
+// (tcgen05).  Inference first; the training kernel, which reuses its forward pass, follows it.
 //
 // One CTA of 128 threads takes two pixels at a time: their 2 x 64 capped samples are the 128 rows
 // of the layer-1 product, and two such pairs are in flight (a two-stage pipeline: while layer 2
@@ -15,8 +16,8 @@
 //   4. four tcgen05.mma (K = 16 each): D2 (128 x 16, columns 0 and 1 used) = H W2^T;
 //   5. each thread reads (z_w, z_c) of its row, adds b2, and forms softplus / sigmoid; the two
 //      warps of each pixel reduce the weighted sums.
-// The arithmetic is that of the training kernel's forward pass (ssvp_mlp.cu): BF16 operands,
-// FP32 accumulation, h rounded to BF16 before layer 2.  Waits on the MMA-completion barrier are
+// BF16 operands, FP32 accumulation, h rounded to BF16 before layer 2 (the training kernel below
+// runs the same forward pass).  Waits on the MMA-completion barrier are
 // bounded: on a time-out the kernel raises the error word, leaves its loop, frees its tensor
 // memory and returns.
 #include <cuda_bf16.h>

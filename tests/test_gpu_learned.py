@@ -238,9 +238,10 @@ def test_training_gradients_match_the_oracle(sess, clip):
         bad = np.flatnonzero(err > tol)
         assert bad.size == 0, (name, bad[:5], err[bad[:5]], tol[bad[:5]])
         # stated: the largest error in units of the entry's term scale
+        big = np.abs(want) > 1e-2 * np.abs(want).max()
         print(f"{name}: max |GPU - oracle| / term scale = {float(np.max(err / np.maximum(scale, 1e-30))):.2e}, "
               f"max relative (entries above 1e-2 of the largest) = "
-              f"{float(np.max((err / np.abs(want))[np.abs(want) > 1e-2 * np.abs(want).max()])):.2e}")
+              f"{float(np.max(err[big] / np.abs(want[big]), initial=0.0)):.2e}")
 
 
 def test_trained_network_gains_over_the_plain_filter_on_held_out_clips(sess):
