@@ -265,6 +265,23 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
 int ssvp_unload_clip(ssvp_ctx *ctx, int clip_id);
 
 /*
+ * Slide a loaded clip's frames forward for streaming video: frames n .. F-1 become frames
+ * 0 .. F-n-1 and the n new frames become frames F-n .. F-1, with their cameras (K: one shared 3x3
+ * or n per-frame ones as in ssvp_set_cameras; w2c: n x 3 x 4).  rgb (n x H x W x 3) and depth
+ * (n x H x W) as in ssvp_load_clip, on the host or the device; 1 <= n <= F.  Only the n new
+ * frames cross to the device: the kept frames are copied on the device into a second window the
+ * clip keeps (allocated by the first call: a second set of planes), which then becomes current.
+ * The work runs on the context's load stream after the work queued before the previous append
+ * (every gather that read the second window) and before the work queued after this call: it
+ * overlaps gathers of the current window queued since the previous append (device inputs are
+ * packed only after all work queued before this call, which may produce them).  The clip's median
+ * and per-frame values are those of the new window; its output frames are not cleared.  Needs
+ * the cameras set and no inpainting mask; invalidates batched plans that include the clip.
+ */
+int ssvp_append_frames(ssvp_ctx *ctx, int clip_id, int n, const float *rgb, const float *depth, int mem_kind,
+                       const double *K, int per_frame_K, const double *w2c);
+
+/*
  * Cameras C of Sec. "Method overview" for clip `clip_id`, in double precision on the host:
  * K intrinsics (3x3 row-major, shared: per_frame_K = 0, or F of them: per_frame_K = 1), upper
  * triangular with zero skew and K[2][2] = 1; w2c world->camera [R|t] (F x 3x4 row-major, R a

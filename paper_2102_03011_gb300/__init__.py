@@ -68,6 +68,7 @@ def _load():
         "ssvp_set_stream": (i, [vp, vp]),
         "ssvp_load_clip": (i, [vp, i, i, i, i, vp, vp, i, i]),
         "ssvp_unload_clip": (i, [vp, i]),
+        "ssvp_append_frames": (i, [vp, i, i, vp, vp, i, vp, i, vp]),
         "ssvp_set_cameras": (i, [vp, i, vp, i, vp]),
         "ssvp_gather_filter": (i, [vp, P, ctypes.POINTER(ctypes.c_int), i]),
         "ssvp_read_output": (i, [vp, i, i, i, vp, i]),
@@ -170,6 +171,19 @@ def ssvp_load_clip(ctx, clip_id: int, W: int, H: int, F: int, rgb, depth, mem_ki
 
 def ssvp_unload_clip(ctx, clip_id: int) -> None:
     _check(ctx, lib.ssvp_unload_clip(ctx, clip_id))
+
+
+def ssvp_append_frames(ctx, clip_id: int, n: int, rgb, depth, K, per_frame_K: int, w2c, mem_kind: int | None = None) -> None:
+    import numpy as np
+    (pr, dr), (pd, dd) = _ptr(rgb), _ptr(depth)
+    if mem_kind is None:
+        if dr != dd:
+            raise ValueError("rgb and depth must both be on the host or both on the device")
+        mem_kind = SSVP_MEM_DEVICE if dr else SSVP_MEM_HOST
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    w2c = np.ascontiguousarray(w2c, dtype=np.float64)
+    _check(ctx, lib.ssvp_append_frames(ctx, clip_id, int(n), pr, pd, mem_kind, K.ctypes.data, int(per_frame_K),
+                                       w2c.ctypes.data))
 
 
 def ssvp_set_cameras(ctx, clip_id: int, K, per_frame_K: int, w2c) -> None:

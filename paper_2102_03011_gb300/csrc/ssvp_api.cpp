@@ -26,7 +26,24 @@ struct Clip {
     Planes p{};
     std::vector<double> K;    // F * 9
     std::vector<double> w2c;  // F * 12
+    // ssvp_append_frames: the spare window (depth and colour planes and the per-window values:
+    // median, depth ranges, gradient sums) the next window is built in while queued gathers still
+    // read the current one, and the event recorded on the context's stream by the previous
+    // append: every read of the spare window precedes it
+    Planes spare{};
+    cudaEvent_t ev_append = nullptr;
 };
+
+// the arrays of one window of a clip (the rest of Planes, such as the output and the mask, is shared)
+void swap_window(Planes &a, Planes &b) {
+    std::swap(a.depth, b.depth);
+    std::swap(a.colour, b.colour);
+    std::swap(a.median, b.median);
+    std::swap(a.zrange, b.zrange);
+    std::swap(a.grad_sum, b.grad_sum);
+    std::swap(a.grad_log2, b.grad_log2);
+    std::swap(a.grad_partial, b.grad_partial);
+}
 
 char g_create_error[512] = "";
 
@@ -125,6 +142,10 @@ void free_clip(Clip &c) {
     if (c.p.grad_log2) cudaFree(c.p.grad_log2);
     if (c.p.grad_partial) cudaFree(c.p.grad_partial);
     if (c.p.mask) cudaFree(c.p.mask);
+    for (void *q : {(void *)c.spare.depth, (void *)c.spare.colour, (void *)c.spare.median, (void *)c.spare.zrange,
+                    (void *)c.spare.grad_sum, (void *)c.spare.grad_log2, (void *)c.spare.grad_partial})
+        if (q) cudaFree(q);
+    if (c.ev_append) cudaEventDestroy(c.ev_append);
     c = Clip();
 }
 
@@ -709,14 +730,12 @@ int ssvp_unload_clip(ssvp_ctx *ctx, int clip_id) {
     return SSVP_OK;
 }
 
-int ssvp_set_cameras(ssvp_ctx *ctx, int clip_id, const double *K, int per_frame_K, const double *w2c) {
-    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
-    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
-    Clip &c = ctx->clips[clip_id];
-    if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
-    if (!K || !w2c) return fail(ctx, SSVP_EINVAL, "K and w2c must not be NULL");
-    const int F = c.p.F;
-    std::vector<double> Kv((size_t)F * 9), Wv(w2c, w2c + (size_t)F * 12);
+// F frames of cameras: per-frame (or one shared) K and world->camera [R|t], checked (finite, zero
+// skew, orthonormal R) and expanded to per-frame arrays
+static int checked_cameras(ssvp_ctx *ctx, int F, const double *K, int per_frame_K, const double *w2c,
+                           std::vector<double> &Kv, std::vector<double> &Wv) {
+    Kv.assign((size_t)F * 9, 0.0);
+    Wv.assign(w2c, w2c + (size_t)F * 12);
     for (int f = 0; f < F; ++f) std::memcpy(&Kv[9 * (size_t)f], K + (per_frame_K ? 9 * (size_t)f : 0), 9 * sizeof(double));
     if (!finite_all(Kv.data(), Kv.size()) || !finite_all(Wv.data(), Wv.size()))
         return fail(ctx, SSVP_EINVAL, "cameras must be finite");
@@ -732,9 +751,121 @@ int ssvp_set_cameras(ssvp_ctx *ctx, int clip_id, const double *K, int per_frame_
                     return fail(ctx, SSVP_EINVAL, "frame %d: w2c rotation is not orthonormal", f);
             }
     }
+    return SSVP_OK;
+}
+
+int ssvp_set_cameras(ssvp_ctx *ctx, int clip_id, const double *K, int per_frame_K, const double *w2c) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    Clip &c = ctx->clips[clip_id];
+    if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    if (!K || !w2c) return fail(ctx, SSVP_EINVAL, "K and w2c must not be NULL");
+    std::vector<double> Kv, Wv;
+    int rc = checked_cameras(ctx, c.p.F, K, per_frame_K, w2c, Kv, Wv);
+    if (rc != SSVP_OK) return rc;
     c.K.swap(Kv);
     c.w2c.swap(Wv);
     c.has_cams = true;
+    return SSVP_OK;
+}
+
+int ssvp_append_frames(ssvp_ctx *ctx, int clip_id, int n, const float *rgb, const float *depth, int mem_kind,
+                       const double *K, int per_frame_K, const double *w2c) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
+    Clip &c = ctx->clips[clip_id];
+    if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
+    if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_id);
+    if (c.p.mask) return fail(ctx, SSVP_EINVAL, "clip %d has an inpainting mask: reload it to append frames", clip_id);
+    const int W = c.p.W, H = c.p.H, F = c.p.F;
+    if (n < 1 || n > F) return fail(ctx, SSVP_EINVAL, "n=%d must be in [1, %d] (the clip's frame count)", n, F);
+    if (!rgb || !depth || !K || !w2c) return fail(ctx, SSVP_EINVAL, "rgb, depth, K and w2c must not be NULL");
+    if (mem_kind != SSVP_MEM_HOST && mem_kind != SSVP_MEM_DEVICE) return fail(ctx, SSVP_EINVAL, "bad mem_kind %d", mem_kind);
+    std::vector<double> Kn, Wn;
+    int rc = checked_cameras(ctx, n, K, per_frame_K, w2c, Kn, Wn);
+    if (rc != SSVP_OK) return rc;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    Planes &p = c.p;
+    const size_t texel = p.colour_fmt == SSVP_COLOUR_F32 ? 16 : 8;
+    const size_t nplane = (size_t)F * (size_t)p.fstride;
+    cudaError_t e = cudaSuccess;
+    Planes &sp = c.spare;
+    if (!sp.depth) {
+        // the spare window, its planes padded like the current ones (padding is never written again)
+        if ((e = cudaMalloc(&sp.depth, nplane * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&sp.colour, nplane * texel)) != cudaSuccess ||
+            (e = cudaMalloc(&sp.median, sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&sp.zrange, 2 * sizeof(unsigned int) * (size_t)F)) != cudaSuccess ||
+            (e = cudaMalloc(&sp.grad_sum, sizeof(double) * (size_t)F)) != cudaSuccess ||
+            (e = cudaMalloc(&sp.grad_log2, sizeof(float) * (size_t)F)) != cudaSuccess ||
+            (e = cudaMalloc(&sp.grad_partial, sizeof(double) * ssvp::grad_partial_words(F))) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&c.ev_append, cudaEventDisableTiming)) != cudaSuccess) {
+            for (void *q : {(void *)sp.depth, (void *)sp.colour, (void *)sp.median, (void *)sp.zrange,
+                            (void *)sp.grad_sum, (void *)sp.grad_log2, (void *)sp.grad_partial})
+                if (q) cudaFree(q);
+            sp = Planes{};
+            return cuda_fail(ctx, e, "cudaMalloc (spare window)");
+        }
+        CK(cudaMemsetAsync(sp.depth, 0xff, nplane * sizeof(float), ctx->stream), "cudaMemsetAsync");
+        CK(cudaMemsetAsync(sp.colour, 0, nplane * texel, ctx->stream), "cudaMemsetAsync");
+        CK(cudaEventRecord(c.ev_append, ctx->stream), "cudaEventRecord");
+    }
+    // the new window is built in the spare planes on the load stream.  It must follow every read of
+    // them, and those were all queued before the previous append (which made the current planes
+    // current): the load stream waits for that point only, not for the gathers queued since,
+    // which read the current planes, so building the next window overlaps them
+    cudaStream_t ls = ctx->load_stream;
+    CK(cudaStreamWaitEvent(ls, c.ev_append, 0), "cudaStreamWaitEvent");
+    CK(cudaEventRecord(c.ev_append, ctx->stream), "cudaEventRecord");
+    Planes q = p;  // the next window: the shared fields of p with the spare window's arrays
+    q.depth = sp.depth;
+    q.colour = sp.colour;
+    q.median = sp.median;
+    q.zrange = sp.zrange;
+    q.grad_sum = sp.grad_sum;
+    q.grad_log2 = sp.grad_log2;
+    q.grad_partial = sp.grad_partial;
+    const size_t keep = (size_t)(F - n) * (size_t)p.fstride;
+    if (keep) {
+        CK(cudaMemcpyAsync(q.depth, p.depth + (size_t)n * p.fstride, keep * sizeof(float), cudaMemcpyDeviceToDevice, ls),
+           "cudaMemcpyAsync (window)");
+        CK(cudaMemcpyAsync(q.colour, (const char *)p.colour + (size_t)n * p.fstride * texel, keep * texel,
+                           cudaMemcpyDeviceToDevice, ls),
+           "cudaMemcpyAsync (window)");
+    }
+    const size_t frame_px = (size_t)W * H;
+    if (mem_kind == SSVP_MEM_DEVICE) {
+        // device inputs may be produced by work queued on the context's stream up to this call
+        CK(cudaStreamWaitEvent(ls, c.ev_append, 0), "cudaStreamWaitEvent");
+        CK(ssvp::launch_pack(rgb, depth, W, H, n, q, F - n, ls), "pack kernel");
+    } else {
+        const size_t need = frame_px * 16 * (size_t)n;
+        if (ctx->staging_bytes < need) {
+            CK(cudaStreamSynchronize(ls), "cudaStreamSynchronize");
+            if (ctx->staging) cudaFree(ctx->staging);
+            ctx->staging = nullptr;
+            ctx->staging_bytes = 0;
+            if ((e = cudaMalloc(&ctx->staging, need)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc (staging)");
+            ctx->staging_bytes = need;
+        }
+        float *srgb = (float *)ctx->staging;
+        float *sdep = srgb + frame_px * 3 * (size_t)n;
+        CK(cudaMemcpyAsync(srgb, rgb, frame_px * 3 * n * sizeof(float), cudaMemcpyHostToDevice, ls), "cudaMemcpyAsync (rgb)");
+        CK(cudaMemcpyAsync(sdep, depth, frame_px * n * sizeof(float), cudaMemcpyHostToDevice, ls), "cudaMemcpyAsync (depth)");
+        CK(ssvp::launch_pack(srgb, sdep, W, H, n, q, F - n, ls), "pack kernel");
+    }
+    CK(ssvp::launch_median(q, ctx->median_scratch, ls), "median kernels");
+    CK(ssvp::launch_zrange(q, ls), "depth range kernel");
+    CK(ssvp::launch_grad_sum(q, ls), "gradient sum kernels");
+    CK(cudaEventRecord(ctx->ev_load_out, ls), "cudaEventRecord");
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_load_out, 0), "cudaStreamWaitEvent");
+    // the spare window becomes current; the cameras slide with the frames
+    swap_window(p, sp);
+    c.K.erase(c.K.begin(), c.K.begin() + 9 * (size_t)n);
+    c.K.insert(c.K.end(), Kn.begin(), Kn.end());
+    c.w2c.erase(c.w2c.begin(), c.w2c.begin() + 12 * (size_t)n);
+    c.w2c.insert(c.w2c.end(), Wn.begin(), Wn.end());
+    c.generation = ++ctx->clip_generation[clip_id];
     return SSVP_OK;
 }
 

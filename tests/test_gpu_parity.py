@@ -262,3 +262,31 @@ def test_full_size_sampled_against_oracle(sess):
         worst.append(err[~band].max())
     e, a, w = sess.ss.ssvp_read_stats(sess.ctx)
     assert a >= clip.W * clip.H  # every valid pixel accepts at least its own sample
+
+
+def test_queued_reload_is_ordered_with_the_work_around_it(sess, tiny):
+    """A clip load runs on the context's internal load stream: it must start only after the work
+    queued before it (a gather of the old contents and an asynchronous read of its output) and
+    finish before the work queued after it (a gather of the new contents), with no
+    synchronisation between the calls."""
+    t, ss = sess.torch, sess.ss
+    other = synth.make_clip("room", tiny.W, tiny.H, tiny.F, seed=9)
+    sess.load(12, tiny)
+    want_old = sess.run(12, 8, k=5, half_window=15).rgb
+    sess.load(13, other)
+    want_new = sess.run(13, 8, k=5, half_window=15).rgb
+    p = sess.params(k=5, half_window=15, frame_begin=8, frame_end=9)
+    a = t.empty((1, tiny.H, tiny.W, 3), dtype=t.float32, device=sess.dev)
+    b = t.empty_like(a)
+    rgb_h = t.from_numpy(other.rgb).pin_memory()
+    dep_h = t.from_numpy(other.depth).pin_memory()
+    for rep in range(2):
+        ss.ssvp_gather_filter(sess.ctx, p, [12])
+        ss.ssvp_read_output(sess.ctx, 12, 8, 9, a)  # device copy: queued, not waited for
+        ss.ssvp_load_clip(sess.ctx, 12, tiny.W, tiny.H, tiny.F, rgb_h, dep_h, ss.SSVP_MEM_HOST, 0)
+        ss.ssvp_set_cameras(sess.ctx, 12, other.K, 1, other.w2c)
+        ss.ssvp_gather_filter(sess.ctx, p, [12])
+        ss.ssvp_read_output(sess.ctx, 12, 8, 9, b)
+        ss.ssvp_sync(sess.ctx)
+        np.testing.assert_array_equal(a.cpu().numpy()[0], want_old if rep == 0 else want_new)
+        np.testing.assert_array_equal(b.cpu().numpy()[0], want_new)
