@@ -204,12 +204,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _workload_clip(seed):
+def _workload_clip(seed, frames=None):
     import synth
+    frames = F if frames is None else frames
     if MODE == 5:
-        c = synth.make_clip("room", W, H, F, seed=seed, sigma_img=DEBLUR_SIGMA_IMG)
-        return synth.shake_blur(c, range(2, F, 4), shake_deg=DEBLUR_SHAKE_DEG, seed=seed)
-    return synth.make_clip("room", W, H, F, seed=seed)
+        c = synth.make_clip("room", W, H, frames, seed=seed, sigma_img=DEBLUR_SIGMA_IMG)
+        return synth.shake_blur(c, range(2, frames, 4), shake_deg=DEBLUR_SHAKE_DEG, seed=seed)
+    return synth.make_clip("room", W, H, frames, seed=seed)
 
 
 def _inpaint_box(clip):
@@ -777,6 +778,8 @@ def main():
     ap.add_argument("--colour", default=None, choices=["fp32", "fp16"],
                     help="colour storage (default: fp16 for the virtual-aperture workloads, fp32 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stream", action="store_true",
+                    help="end to end with a full clip upload per step only (no streaming appends)")
     ap.add_argument("--workload", default="fhd", choices=sorted(WORKLOADS))
     ap.add_argument("--out-frames", type=int, default=None, help="output frames per step (default per workload)")
     ap.add_argument("--train-clips", type=int, default=200, help="learned workload: generated training clips")
@@ -995,8 +998,62 @@ def main():
         ss.ssvp_destroy(ctx2)
     h2d = clip.rgb.nbytes + clip.depth.nbytes
     d2h = out_h.numel() * 4
-    frames_per_chunk = max(1, min(F, (256 << 20) // (W * H * 16)))
+    frames_per_chunk = max(1, min(F, (4 << 30) // (W * H * 16)))
     e2e_launches = -(-F // frames_per_chunk) + 6 + 1 + 2 + 1  # packs, median passes, depth range, gradient sums, gather
+    e2e_full = {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "gpu_launches_per_step": e2e_launches,
+                "pipelining": "two contexts on two streams, step i + 1 queued before step i is read back"
+                              if pipelined else "none",
+                "inputs": "the whole clip uploaded every step (ssvp_load_clip)"}
+    e2e = e2e_full
+    if MODE in (0, 1, 5, 6) and not args.no_stream:
+        # Streaming video: a longer clip of the same scene family arrives N_OUT frames at a time.  A
+        # step appends the N_OUT new frames (ssvp_append_frames: pinned host memory to the device,
+        # the kept frames slid on the device into the clip's second window while the previous
+        # step's gather runs), reads back the previous step's output frames and queues its gather.
+        n_stream = max(2, min(args.steps, 10))
+        video = _workload_clip(seed=shard(rank, world)["seed"], frames=F + N_OUT * (n_stream + 2))
+        v_rgb = torch.from_numpy(video.rgb).pin_memory()
+        v_dep = torch.from_numpy(video.depth).pin_memory()
+        ctx3 = ss.ssvp_create(local, stream)
+        if MODE == 6:
+            ss.ssvp_set_shutter(ctx3, _shutter_xi(), T)
+        ss.ssvp_load_clip(ctx3, 0, W, H, F, v_rgb[:F], v_dep[:F], ss.SSVP_MEM_HOST, cfmt)
+        ss.ssvp_set_cameras(ctx3, 0, video.K[:F], 1, video.w2c[:F])
+        outs_s = (torch.empty_like(out_h).pin_memory(), torch.empty_like(out_h).pin_memory())
+        state = {"next": F}
+
+        def s_append():
+            a = state["next"]
+            ss.ssvp_append_frames(ctx3, 0, N_OUT, v_rgb[a:a + N_OUT], v_dep[a:a + N_OUT], video.K[a:a + N_OUT], 1,
+                                  video.w2c[a:a + N_OUT], ss.SSVP_MEM_HOST)
+            state["next"] = a + N_OUT
+
+        def s_run(n):
+            s_append()
+            ss.ssvp_gather_filter(ctx3, p, [0])
+            for i in range(1, n):
+                s_append()
+                ss.ssvp_read_output(ctx3, 0, O_BEGIN, O_BEGIN + N_OUT, outs_s[(i - 1) % 2], ss.SSVP_MEM_HOST)
+                ss.ssvp_gather_filter(ctx3, p, [0])
+            ss.ssvp_read_output(ctx3, 0, O_BEGIN, O_BEGIN + N_OUT, outs_s[(n - 1) % 2], ss.SSVP_MEM_HOST)
+
+        s_run(2)  # the clip's second window is allocated by the first append
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s_run(n_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s_ms = max_over_ranks(e0.elapsed_time(e1) / n_stream, world, dev)
+        ss.ssvp_destroy(ctx3)
+        e2e = {"value": world * mpix / (s_ms / 1e3), "unit": "Mpix/s",
+               "h2d_bytes_per_step": N_OUT * W * H * 16, "d2h_bytes_per_step": d2h, "ms_per_step": s_ms,
+               "gpu_launches_per_step": 1 + 6 + 1 + 2 + 1,  # pack, median passes, depth range, gradient sums, gather
+               "inputs": f"streaming: each step appends its {N_OUT} new frames (ssvp_append_frames) to the "
+                         f"{F}-frame window of a {video.F}-frame clip of the same scene family",
+               "full_reload": e2e_full}
+        del video, v_rgb, v_dep
 
     peaks, peak_kind = _peaks()
     kernel_ms = float(np.mean(step_ms))
@@ -1023,10 +1080,7 @@ def main():
         "psnr_db": {"output_vs_clean": psnr_out, "input_vs_clean": psnr_in, "reference": psnr_ref, **extra_quality},
         "gpu_launches": args.steps,
         "roofline": roofline,
-        "e2e": {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "gpu_launches_per_step": e2e_launches,
-                "pipelining": "two contexts on two streams, step i + 1 queued before step i is read back"
-                              if pipelined else "none"},
+        "e2e": e2e,
         "clocks": clk_summary,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
