@@ -2,9 +2,10 @@
 // (tcgen05).  Inference first; the training kernel, which reuses its forward pass, follows it.
 //
 // One CTA of 128 threads takes two pixels at a time: their 2 x 64 capped samples are the 128 rows
-// of the layer-1 product, and two such pairs are in flight (a two-stage pipeline: while layer 2
-// of one pair runs, the threads build the next pair's features and finish the previous pair;
-// the next pair's loads are issued before the waits).  Each thread owns one row (one sample):
+// of the layer-1 product.  While layer 2 of one pair runs, the threads build the next pair's
+// features; while its layer 1 runs, they finish the previous pair and load the records of the
+// next.  Seven CTAs share an SM (64 tensor-memory columns each), so that other CTAs' warps issue
+// while one waits for its products.  Each thread owns one row (one sample):
 //   1. it builds the sample's 16 BF16 features and stores them into shared memory in the
 //      tensor cores' K-major core-matrix layout (8 rows x 16 bytes per core matrix);
 //   2. one elected thread issues tcgen05.mma: D1 (128 x 64, FP32, in tensor memory) = F W1^T;
@@ -29,19 +30,23 @@ namespace {
 
 constexpr int kS = 64, kF = 16, kH = 64;
 constexpr int kTcThreads = 128;   // one sample row per thread, two pixels per CTA
-constexpr unsigned kTmemCols = 128;  // two stages of 64 columns (D1; D2 reuses the first 16)
+constexpr unsigned kTmemCols = 64;  // D1; D2 reuses its first 16 columns
+constexpr int kTcCtasPerSm = 7;
 // shared operands, K-major core matrices; core (i, j) of an R x K operand holds rows 8i..8i+7 and
-// K elements 8j..8j+7 at byte offset (i * K / 8 + j) * 128, row r of it at + 16 (r % 8)
-constexpr int kSmStageA1 = 4096, kSmStageA2 = 16384;  // per pipeline stage
-constexpr int kSmA1 = 0;        // features, 128 x 16, two stages
-constexpr int kSmB1 = 8192;     // W1, 64 x 16
-constexpr int kSmA2 = 10240;    // H, 128 x 64, two stages
-constexpr int kSmB2 = 43008;    // W2 padded to 16 rows, 16 x 64
-constexpr int kSmA0 = 45056;    // constant operand for the b1 residual: ones in K slots 0 and 1, 128 x 16
-constexpr int kSmB0 = 49152;    // b1's two lower BF16 parts in K slots 0 and 1, 64 x 16
-constexpr int kSmBytes = 51200;
-// dynamic shared memory per CTA: the operands, 50 KB.  At most four CTAs fit on an SM (all 608 in
-// one wave on 152 SMs), so their 4 x 128 tensor-memory columns always fit in the SM's 512
+// K elements 8j..8j+7 at byte offset (i * K / 8 + j) * 128, row r of it at + 16 (r % 8).  One
+// buffer of each A operand: a pair's features are written after every thread has waited for the
+// previous pair's layer 1, and its H after every thread has waited for the previous layer 2.
+constexpr int kSmA1 = 0;        // features, 128 x 16
+constexpr int kSmB1 = 4096;     // W1, 64 x 16
+constexpr int kSmA2 = 6144;     // H, 128 x 64
+constexpr int kSmB2 = 22528;    // W2 padded to 16 rows, 16 x 64
+constexpr int kSmA0 = 24576;    // constant operand for the b1 residual: ones in K slots 0 and 1, 128 x 16
+constexpr int kSmB0 = 28672;    // b1's two lower BF16 parts in K slots 0 and 1, 64 x 16
+constexpr int kSmBytes = 30720;
+// dynamic shared memory per CTA: the operands, 30 KB.  At most seven CTAs fit on an SM (shared
+// memory: 7 x 32 KB with the static part and the per-CTA reserve; registers: 128 threads x 7 at
+// <= 72), all 1,064 in one wave on 152 SMs, and their 7 x 64 tensor-memory columns always fit in
+// the SM's 512
 constexpr int kSmRequest = kSmBytes;
 // a waiting thread suspends in try_wait for up to kWaitHintNs per poll; kWaitLimit polls (about
 // 1 s) before a wait counts as timed out
@@ -106,6 +111,14 @@ __device__ __forceinline__ void tmem_ld32_nowait(unsigned taddr, unsigned (&r)[3
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16_nowait(unsigned taddr, unsigned (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
@@ -213,7 +226,7 @@ struct RowData {
     unsigned f89;
     float pl[3];
     int n;
-    long long px;
+    int px;  // crop pixel (crops hold fewer than 2^26 pixels)
 };
 
 // what the epilogue of the previous pair keeps
@@ -221,10 +234,10 @@ struct PrevRow {
     float3 c;
     float pl[3];
     int n;
-    long long px;
+    int px;  // crop pixel (crops hold fewer than 2^26 pixels)
 };
 
-__device__ __forceinline__ void load_row(const MlpArgs &m, long long pair, int tid, RowData &r) {
+__device__ __forceinline__ void load_row(const MlpArgs &m, int pair, int tid, RowData &r) {
     r.px = 2 * pair + (tid >> 6);
     const int s = tid & 63;
     r.n = 0;
@@ -234,7 +247,7 @@ __device__ __forceinline__ void load_row(const MlpArgs &m, long long pair, int t
     if (r.px < m.n_px) {
         // the set's storage holds 64 rows per pixel: rows past n are read (in bounds) and ignored,
         // so that no load waits on the count
-        const long long k = r.px * kS + s;
+        const unsigned k = (unsigned)r.px * kS + s;  // below 2^32: crops hold fewer than 2^26 pixels
         r.n = m.sets.n[r.px];
         r.c = __ldg(m.sets.col + k);
         r.f89 = __ldg(m.sets.f89 + k);
@@ -245,10 +258,49 @@ __device__ __forceinline__ void load_row(const MlpArgs &m, long long pair, int t
     }
 }
 
-// Two pixel pairs are in flight: while the tensor cores run layer 2 of pair i, the threads build
-// the features of pair i + 1 and finish pair i - 1.  Stage s = i % 2 owns the operand buffers
-// A1[s], A2[s] and the tensor-memory columns [64 s, 64 s + 64) (D1, then D2 in its first 16).
-__global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpArgs m, int *err) {
+// Iteration i of a CTA takes pixel pair blockIdx.x + i * gridDim.x.  The 64 tensor-memory
+// columns hold D1 of pair i, then D2 of pair i in their first 16: the threads read D2 of pair i - 1
+// (after building the features of pair i) before layer 1 of pair i is issued.
+__device__ __forceinline__ void pair_sums(float zw, float zc, const PrevRow &pr, float b20, float b21, int s_row,
+                                          int warp, int lane, float (*s_red)[5]) {
+    float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
+    if (s_row < pr.n) {
+        const float w = softplusf(zw + b20);
+        sw = w;
+        sr = w * pr.c.x;
+        sg = w * pr.c.y;
+        sb = w * pr.c.z;
+        sc = sigmoidf(zc + b21);
+    }
+    const float t4 = warp_sum4(sw, sr, sg, sb, lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
+    if ((lane & 7) == 0) s_red[warp][lane >> 3] = t4;
+    if (lane == 0) s_red[warp][4] = sc;
+}
+
+// the output of a pixel from the per-warp sums of its two warps (w0, w0 + 1)
+__device__ __forceinline__ void pair_output(const MlpArgs &m, const PrevRow &pr, int w0, const float (*s_red)[5]) {
+    float o0 = pr.pl[0], o1 = pr.pl[1], o2 = pr.pl[2], conf = 0.0f;
+    if (pr.n > 0) {
+        const float tw = s_red[w0][0] + s_red[w0 + 1][0];
+        conf = __fdividef(s_red[w0][4] + s_red[w0 + 1][4], (float)pr.n);
+        if (conf >= m.tau && tw > 0.0f) {
+            const float inv = __frcp_rn(tw);
+            o0 = (s_red[w0][1] + s_red[w0 + 1][1]) * inv;
+            o1 = (s_red[w0][2] + s_red[w0 + 1][2]) * inv;
+            o2 = (s_red[w0][3] + s_red[w0 + 1][3]) * inv;
+        }
+    }
+    const long long u = m.x0 + pr.px % m.cw, v = m.y0 + pr.px / m.cw;
+    float *o = m.out + (((long long)m.O * m.H + v) * m.W + u) * 3;
+    o[0] = o0;
+    o[1] = o1;
+    o[2] = o2;
+    if (m.conf_out) m.conf_out[pr.px] = conf;
+}
+
+__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) mlp_infer_tc_kernel(const MlpArgs m, int *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ float s_red[4][5];
     __shared__ unsigned long long s_mbar[2];  // layer-1 and layer-2 completion
@@ -278,92 +330,81 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpAr
     const unsigned tmem = s_tmem;
     const unsigned lane_base = (unsigned)(warp * 32) << 16;  // this warp's 32 lanes
     const unsigned sbase = smem_u32(sm);
-    const unsigned long long dB1 = smem_desc(sbase + kSmB1, 128, 256), dA0 = smem_desc(sbase + kSmA0, 128, 256),
-                             dB0 = smem_desc(sbase + kSmB0, 128, 256);
+    const unsigned long long dA1 = smem_desc(sbase + kSmA1, 128, 256), dB1 = smem_desc(sbase + kSmB1, 128, 256),
+                             dA0 = smem_desc(sbase + kSmA0, 128, 256), dB0 = smem_desc(sbase + kSmB0, 128, 256);
     constexpr unsigned id1 = instr_desc(kH, 128), id2 = instr_desc(16, 128);
     unsigned ph1 = 0, ph2 = 0;
     bool bad = false;
 
-    const long long n_pairs = (m.n_px + 1) / 2;
-    // two register sets take turns: one is consumed while the loads of the next pair land in the
-    // other, so no copy waits on loads in flight
-    RowData set0, set1;
+    const int n_pairs = (int)((m.n_px + 1) / 2);
+    RowData cur;
     PrevRow prev;
     prev.n = 0;
-    prev.px = m.n_px;
-    long long pair = blockIdx.x;
-    if (pair < n_pairs) load_row(m, pair, tid, set0);
+    prev.px = n_pairs * 2;
+    if ((int)blockIdx.x < n_pairs) load_row(m, blockIdx.x, tid, cur);
     int it = 0;
-    auto body = [&](const RowData &cur, RowData &nxt) -> bool {
-        const int st = it & 1;
-        const unsigned a1 = sbase + kSmA1 + st * kSmStageA1, a2 = sbase + kSmA2 + st * kSmStageA2;
-        const unsigned d_st = tmem + 64u * st;
-        // 1. features of this pair, then layer 1 on the tensor cores
+    for (int pair = blockIdx.x; pair < n_pairs; pair += gridDim.x, ++it) {
+        // 1. this pair's features (the single A1 buffer is free: every thread has waited for the
+        // previous pair's layer 1)
         {
             unsigned wd[8];
 #pragma unroll
             for (int w = 0; w < 8; ++w) wd[w] = s_row < cur.n ? feat_word(w, cur.c, cur.f89, cur.info, cur.pl) : 0u;
             if (s_row < cur.n) wd[7] |= 0x3f80u << 16;  // slot 15 (feature 15 = 0) carries 1.0 for b1
-            unsigned char *A1 = sm + (a1 - sbase);
+            unsigned char *A1 = sm + kSmA1;
             *reinterpret_cast<uint4 *>(A1 + core_off(tid, 0, 2)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
             *reinterpret_cast<uint4 *>(A1 + core_off(tid, 1, 2)) = make_uint4(wd[4], wd[5], wd[6], wd[7]);
         }
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        if (s_bad) return false;  // uniform: written only between the second barrier and the next first one
-        if (tid == 0 && !m.skip_mma) {
-            fence_after();
-            mma_tc(d_st, smem_desc(a1, 128, 256), dB1, id1, 0);
-            mma_tc(d_st, dA0, dB0, id1, 1);
-            mma_commit(bar1);
-        }
-        // 2. the previous pair: (z_w, z_c) from its layer 2, weighted sums per warp
+        // 2. the previous pair's (z_w, z_c), read before this pair's layer 1 overwrites the columns
         if (it > 0) {
             bad |= !mbar_wait(bar2, ph2);
             ph2 ^= 1u;
             fence_after();
             float zw, zc;
-            tmem_ld2(tmem + 64u * (st ^ 1) + lane_base, zw, zc);
-            float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
-            if (s_row < prev.n) {
-                const float w = softplusf(zw + b20);
-                sw = w;
-                sr = w * prev.c.x;
-                sg = w * prev.c.y;
-                sb = w * prev.c.z;
-                sc = sigmoidf(zc + b21);
-            }
-            const float t4 = warp_sum4(sw, sr, sg, sb, lane);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
-            if ((lane & 7) == 0) s_red[warp][lane >> 3] = t4;
-            if (lane == 0) s_red[warp][4] = sc;
+            tmem_ld2(tmem + lane_base, zw, zc);
+            pair_sums(zw, zc, prev, b20, b21, s_row, warp, lane, s_red);
         }
-        // 3. the next pair's loads, in flight during the waits below
-        const long long pair_next = pair + gridDim.x;
-        if (pair_next < n_pairs) load_row(m, pair_next, tid, nxt);
-        // 4. H = ReLU(D1 + b1) in BF16 as layer 2's A operand, then layer 2
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (s_bad) break;  // uniform: written only between the second barrier and the next first one
+        if (tid == 0 && !m.skip_mma) {
+            fence_after();
+            mma_tc(tmem, dA1, dB1, id1, 0);
+            mma_tc(tmem, dA0, dB0, id1, 1);
+            mma_commit(bar1);
+        }
+        // 3. the previous pair's outputs (threads 32 and 96: the second warp of each pixel, so that
+        // warp 0, which issues the MMAs, goes on first)
+        if (it > 0 && s_row == 32 && prev.px < m.n_px) pair_output(m, prev, warp - 1, s_red);
+        prev.c = make_float3(cur.c.x, cur.c.y, cur.c.z);
+        prev.n = cur.n;
+        prev.px = cur.px;
+        prev.pl[0] = cur.pl[0];
+        prev.pl[1] = cur.pl[1];
+        prev.pl[2] = cur.pl[2];
+        // 4. the next pair's records, in flight during the waits below and the next features
+        if (pair + (int)gridDim.x < n_pairs) load_row(m, pair + gridDim.x, tid, cur);
+        // 5. H = ReLU(D1 + b1) in BF16 as layer 2's A operand (the single A2 buffer is free: every
+        // thread has waited for the previous pair's layer 2), then layer 2
         bad |= !mbar_wait(bar1, ph1);
         ph1 ^= 1u;
         fence_after();
         {
-            unsigned char *A2 = sm + (a2 - sbase);
-            // both halves of the row in flight together, one wait
-            unsigned v0[32], v1[32];
-            tmem_ld32_nowait(d_st + lane_base, v0);
-            tmem_ld32_nowait(d_st + lane_base + 32, v1);
-            tmem_wait_ld();
+            unsigned char *A2 = sm + kSmA2;
+            // a quarter of the row (16 columns) at a time, to keep the registers for six CTAs per SM
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const unsigned (&v)[32] = half ? v1 : v0;
-                unsigned h[16];
+            for (int qq = 0; qq < 4; ++qq) {
+                unsigned v[16];
+                tmem_ld16_nowait(tmem + lane_base + 16u * qq, v);
+                tmem_wait_ld();
+                unsigned h[8];
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
+                for (int i = 0; i < 8; ++i)
                     h[i] = relu_bf16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    *reinterpret_cast<uint4 *>(A2 + core_off(tid, 4 * half + q, 8)) =
+                for (int q = 0; q < 2; ++q)
+                    *reinterpret_cast<uint4 *>(A2 + core_off(tid, 2 * qq + q, 8)) =
                         make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
             }
         }
@@ -374,92 +415,23 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_infer_tc_kernel(const MlpAr
             fence_after();
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-                mma_tc(d_st, smem_desc(a2 + kk * 256, 128, 1024), smem_desc(sbase + kSmB2 + kk * 256, 128, 1024), id2,
-                       kk);
+                mma_tc(tmem, smem_desc(sbase + kSmA2 + kk * 256, 128, 1024),
+                       smem_desc(sbase + kSmB2 + kk * 256, 128, 1024), id2, kk);
             mma_commit(bar2);
         }
         if (bad) s_bad = 1;
-        // 5. the previous pair's outputs (its per-warp sums are complete after the barrier)
-        // (threads 32 and 96: the second warp of each pixel, so that warp 0, which issues the
-        // MMAs, reaches the next barrier first)
-        if (it > 0 && s_row == 32 && prev.px < m.n_px) {
-            const int w0 = warp - 1;
-            float o0 = prev.pl[0], o1 = prev.pl[1], o2 = prev.pl[2], conf = 0.0f;
-            if (prev.n > 0) {
-                const float tw = s_red[w0][0] + s_red[w0 + 1][0];
-                conf = __fdividef(s_red[w0][4] + s_red[w0 + 1][4], (float)prev.n);
-                if (conf >= m.tau && tw > 0.0f) {
-                    const float inv = __frcp_rn(tw);
-                    o0 = (s_red[w0][1] + s_red[w0 + 1][1]) * inv;
-                    o1 = (s_red[w0][2] + s_red[w0 + 1][2]) * inv;
-                    o2 = (s_red[w0][3] + s_red[w0 + 1][3]) * inv;
-                }
-            }
-            const long long u = m.x0 + prev.px % m.cw, v = m.y0 + prev.px / m.cw;
-            float *o = m.out + (((long long)m.O * m.H + v) * m.W + u) * 3;
-            o[0] = o0;
-            o[1] = o1;
-            o[2] = o2;
-            if (m.conf_out) m.conf_out[prev.px] = conf;
-        }
-        prev.c = make_float3(cur.c.x, cur.c.y, cur.c.z);
-        prev.n = cur.n;
-        prev.px = cur.px;
-        prev.pl[0] = cur.pl[0];
-        prev.pl[1] = cur.pl[1];
-        prev.pl[2] = cur.pl[2];
-        pair += gridDim.x;
-        ++it;
-        return pair < n_pairs;
-    };
-    while (pair < n_pairs) {
-        if (!body(set0, set1)) break;
-        if (!body(set1, set0)) break;
     }
     __syncthreads();  // s_bad is settled for every thread
     // the last pair: its layer 2 is in flight
     if (it > 0 && !s_bad) {
-        const int st = (it - 1) & 1;
         bad |= !mbar_wait(bar2, ph2);
         ph2 ^= 1u;
         fence_after();
         float zw, zc;
-        tmem_ld2(tmem + 64u * st + lane_base, zw, zc);
-        float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
-        if (s_row < prev.n) {
-            const float w = softplusf(zw + b20);
-            sw = w;
-            sr = w * prev.c.x;
-            sg = w * prev.c.y;
-            sb = w * prev.c.z;
-            sc = sigmoidf(zc + b21);
-        }
-        const float t4 = warp_sum4(sw, sr, sg, sb, lane);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
-        if ((lane & 7) == 0) s_red[warp][lane >> 3] = t4;
-        if (lane == 0) s_red[warp][4] = sc;
+        tmem_ld2(tmem + lane_base, zw, zc);
+        pair_sums(zw, zc, prev, b20, b21, s_row, warp, lane, s_red);
         __syncthreads();
-        if (s_row == 32 && prev.px < m.n_px) {
-            const int w0 = warp - 1;
-            float o0 = prev.pl[0], o1 = prev.pl[1], o2 = prev.pl[2], conf = 0.0f;
-            if (prev.n > 0) {
-                const float tw = s_red[w0][0] + s_red[w0 + 1][0];
-                conf = __fdividef(s_red[w0][4] + s_red[w0 + 1][4], (float)prev.n);
-                if (conf >= m.tau && tw > 0.0f) {
-                    const float inv = __frcp_rn(tw);
-                    o0 = (s_red[w0][1] + s_red[w0 + 1][1]) * inv;
-                    o1 = (s_red[w0][2] + s_red[w0 + 1][2]) * inv;
-                    o2 = (s_red[w0][3] + s_red[w0 + 1][3]) * inv;
-                }
-            }
-            const long long u = m.x0 + prev.px % m.cw, v = m.y0 + prev.px / m.cw;
-            float *o = m.out + (((long long)m.O * m.H + v) * m.W + u) * 3;
-            o[0] = o0;
-            o[1] = o1;
-            o[2] = o2;
-            if (m.conf_out) m.conf_out[prev.px] = conf;
-        }
+        if (s_row == 32 && prev.px < m.n_px) pair_output(m, prev, warp - 1, s_red);
     }
     if (bad) atomicOr(err, 1);
     // after a time-out the tensor cores may still be busy: one more bounded wait on each barrier
@@ -787,7 +759,7 @@ cudaError_t launch_mlp_infer_tc(const MlpArgs &m, int *err, cudaStream_t s) {
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const long long pairs = (m.n_px + 1) / 2;
-    long long blocks = (long long)sms * 4;
+    long long blocks = (long long)sms * kTcCtasPerSm;
     if (blocks > pairs) blocks = pairs;
     static_assert(kSmBytes <= kSmRequest, "operands exceed the requested shared memory");
     mlp_infer_tc_kernel<<<(unsigned)blocks, kTcThreads, kSmRequest, s>>>(m, err);
