@@ -30,6 +30,12 @@ namespace {
 #ifndef SSVP_MIN_CTAS
 #define SSVP_MIN_CTAS 4  // resident CTAs per SM the register allocation must allow
 #endif
+// The extraction gather of the learned filter keeps four more values live than the plain one; at
+// 64 registers (four CTAs per SM) it spills 80 bytes a thread, at 80 (three CTAs) 8.  Short windows,
+// whose accepted samples are nearly all stored, run faster with three CTAs and no spill traffic;
+// long ones, where the candidate loads dominate, with four CTAs and more warps to hide them.
+constexpr int kLearnCtasShort = 3;
+constexpr int kLearnShortSlots = 17;  // windows of up to +-8 frames
 
 
 
@@ -383,8 +389,8 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
 }
 
 // One CTA per 32 x kTileY output tile of one output frame (grid: tiles x output frames).
-template <int K, int CFMT, bool DEBUG, bool LEARN = false>
-__global__ void __launch_bounds__(kThreads, SSVP_MIN_CTAS) gather_kernel(const GatherArgs a) {
+template <int K, int CFMT, bool DEBUG, bool LEARN = false, int MINB = SSVP_MIN_CTAS>
+__global__ void __launch_bounds__(kThreads, MINB) gather_kernel(const GatherArgs a) {
     extern __shared__ float4 sgeom[];
     __shared__ float s_const[4];
     __shared__ unsigned long long s_cnt[2][kThreads / 32];
@@ -560,7 +566,9 @@ cudaError_t launch_k(const GatherArgs &a, cudaStream_t s) {
     dim3 grid((a.cw + kTileX - 1) / kTileX, (a.ch + kTileY - 1) / kTileY, a.n_out);
     size_t smem = sizeof(float4) * kSlotVec * (size_t)a.n_slots;
     const bool dbg = a.membership || a.pixel_stats;
-    if (a.sets.col) gather_kernel<K, CFMT, false, true><<<grid, kThreads, smem, s>>>(a);
+    if (a.sets.col && a.n_slots <= kLearnShortSlots)
+        gather_kernel<K, CFMT, false, true, kLearnCtasShort><<<grid, kThreads, smem, s>>>(a);
+    else if (a.sets.col) gather_kernel<K, CFMT, false, true><<<grid, kThreads, smem, s>>>(a);
     else if (dbg) gather_kernel<K, CFMT, true><<<grid, kThreads, smem, s>>>(a);
     else gather_kernel<K, CFMT, false><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
