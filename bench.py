@@ -579,6 +579,32 @@ def run_learned(args, ss, torch, dev, stream, world, rank):
     with ClockSampler(local) as clk:
         ms_l, out_l = timed(ss.SSVP_MODE_LEARNED, args.steps)
     ms_p, out_p = timed(ss.SSVP_MODE_DENOISE, args.steps)
+    # the two kernels of a learned step, timed apart: a second pass of the same steps with the
+    # library's kernel trace on (CUDA events around each launch)
+    p.mode = ss.SSVP_MODE_LEARNED
+    ss.ssvp_trace_enable(ctx, True)
+    ss.ssvp_trace_read(ctx)
+    for _ in range(args.steps):
+        ss.ssvp_gather_filter(ctx, p, [0])
+    trace = ss.ssvp_trace_read(ctx)
+    ss.ssvp_trace_enable(ctx, False)
+    ex_step, acc_step, _ = ss.ssvp_read_stats(ctx)  # the last call: N_OUT output frames
+    peaks, peak_kind = _peaks()
+    sm_mhz = clk.summary()["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    n_ext, t_ext = trace.get("extract", (0, 0.0))
+    n_inf, t_inf = trace.get("infer", (0, 0.0))
+    ext_ms, inf_ms = t_ext / max(n_ext, 1), t_inf / max(n_inf, 1)
+    rl_ext = roofline_block(0, ex_step / N_OUT, acc_step / N_OUT, ext_ms, sm_mhz, peaks, peak_kind, {},
+                            ex_step / N_OUT * BYTES_PER_CANDIDATE["fp32"])
+    rl_ext["kernel"] = "extraction gather (the window gather with the stores of the capped sample sets), one frame"
+    mlp_flops = 2 * (16 * 64 + 64 * 2) * 64 * W * H  # 16 -> 64 -> 2 over 64 samples per pixel, one frame
+    bf16_peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    rl_inf = {"bound": "tensor", "achieved": mlp_flops / (inf_ms / 1e3) / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+              "frac": mlp_flops / (inf_ms / 1e3) / 1e12 / bf16_peak, "traffic": None, "kernel_ms": inf_ms,
+              "kernel": "tcgen05 inference, one frame",
+              "accounting": "2 x (16 x 64 + 64 x 2) FLOP per sample x 64 samples per pixel x pixels of the frame "
+                            f"(the network, not the padded products) / kernel time; peak = {peak_kind} BF16 "
+                            "(sustained: the kernel runs inside a long step)"}
     clean = clip.clean[O_BEGIN:O_BEGIN + N_OUT]
     psnr = lambda a_: float(10 * np.log10(1.0 / np.mean((a_.astype(np.float64) - clean) ** 2)))
     mpix = N_OUT * W * H / 1e6
@@ -613,8 +639,69 @@ def run_learned(args, ss, torch, dev, stream, world, rank):
         "plain_same_run": {"value": world * mpix / (ms_p / 1e3), "unit": "Mpix/s", "ms_per_step": ms_p},
         "learned_short_window": short,
         "gpu_launches": args.steps * N_OUT * 2,
+        "roofline": rl_ext if ext_ms >= inf_ms else rl_inf,
+        "roofline_other_kernel": rl_inf if ext_ms >= inf_ms else rl_ext,
+        "kernel_trace": {k: {"launches": n, "ms": t} for k, (n, t) in trace.items()},
         "clocks": clk.summary(),
     }
+    # end to end through the C ABI with host buffers: every step uploads the clip from pinned host
+    # memory, runs the learned filter and reads the output frames back (one context, in order)
+    rgb_h = torch.from_numpy(clip.rgb).pin_memory()
+    dep_h = torch.from_numpy(clip.depth).pin_memory()
+    out_h = torch.empty((N_OUT, H, W, 3), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        ss.ssvp_load_clip(ctx, 0, W, H, F, rgb_h, dep_h, ss.SSVP_MEM_HOST, 0)
+        ss.ssvp_set_cameras(ctx, 0, clip.K, 1, clip.w2c)
+        ss.ssvp_gather_filter(ctx, p, [0])
+        ss.ssvp_read_output(ctx, 0, O_BEGIN, O_BEGIN + N_OUT, out_h, ss.SSVP_MEM_HOST)
+
+    e2e_step()
+    n_e2e = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(a.elapsed_time(b) / n_e2e, world, dev)
+    line["e2e"] = {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": clip.rgb.nbytes +
+                   clip.depth.nbytes, "d2h_bytes_per_step": out_h.numel() * 4, "ms_per_step": e2e_ms,
+                   "pipelining": "none (one context; each step's read-back waits for its filter)"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle's learned filter (capped sets and features in C, the BF16-rounded network per
+        # pixel) on a centred crop of the first output frame, grown to about 10 s
+        import oracle
+        W1, b1, W2, b2 = ss.ssvp_get_mlp(ctx)
+        prm = oracle.default_params(clip.depth, k=K_WIN, T=T, radius_rel=RADIUS_REL)
+        v = oracle.ClipView.of(clip)
+        side = 16
+        while True:
+            crop = ((W - side) // 2, (H - side) // 2, side, side)
+            t0 = time.perf_counter()
+            of, oc, on, op = oracle.learned_crop(v, prm, O_BEGIN, crop=crop)
+            res = np.zeros((side, side, 3))
+            for y in range(side):
+                for x in range(side):
+                    res[y, x] = oracle.mlp_pixel(of[y, x], oc[y, x], on[y, x], W1, b1, W2, b2, round_bf16=True,
+                                                 tau=p.conf_threshold, plain=op[y, x])[1]
+            dt = time.perf_counter() - t0
+            if dt > 10.0 or 2 * side > 512:
+                break
+            side *= 2
+        x0, y0, cw, ch = crop
+        diff = np.abs(out_l[0, y0:y0 + ch, x0:x0 + cw].astype(np.float64) - res).max(-1)
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        line["cpu_baseline"] = {"value": side * side / dt / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{side}x{side} crop of output frame {O_BEGIN}, learned filter with the "
+                                          f"trained weights, BF16 rounding as the tensor cores ({dt:.1f} s): capped "
+                                          f"sets and features on {cores} threads, the network one pixel at a time "
+                                          "on one thread"}
+        line["max_abs_vs_oracle"] = {"value": float(diff.max()), "p999": float(np.quantile(diff, 0.999)),
+                                     "frac_above_1e-3": float((diff > 1e-3).mean()), "pixels": int(diff.size),
+                                     "note": "all pixels of the crop, including radius-band, rounding-tie and "
+                                             "confidence-tie pixels"}
     ss.ssvp_destroy(ctx)
     return line
 

@@ -305,6 +305,42 @@ int ssvp_read_output(ssvp_ctx *ctx, int clip_id, int frame_begin, int frame_end,
 /* Device pointer of a clip's output buffer (F*H*W*3 floats, owned by the library). */
 int ssvp_output_device_ptr(ssvp_ctx *ctx, int clip_id, void **dev_ptr);
 
+/*
+ * Kernel timing (no counterpart in the paper; a measurement aid).  While tracing is on
+ * (ssvp_trace_enable(ctx, 1); off when a context is created), each gather, learned-filter
+ * (extraction, inference, training, Adam), mask and batched-plan launch the context queues is
+ * bracketed by a pair of CUDA timing events on its stream and recorded under one of the kinds
+ * below; so is the whole of each ssvp_load_clip / ssvp_append_frames (copies and kernels on the
+ * load stream: one SSVP_TRACE_LOAD entry per call), and a batched plan's launch (one CUDA graph)
+ * is one SSVP_TRACE_BATCH entry.  Not traced: the autotuner's trial launches, the expansion of
+ * ssvp_learned_samples and the weight conversion of ssvp_set_mlp.  ssvp_trace_read waits for the
+ * traced work; for each kind with launches since the last read, in increasing kind order and at
+ * most max_kinds of them, it writes the kind, the launch count and the summed device time in
+ * milliseconds, sets *n_kinds to the number written, and clears the record (kinds beyond
+ * max_kinds are dropped).  The times are those of the bracketed stream intervals: work that
+ * overlaps on other streams shares the device and is not subtracted.  Arrays are host memory,
+ * owned by the caller; any of kind, launches, ms, n_kinds may be NULL.  Errors: SSVP_EINVAL (NULL
+ * ctx, max_kinds < 0), SSVP_ECUDA.
+ */
+enum {
+    SSVP_TRACE_GATHER = 0,    /* window gather and filter (denoise, mean, deblur, shutter) */
+    SSVP_TRACE_APERTURE = 1,  /* virtual-aperture gather (Eq. 13-14) */
+    SSVP_TRACE_FRUSTUM = 2,   /* frustum gather (Eq. 1-2): filter, inpainting, semi-transparency */
+    SSVP_TRACE_SUPERRES = 3,  /* frustum gather on the super-resolution grid (Eq. 6-7) */
+    SSVP_TRACE_EXTRACT = 4,   /* learned filter: capped sample sets (extraction gather) */
+    SSVP_TRACE_INFER = 5,     /* learned filter: tensor-core inference */
+    SSVP_TRACE_TRAIN = 6,     /* learned filter: forward and backward pass on a batch */
+    SSVP_TRACE_ADAM = 7,      /* learned filter: Adam step */
+    SSVP_TRACE_BATCH = 8,     /* one launch of a batched plan */
+    SSVP_TRACE_LOAD = 9,      /* pack, median, depth ranges and gradient sums of a load or append */
+    SSVP_TRACE_MASK = 10,     /* inpainting mask from a scene-space box */
+    SSVP_TRACE_KINDS = 11
+};
+int ssvp_trace_enable(ssvp_ctx *ctx, int on);
+int ssvp_trace_read(ssvp_ctx *ctx, int max_kinds, int *kind, int *launches, double *ms, int *n_kinds);
+/* A short name of a trace kind ("gather", "infer", ...), or "" for an unknown kind. */
+const char *ssvp_trace_kind_name(int kind);
+
 /* Statistics of the last ssvp_gather_filter call (waits for it): examined candidates (window
  * pixels inside the image), accepted samples |S| summed over pixels, and the sum of weights W
  * (Sec. "Filtering" reports W / |S|).  Any pointer may be NULL. */

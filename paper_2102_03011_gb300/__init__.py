@@ -22,6 +22,8 @@ SSVP_MODE_DENOISE, SSVP_MODE_APERTURE, SSVP_MODE_LEARNED, SSVP_MODE_MEAN = 0, 1,
 SSVP_MODE_DEBLUR, SSVP_MODE_SHUTTER, SSVP_MODE_INPAINT, SSVP_MODE_SEMI = 4, 5, 6, 7
 SSVP_GATHER_WINDOW, SSVP_GATHER_FRUSTUM = 0, 1
 SSVP_MAX_CLIPS, SSVP_MAX_K, SSVP_MAX_HALF_WINDOW = 64, 31, 127
+(SSVP_TRACE_GATHER, SSVP_TRACE_APERTURE, SSVP_TRACE_FRUSTUM, SSVP_TRACE_SUPERRES, SSVP_TRACE_EXTRACT, SSVP_TRACE_INFER,
+ SSVP_TRACE_TRAIN, SSVP_TRACE_ADAM, SSVP_TRACE_BATCH, SSVP_TRACE_LOAD, SSVP_TRACE_MASK, SSVP_TRACE_KINDS) = range(12)
 
 
 class SsvpError(RuntimeError):
@@ -97,6 +99,10 @@ def _load():
         "ssvp_train": (i, [vp, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp), i,
                            ctypes.POINTER(ssvp_train_config), vp]),
         "ssvp_mlp_grad": (i, [vp, P, i, vp, i, vp, vp]),
+        "ssvp_trace_enable": (i, [vp, i]),
+        "ssvp_trace_read": (i, [vp, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+        "ssvp_trace_kind_name": (ctypes.c_char_p, [i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -216,6 +222,23 @@ def ssvp_read_stats(ctx):
     e, a, w = ctypes.c_ulonglong(), ctypes.c_ulonglong(), ctypes.c_double()
     _check(ctx, lib.ssvp_read_stats(ctx, ctypes.byref(e), ctypes.byref(a), ctypes.byref(w)))
     return int(e.value), int(a.value), float(w.value)
+
+
+def ssvp_trace_enable(ctx, on: bool = True) -> None:
+    _check(ctx, lib.ssvp_trace_enable(ctx, int(bool(on))))
+
+
+def ssvp_trace_read(ctx) -> dict:
+    """-> {kind name: (launches, summed device ms)} of the traced work since the last read."""
+    n = SSVP_TRACE_KINDS
+    kind, launches, ms = (ctypes.c_int * n)(), (ctypes.c_int * n)(), (ctypes.c_double * n)()
+    got = ctypes.c_int()
+    _check(ctx, lib.ssvp_trace_read(ctx, n, kind, launches, ms, ctypes.byref(got)))
+    return {ssvp_trace_kind_name(kind[j]): (int(launches[j]), float(ms[j])) for j in range(got.value)}
+
+
+def ssvp_trace_kind_name(kind: int) -> str:
+    return lib.ssvp_trace_kind_name(kind).decode()
 
 
 def ssvp_clip_median_depth(ctx, clip_id: int) -> float:

@@ -90,6 +90,14 @@ struct ssvp_ctx {
     // Eq. 10 shutter function (host copy) and its per-slot log2 weights on the device
     std::vector<float> shutter;
     float *d_shutter_log2 = nullptr;
+    // kernel timing (ssvp_trace_enable): the event pairs of traced launches, and spare events
+    struct TraceRec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    bool trace_on = false;
+    std::vector<TraceRec> trace_pending;
+    std::vector<cudaEvent_t> trace_free;
 };
 
 struct ssvp_plan {
@@ -131,6 +139,50 @@ int cuda_fail(ssvp_ctx *c, cudaError_t e, const char *what) {
         cudaError_t e_ = (call);                         \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
     } while (0)
+
+cudaEvent_t trace_event(ssvp_ctx *ctx) {
+    if (!ctx->trace_free.empty()) {
+        cudaEvent_t e = ctx->trace_free.back();
+        ctx->trace_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// While tracing is on, brackets the work queued on stream s during its lifetime with a pair of
+// timing events, recorded under `kind` (never used on a capturing stream)
+struct TraceScope {
+    ssvp_ctx *ctx;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    TraceScope(ssvp_ctx *c, int k, cudaStream_t st) : ctx(c), kind(k), s(st) {
+        if (!c->trace_on || !(a = trace_event(c))) return;
+        if (cudaEventRecord(a, s) != cudaSuccess) {
+            cudaGetLastError();
+            c->trace_free.push_back(a);
+            a = nullptr;
+        }
+    }
+    ~TraceScope() {
+        if (!a) return;
+        cudaEvent_t b = trace_event(ctx);
+        if (b && cudaEventRecord(b, s) == cudaSuccess) {
+            ctx->trace_pending.push_back({kind, a, b});
+            return;
+        }
+        cudaGetLastError();
+        ctx->trace_free.push_back(a);
+        if (b) ctx->trace_free.push_back(b);
+    }
+    TraceScope(const TraceScope &) = delete;
+    TraceScope &operator=(const TraceScope &) = delete;
+};
 
 void free_clip(Clip &c) {
     if (c.p.depth) cudaFree(c.p.depth);
@@ -494,6 +546,7 @@ int extract_samples(ssvp_ctx *ctx, const ssvp_params &p, int clip_id, int O, int
     a.sets = ctx->l_sets;
     a.stat_counts = ctx->stat_counts;
     a.stat_sumw = ctx->stat_sumw;
+    TraceScope ts(ctx, SSVP_TRACE_EXTRACT, ctx->stream);
     CK(ssvp::launch_gather(a, ctx->stream), "gather kernel (learned samples)");
     return SSVP_OK;
 }
@@ -605,6 +658,11 @@ void ssvp_destroy(ssvp_ctx *ctx) {
     free_sets(ctx->l_sets);
     for (void *q : {(void *)ctx->mlp_buf, (void *)ctx->mlp_w1, (void *)ctx->l_loss, (void *)ctx->l_batch})
         if (q) cudaFree(q);
+    for (auto &r : ctx->trace_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : ctx->trace_free) cudaEventDestroy(e);
     if (ctx->ev_load_in) cudaEventDestroy(ctx->ev_load_in);
     if (ctx->ev_load_out) cudaEventDestroy(ctx->ev_load_out);
     if (ctx->load_stream) cudaStreamDestroy(ctx->load_stream);
@@ -668,11 +726,13 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
     cudaStream_t ls = ctx->load_stream;
     CK(cudaEventRecord(ctx->ev_load_in, ctx->stream), "cudaEventRecord");
     CK(cudaStreamWaitEvent(ls, ctx->ev_load_in, 0), "cudaStreamWaitEvent");
-    // padding and invalid depth: NaN (all bits set); colour 0; output 0.  A reload keeps the
-    // padding of the planes it reuses (the packing rewrites every pixel inside them)
-    if (!reuse) {
-        CK(cudaMemsetAsync(p.depth, 0xff, nplane * sizeof(float), ls), "cudaMemsetAsync");
-        CK(cudaMemsetAsync(p.colour, 0, nplane * texel, ls), "cudaMemsetAsync");
+    {
+        TraceScope ts(ctx, SSVP_TRACE_LOAD, ls);
+        // padding and invalid depth: NaN (all bits set); colour 0; output 0.  A reload keeps the
+        // padding of the planes it reuses (the packing rewrites every pixel inside them)
+        if (!reuse) {
+            CK(cudaMemsetAsync(p.depth, 0xff, nplane * sizeof(float), ls), "cudaMemsetAsync");
+            CK(cudaMemsetAsync(p.colour, 0, nplane * texel, ls), "cudaMemsetAsync");
     }
     CK(cudaMemsetAsync(p.out, 0, nout * sizeof(float), ls), "cudaMemsetAsync");
     const size_t frame_px = (size_t)W * H;
@@ -710,6 +770,7 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
     CK(ssvp::launch_median(p, ctx->median_scratch, ls), "median kernels");
     CK(ssvp::launch_zrange(p, ls), "depth range kernel");
     CK(ssvp::launch_grad_sum(p, ls), "gradient sum kernels");
+    }
     // everything queued on the context's stream from here on runs after the load
     CK(cudaEventRecord(ctx->ev_load_out, ls), "cudaEventRecord");
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_load_out, 0), "cudaStreamWaitEvent");
@@ -825,13 +886,15 @@ int ssvp_append_frames(ssvp_ctx *ctx, int clip_id, int n, const float *rgb, cons
     q.grad_sum = sp.grad_sum;
     q.grad_log2 = sp.grad_log2;
     q.grad_partial = sp.grad_partial;
-    const size_t keep = (size_t)(F - n) * (size_t)p.fstride;
-    if (keep) {
-        CK(cudaMemcpyAsync(q.depth, p.depth + (size_t)n * p.fstride, keep * sizeof(float), cudaMemcpyDeviceToDevice, ls),
-           "cudaMemcpyAsync (window)");
-        CK(cudaMemcpyAsync(q.colour, (const char *)p.colour + (size_t)n * p.fstride * texel, keep * texel,
-                           cudaMemcpyDeviceToDevice, ls),
-           "cudaMemcpyAsync (window)");
+    {
+        TraceScope ts(ctx, SSVP_TRACE_LOAD, ls);
+        const size_t keep = (size_t)(F - n) * (size_t)p.fstride;
+        if (keep) {
+            CK(cudaMemcpyAsync(q.depth, p.depth + (size_t)n * p.fstride, keep * sizeof(float), cudaMemcpyDeviceToDevice, ls),
+               "cudaMemcpyAsync (window)");
+            CK(cudaMemcpyAsync(q.colour, (const char *)p.colour + (size_t)n * p.fstride * texel, keep * texel,
+                               cudaMemcpyDeviceToDevice, ls),
+               "cudaMemcpyAsync (window)");
     }
     const size_t frame_px = (size_t)W * H;
     if (mem_kind == SSVP_MEM_DEVICE) {
@@ -857,6 +920,7 @@ int ssvp_append_frames(ssvp_ctx *ctx, int clip_id, int n, const float *rgb, cons
     CK(ssvp::launch_median(q, ctx->median_scratch, ls), "median kernels");
     CK(ssvp::launch_zrange(q, ls), "depth range kernel");
     CK(ssvp::launch_grad_sum(q, ls), "gradient sum kernels");
+    }
     CK(cudaEventRecord(ctx->ev_load_out, ls), "cudaEventRecord");
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_load_out, 0), "cudaStreamWaitEvent");
     // the spare window becomes current; the cameras slide with the frames
@@ -921,6 +985,7 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
                 m.tau = p.conf_threshold;
                 m.out = c.p.out;
                 m.skip_mma = p.test_skip_mma;
+                TraceScope ts(ctx, SSVP_TRACE_INFER, ctx->stream);
                 CK(ssvp::launch_mlp_infer_tc(m, ctx->d_kerr, ctx->stream), "mlp inference kernel");
             }
         }
@@ -1009,6 +1074,9 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         a.frustum_l = p.frustum_l;
         a.near_plane = p.near_plane;
         a.far_plane = p.far_plane;
+        TraceScope ts(ctx, frustum ? SSVP_TRACE_FRUSTUM : p.mode == SSVP_MODE_APERTURE ? SSVP_TRACE_APERTURE
+                                                                                       : SSVP_TRACE_GATHER,
+                      ctx->stream);
         if (frustum) CK(ssvp::launch_frustum(a, ctx->stream), "frustum kernel");
         else if (p.mode == SSVP_MODE_APERTURE) CK(ssvp::launch_aperture(a, ctx->stream), "aperture kernel");
         else CK(ssvp::launch_gather(a, ctx->stream), "gather kernel");
@@ -1088,6 +1156,7 @@ int ssvp_superres(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, int sca
     a.pixel_stats = (int32_t *)p.pixel_stats_out;
     a.stat_counts = ctx->stat_counts;
     a.stat_sumw = ctx->stat_sumw;
+    TraceScope ts(ctx, SSVP_TRACE_SUPERRES, ctx->stream);
     CK(ssvp::launch_frustum(a, ctx->stream), "super-resolution kernel");
     return SSVP_OK;
 }
@@ -1151,7 +1220,10 @@ int ssvp_mask_from_box(ssvp_ctx *ctx, int clip_id, const double *box) {
     double *d_cam = nullptr;
     CK(cudaMalloc(&d_cam, cam.size() * sizeof(double)), "cudaMalloc (cameras)");
     cudaError_t e = cudaMemcpyAsync(d_cam, cam.data(), cam.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = ssvp::launch_mask_box(c->p, d_cam, box, ctx->stream);
+    if (e == cudaSuccess) {
+        TraceScope ts(ctx, SSVP_TRACE_MASK, ctx->stream);
+        e = ssvp::launch_mask_box(c->p, d_cam, box, ctx->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the table is freed next
     cudaFree(d_cam);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "mask from box");
@@ -1403,6 +1475,7 @@ int ssvp_plan_launch(ssvp_plan *plan) {
             return fail(ctx, SSVP_ENOCLIP, "clip %d was reloaded or unloaded after the plan was made", plan->clip_ids[i]);
     }
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    TraceScope ts(ctx, SSVP_TRACE_BATCH, ctx->stream);
     CK(cudaGraphLaunch(plan->exec, ctx->stream), "cudaGraphLaunch");
     return SSVP_OK;
 }
@@ -1516,7 +1589,10 @@ int ssvp_mlp_grad(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, const i
     m.clean = clean;
     m.bce_w = 0.1f;
     m.grad = ctx->mlp.grad;
-    CK(ssvp::launch_mlp_train_tc(m, ctx->d_kerr, ctx->stream), "mlp train kernel");
+    {
+        TraceScope ts(ctx, SSVP_TRACE_TRAIN, ctx->stream);
+        CK(ssvp::launch_mlp_train_tc(m, ctx->d_kerr, ctx->stream), "mlp train kernel");
+    }
     CK(cudaMemcpyAsync(grad_out, ctx->mlp.grad, (ssvp::kMlpParams + 1) * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
        "cudaMemcpyAsync");
     return ssvp_sync(ctx);  // also reports a timed-out tensor-core wait
@@ -1589,8 +1665,14 @@ int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, co
         m.clean = clean[ci];
         m.bce_w = cfg->bce_weight;
         m.grad = ctx->mlp.grad;
-        CK(ssvp::launch_mlp_train_tc(m, ctx->d_kerr, ctx->stream), "mlp train kernel");
-        CK(ssvp::launch_adam(ctx->mlp, cfg->lr, ++ctx->mlp_step, ctx->stream), "adam kernel");
+        {
+            TraceScope ts(ctx, SSVP_TRACE_TRAIN, ctx->stream);
+            CK(ssvp::launch_mlp_train_tc(m, ctx->d_kerr, ctx->stream), "mlp train kernel");
+        }
+        {
+            TraceScope ts(ctx, SSVP_TRACE_ADAM, ctx->stream);
+            CK(ssvp::launch_adam(ctx->mlp, cfg->lr, ++ctx->mlp_step, ctx->stream), "adam kernel");
+        }
         CK(cudaMemcpyAsync(ctx->l_loss + step, ctx->mlp.grad + ssvp::kMlpParams, sizeof(float), cudaMemcpyDeviceToDevice,
                            ctx->stream), "cudaMemcpyAsync");
     }
@@ -1598,6 +1680,53 @@ int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, co
         CK(cudaMemcpyAsync(loss_out, ctx->l_loss, cfg->steps * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
            "cudaMemcpyAsync");
     return ssvp_sync(ctx);  // also reports a timed-out tensor-core wait
+}
+
+int ssvp_trace_enable(ssvp_ctx *ctx, int on) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    ctx->trace_on = on != 0;
+    return SSVP_OK;
+}
+
+int ssvp_trace_read(ssvp_ctx *ctx, int max_kinds, int *kind, int *launches, double *ms, int *n_kinds) {
+    if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
+    if (max_kinds < 0) return fail(ctx, SSVP_EINVAL, "max_kinds %d < 0", max_kinds);
+    if (n_kinds) *n_kinds = 0;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int cnt[SSVP_TRACE_KINDS] = {};
+    double tot[SSVP_TRACE_KINDS] = {};
+    cudaError_t err = cudaSuccess;
+    for (auto &r : ctx->trace_pending) {
+        float t = 0.0f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e == cudaSuccess) {
+            ++cnt[r.kind];
+            tot[r.kind] += t;
+        } else if (err == cudaSuccess) {
+            err = e;
+        }
+        ctx->trace_free.push_back(r.a);
+        ctx->trace_free.push_back(r.b);
+    }
+    ctx->trace_pending.clear();
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "trace events");
+    int w = 0;
+    for (int k = 0; k < SSVP_TRACE_KINDS && w < max_kinds; ++k) {
+        if (!cnt[k]) continue;
+        if (kind) kind[w] = k;
+        if (launches) launches[w] = cnt[k];
+        if (ms) ms[w] = tot[k];
+        ++w;
+    }
+    if (n_kinds) *n_kinds = w;
+    return SSVP_OK;
+}
+
+const char *ssvp_trace_kind_name(int kind) {
+    static const char *const names[SSVP_TRACE_KINDS] = {"gather", "aperture", "frustum", "superres", "extract", "infer",
+                                                        "train", "adam", "batch", "load", "mask"};
+    return kind >= 0 && kind < SSVP_TRACE_KINDS ? names[kind] : "";
 }
 
 int ssvp_sync(ssvp_ctx *ctx) {

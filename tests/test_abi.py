@@ -63,6 +63,8 @@ def test_null_context_is_rejected(ss):
     assert lib.ssvp_read_output(None, 0, 0, 1, None, 0) == ss.SSVP_EINVAL
     assert lib.ssvp_sync(None) == ss.SSVP_EINVAL
     assert lib.ssvp_read_stats(None, None, None, None) == ss.SSVP_EINVAL
+    assert lib.ssvp_trace_enable(None, 1) == ss.SSVP_EINVAL
+    assert lib.ssvp_trace_read(None, 4, None, None, None, None) == ss.SSVP_EINVAL
     assert "NULL" in ss.ssvp_last_error(None)
     lib.ssvp_destroy(None)  # no-op
 
@@ -85,3 +87,13 @@ def test_noalloc_median_refuses_host_arrays_before_any_launch(ss):
         ss.ssvp_median_depth_noalloc(np.ones(8, np.float32), 8, np.zeros(1, np.float32))
     with pytest.raises(TypeError):
         ss.ssvp_median_depth_noalloc(torch.ones(8), 8, torch.zeros(1))
+
+
+def test_trace_kinds_have_names(ss):
+    """Every trace kind of the header has a distinct short name; unknown kinds give ""."""
+    names = [ss.ssvp_trace_kind_name(k) for k in range(ss.SSVP_TRACE_KINDS)]
+    assert names == ["gather", "aperture", "frustum", "superres", "extract", "infer", "train", "adam", "batch", "load",
+                     "mask"]
+    assert ss.ssvp_trace_kind_name(-1) == "" and ss.ssvp_trace_kind_name(ss.SSVP_TRACE_KINDS) == ""
+    text = open(HEADER).read()
+    assert f"SSVP_TRACE_KINDS = {ss.SSVP_TRACE_KINDS}" in text
