@@ -429,6 +429,8 @@ def run_batch(args, ss, torch, dev, stream, world, rank):
         ss.ssvp_read_output(ctx, i, 0, c.F, o)
         ss.ssvp_sync(ctx)
         on = o.cpu().numpy()
+        if i == 0:
+            out0 = on[c.F // 2]  # the middle output frame of the first clip, for the oracle below
         mse = lambda a_, b_: float(np.mean((a_.astype(np.float64) - b_) ** 2))
         psnr_out.append(10 * np.log10(1 / mse(on, c.clean)))
         psnr_in.append(10 * np.log10(1 / mse(c.rgb, c.clean)))
@@ -508,6 +510,38 @@ def run_batch(args, ss, torch, dev, stream, world, rank):
                 "d2h_bytes_per_step": sum(c.clean.nbytes for c in clips), "ms_per_step": e2e_ms},
         "clocks": clk_summary,
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on a centred crop of the first clip's middle frame, grown to about 8 s: on the
+        # FP16-rounded colours the plan stores (its arithmetic error) and on the FP32 colours (its
+        # total error, FP16 storage included)
+        import oracle
+        c0, O0 = clips[0], clips[0].F // 2
+        rgb16 = c0.rgb.astype(np.float16).astype(np.float32)
+        c16 = synth.Clip(c0.W, c0.H, c0.F, c0.K, c0.w2c, c0.w2c_true, rgb16, c0.depth, c0.clean, c0.depth_true)
+        prm = oracle.default_params(c0.depth, k=K_WIN, T=T, radius_rel=RADIUS_REL)
+        side = 16
+        while True:
+            crop = ((c0.W - side) // 2, (c0.H - side) // 2, side, side)
+            t0 = time.perf_counter()
+            r16 = oracle.gather_filter(oracle.ClipView.of(c16), prm, O0, crop=crop)
+            dt = time.perf_counter() - t0
+            if dt > 8.0 or 2 * side > min(c0.W, c0.H):
+                break
+            side *= 2
+        r32 = oracle.gather_filter(oracle.ClipView.of(c0), prm, O0, crop=crop)
+        x0, y0, cw, ch = crop
+        g = out0[y0:y0 + ch, x0:x0 + cw].astype(np.float64)
+        d16, d32 = np.abs(g - r16.rgb).max(-1), np.abs(g - r32.rgb).max(-1)
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        line["cpu_baseline"] = {"value": side * side / dt / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{side}x{side} crop of frame {O0} of the {c0.W}x{c0.H}x{c0.F} clip, "
+                                          f"FP16-rounded colours ({dt:.1f} s)"}
+        line["max_abs_vs_oracle"] = {"value": float(d16.max()), "p999": float(np.quantile(d16, 0.999)),
+                                     "frac_above_1e-3": float((d16 > 1e-3).mean()), "pixels": int(d16.size),
+                                     "total_vs_fp32_colour_oracle": {"value": float(d32.max()),
+                                                                     "p999": float(np.quantile(d32, 0.999))},
+                                     "note": "the plan's output against the oracle on the FP16-rounded colours "
+                                             "(arithmetic) and on the FP32 colours (total); all pixels of the crop"}
     ss.ssvp_destroy(ctx)
     return line
 
