@@ -1061,7 +1061,7 @@ def main():
     rgb_h = torch.from_numpy(clip.rgb).pin_memory()
     dep_h = torch.from_numpy(clip.depth).pin_memory()
     out_h = torch.empty((N_OUT, H, W, 3), dtype=torch.float32).pin_memory()
-    e2e_steps = max(2, min(args.steps, 10))
+    e2e_steps = max(2, min(2 * args.steps, 20))  # the pipeline fill (one unoverlapped load) amortised over 20 steps
 
     # Steps alternate between two contexts on two streams (double buffering, as a streaming
     # deployment would): step i + 1's upload and gather are queued before step i's output is read
