@@ -679,30 +679,50 @@ def run_learned(args, ss, torch, dev, stream, world, rank):
         "clocks": clk.summary(),
     }
     # end to end through the C ABI with host buffers: every step uploads the clip from pinned host
-    # memory, runs the learned filter and reads the output frames back (one context, in order)
+    # memory, runs the learned filter and reads the output frames back; steps alternate between two
+    # contexts (the second holds the same network) on two streams, step i + 1 queued before step i
+    # is read back, as in the default workload
     rgb_h = torch.from_numpy(clip.rgb).pin_memory()
     dep_h = torch.from_numpy(clip.depth).pin_memory()
-    out_h = torch.empty((N_OUT, H, W, 3), dtype=torch.float32).pin_memory()
+    stream2 = torch.cuda.Stream(dev)
+    ctx2 = ss.ssvp_create(local, stream2)
+    ss.ssvp_set_mlp(ctx2, *ss.ssvp_get_mlp(ctx))
+    ctxs = (ctx, ctx2)
+    outs = [torch.empty((N_OUT, H, W, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
 
-    def e2e_step():
-        ss.ssvp_load_clip(ctx, 0, W, H, F, rgb_h, dep_h, ss.SSVP_MEM_HOST, 0)
-        ss.ssvp_set_cameras(ctx, 0, clip.K, 1, clip.w2c)
-        ss.ssvp_gather_filter(ctx, p, [0])
-        ss.ssvp_read_output(ctx, 0, O_BEGIN, O_BEGIN + N_OUT, out_h, ss.SSVP_MEM_HOST)
+    def issue(i):
+        cx = ctxs[i % 2]
+        ss.ssvp_load_clip(cx, 0, W, H, F, rgb_h, dep_h, ss.SSVP_MEM_HOST, 0)
+        ss.ssvp_set_cameras(cx, 0, clip.K, 1, clip.w2c)
+        ss.ssvp_gather_filter(cx, p, [0])
 
-    e2e_step()
-    n_e2e = max(2, min(args.steps, 5))
+    def read_back(i):
+        ss.ssvp_read_output(ctxs[i % 2], 0, O_BEGIN, O_BEGIN + N_OUT, outs[i % 2], ss.SSVP_MEM_HOST)
+
+    def e2e_run(n):
+        issue(0)
+        for i in range(1, n):
+            issue(i)
+            read_back(i - 1)
+        read_back(n - 1)
+
+    e2e_run(2)
+    n_e2e = max(2, min(2 * args.steps, 20))
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for _ in range(n_e2e):
-        e2e_step()
+    stream2.wait_event(a)
+    e2e_run(n_e2e)
+    done2 = torch.cuda.Event()
+    done2.record(stream2)
+    stream.wait_event(done2)
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(a.elapsed_time(b) / n_e2e, world, dev)
+    ss.ssvp_destroy(ctx2)
     line["e2e"] = {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": clip.rgb.nbytes +
-                   clip.depth.nbytes, "d2h_bytes_per_step": out_h.numel() * 4, "ms_per_step": e2e_ms,
-                   "pipelining": "none (one context; each step's read-back waits for its filter)"}
+                   clip.depth.nbytes, "d2h_bytes_per_step": outs[0].numel() * 4, "ms_per_step": e2e_ms,
+                   "pipelining": "two contexts on two streams, step i + 1 queued before step i is read back"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle's learned filter (capped sets and features in C, the BF16-rounded network per
         # pixel) on a centred crop of the first output frame, grown to about 10 s
@@ -1067,15 +1087,14 @@ def main():
     # deployment would): step i + 1's upload and gather are queued before step i's output is read
     # back to the host, so the copies of one step overlap the kernels of the other.  Every step
     # still uploads its own inputs and reads back its own result inside the timed region.
-    # Inpainting re-creates its mask per step, which reallocates: it runs the steps one after
-    # another on one context.
-    pipelined = MODE not in (8, 9)
-    stream2 = torch.cuda.Stream(dev) if pipelined else stream
-    ctx2 = ss.ssvp_create(local, stream2) if pipelined else ctx
-    if pipelined and MODE == 6:  # the context's own state: the Eq. 10 shutter table
+    # Inpainting and semi-transparency also compute the step's mask from the box (a reload with the
+    # same shape keeps the mask's memory).
+    stream2 = torch.cuda.Stream(dev)
+    ctx2 = ss.ssvp_create(local, stream2)
+    if MODE == 6:  # the context's own state: the Eq. 10 shutter table
         ss.ssvp_set_shutter(ctx2, _shutter_xi(), T)
-    ctxs, streams = (ctx, ctx2), (stream, stream2)
-    out_hs = (out_h, torch.empty_like(out_h).pin_memory() if pipelined else out_h)
+    ctxs = (ctx, ctx2)
+    out_hs = (out_h, torch.empty_like(out_h).pin_memory())
 
     def issue(i):
         cx = ctxs[i % 2]
@@ -1091,12 +1110,8 @@ def main():
     def e2e_run(n):
         issue(0)
         for i in range(1, n):
-            if pipelined:
-                issue(i)
-                read_back(i - 1)
-            else:
-                read_back(i - 1)
-                issue(i)
+            issue(i)
+            read_back(i - 1)
         read_back(n - 1)
 
     e2e_run(2)  # both contexts hold the clip's planes: later reloads reuse them
@@ -1105,26 +1120,23 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    if pipelined:
-        stream2.wait_event(e0)
+    stream2.wait_event(e0)
     e2e_run(e2e_steps)
-    if pipelined:
-        done2 = torch.cuda.Event()
-        done2.record(stream2)
-        stream.wait_event(done2)
+    done2 = torch.cuda.Event()
+    done2.record(stream2)
+    stream.wait_event(done2)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
-    if pipelined:
-        ss.ssvp_destroy(ctx2)
+    ss.ssvp_destroy(ctx2)
     h2d = clip.rgb.nbytes + clip.depth.nbytes
     d2h = out_h.numel() * 4
     frames_per_chunk = max(1, min(F, (4 << 30) // (W * H * 16)))
     e2e_launches = -(-F // frames_per_chunk) + 6 + 1 + 2 + 1  # packs, median passes, depth range, gradient sums, gather
+    e2e_launches += 1 if MODE in (8, 9) else 0  # the mask from the box
     e2e_full = {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "gpu_launches_per_step": e2e_launches,
-                "pipelining": "two contexts on two streams, step i + 1 queued before step i is read back"
-                              if pipelined else "none",
+                "pipelining": "two contexts on two streams, step i + 1 queued before step i is read back",
                 "inputs": "the whole clip uploaded every step (ssvp_load_clip)"}
     e2e_stream = None
     if MODE in (0, 1, 5, 6) and not args.no_stream:

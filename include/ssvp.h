@@ -175,7 +175,8 @@ int ssvp_superres(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, int sca
  * w = exp(-|c_ref - c|^2 / (2 sigma_rgb^2)) over the unmasked samples (masked ones weigh 0,
  * Eq. 9), each step's result being the next step's c_ref; a step whose weights are all 0 keeps
  * its reference, an empty S(p) keeps the input colour.  Unmasked pixels keep their input colour.
- * The paper uses sigma_rgb = 55 on a 0-255 scale.  The mask lives until the clip is unloaded.
+ * The paper uses sigma_rgb = 55 on a 0-255 scale.  The mask lives until the clip is unloaded or
+ * reloaded with another shape or colour format (a reload with the same ones keeps it).
  *
  * SSVP_MODE_SEMI (semi-transparency, same gather and mask) makes the masked region see-through
  * instead: its second step also gives every sample s of S(p), masked or not, the Eq. 4 weight
@@ -190,7 +191,8 @@ int ssvp_set_mask(ssvp_ctx *ctx, int clip_id, const uint8_t *mask, int mem_kind)
  * The same mask from a scene-space region (the paper's alternative to painted masks): box =
  * {xmin, ymin, zmin, xmax, ymax, zmax} in world coordinates (inclusive).  A pixel of any frame is
  * masked when its depth, unprojected with its frame's camera (FP64), gives a world point inside
- * the box; invalid depths are not masked.  Needs the clip's cameras; waits for the stream.
+ * the box; invalid depths are not masked.  Needs the clip's cameras; queued on the stream (the
+ * cameras are copied before the call returns).
  */
 int ssvp_mask_from_box(ssvp_ctx *ctx, int clip_id, const double *box);
 
@@ -254,8 +256,9 @@ int ssvp_set_stream(ssvp_ctx *ctx, void *cuda_stream);
  * work queued after the call sees the new clip.  (Its kernels are short: at high priority they
  * overlap a long gather another context runs on another stream.)  Host inputs up to 4 GB go to
  * the device in one copy through a staging buffer the context keeps.  Reloading
- * an id with the same W, H, F and colour_fmt (and no inpainting mask set) reuses its device
- * planes without allocating; work already queued on the stream still sees the old contents.
+ * an id with the same W, H, F and colour_fmt reuses its device planes (and keeps its inpainting
+ * mask, if one is set) without allocating; work already queued on the stream still sees the old
+ * contents.
  * Any reload invalidates batched plans that include the id.
  */
 int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float *rgb, const float *depth,

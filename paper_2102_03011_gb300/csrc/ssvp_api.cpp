@@ -98,6 +98,9 @@ struct ssvp_ctx {
     bool trace_on = false;
     std::vector<TraceRec> trace_pending;
     std::vector<cudaEvent_t> trace_free;
+    // ssvp_mask_from_box: the per-frame cameras (K^-1, R, t; 21 doubles a frame) on the device
+    double *mask_cam = nullptr;
+    size_t mask_cam_cap = 0;  // doubles
 };
 
 struct ssvp_plan {
@@ -655,6 +658,7 @@ void ssvp_destroy(ssvp_ctx *ctx) {
     if (ctx->geom) cudaFree(ctx->geom);
     if (ctx->staging) cudaFree(ctx->staging);
     if (ctx->d_shutter_log2) cudaFree(ctx->d_shutter_log2);
+    if (ctx->mask_cam) cudaFree(ctx->mask_cam);
     free_sets(ctx->l_sets);
     for (void *q : {(void *)ctx->mlp_buf, (void *)ctx->mlp_w1, (void *)ctx->l_loss, (void *)ctx->l_batch})
         if (q) cudaFree(q);
@@ -689,10 +693,9 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
         return fail(ctx, SSVP_EINVAL, "bad colour_fmt %d", colour_fmt);
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     Clip &c = ctx->clips[clip_id];
-    // a reload with the same shape and format (and no inpainting mask) keeps the planes: the work
-    // queued on the context's stream that still reads them runs before the new upload
-    const bool reuse = c.loaded && c.p.W == W && c.p.H == H && c.p.F == F && c.p.colour_fmt == colour_fmt &&
-                       c.p.mask == nullptr;
+    // a reload with the same shape and format keeps the planes (and the inpainting mask, if one is
+    // set): the work queued on the context's stream that still reads them runs before the upload
+    const bool reuse = c.loaded && c.p.W == W && c.p.H == H && c.p.F == F && c.p.colour_fmt == colour_fmt;
     if (c.loaded && !reuse) {
         CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
         CK(cudaStreamSynchronize(ctx->load_stream), "cudaStreamSynchronize");
@@ -837,7 +840,8 @@ int ssvp_append_frames(ssvp_ctx *ctx, int clip_id, int n, const float *rgb, cons
     Clip &c = ctx->clips[clip_id];
     if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
     if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_id);
-    if (c.p.mask) return fail(ctx, SSVP_EINVAL, "clip %d has an inpainting mask: reload it to append frames", clip_id);
+    if (c.p.mask)
+        return fail(ctx, SSVP_EINVAL, "clip %d has an inpainting mask: unload and load it to append frames", clip_id);
     const int W = c.p.W, H = c.p.H, F = c.p.F;
     if (n < 1 || n > F) return fail(ctx, SSVP_EINVAL, "n=%d must be in [1, %d] (the clip's frame count)", n, F);
     if (!rgb || !depth || !K || !w2c) return fail(ctx, SSVP_EINVAL, "rgb, depth, K and w2c must not be NULL");
@@ -1217,16 +1221,21 @@ int ssvp_mask_from_box(ssvp_ctx *ctx, int clip_id, const double *box) {
             o[18 + r] = w[4 * r + 3];
         }
     }
-    double *d_cam = nullptr;
-    CK(cudaMalloc(&d_cam, cam.size() * sizeof(double)), "cudaMalloc (cameras)");
-    cudaError_t e = cudaMemcpyAsync(d_cam, cam.data(), cam.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) {
-        TraceScope ts(ctx, SSVP_TRACE_MASK, ctx->stream);
-        e = ssvp::launch_mask_box(c->p, d_cam, box, ctx->stream);
+    // the camera table goes to a device buffer the context keeps: the next call's copy into it is
+    // queued after this call's kernel on the same stream (a pageable source is staged before the
+    // copy call returns)
+    if (ctx->mask_cam_cap < cam.size()) {
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        if (ctx->mask_cam) cudaFree(ctx->mask_cam);
+        ctx->mask_cam = nullptr;
+        ctx->mask_cam_cap = 0;
+        CK(cudaMalloc(&ctx->mask_cam, cam.size() * sizeof(double)), "cudaMalloc (cameras)");
+        ctx->mask_cam_cap = cam.size();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the table is freed next
-    cudaFree(d_cam);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "mask from box");
+    CK(cudaMemcpyAsync(ctx->mask_cam, cam.data(), cam.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
+       "cudaMemcpyAsync (cameras)");
+    TraceScope ts(ctx, SSVP_TRACE_MASK, ctx->stream);
+    CK(ssvp::launch_mask_box(c->p, ctx->mask_cam, box, ctx->stream), "mask from box");
     return SSVP_OK;
 }
 

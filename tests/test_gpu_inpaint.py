@@ -153,3 +153,24 @@ def test_semitransparency_of_a_fully_masked_frame_is_the_eq4_frustum_filter(sess
     compare_frustum(g, o, masked)
     f = run_frustum(sess, 6, 3, crop=(5, 3, 41, 29), half_window=3, sigma_rgb=SEMI_SIGMA_RGB, sigma_xyz=sx)
     assert np.abs(g.rgb - f.rgb).max() <= 1e-5
+
+
+def test_reload_keeps_the_mask_and_box_masks_queue_without_waiting(sess):
+    """A reload with the same shape keeps the mask (and its memory); masks from two boxes queued
+    back to back, each followed by a gather, give each gather its own mask."""
+    c = synth.make_clip("exact_const", 96, 54, 9, seed=0)
+    sess.load(7, c)
+    sess.ss.ssvp_mask_from_box(sess.ctx, 7, BOX)
+    want = oracle.mask_from_box(oracle.ClipView.of(c), BOX)
+    sess.load(7, c)  # same shape and format: planes and mask kept
+    np.testing.assert_array_equal(sess.ss.ssvp_read_mask(sess.ctx, 7, c.F, c.H, c.W), want)
+    g1, o1, masked = _both(sess, c, 7, want, 4, 4)
+    assert masked.sum() > 20
+    s = compare_frustum(g1, o1, masked)
+    assert s["excluded"] == 0
+    box2 = (-10.0, -10.0, 0.0, 10.0, 10.0, 100.0)  # everything with a valid depth
+    want2 = oracle.mask_from_box(oracle.ClipView.of(c), box2)
+    assert want2.sum() > want.sum()
+    sess.ss.ssvp_mask_from_box(sess.ctx, 7, BOX)
+    sess.ss.ssvp_mask_from_box(sess.ctx, 7, box2)
+    np.testing.assert_array_equal(sess.ss.ssvp_read_mask(sess.ctx, 7, c.F, c.H, c.W), want2)
