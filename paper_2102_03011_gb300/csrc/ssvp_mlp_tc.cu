@@ -4,7 +4,7 @@
 // One CTA of 128 threads takes two pixels at a time: their 2 x 64 capped samples are the 128 rows
 // of the layer-1 product.  While layer 2 of one pair runs, the threads build the next pair's
 // features; while its layer 1 runs, they finish the previous pair and load the records of the
-// next.  Seven CTAs share an SM (64 tensor-memory columns each), so that other CTAs' warps issue
+// next.  Eight CTAs share an SM (64 tensor-memory columns each), so that other CTAs' warps issue
 // while one waits for its products.  Each thread owns one row (one sample):
 //   1. it builds the sample's 16 BF16 features and stores them into shared memory in the
 //      tensor cores' K-major core-matrix layout (8 rows x 16 bytes per core matrix);
@@ -13,8 +13,10 @@
 //      carries 1.0 and W1's column 15 b1's leading BF16 part, and a second MMA with a constant
 //      operand adds b1's two lower BF16 parts (hi + mid + lo represent the FP32 b1 exactly);
 //   3. each thread reads its row of D1 back (tcgen05.ld), applies the ReLU and rounds to BF16 in
-//      one conversion, and stores the row as layer 2's A operand;
-//   4. four tcgen05.mma (K = 16 each): D2 (128 x 16, columns 0 and 1 used) = H W2^T;
+//      one conversion, and writes the row back into tensor memory (tcgen05.st) as layer 2's A
+//      operand: H's 64 BF16 values take D1's first 32 columns, two to a column;
+//   4. four tcgen05.mma with A in tensor memory (K = 16 each): D2 (128 x 16 in the columns after
+//      H, columns 0 and 1 used) = H W2^T;
 //   5. each thread reads (z_w, z_c) of its row, adds b2, and forms softplus / sigmoid; the two
 //      warps of each pixel reduce the weighted sums.
 // BF16 operands, FP32 accumulation, h rounded to BF16 before layer 2 (the training kernel below
@@ -30,23 +32,22 @@ namespace {
 
 constexpr int kS = 64, kF = 16, kH = 64;
 constexpr int kTcThreads = 128;   // one sample row per thread, two pixels per CTA
-constexpr unsigned kTmemCols = 64;  // D1; D2 reuses its first 16 columns
-constexpr int kTcCtasPerSm = 7;
+constexpr unsigned kTmemCols = 64;  // D1; then H in its first 32 columns and D2 in the next 16
+constexpr unsigned kColD2 = 32;
+constexpr int kTcCtasPerSm = 8;
 // shared operands, K-major core matrices; core (i, j) of an R x K operand holds rows 8i..8i+7 and
 // K elements 8j..8j+7 at byte offset (i * K / 8 + j) * 128, row r of it at + 16 (r % 8).  One
-// buffer of each A operand: a pair's features are written after every thread has waited for the
-// previous pair's layer 1, and its H after every thread has waited for the previous layer 2.
+// feature buffer: a pair's features are written after every thread has waited for the previous
+// pair's layer 1.
 constexpr int kSmA1 = 0;        // features, 128 x 16
 constexpr int kSmB1 = 4096;     // W1, 64 x 16
-constexpr int kSmA2 = 6144;     // H, 128 x 64
-constexpr int kSmB2 = 22528;    // W2 padded to 16 rows, 16 x 64
-constexpr int kSmA0 = 24576;    // constant operand for the b1 residual: ones in K slots 0 and 1, 128 x 16
-constexpr int kSmB0 = 28672;    // b1's two lower BF16 parts in K slots 0 and 1, 64 x 16
-constexpr int kSmBytes = 30720;
-// dynamic shared memory per CTA: the operands, 30 KB.  At most seven CTAs fit on an SM (shared
-// memory: 7 x 32 KB with the static part and the per-CTA reserve; registers: 128 threads x 7 at
-// <= 72), all 1,064 in one wave on 152 SMs, and their 7 x 64 tensor-memory columns always fit in
-// the SM's 512
+constexpr int kSmB2 = 6144;     // W2 padded to 16 rows, 16 x 64
+constexpr int kSmA0 = 8192;     // constant operand for the b1 residual: ones in K slots 0 and 1, 128 x 16
+constexpr int kSmB0 = 12288;    // b1's two lower BF16 parts in K slots 0 and 1, 64 x 16
+constexpr int kSmBytes = 14336;
+// dynamic shared memory per CTA: the operands, 14 KB.  At most eight CTAs fit on an SM (registers:
+// 128 threads x 8 at <= 64), all 1,216 in one wave on 152 SMs, and their 8 x 64 tensor-memory
+// columns fit in the SM's 512
 constexpr int kSmRequest = kSmBytes;
 // a waiting thread suspends in try_wait for up to kWaitHintNs per poll; kWaitLimit polls (about
 // 1 s) before a wait counts as timed out
@@ -77,6 +78,23 @@ __device__ __forceinline__ void mma_tc(unsigned d_tmem, unsigned long long adesc
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
+
+// the same product with A (M x 16, BF16, two to a 32-bit column, row i in lane i) in tensor memory
+__device__ __forceinline__ void mma_tc_ta(unsigned d_tmem, unsigned a_tmem, unsigned long long bdesc, unsigned idesc,
+                                          int accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// 8 consecutive 32-bit columns of this thread's tensor-memory lane; the caller waits (tcgen05.wait::st)
+__device__ __forceinline__ void tmem_st8(unsigned taddr, const unsigned (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
 __device__ __forceinline__ void mma_commit(unsigned mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
@@ -259,8 +277,8 @@ __device__ __forceinline__ void load_row(const MlpArgs &m, int pair, int tid, Ro
 }
 
 // Iteration i of a CTA takes pixel pair blockIdx.x + i * gridDim.x.  The 64 tensor-memory
-// columns hold D1 of pair i, then D2 of pair i in their first 16: the threads read D2 of pair i - 1
-// (after building the features of pair i) before layer 1 of pair i is issued.
+// columns hold D1 of pair i, then its H (columns 0-31) and D2 (columns 32-47): the threads read D2
+// of pair i - 1 (after building the features of pair i) before layer 1 of pair i is issued.
 __device__ __forceinline__ void pair_sums(float zw, float zc, const PrevRow &pr, float b20, float b21, int s_row,
                                           int warp, int lane, float (*s_red)[5]) {
     float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sc = 0.f;
@@ -361,7 +379,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) mlp_infer_tc_kernel(
             ph2 ^= 1u;
             fence_after();
             float zw, zc;
-            tmem_ld2(tmem + lane_base, zw, zc);
+            tmem_ld2(tmem + kColD2 + lane_base, zw, zc);
             pair_sums(zw, zc, prev, b20, b21, s_row, warp, lane, s_red);
         }
         fence_async_smem();
@@ -385,38 +403,31 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) mlp_infer_tc_kernel(
         prev.pl[2] = cur.pl[2];
         // 4. the next pair's records, in flight during the waits below and the next features
         if (pair + (int)gridDim.x < n_pairs) load_row(m, pair + gridDim.x, tid, cur);
-        // 5. H = ReLU(D1 + b1) in BF16 as layer 2's A operand (the single A2 buffer is free: every
-        // thread has waited for the previous pair's layer 2), then layer 2
+        // 5. H = ReLU(D1 + b1) in BF16, written over D1's first 32 columns as layer 2's A operand,
+        // then layer 2 into the next 16 columns
         bad |= !mbar_wait(bar1, ph1);
         ph1 ^= 1u;
         fence_after();
-        {
-            unsigned char *A2 = sm + kSmA2;
-            // a quarter of the row (16 columns) at a time, to keep the registers for six CTAs per SM
+        // a quarter of the row (16 columns) at a time: quarter q's 8 packed columns go to columns
+        // 8q..8q+7, which this thread has read already (quarters 0 and 1)
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                unsigned v[16];
-                tmem_ld16_nowait(tmem + lane_base + 16u * qq, v);
-                tmem_wait_ld();
-                unsigned h[8];
+        for (int qq = 0; qq < 4; ++qq) {
+            unsigned v[16];
+            tmem_ld16_nowait(tmem + lane_base + 16u * qq, v);
+            tmem_wait_ld();
+            unsigned h[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    h[i] = relu_bf16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-#pragma unroll
-                for (int q = 0; q < 2; ++q)
-                    *reinterpret_cast<uint4 *>(A2 + core_off(tid, 2 * qq + q, 8)) =
-                        make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
-            }
+            for (int i = 0; i < 8; ++i) h[i] = relu_bf16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+            tmem_st8(tmem + lane_base + 8u * qq, h);
         }
-        fence_async_smem();
+        tmem_wait_st();
         fence_before();
         __syncthreads();
         if (tid == 0 && !m.skip_mma) {
             fence_after();
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-                mma_tc(tmem, smem_desc(sbase + kSmA2 + kk * 256, 128, 1024),
-                       smem_desc(sbase + kSmB2 + kk * 256, 128, 1024), id2, kk);
+                mma_tc_ta(tmem + kColD2, tmem + 8u * kk, smem_desc(sbase + kSmB2 + kk * 256, 128, 1024), id2, kk);
             mma_commit(bar2);
         }
         if (bad) s_bad = 1;
@@ -428,7 +439,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) mlp_infer_tc_kernel(
         ph2 ^= 1u;
         fence_after();
         float zw, zc;
-        tmem_ld2(tmem + lane_base, zw, zc);
+        tmem_ld2(tmem + kColD2 + lane_base, zw, zc);
         pair_sums(zw, zc, prev, b20, b21, s_row, warp, lane, s_red);
         __syncthreads();
         if (s_row == 32 && prev.px < m.n_px) pair_output(m, prev, warp - 1, s_red);
