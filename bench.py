@@ -1132,7 +1132,9 @@ def main():
     h2d = clip.rgb.nbytes + clip.depth.nbytes
     d2h = out_h.numel() * 4
     frames_per_chunk = max(1, min(F, (4 << 30) // (W * H * 16)))
-    e2e_launches = -(-F // frames_per_chunk) + 6 + 1 + 2 + 1  # packs, median passes, depth range, gradient sums, gather
+    e2e_launches = -(-F // frames_per_chunk) + 6 + 1  # packs, median passes, the gather
+    e2e_launches += 1 if MODE in (4, 7, 8, 9) else 0  # frame depth ranges (frustum gathers, after each load)
+    e2e_launches += 2 if MODE == 5 else 0  # Eq. 5 gradient sums (deblurring, after each load)
     e2e_launches += 1 if MODE in (8, 9) else 0  # the mask from the box
     e2e_full = {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "gpu_launches_per_step": e2e_launches,
@@ -1192,7 +1194,7 @@ def main():
         e2e_stream = {"value": world * mpix / (s_ms / 1e3), "unit": "Mpix/s",
                       "h2d_bytes_per_step": N_OUT * W * H * 16, "d2h_bytes_per_step": d2h, "ms_per_step": s_ms,
                       "gather_only_ms_same_window": g_ms, "added_ms_per_step": s_ms - g_ms,
-                      "gpu_launches_per_step": 1 + 6 + 1 + 2 + 1,  # pack, median passes, depth range, gradient sums, gather
+                      "gpu_launches_per_step": 1 + 6 + 1 + (2 if MODE == 5 else 0),  # pack, median passes, gather, Eq. 5 sums
                       "inputs": f"streaming: each step appends its {N_OUT} new frames (ssvp_append_frames) to the "
                                 f"{F}-frame window of a {video.F}-frame clip of the same scene family (a different "
                                 f"camera path from the benchmark clip's)"}

@@ -314,8 +314,10 @@ int ssvp_output_device_ptr(ssvp_ctx *ctx, int clip_id, void **dev_ptr);
  * (extraction, inference, training, Adam), mask and batched-plan launch the context queues is
  * bracketed by a pair of CUDA timing events on its stream and recorded under one of the kinds
  * below; so is the whole of each ssvp_load_clip / ssvp_append_frames (copies and kernels on the
- * load stream: one SSVP_TRACE_LOAD entry per call), and a batched plan's launch (one CUDA graph)
- * is one SSVP_TRACE_BATCH entry.  Not traced: the autotuner's trial launches, the expansion of
+ * load stream: one SSVP_TRACE_LOAD entry per call) and the per-frame values a call computes the
+ * first time it needs them after one (the frames' depth ranges for the frustum gathers, the Eq. 5
+ * gradient sums for deblurring and ssvp_frame_sharpness: one more SSVP_TRACE_LOAD entry), and a
+ * batched plan's launch (one CUDA graph) is one SSVP_TRACE_BATCH entry.  Not traced: the autotuner's trial launches, the expansion of
  * ssvp_learned_samples and the weight conversion of ssvp_set_mlp.  ssvp_trace_read waits for the
  * traced work; for each kind with launches since the last read, in increasing kind order and at
  * most max_kinds of them, it writes the kind, the launch count and the summed device time in

@@ -32,6 +32,9 @@ struct Clip {
     // append: every read of the spare window precedes it
     Planes spare{};
     cudaEvent_t ev_append = nullptr;
+    // per-frame values of the current window that only some calls need, computed on first use:
+    // the valid depth range of each frame (the frustum gathers) and the Eq. 5 gradient sums
+    bool zrange_ready = false, grad_ready = false;
 };
 
 // the arrays of one window of a clip (the rest of Planes, such as the output and the mask, is shared)
@@ -186,6 +189,33 @@ struct TraceScope {
     TraceScope(const TraceScope &) = delete;
     TraceScope &operator=(const TraceScope &) = delete;
 };
+
+// The per-frame values some calls need, the first time a call needs them for this window: like
+// the load's kernels, on the load stream of the device's highest priority (so that they start
+// as soon as SMs free up instead of queueing behind another context's gather), after the work
+// queued on the context's stream and before the work queued after them
+int ensure_frame_values(ssvp_ctx *ctx, Clip &c, bool zrange, bool grad) {
+    zrange = zrange && !c.zrange_ready;
+    grad = grad && !c.grad_ready;
+    if (!zrange && !grad) return SSVP_OK;
+    cudaStream_t ls = ctx->load_stream;
+    CK(cudaEventRecord(ctx->ev_load_in, ctx->stream), "cudaEventRecord");
+    CK(cudaStreamWaitEvent(ls, ctx->ev_load_in, 0), "cudaStreamWaitEvent");
+    {
+        TraceScope ts(ctx, SSVP_TRACE_LOAD, ls);
+        if (zrange) {
+            CK(ssvp::launch_zrange(c.p, ls), "depth range kernel");
+            c.zrange_ready = true;
+        }
+        if (grad) {
+            CK(ssvp::launch_grad_sum(c.p, ls), "gradient sum kernels");
+            c.grad_ready = true;
+        }
+    }
+    CK(cudaEventRecord(ctx->ev_load_out, ls), "cudaEventRecord");
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_load_out, 0), "cudaStreamWaitEvent");
+    return SSVP_OK;
+}
 
 void free_clip(Clip &c) {
     if (c.p.depth) cudaFree(c.p.depth);
@@ -736,44 +766,43 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
         if (!reuse) {
             CK(cudaMemsetAsync(p.depth, 0xff, nplane * sizeof(float), ls), "cudaMemsetAsync");
             CK(cudaMemsetAsync(p.colour, 0, nplane * texel, ls), "cudaMemsetAsync");
-    }
-    CK(cudaMemsetAsync(p.out, 0, nout * sizeof(float), ls), "cudaMemsetAsync");
-    const size_t frame_px = (size_t)W * H;
-    if (mem_kind == SSVP_MEM_DEVICE) {
-        CK(ssvp::launch_pack(rgb, depth, W, H, F, p, 0, ls), "pack kernel");
-    } else {
-        // stage the frames through a device buffer: the whole clip in one copy up to 4 GB (the
-        // copy engines then run without waiting for a pack kernel between chunks), larger clips
-        // in chunks of that size
-        const size_t per_frame = frame_px * 16;
-        int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)F, ((size_t)4 << 30) / per_frame));
-        const size_t need = per_frame * (size_t)chunk;
-        if (ctx->staging_bytes < need) {
-            CK(cudaStreamSynchronize(ls), "cudaStreamSynchronize");
-            if (ctx->staging) cudaFree(ctx->staging);
-            ctx->staging = nullptr;
-            ctx->staging_bytes = 0;
-            if ((e = cudaMalloc(&ctx->staging, need)) != cudaSuccess) {
-                free_clip(c);
-                return cuda_fail(ctx, e, "cudaMalloc (staging)");
+        }
+        CK(cudaMemsetAsync(p.out, 0, nout * sizeof(float), ls), "cudaMemsetAsync");
+        const size_t frame_px = (size_t)W * H;
+        if (mem_kind == SSVP_MEM_DEVICE) {
+            CK(ssvp::launch_pack(rgb, depth, W, H, F, p, 0, ls), "pack kernel");
+        } else {
+            // stage the frames through a device buffer: the whole clip in one copy up to 4 GB (the
+            // copy engines then run without waiting for a pack kernel between chunks), larger clips
+            // in chunks of that size
+            const size_t per_frame = frame_px * 16;
+            int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)F, ((size_t)4 << 30) / per_frame));
+            const size_t need = per_frame * (size_t)chunk;
+            if (ctx->staging_bytes < need) {
+                CK(cudaStreamSynchronize(ls), "cudaStreamSynchronize");
+                if (ctx->staging) cudaFree(ctx->staging);
+                ctx->staging = nullptr;
+                ctx->staging_bytes = 0;
+                if ((e = cudaMalloc(&ctx->staging, need)) != cudaSuccess) {
+                    free_clip(c);
+                    return cuda_fail(ctx, e, "cudaMalloc (staging)");
+                }
+                ctx->staging_bytes = need;
             }
-            ctx->staging_bytes = need;
+            float *srgb = (float *)ctx->staging;
+            float *sdep = srgb + frame_px * 3 * (size_t)chunk;
+            for (int f0 = 0; f0 < F; f0 += chunk) {
+                int nf = std::min(chunk, F - f0);
+                CK(cudaMemcpyAsync(srgb, rgb + frame_px * 3 * (size_t)f0, frame_px * 3 * nf * sizeof(float),
+                    cudaMemcpyHostToDevice, ls), "cudaMemcpyAsync (rgb)");
+                CK(cudaMemcpyAsync(sdep, depth + frame_px * (size_t)f0, frame_px * nf * sizeof(float), cudaMemcpyHostToDevice,
+                    ls), "cudaMemcpyAsync (depth)");
+                CK(ssvp::launch_pack(srgb, sdep, W, H, nf, p, f0, ls), "pack kernel");
+            }
         }
-        float *srgb = (float *)ctx->staging;
-        float *sdep = srgb + frame_px * 3 * (size_t)chunk;
-        for (int f0 = 0; f0 < F; f0 += chunk) {
-            int nf = std::min(chunk, F - f0);
-            CK(cudaMemcpyAsync(srgb, rgb + frame_px * 3 * (size_t)f0, frame_px * 3 * nf * sizeof(float),
-                               cudaMemcpyHostToDevice, ls), "cudaMemcpyAsync (rgb)");
-            CK(cudaMemcpyAsync(sdep, depth + frame_px * (size_t)f0, frame_px * nf * sizeof(float), cudaMemcpyHostToDevice,
-                               ls), "cudaMemcpyAsync (depth)");
-            CK(ssvp::launch_pack(srgb, sdep, W, H, nf, p, f0, ls), "pack kernel");
-        }
+        CK(ssvp::launch_median(p, ctx->median_scratch, ls), "median kernels");
     }
-    CK(ssvp::launch_median(p, ctx->median_scratch, ls), "median kernels");
-    CK(ssvp::launch_zrange(p, ls), "depth range kernel");
-    CK(ssvp::launch_grad_sum(p, ls), "gradient sum kernels");
-    }
+    c.zrange_ready = c.grad_ready = false;
     // everything queued on the context's stream from here on runs after the load
     CK(cudaEventRecord(ctx->ev_load_out, ls), "cudaEventRecord");
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_load_out, 0), "cudaStreamWaitEvent");
@@ -895,40 +924,39 @@ int ssvp_append_frames(ssvp_ctx *ctx, int clip_id, int n, const float *rgb, cons
         const size_t keep = (size_t)(F - n) * (size_t)p.fstride;
         if (keep) {
             CK(cudaMemcpyAsync(q.depth, p.depth + (size_t)n * p.fstride, keep * sizeof(float), cudaMemcpyDeviceToDevice, ls),
-               "cudaMemcpyAsync (window)");
+                "cudaMemcpyAsync (window)");
             CK(cudaMemcpyAsync(q.colour, (const char *)p.colour + (size_t)n * p.fstride * texel, keep * texel,
-                               cudaMemcpyDeviceToDevice, ls),
-               "cudaMemcpyAsync (window)");
-    }
-    const size_t frame_px = (size_t)W * H;
-    if (mem_kind == SSVP_MEM_DEVICE) {
-        // device inputs may be produced by work queued on the context's stream up to this call
-        CK(cudaStreamWaitEvent(ls, c.ev_append, 0), "cudaStreamWaitEvent");
-        CK(ssvp::launch_pack(rgb, depth, W, H, n, q, F - n, ls), "pack kernel");
-    } else {
-        const size_t need = frame_px * 16 * (size_t)n;
-        if (ctx->staging_bytes < need) {
-            CK(cudaStreamSynchronize(ls), "cudaStreamSynchronize");
-            if (ctx->staging) cudaFree(ctx->staging);
-            ctx->staging = nullptr;
-            ctx->staging_bytes = 0;
-            if ((e = cudaMalloc(&ctx->staging, need)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc (staging)");
-            ctx->staging_bytes = need;
+                cudaMemcpyDeviceToDevice, ls),
+                "cudaMemcpyAsync (window)");
         }
-        float *srgb = (float *)ctx->staging;
-        float *sdep = srgb + frame_px * 3 * (size_t)n;
-        CK(cudaMemcpyAsync(srgb, rgb, frame_px * 3 * n * sizeof(float), cudaMemcpyHostToDevice, ls), "cudaMemcpyAsync (rgb)");
-        CK(cudaMemcpyAsync(sdep, depth, frame_px * n * sizeof(float), cudaMemcpyHostToDevice, ls), "cudaMemcpyAsync (depth)");
-        CK(ssvp::launch_pack(srgb, sdep, W, H, n, q, F - n, ls), "pack kernel");
-    }
-    CK(ssvp::launch_median(q, ctx->median_scratch, ls), "median kernels");
-    CK(ssvp::launch_zrange(q, ls), "depth range kernel");
-    CK(ssvp::launch_grad_sum(q, ls), "gradient sum kernels");
+        const size_t frame_px = (size_t)W * H;
+        if (mem_kind == SSVP_MEM_DEVICE) {
+            // device inputs may be produced by work queued on the context's stream up to this call
+            CK(cudaStreamWaitEvent(ls, c.ev_append, 0), "cudaStreamWaitEvent");
+            CK(ssvp::launch_pack(rgb, depth, W, H, n, q, F - n, ls), "pack kernel");
+        } else {
+            const size_t need = frame_px * 16 * (size_t)n;
+            if (ctx->staging_bytes < need) {
+                CK(cudaStreamSynchronize(ls), "cudaStreamSynchronize");
+                if (ctx->staging) cudaFree(ctx->staging);
+                ctx->staging = nullptr;
+                ctx->staging_bytes = 0;
+                if ((e = cudaMalloc(&ctx->staging, need)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc (staging)");
+                ctx->staging_bytes = need;
+            }
+            float *srgb = (float *)ctx->staging;
+            float *sdep = srgb + frame_px * 3 * (size_t)n;
+            CK(cudaMemcpyAsync(srgb, rgb, frame_px * 3 * n * sizeof(float), cudaMemcpyHostToDevice, ls), "cudaMemcpyAsync (rgb)");
+            CK(cudaMemcpyAsync(sdep, depth, frame_px * n * sizeof(float), cudaMemcpyHostToDevice, ls), "cudaMemcpyAsync (depth)");
+            CK(ssvp::launch_pack(srgb, sdep, W, H, n, q, F - n, ls), "pack kernel");
+        }
+        CK(ssvp::launch_median(q, ctx->median_scratch, ls), "median kernels");
     }
     CK(cudaEventRecord(ctx->ev_load_out, ls), "cudaEventRecord");
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_load_out, 0), "cudaStreamWaitEvent");
     // the spare window becomes current; the cameras slide with the frames
     swap_window(p, sp);
+    c.zrange_ready = c.grad_ready = false;
     c.K.erase(c.K.begin(), c.K.begin() + 9 * (size_t)n);
     c.K.insert(c.K.end(), Kn.begin(), Kn.end());
     c.w2c.erase(c.w2c.begin(), c.w2c.begin() + 12 * (size_t)n);
@@ -1073,6 +1101,7 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         a.stat_counts = ctx->stat_counts;
         a.stat_sumw = ctx->stat_sumw;
         a.geom_back = frustum ? ctx->geom + total + off : nullptr;
+        if ((rc = ensure_frame_values(ctx, c, frustum, p.mode == SSVP_MODE_DEBLUR)) != SSVP_OK) return rc;
         a.frame_log2w = p.mode == SSVP_MODE_DEBLUR ? c.p.grad_log2 : nullptr;
         a.slot_log2w = shutter ? ctx->d_shutter_log2 : nullptr;
         a.frustum_l = p.frustum_l;
@@ -1119,6 +1148,7 @@ int ssvp_superres(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, int sca
         return fail(ctx, SSVP_EINVAL, "debug outputs need at most one output frame");
     if (n_out == 0) return SSVP_OK;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((rc = ensure_frame_values(ctx, c, true, p.mode == SSVP_MODE_DEBLUR)) != SSVP_OK) return rc;
     const size_t total = (size_t)n_out * ns;
     if (2 * total > ctx->geom_cap) {
         CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
@@ -1275,6 +1305,8 @@ int ssvp_frame_sharpness(ssvp_ctx *ctx, int clip_id, double *out) {
     if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
     if (!out) return fail(ctx, SSVP_EINVAL, "out is NULL");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = ensure_frame_values(ctx, c, false, true);
+    if (rc != SSVP_OK) return rc;
     CK(cudaMemcpyAsync(out, c.p.grad_sum, sizeof(double) * (size_t)c.p.F, cudaMemcpyDeviceToHost, ctx->stream),
        "cudaMemcpyAsync (gradient sums)");
     CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");

@@ -59,10 +59,17 @@ def test_load_and_gathers_are_recorded_by_kind(sess, clip):
         pf = sess.params(gather=ss.SSVP_GATHER_FRUSTUM, half_window=3, frame_begin=7, frame_end=8,
                          crop_x=100, crop_y=60, crop_w=40, crop_h=30)
         ss.ssvp_gather_filter(sess.ctx, pf, [0])
+        ss.ssvp_gather_filter(sess.ctx, pf, [0])
         ss.ssvp_gather_filter(sess.ctx, p, [0])
         rec = ss.ssvp_trace_read(sess.ctx)
-        assert {k: v[0] for k, v in rec.items()} == {"gather": 1, "aperture": 1, "frustum": 1}
+        # the frames' depth ranges are computed once, at the first frustum gather after the load
+        assert {k: v[0] for k, v in rec.items()} == {"gather": 1, "aperture": 1, "frustum": 2, "load": 1}
         assert all(v[1] > 0.0 for v in rec.values())
+        db = sess.params(mode=ss.SSVP_MODE_DEBLUR, half_window=7, frame_begin=7, frame_end=8)
+        ss.ssvp_gather_filter(sess.ctx, db, [0])
+        ss.ssvp_gather_filter(sess.ctx, db, [0])
+        rec = ss.ssvp_trace_read(sess.ctx)
+        assert {k: v[0] for k, v in rec.items()} == {"gather": 2, "load": 1}  # the Eq. 5 sums, once
     finally:
         ss.ssvp_trace_enable(sess.ctx, False)
 
