@@ -302,10 +302,12 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
 
 /* Copy output frames [frame_begin, frame_end) of a clip (full frames, F*H*W*3 layout) to `dst`
  * on the host (mem_kind = SSVP_MEM_HOST; waits for completion) or device (SSVP_MEM_DEVICE;
- * queued).  Pixels never written by a gather call hold 0. */
+ * queued).  Pixels no gather call has written since the clip was loaded hold 0 (a reload with the
+ * same shape clears the frames written before it). */
 int ssvp_read_output(ssvp_ctx *ctx, int clip_id, int frame_begin, int frame_end, float *dst, int mem_kind);
 
-/* Device pointer of a clip's output buffer (F*H*W*3 floats, owned by the library). */
+/* Device pointer of a clip's output buffer (F*H*W*3 floats, owned by the library).  The caller
+ * may write it; the next same-shape reload then clears the whole buffer. */
 int ssvp_output_device_ptr(ssvp_ctx *ctx, int clip_id, void **dev_ptr);
 
 /*

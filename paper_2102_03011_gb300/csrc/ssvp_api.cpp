@@ -35,6 +35,19 @@ struct Clip {
     // per-frame values of the current window that only some calls need, computed on first use:
     // the valid depth range of each frame (the frustum gathers) and the Eq. 5 gradient sums
     bool zrange_ready = false, grad_ready = false;
+    // output frames [out_lo, out_hi) may hold values written since the buffer was last cleared
+    // (a reload with the same shape clears only these)
+    int out_lo = 0, out_hi = 0;
+    void mark_out(int b, int e) {
+        if (e <= b) return;
+        if (out_hi <= out_lo) {
+            out_lo = b;
+            out_hi = e;
+        } else {
+            out_lo = std::min(out_lo, b);
+            out_hi = std::max(out_hi, e);
+        }
+    }
 };
 
 // the arrays of one window of a clip (the rest of Planes, such as the output and the mask, is shared)
@@ -767,7 +780,14 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
             CK(cudaMemsetAsync(p.depth, 0xff, nplane * sizeof(float), ls), "cudaMemsetAsync");
             CK(cudaMemsetAsync(p.colour, 0, nplane * texel, ls), "cudaMemsetAsync");
         }
-        CK(cudaMemsetAsync(p.out, 0, nout * sizeof(float), ls), "cudaMemsetAsync");
+        if (!reuse) {
+            CK(cudaMemsetAsync(p.out, 0, nout * sizeof(float), ls), "cudaMemsetAsync");
+        } else if (c.out_hi > c.out_lo) {
+            const size_t per = (size_t)W * H * 3;
+            CK(cudaMemsetAsync(p.out + per * (size_t)c.out_lo, 0, per * (size_t)(c.out_hi - c.out_lo) * sizeof(float), ls),
+               "cudaMemsetAsync");
+        }
+        c.out_lo = c.out_hi = 0;
         const size_t frame_px = (size_t)W * H;
         if (mem_kind == SSVP_MEM_DEVICE) {
             CK(ssvp::launch_pack(rgb, depth, W, H, F, p, 0, ls), "pack kernel");
@@ -988,6 +1008,7 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         if (x0 < 0 || y0 < 0 || x0 + w > c.p.W || y0 + h > c.p.H)
             return fail(ctx, SSVP_EINVAL, "crop (%d, %d, %d, %d) outside clip %d (%dx%d)", x0, y0, w, h, id, c.p.W, c.p.H);
         fb[i] = b; nout[i] = e - b; cx0[i] = x0; cy0[i] = y0; cw[i] = w; chh[i] = h;
+        c.mark_out(b, e);
         total += (size_t)(e - b) * ns;
     }
     if ((p.membership_out || p.pixel_stats_out) && (n_clips != 1 || nout[0] > 1))
@@ -1339,7 +1360,9 @@ int ssvp_output_device_ptr(ssvp_ctx *ctx, int clip_id, void **dev_ptr) {
     if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
     if (!ctx->clips[clip_id].loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
     if (!dev_ptr) return fail(ctx, SSVP_EINVAL, "dev_ptr is NULL");
-    *dev_ptr = ctx->clips[clip_id].p.out;
+    Clip &c = ctx->clips[clip_id];
+    c.mark_out(0, c.p.F);  // the caller may write the buffer: a reload clears all of it
+    *dev_ptr = c.p.out;
     return SSVP_OK;
 }
 
@@ -1387,6 +1410,8 @@ int ssvp_autotune(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids,
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     BatchSetup bs;
     batch_tables(ctx, *params, clip_ids, n_clips, 8, bs);
+    for (int i = 0; i < n_clips; ++i)  // the trial launches write these output frames
+        ctx->clips[clip_ids[i]].mark_out(bs.clips[i].frame_begin, bs.clips[i].frame_begin + bs.clips[i].n_out);
     PairGeom *d_geom = nullptr;
     unsigned long long *d_counter = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1516,6 +1541,10 @@ int ssvp_plan_launch(ssvp_plan *plan) {
             return fail(ctx, SSVP_ENOCLIP, "clip %d was reloaded or unloaded after the plan was made", plan->clip_ids[i]);
     }
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    for (int id : plan->clip_ids) {
+        Clip &c = ctx->clips[id];
+        c.mark_out(plan->params.frame_begin, plan->params.frame_end < 0 ? c.p.F : plan->params.frame_end);
+    }
     TraceScope ts(ctx, SSVP_TRACE_BATCH, ctx->stream);
     CK(cudaGraphLaunch(plan->exec, ctx->stream), "cudaGraphLaunch");
     return SSVP_OK;

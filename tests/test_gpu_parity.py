@@ -175,6 +175,44 @@ def test_reload_with_the_same_shape_replaces_the_contents(sess, tiny):
     np.testing.assert_array_equal(sess.run(9, 8, k=5, half_window=15).rgb, want_other)
 
 
+def test_reload_clears_every_output_frame_written_since_the_load(sess, tiny):
+    """Pixels no gather has written since the (re)load read 0: a same-shape reload clears the
+    frames written by gathers, batched plans and the caller through the device pointer."""
+    ss, t = sess.ss, sess.torch
+    sess.load(14, tiny)
+    ss.ssvp_gather_filter(sess.ctx, sess.params(k=5, half_window=2, frame_begin=2, frame_end=4), [14])
+    plan = ss.ssvp_plan_create(sess.ctx, sess.params(k=5, half_window=2, frame_begin=9, frame_end=11), [14])
+    ss.ssvp_plan_launch(plan)
+    ss.ssvp_plan_destroy(plan)
+    out = t.empty((tiny.F, tiny.H, tiny.W, 3), dtype=t.float32, device=sess.dev)
+    ss.ssvp_read_output(sess.ctx, 14, 0, tiny.F, out)
+    ss.ssvp_sync(sess.ctx)
+    written = [f for f in range(tiny.F) if bool((out[f] != 0).any())]
+    assert written == [2, 3, 9, 10]
+    sess.load(14, tiny)  # same shape: planes reused, the written frames cleared
+    ss.ssvp_read_output(sess.ctx, 14, 0, tiny.F, out)
+    ss.ssvp_sync(sess.ctx)
+    assert not bool((out != 0).any())
+    # the caller writes the last frame through the device pointer (wrapped without a copy)
+    ptr = ss.ssvp_output_device_ptr(sess.ctx, 14)
+
+    class _Buf:
+        __cuda_array_interface__ = {"shape": (tiny.F, tiny.H, tiny.W, 3), "typestr": "<f4", "data": (ptr, False),
+                                    "version": 2}
+
+    buf = t.as_tensor(_Buf(), device=sess.dev)
+    sess.stream.synchronize()
+    buf[tiny.F - 1].fill_(2.0)
+    t.cuda.synchronize()
+    ss.ssvp_read_output(sess.ctx, 14, tiny.F - 1, tiny.F, out[:1])
+    ss.ssvp_sync(sess.ctx)
+    assert bool((out[0] == 2.0).all())
+    sess.load(14, tiny)
+    ss.ssvp_read_output(sess.ctx, 14, 0, tiny.F, out)
+    ss.ssvp_sync(sess.ctx)
+    assert not bool((out != 0).any())
+
+
 def test_empty_frame_range_is_a_no_op(sess, tiny):
     """frame_begin == frame_end: nothing is gathered, the output and the statistics stay as they are."""
     ss = sess.ss
