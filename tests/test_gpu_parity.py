@@ -213,6 +213,23 @@ def test_reload_clears_every_output_frame_written_since_the_load(sess, tiny):
     assert not bool((out != 0).any())
 
 
+def test_allocation_failure_is_a_status_and_the_context_stays_usable(sess, tiny):
+    """A clip whose planes exceed the device (16384 x 16384 x 4096: ~4 TB of depth alone) is refused
+    with SSVP_ENOMEM by the first allocation, before any input is read; nothing stays allocated,
+    the id is not loaded, and the context goes on working."""
+    ss = sess.ss
+    host = np.zeros(16, np.float32)  # never read: the allocation fails first
+    with pytest.raises(ss.SsvpError) as e:
+        ss.ssvp_load_clip(sess.ctx, 15, 16384, 16384, 4096, host, host, ss.SSVP_MEM_HOST)
+    assert e.value.code == ss.SSVP_ENOMEM and "cudaMalloc" in str(e.value)
+    with pytest.raises(ss.SsvpError) as e2:
+        ss.ssvp_clip_median_depth(sess.ctx, 15)
+    assert e2.value.code == ss.SSVP_ENOCLIP
+    sess.load(15, tiny)
+    sess.load(16, tiny)
+    np.testing.assert_array_equal(sess.run(15, 8, k=5, half_window=2).rgb, sess.run(16, 8, k=5, half_window=2).rgb)
+
+
 def test_empty_frame_range_is_a_no_op(sess, tiny):
     """frame_begin == frame_end: nothing is gathered, the output and the statistics stay as they are."""
     ss = sess.ss
