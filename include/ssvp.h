@@ -359,9 +359,10 @@ int ssvp_read_stats(ssvp_ctx *ctx, unsigned long long *examined, unsigned long l
  * transform once, numbers the work items (clip, output-frame chunk, 32 x tile_rows tile),
  * sizes a persistent grid from the kernel's occupancy, and captures "reset counters + launch"
  * as a CUDA graph that ssvp_plan_launch replays on the context's stream.  Denoise and mean
- * modes, full frames, no debug outputs; all clips must share one colour format.  A plan must
- * be destroyed before any of its clips is reloaded or unloaded (its launch then fails with
- * SSVP_ENOCLIP) and re-created after ssvp_set_cameras.
+ * modes, full frames, no debug outputs; all clips must share one colour format.  After any of
+ * its clips is reloaded or unloaded the plan's launch fails with SSVP_ENOCLIP until the plan is
+ * updated (ssvp_plan_update, for reloads with the same shapes) or re-created; after
+ * ssvp_set_cameras it must be updated or re-created too.
  */
 typedef struct ssvp_plan ssvp_plan;
 typedef struct ssvp_plan_config {
@@ -383,6 +384,14 @@ int ssvp_plan_create(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_i
 /* Replay the plan's graph on the context's stream (asynchronous); statistics as for
  * ssvp_gather_filter. */
 int ssvp_plan_launch(ssvp_plan *plan);
+
+/* Refresh a plan for its clips' current contents and cameras, keeping its captured graph: valid
+ * after reloads with the same W, H, F and colour format (which keep the clips' planes) and after
+ * ssvp_set_cameras.  Recomposes every per-(O, J) transform from the current cameras into the
+ * plan's table (a copy queued on the context's stream after the plan's earlier launches; does
+ * not wait).  SSVP_ENOCLIP / SSVP_ENOCAM for a clip not loaded / without cameras, SSVP_EINVAL if a
+ * clip's planes moved (another shape or format, or ssvp_append_frames): make a new plan. */
+int ssvp_plan_update(ssvp_plan *plan);
 
 /* Shape, number of work items and persistent grid size of a plan (any pointer may be NULL). */
 int ssvp_plan_get_config(const ssvp_plan *plan, ssvp_plan_config *config, long long *n_items, int *grid);

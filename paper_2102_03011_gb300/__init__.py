@@ -90,6 +90,7 @@ def _load():
         "ssvp_plan_create": (i, [vp, P, ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(ssvp_plan_config),
                                  ctypes.POINTER(vp)]),
         "ssvp_plan_launch": (i, [vp]),
+        "ssvp_plan_update": (i, [vp]),
         "ssvp_plan_get_config": (i, [vp, ctypes.POINTER(ssvp_plan_config), ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_int)]),
         "ssvp_plan_destroy": (None, [vp]),
@@ -350,6 +351,10 @@ def ssvp_plan_create(ctx, params: ssvp_params, clip_ids, config: ssvp_plan_confi
 
 def ssvp_plan_launch(plan: Plan) -> None:
     _check(plan.ctx, lib.ssvp_plan_launch(plan.handle))
+
+
+def ssvp_plan_update(plan: Plan) -> None:
+    _check(plan.ctx, lib.ssvp_plan_update(plan.handle))
 
 
 def ssvp_plan_get_config(plan: Plan):

@@ -124,6 +124,19 @@ struct ssvp_plan {
     ssvp_params params{};
     std::vector<int> clip_ids;
     std::vector<unsigned> generations;
+    // what the captured graph holds of each clip: its plane pointers and the shape they have
+    struct Frozen {
+        const void *depth, *colour, *out, *median;
+        int W, H, F, fmt;
+        bool operator==(const Frozen &o) const {
+            return depth == o.depth && colour == o.colour && out == o.out && median == o.median && W == o.W &&
+                   H == o.H && F == o.F && fmt == o.fmt;
+        }
+    };
+    static Frozen frozen(const Planes &p) {
+        return Frozen{p.depth, p.colour, p.out, p.median, p.W, p.H, p.F, p.colour_fmt};
+    }
+    std::vector<Frozen> planes;
     ssvp_plan_config cfg{8, 1};
     long long n_items = 0;
     int grid = 0;
@@ -1492,7 +1505,10 @@ int ssvp_plan_create(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_i
     plan->ctx = ctx;
     plan->params = *params;
     plan->clip_ids.assign(clip_ids, clip_ids + n_clips);
-    for (int i = 0; i < n_clips; ++i) plan->generations.push_back(ctx->clips[clip_ids[i]].generation);
+    for (int i = 0; i < n_clips; ++i) {
+        plan->generations.push_back(ctx->clips[clip_ids[i]].generation);
+        plan->planes.push_back(ssvp_plan::frozen(ctx->clips[clip_ids[i]].p));
+    }
     plan->cfg = cfg;
     BatchSetup bs;
     batch_tables(ctx, *params, clip_ids, n_clips, 1 << 30, bs);
@@ -1547,6 +1563,33 @@ int ssvp_plan_launch(ssvp_plan *plan) {
     }
     TraceScope ts(ctx, SSVP_TRACE_BATCH, ctx->stream);
     CK(cudaGraphLaunch(plan->exec, ctx->stream), "cudaGraphLaunch");
+    return SSVP_OK;
+}
+
+int ssvp_plan_update(ssvp_plan *plan) {
+    if (!plan) return fail(nullptr, SSVP_EINVAL, "plan is NULL");
+    ssvp_ctx *ctx = plan->ctx;
+    const int n = (int)plan->clip_ids.size();
+    for (int i = 0; i < n; ++i) {
+        const int id = plan->clip_ids[i];
+        const Clip &c = ctx->clips[id];
+        if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", id);
+        if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", id);
+        // the captured graph holds the clip's plane pointers and strides: a reload with another
+        // shape or format, or an append (which swaps windows), changed them
+        if (!(ssvp_plan::frozen(c.p) == plan->planes[i]))
+            return fail(ctx, SSVP_EINVAL, "clip %d's planes changed since the plan was made (another shape, format or "
+                                          "an append): make a new plan", id);
+    }
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    BatchSetup bs;
+    batch_tables(ctx, plan->params, plan->clip_ids.data(), n, 1 << 30, bs);
+    // queued after the plan's earlier launches on the same stream; a pageable source is staged
+    // before the call returns
+    CK(cudaMemcpyAsync(plan->d_geom, bs.geom.data(), bs.geom.size() * sizeof(PairGeom), cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "cudaMemcpyAsync (plan geometry)");
+    for (int i = 0; i < n; ++i) plan->generations[i] = ctx->clips[plan->clip_ids[i]].generation;
     return SSVP_OK;
 }
 

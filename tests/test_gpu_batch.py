@@ -123,3 +123,41 @@ def test_plan_argument_checks(sess):
     with pytest.raises(ss.SsvpError) as e:
         ss.ssvp_plan_create(sess.ctx, sess.params(crop_w=8, crop_h=8), [30])
     assert e.value.code == ss.SSVP_EINVAL
+
+
+def test_plan_update_after_same_shape_reloads_and_new_cameras(sess):
+    """ssvp_plan_update keeps the captured graph and recomposes the geometry: after a same-shape
+    reload with new contents and cameras, and after ssvp_set_cameras, the plan again gives the
+    plain path's output to the bit; a reload with another shape is refused."""
+    ss = sess.ss
+    p = sess.params(k=5, half_window=3)
+    plan = ss.ssvp_plan_create(sess.ctx, p, [30, 31, 32], ss.ssvp_plan_config(8, 1))
+    try:
+        ss.ssvp_plan_launch(plan)
+        other = synth.make_clip("room", 96, 54, 9, seed=7)  # clip 31's shape, other scene and path
+        sess.load(31, other, colour_fmt=1)
+        with pytest.raises(ss.SsvpError) as e:
+            ss.ssvp_plan_launch(plan)
+        assert e.value.code == ss.SSVP_ENOCLIP
+        ss.ssvp_plan_update(plan)
+        ss.ssvp_plan_launch(plan)
+        got = _outputs(sess)
+        want, _ = _plain(sess, p)
+        for a, b in zip(got, want):
+            np.testing.assert_array_equal(a, b)
+        c0 = synth.make_clip(*SIZES[0][:4], seed=SIZES[0][4])
+        ss.ssvp_set_cameras(sess.ctx, 30, c0.K, 1, c0.w2c_true)  # the exact cameras instead
+        ss.ssvp_plan_update(plan)
+        ss.ssvp_plan_launch(plan)
+        got = _outputs(sess)
+        want, _ = _plain(sess, p)
+        for a, b in zip(got, want):
+            np.testing.assert_array_equal(a, b)
+        sess.load(32, synth.make_clip("planes3", 160, 90, 12, seed=3), colour_fmt=1)  # another F
+        with pytest.raises(ss.SsvpError) as e:
+            ss.ssvp_plan_update(plan)
+        assert e.value.code == ss.SSVP_EINVAL
+    finally:
+        ss.ssvp_plan_destroy(plan)
+        for i, (preset, W, H, F, seed) in enumerate(SIZES):  # the module's clips as they were
+            sess.load(30 + i, synth.make_clip(preset, W, H, F, seed=seed), colour_fmt=1)
