@@ -959,6 +959,9 @@ def main():
     ap.add_argument("--no-stream", action="store_true",
                     help="end to end with a full clip upload per step only (no streaming appends)")
     ap.add_argument("--workload", default="fhd", choices=sorted(WORKLOADS))
+    ap.add_argument("--gather", default="window", choices=["window", "tma"],
+                    help="window-gather workloads: candidate depths from the global planes (window) or from "
+                         "shared-memory boxes filled by TMA tensor copies (tma, SSVP_GATHER_WINDOW_TMA)")
     ap.add_argument("--out-frames", type=int, default=None, help="output frames per step (default per workload)")
     ap.add_argument("--train-clips", type=int, default=200, help="learned workload: generated training clips")
     ap.add_argument("--train-steps-per-group", type=int, default=120,
@@ -1032,6 +1035,10 @@ def main():
         p.mode, p.gather, p.frustum_l, p.sigma_rgb = ss.SSVP_MODE_SEMI, ss.SSVP_GATHER_FRUSTUM, FRUSTUM_L, SEMI_SIGMA_RGB
         p.radius, p.sigma_xyz = -FRUSTUM_SIGMA_XYZ_REL, 0.0  # sigma_xyz of the Eq. 4 term: 3 % of the median depth
         ss.ssvp_mask_from_box(ctx, 0, _inpaint_box(clip))
+    if args.gather == "tma":
+        if MODE not in (0, 5, 6):
+            raise SystemExit("--gather tma applies to the window-gather workloads (fhd, hd, deblur, shutter)")
+        p.gather = ss.SSVP_GATHER_WINDOW_TMA
 
     def barrier():
         if world > 1:
@@ -1249,13 +1256,16 @@ def main():
         rl_mode, rl_exam, rl_acc = (1 if MODE == 1 else 0), examined, accepted
     clk_summary = clk.summary()
     sm_mhz = clk_summary["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    prof = _profile_figures(args.workload, args.colour, N_OUT)
+    # the committed counters are those of the window gather reading the global planes
+    prof = _profile_figures(args.workload, args.colour, N_OUT) if args.gather == "window" else {}
     roofline = roofline_block(rl_mode, rl_exam, rl_acc, kernel_ms, sm_mhz, peaks, peak_kind, prof, touched)
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.colour == "fp32" else "f16-colour/f32",
-        "data": "synthetic (seeded procedural scene, rendered on the host)", "config": _config(args.colour),
+        "data": "synthetic (seeded procedural scene, rendered on the host)",
+        "config": {**_config(args.colour), **({"gather": "window, candidate depths staged by TMA tensor copies "
+                                                          "(SSVP_GATHER_WINDOW_TMA)"} if args.gather == "tma" else {})},
         "samples_per_s": {"examined": world * examined / (ms_per_step / 1e3),
                           "accepted": world * accepted / (ms_per_step / 1e3)},
         "accepted_per_pixel": accepted / (N_OUT * W * H), "kept_weight_fraction": sum_w / max(accepted, 1),

@@ -64,7 +64,10 @@ enum {
 };
 enum {
     SSVP_GATHER_WINDOW = 0,  /* depth-seeded k x k window + radius (or the aperture cone) */
-    SSVP_GATHER_FRUSTUM = 1  /* the pixel frustum of Sec. "Sample Gathering", Eq. 1-2 */
+    SSVP_GATHER_FRUSTUM = 1, /* the pixel frustum of Sec. "Sample Gathering", Eq. 1-2 */
+    SSVP_GATHER_WINDOW_TMA = 2 /* the window gather of SSVP_GATHER_WINDOW, same samples and
+                                results, with each warp's window footprint in frame J copied into
+                                shared memory by a TMA tensor copy before its radius tests */
 };
 
 #define SSVP_MAX_CLIPS 64
@@ -94,14 +97,25 @@ enum {
  *                 gather, only for s_ref in Eq. 4 (an invalid output depth still gives c_ref).
  *                 Denoise, mean, deblur, shutter and inpaint modes; k is ignored and the radius
  *                 serves only as the default sigma_xyz.  Not available in batched plans.
+ *                 SSVP_GATHER_WINDOW_TMA: the window gather with the candidate depths of each
+ *                 warp (32 output pixels of a row) staged, frame by frame, into shared memory by
+ *                 TMA tensor copies (a 48 x 12 box of frame J around the warp's windows, two
+ *                 buffers, frame J + 1 copied while J is tested); lanes whose window is not
+ *                 inside the box read the global plane.  Same samples and outputs as
+ *                 SSVP_GATHER_WINDOW.  Denoise, mean, deblur and shutter modes, k <= 7; not in
+ *                 batched plans.
  *   frustum_l, near_plane, far_plane   frustum size l in pixels (0 < l <= 64; the paper uses 3)
  *                 and its O depth range (0 < near < far; the paper uses 0.01 and 1000)
  *   sigma_area    ssvp_superres only: length scale of Eq. 7's area term (scene units); <= 0 means
  *                 one input-pixel footprint at the median depth (median depth / fx of O)
- *   test_skip_mma 0 normally.  1 (a test of the time-out path, learned mode only): the learned
+ *   test_skip_mma 0 normally.  1 (a test of the time-out paths): in learned mode the learned
  *                 inference issues none of its tensor-core products, so its bounded waits for
  *                 them run out (within about 1 s each); ssvp_sync then returns SSVP_ETIMEOUT, the
- *                 outputs of the call are not valid, and the context stays usable.
+ *                 outputs of the call are not valid, and the context stays usable.  With
+ *                 SSVP_GATHER_WINDOW_TMA the gather issues none of its tensor copies: each warp's
+ *                 first wait runs out (about 1 s, then up to 2 s more waiting for copies that
+ *                 might be in flight), the warp reads the global planes, ssvp_sync returns
+ *                 SSVP_ETIMEOUT and the outputs are those of SSVP_GATHER_WINDOW.  Ignored otherwise.
  *   membership_out   optional device buffer (debug): per crop pixel (row-major) and per slot
  *                 j = 0..2T (J = O-T+j) a record of 3 + ceil(k*k/32) int32 words:
  *                 status (-2 invalid reference depth, -1 J outside the clip, 0 J skipped: the
@@ -457,9 +471,12 @@ int ssvp_mlp_grad(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, const i
 int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median);
 
 /* Wait for all work queued on the context's stream; returns the first pending error, or
- * SSVP_ETIMEOUT when a kernel's bounded wait for its tensor-core products gave up since the last
- * call (the learned inference waits on an MMA-completion barrier with a limit of about 1 s; the
- * outputs of that launch are then not valid).  The time-out is reported once. */
+ * SSVP_ETIMEOUT when a kernel's bounded device-side wait gave up since the last call: the learned
+ * inference waits for its tensor-core products on an MMA-completion barrier with a limit of about
+ * 1 s (the outputs of that launch are then not valid); the staged window gather
+ * (SSVP_GATHER_WINDOW_TMA) waits for its tensor copies with the same limit (a warp whose wait gave
+ * up tests the rest of its frames from the global planes, so its outputs stay valid).  The
+ * time-out is reported once. */
 int ssvp_sync(ssvp_ctx *ctx);
 
 /*

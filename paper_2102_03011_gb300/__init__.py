@@ -20,7 +20,7 @@ SSVP_MEM_HOST, SSVP_MEM_DEVICE = 0, 1
 SSVP_COLOUR_F32, SSVP_COLOUR_F16 = 0, 1
 SSVP_MODE_DENOISE, SSVP_MODE_APERTURE, SSVP_MODE_LEARNED, SSVP_MODE_MEAN = 0, 1, 2, 3
 SSVP_MODE_DEBLUR, SSVP_MODE_SHUTTER, SSVP_MODE_INPAINT, SSVP_MODE_SEMI = 4, 5, 6, 7
-SSVP_GATHER_WINDOW, SSVP_GATHER_FRUSTUM = 0, 1
+SSVP_GATHER_WINDOW, SSVP_GATHER_FRUSTUM, SSVP_GATHER_WINDOW_TMA = 0, 1, 2
 SSVP_MAX_CLIPS, SSVP_MAX_K, SSVP_MAX_HALF_WINDOW = 64, 31, 127
 (SSVP_TRACE_GATHER, SSVP_TRACE_APERTURE, SSVP_TRACE_FRUSTUM, SSVP_TRACE_SUPERRES, SSVP_TRACE_EXTRACT, SSVP_TRACE_INFER,
  SSVP_TRACE_TRAIN, SSVP_TRACE_ADAM, SSVP_TRACE_BATCH, SSVP_TRACE_LOAD, SSVP_TRACE_MASK, SSVP_TRACE_KINDS) = range(12)

@@ -403,8 +403,14 @@ int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
         if (!std::isfinite(p->focal_depth) || !std::isfinite(p->a0))
             return fail(ctx, SSVP_EINVAL, "focal_depth and a0 must be finite");
     }
-    if (p->gather != SSVP_GATHER_WINDOW && p->gather != SSVP_GATHER_FRUSTUM)
+    if (p->gather != SSVP_GATHER_WINDOW && p->gather != SSVP_GATHER_FRUSTUM && p->gather != SSVP_GATHER_WINDOW_TMA)
         return fail(ctx, SSVP_EINVAL, "gather %d is not available in this build", p->gather);
+    if (p->gather == SSVP_GATHER_WINDOW_TMA &&
+        (p->mode == SSVP_MODE_APERTURE || p->mode == SSVP_MODE_LEARNED || p->k > 7))
+        return fail(ctx, SSVP_EINVAL, "the staged window gather supports the denoise, mean, deblur and shutter modes "
+                                      "with k <= 7");
+    if (p->gather == SSVP_GATHER_WINDOW_TMA && p->test_skip_mma != 0 && p->test_skip_mma != 1)
+        return fail(ctx, SSVP_EINVAL, "test_skip_mma must be 0 or 1");
     if ((p->mode == SSVP_MODE_INPAINT || p->mode == SSVP_MODE_SEMI) && p->gather != SSVP_GATHER_FRUSTUM)
         return fail(ctx, SSVP_EINVAL, "inpainting gathers the pixel frustum: set gather = SSVP_GATHER_FRUSTUM");
     if (p->gather == SSVP_GATHER_FRUSTUM) {
@@ -1132,6 +1138,8 @@ int ssvp_gather_filter(ssvp_ctx *ctx, const ssvp_params *params, const int *clip
         }
         a.membership = (int32_t *)p.membership_out;
         a.pixel_stats = (int32_t *)p.pixel_stats_out;
+        a.stage = p.gather == SSVP_GATHER_WINDOW_TMA ? (p.test_skip_mma ? 2 : 1) : 0;
+        a.err = ctx->d_kerr;
         a.stat_counts = ctx->stat_counts;
         a.stat_sumw = ctx->stat_sumw;
         a.geom_back = frustum ? ctx->geom + total + off : nullptr;
@@ -1851,7 +1859,8 @@ int ssvp_sync(ssvp_ctx *ctx) {
     CK(cudaMemcpy(&kerr, ctx->d_kerr, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy (kernel error word)");
     if (kerr) {
         CK(cudaMemset(ctx->d_kerr, 0, sizeof(int)), "cudaMemset (kernel error word)");
-        return fail(ctx, SSVP_ETIMEOUT, "a tensor-core completion wait of the learned filter timed out");
+        if (kerr & 1) return fail(ctx, SSVP_ETIMEOUT, "a tensor-core completion wait of the learned filter timed out");
+        return fail(ctx, SSVP_ETIMEOUT, "a tensor-copy wait of the staged window gather timed out");
     }
     return SSVP_OK;
 }

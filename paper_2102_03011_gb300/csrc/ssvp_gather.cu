@@ -17,6 +17,7 @@
 // Accepted candidates are recorded in a per-thread bit mask during the test loop and filtered
 // afterwards by iterating the set bits, so a warp pays for the filter arithmetic only as often
 // as its busiest lane accepts (warp-level compaction of the accepted samples).
+#include <cuda.h>  // CUtensorMap (the type only; the host encodes maps through the runtime's driver entry point)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -43,6 +44,100 @@ constexpr int kLearnShortSlots = 17;  // windows of up to +-8 frames
 #define SSVP_TILE_Y 8  // output rows per CTA (a warp covers 32 pixels of one row)
 #endif
 constexpr int kTileX = 32, kTileY = SSVP_TILE_Y, kThreads = kTileX * kTileY;
+// ---------------------------------------------------------------- TMA staging of the window frames
+// SSVP_GATHER_WINDOW_TMA.  Each warp (32 output pixels of one row) stages, for every window frame J,
+// the depth of a kBoxW x kBoxH box of J's padded depth plane into shared memory with one 3-D tensor
+// copy (cp.async.bulk.tensor, completion counted on an mbarrier), in two buffers: the copy of frame
+// j + 1 is issued before frame j is tested.  The box is placed around the window of the warp's first
+// gathering lane, whose projection into J is recomputed in FP32 for the purpose (a box needs no
+// more); on a smooth surface the other lanes' windows lie beside it.  A lane whose window is not
+// inside the box (at depth edges neighbouring pixels reproject far apart) tests from the global
+// plane, so membership and results are those of the global-load path.  The waits are bounded: on a
+// time-out the warp raises bit 1 of the error word, returns to global loads for its remaining
+// frames, and its issuing lane waits once more (bounded) for the copies it has in flight.
+constexpr int kBoxW = 48, kBoxH = 12;               // floats; a box row is 192 bytes (a multiple of 16)
+constexpr unsigned kBoxBytes = kBoxW * kBoxH * 4;   // 2,304 bytes, a multiple of 128
+constexpr int kNoBox = 0x40000000;                  // origin of a buffer holding no box: no window fits
+constexpr int kStageMaxK = 7;
+constexpr unsigned kStgWaitHintNs = 100000, kStgWaitLimit = 10000;  // about 1 s per wait
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// bounded wait for the completion of the phase with parity `parity`; false on time-out
+__device__ __forceinline__ bool stg_wait(unsigned bar, unsigned parity) {
+    for (unsigned it = 0; it < kStgWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity), "r"(kStgWaitHintNs)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Per warp of a staging CTA: two mbarriers (one per box) and the origin (x, y) in J's padded plane
+// of each box, or kNoBox.  The boxes themselves follow the slot geometry in dynamic shared memory,
+// 128-byte aligned, two per warp.
+constexpr int kStgWarps = kThreads / 32;
+__shared__ unsigned long long g_stg_bar[kStgWarps][2];
+__shared__ int2 g_stg_org[kStgWarps][2];
+
+// shared-space address of buffer b of this warp's boxes (the slot geometry has n_slots entries)
+__device__ __forceinline__ unsigned stg_box(const float4 *sgeom, int n_slots, int b) {
+    const unsigned end = smem_addr(sgeom + kSlotVec * n_slots);
+    return ((end + 127u) & ~127u) + ((threadIdx.x >> 5) * 2 + b) * kBoxBytes;
+}
+__device__ __forceinline__ unsigned stg_bar(int b) { return smem_addr(&g_stg_bar[threadIdx.x >> 5][b]); }
+
+// Issue the copy of window slot s (frame J) into buffer s & 1: called by the warp's first gathering
+// lane, whose pixel offset in the tile is (du, dv), depth dref and lane index `lane`; tmap describes
+// the clip's depth planes ({pitch, rows, F} floats, box {kBoxW, kBoxH, 1}).  skip (a test of the
+// time-out path): the barrier is told to expect the box's bytes but no copy is issued, so the wait
+// for it runs out.
+template <int K>
+__device__ __forceinline__ void stage_issue(const CUtensorMap *tmap, const float4 *sgeom, int n_slots, int s, float du,
+                                            float dv, float dref, int lane, bool skip) {
+    constexpr int h = (K - 1) / 2;
+    const int b = s & 1;
+    const float4 *g = sgeom + kSlotVec * s;
+    const int J = __float_as_int(g[5].w);
+    int x0 = kNoBox, y0 = kNoBox;
+    if (J >= 0) {
+        const float4 q0 = g[0], q1 = g[1], q2 = g[2], q3 = g[3];
+        const float w0 = fmaf(dref, q0.x + fmaf(q1.z, du, q1.w * dv), q3.x);
+        const float w1 = fmaf(dref, q0.y + fmaf(q2.x, du, q2.y * dv), q3.y);
+        const float w2 = fmaf(dref, q0.z + fmaf(q2.z, du, q2.w * dv), q3.z);
+        if (w2 > 1e-6f * dref) {
+            const float rz = rcp_approx(w2), U = w0 * rz, V = w1 * rz;
+            if (fabsf(U) < 1e6f && fabsf(V) < 1e6f) {
+                const int ax = (int)floorf(U + 0.5f), ay = (int)floorf(V + 0.5f);
+                // the warp's windows span columns [ax - lane - h, ax - lane + 31 + h]: centre them in
+                // the box, x rounded down to a multiple of 4 floats (16 bytes, as tensor copies need)
+                x0 = (ax - lane - h + kPad - (kBoxW - 34 - K) / 2) & ~3;
+                y0 = ay - h + kPad - (kBoxH - K) / 2;
+            }
+        }
+    }
+    g_stg_org[threadIdx.x >> 5][b] = make_int2(x0, y0);
+    const unsigned bar = stg_bar(b);
+    if (x0 != kNoBox) {
+        const unsigned dst = stg_box(sgeom, n_slots, b);
+        // the warp's generic-proxy reads of this buffer (frame s - 2) precede the copy's writes
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(kBoxBytes) : "memory");
+        if (!skip)
+            asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];\n" ::"r"(dst),
+            "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(x0), "r"(y0), "r"(J), "r"(bar)
+            : "memory");
+    } else {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+    }
+}
+
 // The gather and filter of one output pixel (u, v) of frame O (steps A3-A7).  sgeom holds the
 // per-slot geometry built for the tile whose first pixel is (u0, v0).  n_acc, n_exam and acc_w
 // return the pixel's accepted and examined counts and sum of weights (they start at 0).
@@ -77,12 +172,15 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // first kMaxSamples accepted samples (learned filter); the Eq. 3/4 result goes to a.sets.plain.
 // ACCB: accepted samples taken per iteration of the filter loop of a compile-time window (1, or
 // 2 in packed FP32x2, which the kernels use; the runtime-k path takes them one at a time)
-template <int K, int CFMT, bool DEBUG, bool LEARN = false, int ACCB = 1>
+// STG: the candidate depths of the test loop come from the warp's staged boxes (K > 0, not LEARN);
+// tmap describes the clip's depth planes
+template <int K, int CFMT, bool DEBUG, bool LEARN = false, int ACCB = 1, bool STG = false>
 __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &P, const int O, const int u0,
                                              const int v0, const int u, const int v, const bool active,
                                              const long long crop_idx, const float4 *sgeom, const int n_slots,
                                              const float r2, const float a_rgb, const float a_xyz, const bool weighted,
-                                             int &n_acc, int &n_exam, float &acc_w) {
+                                             int &n_acc, int &n_exam, float &acc_w, const CUtensorMap *tmap = nullptr) {
+    static_assert(!STG || (K > 0 && K <= kStageMaxK && !LEARN), "staging: compile-time k <= 7, plain gather");
     const int k = K > 0 ? K : a.k;
     const int h = (k - 1) >> 1;
     const int rec_words = 3 + (k * k + 31) / 32;
@@ -99,13 +197,34 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
         cref = load_colour<CFMT>(P.colour, pix);
     }
     const bool gather = active && dref > 0.0f;  // false for NaN (invalid) depth
+    // staging: the warp's gathering lanes, the first of them issues the copies
+    const unsigned G = STG ? __ballot_sync(0xffffffffu, gather) : 0u;
+    int stg_fail = -1;  // staging: the slot whose wait gave up (-1: staging on)
     if (DEBUG && active && !gather && a.membership) {
         for (int j = 0; j < n_slots; ++j) a.membership[(crop_idx * n_slots + j) * rec_words] = -2;
     }
 
     if (gather) {
         const float du = (float)(u - u0), dv = (float)(v - v0);
+        if (STG && (int)(threadIdx.x & 31) == __ffs(G) - 1)
+            stage_issue<K>(tmap, sgeom, n_slots, 0, du, dv, dref, threadIdx.x & 31, a.stage == 2);
         for (int jj = 0; jj < n_slots; ++jj) {
+            int2 org = make_int2(kNoBox, kNoBox);
+            if (STG) {
+                // every lane of G is done with buffer (jj + 1) & 1 (slot jj - 1): refill it with slot
+                // jj + 1, then wait for slot jj
+                __syncwarp(G);
+                const bool leader = (int)(threadIdx.x & 31) == __ffs(G) - 1;
+                if (stg_fail < 0 && leader && jj + 1 < n_slots)
+                    stage_issue<K>(tmap, sgeom, n_slots, jj + 1, du, dv, dref, threadIdx.x & 31, a.stage == 2);
+                const bool ok = stg_fail >= 0 || stg_wait(stg_bar(jj & 1), (unsigned)(jj >> 1) & 1u);
+                if (__all_sync(G, ok)) {
+                    if (stg_fail < 0) org = g_stg_org[threadIdx.x >> 5][jj & 1];
+                } else if (stg_fail < 0) {
+                    stg_fail = jj;  // the rest of this warp's frames test from the global plane
+                    if (leader) atomicOr(a.err, 2);
+                }
+            }
             // canonical order for the learned filter: O, O-1, O+1, O-2, O+2, ...
             const int j = LEARN ? Tw + (jj == 0 ? 0 : ((jj & 1) ? -((jj + 1) >> 1) : (jj >> 1))) : jj;
             const float4 *g = sgeom + kSlotVec * j;
@@ -161,6 +280,18 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
             if (DEBUG && rec) { rec[0] = 1; rec[1] = cx; rec[2] = cy; }
 
             if (K > 0) {
+                // the test loop's depths: this lane's window in the staged box if it lies inside it
+                const float *dtest = dwin;
+                long long tpitch = P.pitch;
+                if (STG) {
+                    const int ox = cx - h + kPad - org.x, oy = cy - h + kPad - org.y;
+                    if ((unsigned)ox <= (unsigned)(kBoxW - K) && (unsigned)oy <= (unsigned)(kBoxH - K)) {
+                        dtest = reinterpret_cast<const float *>(reinterpret_cast<const char *>(sgeom) +
+                                                                (stg_box(sgeom, n_slots, jj & 1) - smem_addr(sgeom))) +
+                                oy * kBoxW + ox;
+                        tpitch = kBoxW;
+                    }
+                }
                 float Ax[K > 0 ? K : 1], Bx[K > 0 ? K : 1];
 #pragma unroll
                 for (int dx = 0; dx < K; ++dx) {
@@ -182,10 +313,13 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                 for (int dy = 0; dy < K; ++dy) {
                     const float Ay = __fmaf_rn((float)dy, ify, Ay0), By = __fmaf_rn((float)dy, ziy, By0);
                     const f32x2 Ay2 = f2_pack(Ay, Ay), By2 = f2_pack(By, By);
-                    const float *drow = dwin + (long long)dy * P.pitch;
+                    const float *drow = dtest + (long long)dy * tpitch;
 #pragma unroll
                     for (int q = 0; q < KP; ++q) {
-                        const f32x2 dz = f2_sub(f2_sub(f2_pack(__ldg(drow + 2 * q), __ldg(drow + 2 * q + 1)), zh2), zl2);
+                        // staged: a generic load (shared memory, or the global plane outside the box)
+                        const float da = STG ? drow[2 * q] : __ldg(drow + 2 * q);
+                        const float db = STG ? drow[2 * q + 1] : __ldg(drow + 2 * q + 1);
+                        const f32x2 dz = f2_sub(f2_sub(f2_pack(da, db), zh2), zl2);
                         const f32x2 X = f2_fma(dz, AxP[q], BxP[q]);
                         const f32x2 Y = f2_fma(dz, Ay2, By2);
                         const f32x2 d2 = f2_fma(X, X, f2_fma(Y, Y, f2_mul(dz, dz)));
@@ -196,7 +330,7 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                     }
                     if (K & 1) {
                         constexpr int dx = K - 1;
-                        const float dz = (__ldg(drow + dx) - zh) - zl;
+                        const float dz = ((STG ? drow[dx] : __ldg(drow + dx)) - zh) - zl;
                         const float X = fmaf(dz, Ax[dx], Bx[dx]);
                         const float Y = fmaf(dz, Ay, By);
                         const float d2 = fmaf(X, X, fmaf(Y, Y, dz * dz));
@@ -357,6 +491,12 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
                 }
             }
         }
+        if (STG && stg_fail >= 0 && (int)(threadIdx.x & 31) == __ffs(G) - 1) {
+            // after a time-out: wait once more (bounded) for the copies that may still be in flight,
+            // slot stg_fail and the slot issued before its wait
+            stg_wait(stg_bar(stg_fail & 1), (unsigned)(stg_fail >> 1) & 1u);
+            if (stg_fail + 1 < n_slots) stg_wait(stg_bar((stg_fail + 1) & 1), (unsigned)((stg_fail + 1) >> 1) & 1u);
+        }
     }
 
     if (active) {
@@ -389,12 +529,19 @@ __device__ __forceinline__ void gather_pixel(const GatherArgs &a, const Planes &
 }
 
 // One CTA per 32 x kTileY output tile of one output frame (grid: tiles x output frames).
-template <int K, int CFMT, bool DEBUG, bool LEARN = false, int MINB = SSVP_MIN_CTAS>
-__global__ void __launch_bounds__(kThreads, MINB) gather_kernel(const GatherArgs a) {
+// STG: the staged gather; dynamic shared memory then holds, after the slot geometry (aligned up to
+// 128 bytes), two boxes per warp, and tmap describes the clip's depth planes.
+template <int K, int CFMT, bool DEBUG, bool LEARN = false, int MINB = SSVP_MIN_CTAS, bool STG = false>
+__global__ void __launch_bounds__(kThreads, MINB) gather_kernel(const GatherArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ float4 sgeom[];
     __shared__ float s_const[4];
     __shared__ unsigned long long s_cnt[2][kThreads / 32];
     __shared__ float s_w[kThreads / 32];
+    if (STG && (threadIdx.x & 31) == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(stg_bar(0)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(stg_bar(1)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
 
     const int oi = blockIdx.z;
     const int O = a.frame_begin + oi;
@@ -425,9 +572,9 @@ __global__ void __launch_bounds__(kThreads, MINB) gather_kernel(const GatherArgs
     const long long crop_idx = (long long)(v - a.y0) * a.cw + (u - a.x0);
     int n_acc = 0, n_exam = 0;
     float acc_w = 0.0f;
-    gather_pixel<K, CFMT, DEBUG, LEARN, 2>(a, a.clip, O, u0, v0, u, v, active, crop_idx, sgeom, a.n_slots,
-                                                       s_const[0], s_const[1], s_const[2], s_const[3] != 0.0f, n_acc,
-                                                       n_exam, acc_w);
+    gather_pixel<K, CFMT, DEBUG, LEARN, 2, STG>(a, a.clip, O, u0, v0, u, v, active, crop_idx, sgeom, a.n_slots,
+                                                s_const[0], s_const[1], s_const[2], s_const[3] != 0.0f, n_acc, n_exam,
+                                                acc_w, &tmap);
 
     // launch statistics: warp, then block, then one atomic per CTA
     unsigned long long ce = (unsigned long long)n_exam, ca = (unsigned long long)n_acc;
@@ -561,16 +708,67 @@ void *batch_fn_any(int k, int tile_rows, int cfmt) {
     return nullptr;
 }
 
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// The clip's depth planes as a 3-D FP32 tensor {pitch, rows, F} (row and frame strides in bytes are
+// multiples of 16: the pitch is a multiple of 32 floats), read in boxes of kBoxW x kBoxH x 1; reads
+// outside the tensor return NaN, which fails the radius test as the padding does.
+cudaError_t encode_depth_map(const Planes &P, CUtensorMap *m) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return cudaErrorSymbolNotFound;
+    const cuuint64_t dims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.rows, (cuuint64_t)P.F};
+    const cuuint64_t strides[2] = {(cuuint64_t)P.pitch * sizeof(float), (cuuint64_t)P.fstride * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)kBoxH, 1u}, elem[3] = {1u, 1u, 1u};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P.depth, dims, strides, box, elem,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int K, int CFMT>
 cudaError_t launch_k(const GatherArgs &a, cudaStream_t s) {
     dim3 grid((a.cw + kTileX - 1) / kTileX, (a.ch + kTileY - 1) / kTileY, a.n_out);
     size_t smem = sizeof(float4) * kSlotVec * (size_t)a.n_slots;
     const bool dbg = a.membership || a.pixel_stats;
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if (a.stage) {
+        if constexpr (K > 0 && K <= kStageMaxK) {
+            if (a.sets.col) return cudaErrorInvalidValue;
+            cudaError_t e = encode_depth_map(a.clip, &tmap);
+            if (e != cudaSuccess) return e;
+            smem += 128 + (size_t)(kThreads / 32) * 2 * kBoxBytes;
+            void (*fn)(const GatherArgs, const CUtensorMap) =
+                dbg ? gather_kernel<K, CFMT, true, false, SSVP_MIN_CTAS, true>
+                    : gather_kernel<K, CFMT, false, false, SSVP_MIN_CTAS, true>;
+            if (smem > 48 * 1024 &&
+                (e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+                return e;
+            fn<<<grid, kThreads, smem, s>>>(a, tmap);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     if (a.sets.col && a.n_slots <= kLearnShortSlots)
-        gather_kernel<K, CFMT, false, true, kLearnCtasShort><<<grid, kThreads, smem, s>>>(a);
-    else if (a.sets.col) gather_kernel<K, CFMT, false, true><<<grid, kThreads, smem, s>>>(a);
-    else if (dbg) gather_kernel<K, CFMT, true><<<grid, kThreads, smem, s>>>(a);
-    else gather_kernel<K, CFMT, false><<<grid, kThreads, smem, s>>>(a);
+        gather_kernel<K, CFMT, false, true, kLearnCtasShort><<<grid, kThreads, smem, s>>>(a, tmap);
+    else if (a.sets.col) gather_kernel<K, CFMT, false, true><<<grid, kThreads, smem, s>>>(a, tmap);
+    else if (dbg) gather_kernel<K, CFMT, true><<<grid, kThreads, smem, s>>>(a, tmap);
+    else gather_kernel<K, CFMT, false><<<grid, kThreads, smem, s>>>(a, tmap);
     return cudaGetLastError();
 }
 

@@ -92,6 +92,10 @@ struct GatherArgs {
     int32_t *pixel_stats;     // debug record per crop pixel or null
     unsigned long long *stat_counts;  // [0] examined, [1] accepted
     double *stat_sumw;
+    // window gather: 1 stages the candidate depths into shared memory by tensor copies (k <= 7);
+    // 2 as 1 but issues no copies, so that the waits run out (a test of the time-out path)
+    int stage;
+    int *err;                 // error word: bit 1 set when a staging wait timed out
 };
 
 // One clip of a batched launch (A10).  Work items are (clip, output-frame chunk, tile) triples
