@@ -20,6 +20,10 @@
  *     F*H*W floats, output F*H*W*3 floats.
  *   - Inputs are copied; the caller keeps ownership of its buffers.  The library owns its
  *     device buffers until ssvp_destroy().
+ *   - Caller buffers are checked for where they live before any work touches them: one given
+ *     as device memory (SSVP_MEM_DEVICE, or documented as a device buffer) must be device
+ *     memory of the context's device or managed memory, one given as host memory must not be
+ *     device memory; otherwise the call returns SSVP_EINVAL and queues nothing.
  *   - A context is not thread-safe: one host thread per context at a time.
  */
 #ifndef SSVP_H

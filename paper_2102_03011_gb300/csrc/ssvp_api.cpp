@@ -166,6 +166,30 @@ int cuda_fail(ssvp_ctx *c, cudaError_t e, const char *what) {
     return fail(c, SSVP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Where a caller's buffer really lives, before any work touches it.  A buffer given as device memory
+// must be device memory of the context's device (or managed memory): a kernel handed a host address
+// faults, or, where the GPU can reach host memory, reads and writes the wrong memory.  A buffer
+// given as host memory must not be device memory: the copy would name the wrong direction, and a
+// host loop reading it would crash.
+int check_mem(ssvp_ctx *ctx, const void *ptr, int mem_kind, const char *what) {
+    cudaPointerAttributes at{};
+    const cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SSVP_EINVAL, "%s: not an address CUDA can classify (%s)", what, cudaGetErrorString(e));
+    }
+    if (mem_kind == SSVP_MEM_DEVICE) {
+        if (at.type == cudaMemoryTypeManaged) return SSVP_OK;
+        if (at.type != cudaMemoryTypeDevice) return fail(ctx, SSVP_EINVAL, "%s is not device memory", what);
+        if (at.device != ctx->device)
+            return fail(ctx, SSVP_EINVAL, "%s is memory of device %d, not of the context's device %d", what, at.device,
+                        ctx->device);
+    } else if (at.type == cudaMemoryTypeDevice) {
+        return fail(ctx, SSVP_EINVAL, "%s is device memory but was given as host memory", what);
+    }
+    return SSVP_OK;
+}
+
 #define CK(call, what)                                   \
     do {                                                 \
         cudaError_t e_ = (call);                         \
@@ -428,6 +452,11 @@ int check_params(ssvp_ctx *ctx, const ssvp_params *p) {
     if (!(p->sigma_f > 0.0f && std::isfinite(p->sigma_f))) return fail(ctx, SSVP_EINVAL, "sigma_f must be > 0");
     if (!std::isfinite(p->sigma_xyz)) return fail(ctx, SSVP_EINVAL, "sigma_xyz must be finite");
     if (p->crop_w < 0 || p->crop_h < 0) return fail(ctx, SSVP_EINVAL, "negative crop size");
+    int rc;
+    if (p->membership_out && (rc = check_mem(ctx, p->membership_out, SSVP_MEM_DEVICE, "membership_out")) != SSVP_OK)
+        return rc;
+    if (p->pixel_stats_out && (rc = check_mem(ctx, p->pixel_stats_out, SSVP_MEM_DEVICE, "pixel_stats_out")) != SSVP_OK)
+        return rc;
     return SSVP_OK;
 }
 
@@ -754,6 +783,9 @@ int ssvp_load_clip(ssvp_ctx *ctx, int clip_id, int W, int H, int F, const float 
     if (colour_fmt != SSVP_COLOUR_F32 && colour_fmt != SSVP_COLOUR_F16)
         return fail(ctx, SSVP_EINVAL, "bad colour_fmt %d", colour_fmt);
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc;
+    if ((rc = check_mem(ctx, rgb, mem_kind, "rgb")) != SSVP_OK || (rc = check_mem(ctx, depth, mem_kind, "depth")) != SSVP_OK)
+        return rc;
     Clip &c = ctx->clips[clip_id];
     // a reload with the same shape and format keeps the planes (and the inpainting mask, if one is
     // set): the work queued on the context's stream that still reads them runs before the upload
@@ -918,6 +950,8 @@ int ssvp_append_frames(ssvp_ctx *ctx, int clip_id, int n, const float *rgb, cons
     int rc = checked_cameras(ctx, n, K, per_frame_K, w2c, Kn, Wn);
     if (rc != SSVP_OK) return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((rc = check_mem(ctx, rgb, mem_kind, "rgb")) != SSVP_OK || (rc = check_mem(ctx, depth, mem_kind, "depth")) != SSVP_OK)
+        return rc;
     Planes &p = c.p;
     const size_t texel = p.colour_fmt == SSVP_COLOUR_F32 ? 16 : 8;
     const size_t nplane = (size_t)F * (size_t)p.fstride;
@@ -1169,6 +1203,7 @@ int ssvp_superres(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, int sca
         return fail(ctx, SSVP_EINVAL, "super-resolution weights are Eq. 7 (SSVP_MODE_DENOISE) or w = 1 (SSVP_MODE_MEAN)");
     if (scale < 1 || scale > 8) return fail(ctx, SSVP_EINVAL, "scale=%d must be in [1, 8]", scale);
     if (!out) return fail(ctx, SSVP_EINVAL, "out is NULL");
+    if ((rc = check_mem(ctx, out, SSVP_MEM_DEVICE, "out")) != SSVP_OK) return rc;
     if (!(p.frustum_l > 0.0f && p.frustum_l <= 64.0f)) return fail(ctx, SSVP_EINVAL, "frustum_l must be in (0, 64]");
     if (!(p.near_plane > 0.0f && p.far_plane > p.near_plane && std::isfinite(p.far_plane)))
         return fail(ctx, SSVP_EINVAL, "need 0 < near_plane < far_plane < inf");
@@ -1262,6 +1297,7 @@ int ssvp_set_mask(ssvp_ctx *ctx, int clip_id, const uint8_t *mask, int mem_kind)
     if (!mask) return fail(ctx, SSVP_EINVAL, "mask is NULL");
     if (mem_kind != SSVP_MEM_HOST && mem_kind != SSVP_MEM_DEVICE) return fail(ctx, SSVP_EINVAL, "bad mem_kind %d", mem_kind);
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((rc = check_mem(ctx, mask, mem_kind, "mask")) != SSVP_OK) return rc;
     if ((rc = ensure_mask(ctx, *c)) != SSVP_OK) return rc;
     const Planes &p = c->p;
     for (int f = 0; f < p.F; ++f)
@@ -1365,6 +1401,8 @@ int ssvp_read_output(ssvp_ctx *ctx, int clip_id, int frame_begin, int frame_end,
         return fail(ctx, SSVP_EINVAL, "frame range [%d, %d) outside the clip", frame_begin, frame_end);
     if (mem_kind != SSVP_MEM_HOST && mem_kind != SSVP_MEM_DEVICE) return fail(ctx, SSVP_EINVAL, "bad mem_kind %d", mem_kind);
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = check_mem(ctx, dst, mem_kind, "dst");
+    if (rc != SSVP_OK) return rc;
     const size_t per = (size_t)c.p.W * c.p.H * 3;
     const size_t bytes = per * (size_t)(frame_end - frame_begin) * sizeof(float);
     if (bytes) {
@@ -1656,6 +1694,11 @@ int ssvp_learned_samples(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, 
     if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
     if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_id);
     if (!feat || !col || !nsamp || !plain) return fail(ctx, SSVP_EINVAL, "output buffers must not be NULL");
+    if ((rc = check_mem(ctx, feat, SSVP_MEM_DEVICE, "feat")) != SSVP_OK ||
+        (rc = check_mem(ctx, col, SSVP_MEM_DEVICE, "col")) != SSVP_OK ||
+        (rc = check_mem(ctx, nsamp, SSVP_MEM_DEVICE, "nsamp")) != SSVP_OK ||
+        (rc = check_mem(ctx, plain, SSVP_MEM_DEVICE, "plain")) != SSVP_OK)
+        return rc;
     const ssvp_params &p = *params;
     if (p.frame_begin < 0 || p.frame_begin >= c.p.F) return fail(ctx, SSVP_EINVAL, "frame %d outside the clip", p.frame_begin);
     if (p.k > 7) return fail(ctx, SSVP_EINVAL, "the learned filter supports k <= 7");
@@ -1681,6 +1724,10 @@ int ssvp_mlp_grad(ssvp_ctx *ctx, const ssvp_params *params, int clip_id, const i
     if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
     if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_id);
     if (!pixels || n_pixels < 1 || !clean || !grad_out) return fail(ctx, SSVP_EINVAL, "bad pixel list or buffers");
+    if ((rc = check_mem(ctx, pixels, SSVP_MEM_HOST, "pixels")) != SSVP_OK ||
+        (rc = check_mem(ctx, clean, SSVP_MEM_DEVICE, "clean")) != SSVP_OK ||
+        (rc = check_mem(ctx, grad_out, SSVP_MEM_HOST, "grad_out")) != SSVP_OK)
+        return rc;
     if (params->k > 7) return fail(ctx, SSVP_EINVAL, "the learned filter supports k <= 7");
     const int O = params->frame_begin;
     if (O < 0 || O >= c.p.F) return fail(ctx, SSVP_EINVAL, "frame %d outside the clip", O);
@@ -1735,6 +1782,7 @@ int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, co
         if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_ids[i]);
         if (!c.has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_ids[i]);
         if (!clean[i]) return fail(ctx, SSVP_EINVAL, "clean target of clip %d is NULL", clip_ids[i]);
+        if ((rc = check_mem(ctx, clean[i], SSVP_MEM_DEVICE, "clean target")) != SSVP_OK) return rc;
         max_px = std::max(max_px, (size_t)c.p.W * c.p.H);
     }
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");

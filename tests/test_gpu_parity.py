@@ -297,6 +297,37 @@ def test_argument_errors(sess, tiny):
     assert e.value.code == ss.SSVP_EINVAL
 
 
+def test_buffers_in_the_wrong_memory_are_refused(sess, tiny):
+    """Every buffer is checked for where it lives before any work touches it: host memory given as
+    device memory (which a kernel would fault on), device memory given as host memory, and debug
+    or output buffers that are not device memory are SSVP_EINVAL, and the context goes on working."""
+    ss, t = sess.ss, sess.torch
+    sess.load(0, tiny)
+    want = sess.run(0, 4, k=5, half_window=2).rgb
+    W, H, F = tiny.W, tiny.H, tiny.F
+    rgb_d = t.from_numpy(tiny.rgb).to(sess.dev)
+    dep_d = t.from_numpy(tiny.depth).to(sess.dev)
+    cases = [
+        lambda: ss.ssvp_load_clip(sess.ctx, 17, W, H, F, tiny.rgb, tiny.depth, ss.SSVP_MEM_DEVICE),
+        lambda: ss.ssvp_load_clip(sess.ctx, 17, W, H, F, rgb_d, dep_d, ss.SSVP_MEM_HOST),
+        lambda: ss.ssvp_load_clip(sess.ctx, 17, W, H, F, rgb_d, tiny.depth, ss.SSVP_MEM_DEVICE),
+        lambda: ss.ssvp_read_output(sess.ctx, 0, 4, 5, np.zeros((1, H, W, 3), np.float32), ss.SSVP_MEM_DEVICE),
+        lambda: ss.ssvp_read_output(sess.ctx, 0, 4, 5, t.zeros((1, H, W, 3), device=sess.dev), ss.SSVP_MEM_HOST),
+        lambda: ss.ssvp_superres(sess.ctx, sess.params(gather=ss.SSVP_GATHER_FRUSTUM, frame_begin=4, frame_end=5), 0,
+                                 2, np.zeros((1, 2 * H, 2 * W, 3), np.float32).ctypes.data),
+    ]
+    host_rec = np.zeros((H, W, 5, 4), np.int32)
+    p = sess.params(k=5, half_window=2, frame_begin=4, frame_end=5)
+    p.membership_out = host_rec.ctypes.data
+    cases.append(lambda: ss.ssvp_gather_filter(sess.ctx, p, [0]))
+    for call in cases:
+        with pytest.raises(ss.SsvpError) as e:
+            call()
+        assert e.value.code == ss.SSVP_EINVAL and "memory" in str(e.value)
+    assert not host_rec.any()
+    np.testing.assert_array_equal(sess.run(0, 4, k=5, half_window=2).rgb, want)
+
+
 def test_full_size_sampled_against_oracle(sess):
     """1920x1080, +-30 frames, k = 7 in the benchmark's launch (all pixels of the output frame,
     no debug outputs); sampled crops compared with the oracle."""
