@@ -187,3 +187,37 @@ def test_staged_copy_wait_time_out(sess):
     np.testing.assert_array_equal(out[0, y0:y0 + ch, x0:x0 + cw].cpu().numpy(), want)
     g = _staged_and_plain(sess, 9, 8, crop=crop, k=5, half_window=3)
     np.testing.assert_array_equal(g.rgb, want)
+
+
+def test_staged_frame_weight_modes(sess):
+    """Deblurring (Eq. 5) and the shutter (Eq. 10) through the staged gather: identical to the
+    window gather, and the deblurred frame against the oracle."""
+    ss = sess.ss
+    room = synth.make_clip("room", 96, 54, 9, seed=7)
+    sess.load(10, room)
+    g = _staged_and_plain(sess, 10, 4, k=5, half_window=4, mode=ss.SSVP_MODE_DEBLUR, radius=-0.03)
+    g_w = oracle.frame_sharpness(oracle.ClipView.of(room))
+    o = oracle.gather_filter(oracle.ClipView.of(room),
+                             oracle_params(oracle.median_depth(room.depth), 5, 4, mode=oracle.MODE_DEBLUR,
+                                           radius_rel=0.03, frame_w=g_w / g_w.max()), 4, membership=True)
+    compare(g, o, 5)
+    xi = np.array([0.5 ** abs(4 - j) for j in range(9)], np.float32)
+    ss.ssvp_set_shutter(sess.ctx, xi, 4)
+    _staged_and_plain(sess, 10, 4, k=7, half_window=4, mode=ss.SSVP_MODE_SHUTTER)
+
+
+def test_staged_gather_after_streaming_appends(sess):
+    """After ssvp_append_frames the clip's planes live in its second window: the staged gather
+    copies from the planes of the current window (its tensor map is made per launch)."""
+    ss, t = sess.ss, sess.torch
+    W, H, F, N = 96, 54, 9, 3
+    video = synth.make_clip("room", W, H, F + 2 * N, seed=6)
+    sl = slice(0, F)
+    sess.load(11, synth.Clip(W, H, F, video.K[sl], video.w2c[sl], video.w2c_true[sl], video.rgb[sl],
+                             video.depth[sl], video.clean[sl], video.depth_true[sl]))
+    for i in range(2):
+        new = slice(F + i * N, F + (i + 1) * N)
+        ss.ssvp_append_frames(sess.ctx, 11, N, np.ascontiguousarray(video.rgb[new]),
+                              np.ascontiguousarray(video.depth[new]), video.K[new], 1, video.w2c[new])
+        for O in (2, F - 1):
+            _staged_and_plain(sess, 11, O, membership=False, k=7, half_window=4)
