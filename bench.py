@@ -185,7 +185,7 @@ class ClockSampler:
 
     def summary(self):
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         for line in (self.out or "").splitlines():
             f = [x.strip() for x in line.split(",")]
             if len(f) < 7:
@@ -195,13 +195,18 @@ class ClockSampler:
                 mx.append(float(f[1]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(f[2]))
+            except ValueError:
+                pass
             for n, v in zip(names, f[3:7]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "sm_mhz_min": float(min(sm)),
+                "power_w_median": float(np.median(pw)) if pw else None}
 
 
 def _workload_clip(seed, frames=None):
@@ -1163,14 +1168,15 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    stream2.wait_event(e0)
-    e2e_run(e2e_steps)
-    done2 = torch.cuda.Event()
-    done2.record(stream2)
-    stream.wait_event(done2)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(local) as clk_e2e:
+        e0.record(stream)
+        stream2.wait_event(e0)
+        e2e_run(e2e_steps)
+        done2 = torch.cuda.Event()
+        done2.record(stream2)
+        stream.wait_event(done2)
+        e1.record(stream)
+        torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
     ss.ssvp_destroy(ctx2)
     h2d = clip.rgb.nbytes + clip.depth.nbytes
@@ -1183,7 +1189,7 @@ def main():
     e2e_full = {"value": world * mpix / (e2e_ms / 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "gpu_launches_per_step": e2e_launches,
                 "pipelining": "two contexts on two streams, step i + 1 queued before step i is read back",
-                "inputs": "the whole clip uploaded every step (ssvp_load_clip)"}
+                "inputs": "the whole clip uploaded every step (ssvp_load_clip)", "clocks": clk_e2e.summary()}
     e2e_stream = None
     if MODE in (0, 1, 5, 6) and not args.no_stream:
         # Streaming video: a longer clip of the same scene family arrives N_OUT frames at a time.  A
