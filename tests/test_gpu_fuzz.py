@@ -1,0 +1,74 @@
+"""Seeded random parity cases of the window gathers against the FP64 oracle: clip shapes from one
+pixel up, windows reaching past the clip's ends, odd crops, radii from tight to loose, invalid
+depths, both colour formats, the denoise and mean modes and both window gathers (global loads and
+TMA-staged boxes).  Every case must pass the same membership and colour comparison as the fixed
+parity tests; the draws are fixed by the seed, so a failure names a reproducible case."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import Session, compare, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+N_CASES = 32
+
+
+@pytest.fixture(scope="module")
+def sess():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    s = Session()
+    yield s
+    s.close()
+
+
+def _case(i):
+    rng = np.random.default_rng(9000 + i)
+    W, H = int(rng.integers(1, 90)), int(rng.integers(1, 60))
+    F = int(rng.integers(1, 9))
+    k = int(rng.choice([1, 3, 5, 7, 9, 11]))
+    return dict(
+        preset=str(rng.choice(["planes3", "room"])), W=W, H=H, F=F, seed=int(rng.integers(0, 1000)), k=k,
+        T=int(rng.integers(0, F + 3)), O=int(rng.integers(0, F)),
+        x0=int(rng.integers(0, max(1, W // 2))), y0=int(rng.integers(0, max(1, H // 2))),
+        radius_rel=float(rng.choice([0.002, 0.005, 0.02, 0.05])),
+        mode=int(rng.choice([oracle.MODE_DENOISE, oracle.MODE_MEAN])), cfmt=int(rng.integers(0, 2)),
+        bad_frac=float(rng.choice([0.0, 0.0, 0.1])), staged=bool(k <= 7 and rng.integers(0, 2)),
+        bad_seed=int(rng.integers(0, 1 << 30)), cw_frac=0.3 + 0.7 * float(rng.random()),
+        ch_frac=0.3 + 0.7 * float(rng.random()))
+
+
+@pytest.mark.parametrize("i", range(N_CASES))
+def test_random_case_matches_the_oracle(sess, i):
+    c = _case(i)
+    clip = synth.make_clip(c["preset"], c["W"], c["H"], c["F"], seed=c["seed"])
+    depth = clip.depth.copy()
+    if c["bad_frac"]:
+        rng = np.random.default_rng(c["bad_seed"])
+        bad = rng.random(depth.shape) < c["bad_frac"]
+        depth[bad] = np.array([np.nan, 0.0, -1.0, np.inf], np.float32)[rng.integers(0, 4, int(bad.sum()))]
+    rgb = clip.rgb if c["cfmt"] == 0 else clip.rgb.astype(np.float16).astype(np.float32)
+    v = synth.Clip(clip.W, clip.H, clip.F, clip.K, clip.w2c, clip.w2c_true, rgb, depth, clip.clean, clip.depth_true)
+    sess.load(30 + i % 8, v, colour_fmt=c["cfmt"])
+    x0, y0 = c["x0"], c["y0"]
+    cw = max(1, int(round((c["W"] - x0) * c["cw_frac"])))
+    ch = max(1, int(round((c["H"] - y0) * c["ch_frac"])))
+    crop = (x0, y0, cw, ch)
+    ss = sess.ss
+    g = sess.run(30 + i % 8, c["O"], crop=crop, membership=True, k=c["k"], half_window=c["T"], mode=c["mode"],
+                 radius=-c["radius_rel"],
+                 gather=ss.SSVP_GATHER_WINDOW_TMA if c["staged"] else ss.SSVP_GATHER_WINDOW)
+    med = oracle.median_depth(depth)
+    if not np.isfinite(med):
+        # no valid depth anywhere: every pixel keeps its own colour
+        np.testing.assert_array_equal(g.rgb, rgb[c["O"], y0:y0 + ch, x0:x0 + cw])
+        return
+    o = oracle.gather_filter(oracle.ClipView.of(v), oracle_params(med, c["k"], c["T"], mode=c["mode"],
+                                                                  radius_rel=c["radius_rel"]),
+                             c["O"], crop=crop, membership=True)
+    compare(g, o, c["k"])
