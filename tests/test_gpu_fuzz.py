@@ -1,14 +1,15 @@
-"""Seeded random parity cases of the window gathers against the FP64 oracle: clip shapes from one
-pixel up, windows reaching past the clip's ends, odd crops, radii from tight to loose, invalid
-depths, both colour formats, the denoise and mean modes and both window gathers (global loads and
-TMA-staged boxes).  Every case must pass the same membership and colour comparison as the fixed
+"""Seeded random parity cases of the gathers against the FP64 oracle: clip shapes from one pixel
+up, windows reaching past the clip's ends, odd crops, radii from tight to loose, invalid depths,
+both colour formats, the denoise and mean modes and both window gathers (global loads and
+TMA-staged boxes); the virtual-aperture and frustum gathers with random caps, lens radii, focal
+depths, frustum sizes and near / far planes.  Every case must pass the same membership and colour comparison as the fixed
 parity tests; the draws are fixed by the seed, so a failure names a reproducible case."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from _gpu import Session, compare, oracle_params
+from _gpu import Session, compare, compare_aperture, compare_frustum, oracle_params, run_frustum
 
 pytestmark = pytest.mark.gpu
 
@@ -72,3 +73,67 @@ def test_random_case_matches_the_oracle(sess, i):
                                                                   radius_rel=c["radius_rel"]),
                              c["O"], crop=crop, membership=True)
     compare(g, o, c["k"])
+
+
+def _crop(c):
+    x0, y0 = c["x0"], c["y0"]
+    return (x0, y0, max(1, int(round((c["W"] - x0) * c["cw_frac"]))), max(1, int(round((c["H"] - y0) * c["ch_frac"]))))
+
+
+def _clip(c):
+    clip = synth.make_clip(c["preset"], c["W"], c["H"], c["F"], seed=c["seed"])
+    depth = clip.depth.copy()
+    if c["bad_frac"]:
+        rng = np.random.default_rng(c["bad_seed"])
+        bad = rng.random(depth.shape) < c["bad_frac"]
+        depth[bad] = np.array([np.nan, 0.0, -1.0, np.inf], np.float32)[rng.integers(0, 4, int(bad.sum()))]
+    return synth.Clip(clip.W, clip.H, clip.F, clip.K, clip.w2c, clip.w2c_true, clip.rgb, depth, clip.clean,
+                      clip.depth_true)
+
+
+@pytest.mark.parametrize("i", range(12))
+def test_random_aperture_case_matches_the_oracle(sess, i):
+    """The virtual-aperture gather (Eq. 13-14) on random shapes, caps, windows, lens radii and
+    focal depths."""
+    c = _case(100 + i)
+    rng = np.random.default_rng(7000 + i)
+    v = _clip(c)
+    med = oracle.median_depth(v.depth)
+    if not np.isfinite(med):
+        return
+    cap = int(rng.choice([1, 3, 9, 15, 31]))
+    aperture = float(rng.choice([0.0, 0.02, 0.05, 0.1]))
+    focal = float(med * rng.choice([0.5, 1.0, 2.0]))
+    lens = int(rng.choice([1, 4, 16, 64]))
+    sess.load(40 + i % 4, v)
+    crop = _crop(c)
+    g = sess.run(40 + i % 4, c["O"], crop=crop, membership=True, mode=1, k=c["k"], half_window=c["T"],
+                 aperture=aperture, focal_depth=focal, cap=cap, lens_samples=lens)
+    prm = oracle.Params(mode=oracle.MODE_APERTURE, k=c["k"], T=c["T"], aperture=aperture, focal_depth=focal,
+                        lens_samples=lens, cap=cap)
+    o = oracle.gather_filter(oracle.ClipView.of(v), prm, c["O"], crop=crop, membership=True)
+    compare_aperture(g, o, cap)
+
+
+@pytest.mark.parametrize("i", range(12))
+def test_random_frustum_case_matches_the_oracle(sess, i):
+    """The paper's frustum gather (Eq. 1-2) on random shapes, frustum sizes, windows and near /
+    far planes, denoise and mean modes."""
+    c = _case(200 + i)
+    rng = np.random.default_rng(8000 + i)
+    v = _clip(c)
+    med = oracle.median_depth(v.depth)
+    if not np.isfinite(med):
+        return
+    l = float(rng.choice([1.0, 2.5, 3.0, 5.0]))
+    near, far = (0.01, 1000.0) if rng.integers(0, 2) else (0.6 * med, 1.5 * med)
+    prm = oracle.Params(mode=c["mode"], k=1, T=c["T"], radius=0.005 * med, sigma_xyz=0.03 * med,
+                        gather=oracle.GATHER_FRUSTUM, frustum_l=l, near_plane=near, far_plane=far)
+    sess.load(44 + i % 4, v)
+    crop = _crop(c)
+    g = run_frustum(sess, 44 + i % 4, c["O"], crop=crop, membership=True, half_window=c["T"], mode=c["mode"],
+                    frustum_l=l, sigma_xyz=prm.sigma_xyz, near_plane=near, far_plane=far)
+    o = oracle.frustum_filter(oracle.ClipView.of(v), prm, c["O"], crop=crop, membership=True)
+    x0, y0, cw, ch = crop
+    d = v.depth[c["O"], y0:y0 + ch, x0:x0 + cw]
+    compare_frustum(g, o, np.isfinite(d) & (d > 0))
