@@ -2,7 +2,8 @@
 up, windows reaching past the clip's ends, odd crops, radii from tight to loose, invalid depths,
 both colour formats, the denoise and mean modes and both window gathers (global loads and
 TMA-staged boxes); the virtual-aperture and frustum gathers with random caps, lens radii, focal
-depths, frustum sizes and near / far planes.  Every case must pass the same membership and colour comparison as the fixed
+depths, frustum sizes and near / far planes; the learned weighting with random networks,
+confidence thresholds and set sizes.  Every case must pass the same membership and colour comparison as the fixed
 parity tests; the draws are fixed by the seed, so a failure names a reproducible case."""
 import numpy as np
 import pytest
@@ -137,3 +138,39 @@ def test_random_frustum_case_matches_the_oracle(sess, i):
     x0, y0, cw, ch = crop
     d = v.depth[c["O"], y0:y0 + ch, x0:x0 + cw]
     compare_frustum(g, o, np.isfinite(d) & (d > 0))
+
+
+@pytest.mark.parametrize("i", range(10))
+def test_random_learned_case_matches_the_oracle(sess, i):
+    """The learned weighting (capped sets, tcgen05 inference, plain fallback) on random shapes,
+    windows, radii (up to sets past the 64-sample cap), networks and confidence thresholds, pixel
+    by pixel against the oracle with the tensor cores' BF16 rounding."""
+    rng = np.random.default_rng(6000 + i)
+    W, H, F = int(rng.integers(8, 70)), int(rng.integers(4, 40)), int(rng.integers(2, 9))
+    k, T, O = int(rng.choice([1, 3, 5, 7, 7])), int(rng.integers(1, F + 2)), int(rng.integers(0, F))
+    radius_rel = float(rng.choice([0.005, 0.05, 0.1, 0.2]))
+    tau = float(rng.choice([0.0, 0.5, 0.5, 2.0]))
+    clip = synth.make_clip(str(rng.choice(["planes3", "room"])), W, H, F, seed=int(rng.integers(0, 1000)))
+    x0, y0 = int(rng.integers(0, W // 2)), int(rng.integers(0, H // 2))
+    crop = (x0, y0, max(1, int((W - x0) * (0.3 + 0.7 * rng.random()))), max(1, int((H - y0) * (0.3 + 0.7 * rng.random()))))
+    W1, b1, W2, b2 = oracle.he_init(int(rng.integers(0, 1000)))
+    b1 = rng.normal(0, 0.1, 64)
+    b2 = np.array([rng.normal(0, 0.5), rng.normal(0.5, 1.0)])
+    sess.load(50 + i % 4, clip)
+    sess.ss.ssvp_set_mlp(sess.ctx, W1, b1, W2, b2)
+    g = sess.run(50 + i % 4, O, crop=crop, mode=2, k=k, half_window=T, radius=-radius_rel, conf_threshold=tau)
+    prm = oracle.default_params(clip.depth, k=k, T=T, radius_rel=radius_rel)
+    of, oc, on, op = oracle.learned_crop(oracle.ClipView.of(clip), prm, O, crop=crop)
+    o = oracle.gather_filter(oracle.ClipView.of(clip), prm, O, crop=crop, membership=True)
+    flagged = ((o.codes & oracle.CODE_BAND) != 0).any(axis=(-1, -2, -3)) | ((o.amb == 1) & (o.status == 1)).any(-1)
+    worst = 0.0
+    for y in range(crop[3]):
+        for x in range(crop[2]):
+            if flagged[y, x]:
+                continue
+            _, ofin, conf, _ = oracle.mlp_pixel(of[y, x], oc[y, x], on[y, x], W1, b1, W2, b2, round_bf16=True,
+                                                tau=tau, plain=op[y, x])
+            if on[y, x] > 0 and abs(conf - tau) < 1e-3:
+                continue  # the fallback decision is a tie between FP32 and FP64
+            worst = max(worst, float(np.abs(g.rgb[y, x] - ofin).max()))
+    assert worst <= 1e-3, worst
