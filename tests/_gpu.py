@@ -268,3 +268,17 @@ def compare_flagged(rgb: np.ndarray, o: oracle.Result):
         f"colour max abs {cerr[ok].max()} > {COLOUR_TOL} at {np.argwhere(ok & (cerr > COLOUR_TOL))[:5]}"
     return dict(pixels=int(ok.size), flagged=int((~ok).sum()), differing=int((cerr > COLOUR_TOL).sum()),
                 max_colour_err=float(cerr[ok].max(initial=0.0)), max_colour_err_all=float(cerr.max()))
+
+
+def superres_ref_valid(c, O, scale, crop):
+    """Validity of super-resolution's bilinear reference depth per output-grid pixel of the crop:
+    all four input pixels valid (coordinates clamped to the image)."""
+    Wo, Ho = c.W * scale, c.H * scale
+    x0, y0, cw, ch = crop if crop is not None else (0, 0, Wo, Ho)
+    U = np.clip((np.arange(x0, x0 + cw) + 0.5) / scale - 0.5, 0, c.W - 1)
+    V = np.clip((np.arange(y0, y0 + ch) + 0.5) / scale - 0.5, 0, c.H - 1)
+    ux0, vy0 = np.floor(U).astype(int), np.floor(V).astype(int)
+    ux1, vy1 = np.minimum(ux0 + 1, c.W - 1), np.minimum(vy0 + 1, c.H - 1)
+    d = c.depth[O]
+    ok = np.isfinite(d) & (d > 0)
+    return ok[vy0][:, ux0] & ok[vy0][:, ux1] & ok[vy1][:, ux0] & ok[vy1][:, ux1]

@@ -3,14 +3,16 @@ up, windows reaching past the clip's ends, odd crops, radii from tight to loose,
 both colour formats, the denoise and mean modes and both window gathers (global loads and
 TMA-staged boxes); the virtual-aperture and frustum gathers with random caps, lens radii, focal
 depths, frustum sizes and near / far planes; the learned weighting with random networks,
-confidence thresholds and set sizes.  Every case must pass the same membership and colour comparison as the fixed
+confidence thresholds and set sizes; super-resolution, inpainting and semi-transparency with random
+scales, painted masks and crops.  Every case must pass the same membership and colour comparison as the fixed
 parity tests; the draws are fixed by the seed, so a failure names a reproducible case."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from _gpu import Session, compare, compare_aperture, compare_frustum, oracle_params, run_frustum
+from _gpu import (Session, compare, compare_aperture, compare_frustum, oracle_params, run_frustum, run_superres,
+                  superres_ref_valid)
 
 pytestmark = pytest.mark.gpu
 
@@ -174,3 +176,72 @@ def test_random_learned_case_matches_the_oracle(sess, i):
                 continue  # the fallback decision is a tie between FP32 and FP64
             worst = max(worst, float(np.abs(g.rgb[y, x] - ofin).max()))
     assert worst <= 1e-3, worst
+
+
+@pytest.mark.parametrize("i", range(8))
+def test_random_superres_case_matches_the_oracle(sess, i):
+    """Super-resolution (Eq. 6-7) on random shapes, scales 1-4, frustum sizes, windows and
+    output-grid crops, with invalid depths in some cases."""
+    rng = np.random.default_rng(5000 + i)
+    W, H, F = int(rng.integers(6, 48)), int(rng.integers(4, 30)), int(rng.integers(1, 7))
+    scale, l = int(rng.choice([1, 2, 3, 4])), float(rng.choice([1.0, 2.0, 3.0]))
+    T, O = int(rng.integers(0, F + 1)), int(rng.integers(0, F))
+    mode = int(rng.choice([oracle.MODE_DENOISE, oracle.MODE_MEAN]))
+    c = dict(preset=str(rng.choice(["planes3", "room"])), W=W, H=H, F=F, seed=int(rng.integers(0, 1000)),
+             bad_frac=float(rng.choice([0.0, 0.05])), bad_seed=int(rng.integers(0, 1 << 30)))
+    v = _clip(c)
+    med = oracle.median_depth(v.depth)
+    if not np.isfinite(med):
+        return
+    Wo, Ho = W * scale, H * scale
+    x0, y0 = int(rng.integers(0, Wo // 2 + 1)), int(rng.integers(0, Ho // 2 + 1))
+    crop = (x0, y0, max(1, int((Wo - x0) * (0.3 + 0.7 * rng.random()))), max(1, int((Ho - y0) * (0.3 + 0.7 * rng.random()))))
+    p = oracle.Params(mode=mode, k=1, T=T, radius=0.005 * med, sigma_rgb=50.0 / 255.0, sigma_xyz=0.03 * med,
+                      gather=oracle.GATHER_FRUSTUM, frustum_l=l)
+    sess.load(54 + i % 4, v)
+    g = run_superres(sess, 54 + i % 4, O, scale, crop=crop, membership=True, half_window=T, mode=mode, frustum_l=l,
+                     sigma_rgb=p.sigma_rgb, sigma_xyz=p.sigma_xyz)
+    o = oracle.superres_filter(oracle.ClipView.of(v), p, O, scale, crop=crop, membership=True)
+    compare_frustum(g, o, superres_ref_valid(v, O, scale, crop))
+
+
+@pytest.mark.parametrize("i", range(8))
+def test_random_inpaint_case_matches_the_oracle(sess, i):
+    """Inpainting and semi-transparency (Eq. 8-9 and the variant after it) with random painted
+    masks (discs drifting over the frames), windows, crops and Eq. 4 scales."""
+    rng = np.random.default_rng(4000 + i)
+    W, H, F = int(rng.integers(16, 64)), int(rng.integers(10, 40)), int(rng.integers(2, 8))
+    T, O = int(rng.integers(1, F + 1)), int(rng.integers(0, F))
+    semi = bool(rng.integers(0, 2))
+    c = dict(preset=str(rng.choice(["planes3", "room"])), W=W, H=H, F=F, seed=int(rng.integers(0, 1000)),
+             bad_frac=float(rng.choice([0.0, 0.05])), bad_seed=int(rng.integers(0, 1 << 30)))
+    v = _clip(c)
+    med = oracle.median_depth(v.depth)
+    if not np.isfinite(med):
+        return
+    yy, xx = np.mgrid[0:H, 0:W]
+    cx, cy, r = rng.uniform(0, W), rng.uniform(0, H), rng.uniform(2, max(3, min(W, H) / 2))
+    vx, vy = rng.uniform(-2, 2), rng.uniform(-1, 1)
+    mask = np.stack([((xx - cx - vx * f) ** 2 + (yy - cy - vy * f) ** 2 < r * r) for f in range(F)]).astype(np.uint8)
+    # a crop around the disc as it lies in frame O (clipped to the image)
+    ox, oy = cx + vx * O, cy + vy * O
+    x0 = int(np.clip(ox - r - rng.integers(0, 4), 0, W - 1))
+    y0 = int(np.clip(oy - r - rng.integers(0, 4), 0, H - 1))
+    crop = (x0, y0, int(np.clip(2 * r + rng.integers(1, 8), 1, W - x0)), int(np.clip(2 * r + rng.integers(1, 8), 1, H - y0)))
+    cid = 58 + i % 4
+    sess.load(cid, v)
+    sess.ss.ssvp_set_mask(sess.ctx, cid, mask)
+    if semi:
+        sx = float(med * rng.choice([0.01, 0.03, 0.1]))
+        g = run_frustum(sess, cid, O, crop=crop, membership=True, half_window=T, mode=sess.ss.SSVP_MODE_SEMI,
+                        sigma_rgb=80.0 / 255.0, sigma_xyz=sx)
+        prm = oracle.Params(mode=oracle.MODE_DENOISE, k=1, T=T, radius=0.01, sigma_rgb=80.0 / 255.0, sigma_xyz=sx,
+                            gather=oracle.GATHER_FRUSTUM, frustum_l=3.0)
+    else:
+        g = run_frustum(sess, cid, O, crop=crop, membership=True, half_window=T, mode=sess.ss.SSVP_MODE_INPAINT,
+                        sigma_rgb=55.0 / 255.0)
+        prm = oracle.Params(mode=oracle.MODE_DENOISE, k=1, T=T, radius=0.01, sigma_rgb=55.0 / 255.0,
+                            gather=oracle.GATHER_FRUSTUM, frustum_l=3.0)
+    o = oracle.inpaint_filter(oracle.ClipView.of(v), prm, mask, O, crop=crop, membership=True, semi=semi)
+    x0, y0, cw, ch = crop
+    compare_frustum(g, o, mask[O, y0:y0 + ch, x0:x0 + cw] != 0)

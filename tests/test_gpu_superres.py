@@ -7,6 +7,7 @@ import pytest
 import oracle
 import synth
 from _gpu import COLOUR_TOL, Session, compare_frustum, run_superres
+from _gpu import superres_ref_valid as _ref_valid
 
 pytestmark = pytest.mark.gpu
 
@@ -35,19 +36,6 @@ def _both(sess, c, cid, O, T, scale, mode=0, l=3.0, crop=None):
                      sigma_rgb=p.sigma_rgb, sigma_xyz=p.sigma_xyz)
     o = oracle.superres_filter(oracle.ClipView.of(c), p, O, scale, crop=crop, membership=True)
     return g, o
-
-
-def _ref_valid(c, O, scale, crop):
-    """Validity of the bilinear reference depth: all four input pixels valid (clamped)."""
-    Wo, Ho = c.W * scale, c.H * scale
-    x0, y0, cw, ch = crop if crop is not None else (0, 0, Wo, Ho)
-    U = np.clip((np.arange(x0, x0 + cw) + 0.5) / scale - 0.5, 0, c.W - 1)
-    V = np.clip((np.arange(y0, y0 + ch) + 0.5) / scale - 0.5, 0, c.H - 1)
-    ux0, vy0 = np.floor(U).astype(int), np.floor(V).astype(int)
-    ux1, vy1 = np.minimum(ux0 + 1, c.W - 1), np.minimum(vy0 + 1, c.H - 1)
-    d = c.depth[O]
-    ok = np.isfinite(d) & (d > 0)
-    return ok[vy0][:, ux0] & ok[vy0][:, ux1] & ok[vy1][:, ux0] & ok[vy1][:, ux1]
 
 
 @pytest.mark.parametrize("scale", [2, 3])
