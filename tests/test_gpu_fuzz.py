@@ -4,15 +4,15 @@ both colour formats, the denoise and mean modes and both window gathers (global 
 TMA-staged boxes); the virtual-aperture and frustum gathers with random caps, lens radii, focal
 depths, frustum sizes and near / far planes; the learned weighting with random networks,
 confidence thresholds and set sizes; super-resolution, inpainting and semi-transparency with random
-scales, painted masks and crops.  Every case must pass the same membership and colour comparison as the fixed
+scales, painted masks and crops; batched plans over random sets of uneven clips.  Every case must pass the same membership and colour comparison as the fixed
 parity tests; the draws are fixed by the seed, so a failure names a reproducible case."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from _gpu import (Session, compare, compare_aperture, compare_frustum, oracle_params, run_frustum, run_superres,
-                  superres_ref_valid)
+from _gpu import (Session, compare, compare_aperture, compare_flagged, compare_frustum, oracle_params, run_frustum,
+                  run_superres, superres_ref_valid)
 
 pytestmark = pytest.mark.gpu
 
@@ -245,3 +245,49 @@ def test_random_inpaint_case_matches_the_oracle(sess, i):
     o = oracle.inpaint_filter(oracle.ClipView.of(v), prm, mask, O, crop=crop, membership=True, semi=semi)
     x0, y0, cw, ch = crop
     compare_frustum(g, o, mask[O, y0:y0 + ch, x0:x0 + cw] != 0)
+
+
+@pytest.mark.parametrize("i", range(6))
+def test_random_batched_plan_matches_the_oracle(sess, i):
+    """A graph-captured batched plan over 1-5 clips of random, uneven shapes and lengths (from one
+    pixel and one frame up), with a random tile height and frame chunk, both colour formats and
+    both modes: every output frame of every clip against the oracle."""
+    ss, t = sess.ss, sess.torch
+    rng = np.random.default_rng(3000 + i)
+    n = int(rng.integers(1, 6))
+    cfmt = int(rng.integers(0, 2))
+    k, T = int(rng.choice([1, 3, 5, 7, 9])), int(rng.integers(0, 7))
+    mode = int(rng.choice([oracle.MODE_DENOISE, oracle.MODE_MEAN]))
+    clips, ids = [], []
+    for j in range(n):
+        W, H, F = int(rng.integers(1, 80)), int(rng.integers(1, 50)), int(rng.integers(1, 11))
+        c = synth.make_clip(str(rng.choice(["planes3", "room"])), W, H, F, seed=int(rng.integers(0, 1000)))
+        if cfmt:
+            c = synth.Clip(c.W, c.H, c.F, c.K, c.w2c, c.w2c_true, c.rgb.astype(np.float16).astype(np.float32), c.depth,
+                           c.clean, c.depth_true)
+        sess.load(20 + j, c, colour_fmt=cfmt)
+        clips.append(c)
+        ids.append(20 + j)
+    fb = int(rng.integers(0, min(c.F for c in clips)))
+    cfg = ss.ssvp_plan_config()
+    cfg.tile_rows, cfg.frame_chunk = int(rng.choice([4, 8])), int(rng.choice([1, 2, 3, 5, 16]))
+    p = sess.params(k=k, half_window=T, frame_begin=fb, frame_end=-1, mode=mode)
+    plan = ss.ssvp_plan_create(sess.ctx, p, ids, cfg)
+    try:
+        ss.ssvp_plan_launch(plan)
+        ss.ssvp_sync(sess.ctx)
+    finally:
+        ss.ssvp_plan_destroy(plan)
+    for cid, c in zip(ids, clips):
+        out = t.empty((c.F, c.H, c.W, 3), dtype=t.float32, device=sess.dev)
+        ss.ssvp_read_output(sess.ctx, cid, 0, c.F, out)
+        ss.ssvp_sync(sess.ctx)
+        out = out.cpu().numpy()
+        med = oracle.median_depth(c.depth)
+        if not np.isfinite(med):
+            continue
+        prm = oracle_params(med, k, T, mode=mode)
+        for O in range(fb, c.F):
+            o = oracle.gather_filter(oracle.ClipView.of(c), prm, O, membership=True)
+            s = compare_flagged(out[O], o)
+            assert s["differing"] <= 0.01 * s["pixels"] + 2, s
