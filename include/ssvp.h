@@ -22,8 +22,9 @@
  *     device buffers until ssvp_destroy().
  *   - Caller buffers are checked for where they live before any work touches them: one given
  *     as device memory (SSVP_MEM_DEVICE, or documented as a device buffer) must be device
- *     memory of the context's device or managed memory, one given as host memory must not be
- *     device memory; otherwise the call returns SSVP_EINVAL and queues nothing.
+ *     memory of the context's device or managed memory, one given as or documented as host
+ *     memory (cameras, shutter table, box, network weights, host outputs) must not be device
+ *     memory; otherwise the call returns SSVP_EINVAL and queues nothing.
  *   - A context is not thread-safe: one host thread per context at a time.
  */
 #ifndef SSVP_H

@@ -924,8 +924,11 @@ int ssvp_set_cameras(ssvp_ctx *ctx, int clip_id, const double *K, int per_frame_
     Clip &c = ctx->clips[clip_id];
     if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
     if (!K || !w2c) return fail(ctx, SSVP_EINVAL, "K and w2c must not be NULL");
+    int rc;
+    if ((rc = check_mem(ctx, K, SSVP_MEM_HOST, "K")) != SSVP_OK || (rc = check_mem(ctx, w2c, SSVP_MEM_HOST, "w2c")) != SSVP_OK)
+        return rc;
     std::vector<double> Kv, Wv;
-    int rc = checked_cameras(ctx, c.p.F, K, per_frame_K, w2c, Kv, Wv);
+    rc = checked_cameras(ctx, c.p.F, K, per_frame_K, w2c, Kv, Wv);
     if (rc != SSVP_OK) return rc;
     c.K.swap(Kv);
     c.w2c.swap(Wv);
@@ -946,8 +949,11 @@ int ssvp_append_frames(ssvp_ctx *ctx, int clip_id, int n, const float *rgb, cons
     if (n < 1 || n > F) return fail(ctx, SSVP_EINVAL, "n=%d must be in [1, %d] (the clip's frame count)", n, F);
     if (!rgb || !depth || !K || !w2c) return fail(ctx, SSVP_EINVAL, "rgb, depth, K and w2c must not be NULL");
     if (mem_kind != SSVP_MEM_HOST && mem_kind != SSVP_MEM_DEVICE) return fail(ctx, SSVP_EINVAL, "bad mem_kind %d", mem_kind);
+    int rc;
+    if ((rc = check_mem(ctx, K, SSVP_MEM_HOST, "K")) != SSVP_OK || (rc = check_mem(ctx, w2c, SSVP_MEM_HOST, "w2c")) != SSVP_OK)
+        return rc;
     std::vector<double> Kn, Wn;
-    int rc = checked_cameras(ctx, n, K, per_frame_K, w2c, Kn, Wn);
+    rc = checked_cameras(ctx, n, K, per_frame_K, w2c, Kn, Wn);
     if (rc != SSVP_OK) return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     if ((rc = check_mem(ctx, rgb, mem_kind, "rgb")) != SSVP_OK || (rc = check_mem(ctx, depth, mem_kind, "depth")) != SSVP_OK)
@@ -1313,7 +1319,9 @@ int ssvp_mask_from_box(ssvp_ctx *ctx, int clip_id, const double *box) {
     int rc = mask_clip(ctx, clip_id, &c);
     if (rc != SSVP_OK) return rc;
     if (!c->has_cams) return fail(ctx, SSVP_ENOCAM, "clip %d has no cameras", clip_id);
-    if (!box || !finite_all(box, 6)) return fail(ctx, SSVP_EINVAL, "box must hold 6 finite values");
+    if (!box) return fail(ctx, SSVP_EINVAL, "box is NULL");
+    if ((rc = check_mem(ctx, box, SSVP_MEM_HOST, "box")) != SSVP_OK) return rc;
+    if (!finite_all(box, 6)) return fail(ctx, SSVP_EINVAL, "box must hold 6 finite values");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     if ((rc = ensure_mask(ctx, *c)) != SSVP_OK) return rc;
     const int F = c->p.F;
@@ -1352,6 +1360,7 @@ int ssvp_read_mask(ssvp_ctx *ctx, int clip_id, uint8_t *out) {
     int rc = mask_clip(ctx, clip_id, &c);
     if (rc != SSVP_OK) return rc;
     if (!out) return fail(ctx, SSVP_EINVAL, "out is NULL");
+    if ((rc = check_mem(ctx, out, SSVP_MEM_HOST, "out")) != SSVP_OK) return rc;
     if (!c->p.mask) return fail(ctx, SSVP_EINVAL, "clip %d has no mask", clip_id);
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     const Planes &p = c->p;
@@ -1367,6 +1376,7 @@ int ssvp_read_mask(ssvp_ctx *ctx, int clip_id, uint8_t *out) {
 int ssvp_set_shutter(ssvp_ctx *ctx, const float *xi, int half_window) {
     if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
     if (!xi) return fail(ctx, SSVP_EINVAL, "xi is NULL");
+    if (int rc = check_mem(ctx, xi, SSVP_MEM_HOST, "xi"); rc != SSVP_OK) return rc;
     if (half_window < 0 || half_window > SSVP_MAX_HALF_WINDOW)
         return fail(ctx, SSVP_EINVAL, "half_window=%d must be in [0, 127]", half_window);
     const int n = 2 * half_window + 1;
@@ -1382,8 +1392,10 @@ int ssvp_frame_sharpness(ssvp_ctx *ctx, int clip_id, double *out) {
     Clip &c = ctx->clips[clip_id];
     if (!c.loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
     if (!out) return fail(ctx, SSVP_EINVAL, "out is NULL");
+    int rc = check_mem(ctx, out, SSVP_MEM_HOST, "out");
+    if (rc != SSVP_OK) return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    int rc = ensure_frame_values(ctx, c, false, true);
+    rc = ensure_frame_values(ctx, c, false, true);
     if (rc != SSVP_OK) return rc;
     CK(cudaMemcpyAsync(out, c.p.grad_sum, sizeof(double) * (size_t)c.p.F, cudaMemcpyDeviceToHost, ctx->stream),
        "cudaMemcpyAsync (gradient sums)");
@@ -1444,6 +1456,7 @@ int ssvp_clip_median_depth(ssvp_ctx *ctx, int clip_id, float *median) {
     if (clip_id < 0 || clip_id >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id %d out of range", clip_id);
     if (!ctx->clips[clip_id].loaded) return fail(ctx, SSVP_ENOCLIP, "clip %d is not loaded", clip_id);
     if (!median) return fail(ctx, SSVP_EINVAL, "median is NULL");
+    if (int rc = check_mem(ctx, median, SSVP_MEM_HOST, "median"); rc != SSVP_OK) return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     CK(cudaMemcpyAsync(median, ctx->clips[clip_id].p.median, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
     CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
@@ -1650,8 +1663,12 @@ int ssvp_plan_get_config(const ssvp_plan *plan, ssvp_plan_config *config, long l
 int ssvp_set_mlp(ssvp_ctx *ctx, const float *W1, const float *b1, const float *W2, const float *b2) {
     if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
     if (!W1 || !b1 || !W2 || !b2) return fail(ctx, SSVP_EINVAL, "weights must not be NULL");
+    int rc;
+    if ((rc = check_mem(ctx, W1, SSVP_MEM_HOST, "W1")) != SSVP_OK || (rc = check_mem(ctx, b1, SSVP_MEM_HOST, "b1")) != SSVP_OK ||
+        (rc = check_mem(ctx, W2, SSVP_MEM_HOST, "W2")) != SSVP_OK || (rc = check_mem(ctx, b2, SSVP_MEM_HOST, "b2")) != SSVP_OK)
+        return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    int rc = mlp_alloc(ctx);
+    rc = mlp_alloc(ctx);
     if (rc != SSVP_OK) return rc;
     std::vector<float> flat(ssvp::kMlpParams);
     std::memcpy(flat.data(), W1, 1024 * sizeof(float));
@@ -1672,6 +1689,13 @@ int ssvp_set_mlp(ssvp_ctx *ctx, const float *W1, const float *b1, const float *W
 int ssvp_get_mlp(ssvp_ctx *ctx, float *W1, float *b1, float *W2, float *b2) {
     if (!ctx) return fail(nullptr, SSVP_EINVAL, "ctx is NULL");
     if (!ctx->mlp_set) return fail(ctx, SSVP_EINVAL, "no network has been set or trained");
+    {
+        const float *outs[4] = {W1, b1, W2, b2};
+        const char *names[4] = {"W1", "b1", "W2", "b2"};
+        for (int i = 0; i < 4; ++i)
+            if (outs[i])
+                if (int rc = check_mem(ctx, outs[i], SSVP_MEM_HOST, names[i]); rc != SSVP_OK) return rc;
+    }
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     std::vector<float> flat(ssvp::kMlpParams);
     CK(cudaMemcpyAsync(flat.data(), ctx->mlp.master, flat.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
@@ -1775,6 +1799,7 @@ int ssvp_train(ssvp_ctx *ctx, const ssvp_params *params, const int *clip_ids, co
         return fail(ctx, SSVP_EINVAL, "bad training configuration");
     if (!clip_ids || !clean || n_clips < 1) return fail(ctx, SSVP_EINVAL, "bad clip list");
     if (params->k > 7) return fail(ctx, SSVP_EINVAL, "the learned filter supports k <= 7");
+    if (loss_out && (rc = check_mem(ctx, loss_out, SSVP_MEM_HOST, "loss_out")) != SSVP_OK) return rc;
     size_t max_px = 0;
     for (int i = 0; i < n_clips; ++i) {
         if (clip_ids[i] < 0 || clip_ids[i] >= SSVP_MAX_CLIPS) return fail(ctx, SSVP_EINVAL, "clip_id out of range");

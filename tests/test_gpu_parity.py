@@ -325,6 +325,17 @@ def test_buffers_in_the_wrong_memory_are_refused(sess, tiny):
             call()
         assert e.value.code == ss.SSVP_EINVAL and "memory" in str(e.value)
     assert not host_rec.any()
+    # arguments the library reads or writes on the host, given device addresses through the C ABI
+    import ctypes
+    lib = ss.lib
+    k_d = t.from_numpy(np.ascontiguousarray(tiny.K, np.float64)).to(sess.dev)
+    w_d = t.from_numpy(np.ascontiguousarray(tiny.w2c, np.float64)).to(sess.dev)
+    f_d = t.zeros(64, dtype=t.float64, device=sess.dev)
+    for rc in (lib.ssvp_set_cameras(sess.ctx, 0, k_d.data_ptr(), 1, w_d.data_ptr()),
+               lib.ssvp_set_shutter(sess.ctx, ctypes.cast(f_d.data_ptr(), ctypes.POINTER(ctypes.c_float)), 2),
+               lib.ssvp_frame_sharpness(sess.ctx, 0, ctypes.cast(f_d.data_ptr(), ctypes.POINTER(ctypes.c_double))),
+               lib.ssvp_clip_median_depth(sess.ctx, 0, ctypes.cast(f_d.data_ptr(), ctypes.POINTER(ctypes.c_float)))):
+        assert rc == ss.SSVP_EINVAL and "memory" in ss.ssvp_last_error(sess.ctx)
     np.testing.assert_array_equal(sess.run(0, 4, k=5, half_window=2).rgb, want)
 
 
