@@ -60,3 +60,23 @@ def test_committed_counters_summary_names_the_benchmark_launch(bench):
     for key in ("source_sha256:", "workload: fhd", "colour: fp32", "out_frames: 8", "dram_bytes_per_launch:",
                 "warp_inst_per_examined:"):
         assert key in text
+
+
+def test_clock_summary_reads_the_sampled_lines(bench):
+    """The clock record of a timed region: median and minimum SM clock, the maximum clock, the
+    median power and every throttle reason that was active in any sample."""
+    cs = bench.ClockSampler(0)
+    cs.out = "\n".join([
+        "2070, 2070, 450.5, Not Active, Not Active, Not Active, Not Active",
+        "1980, 2070, 1390.0, Not Active, Not Active, Not Active, Active",
+        "2070, 2070, 460.0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "[N/A], 2070, [N/A], Not Active, Not Active, Not Active, Not Active",
+    ])
+    s = cs.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["sm_mhz_min"] == 1980.0
+    assert s["sm_max_mhz"] == 2070.0 and s["power_w_median"] == pytest.approx(460.0)
+    assert s["reasons"] == ["sw_power_cap"]
+    empty = bench.ClockSampler(0)
+    empty.out = ""
+    assert empty.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
