@@ -49,3 +49,34 @@ def test_a_c99_program_builds_against_the_header_and_runs(tmp_path):
     run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert run.returncode == 0, (run.returncode, run.stdout, run.stderr)
     assert run.stdout.startswith("create ")
+
+
+def test_binding_structs_match_the_header_field_by_field(tmp_path):
+    """Every field of the public structures sits at the same offset in the C header and in the
+    ctypes binding, and the structures have the same size."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    import ctypes
+    import paper_2102_03011_gb300 as ss
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ssvp.h"', "int main(void) {"]
+    structs = {"ssvp_params": ss.ssvp_params, "ssvp_plan_config": ss.ssvp_plan_config,
+               "ssvp_train_config": ss.ssvp_train_config}
+    for cname, py in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
