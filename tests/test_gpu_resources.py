@@ -3,7 +3,6 @@ other shapes, appended to and unloaded, window / staged / frustum / aperture gat
 plans created and destroyed, the learned filter set and run.  After every cycle the device's free
 memory must come back to what it was after the first cycle (the library frees all it allocates;
 the first cycle also pays for one-time costs such as module loading)."""
-import numpy as np
 import pytest
 
 import synth
